@@ -1,0 +1,195 @@
+"""The reduced aperture system (EJ1) / (uT1) (oracle; test infrastructure only).
+
+Unknowns x = [E1; E2; E3] at the aperture level (Appendix A ordering).  Rows:
+
+ row 1, (m,n) in N1 (ENU14 with E_{1,Nz-1} eliminated by the top relation):
+   (-1 + tau1) E1 + (m pi h / a + vs1) E3[m,n] (m >= 1)
+     + (h/q) [ 2 kappa0^2 <cs_mn, G*u1>  -  (2 n pi / b) <cc_mn, G*w> ]  = g1
+ row 2, (m,n) in N2 (ENU24):
+   (-1 + tau2) E2 + (n pi h / b + vs2) E3[m,n] (n >= 1)
+     + (h/c) [ 2 kappa0^2 <sc_mn, G*u2>  +  (2 m pi / a) <cc_mn, G*w> ]  = g2
+ row 3, (m,n) in N3 (ENU34, with the factor h on both coupling terms):
+   (m pi h / a) E1 + (n pi h / b) E2 + (-1 + tau3) E3 = 0
+
+where u1 = sum_k E1^k cs_k, u2 = sum_k E2^k sc_k and
+w = sum_{N1} (k2 pi/b) E1^k cc_k - sum_{N2} (k1 pi/a) E2^k cc_k = div_Gamma(z x E).
+The bracketed terms are the F1 + H1 and G1 (resp. H2 and F2 + G2) blocks of
+Sec. 3 and Appendix A after the integration by parts of Sec. 5.1
+(G~1 = H~1 = -(n pi/b) I3,  G~2 = H~2 = -(m pi/a) I3).
+tau_l = -1/r_JJ (EJJ1) or -1/r_II (uTT1); vs_l = s_l / r_II is the layered
+coupling of (uT1) column 3 (zero for a homogeneous fill).
+
+Sign of the TBC operator (reading).  Taking the curl of (EGa2) gives
+curl E^s = +2 kappa0^2 int (z x E) . G0 ds (curl curl of g M is
+grad div (g M) + kappa0^2 g M off the aperture); (ENU) prints -2 kappa0^2.  With
+the printed sign the operator T of (ENU1) equals, for every evanescent Fourier
+component, the interior value of d1 E3 - d3 E1 itself, so the reduced system is
+singular in the continuum limit and the aperture absorbs instead of radiates.
+The rows above therefore carry F, G, H with the sign that follows from (EGa2):
+T(E) is the half-space exterior admittance z x curl E^s.  The printed sign of
+the data g (z x curl of incident plus reflected wave) is unaffected.
+"""
+
+import numpy as np
+import scipy.linalg as sla
+from scipy.sparse.linalg import LinearOperator, gmres
+
+from .geometry import Cavity
+from .excitation import q_norm
+from .tbc import TBCOperator
+from .zsystem import Profiles
+
+
+class ApertureSystem:
+    def __init__(self, cav: Cavity, prof: Profiles = None, tbc: TBCOperator = None):
+        self.cav = cav
+        self.prof = prof if prof is not None else Profiles(cav)
+        self.tbc = tbc if tbc is not None else TBCOperator(cav)
+        M, N = cav.M, cav.N
+        self.q, self.cn = q_norm(cav)
+        self.mx = np.arange(0, M + 1) * np.pi / cav.a      # m pi / a, m = 0..M
+        self.ny = np.arange(0, N + 1) * np.pi / cav.b      # n pi / b, n = 0..N
+
+    # -- pieces --------------------------------------------------------------
+    def w_coeffs(self, e1, e2):
+        """cc-coefficients of w = div_Gamma(z x E), k1 = 0..M, k2 = 0..N."""
+        M, N = self.cav.M, self.cav.N
+        wc = np.zeros(e1.shape[:-2] + (M + 1, N + 1), dtype=complex)
+        wc[..., :, 1:] += self.ny[None, 1:] * e1
+        wc[..., 1:, :] -= self.mx[1:, None] * e2
+        return wc
+
+    def local(self, e1, e2, e3):
+        """The cavity (non-TBC) part of (EJ1)/(uT1)."""
+        p, h = self.prof, self.cav.h
+        y1 = (-1.0 + p.tau1) * e1
+        y1[..., 1:, :] += (self.mx[1:, None] * h + p.vs1[1:, :]) * e3
+        y2 = (-1.0 + p.tau2) * e2
+        y2[..., :, 1:] += (self.ny[None, 1:] * h + p.vs2[:, 1:]) * e3
+        y3 = (self.mx[1:, None] * h) * e1[..., 1:, :] \
+            + (self.ny[None, 1:] * h) * e2[..., :, 1:] + (-1.0 + p.tau3) * e3
+        return y1, y2, y3
+
+    def apply(self, x):
+        cav = self.cav
+        e1, e2, e3 = cav.split(x)
+        y1, y2, y3 = self.local(e1, e2, e3)
+        k2 = 2.0 * cav.kappa0 ** 2
+        h = cav.h
+        U1 = self.tbc.apply('cs', e1)
+        U2 = self.tbc.apply('sc', e2)
+        W = self.tbc.apply('cc', self.w_coeffs(e1, e2))
+        y1 = y1 + (h / self.q)[:, None] * (k2 * U1 - 2.0 * self.ny[None, 1:] * W[:, 1:])
+        y2 = y2 + (h / self.cn)[None, :] * (k2 * U2 + 2.0 * self.mx[1:, None] * W[1:, :])
+        return cav.join(y1, y2, y3)
+
+    def dense(self):
+        """Assemble the full n_ap x n_ap matrix (small grids only)."""
+        cav = self.cav
+        eye = np.eye(cav.n_ap, dtype=complex)
+        e1, e2, e3 = cav.split(eye)
+        y1, y2, y3 = self.local(e1, e2, e3)
+        return cav.join(y1, y2, y3).T + self.dense_tbc()
+
+    def dense_tbc(self):
+        """The TBC part alone (F, G, H blocks of (ENUGa)) as a dense matrix."""
+        cav = self.cav
+        n1, n2 = cav.n1, cav.n2
+        nap = cav.n_ap
+        A = np.zeros((nap, nap), dtype=complex)
+        k2 = 2.0 * cav.kappa0 ** 2
+        h = cav.h
+        I1 = self.tbc.dense('cs')            # [m, n, k1, k2] over (M+1, N) x (M+1, N)
+        I2 = self.tbc.dense('sc')            # (M, N+1) x (M, N+1)
+        I3 = self.tbc.dense('cc')            # (M+1, N+1) x (M+1, N+1)
+        s1 = (h / self.q)[:, None]
+        s2 = (h / self.cn)[None, :]
+        # row 1 <- E1 via I1 and via w (k2 pi / b) I3
+        B11 = k2 * s1[:, :, None, None] * I1
+        B11 -= (s1 * 2.0 * self.ny[None, 1:])[:, :, None, None] * \
+            I3[:, 1:, :, 1:] * self.ny[None, None, None, 1:]
+        # row 1 <- E2 via w: -(k1 pi/a) I3
+        B12 = (s1 * 2.0 * self.ny[None, 1:])[:, :, None, None] * \
+            I3[:, 1:, 1:, :] * self.mx[None, None, 1:, None]
+        # row 2 <- E1 via w
+        B21 = (s2 * 2.0 * self.mx[1:, None])[:, :, None, None] * \
+            I3[1:, :, :, 1:] * self.ny[None, None, None, 1:]
+        # row 2 <- E2 via I2 and w
+        B22 = k2 * s2[:, :, None, None] * I2
+        B22 -= (s2 * 2.0 * self.mx[1:, None])[:, :, None, None] * \
+            I3[1:, :, 1:, :] * self.mx[None, None, 1:, None]
+        A[:n1, :n1] += B11.reshape(n1, n1)
+        A[:n1, n1:n1 + n2] += B12.reshape(n1, n2)
+        A[n1:n1 + n2, :n1] += B21.reshape(n2, n1)
+        A[n1:n1 + n2, n1:n1 + n2] += B22.reshape(n2, n2)
+        return A
+
+    def block_diagonal(self):
+        """The 3x3 (2x2 / 1x1 at m = 0 or n = 0) diagonal blocks of the reduced
+        matrix that couple E1, E2, E3 of one mode (m, n); B[m, n, r, c] with
+        component order (E1, E2, E3) and absent components left as identity."""
+        cav = self.cav
+        M, N, h = cav.M, cav.N, cav.h
+        k2 = 2.0 * cav.kappa0 ** 2
+        p = self.prof
+        d1 = self.tbc.diag('cs')       # (M+1, N)   n = 1..N
+        d2 = self.tbc.diag('sc')       # (M, N+1)   m = 1..M
+        d3 = self.tbc.diag('cc')       # (M+1, N+1)
+        B = np.zeros((M + 1, N + 1, 3, 3), dtype=complex)
+        for r in range(3):
+            B[:, :, r, r] = 1.0
+        mx = self.mx[:, None]
+        ny = self.ny[None, :]
+        sq = (h / self.q)[:, None]
+        sc = (h / self.cn)[None, :]
+        # E1 row (n >= 1)
+        B[:, 1:, 0, 0] = (-1.0 + p.tau1) + sq * (k2 * d1 - 2.0 * ny[:, 1:] ** 2 * d3[:, 1:])
+        B[1:, 1:, 0, 1] = (sq * 2.0 * ny * mx * d3)[1:, 1:]
+        B[1:, 1:, 0, 2] = mx[1:] * h + p.vs1[1:, :]
+        # E2 row (m >= 1)
+        B[1:, 1:, 1, 0] = (sc * 2.0 * mx * ny * d3)[1:, 1:]
+        B[1:, :, 1, 1] = (-1.0 + p.tau2) + sc * (k2 * d2 - 2.0 * mx[1:] ** 2 * d3[1:, :])
+        B[1:, 1:, 1, 2] = ny[:, 1:] * h + p.vs2[:, 1:]
+        # E3 row
+        B[1:, 1:, 2, 0] = (mx * h)[1:] + 0 * ny[:, 1:]
+        B[1:, 1:, 2, 1] = (ny * h)[:, 1:] + 0 * mx[1:]
+        B[1:, 1:, 2, 2] = -1.0 + p.tau3
+        return B
+
+    def preconditioner(self):
+        """x -> (block diagonal)^{-1} x, used only to speed up GMRES."""
+        cav = self.cav
+        Binv = np.linalg.inv(self.block_diagonal())
+
+        def apply(v):
+            e1, e2, e3 = cav.split(v)
+            M, N = cav.M, cav.N
+            V = np.zeros((M + 1, N + 1, 3), dtype=complex)
+            V[:, 1:, 0] = e1
+            V[1:, :, 1] = e2
+            V[1:, 1:, 2] = e3
+            Y = np.einsum('mnrc,mnc->mnr', Binv, V)
+            return cav.join(Y[:, 1:, 0], Y[1:, :, 1], Y[1:, 1:, 2])
+        return apply
+
+    # -- solves --------------------------------------------------------------
+    def solve_dense(self, b):
+        A = self.dense()
+        return sla.solve(A, np.asarray(b).T).T
+
+    def solve_gmres(self, b, rtol=1e-13, restart=200, maxiter=200):
+        """Restarted GMRES (SciPy) on the matrix-free operator with the block
+        diagonal as preconditioner; the true residual is recomputed afterwards.
+        Returns (x, relative residuals)."""
+        nap = self.cav.n_ap
+        op = LinearOperator((nap, nap), matvec=self.apply, dtype=complex)
+        pre = LinearOperator((nap, nap), matvec=self.preconditioner(), dtype=complex)
+        b = np.atleast_2d(b)
+        xs, res = [], []
+        for bi in b:
+            x, info = gmres(op, bi, rtol=rtol, atol=0.0, restart=restart,
+                            maxiter=maxiter, M=pre)
+            r = np.linalg.norm(self.apply(x) - bi) / np.linalg.norm(bi)
+            xs.append(x)
+            res.append(r)
+        return np.array(xs), np.array(res)

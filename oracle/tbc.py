@@ -1,0 +1,163 @@
+"""Singular integrals of the transparent boundary condition by the FFT route of
+Sec. 5 (oracle; test infrastructure only).
+
+Sec. 5.1 reduces every coefficient of (sig1)-(sig3) and their Appendix A
+counterparts to three integrals over the aperture Gamma = [0,a] x [0,b]:
+
+    I1^{mn}_k = <cs_mn, G * cs_k>,  I2^{mn}_k = <sc_mn, G * sc_k>,
+    I3^{mn}_k = <cc_mn, G * cc_k>,
+
+with cs_k(y) = cos(k1 pi y1/a) sin(k2 pi y2/b) etc. and the weakly singular kernel
+g(x, y) = exp(i kappa0 |x-y|)/(4 pi |x-y|).  Sec. 5.2 evaluates the inner
+integral I_k(x) = int F(y) G(x-y) dy as F^{-1}(F(F) F(G)) and the outer integral
+by the trapezoid rule.  The discrete rule written out here (and binding for the
+CUDA path) is:
+
+  * the convolution is periodised with period Lx = pad*a, Ly = pad*b; for x, y in
+    Gamma and the truncation radius R = sqrt(2) max(a,b) no image contributes
+    while pad*min(a,b) > min(a,b) + R;
+  * the inverse transform is the Fourier series on that torus truncated to the
+    symmetric box |j1| <= Px/2 - 1, |j2| <= Py/2 - 1 with Px = pad*Nx,
+    Py = pad*Ny (so the torus grid of spacing a/Nx contains the aperture
+    nodes):  I_k(x) = (Lx Ly)^{-1} sum_j F(F)(j/L) F(G)(|j/L|) exp(2 pi i j.x/L);
+  * F(F) is the exact transform of the truncated basis function, separable into
+    1-D factors  f^c_k(xi) = [E(xi - k/2a) + E(xi + k/2a)]/2 and
+    f^s_k(xi) = [E(xi - k/2a) - E(xi + k/2a)]/(2i) with
+    E(nu) = int_0^a exp(-2 pi i nu y) dy = (1 - exp(-2 pi i nu a))/(2 pi i nu),
+    E(0) = a  (the paper's closed form for F(F), with the missing factor i
+    restored);
+  * F(G) is the radial integral of `khat`;
+  * the outer integral is the trapezoid rule on x1_p = p a/Nx, x2_q = q b/Ny.
+
+Each step is a dense matrix here (numpy matmul as the only library step).
+"""
+
+import numpy as np
+
+from .geometry import Cavity
+from .khat import khat
+
+
+def freq_index(P):
+    """Symmetric frequency box -(P/2-1) .. (P/2-1) (the Nyquist line is left out
+    so that the box, and with it every mirror symmetry of the problem, is
+    symmetric)."""
+    h = P // 2 - 1
+    return np.arange(-h, h + 1)
+
+
+def _E(D, a, pad):
+    """E(nu) at nu = D / (2 pad a) for integer D."""
+    D = np.asarray(D, dtype=float)
+    nu = D / (2.0 * pad * a)
+    safe = np.where(D == 0, 1.0, nu)
+    val = (1.0 - np.exp(-2j * np.pi * safe * a)) / (2j * np.pi * safe)
+    return np.where(D == 0, a + 0j, val)
+
+
+def phi_matrix(kind, ks, js, a, pad):
+    """Phi[j, k] = exact 1-D Fourier transform at xi = j / (pad a) of
+    cos(k pi y / a) 1_[0,a](y)  (kind 'c')  or  sin(k pi y / a) 1_[0,a](y) ('s')."""
+    js = np.asarray(js)[:, None]
+    ks = np.asarray(ks)[None, :]
+    em = _E(2 * js - pad * ks, a, pad)
+    ep = _E(2 * js + pad * ks, a, pad)
+    if kind == 'c':
+        return 0.5 * (em + ep)
+    return (em - ep) / 2j
+
+
+def idft_matrix(nodes, js, P):
+    """X[p, j] = exp(2 pi i j p / P): the torus Fourier series at x_p = p a/Nx."""
+    return np.exp(2j * np.pi * np.outer(nodes, js) / P)
+
+
+def trap_matrix(kind, ms, n_int, a):
+    """T[m, p] = w_p cos(m pi p / n_int) or w_p sin(...), trapezoid weights
+    w_p = (a / n_int) (1/2 at p = 0 and p = n_int)."""
+    p = np.arange(n_int + 1)
+    w = np.full(n_int + 1, a / n_int)
+    w[0] *= 0.5
+    w[-1] *= 0.5
+    arg = np.pi * np.outer(ms, p) / n_int
+    base = np.cos(arg) if kind == 'c' else np.sin(arg)
+    return base * w[None, :]
+
+
+class TBCOperator:
+    """The three convolution-projection maps of a cavity, as dense factors.
+
+    apply(kind, C):  C[k1, k2] (coefficients of the basis of type `kind`,
+    'cs', 'sc' or 'cc', over the full ranges k1 = 0..M or 1..M etc.) ->
+    out[m, n] = sum_k I^{mn}_k C[k] over the same index ranges.
+    """
+
+    def __init__(self, cav: Cavity, kh=None):
+        self.cav = cav
+        a, b, nx, ny, pad = cav.a, cav.b, cav.nx, cav.ny, cav.pad
+        self.Px, self.Py = pad * nx, pad * ny
+        self.jx, self.jy = freq_index(self.Px), freq_index(self.Py)
+        self.Lx, self.Ly = pad * a, pad * b
+        R = np.sqrt(2.0) * max(a, b)
+        if pad * min(a, b) <= min(a, b) + R:
+            raise ValueError("period too short for the truncated kernel")
+        if kh is None:
+            kh = self._kernel_table(R)
+        self.Kh = kh
+        M, N = cav.M, cav.N
+        rng = {'c': (np.arange(0, M + 1), np.arange(0, N + 1)),
+               's': (np.arange(1, M + 1), np.arange(1, N + 1))}
+        self._fx, self._fy = {}, {}
+        self._tx, self._ty = {}, {}
+        for kind in 'cs':
+            kx = rng[kind][0]
+            ky = rng[kind][1]
+            self._fx[kind] = phi_matrix(kind, kx, self.jx, a, pad)
+            self._fy[kind] = phi_matrix(kind, ky, self.jy, b, pad)
+            self._tx[kind] = trap_matrix(kind, kx, nx, a)
+            self._ty[kind] = trap_matrix(kind, ky, ny, b)
+        self._ex = idft_matrix(np.arange(nx + 1), self.jx, self.Px) / self.Lx
+        self._ey = idft_matrix(np.arange(ny + 1), self.jy, self.Py) / self.Ly
+
+    def _kernel_table(self, R):
+        """F(G) on the frequency box, evaluated once per distinct radius: the
+        table is even in j1 and in j2 (and depends on j1^2 + j2^2 only when the
+        two periods agree)."""
+        ax, ay = np.abs(self.jx), np.abs(self.jy)
+        if self.Lx == self.Ly:
+            key = ax[:, None] ** 2 + ay[None, :] ** 2
+            uniq, inv = np.unique(key, return_inverse=True)
+            vals = khat(np.sqrt(uniq) / self.Lx, self.cav.kappa0, R)
+            return vals[inv].reshape(key.shape)
+        ux, ix = np.unique(ax, return_inverse=True)
+        uy, iy = np.unique(ay, return_inverse=True)
+        rho = np.sqrt((ux[:, None] / self.Lx) ** 2 + (uy[None, :] / self.Ly) ** 2)
+        q = khat(rho, self.cav.kappa0, R)
+        return q[ix][:, iy]
+
+    def factors(self, kind):
+        """X[m, j1] (projection after inverse DFT) and Phi[j1, k1] per axis."""
+        kx, ky = kind[0], kind[1]
+        Xx = self._tx[kx] @ self._ex
+        Xy = self._ty[ky] @ self._ey
+        return (Xx, self._fx[kx]), (Xy, self._fy[ky])
+
+    def apply(self, kind, C):
+        """Matrix-free I C for one coefficient array (or a batch, leading axes)."""
+        kx, ky = kind[0], kind[1]
+        V = self._fx[kx] @ C @ self._fy[ky].T           # frequency box
+        V = V * self.Kh
+        U = self._ex @ V @ self._ey.T                      # aperture nodes
+        return self._tx[kx] @ U @ self._ty[ky].T           # trapezoid projection
+
+    def diag(self, kind):
+        """The diagonal I^{mn}_{mn} over the full index ranges of `kind`:
+        sum_j X(m,j1) Phi(j1,m) Kh(j1,j2) Y(n,j2) Psi(j2,n)."""
+        (Xx, Fx), (Xy, Fy) = self.factors(kind)
+        return (Xx * Fx.T) @ self.Kh @ (Xy * Fy.T).T
+
+    def dense(self, kind):
+        """I[m, n, k1, k2] for the full index ranges of `kind` (small grids)."""
+        (Xx, Fx), (Xy, Fy) = self.factors(kind)
+        T1 = np.einsum('mj,jl,jk->mkl', Xx, self.Kh, Fx, optimize=True)
+        return np.einsum('nl,mkl,lq->mnkq', Xy, T1, Fy, optimize=True)

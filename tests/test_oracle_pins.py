@@ -1,0 +1,337 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Every test here runs on the CPU.  None of them compares the oracle with itself:
+each checks it against a closed form, an independent library routine with a
+different algorithm, a brute-force solve of the unreduced equations, an exact
+symmetry, or a convergence order to a continuous solution.
+"""
+
+import numpy as np
+import pytest
+import scipy.fft as sfft
+from scipy import integrate, special
+
+from oracle.aperture import ApertureSystem
+from oracle.brute import solve_unreduced
+from oracle.excitation import g_tilde, incident, rhs
+from oracle.field import field, level_coeffs, synth_mats
+from oracle.geometry import Cavity, Layer
+from oracle.khat import khat, khat_zero
+from oracle.rcs import backscatter
+from oracle.tbc import TBCOperator
+from oracle.zsystem import Profiles, _e3_profile_homogeneous, e3_profile, tangential_profiles
+
+
+# ---------------------------------------------------------------- z-direction
+@pytest.mark.parametrize("kap,m,n", [(7.0, 1, 2), (30.0, 3, 1), (3.0, 9, 9)])
+def test_last_pivot_closed_form(kap, m, n):
+    """T1: the last pivot of tridiag(1, sigma-2, 1) (A1 + D, Sec. 3) is
+    sin((J+1)phi)/sin(J phi) with 2 cos(phi) = sigma - 2; for A2 + D (Neumann
+    first row) it is -cos((J+1/2)t)/cos((J-1/2)t) with 2 cos(t) = 2 - sigma.
+    The oracle's top relation is tau = -1/r_JJ (EJJ1)."""
+    cav = Cavity(1.0, 1.0, 0.5, 16, 16, 24, kap)
+    s = cav.sigma(0, cav.lam(m, n))
+    J = cav.nz - 1
+    phi = np.arccos((s - 2) / 2 + 0j)
+    r1 = np.sin((J + 1) * phi) / np.sin(J * phi)
+    P, Q = tangential_profiles(cav, m, n, 0.0)
+    assert abs(P[cav.nz - 1] - (-1 / r1)) < 1e-12 * max(1, abs(1 / r1))
+    assert np.all(Q == 0)
+    th = np.arccos((2 - s) / 2 + 0j)
+    r2 = -np.cos((J + .5) * th) / np.cos((J - .5) * th)
+    P3 = _e3_profile_homogeneous(cav, m, n)
+    assert abs(P3[cav.nz - 1] - (-1 / r2)) < 1e-12 * max(1, abs(1 / r2))
+    # the general (layer-capable) E3 assembly agrees on a one-layer fill
+    P3b, _ = e3_profile(cav, m, n)
+    assert np.allclose(P3b, P3, rtol=1e-13, atol=1e-15)
+
+
+def _order(errs):
+    errs = np.asarray(errs)
+    return np.log2(errs[:-1] / errs[1:])
+
+
+def test_homogeneous_profiles_converge_to_continuous_modes():
+    """T2: in an empty homogeneous cavity with unit aperture value the FD
+    profiles approach sin(g(x3+c))/sin(g c) (E1, Dirichlet bottom, second order)
+    and cos(g(x3+c))/cos(g c) (E3, Neumann bottom imposed as E_{3,0} = E_{3,1},
+    first order), g^2 = kappa^2 - lambda_mn (ode1x3)/(ode3x3)."""
+    kap, m, n = 7.0, 1, 1
+    e1, e3 = [], []
+    for nz in (16, 32, 64, 128):
+        cav = Cavity(1.0, 1.0, 0.5, 4, 4, nz, kap)
+        g = np.sqrt(kap ** 2 - cav.lam(m, n) + 0j)
+        z = -cav.c + np.arange(nz + 1) * cav.h
+        P, _ = tangential_profiles(cav, m, n, 0.0)
+        e1.append(np.abs(P - np.sin(g * (z + cav.c)) / np.sin(g * cav.c)).max())
+        P3 = _e3_profile_homogeneous(cav, m, n)
+        e3.append(np.abs(P3 - np.cos(g * (z + cav.c)) / np.cos(g * cav.c)).max())
+    assert np.all(_order(e1) > 1.9)
+    assert np.all(_order(e3) > 0.95)
+    assert e1[-1] < 5e-4 and e3[-1] < 2e-2
+
+
+def _two_layer_continuous(cav, m, eps1, eps2, c1, kap0):
+    """Continuous E3 and the E3-driven E1 profile of mode (m, 1) in a two-layer
+    cavity: Helmholtz in each layer, eps1 u3 = eps2 v3 and d3 u3 = d3 v3 at the
+    interface (con31, con61), u1 = v1 and
+    d3 u1 - d3 v1 = (m pi / a)(u3 - v3) (con11, con41), E1(-c) = 0,
+    d3 E3(-c) = 0, E3(0) = 1, E1(0) = 0."""
+    lam = cav.lam(m, 1)
+    g1 = np.sqrt(kap0 ** 2 * eps1 - lam + 0j)
+    g2 = np.sqrt(kap0 ** 2 * eps2 - lam + 0j)
+    c2 = cav.c - c1
+    v3c, dv3 = np.cos(g2 * c2), -g2 * np.sin(g2 * c2)
+    B, C = eps2 / eps1 * v3c, dv3
+    top = B * np.cos(g1 * c1) + C * np.sin(g1 * c1) / g1
+    A, B, C, v3c = 1 / top, B / top, C / top, v3c / top
+
+    def e3(z):
+        return np.where(z > -c1, B * np.cos(g1 * (z + c1)) + C * np.sin(g1 * (z + c1)) / g1,
+                        A * np.cos(g2 * (z + cav.c)))
+    mu = m * np.pi / cav.a
+    jump = B - v3c
+    s1 = np.sin(g1 * c1) / g1
+    D = -(mu * jump * s1) / (np.sin(g2 * c2) * np.cos(g1 * c1) + g2 * np.cos(g2 * c2) * s1)
+    F, G = D * np.sin(g2 * c2), D * g2 * np.cos(g2 * c2) + mu * jump
+
+    def q1(z):
+        return np.where(z > -c1, F * np.cos(g1 * (z + c1)) + G * np.sin(g1 * (z + c1)) / g1,
+                        D * np.sin(g2 * (z + cav.c)))
+    return e3, q1
+
+
+def test_layered_profiles_converge_to_transmission_solution():
+    """The discrete interface rows (con32), (con61) and (con42-2) converge, at
+    first order (one-sided differences at the interface), to the continuous
+    two-layer solution -- including the E3-driven E1 profile Q (the s_l
+    coupling of (uTT1)).  A wrong sign or factor in any interface row fails."""
+    eps1, eps2, kap, m = 4 + 1j, 2 + 0.5j, 7.0, 2
+    err3, errq = [], []
+    for nz in (32, 64, 128, 256):
+        nl = nz // 2
+        cav = Cavity(1.0, 1.0, 0.5, 4, 4, nz, kap,
+                     layers=[Layer(nl, eps1), Layer(nz - nl, eps2)])
+        e3c, q1c = _two_layer_continuous(cav, m, eps1, eps2, nl * cav.h, kap)
+        z = -cav.c + np.arange(nz + 1) * cav.h
+        P3, _ = e3_profile(cav, m, 1)
+        _, Q1 = tangential_profiles(cav, m, 1, m * np.pi / cav.a, P3)
+        err3.append(np.abs(P3[1:] - e3c(z[1:] + 1e-12)).max())
+        errq.append(np.abs(Q1[1:] - q1c(z[1:])).max())
+    assert np.all(_order(err3) > 0.9) and np.all(_order(errq) > 0.85)
+    assert err3[-1] < 0.03 and errq[-1] < 0.003
+
+
+@pytest.mark.parametrize("layers", [[], [Layer(3, 4 + 1j), Layer(3, 2 + .5j), Layer(2, 1.0)]])
+def test_reduction_matches_unreduced_system(layers):
+    """T3: Gaussian elimination onto the aperture, (EJ1)/(uT1), followed by the
+    back-substitution (EInter) reproduces the dense solve of the full unreduced
+    system (all levels, all modes, (ENUGa)/(uNUGa) rows)."""
+    cav = Cavity(1.0, 1.0, 0.5, 4, 4, 8, 6.0, layers=layers)
+    sysm = ApertureSystem(cav)
+    b = rhs(cav, 0.3, 0.7, 0.2)
+    x = sysm.solve_dense(b)
+    bru = solve_unreduced(cav, sysm.dense_tbc(), b)
+    scale = np.abs(x).max()
+    ap = np.concatenate([bru[1][:, -1], bru[2][:, -1], bru[3][:, -1]])
+    assert np.abs(ap - x).max() < 1e-12 * scale
+    for j in range(1, cav.nz + 1):
+        c1, c2, c3 = level_coeffs(cav, sysm.prof, x, j)
+        assert np.abs(c1.ravel() - bru[1][:, j - 1]).max() < 1e-12 * scale
+        assert np.abs(c2.ravel() - bru[2][:, j - 1]).max() < 1e-12 * scale
+        assert np.abs(c3.ravel() - bru[3][:, j - 1]).max() < 1e-12 * scale
+
+
+# ---------------------------------------------------------------- transforms
+def test_synthesis_matches_scipy_dct_dst_type1():
+    """T4: the explicit cos/sin synthesis of (E123F) on the grid equals
+    SciPy's type-I DCT/DST (a different algorithm: FFT based)."""
+    rng = np.random.default_rng(0)
+    cav = Cavity(1.0, 1.0, 0.5, 16, 8, 4, 3.0)
+    cosx, sinx, cosy, siny = synth_mats(cav)
+    c = rng.standard_normal((cav.M + 1, cav.N)) + 1j * rng.standard_normal((cav.M + 1, cav.N))
+    ref = cosx @ c @ siny.T
+    # DCT-I over x (length nx+1, coefficient nx set to 0), DST-I over y
+    cpad = np.zeros((cav.nx + 1, cav.N), dtype=complex)
+    cpad[:cav.M + 1] = c
+    cpad[0] *= 2.0
+    tx = sfft.dct(cpad, type=1, axis=0) / 2.0
+    # dct type 1: y_k = x_0 + (-1)^k x_{N-1} + 2 sum x_n cos(...): undo the
+    # scaling of the first entry and the zero last coefficient
+    ty = sfft.dst(tx, type=1, axis=1) / 2.0
+    assert np.allclose(ty, ref, atol=1e-12)
+
+
+def test_gtilde_trapezoid_second_order():
+    """T9: the trapezoid test integral g~ of (nosig) converges at second order
+    to the closed form int_0^a cos(m pi x/a) e^{i a1 x} dx *
+    int_0^b sin(n pi y/b) e^{i a2 y} dy."""
+    a1, a2, m, n = 5.3, -2.1, 3, 2
+
+    def exact1(k, al, L, kind):
+        s = np.array([al - k * np.pi / L, al + k * np.pi / L])
+        f = np.where(s == 0, L, (np.exp(1j * s * L) - 1) / (1j * np.where(s == 0, 1, s)))
+        return 0.5 * (f[0] + f[1]) if kind == 'c' else (f[1] - f[0]) / 2j
+    ex = exact1(m, a1, 1.0, 'c') * exact1(n, a2, 1.0, 's')
+    errs = []
+    for nx in (16, 32, 64, 128):
+        cav = Cavity(1.0, 1.0, 0.5, nx, nx, 4, 1.0)
+        gt1, _ = g_tilde(cav, a1, a2)
+        errs.append(abs(gt1[m, n - 1] - ex))
+    assert np.all(_order(errs) > 1.9)
+
+
+# ---------------------------------------------------------------- kernel
+def test_khat_at_zero_frequency():
+    """T5a: F(G)(0) = 1/2 int_0^R e^{i k r} dr = (e^{i k R} - 1)/(2 i k)."""
+    for kap in (0.5, 8 * np.pi, 160.0):
+        R = np.sqrt(2.0)
+        assert abs(khat(np.array([0.0]), kap, R)[0] - khat_zero(kap, R)) < 1e-14 * abs(khat_zero(kap, R)) + 1e-15
+
+
+def test_khat_static_limit_struve():
+    """T5b: for kappa0 = 0, 1/2 int_0^R J0(c r) dr = (1/2c) [x J0(x) +
+    (pi x/2)(J1(x) H0(x) - J0(x) H1(x))], x = c R (Struve functions H)."""
+    R = np.sqrt(2.0)
+    rho = np.array([0.3, 2.0, 17.5, 90.25])
+    c = 2 * np.pi * rho
+    x = c * R
+    ref = (x * special.j0(x) + np.pi * x / 2 * (special.j1(x) * special.struve(0, x)
+                                                 - special.j0(x) * special.struve(1, x))) / (2 * c)
+    got = khat(rho, 0.0, R)
+    assert np.allclose(got.real, ref, rtol=1e-11, atol=1e-14)
+    assert np.abs(got.imag).max() < 1e-15
+
+
+def test_khat_against_adaptive_quadrature():
+    """T5c: against QUADPACK's adaptive Gauss-Kronrod on the real and imaginary
+    parts (a different quadrature rule and subdivision)."""
+    R, kap = np.sqrt(2.0), 25.0
+    for rho in (0.0, 1.7, 3.9, 12.25):
+        c = 2 * np.pi * rho
+        re = integrate.quad(lambda r: special.j0(c * r) * np.cos(kap * r), 0, R,
+                            limit=400, epsabs=1e-15, epsrel=1e-13)[0]
+        im = integrate.quad(lambda r: special.j0(c * r) * np.sin(kap * r), 0, R,
+                            limit=400, epsabs=1e-15, epsrel=1e-13)[0]
+        ref = 0.5 * (re + 1j * im)
+        assert abs(khat(np.array([rho]), kap, R)[0] - ref) < 1e-12
+
+
+def test_static_self_potential_of_the_square():
+    """The kappa0 -> 0 limit of I3^{00}_{00} is the electrostatic self-potential
+    of the unit square, (1/4 pi)[4 ln(1 + sqrt 2) - (4/3)(sqrt 2 - 1)].  The
+    discrete rule (periodised FFT convolution with the closed-form basis
+    transform and trapezoid outer rule, Sec. 5.2) converges to it at about
+    second order; this fixes every prefactor of the rule (1/2 in F(G), 1/L^2,
+    E(nu), the trapezoid weights)."""
+    exact = (4 * np.log(1 + np.sqrt(2)) - 4 / 3 * (np.sqrt(2) - 1)) / (4 * np.pi)
+    errs = []
+    for nx in (8, 16, 32):
+        cav = Cavity(1.0, 1.0, 0.5, nx, nx, 4, 1e-9)
+        errs.append(abs(TBCOperator(cav).diag('cc')[0, 0] - exact) / exact)
+    assert errs[-1] < 2e-3
+    assert np.all(_order(errs) > 1.5)
+
+
+def test_tbc_row_is_the_exterior_admittance():
+    """For an evanescent mode the TBC part of row 1 of (EJ1) must be -h times
+    the half-space admittance z x curl E^s of (ENU1): for E1 alone that is
+    h (kappa0^2 - (n pi/b)^2) / gamma, gamma^2 = lambda_mn - kappa0^2 (the field
+    above the aperture decays upward).  This fixes the sign of the TBC operator
+    (see the reading in oracle.aperture) and the magnitude of I1 and I3."""
+    nx = 64
+    kap = 2 * np.pi * nx / 10
+    cav = Cavity(1.0, 1.0, 0.5, nx, nx, 8, kap)
+    sysm = ApertureSystem(cav)
+    tb = sysm.tbc
+    d1, d3 = tb.diag('cs'), tb.diag('cc')
+    k2 = 2 * kap ** 2
+    for (m, n) in ((32, 32), (48, 48), (3, 60)):
+        g = np.sqrt((m * np.pi) ** 2 + (n * np.pi) ** 2 - kap ** 2)
+        q = cav.a * cav.b / 4
+        row = cav.h / q * (k2 * d1[m, n - 1] - 2 * (n * np.pi) ** 2 * d3[m, n])
+        adm = cav.h * (kap ** 2 - (n * np.pi) ** 2) / g
+        assert abs(row / adm - 1) < 0.06
+    # the block diagonal used by the preconditioner is the matrix diagonal
+    B = sysm.block_diagonal()
+    cav2 = Cavity(1.0, 1.0, 0.5, 8, 8, 8, 9.0)
+    s2 = ApertureSystem(cav2)
+    A = s2.dense()
+    B2 = s2.block_diagonal()
+    N = cav2.N
+    assert abs(B2[3, 4, 0, 0] - A[3 * N + 3, 3 * N + 3]) < 1e-14
+    assert B.shape == (cav.M + 1, cav.N + 1, 3, 3)
+
+
+# ---------------------------------------------------------------- whole solve
+def test_normal_incidence_selection_rules():
+    """T6: at normal incidence with p = x_hat on a square aperture the problem
+    is even under x1 -> a - x1 (as a polar vector field: E1 even, E2, E3 odd)
+    and under x2 -> b - x2 (E1, E3 even, E2 odd); so only E1 modes with m even,
+    n odd, E2 modes with m even, n odd and E3 modes with m even, n odd are
+    nonzero.  The symmetric frequency box keeps this exact."""
+    cav = Cavity(1.0, 1.0, 0.5, 16, 16, 16, 4 * np.pi)
+    x = ApertureSystem(cav).solve_dense(rhs(cav, 0.0, 0.0, 0.0))
+    e1, e2, e3 = cav.split(x)
+    M = cav.M
+    scale = np.abs(x).max()
+    m1, n1 = np.arange(0, M + 1)[:, None], np.arange(1, M + 1)[None, :]
+    m2, n2 = np.arange(1, M + 1)[:, None], np.arange(0, M + 1)[None, :]
+    m3, n3 = np.arange(1, M + 1)[:, None], np.arange(1, M + 1)[None, :]
+    assert np.abs(e1[(m1 % 2 == 1) | (n1 % 2 == 0)]).max() < 1e-12 * scale
+    assert np.abs(e2[(m2 % 2 == 1) | (n2 % 2 == 0)]).max() < 1e-12 * scale
+    assert np.abs(e3[(m3 % 2 == 1) | (n3 % 2 == 0)]).max() < 1e-12 * scale
+    assert np.abs(e1[(m1 % 2 == 0) & (n1 % 2 == 1)]).max() > 0.1 * scale
+
+
+def test_gmres_agrees_with_dense_solve():
+    """The matrix-free operator (FFT route as dense factors) with GMRES agrees
+    with the assembled matrix and a direct solve."""
+    cav = Cavity(1.0, 1.0, 0.5, 16, 16, 12, 2 * np.pi * 16 / 8)
+    sysm = ApertureSystem(cav)
+    b = rhs(cav, 0.4, 1.1, 0.3)
+    xd = sysm.solve_dense(b)
+    xg, res = sysm.solve_gmres(b, rtol=1e-13)
+    assert res[0] < 1e-12
+    assert np.linalg.norm(xg[0] - xd) < 1e-11 * np.linalg.norm(xd)
+    A = sysm.dense()
+    v = np.random.default_rng(1).standard_normal(cav.n_ap) + 0j
+    assert np.allclose(A @ v, sysm.apply(v), rtol=1e-12, atol=1e-12)
+
+
+def test_rcs_square_swap_symmetry():
+    """On a square aperture with Nx = Ny, reflection across the diagonal swaps
+    E1 and E2; at normal incidence an x-polarised and a y-polarised wave give
+    the same backscatter RCS (theta-theta at phi = 0 vs phi-phi at phi = 0)."""
+    cav = Cavity(1.0, 1.0, 0.5, 12, 12, 12, 3 * np.pi)
+    sysm = ApertureSystem(cav)
+    xa = sysm.solve_dense(rhs(cav, 0.0, 0.0, 0.0))            # p = x_hat
+    xb = sysm.solve_dense(rhs(cav, 0.0, 0.0, np.pi / 2))      # p = y_hat
+    sa = backscatter(cav, xa, 0.0, 0.0, 'theta')
+    sb = backscatter(cav, xb, 0.0, 0.0, 'phi')
+    assert sa > 0 and abs(sa - sb) < 1e-11 * sa
+    # and the E1 <-> E2 swap of the solutions themselves
+    e1a, e2a, e3a = cav.split(xa)
+    e1b, e2b, e3b = cav.split(xb)
+    assert np.allclose(e1a.T, e2b, atol=1e-12 * np.abs(xa).max())
+
+
+def test_incident_wave_is_transverse():
+    """p . q = 0 for the Sec. 7 parametrisation, and beta >= 0 (Sec. 2)."""
+    for th, ph, al in ((0.3, 1.2, 0.0), (1.0, 4.0, 0.7), (0.0, 0.0, 0.0)):
+        a1, a2, beta, p = incident(5.0, th, ph, al)
+        assert abs(a1 * p[0] + a2 * p[1] - beta * p[2]) < 1e-14
+        assert beta >= 0 and abs(np.linalg.norm(p) - 1) < 1e-14
+
+
+def test_field_top_level_is_aperture_synthesis():
+    """The field at level Nz is the plain synthesis of the aperture values."""
+    cav = Cavity(1.0, 1.0, 0.5, 8, 8, 6, 5.0)
+    prof = Profiles(cav)
+    x = np.random.default_rng(3).standard_normal(cav.n_ap) + 1j
+    f = field(cav, prof, x, levels=[cav.nz])[0]
+    e1, e2, e3 = cav.split(x)
+    cosx, sinx, cosy, siny = synth_mats(cav)
+    ref = np.concatenate([(cosx @ e1 @ siny.T).ravel(), (sinx @ e2 @ cosy.T).ravel(),
+                          (sinx @ e3 @ siny.T).ravel()])
+    assert np.allclose(f, ref, atol=1e-13)
