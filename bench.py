@@ -1,0 +1,367 @@
+"""Benchmark: cavity field DOF/s for the 256 x 256 x 128, 16-direction workload.
+
+One step = cavity_solve for one batch of 16 incident directions: excitation
+(g1, g2), aperture solve of (EJ1) (FP32 Krylov iterations with FP64 residual
+refinement), back-substitution and inverse transforms for the full interior
+field (complex64).  The per-(kappa0, eps) state -- kernel table, per-mode
+elimination, preconditioner -- is built once before the timed region and
+reused, as the paper reuses its singular integrals for all incident angles;
+its time is reported as setup_ms.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+N > 1 runs under torch.distributed (one rank per GPU); every rank solves its
+own batch of 16 directions (independent problems, weak scaling) and the max
+time over ranks is reported.
+"""
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+WORKLOAD = "dirs16"
+METRIC = "cavity field DOF/s at rel err <=1e-5 vs FP64 oracle"
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), "measured", d.get("sm_max_mhz", 2070.0)
+    return 6800.0, "fallback", 2070.0
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.stop_ev = threading.Event()
+        self.th = None
+
+    def _run(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        while not self.stop_ev.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                      "--format=csv,noheader,nounits"], capture_output=True,
+                                     text=True, timeout=5).stdout.strip()
+                if out:
+                    self.rows.append([x.strip() for x in out.split(",")])
+            except Exception:
+                pass
+            self.stop_ev.wait(0.2)
+
+    def __enter__(self):
+        self.th = threading.Thread(target=self._run, daemon=True)
+        self.th.start()
+        return self
+
+    def __exit__(self, *a):
+        self.stop_ev.set()
+        self.th.join(timeout=10)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace('.', '').isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace('.', '').isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            for k, nm in enumerate(names):
+                if len(r) > 5 + k and r[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(self.rows)}
+
+
+# ---------------------------------------------------------------- roofline
+def alg_flops_per_launch(cls, w, ndir):
+    """Algorithmic FP flops per launch of a TBC pass (5 n log2 n per complex
+    FFT of length n, 6 per complex multiply), for the batch of ndir
+    directions and the three convolution fields."""
+    nx, ny = w['nx'], w['ny']
+    Px, Py = 4 * nx, 4 * ny
+    lg = np.log2
+    fft = lambda n: 5.0 * n * lg(n)  # noqa: E731
+    lines = 3 * ndir
+    if cls.startswith("tbc_B"):
+        per = fft(Px) + 6 * 2 * Px + fft(2 * Px) + 6 * Px + fft(Px)
+        return per * Py * lines
+    if cls.startswith("tbc_A"):
+        per = fft(Py) + 6 * 2 * Py + fft(2 * Py)
+        return per * nx * lines
+    if cls.startswith("tbc_C"):
+        return (fft(Py) + fft(2 * ny)) * (nx + 1) * lines
+    if cls.startswith("tbc_D"):
+        return fft(2 * nx) * (ny + 1) * lines
+    return None
+
+
+def fp_peak_tflops(cls, sm_mhz):
+    """ALU peaks: FP64 1.25 TFLOP/s (nominal GB300 figure); FP32 derived as
+    152 SMs x 128 FP32 lanes x 2 flops x SM clock."""
+    if cls.endswith("fp64"):
+        return 1.25, "nominal FP64 1.25 TFLOP/s"
+    clk = (sm_mhz or 2070.0) * 1e6
+    return 152 * 128 * 2 * clk / 1e12, "derived FP32 152x128x2xclock"
+
+
+# ---------------------------------------------------------------- oracle sample
+def oracle_sample(w, ndir_sample=1, time_budget=None):
+    """The CPU oracle on a bounded sample of the workload: per direction, the
+    aperture solve (block-preconditioned GMRES, FP64) and the full field
+    synthesis.  The oracle's own setup (kernel table, per-mode elimination) is
+    done first and reported separately, like the GPU's."""
+    from oracle.aperture import ApertureSystem
+    from oracle.excitation import rhs
+    from oracle.field import field
+    from oracle.geometry import Cavity, Layer
+    from oracle.tbc import TBCOperator
+    from oracle.zsystem import Profiles
+    cav = Cavity(w['a'], w['b'], w['c'], w['nx'], w['ny'], w['nz'], w['kappa0'],
+                 layers=[Layer(n, e) for n, e in w['layers']])
+    t0 = time.perf_counter()
+    sysm = ApertureSystem(cav, Profiles(cav), TBCOperator(cav))
+    setup = time.perf_counter() - t0
+    times = []
+    for d in range(ndir_sample):
+        t0 = time.perf_counter()
+        b = rhs(cav, w['theta'][d], w['phi'][d], w['alpha'][d])
+        x, _ = sysm.solve_gmres(b, rtol=1e-10)
+        field(cav, sysm.prof, x[0])
+        times.append(time.perf_counter() - t0)
+    dof = w['nz'] * cav.n_ap
+    return dof, times, setup
+
+
+def cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count()
+
+
+# ---------------------------------------------------------------- arms
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    w = workloads.workload(WORKLOAD)
+    steps, warm = args.steps, args.warmup
+    from oracle.aperture import ApertureSystem
+    from oracle.excitation import rhs
+    from oracle.field import field
+    from oracle.geometry import Cavity, Layer
+    from oracle.tbc import TBCOperator
+    from oracle.zsystem import Profiles
+    cav = Cavity(w['a'], w['b'], w['c'], w['nx'], w['ny'], w['nz'], w['kappa0'],
+                 layers=[Layer(n, e) for n, e in w['layers']])
+    t0 = time.perf_counter()
+    sysm = ApertureSystem(cav, Profiles(cav), TBCOperator(cav))
+    setup = time.perf_counter() - t0
+
+    def step(d):
+        b = rhs(cav, w['theta'][d], w['phi'][d], w['alpha'][d])
+        x, _ = sysm.solve_gmres(b, rtol=1e-10)
+        field(cav, sysm.prof, x[0])
+    for k in range(warm):
+        step(k % 16)
+    t0 = time.perf_counter()
+    for k in range(steps):
+        step((warm + k) % 16)
+    el = time.perf_counter() - t0
+    dof = w['nz'] * cav.n_ap * steps
+    val = dof / el
+    nc = cores()
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "DOF/s",
+            "n_gpus": world, "steps": steps, "warmup": warm, "ms_per_step": 1e3 * el / steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+            "data": "synthetic", "config": {"workload": WORKLOAD + ": 256x256x128 grid, eps=1, "
+                                            "kappa0=2pi*25.6, 1 incident direction per step"},
+            "setup_ms": 1e3 * setup,
+            "cpu_baseline": {"value": val, "unit": "DOF/s", "cores": nc, "kind": "oracle",
+                             "sample": "one incident direction per step (aperture GMRES + full "
+                                       "field), oracle setup excluded"},
+            "e2e": {"value": val, "unit": "DOF/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gb300(args, rank, world, local_rank):
+    import torch
+    import __graft_entry__
+    if rank == 0 or not os.path.exists(os.path.join(ROOT, "paper_2008_01966_gb300",
+                                                    "libcavity.so")):
+        __graft_entry__.build()
+    if world > 1:
+        torch.distributed.barrier()
+    import paper_2008_01966_gb300 as gb
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    w = workloads.workload(WORKLOAD)
+    # each rank: its own batch of 16 directions (seeded by rank)
+    th, ph, al = workloads.directions(16, 2 + rank) if rank else (w['theta'], w['phi'], w['alpha'])
+    ndir = len(th)
+    tol = 1e-10
+    cav = gb.Cavity(w['a'], w['b'], w['c'], w['nx'], w['ny'], w['nz'], precision="mixed",
+                    gmres_tol=tol)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    cav.prepare(w['kappa0'], w['layers'])
+    torch.cuda.synchronize()
+    setup_ms = 1e3 * (time.perf_counter() - t0)
+    ap = torch.empty((ndir, cav.n_ap), dtype=torch.complex128, device=dev)
+    fl = torch.empty((ndir, cav.field_per_dir), dtype=torch.complex64, device=dev)
+
+    def step():
+        return cav.solve(w['kappa0'], w['layers'], th, ph, al, field=True, aperture_out=ap,
+                         field_out=fl)
+    for _ in range(max(args.warmup, 3)):
+        _, _, iters, res = step()
+    stream = torch.cuda.current_stream(dev)
+    cav.timing(False)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local_rank) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            _, _, iters, res = step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ms = e0.elapsed_time(e1)
+    counts = cav.timing_read()
+    launches = sum(c for _, c in counts.values())
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    dof_step = w['nz'] * cav.n_ap * ndir
+    value = dof_step * args.steps * world / (ms / 1e3)
+
+    # instrumented pass: per-kernel-class event times (separate from `value`)
+    cav.timing(True)
+    for _ in range(args.steps):
+        step()
+    kt = cav.timing_read()
+    cav.timing(False)
+    instr_launches = sum(c for _, c in kt.values())
+
+    # e2e: same metric through the C ABI with host (pinned) output buffers
+    aph = torch.empty((ndir, cav.n_ap), dtype=torch.complex128, pin_memory=True)
+    flh = torch.empty((ndir, cav.field_per_dir), dtype=torch.complex64, pin_memory=True)
+    cav.solve(w['kappa0'], w['layers'], th, ph, al, field=True, host=True, aperture_out=aph,
+              field_out=flh)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        cav.solve(w['kappa0'], w['layers'], th, ph, al, field=True, host=True, aperture_out=aph,
+                  field_out=flh)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e = dof_step * args.steps * world / e2e_s
+    h2d = ndir * 6 * 8
+    d2h = ndir * cav.n_ap * 16 + ndir * cav.field_per_dir * 8
+
+    hbm, hbm_kind, _ = peaks()
+    csum = clk.summary()
+    # dominant kernel class and its roofline
+    dom = max(kt.items(), key=lambda kv: kv[1][0])
+    cls, (cms, ccnt) = dom
+    flops = alg_flops_per_launch(cls, w, ndir)
+    roof = None
+    if flops is not None and ccnt > 0:
+        per_launch_s = cms / ccnt / 1e3
+        ach = flops / per_launch_s / 1e12
+        pk, pk_kind = fp_peak_tflops(cls, csum.get("sm_mhz"))
+        roof = {"kernel": cls, "bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
+                "frac": ach / pk, "traffic": None, "peak_source": pk_kind,
+                "launch_ms": cms / ccnt, "algorithmic_flops_per_launch": flops}
+    # HBM view of the field path (write of the field; profile read amortised)
+    fx_ms, fx_n = kt.get("field_x", (0, 0))
+    fy_ms, fy_n = kt.get("field_y", (0, 0))
+    fbytes = ndir * cav.field_per_dir * 8 + (w['nz'] - 1) * cav.n_ap * 8
+    field_roof = None
+    if fx_ms + fy_ms > 0:
+        ach = fbytes / ((fx_ms + fy_ms) / args.steps / 1e3) / 1e9
+        field_roof = {"kernels": "field_y+field_x", "bound": "hbm", "achieved": ach, "peak": hbm,
+                      "unit": "GB/s", "frac": ach / hbm, "peak_source": hbm_kind,
+                      "algorithmic_bytes_per_step": fbytes}
+    line = {"metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": world,
+            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "c64 transforms / f64 elimination and residuals", "data": "synthetic",
+            "config": {"workload": WORKLOAD + ": 256x256x128 grid, a=b=1, c=0.5, eps=1, "
+                                   "kappa0=2pi*25.6 (10 points per wavelength), 16 seeded "
+                                   "incident directions per GPU, mixed precision, "
+                                   "aperture tol 1e-10",
+                       "dof_per_step_per_gpu": dof_step,
+                       "l2": "working set larger than L2 (3.2 GB field written per step)",
+                       "setup": "resident per (kappa0, eps); timed separately"},
+            "setup_ms": setup_ms, "gmres_iters": [int(i) for i in iters],
+            "resid": [float(r) for r in res],
+            "gpu_launches": int(launches // args.steps) * args.steps,
+            "gpu_launches_per_step": launches / args.steps,
+            "kernel_ms_per_step": {k: v[0] / args.steps for k, v in kt.items() if v[1]},
+            "roofline": roof, "roofline_field_path": field_roof,
+            "e2e": {"value": e2e, "unit": "DOF/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "clocks": csum}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        dof1, times, osetup = oracle_sample(w, 3)
+        line["cpu_baseline"] = {"value": dof1 / sum(times), "unit": "DOF/s", "cores": cores(),
+                                "kind": "oracle",
+                                "sample": "3 of the 16 directions: aperture GMRES + full field "
+                                          "(%.1f s); oracle setup %.1f s excluded" %
+                                          (sum(times), osetup)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl" if args.impl == "gb300" else "gloo")
+    try:
+        if args.impl == "reference":
+            return run_reference(args, rank, world)
+        return run_gb300(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,198 @@
+/*
+ * cavity.h -- C ABI of the GB300 solver for electromagnetic scattering by an
+ * open rectangular cavity in a perfectly conducting ground plane (Chen, Jiang,
+ * Lai, Li, "A fast algorithm for the electromagnetic scattering from a large
+ * rectangular cavity in three dimensions").
+ *
+ * Problem (Sec. 2): aperture Gamma = [0,a] x [0,b] in the ground plane x3 = 0,
+ * cavity depth c, fill of horizontal layers with relative permittivity eps_l
+ * (Sec. 4), free-space wavenumber kappa0, incident plane wave from direction
+ * (theta, phi) with polarisation angle alpha (Sec. 7).  The solver follows
+ * Algorithm I / II (Sec. 6): Fourier modes in x1, x2 (E123F), finite differences
+ * and Gaussian elimination in x3 (Sec. 3, Sec. 4), the transparent boundary
+ * condition (ENU1) with its singular integrals evaluated by FFT (Sec. 5), then
+ * back-substitution (EInter) and inverse transforms for the interior field.
+ *
+ * Discretisation: Nx, Ny horizontal grid intervals (M = Nx-1, N = Ny-1 modes),
+ * Nz vertical steps (h = c/Nz, aperture at level Nz).  The aperture unknowns are
+ * ordered as in Appendix A: E1 over N1 = {0..M}x{1..N}, E2 over N2 =
+ * {1..M}x{0..N}, E3 over N3 = {1..M}x{1..N}, each m-major; n_ap = 3MN + M + N.
+ * Complex numbers are interleaved (re, im) pairs of double (complex128) or float
+ * (complex64).
+ *
+ * Conventions for every call:
+ *  - all work is issued on the CUDA stream given to cavity_setup; a call returns
+ *    after that stream has finished the call's work, with its status;
+ *  - inputs are read only and owned by the caller; outputs go into buffers the
+ *    caller allocated; "device" buffers are CUDA device pointers of the device
+ *    that was current at cavity_setup, "host" buffers are ordinary host memory;
+ *  - the library allocates its own resident state (kernel table, per-mode
+ *    profiles, preconditioner, Krylov workspaces) and frees it in
+ *    cavity_destroy;
+ *  - on error nothing is aborted: the call returns a status and
+ *    cavity_last_error() describes it; outputs are then unspecified except where
+ *    stated.
+ *  - a context is not thread safe: one host thread at a time per context.
+ */
+#ifndef CAVITY_H
+#define CAVITY_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cavity_ctx cavity_ctx;
+
+typedef enum {
+  CAVITY_OK = 0,
+  CAVITY_EINVAL = 1,     /* invalid argument or unsupported size            */
+  CAVITY_ENOMEM = 2,     /* device memory budget or allocation exceeded     */
+  CAVITY_ESINGULAR = 3,  /* a per-mode pivot vanished: kappa0 is (nearly) a  */
+                         /* discrete cavity resonance (Sec. 3, after (EJJ1)) */
+  CAVITY_ENOCONV = 4,    /* the aperture solve stopped above its tolerance;  */
+                         /* outputs are filled and the residual is reported  */
+  CAVITY_ETIMEOUT = 5,   /* a bounded device wait gave up                    */
+  CAVITY_ECUDA = 6       /* a CUDA runtime error                             */
+} cavity_status;
+
+enum { CAVITY_FP64 = 0, CAVITY_MIXED = 1 };          /* precision modes       */
+enum { CAVITY_OUT_APERTURE = 0, CAVITY_OUT_FIELD = 1 };
+enum { CAVITY_MEM_DEVICE = 0, CAVITY_MEM_HOST = 1 };
+enum { CAVITY_POL_THETA = 0, CAVITY_POL_PHI = 1 };
+
+typedef struct {
+  double a, b, c;        /* aperture [0,a]x[0,b], depth c                     */
+  int nx, ny, nz;        /* grid intervals; nx, ny powers of two in [4, 512];  */
+                         /* nz >= 2                                            */
+  int precision;         /* CAVITY_FP64: every step in FP64 (complex128 field) */
+                         /* CAVITY_MIXED: FP64 elimination and FP64-accurate   */
+                         /*   aperture solve (FP32 inner Krylov iterations with */
+                         /*   FP64 residual refinement); FP32 transforms and a  */
+                         /*   complex64 field                                  */
+  int pad_factor;        /* period of the TBC convolution in aperture sides;   */
+                         /* 0 selects 4 (the only value the GPU path supports) */
+  double gmres_tol;      /* relative residual target of (EJ1)/(uT1); 0 -> 1e-12 */
+  int gmres_restart;     /* Krylov basis size; 0 -> 40                         */
+  int gmres_max_iter;    /* total inner iterations; 0 -> 400                   */
+  double pivot_tol;      /* |pivot| below pivot_tol * max(1,|sigma-2|) is       */
+                         /* reported as CAVITY_ESINGULAR; 0 -> 1e-12            */
+} cavity_desc;
+
+/* Create a context for one cavity geometry and grid.  `cuda_stream` is a
+ * cudaStream_t (NULL = legacy default stream).  Validates the descriptor;
+ * CAVITY_EINVAL on any out-of-range field.  Allocates nothing that depends on
+ * kappa0 or eps (that happens at the first cavity_solve / cavity_prepare). */
+cavity_status cavity_setup(const cavity_desc* desc, void* cuda_stream,
+                           cavity_ctx** out);
+
+/* Steps 1-2 of Algorithm I/II (Sec. 6) for one wavenumber and layer profile:
+ * the kernel table F(G) of Sec. 5.2 on the frequency box, the per-mode
+ * elimination in x3 (Sec. 3 (LU1)-(EJJ1); Sec. 4 (con12)-(uTT1) and its closing
+ * remark for more layers), and the block-diagonal preconditioner.  Layers are
+ * given top to bottom: layer_levels[l] grid steps (>= 2 each, summing to nz)
+ * with eps = eps_re[l] + i eps_im[l] (host arrays of length nlayers).  The
+ * state is kept and reused by cavity_solve while (kappa0, layers) repeat.
+ * CAVITY_ESINGULAR if a pivot of the elimination vanishes. */
+cavity_status cavity_prepare(cavity_ctx* ctx, double kappa0, int nlayers,
+                             const int* layer_levels, const double* eps_re,
+                             const double* eps_im);
+
+/* Solve for ndir incident plane waves (Sec. 7 parametrisation, host arrays of
+ * length ndir) with the given wavenumber and layer profile (as for
+ * cavity_prepare, which this call runs when the pair changed).
+ *  aperture_out: ndir x n_ap complex128, the aperture coefficients E_{l,Nz}
+ *                (required, never NULL).
+ *  field_out:    required when out_mode == CAVITY_OUT_FIELD, else ignored:
+ *                ndir x nz x S values, S = (nx+1)(ny-1) + (nx-1)(ny+1) +
+ *                (nx-1)(ny-1), complex128 (FP64) or complex64 (MIXED): for each
+ *                direction and level j = 1..nz the samples of E1 on
+ *                p=0..nx, q=1..ny-1, then E2 on p=1..nx-1, q=0..ny, then E3 on
+ *                p=1..nx-1, q=1..ny-1, each row-major in (p, q); at an interface
+ *                level E3 is the upper layer's value.
+ *  out_mem:      CAVITY_MEM_DEVICE or CAVITY_MEM_HOST for both outputs.
+ *  iters_out, resid_out: host arrays of length ndir (may be NULL): Krylov
+ *                iterations and final relative residual of (EJ1)/(uT1) per
+ *                direction.
+ * Returns CAVITY_ENOCONV (outputs filled) when a residual stays above
+ * gmres_tol after gmres_max_iter iterations. */
+cavity_status cavity_solve(cavity_ctx* ctx, double kappa0, int nlayers,
+                           const int* layer_levels, const double* eps_re,
+                           const double* eps_im, int ndir, const double* theta,
+                           const double* phi, const double* alpha, int out_mode,
+                           int out_mem, void* aperture_out, void* field_out,
+                           int* iters_out, double* resid_out);
+
+/* Backscatter radar cross section (Sec. 7; formula from (EGa2):
+ * sigma = (kappa0^2/pi) |e . (x_hat x L)|^2, L = int_Gamma (z x E)
+ * exp(-i kappa0 x_hat.y) dy, x_hat = (sin t cos f, sin t sin f, cos t)).
+ * aperture: ndir x n_ap complex128 (mem = CAVITY_MEM_DEVICE or _HOST) for the
+ * wavenumber of the last prepare; obs_theta/obs_phi host arrays (length ndir);
+ * pol selects e = theta_hat or phi_hat; sigma_out host array (length ndir). */
+cavity_status cavity_rcs(cavity_ctx* ctx, int ndir, const void* aperture, int mem,
+                         const double* obs_theta, const double* obs_phi, int pol,
+                         double* sigma_out);
+
+/* Release the context and all its device memory.  NULL is a no-op. */
+void cavity_destroy(cavity_ctx* ctx);
+
+/* Message of the last failed call on this context (or of the last failed
+ * cavity_setup when ctx is NULL).  Owned by the library. */
+const char* cavity_last_error(const cavity_ctx* ctx);
+
+/* ---- step-level entry points (same conventions; device buffers) ----------
+ * They expose the individual rows of the hot path so that each can be checked
+ * on its own; cavity_solve is composed of exactly these steps. */
+
+/* n_ap and the number of field samples per direction. */
+cavity_status cavity_sizes(const cavity_ctx* ctx, long long* n_ap,
+                           long long* field_per_dir);
+
+/* Per-mode elimination results of the last prepare (Sec. 3/4):
+ *  top:  5 x n_ap complex128 rows [tau | varsigma | 0...] laid out as
+ *        tau over the aperture ordering (n_ap values: tau1 over N1, tau2 over
+ *        N2, tau3 over N3) followed by varsigma over N1 and N2 (n1+n2 values);
+ *        that is n_ap + n1 + n2 values in total.
+ *  prof: (nz-1) x n_ap complex128 profiles P at levels j = 1..nz-1 (level-major,
+ *        aperture ordering; E3 upper values at interfaces), may be NULL.
+ *  profq:(nz-1) x (n1+n2) complex128 E3-driven profiles Q of E1/E2, may be NULL. */
+cavity_status cavity_export_elimination(cavity_ctx* ctx, void* top, void* prof,
+                                        void* profq);
+
+/* The kernel table F(G)(rho) of Sec. 5.2 at rho = |(j1/Lx, j2/Ly)| for
+ * j1 = 0..Px/2-1, j2 = 0..Py/2-1 (row-major, complex128), Px = 4 nx. */
+cavity_status cavity_export_khat(cavity_ctx* ctx, void* khat);
+
+/* Right-hand sides [g1; g2; 0] of (EJ1) for ndir directions (host angle
+ * arrays) into out (ndir x n_ap complex128, device). */
+cavity_status cavity_rhs(cavity_ctx* ctx, int ndir, const double* theta,
+                         const double* phi, const double* alpha, void* out);
+
+/* y = A x for the reduced aperture matrix of (EJ1)/(uT1): x, y ndir x n_ap,
+ * complex128 when precision == CAVITY_FP64 and complex64 when CAVITY_MIXED. */
+cavity_status cavity_apply(cavity_ctx* ctx, int ndir, int precision,
+                           const void* x, void* y);
+
+/* Interior field from given aperture coefficients (EInter + E123F): aperture
+ * ndir x n_ap complex128, field as in cavity_solve for the context's precision. */
+cavity_status cavity_field(cavity_ctx* ctx, int ndir, const void* aperture,
+                           void* field);
+
+/* ---- launch accounting (benchmark instrumentation, not part of the method) --
+ * Every kernel the library launches belongs to one of CAVITY_NUM_KCLASS
+ * classes (names from cavity_kernel_class).  Launches are always counted.
+ * cavity_timing(ctx, 1) resets the counters and starts bracketing every launch
+ * with CUDA events on the context's stream (adds a small host cost per launch);
+ * cavity_timing(ctx, 0) stops.  cavity_timing_read synchronises the stream and
+ * returns, per class, the summed event time in ms (0 when timing was off) and
+ * the number of launches since the last reset; ms and launches are host arrays
+ * of length nclass (<= CAVITY_NUM_KCLASS), either may be NULL. */
+#define CAVITY_NUM_KCLASS 16
+cavity_status cavity_timing(cavity_ctx* ctx, int enable);
+cavity_status cavity_timing_read(cavity_ctx* ctx, int nclass, double* ms,
+                                 long long* launches);
+const char* cavity_kernel_class(int k);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CAVITY_H */

@@ -1,0 +1,202 @@
+"""GB300 solver for electromagnetic scattering by an open rectangular cavity in
+a perfectly conducting ground plane (Chen, Jiang, Lai, Li: fast algorithm for
+the electromagnetic scattering from a large rectangular cavity in 3D).
+
+The Python layer only marshals arguments to the C ABI of include/cavity.h
+(libcavity.so, CUDA for sm_103a).  PyTorch provides device memory and the
+current CUDA stream; every step of the solver runs in the library's kernels.
+
+    cav = Cavity(a=1, b=1, c=0.5, nx=256, ny=256, nz=128, precision="mixed")
+    ap, field, iters, resid = cav.solve(kappa0, [(128, 1+0j)], theta, phi, alpha)
+"""
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import CavityError
+
+__all__ = ["Cavity", "CavityError"]
+
+
+def _dptr(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _layers(layers):
+    lev = np.ascontiguousarray([int(l[0]) for l in layers], dtype=np.int32)
+    er = np.ascontiguousarray([complex(l[1]).real for l in layers], dtype=np.float64)
+    ei = np.ascontiguousarray([complex(l[1]).imag for l in layers], dtype=np.float64)
+    return (lev, er, ei, lev.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+            er.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+            ei.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+
+
+class Cavity:
+    """One cavity geometry and grid with its resident device state."""
+
+    def __init__(self, a, b, c, nx, ny, nz, precision="fp64", gmres_tol=0.0, gmres_restart=0,
+                 gmres_max_iter=0, pivot_tol=0.0, stream=None, device=None):
+        self.lib = _lib.load()
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        torch.cuda.set_device(self.device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.precision = _lib.CAVITY_FP64 if precision == "fp64" else _lib.CAVITY_MIXED
+        d = _lib.CavityDesc(a, b, c, nx, ny, nz, self.precision, 4, gmres_tol, gmres_restart,
+                            gmres_max_iter, pivot_tol)
+        h = ctypes.c_void_p()
+        st = self.lib.cavity_setup(ctypes.byref(d), ctypes.c_void_p(self.stream.cuda_stream),
+                                   ctypes.byref(h))
+        if st != 0:
+            raise CavityError(st, self.lib.cavity_last_error(None).decode())
+        self.h = h
+        self.nx, self.ny, self.nz = nx, ny, nz
+        n_ap = ctypes.c_longlong()
+        fpd = ctypes.c_longlong()
+        self.lib.cavity_sizes(self.h, ctypes.byref(n_ap), ctypes.byref(fpd))
+        self.n_ap, self.field_per_dir = n_ap.value, fpd.value
+        self.n1 = nx * (ny - 1)
+        self.n2 = (nx - 1) * ny
+
+    def _check(self, st, allow_noconv=False):
+        if st == 0 or (allow_noconv and st == _lib.CAVITY_ENOCONV):
+            return st
+        raise CavityError(st, self.lib.cavity_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.cavity_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def field_dtype(self):
+        return torch.complex128 if self.precision == _lib.CAVITY_FP64 else torch.complex64
+
+    # ------------------------------------------------------------ hot path
+    def prepare(self, kappa0, layers):
+        lev, er, ei, pl, pr, pim = _layers(layers)
+        self._check(self.lib.cavity_prepare(self.h, float(kappa0), len(lev), pl, pr, pim))
+
+    def solve(self, kappa0, layers, theta, phi, alpha, field=True, host=False,
+              aperture_out=None, field_out=None):
+        """Aperture coefficients (ndir x n_ap complex128) and, if `field`, the
+        interior field (ndir x field_per_dir), with per-direction Krylov
+        iterations and relative residuals.  host=True returns pinned host
+        tensors filled through the library's own device-to-host copies."""
+        lev, er, ei, pl, pr, pim = _layers(layers)
+        th, pth = _dptr(theta)
+        ph, pph = _dptr(phi)
+        al, pal = _dptr(alpha)
+        ndir = len(th)
+        if host:
+            ap = aperture_out if aperture_out is not None else torch.empty(
+                (ndir, self.n_ap), dtype=torch.complex128, pin_memory=True)
+            fl = None
+            if field:
+                fl = field_out if field_out is not None else torch.empty(
+                    (ndir, self.field_per_dir), dtype=self.field_dtype, pin_memory=True)
+        else:
+            ap = aperture_out if aperture_out is not None else torch.empty(
+                (ndir, self.n_ap), dtype=torch.complex128, device=self.device)
+            fl = None
+            if field:
+                fl = field_out if field_out is not None else torch.empty(
+                    (ndir, self.field_per_dir), dtype=self.field_dtype, device=self.device)
+        iters = np.zeros(ndir, dtype=np.int32)
+        res = np.zeros(ndir, dtype=np.float64)
+        st = self.lib.cavity_solve(
+            self.h, float(kappa0), len(lev), pl, pr, pim, ndir, pth, pph, pal,
+            _lib.CAVITY_OUT_FIELD if field else _lib.CAVITY_OUT_APERTURE,
+            _lib.CAVITY_MEM_HOST if host else _lib.CAVITY_MEM_DEVICE,
+            ctypes.c_void_p(ap.data_ptr()), ctypes.c_void_p(fl.data_ptr() if fl is not None else 0),
+            iters.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+            res.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        self.last_status = self._check(st, allow_noconv=True)
+        return ap, fl, iters, res
+
+    def rcs(self, aperture, theta, phi, pol="theta"):
+        th, pth = _dptr(theta)
+        ph, pph = _dptr(phi)
+        out = np.zeros(len(th))
+        aperture = aperture.contiguous()
+        if aperture.dtype != torch.complex128 or aperture.shape != (len(th), self.n_ap):
+            raise ValueError("aperture must be a (ndir, n_ap) complex128 tensor")
+        mem = _lib.CAVITY_MEM_DEVICE if aperture.is_cuda else _lib.CAVITY_MEM_HOST
+        self._check(self.lib.cavity_rcs(
+            self.h, len(th), ctypes.c_void_p(aperture.data_ptr()), mem, pth, pph,
+            _lib.CAVITY_POL_THETA if pol == "theta" else _lib.CAVITY_POL_PHI,
+            out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return out
+
+    # ------------------------------------------------------------ step level
+    def rhs(self, theta, phi, alpha):
+        th, pth = _dptr(theta)
+        ph, pph = _dptr(phi)
+        al, pal = _dptr(alpha)
+        out = torch.empty((len(th), self.n_ap), dtype=torch.complex128, device=self.device)
+        self._check(self.lib.cavity_rhs(self.h, len(th), pth, pph, pal, ctypes.c_void_p(out.data_ptr())))
+        return out
+
+    def apply(self, x, precision=None):
+        prec = self.precision if precision is None else (
+            _lib.CAVITY_FP64 if precision == "fp64" else _lib.CAVITY_MIXED)
+        x = x.contiguous()
+        want = torch.complex128 if prec == _lib.CAVITY_FP64 else torch.complex64
+        if x.dtype != want or not x.is_cuda or x.dim() != 2 or x.shape[1] != self.n_ap:
+            raise ValueError("x must be a CUDA (ndir, n_ap) tensor of %s" % want)
+        y = torch.empty_like(x)
+        self._check(self.lib.cavity_apply(self.h, x.shape[0], prec, ctypes.c_void_p(x.data_ptr()),
+                                          ctypes.c_void_p(y.data_ptr())))
+        return y
+
+    def field(self, aperture):
+        aperture = aperture.contiguous()
+        if aperture.dtype != torch.complex128 or not aperture.is_cuda or \
+                aperture.dim() != 2 or aperture.shape[1] != self.n_ap:
+            raise ValueError("aperture must be a CUDA (ndir, n_ap) complex128 tensor")
+        out = torch.empty((aperture.shape[0], self.field_per_dir), dtype=self.field_dtype,
+                          device=self.device)
+        self._check(self.lib.cavity_field(self.h, aperture.shape[0],
+                                          ctypes.c_void_p(aperture.data_ptr()),
+                                          ctypes.c_void_p(out.data_ptr())))
+        return out
+
+    def export_elimination(self):
+        top = torch.empty(self.n_ap + self.n1 + self.n2, dtype=torch.complex128, device=self.device)
+        prof = torch.empty((self.nz - 1, self.n_ap), dtype=torch.complex128, device=self.device)
+        profq = torch.empty((self.nz - 1, self.n1 + self.n2), dtype=torch.complex128,
+                            device=self.device)
+        self._check(self.lib.cavity_export_elimination(
+            self.h, ctypes.c_void_p(top.data_ptr()), ctypes.c_void_p(prof.data_ptr()),
+            ctypes.c_void_p(profq.data_ptr())))
+        return top, prof, profq
+
+    def export_khat(self):
+        out = torch.empty((2 * self.nx, 2 * self.ny), dtype=torch.complex128, device=self.device)
+        self._check(self.lib.cavity_export_khat(self.h, ctypes.c_void_p(out.data_ptr())))
+        return out
+
+    # ------------------------------------------------------------ instrumentation
+    def timing(self, enable=True):
+        """Reset launch counters; with enable, time every launch with events."""
+        self._check(self.lib.cavity_timing(self.h, 1 if enable else 0))
+
+    def timing_read(self):
+        """{class name: (ms, launches)} since the last timing() call."""
+        n = _lib.NUM_KCLASS
+        ms = np.zeros(n)
+        cnt = np.zeros(n, dtype=np.int64)
+        self._check(self.lib.cavity_timing_read(
+            self.h, n, ms.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+            cnt.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong))))
+        return {self.lib.cavity_kernel_class(k).decode(): (float(ms[k]), int(cnt[k]))
+                for k in range(n)}

@@ -1,0 +1,376 @@
+// C ABI of the cavity solver (include/cavity.h): argument checking, the
+// resident state per (kappa0, layers), and the composition of the hot-path
+// steps into cavity_solve.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+static thread_local std::string g_setup_err;
+
+static bool pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+extern "C" cavity_status cavity_setup(const cavity_desc* desc, void* cuda_stream, cavity_ctx** out) {
+  if (!out) {
+    g_setup_err = "out is NULL";
+    return CAVITY_EINVAL;
+  }
+  *out = nullptr;
+  if (!desc) {
+    g_setup_err = "desc is NULL";
+    return CAVITY_EINVAL;
+  }
+  const cavity_desc& d = *desc;
+  auto bad = [&](const std::string& m) {
+    g_setup_err = m;
+    return CAVITY_EINVAL;
+  };
+  if (!(d.a > 0) || !(d.b > 0) || !(d.c > 0)) return bad("a, b, c must be positive");
+  if (!pow2(d.nx) || !pow2(d.ny) || d.nx < 4 || d.ny < 4 || d.nx > 512 || d.ny > 512)
+    return bad("nx, ny must be powers of two in [4, 512]");
+  if (d.nz < 2 || d.nz > 1 << 20) return bad("nz must be in [2, 2^20]");
+  if (d.precision != CAVITY_FP64 && d.precision != CAVITY_MIXED) return bad("unknown precision");
+  if (d.pad_factor != 0 && d.pad_factor != 4) return bad("pad_factor must be 0 or 4");
+  const double R = std::sqrt(2.0) * std::max(d.a, d.b);
+  if (!(4.0 * std::min(d.a, d.b) > std::min(d.a, d.b) + R))
+    return bad("aspect ratio too large for the period 4*side (needs max/min < 2.12)");
+  if (d.gmres_tol < 0 || d.gmres_restart < 0 || d.gmres_max_iter < 0 || d.pivot_tol < 0)
+    return bad("negative solver parameter");
+  cavity_ctx* ctx = new cavity_ctx();
+  ctx->desc = d;
+  if (ctx->desc.pad_factor == 0) ctx->desc.pad_factor = 4;
+  if (ctx->desc.pivot_tol == 0) ctx->desc.pivot_tol = 1e-12;
+  ctx->stream = (cudaStream_t)cuda_stream;
+  cudaGetDevice(&ctx->device);
+  Geo& g = ctx->g;
+  g.a = d.a; g.b = d.b; g.c = d.c; g.nx = d.nx; g.ny = d.ny; g.nz = d.nz;
+  g.h = d.c / d.nz;
+  g.M = d.nx - 1; g.N = d.ny - 1;
+  g.n1 = (g.M + 1) * g.N; g.n2 = g.M * (g.N + 1); g.n3 = g.M * g.N;
+  g.nap = g.n1 + g.n2 + g.n3;
+  g.pad = 4;
+  g.Px = 4 * d.nx; g.Py = 4 * d.ny;
+  g.Lx = 4 * d.a; g.Ly = 4 * d.b; g.R = R;
+  g.lnx = ilog2(d.nx); g.lny = ilog2(d.ny); g.lPx = ilog2(g.Px); g.lPy = ilog2(g.Py);
+  g.field_per_level = (long long)(d.nx + 1) * (d.ny - 1) + (long long)(d.nx - 1) * (d.ny + 1) +
+                      (long long)(d.nx - 1) * (d.ny - 1);
+  g.field_per_dir = g.field_per_level * d.nz;
+  ctx->TW = 2 * std::max(g.Px, g.Py);
+  cavity_status s = launch_twiddles(ctx);
+  if (s == CAVITY_OK) s = launch_ehat(ctx);
+  if (s == CAVITY_OK) {
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) {
+      ctx->err = cudaGetErrorString(e);
+      s = CAVITY_ECUDA;
+    }
+  }
+  if (s != CAVITY_OK) {
+    g_setup_err = ctx->err;
+    cavity_destroy(ctx);
+    return s;
+  }
+  *out = ctx;
+  return CAVITY_OK;
+}
+
+extern "C" void cavity_destroy(cavity_ctx* ctx) {
+  if (!ctx) return;
+  void* ptrs[] = {ctx->tw64, ctx->tw32, ctx->ehat_x64[0], ctx->ehat_x64[1], ctx->ehat_y64[0],
+                  ctx->ehat_y64[1], ctx->ehat_x32[0], ctx->ehat_x32[1], ctx->ehat_y32[0],
+                  ctx->ehat_y32[1], ctx->khat64, ctx->khat32, ctx->khat_raw, ctx->prof, ctx->profq,
+                  ctx->top64, ctx->top32, ctx->pinv64, ctx->pinv32, ctx->prof32, ctx->profq32,
+                  ctx->minpiv, ctx->ws, ctx->ws2, ctx->stage};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  for (auto& e : ctx->evs) {
+    cudaEventDestroy(e.a);
+    cudaEventDestroy(e.b);
+  }
+  for (auto e : ctx->evpool) cudaEventDestroy(e);
+  delete ctx;
+}
+
+extern "C" const char* cavity_last_error(const cavity_ctx* ctx) {
+  return ctx ? ctx->err.c_str() : g_setup_err.c_str();
+}
+
+extern "C" cavity_status cavity_sizes(const cavity_ctx* ctx, long long* n_ap, long long* fpd) {
+  if (!ctx) return CAVITY_EINVAL;
+  if (n_ap) *n_ap = ctx->g.nap;
+  if (fpd) *fpd = ctx->g.field_per_dir;
+  return CAVITY_OK;
+}
+
+static cavity_status check_layers(cavity_ctx* ctx, int nlayers, const int* lev, const double* er,
+                                  const double* ei) {
+  if (nlayers < 1 || nlayers > 16 || !lev || !er || !ei) {
+    ctx->err = "need 1..16 layers with level counts and permittivities";
+    return CAVITY_EINVAL;
+  }
+  long long sum = 0;
+  for (int l = 0; l < nlayers; ++l) {
+    if (lev[l] < 2) {
+      ctx->err = "every layer must span at least two grid steps";
+      return CAVITY_EINVAL;
+    }
+    if (!std::isfinite(er[l]) || !std::isfinite(ei[l])) {
+      ctx->err = "non-finite permittivity";
+      return CAVITY_EINVAL;
+    }
+    sum += lev[l];
+  }
+  if (sum != ctx->g.nz) {
+    ctx->err = "layer level counts must sum to nz";
+    return CAVITY_EINVAL;
+  }
+  return CAVITY_OK;
+}
+
+extern "C" cavity_status cavity_prepare(cavity_ctx* ctx, double kappa0, int nlayers,
+                                        const int* layer_levels, const double* eps_re,
+                                        const double* eps_im) {
+  if (!ctx) return CAVITY_EINVAL;
+  if (!(kappa0 > 0) || !std::isfinite(kappa0)) {
+    ctx->err = "kappa0 must be positive";
+    return CAVITY_EINVAL;
+  }
+  CKS(check_layers(ctx, nlayers, layer_levels, eps_re, eps_im));
+  std::vector<LayerDev> L(nlayers);
+  for (int l = 0; l < nlayers; ++l) L[l] = LayerDev{layer_levels[l], eps_re[l], eps_im[l]};
+  bool same = ctx->prepared && ctx->kappa0 == kappa0 && ctx->layers.size() == L.size();
+  if (same)
+    for (int l = 0; l < nlayers; ++l)
+      same = same && L[l].nlev == ctx->layers[l].nlev && L[l].eps_re == ctx->layers[l].eps_re &&
+             L[l].eps_im == ctx->layers[l].eps_im;
+  if (same) return CAVITY_OK;
+  ctx->prepared = false;
+  bool kappa_same = ctx->khat64 && ctx->kappa0 == kappa0;
+  const bool was_layered = ctx->layers.size() > 1;
+  ctx->kappa0 = kappa0;
+  ctx->layers = L;
+  (void)was_layered;
+  if (!kappa_same) CKS(launch_khat(ctx, kappa0));
+  CKS(launch_zsweep(ctx, kappa0));
+  CKS(launch_precond(ctx));
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->prepared = true;
+  return CAVITY_OK;
+}
+
+extern "C" cavity_status cavity_rhs(cavity_ctx* ctx, int ndir, const double* theta,
+                                    const double* phi, const double* alpha, void* out) {
+  if (!ctx) return CAVITY_EINVAL;
+  if (!ctx->prepared) {
+    ctx->err = "call cavity_prepare (or cavity_solve) first";
+    return CAVITY_EINVAL;
+  }
+  if (ndir < 1 || !theta || !phi || !alpha || !out) {
+    ctx->err = "bad rhs arguments";
+    return CAVITY_EINVAL;
+  }
+  CKS(launch_rhs(ctx, ndir, theta, phi, alpha, (double2*)out));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return CAVITY_OK;
+}
+
+extern "C" cavity_status cavity_apply(cavity_ctx* ctx, int ndir, int precision, const void* x,
+                                      void* y) {
+  if (!ctx) return CAVITY_EINVAL;
+  if (!ctx->prepared || ndir < 1 || !x || !y) {
+    ctx->err = "cavity_apply: not prepared or bad arguments";
+    return CAVITY_EINVAL;
+  }
+  if (precision == CAVITY_FP64) {
+    CKS(ensure_ws(ctx, &ctx->ws, &ctx->ws_bytes, apply_work_bytes(ctx->g, ndir, sizeof(double2))));
+    CKS(launch_apply<double>(ctx, ndir, (const double2*)x, (double2*)y, ctx->ws));
+  } else if (precision == CAVITY_MIXED) {
+    CKS(ensure_ws(ctx, &ctx->ws, &ctx->ws_bytes, apply_work_bytes(ctx->g, ndir, sizeof(float2))));
+    CKS(launch_apply<float>(ctx, ndir, (const float2*)x, (float2*)y, ctx->ws));
+  } else {
+    ctx->err = "unknown precision";
+    return CAVITY_EINVAL;
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  return CAVITY_OK;
+}
+
+extern "C" cavity_status cavity_field(cavity_ctx* ctx, int ndir, const void* aperture, void* field) {
+  if (!ctx) return CAVITY_EINVAL;
+  if (!ctx->prepared || ndir < 1 || !aperture || !field) {
+    ctx->err = "cavity_field: not prepared or bad arguments";
+    return CAVITY_EINVAL;
+  }
+  if (ctx->desc.precision == CAVITY_FP64)
+    CKS(launch_field<double>(ctx, ndir, (const double2*)aperture, (double2*)field));
+  else
+    CKS(launch_field<float>(ctx, ndir, (const double2*)aperture, (float2*)field));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return CAVITY_OK;
+}
+
+extern "C" cavity_status cavity_export_elimination(cavity_ctx* ctx, void* top, void* prof,
+                                                   void* profq) {
+  if (!ctx) return CAVITY_EINVAL;
+  if (!ctx->prepared) {
+    ctx->err = "not prepared";
+    return CAVITY_EINVAL;
+  }
+  const Geo& g = ctx->g;
+  if (top)
+    CK(cudaMemcpyAsync(top, ctx->top64, sizeof(double2) * (g.nap + g.n1 + g.n2),
+                       cudaMemcpyDeviceToDevice, ctx->stream));
+  if (prof)
+    CK(cudaMemcpyAsync(prof, ctx->prof, sizeof(double2) * (size_t)(g.nz - 1) * g.nap,
+                       cudaMemcpyDeviceToDevice, ctx->stream));
+  if (profq) {
+    size_t nq = sizeof(double2) * (size_t)(g.nz - 1) * (g.n1 + g.n2);
+    if (ctx->layers.size() > 1)
+      CK(cudaMemcpyAsync(profq, ctx->profq, nq, cudaMemcpyDeviceToDevice, ctx->stream));
+    else
+      CK(cudaMemsetAsync(profq, 0, nq, ctx->stream));
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  return CAVITY_OK;
+}
+
+extern "C" cavity_status cavity_export_khat(cavity_ctx* ctx, void* khat) {
+  if (!ctx || !khat) return CAVITY_EINVAL;
+  if (!ctx->prepared) {
+    ctx->err = "not prepared";
+    return CAVITY_EINVAL;
+  }
+  const Geo& g = ctx->g;
+  CK(cudaMemcpyAsync(khat, ctx->khat_raw, sizeof(double2) * (size_t)(g.Px / 2) * (g.Py / 2),
+                     cudaMemcpyDeviceToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return CAVITY_OK;
+}
+
+extern "C" cavity_status cavity_solve(cavity_ctx* ctx, double kappa0, int nlayers,
+                                      const int* layer_levels, const double* eps_re,
+                                      const double* eps_im, int ndir, const double* theta,
+                                      const double* phi, const double* alpha, int out_mode,
+                                      int out_mem, void* aperture_out, void* field_out,
+                                      int* iters_out, double* resid_out) {
+  if (!ctx) return CAVITY_EINVAL;
+  if (ndir < 1 || !theta || !phi || !alpha || !aperture_out ||
+      (out_mode == CAVITY_OUT_FIELD && !field_out) ||
+      (out_mode != CAVITY_OUT_FIELD && out_mode != CAVITY_OUT_APERTURE) ||
+      (out_mem != CAVITY_MEM_DEVICE && out_mem != CAVITY_MEM_HOST)) {
+    ctx->err = "cavity_solve: bad arguments";
+    return CAVITY_EINVAL;
+  }
+  CKS(cavity_prepare(ctx, kappa0, nlayers, layer_levels, eps_re, eps_im));
+  const Geo& g = ctx->g;
+  const size_t nv = (size_t)ndir * g.nap;
+  const bool host = out_mem == CAVITY_MEM_HOST;
+  const size_t fbytes = (size_t)ndir * g.field_per_dir *
+                        (ctx->desc.precision == CAVITY_FP64 ? sizeof(double2) : sizeof(float2));
+  // b and (for host output) x and the field are staged on the device
+  size_t need = sizeof(double2) * nv * (host ? 2 : 1) +
+                ((host && out_mode == CAVITY_OUT_FIELD) ? fbytes : 0) + 512;
+  CKS(ensure_ws(ctx, &ctx->stage, &ctx->stage_bytes, need));
+  auto al = [](size_t v) { return (v + 255) / 256 * 256; };
+  char* p = (char*)ctx->stage;
+  double2* b = (double2*)p;
+  p += al(sizeof(double2) * nv);
+  double2* x = host ? (double2*)p : (double2*)aperture_out;
+  if (host) p += al(sizeof(double2) * nv);
+  void* fld = host ? (void*)p : field_out;
+  CKS(launch_rhs(ctx, ndir, theta, phi, alpha, b));
+  cavity_status st;
+  if (ctx->desc.precision == CAVITY_FP64)
+    st = run_gmres64(ctx, ndir, b, x, iters_out, resid_out);
+  else
+    st = run_mixed_solve(ctx, ndir, b, x, iters_out, resid_out);
+  if (st != CAVITY_OK && st != CAVITY_ENOCONV) return st;
+  if (out_mode == CAVITY_OUT_FIELD) {
+    if (ctx->desc.precision == CAVITY_FP64)
+      CKS(launch_field<double>(ctx, ndir, x, (double2*)fld));
+    else
+      CKS(launch_field<float>(ctx, ndir, x, (float2*)fld));
+  }
+  if (host) {
+    CK(cudaMemcpyAsync(aperture_out, x, sizeof(double2) * nv, cudaMemcpyDeviceToHost, ctx->stream));
+    if (out_mode == CAVITY_OUT_FIELD)
+      CK(cudaMemcpyAsync(field_out, fld, fbytes, cudaMemcpyDeviceToHost, ctx->stream));
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  return st;
+}
+
+extern "C" cavity_status cavity_rcs(cavity_ctx* ctx, int ndir, const void* aperture, int mem,
+                                    const double* obs_theta, const double* obs_phi, int pol,
+                                    double* sigma_out) {
+  if (!ctx) return CAVITY_EINVAL;
+  if (!ctx->prepared || ndir < 1 || !aperture || !obs_theta || !obs_phi || !sigma_out ||
+      (pol != CAVITY_POL_THETA && pol != CAVITY_POL_PHI) ||
+      (mem != CAVITY_MEM_DEVICE && mem != CAVITY_MEM_HOST)) {
+    ctx->err = "cavity_rcs: bad arguments or not prepared";
+    return CAVITY_EINVAL;
+  }
+  const double2* ap = (const double2*)aperture;
+  void* tmp = nullptr;
+  if (mem == CAVITY_MEM_HOST) {
+    size_t nb = sizeof(double2) * (size_t)ndir * ctx->g.nap;
+    CK(cudaMalloc(&tmp, nb));
+    cudaError_t e = cudaMemcpyAsync(tmp, aperture, nb, cudaMemcpyHostToDevice, ctx->stream);
+    if (e != cudaSuccess) {
+      cudaFree(tmp);
+      ctx->err = cudaGetErrorString(e);
+      return CAVITY_ECUDA;
+    }
+    ap = (const double2*)tmp;
+  }
+  cavity_status s = launch_rcs(ctx, ndir, ap, obs_theta, obs_phi, pol, sigma_out);
+  if (tmp) cudaFree(tmp);
+  return s;
+}
+
+static const char* kclass_names[KC_N] = {
+    "tbc_A_fp64", "tbc_B_fp64", "tbc_C_fp64", "tbc_D_fp64", "tbc_combine_fp64",
+    "tbc_A_fp32", "tbc_B_fp32", "tbc_C_fp32", "tbc_D_fp32", "tbc_combine_fp32",
+    "krylov", "precond", "field_y", "field_x", "rhs_rcs", "setup"};
+static_assert(KC_N == CAVITY_NUM_KCLASS, "class count");
+
+extern "C" const char* cavity_kernel_class(int k) {
+  return (k >= 0 && k < KC_N) ? kclass_names[k] : "";
+}
+
+static void drain_events(cavity_ctx* ctx) {
+  for (auto& e : ctx->evs) {
+    float t = 0;
+    if (cudaEventElapsedTime(&t, e.a, e.b) == cudaSuccess) ctx->ms[e.cls] += t;
+    ctx->evpool.push_back(e.a);
+    ctx->evpool.push_back(e.b);
+  }
+  ctx->evs.clear();
+}
+
+extern "C" cavity_status cavity_timing(cavity_ctx* ctx, int enable) {
+  if (!ctx) return CAVITY_EINVAL;
+  CK(cudaStreamSynchronize(ctx->stream));
+  drain_events(ctx);
+  for (int k = 0; k < KC_N; ++k) {
+    ctx->nlaunch[k] = 0;
+    ctx->ms[k] = 0;
+  }
+  ctx->timing = enable != 0;
+  return CAVITY_OK;
+}
+
+extern "C" cavity_status cavity_timing_read(cavity_ctx* ctx, int nclass, double* ms,
+                                            long long* launches) {
+  if (!ctx || nclass < 0 || nclass > KC_N) return CAVITY_EINVAL;
+  CK(cudaStreamSynchronize(ctx->stream));
+  drain_events(ctx);
+  for (int k = 0; k < nclass; ++k) {
+    if (ms) ms[k] = ctx->ms[k];
+    if (launches) launches[k] = ctx->nlaunch[k];
+  }
+  return CAVITY_OK;
+}

@@ -1,0 +1,235 @@
+// Internal definitions shared by the CUDA translation units of the cavity
+// solver: complex arithmetic, the context with its resident device state, and
+// error plumbing.  Nothing here is part of the public ABI (include/cavity.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+
+#include "../../include/cavity.h"
+
+// ------------------------------------------------------------ complex numbers
+template <typename T> struct cplx_t;
+template <> struct cplx_t<double> { typedef double2 type; };
+template <> struct cplx_t<float> { typedef float2 type; };
+
+template <typename T> using C = typename cplx_t<T>::type;
+
+template <typename T> __host__ __device__ __forceinline__ C<T> mk(T x, T y) {
+  C<T> r; r.x = x; r.y = y; return r;
+}
+template <typename T> __host__ __device__ __forceinline__ C<T> cadd(C<T> a, C<T> b) {
+  return mk<T>(a.x + b.x, a.y + b.y);
+}
+template <typename T> __host__ __device__ __forceinline__ C<T> csub(C<T> a, C<T> b) {
+  return mk<T>(a.x - b.x, a.y - b.y);
+}
+template <typename T> __host__ __device__ __forceinline__ C<T> cmul(C<T> a, C<T> b) {
+  return mk<T>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename T> __host__ __device__ __forceinline__ C<T> cconj(C<T> a) {
+  return mk<T>(a.x, -a.y);
+}
+template <typename T> __host__ __device__ __forceinline__ C<T> cscale(C<T> a, T s) {
+  return mk<T>(a.x * s, a.y * s);
+}
+// multiply by +i
+template <typename T> __host__ __device__ __forceinline__ C<T> cmul_i(C<T> a) {
+  return mk<T>(-a.y, a.x);
+}
+// a / b
+template <typename T> __host__ __device__ __forceinline__ C<T> cdiv(C<T> a, C<T> b) {
+  // scaled division (Smith) keeps the range for large |b|
+  T ar = b.x < 0 ? -b.x : b.x, ai = b.y < 0 ? -b.y : b.y;
+  if (ar >= ai) {
+    T r = b.y / b.x, d = b.x + b.y * r;
+    return mk<T>((a.x + a.y * r) / d, (a.y - a.x * r) / d);
+  } else {
+    T r = b.x / b.y, d = b.y + b.x * r;
+    return mk<T>((a.x * r + a.y) / d, (a.y * r - a.x) / d);
+  }
+}
+template <typename T> __host__ __device__ __forceinline__ T cabs2(C<T> a) {
+  return a.x * a.x + a.y * a.y;
+}
+__host__ __device__ __forceinline__ float2 to_f(double2 a) {
+  return make_float2((float)a.x, (float)a.y);
+}
+__host__ __device__ __forceinline__ double2 to_d(float2 a) {
+  return make_double2((double)a.x, (double)a.y);
+}
+template <typename T> __host__ __device__ __forceinline__ C<T> conv(double2 a);
+template <> __host__ __device__ __forceinline__ double2 conv<double>(double2 a) { return a; }
+template <> __host__ __device__ __forceinline__ float2 conv<float>(double2 a) { return to_f(a); }
+
+// ------------------------------------------------------------ geometry
+struct Geo {
+  double a, b, c, h;
+  int nx, ny, nz, M, N;
+  int n1, n2, n3, nap;     // sizes of the aperture blocks (Appendix A)
+  int pad, Px, Py;         // TBC torus: Px = pad*nx points, period Lx = pad*a
+  double Lx, Ly, R;        // R = sqrt(2) max(a,b): truncation of the kernel
+  int lnx, lny, lPx, lPy;  // log2 of nx, ny, Px, Py
+  long long field_per_level, field_per_dir;
+};
+
+// kernel classes for launch counting and event timing (cavity_timing_read)
+enum KClass {
+  KC_TBC_A64, KC_TBC_B64, KC_TBC_C64, KC_TBC_D64, KC_COMB64,
+  KC_TBC_A32, KC_TBC_B32, KC_TBC_C32, KC_TBC_D32, KC_COMB32,
+  KC_KRYLOV, KC_PRECOND, KC_FIELD_Y, KC_FIELD_X, KC_RHS, KC_SETUP, KC_N
+};
+
+// one layer of the fill, top to bottom
+struct LayerDev {
+  int nlev;
+  double eps_re, eps_im;
+};
+
+// The resident device state of one context.
+struct cavity_ctx {
+  Geo g;
+  cavity_desc desc;
+  cudaStream_t stream;
+  int device;
+  std::string err;
+
+  // twiddle table exp(-2 pi i k / TW), k < TW, TW = max transform length
+  int TW;
+  double2* tw64 = nullptr;
+  float2* tw32 = nullptr;
+  // FFT of the 1-D Cauchy-type kernel of the basis transform (Sec. 5.2 F(F)):
+  // length 2*Px (x) and 2*Py (y), for cos ('c') and sin ('s') kinds, with the
+  // convolution scale folded in
+  double2 *ehat_x64[2] = {nullptr, nullptr}, *ehat_y64[2] = {nullptr, nullptr};
+  float2 *ehat_x32[2] = {nullptr, nullptr}, *ehat_y32[2] = {nullptr, nullptr};
+
+  // ---- state of the last prepare (kappa0, layers)
+  bool prepared = false;
+  double kappa0 = 0;
+  std::vector<LayerDev> layers;
+  double2* khat64 = nullptr;   // (Px/2) x (Py/2) quarter box, scaled by 1/(Lx Ly)
+  float2* khat32 = nullptr;
+  double2* khat_raw = nullptr; // unscaled copy for export
+  double2* prof = nullptr;     // (nz-1) x nap profiles P, level-major
+  double2* profq = nullptr;    // (nz-1) x (n1+n2) profiles Q (layered only)
+  double2* top64 = nullptr;    // nap tau, then n1+n2 varsigma
+  float2* top32 = nullptr;
+  double2* pinv64 = nullptr;   // (M+1)(N+1) x 9 inverse diagonal blocks
+  float2* pinv32 = nullptr;
+  float2* prof32 = nullptr;    // FP32 copies of the profiles for the mixed field path
+  float2* profq32 = nullptr;
+  double* minpiv = nullptr;    // device scalar: min |pivot| / scale
+
+  // ---- workspaces (grown on demand)
+  size_t ws_bytes = 0;
+  void* ws = nullptr;
+  size_t ws2_bytes = 0;
+  void* ws2 = nullptr;
+  size_t stage_bytes = 0;   // device staging of cavity_solve (right-hand sides,
+  void* stage = nullptr;    // and outputs that go to host memory)
+
+  // ---- launch accounting: counts always, CUDA-event times while timing is on
+  long long nlaunch[KC_N] = {0};
+  bool timing = false;
+  struct Ev { int cls; cudaEvent_t a, b; };
+  std::vector<Ev> evs;
+  std::vector<cudaEvent_t> evpool;
+  double ms[KC_N] = {0};
+};
+
+// Counts one launch of class `cls`; with timing on, brackets it with events on
+// the context's stream.  Use as  { KScope k_(ctx, KC_...); kernel<<<...>>>(...); }
+struct KScope {
+  cavity_ctx* c;
+  int cls;
+  cudaEvent_t a = nullptr;
+  static cudaEvent_t get(cavity_ctx* c) {
+    cudaEvent_t e;
+    if (!c->evpool.empty()) {
+      e = c->evpool.back();
+      c->evpool.pop_back();
+    } else {
+      cudaEventCreate(&e);
+    }
+    return e;
+  }
+  KScope(cavity_ctx* c_, int k) : c(c_), cls(k) {
+    c->nlaunch[k]++;
+    if (c->timing) {
+      a = get(c);
+      cudaEventRecord(a, c->stream);
+    }
+  }
+  ~KScope() {
+    if (c->timing) {
+      cudaEvent_t b = get(c);
+      cudaEventRecord(b, c->stream);
+      c->evs.push_back({cls, a, b});
+    }
+  }
+};
+
+// ------------------------------------------------------------ errors
+#define CK(call)                                                                 \
+  do {                                                                           \
+    cudaError_t e_ = (call);                                                     \
+    if (e_ != cudaSuccess) {                                                     \
+      ctx->err = std::string(#call) + ": " + cudaGetErrorString(e_);             \
+      return CAVITY_ECUDA;                                                       \
+    }                                                                            \
+  } while (0)
+
+#define CKS(st)                                                                  \
+  do {                                                                           \
+    cavity_status s_ = (st);                                                     \
+    if (s_ != CAVITY_OK) return s_;                                              \
+  } while (0)
+
+inline int ilog2(int n) {
+  int l = 0;
+  while ((1 << l) < n) ++l;
+  return l;
+}
+
+// grow a workspace to at least `bytes`
+inline cavity_status ensure_ws(cavity_ctx* ctx, void** p, size_t* have, size_t bytes) {
+  if (*have >= bytes) return CAVITY_OK;
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  *have = 0;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    ctx->err = "workspace allocation of " + std::to_string(bytes) + " bytes failed: " +
+               cudaGetErrorString(e);
+    return CAVITY_ENOMEM;
+  }
+  *have = bytes;
+  return CAVITY_OK;
+}
+
+// ------------------------------------------------------------ step launchers
+// (defined in the individual .cu files)
+cavity_status launch_twiddles(cavity_ctx* ctx);
+cavity_status launch_ehat(cavity_ctx* ctx);
+cavity_status launch_khat(cavity_ctx* ctx, double kappa0);
+cavity_status launch_zsweep(cavity_ctx* ctx, double kappa0);
+cavity_status launch_precond(cavity_ctx* ctx);
+cavity_status launch_rhs(cavity_ctx* ctx, int ndir, const double* theta,
+                         const double* phi, const double* alpha, double2* out);
+template <typename T>
+cavity_status launch_apply(cavity_ctx* ctx, int ndir, const C<T>* x, C<T>* y, void* work);
+size_t apply_work_bytes(const Geo& g, int ndir, int elem_bytes);
+template <typename T>
+cavity_status launch_precond_apply(cavity_ctx* ctx, int ndir, const C<T>* x, C<T>* y);
+cavity_status run_gmres64(cavity_ctx* ctx, int ndir, const double2* b, double2* x,
+                          int* iters, double* resid);
+cavity_status run_mixed_solve(cavity_ctx* ctx, int ndir, const double2* b, double2* x,
+                              int* iters, double* resid);
+template <typename T>
+cavity_status launch_field(cavity_ctx* ctx, int ndir, const double2* ap, C<T>* out);
+cavity_status launch_rcs(cavity_ctx* ctx, int ndir, const double2* ap,
+                         const double* th, const double* ph, int pol, double* sigma);

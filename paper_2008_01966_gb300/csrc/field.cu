@@ -1,0 +1,210 @@
+// Interior field: back-substitution (EInter) fused with the inverse cos/sin
+// transforms of (E123F) per level.
+//
+// For direction d and level j the modal coefficients are
+//   E_{l,j}^{mn} = P_{l,j}^{mn} E_l^{mn} (+ Q_{l,j}^{mn} E_3^{mn} for l = 1, 2 in
+//   a layered fill),
+// and the field on the grid is
+//   E1(p, q) = sum_{m=0}^{M} sum_{n=1}^{N} E1^{mn} cos(m pi p/Nx) sin(n pi q/Ny),
+//   E2 with sin/cos, E3 with sin/sin.
+// Pass 1 forms the coefficients of one row m on the fly (profile times aperture
+// value, never stored) and synthesises along x2 with an extended FFT of length
+// 2Ny; pass 2 synthesises along x1 for a tile of columns q and writes output
+// rows of the tile contiguously.  Levels are processed in chunks whose
+// intermediate fits in L2, so HBM traffic is essentially the field write plus
+// the profile read (amortised over the directions of a batch).
+//
+// Output per direction and level j = 1..Nz: E1 on p = 0..Nx, q = 1..Ny-1,
+// E2 on p = 1..Nx-1, q = 0..Ny, E3 on p = 1..Nx-1, q = 1..Ny-1, row-major.
+#include <algorithm>
+
+#include "common.cuh"
+#include "fft.cuh"
+
+struct FP {
+  int nx, ny, nz, M, N, n1, n2, nap, lnx, lny, twlog;
+  int j0, lc;           // first level (1-based) and levels in this chunk
+  int ndir;
+  bool layered;
+  long long S;          // samples per level
+};
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_field_y(const C<T>* __restrict__ ap, const C<T>* __restrict__ prof,
+                                                 const C<T>* __restrict__ profq, C<T>* __restrict__ T1,
+                                                 FP p, const C<T>* __restrict__ tw) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  const int ny = p.ny, L = 2 * ny;
+  C<T>* A = (C<T>*)sm_raw;
+  C<T>* B = A + L;
+  const int r = blockIdx.x, comp = blockIdx.y, s = blockIdx.z;
+  const int d = s / p.lc, jj = s - d * p.lc;
+  const int j = p.j0 + jj;
+  if (j > p.nz) return;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int m = comp == 0 ? r : r + 1;
+  const bool valid_row = (comp == 0) || (m <= p.M);
+  const C<T>* E = ap + (size_t)d * p.nap;
+  const bool top = (j == p.nz);
+  const C<T>* Pj = prof + (size_t)(j - 1) * p.nap;
+  const C<T>* Qj = profq ? profq + (size_t)(j - 1) * (p.n1 + p.n2) : nullptr;
+  const bool ycos = (comp == 1);
+  for (int t = tid; t < L; t += nthr) A[t] = mk<T>(0, 0);
+  __syncthreads();
+  if (valid_row) {
+    for (int n = tid; n <= p.N; n += nthr) {
+      int i = -1;
+      if (comp == 0) { if (n >= 1) i = m * p.N + (n - 1); }
+      else if (comp == 1) i = p.n1 + (m - 1) * (p.N + 1) + n;
+      else { if (n >= 1) i = p.n1 + p.n2 + (m - 1) * p.N + (n - 1); }
+      if (i < 0) continue;
+      C<T> c = E[i];
+      if (!top) {
+        c = cmul<T>(Pj[i], c);
+        if (p.layered && comp < 2 && m >= 1 && n >= 1)
+          c = cadd<T>(c, cmul<T>(Qj[i], E[p.n1 + p.n2 + (m - 1) * p.N + (n - 1)]));
+      }
+      if (ycos) {
+        if (n == 0) A[0] = cscale<T>(c, (T)2);
+        else { A[n] = c; A[L - n] = c; }
+      } else {
+        A[n] = c;
+        A[L - n] = mk<T>(-c.x, -c.y);
+      }
+    }
+  }
+  __syncthreads();
+  C<T>* Z = fft_lines<T, true>(A, B, L, p.lny + 1, 1, tw, p.twlog);
+  C<T>* dst = T1 + (((size_t)s * 3 + comp) * p.nx + r) * (ny + 1);
+  for (int q = tid; q <= ny; q += nthr) {
+    C<T> v = Z[q];
+    // cos: Z/2 ; sin: Z/(2i)
+    dst[q] = ycos ? mk<T>(v.x * (T)0.5, v.y * (T)0.5) : mk<T>(v.y * (T)0.5, -v.x * (T)0.5);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_field_x(const C<T>* __restrict__ T1, C<T>* __restrict__ out, FP p,
+                                                 const C<T>* __restrict__ tw, int CB) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  const int nx = p.nx, ny = p.ny, L = 2 * nx;
+  C<T>* A = (C<T>*)sm_raw;
+  C<T>* B = A + (size_t)CB * L;
+  const int qt = blockIdx.x, comp = blockIdx.y, s = blockIdx.z;
+  const int d = s / p.lc, jj = s - d * p.lc;
+  const int j = p.j0 + jj;
+  if (j > p.nz) return;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int q0 = qt * CB;
+  const bool xcos = (comp == 0);
+  const C<T>* src = T1 + ((size_t)s * 3 + comp) * nx * (ny + 1);
+  // A[l * L + t]: line l = column q0 + l
+  for (int t = tid; t < CB * L; t += nthr) A[t] = mk<T>(0, 0);
+  __syncthreads();
+  const int nrows = xcos ? nx : nx - 1;    // E1: m = 0..M; E2/E3: m = 1..M
+  for (int t = tid; t < CB * nrows; t += nthr) {
+    const int r = t / CB, l = t - r * CB;
+    const int q = q0 + l;
+    if (q > ny) continue;
+    C<T> c = src[(size_t)r * (ny + 1) + q];
+    C<T>* line = A + (size_t)l * L;
+    if (xcos) {
+      const int m = r;
+      if (m == 0) line[0] = cscale<T>(c, (T)2);
+      else { line[m] = c; line[L - m] = c; }
+    } else {
+      const int m = r + 1;
+      line[m] = c;
+      line[L - m] = mk<T>(-c.x, -c.y);
+    }
+  }
+  __syncthreads();
+  C<T>* Z = fft_lines<T, true>(A, B, L, p.lnx + 1, CB, tw, p.twlog);
+  // output block of this component
+  long long off;
+  int ncol, qlo, qhi, plo, phi;
+  if (comp == 0) { off = 0; ncol = ny - 1; qlo = 1; qhi = ny - 1; plo = 0; phi = nx; }
+  else if (comp == 1) { off = (long long)(nx + 1) * (ny - 1); ncol = ny + 1; qlo = 0; qhi = ny; plo = 1; phi = nx - 1; }
+  else { off = (long long)(nx + 1) * (ny - 1) + (long long)(nx - 1) * (ny + 1); ncol = ny - 1; qlo = 1; qhi = ny - 1; plo = 1; phi = nx - 1; }
+  C<T>* dst = out + ((size_t)d * p.nz + (j - 1)) * p.S + off;
+  const int np = phi - plo + 1;
+  for (int t = tid; t < CB * np; t += nthr) {
+    const int pr = t / CB, l = t - pr * CB;
+    const int q = q0 + l;
+    if (q < qlo || q > qhi) continue;
+    const int pp = plo + pr;
+    C<T> v = Z[(size_t)l * L + pp];
+    C<T> o = xcos ? mk<T>(v.x * (T)0.5, v.y * (T)0.5) : mk<T>(v.y * (T)0.5, -v.x * (T)0.5);
+    dst[(size_t)pr * ncol + (q - qlo)] = o;
+  }
+}
+
+__global__ void k_ap32(const double2* __restrict__ a, float2* __restrict__ b, long long n) {
+  long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (k < n) b[k] = make_float2((float)a[k].x, (float)a[k].y);
+}
+
+template <typename T>
+cavity_status launch_field(cavity_ctx* ctx, int ndir, const double2* ap, C<T>* out) {
+  const Geo& g = ctx->g;
+  const bool layered = ctx->layers.size() > 1;
+  const size_t slab = (size_t)3 * g.nx * (g.ny + 1) * sizeof(C<T>);
+  int lc = (int)std::max<size_t>(1, ((size_t)64 << 20) / (slab * ndir));
+  lc = std::min(lc, g.nz);
+  const size_t t1 = slab * ndir * lc;
+  const size_t apb = sizeof(C<T>) == 8 ? ((sizeof(float2) * (size_t)ndir * g.nap + 255) / 256) * 256 : 0;
+  CKS(ensure_ws(ctx, &ctx->ws2, &ctx->ws2_bytes, t1 + apb));
+  C<T>* T1 = (C<T>*)((char*)ctx->ws2 + apb);
+  const C<T>* apT;
+  const C<T>* prof;
+  const C<T>* profq;
+  if (sizeof(T) == 8) {
+    apT = (const C<T>*)ap;
+    prof = (const C<T>*)ctx->prof;
+    profq = layered ? (const C<T>*)ctx->profq : nullptr;
+  } else {
+    float2* a32 = (float2*)ctx->ws2;
+    long long n = (long long)ndir * g.nap;
+    {
+      KScope ks_(ctx, KC_FIELD_Y);
+      k_ap32<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(ap, a32, n);
+    }
+    apT = (const C<T>*)a32;
+    prof = (const C<T>*)ctx->prof32;
+    profq = layered ? (const C<T>*)ctx->profq32 : nullptr;
+  }
+  const C<T>* tw = sizeof(T) == 8 ? (const C<T>*)ctx->tw64 : (const C<T>*)ctx->tw32;
+  int CB = (int)std::max<size_t>(1, std::min<size_t>(16, ((size_t)128 << 10) / (4 * g.nx * sizeof(C<T>))));
+  size_t smy = sizeof(C<T>) * 4 * g.ny, smx = sizeof(C<T>) * 2 * (size_t)CB * 2 * g.nx;
+  static size_t set_y[2] = {0, 0}, set_x[2] = {0, 0};
+  const int ti = sizeof(T) == 8 ? 0 : 1;
+  if (smy > set_y[ti]) {
+    CK(cudaFuncSetAttribute(k_field_y<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smy));
+    set_y[ti] = smy;
+  }
+  if (smx > set_x[ti]) {
+    CK(cudaFuncSetAttribute(k_field_x<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smx));
+    set_x[ti] = smx;
+  }
+  FP p;
+  p.nx = g.nx; p.ny = g.ny; p.nz = g.nz; p.M = g.M; p.N = g.N; p.n1 = g.n1; p.n2 = g.n2;
+  p.nap = g.nap; p.lnx = g.lnx; p.lny = g.lny; p.twlog = ilog2(ctx->TW);
+  p.lc = lc; p.ndir = ndir; p.layered = layered; p.S = g.field_per_level;
+  const int qtiles = (g.ny + 1 + CB - 1) / CB;
+  for (int j0 = 1; j0 <= g.nz; j0 += lc) {
+    p.j0 = j0;
+    {
+      KScope ks_(ctx, KC_FIELD_Y);
+      k_field_y<T><<<dim3(g.nx, 3, ndir * lc), 128, smy, ctx->stream>>>(apT, prof, profq, T1, p, tw);
+    }
+    {
+      KScope ks_(ctx, KC_FIELD_X);
+      k_field_x<T><<<dim3(qtiles, 3, ndir * lc), 256, smx, ctx->stream>>>(T1, out, p, tw, CB);
+    }
+  }
+  CK(cudaGetLastError());
+  return CAVITY_OK;
+}
+
+template cavity_status launch_field<double>(cavity_ctx*, int, const double2*, double2*);
+template cavity_status launch_field<float>(cavity_ctx*, int, const double2*, float2*);

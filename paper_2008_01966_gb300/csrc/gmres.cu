@@ -1,0 +1,501 @@
+// Aperture solve of (EJ1)/(uT1): restarted GMRES with right block-diagonal
+// preconditioning, batched over the incident directions (one Krylov basis per
+// right-hand side, all advanced together).
+//
+// The paper solves the aperture system directly and notes that large
+// apertures need an iterative solver (Sec. 6); GMRES is that solver here.
+// Orthogonalisation: classical Gram-Schmidt applied twice (CGS2): two batched
+// dot-product passes and two basis updates per Arnoldi step.  All reductions
+// are fixed-order block trees, so a direction's result does not depend on the
+// other directions in the batch.  The small Hessenberg least-squares problems
+// (complex Givens rotations) are solved on the host from the coefficients
+// copied back once per iteration.
+//
+// Mixed precision (CAVITY_MIXED): iterative refinement with FP64 residuals:
+//   r = b - A x (FP64 operator); solve A d = r with FP32 GMRES to ~1e-5;
+//   x += d (FP64); repeat until ||r|| <= tol ||b||.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "common.cuh"
+
+// h[d*hstride + i] = sum_e conj(V[d*vs + i*nap + e]) w[d*ws + e]   (grid (cnt, ndir))
+template <typename T>
+__global__ void __launch_bounds__(256) k_dots(const C<T>* __restrict__ V, long long vs,
+                                              const C<T>* __restrict__ w, long long ws,
+                                              double2* __restrict__ h, int hstride, int nap) {
+  const int i = blockIdx.x, d = blockIdx.y;
+  const C<T>* v = V + (size_t)d * vs + (size_t)i * nap;
+  const C<T>* x = w + (size_t)d * ws;
+  double sr = 0, si = 0;
+  for (int e = threadIdx.x; e < nap; e += blockDim.x) {
+    C<T> a = v[e], b = x[e];
+    sr += (double)a.x * b.x + (double)a.y * b.y;
+    si += (double)a.x * b.y - (double)a.y * b.x;
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    sr += __shfl_xor_sync(0xffffffffu, sr, off);
+    si += __shfl_xor_sync(0xffffffffu, si, off);
+  }
+  __shared__ double rr[8], ri[8];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) { rr[wid] = sr; ri[wid] = si; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0, b = 0;
+    for (int k = 0; k < 8; ++k) { a += rr[k]; b += ri[k]; }
+    h[(size_t)d * hstride + i] = make_double2(a, b);
+  }
+}
+
+// w[d][e] += sgn * sum_{i<cnt} V[d*vs + i*nap + e] c[d*cstride + i]
+template <typename T>
+__global__ void k_basis_axpy(const C<T>* __restrict__ V, long long vs, const double2* __restrict__ c,
+                             int cstride, int cnt, C<T>* __restrict__ w, int nap, int ndir, double sgn) {
+  long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (gid >= (long long)ndir * nap) return;
+  const int d = (int)(gid / nap), e = (int)(gid - (long long)d * nap);
+  const C<T>* v = V + (size_t)d * vs + e;
+  double ar = 0, ai = 0;
+  for (int i = 0; i < cnt; ++i) {
+    C<T> a = v[(size_t)i * nap];
+    double2 b = c[(size_t)d * cstride + i];
+    ar += (double)a.x * b.x - (double)a.y * b.y;
+    ai += (double)a.x * b.y + (double)a.y * b.x;
+  }
+  C<T> o = w[gid];
+  w[gid] = mk<T>((T)(o.x + sgn * ar), (T)(o.y + sgn * ai));
+}
+
+// out[d*os + e] = s[d] * in[d*is + e]
+template <typename T>
+__global__ void k_copy_scale(const C<T>* __restrict__ in, long long is, C<T>* __restrict__ out,
+                             long long os, const double* __restrict__ s, int nap, int ndir) {
+  long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (gid >= (long long)ndir * nap) return;
+  const int d = (int)(gid / nap), e = (int)(gid - (long long)d * nap);
+  C<T> a = in[(size_t)d * is + e];
+  T f = (T)s[d];
+  out[(size_t)d * os + e] = mk<T>(a.x * f, a.y * f);
+}
+
+// y += x  (contiguous [d][nap])
+template <typename T>
+__global__ void k_add(const C<T>* __restrict__ x, C<T>* __restrict__ y, long long n) {
+  long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (k < n) y[k] = cadd<T>(y[k], x[k]);
+}
+
+// w = b - w
+template <typename T>
+__global__ void k_bminus(const C<T>* __restrict__ b, C<T>* __restrict__ w, long long n) {
+  long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (k < n) w[k] = csub<T>(b[k], w[k]);
+}
+
+// x64 += d32 / s[d]
+__global__ void k_acc32(double2* __restrict__ x, const float2* __restrict__ dx,
+                        const double* __restrict__ s, int nap, int ndir) {
+  long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (gid >= (long long)ndir * nap) return;
+  const int d = (int)(gid / nap);
+  const double f = s[d] > 0 ? 1.0 / s[d] : 0.0;
+  x[gid].x += f * (double)dx[gid].x;
+  x[gid].y += f * (double)dx[gid].y;
+}
+
+// r32 = s[d] * r64
+__global__ void k_to32(const double2* __restrict__ r, float2* __restrict__ o,
+                       const double* __restrict__ s, int nap, int ndir) {
+  long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (gid >= (long long)ndir * nap) return;
+  const int d = (int)(gid / nap);
+  o[gid] = make_float2((float)(r[gid].x * s[d]), (float)(r[gid].y * s[d]));
+}
+
+static inline unsigned nblk(long long n, int b) { return (unsigned)((n + b - 1) / b); }
+
+static inline double2 h_add(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+static inline double2 h_mul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+static inline double2 h_conj(double2 a) { return make_double2(a.x, -a.y); }
+static inline double h_abs(double2 a) { return std::hypot(a.x, a.y); }
+
+template <typename T> struct GW {
+  C<T>* V;      // ndir x (m+1) x nap
+  C<T>* w;      // ndir x nap
+  C<T>* z;      // ndir x nap
+  double2* h;   // ndir x (m+1)
+  double2* h2;  // ndir x (m+1)
+  double2* y;   // ndir x (m+1)
+  double* s;    // ndir
+  void* apw;    // operator workspace
+};
+
+template <typename T>
+static size_t gw_bytes(const Geo& g, int ndir, int m) {
+  size_t b = 0;
+  auto al = [](size_t x) { return (x + 255) / 256 * 256; };
+  b += al(sizeof(C<T>) * (size_t)ndir * (m + 1) * g.nap);
+  b += 2 * al(sizeof(C<T>) * (size_t)ndir * g.nap);
+  b += 3 * al(sizeof(double2) * (size_t)ndir * (m + 1));
+  b += al(sizeof(double) * ndir);
+  b += al(apply_work_bytes(g, ndir, sizeof(C<T>)));
+  return b;
+}
+
+template <typename T>
+static GW<T> gw_carve(void* base, const Geo& g, int ndir, int m) {
+  auto al = [](size_t x) { return (x + 255) / 256 * 256; };
+  char* p = (char*)base;
+  GW<T> W;
+  W.V = (C<T>*)p; p += al(sizeof(C<T>) * (size_t)ndir * (m + 1) * g.nap);
+  W.w = (C<T>*)p; p += al(sizeof(C<T>) * (size_t)ndir * g.nap);
+  W.z = (C<T>*)p; p += al(sizeof(C<T>) * (size_t)ndir * g.nap);
+  W.h = (double2*)p; p += al(sizeof(double2) * (size_t)ndir * (m + 1));
+  W.h2 = (double2*)p; p += al(sizeof(double2) * (size_t)ndir * (m + 1));
+  W.y = (double2*)p; p += al(sizeof(double2) * (size_t)ndir * (m + 1));
+  W.s = (double*)p; p += al(sizeof(double) * ndir);
+  W.apw = p;
+  return W;
+}
+
+// norms of ndir contiguous vectors (host result)
+template <typename T>
+static cavity_status norms(cavity_ctx* ctx, const C<T>* v, int ndir, double2* scratch, int sstride,
+                           std::vector<double>& out) {
+  const int nap = ctx->g.nap;
+  {
+    KScope ks_(ctx, KC_KRYLOV);
+    k_dots<T><<<dim3(1, ndir), 256, 0, ctx->stream>>>(v, nap, v, nap, scratch, sstride, nap);
+  }
+  std::vector<double2> hh((size_t)ndir);
+  CK(cudaMemcpy2DAsync(hh.data(), sizeof(double2), scratch, sizeof(double2) * sstride,
+                       sizeof(double2), ndir, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  out.resize(ndir);
+  for (int d = 0; d < ndir; ++d) out[d] = std::sqrt(std::max(hh[d].x, 0.0));
+  return CAVITY_OK;
+}
+
+// Solve A x = b (x starts at zero).  tol[d]: relative target per direction.
+// iters[d] accumulates Arnoldi steps; est[d] is the final GMRES residual
+// estimate relative to ||b_d||.
+template <typename T>
+static cavity_status gmres_core(cavity_ctx* ctx, int ndir, const C<T>* b, C<T>* x,
+                                const std::vector<double>& tol, int m, int maxit, GW<T> W,
+                                std::vector<int>& iters, std::vector<double>& est) {
+  const Geo& g = ctx->g;
+  const int nap = g.nap;
+  const long long nv = (long long)ndir * nap;
+  const long long vs = (long long)(m + 1) * nap;
+  cudaStream_t st = ctx->stream;
+  std::vector<double> bnorm, rn;
+  CKS(norms<T>(ctx, b, ndir, W.h, m + 1, bnorm));
+  rn = bnorm;
+  est.assign(ndir, 0.0);
+  CK(cudaMemsetAsync(x, 0, sizeof(C<T>) * nv, st));
+  CK(cudaMemcpyAsync(W.w, b, sizeof(C<T>) * nv, cudaMemcpyDeviceToDevice, st));   // r = b
+  std::vector<char> done(ndir, 0);
+  for (int d = 0; d < ndir; ++d) {
+    if (!(bnorm[d] > 0)) done[d] = 1;
+    else est[d] = 1.0;
+  }
+  std::vector<double> sc(ndir);
+  std::vector<double2> h1((size_t)ndir * (m + 1)), h2v((size_t)ndir * (m + 1)), nw((size_t)ndir * (m + 1));
+  std::vector<double2> hy((size_t)ndir * (m + 1));
+  int total = 0;
+  while (true) {
+    bool alldone = true;
+    for (int d = 0; d < ndir; ++d) alldone = alldone && done[d];
+    if (alldone || total >= maxit) break;
+    // V_0 = r / ||r||
+    for (int d = 0; d < ndir; ++d) sc[d] = (!done[d] && rn[d] > 0) ? 1.0 / rn[d] : 0.0;
+    CK(cudaMemcpyAsync(W.s, sc.data(), sizeof(double) * ndir, cudaMemcpyHostToDevice, st));
+    {
+      KScope ks_(ctx, KC_KRYLOV);
+      k_copy_scale<T><<<nblk(nv, 256), 256, 0, st>>>(W.w, nap, W.V, vs, W.s, nap, ndir);
+    }
+    std::vector<std::vector<std::vector<double2>>> H(ndir);
+    std::vector<std::vector<double>> cs(ndir, std::vector<double>(m, 0.0));
+    std::vector<std::vector<double2>> sn(ndir, std::vector<double2>(m, make_double2(0, 0)));
+    std::vector<std::vector<double2>> gv(ndir, std::vector<double2>(m + 1, make_double2(0, 0)));
+    std::vector<int> kd(ndir, 0);
+    std::vector<char> act(ndir, 0);
+    for (int d = 0; d < ndir; ++d) {
+      act[d] = !done[d];
+      gv[d][0] = make_double2(rn[d], 0);
+    }
+    for (int k = 0; k < m && total < maxit; ++k, ++total) {
+      // w = A M^{-1} V_k
+      std::fill(sc.begin(), sc.end(), 1.0);
+      CK(cudaMemcpyAsync(W.s, sc.data(), sizeof(double) * ndir, cudaMemcpyHostToDevice, st));
+      {
+        KScope ks_(ctx, KC_KRYLOV);
+        k_copy_scale<T><<<nblk(nv, 256), 256, 0, st>>>(W.V + (size_t)k * nap, vs, W.w, nap, W.s, nap, ndir);
+      }
+      CKS(launch_precond_apply<T>(ctx, ndir, W.w, W.z));
+      CKS(launch_apply<T>(ctx, ndir, W.z, W.w, W.apw));
+      // CGS2
+      {
+        KScope ks_(ctx, KC_KRYLOV);
+        k_dots<T><<<dim3(k + 1, ndir), 256, 0, st>>>(W.V, vs, W.w, nap, W.h, m + 1, nap);
+      }
+      {
+        KScope ks_(ctx, KC_KRYLOV);
+        k_basis_axpy<T><<<nblk(nv, 256), 256, 0, st>>>(W.V, vs, W.h, m + 1, k + 1, W.w, nap, ndir, -1.0);
+      }
+      {
+        KScope ks_(ctx, KC_KRYLOV);
+        k_dots<T><<<dim3(k + 1, ndir), 256, 0, st>>>(W.V, vs, W.w, nap, W.h2, m + 1, nap);
+      }
+      {
+        KScope ks_(ctx, KC_KRYLOV);
+        k_basis_axpy<T><<<nblk(nv, 256), 256, 0, st>>>(W.V, vs, W.h2, m + 1, k + 1, W.w, nap, ndir, -1.0);
+      }
+      {
+        KScope ks_(ctx, KC_KRYLOV);
+        k_dots<T><<<dim3(1, ndir), 256, 0, st>>>(W.w, nap, W.w, nap, W.y, m + 1, nap);
+      }
+      CK(cudaMemcpyAsync(h1.data(), W.h, sizeof(double2) * ndir * (m + 1), cudaMemcpyDeviceToHost, st));
+      CK(cudaMemcpyAsync(h2v.data(), W.h2, sizeof(double2) * ndir * (m + 1), cudaMemcpyDeviceToHost, st));
+      CK(cudaMemcpyAsync(nw.data(), W.y, sizeof(double2) * ndir * (m + 1), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      bool any = false;
+      for (int d = 0; d < ndir; ++d) {
+        sc[d] = 0.0;
+        if (!act[d]) continue;
+        const double hn = std::sqrt(std::max(nw[(size_t)d * (m + 1)].x, 0.0));
+        std::vector<double2> col(k + 2);
+        for (int i = 0; i <= k; ++i)
+          col[i] = h_add(h1[(size_t)d * (m + 1) + i], h2v[(size_t)d * (m + 1) + i]);
+        col[k + 1] = make_double2(hn, 0);
+        for (int i = 0; i < k; ++i) {
+          double2 a = col[i], bb = col[i + 1];
+          const double c = cs[d][i];
+          const double2 s = sn[d][i];
+          col[i] = h_add(make_double2(c * a.x, c * a.y), h_mul(s, bb));
+          double2 t = h_mul(h_conj(s), a);
+          col[i + 1] = make_double2(c * bb.x - t.x, c * bb.y - t.y);
+        }
+        double2 a = col[k], bb = col[k + 1];
+        const double na = h_abs(a), nb = h_abs(bb), rho = std::hypot(na, nb);
+        double c;
+        double2 s, r;
+        if (na == 0.0) {
+          c = 0.0;
+          s = nb > 0 ? make_double2(bb.x / nb, -bb.y / nb) : make_double2(1, 0);
+          r = make_double2(nb, 0);
+        } else {
+          const double2 ph = make_double2(a.x / na, a.y / na);
+          c = na / rho;
+          // s = (a/|a|) conj(b) / rho
+          s = make_double2((ph.x * bb.x + ph.y * bb.y) / rho, (ph.y * bb.x - ph.x * bb.y) / rho);
+          r = make_double2(ph.x * rho, ph.y * rho);
+        }
+        cs[d][k] = c;
+        sn[d][k] = s;
+        col[k] = r;
+        col[k + 1] = make_double2(0, 0);
+        const double2 gk = gv[d][k];
+        gv[d][k] = make_double2(c * gk.x, c * gk.y);
+        const double2 t = h_mul(h_conj(s), gk);
+        gv[d][k + 1] = make_double2(-t.x, -t.y);
+        H[d].push_back(col);
+        kd[d] = k + 1;
+        iters[d] += 1;
+        const double e = h_abs(gv[d][k + 1]);
+        est[d] = e / bnorm[d];
+        const bool breakdown = hn <= 1e-300 || hn < 1e-15 * rho;
+        if (e <= tol[d] * bnorm[d] || breakdown) act[d] = 0;
+        else sc[d] = 1.0 / hn;
+        any = any || act[d];
+      }
+      CK(cudaMemcpyAsync(W.s, sc.data(), sizeof(double) * ndir, cudaMemcpyHostToDevice, st));
+      {
+        KScope ks_(ctx, KC_KRYLOV);
+        k_copy_scale<T><<<nblk(nv, 256), 256, 0, st>>>(W.w, nap, W.V + (size_t)(k + 1) * nap, vs, W.s,
+                                                        nap, ndir);
+      }
+      if (!any) { ++total; break; }
+    }
+    // y = H^{-1} g; x += M^{-1} (V y)
+    std::fill(hy.begin(), hy.end(), make_double2(0, 0));
+    int kmax = 0;
+    for (int d = 0; d < ndir; ++d) {
+      const int kk = kd[d];
+      kmax = std::max(kmax, kk);
+      for (int i = kk - 1; i >= 0; --i) {
+        double2 s = gv[d][i];
+        for (int j = i + 1; j < kk; ++j) {
+          double2 t = h_mul(H[d][j][i], hy[(size_t)d * (m + 1) + j]);
+          s = make_double2(s.x - t.x, s.y - t.y);
+        }
+        const double2 dg = H[d][i][i];
+        const double den = dg.x * dg.x + dg.y * dg.y;
+        hy[(size_t)d * (m + 1) + i] =
+            den > 0 ? make_double2((s.x * dg.x + s.y * dg.y) / den, (s.y * dg.x - s.x * dg.y) / den)
+                    : make_double2(0, 0);
+      }
+    }
+    CK(cudaMemcpyAsync(W.y, hy.data(), sizeof(double2) * ndir * (m + 1), cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(W.w, 0, sizeof(C<T>) * nv, st));
+    {
+      KScope ks_(ctx, KC_KRYLOV);
+      k_basis_axpy<T><<<nblk(nv, 256), 256, 0, st>>>(W.V, vs, W.y, m + 1, kmax, W.w, nap, ndir, 1.0);
+    }
+    CKS(launch_precond_apply<T>(ctx, ndir, W.w, W.z));
+    {
+      KScope ks_(ctx, KC_KRYLOV);
+      k_add<T><<<nblk(nv, 256), 256, 0, st>>>(W.z, x, nv);
+    }
+    for (int d = 0; d < ndir; ++d)
+      if (est[d] <= tol[d]) done[d] = 1;
+    bool finished = true;
+    for (int d = 0; d < ndir; ++d) finished = finished && done[d];
+    if (finished || total >= maxit) break;
+    // restart from the true residual r = b - A x
+    CKS(launch_apply<T>(ctx, ndir, x, W.w, W.apw));
+    {
+      KScope ks_(ctx, KC_KRYLOV);
+      k_bminus<T><<<nblk(nv, 256), 256, 0, st>>>(b, W.w, nv);
+    }
+    CKS(norms<T>(ctx, W.w, ndir, W.h, m + 1, rn));
+    for (int d = 0; d < ndir; ++d) {
+      if (bnorm[d] > 0) est[d] = rn[d] / bnorm[d];
+      if (est[d] <= tol[d]) done[d] = 1;
+    }
+  }
+  CK(cudaGetLastError());
+  return CAVITY_OK;
+}
+
+static void solver_params(const cavity_ctx* ctx, double& tol, int& m, int& maxit) {
+  tol = ctx->desc.gmres_tol > 0 ? ctx->desc.gmres_tol : 1e-12;
+  m = ctx->desc.gmres_restart > 0 ? ctx->desc.gmres_restart : 40;
+  maxit = ctx->desc.gmres_max_iter > 0 ? ctx->desc.gmres_max_iter : 400;
+}
+
+// FP64 path: GMRES in FP64, then the true residual.
+cavity_status run_gmres64(cavity_ctx* ctx, int ndir, const double2* b, double2* x, int* iters,
+                          double* resid) {
+  const Geo& g = ctx->g;
+  double tol;
+  int m, maxit;
+  solver_params(ctx, tol, m, maxit);
+  size_t need = gw_bytes<double>(g, ndir, m);
+  CKS(ensure_ws(ctx, &ctx->ws, &ctx->ws_bytes, need));
+  GW<double> W = gw_carve<double>(ctx->ws, g, ndir, m);
+  std::vector<int> it(ndir, 0);
+  std::vector<double> est;
+  std::vector<double> tv(ndir, tol);
+  CKS(gmres_core<double>(ctx, ndir, b, x, tv, m, maxit, W, it, est));
+  // true residual
+  const long long nv = (long long)ndir * g.nap;
+  CKS(launch_apply<double>(ctx, ndir, x, W.w, W.apw));
+  {
+    KScope ks_(ctx, KC_KRYLOV);
+    k_bminus<double><<<nblk(nv, 256), 256, 0, ctx->stream>>>(b, W.w, nv);
+  }
+  std::vector<double> rn, bn;
+  CKS(norms<double>(ctx, W.w, ndir, W.h, m + 1, rn));
+  CKS(norms<double>(ctx, b, ndir, W.h, m + 1, bn));
+  bool ok = true;
+  for (int d = 0; d < ndir; ++d) {
+    double r = bn[d] > 0 ? rn[d] / bn[d] : 0.0;
+    if (iters) iters[d] = it[d];
+    if (resid) resid[d] = r;
+    ok = ok && (r <= tol * 10);
+  }
+  if (!ok) {
+    ctx->err = "aperture GMRES stopped above tolerance";
+    return CAVITY_ENOCONV;
+  }
+  return CAVITY_OK;
+}
+
+// MIXED path: FP64 iterative refinement around FP32 GMRES.
+cavity_status run_mixed_solve(cavity_ctx* ctx, int ndir, const double2* b, double2* x, int* iters,
+                              double* resid) {
+  const Geo& g = ctx->g;
+  double tol;
+  int m, maxit;
+  solver_params(ctx, tol, m, maxit);
+  auto al = [](size_t v) { return (v + 255) / 256 * 256; };
+  const long long nv = (long long)ndir * g.nap;
+  size_t n32 = gw_bytes<float>(g, ndir, m);
+  size_t extra = 3 * al(sizeof(double2) * nv) + 2 * al(sizeof(float2) * nv) +
+                 al(apply_work_bytes(g, ndir, sizeof(double2))) + al(sizeof(double) * ndir) +
+                 al(sizeof(double2) * ndir);
+  CKS(ensure_ws(ctx, &ctx->ws, &ctx->ws_bytes, n32 + extra));
+  GW<float> W = gw_carve<float>(ctx->ws, g, ndir, m);
+  char* p = (char*)ctx->ws + n32;
+  double2* r64 = (double2*)p; p += al(sizeof(double2) * nv);
+  double2* tmp64 = (double2*)p; p += al(sizeof(double2) * nv);
+  p += al(sizeof(double2) * nv);
+  float2* r32 = (float2*)p; p += al(sizeof(float2) * nv);
+  float2* d32 = (float2*)p; p += al(sizeof(float2) * nv);
+  void* apw64 = p; p += al(apply_work_bytes(g, ndir, sizeof(double2)));
+  double* sdev = (double*)p; p += al(sizeof(double) * ndir);
+  double2* sc2 = (double2*)p;
+  cudaStream_t st = ctx->stream;
+  std::vector<double> bn, rn;
+  CK(cudaMemsetAsync(x, 0, sizeof(double2) * nv, st));
+  CK(cudaMemcpyAsync(r64, b, sizeof(double2) * nv, cudaMemcpyDeviceToDevice, st));
+  CKS(norms<double>(ctx, b, ndir, sc2, 1, bn));
+  rn = bn;
+  std::vector<int> it(ndir, 0);
+  std::vector<double> est, s(ndir), tin(ndir);
+  int used = 0;
+  bool conv = false;
+  for (int outer = 0; outer < 12 && used < maxit; ++outer) {
+    bool all = true;
+    for (int d = 0; d < ndir; ++d) all = all && (bn[d] == 0 || rn[d] <= tol * bn[d]);
+    if (all) { conv = true; break; }
+    for (int d = 0; d < ndir; ++d) {
+      s[d] = rn[d] > 0 ? 1.0 / rn[d] : 0.0;
+      // reduction still needed, with margin; FP32 reaches about 1e-6
+      double need = bn[d] > 0 ? 0.5 * tol * bn[d] / std::max(rn[d], 1e-300) : 1.0;
+      tin[d] = std::min(0.5, std::max(need, 1e-5));
+      if (bn[d] == 0 || rn[d] <= tol * bn[d]) s[d] = 0.0;
+    }
+    CK(cudaMemcpyAsync(sdev, s.data(), sizeof(double) * ndir, cudaMemcpyHostToDevice, st));
+    {
+      KScope ks_(ctx, KC_KRYLOV);
+      k_to32<<<nblk(nv, 256), 256, 0, st>>>(r64, r32, sdev, g.nap, ndir);
+    }
+    std::vector<int> it_in(ndir, 0);
+    CKS(gmres_core<float>(ctx, ndir, r32, d32, tin, m, maxit - used, W, it_in, est));
+    int mx = 0;
+    for (int d = 0; d < ndir; ++d) { it[d] += it_in[d]; mx = std::max(mx, it_in[d]); }
+    used += std::max(mx, 1);
+    {
+      KScope ks_(ctx, KC_KRYLOV);
+      k_acc32<<<nblk(nv, 256), 256, 0, st>>>(x, d32, sdev, g.nap, ndir);
+    }
+    // r = b - A x in FP64
+    CKS(launch_apply<double>(ctx, ndir, x, tmp64, apw64));
+    CK(cudaMemcpyAsync(r64, b, sizeof(double2) * nv, cudaMemcpyDeviceToDevice, st));
+    {
+      KScope ks_(ctx, KC_KRYLOV);
+      k_bminus<double><<<nblk(nv, 256), 256, 0, st>>>(b, tmp64, nv);
+    }
+    CK(cudaMemcpyAsync(r64, tmp64, sizeof(double2) * nv, cudaMemcpyDeviceToDevice, st));
+    CKS(norms<double>(ctx, r64, ndir, sc2, 1, rn));
+  }
+  bool all = true;
+  for (int d = 0; d < ndir; ++d) {
+    double r = bn[d] > 0 ? rn[d] / bn[d] : 0.0;
+    if (iters) iters[d] = it[d];
+    if (resid) resid[d] = r;
+    all = all && r <= tol;
+  }
+  conv = conv || all;
+  if (!conv) {
+    ctx->err = "mixed-precision aperture solve stopped above tolerance";
+    return CAVITY_ENOCONV;
+  }
+  return CAVITY_OK;
+}

@@ -1,0 +1,122 @@
+// Kernel table of Sec. 5.2: the 2-D Fourier transform of the truncated
+// free-space Green's function,
+//     F(G)(rho) = 1/2 int_0^R J0(2 pi rho r) exp(i kappa0 r) dr,
+// R = sqrt(2) max(a, b), at rho = |(j1/Lx, j2/Ly)| for the quarter box
+// 0 <= j1 < Px/2, 0 <= j2 < Py/2 (the table is even in j1 and in j2).
+// (The paper prints 1/(4 pi) in front of the radial integral; the angular
+// integral contributes 2 pi J0, hence the 1/2.)
+//
+// The integrand is entire, so composite Gauss-Legendre quadrature converges
+// geometrically: panels no wider than pi / (2 pi rho + |kappa0|), 16 nodes
+// each.  One warp per table entry, lanes striding over panels, a fixed-order
+// shuffle reduction (deterministic).  FP64 throughout; J0 is CUDA's j0().
+#include <cmath>
+#include <vector>
+
+#include "common.cuh"
+
+#define GLN 16
+__constant__ double c_gl_x[GLN];
+__constant__ double c_gl_w[GLN];
+
+// Gauss-Legendre nodes and weights on [-1, 1] by Newton's iteration on the
+// three-term recurrence of the Legendre polynomials.
+static void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.resize(n);
+  w.resize(n);
+  for (int i = 0; i < n; ++i) {
+    double z = std::cos(M_PI * (i + 0.75) / (n + 0.5));
+    double dp = 0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+      double dz = p1 / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-17) break;
+    }
+    double p0 = 1.0, p1 = z;
+    for (int k = 2; k <= n; ++k) {
+      double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+      p0 = p1;
+      p1 = p2;
+    }
+    dp = n * (z * p1 - p0) / (z * z - 1.0);
+    x[i] = z;
+    w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+__global__ void k_khat(double2* __restrict__ raw, double2* __restrict__ s64, float2* __restrict__ s32,
+                       int hx, int hy, double Lx, double Ly, double kappa0, double R, double scale) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= hx * hy) return;
+  const int j1 = warp / hy, j2 = warp - j1 * hy;
+  const double r1 = j1 / Lx, r2 = j2 / Ly;
+  const double rho = sqrt(r1 * r1 + r2 * r2);
+  const double c = 2.0 * M_PI * rho;
+  const double omega = c + fabs(kappa0);
+  int npan = (int)ceil(omega * R / M_PI);
+  if (npan < 1) npan = 1;
+  const double width = R / npan;
+  double sr = 0.0, si = 0.0;
+  for (int pn = lane; pn < npan; pn += 32) {
+    const double r0 = pn * width;
+    double pr = 0.0, pi_ = 0.0;
+#pragma unroll
+    for (int k = 0; k < GLN; ++k) {
+      const double r = r0 + 0.5 * width * (c_gl_x[k] + 1.0);
+      double s, co;
+      sincos(kappa0 * r, &s, &co);
+      const double jv = j0(c * r) * c_gl_w[k];
+      pr += jv * co;
+      pi_ += jv * s;
+    }
+    sr += 0.5 * width * pr;
+    si += 0.5 * width * pi_;
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    sr += __shfl_xor_sync(0xffffffffu, sr, off);
+    si += __shfl_xor_sync(0xffffffffu, si, off);
+  }
+  if (lane == 0) {
+    double2 v = make_double2(0.5 * sr, 0.5 * si);
+    size_t o = (size_t)j1 * hy + j2;
+    raw[o] = v;
+    s64[o] = make_double2(v.x * scale, v.y * scale);
+    s32[o] = make_float2((float)(v.x * scale), (float)(v.y * scale));
+  }
+}
+
+cavity_status launch_khat(cavity_ctx* ctx, double kappa0) {
+  const Geo& g = ctx->g;
+  static bool gl_done = false;
+  if (!gl_done) {
+    std::vector<double> x, w;
+    gauss_legendre(GLN, x, w);
+    CK(cudaMemcpyToSymbol(c_gl_x, x.data(), sizeof(double) * GLN));
+    CK(cudaMemcpyToSymbol(c_gl_w, w.data(), sizeof(double) * GLN));
+    gl_done = true;
+  }
+  const int hx = g.Px / 2, hy = g.Py / 2;
+  size_t n = (size_t)hx * hy;
+  if (!ctx->khat64) {
+    CK(cudaMalloc(&ctx->khat64, sizeof(double2) * n));
+    CK(cudaMalloc(&ctx->khat32, sizeof(float2) * n));
+    CK(cudaMalloc(&ctx->khat_raw, sizeof(double2) * n));
+  }
+  const long long threads = (long long)n * 32;
+  {
+    KScope ks_(ctx, KC_SETUP);
+    k_khat<<<(unsigned)((threads + 255) / 256), 256, 0, ctx->stream>>>(
+        ctx->khat_raw, ctx->khat64, ctx->khat32, hx, hy, g.Lx, g.Ly, kappa0, g.R,
+        1.0 / (g.Lx * g.Ly));
+  }
+  CK(cudaGetLastError());
+  return CAVITY_OK;
+}

@@ -1,0 +1,461 @@
+// The aperture operator of (EJ1)/(uT1): the cavity (local) part and the TBC
+// part whose singular integrals follow Sec. 5 (discrete rule: periodised FFT
+// convolution with the exact transform of the truncated basis, the kernel
+// table F(G), inverse transform on the torus grid, trapezoid outer rule).
+//
+// For each right-hand side the TBC needs three convolution-projections,
+//   U1 = <cs_mn, G*u1>,  U2 = <sc_mn, G*u2>,  W = <cc_mn, G*w>,
+// u1 = sum E1 cs, u2 = sum E2 sc, w = div_Gamma(z x E) = sum (k2 pi/b) E1 cc -
+// sum (k1 pi/a) E2 cc (Sec. 5.1 reduces every coefficient to I1, I2, I3).
+// Each one is four passes of batched line transforms in shared memory:
+//   A  (rows k1)   basis transform along x2: FFT convolution of the mirrored
+//                  coefficients with the 1-D kernel E(nu) of F(F)
+//   B  (cols j2)   basis transform along x1, times F(G)/(Lx Ly), inverse DFT
+//                  along x1 evaluated at the nodes p = 0..Nx
+//   C  (rows p)    inverse DFT along x2 at q = 0..Ny, trapezoid projection
+//                  onto cos/sin(n pi q/Ny) (an extended FFT of length 2Ny)
+//   D  (cols n)    trapezoid projection along x1 (extended FFT of length 2Nx)
+// and a final elementwise pass adds the local part of (EJ1)/(uT1).
+// Templated on the arithmetic type: FP64 for the FP64 path and the residuals,
+// FP32 for the inner Krylov iterations of the mixed path.
+#include <algorithm>
+
+#include "common.cuh"
+#include "fft.cuh"
+
+struct TbcP {
+  int nx, ny, M, N, Px, Py, lPx, lPy, lnx, lny, nap, n1, n2;
+  double a, b, h, k2x2;  // k2x2 = 2 kappa0^2
+  int twlog;
+};
+
+static TbcP make_params(const cavity_ctx* ctx) {
+  const Geo& g = ctx->g;
+  TbcP p;
+  p.nx = g.nx; p.ny = g.ny; p.M = g.M; p.N = g.N; p.Px = g.Px; p.Py = g.Py;
+  p.lPx = g.lPx; p.lPy = g.lPy; p.lnx = g.lnx; p.lny = g.lny;
+  p.nap = g.nap; p.n1 = g.n1; p.n2 = g.n2;
+  p.a = g.a; p.b = g.b; p.h = g.h; p.k2x2 = 2.0 * ctx->kappa0 * ctx->kappa0;
+  p.twlog = ilog2(ctx->TW);
+  return p;
+}
+
+template <typename T> __device__ __forceinline__ C<T> czero() { return mk<T>(0, 0); }
+
+// ------------------------------------------------------------------ setup
+__global__ void k_twiddles(double2* tw64, float2* tw32, int TW) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= TW) return;
+  double s, c;
+  sincospi(-2.0 * (double)k / (double)TW, &s, &c);
+  tw64[k] = make_double2(c, s);
+  tw32[k] = make_float2((float)c, (float)s);
+}
+
+cavity_status launch_twiddles(cavity_ctx* ctx) {
+  int TW = ctx->TW;
+  CK(cudaMalloc(&ctx->tw64, sizeof(double2) * TW));
+  CK(cudaMalloc(&ctx->tw32, sizeof(float2) * TW));
+  {
+    KScope ks_(ctx, KC_SETUP);
+    k_twiddles<<<(TW + 255) / 256, 256, 0, ctx->stream>>>(ctx->tw64, ctx->tw32, TW);
+  }
+  CK(cudaGetLastError());
+  return CAVITY_OK;
+}
+
+// eps(d) = E(d/L) = int_0^side exp(-2 pi i (d/L) y) dy for |d| <= P-1 (0 at d=-P),
+// transformed with a length-2P FFT; the convolution scale (1/2 for the cosine
+// basis, 1/(2i) for the sine basis) and the 1/(2P) of the inverse are folded in.
+__global__ void k_ehat(double2* out64, float2* out32, int P, int lP, double side, int pad,
+                       int kind, const double2* __restrict__ tw, int twlog) {
+  extern __shared__ double2 sm_e[];
+  const int Q = 2 * P;
+  double2* A = sm_e;
+  double2* B = sm_e + Q;
+  for (int t = threadIdx.x; t < Q; t += blockDim.x) {
+    int d = t < P ? t : t - Q;
+    double2 v;
+    if (d == 0) {
+      v = make_double2(side, 0.0);
+    } else if (d == -P) {
+      v = make_double2(0.0, 0.0);
+    } else {
+      // (1 - exp(-2 pi i d / pad)) * L / (2 pi i d),  L = pad * side
+      double s, c;
+      sincospi(-2.0 * (double)d / (double)pad, &s, &c);
+      double2 num = make_double2(1.0 - c, -s);
+      double L = pad * side;
+      double f = L / (2.0 * M_PI * (double)d);
+      // num / i = (num.y, -num.x)
+      v = make_double2(num.y * f, -num.x * f);
+    }
+    A[t] = v;
+  }
+  __syncthreads();
+  double2* R = fft_lines<double, false>(A, B, Q, lP + 1, 1, tw, twlog);
+  for (int t = threadIdx.x; t < Q; t += blockDim.x) {
+    double2 v = R[t];
+    double sc = 1.0 / (double)Q;
+    double2 r;
+    if (kind == 0) r = make_double2(0.5 * sc * v.x, 0.5 * sc * v.y);   // * 1/2
+    else r = make_double2(0.5 * sc * v.y, -0.5 * sc * v.x);           // * 1/(2i)
+    out64[t] = r;
+    out32[t] = make_float2((float)r.x, (float)r.y);
+  }
+}
+
+cavity_status launch_ehat(cavity_ctx* ctx) {
+  const Geo& g = ctx->g;
+  int twlog = ilog2(ctx->TW);
+  for (int kind = 0; kind < 2; ++kind) {
+    CK(cudaMalloc(&ctx->ehat_x64[kind], sizeof(double2) * 2 * g.Px));
+    CK(cudaMalloc(&ctx->ehat_x32[kind], sizeof(float2) * 2 * g.Px));
+    CK(cudaMalloc(&ctx->ehat_y64[kind], sizeof(double2) * 2 * g.Py));
+    CK(cudaMalloc(&ctx->ehat_y32[kind], sizeof(float2) * 2 * g.Py));
+    size_t smx = sizeof(double2) * 4 * g.Px, smy = sizeof(double2) * 4 * g.Py;
+    CK(cudaFuncSetAttribute(k_ehat, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)std::max(smx, smy)));
+    {
+      KScope ks_(ctx, KC_SETUP);
+      k_ehat<<<1, 512, smx, ctx->stream>>>(ctx->ehat_x64[kind], ctx->ehat_x32[kind], g.Px,
+                                            g.lPx, g.a, g.pad, kind, ctx->tw64, twlog);
+    }
+    {
+      KScope ks_(ctx, KC_SETUP);
+      k_ehat<<<1, 512, smy, ctx->stream>>>(ctx->ehat_y64[kind], ctx->ehat_y32[kind], g.Py,
+                                            g.lPy, g.b, g.pad, kind, ctx->tw64, twlog);
+    }
+    CK(cudaGetLastError());
+  }
+  return CAVITY_OK;
+}
+
+// ------------------------------------------------------------------ pass A
+// grid (nx rows k1, 3 fields, ndir); field 0: cs (E1), 1: sc (E2), 2: cc (w)
+template <typename T>
+__global__ void __launch_bounds__(256) k_tbcA(const C<T>* __restrict__ x, C<T>* __restrict__ Vy,
+                                              TbcP p, const C<T>* __restrict__ tw,
+                                              const C<T>* __restrict__ eh_c,
+                                              const C<T>* __restrict__ eh_s) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  C<T>* bufA = (C<T>*)sm_raw;
+  C<T>* bufB = bufA + 2 * p.Py;
+  const int k1 = blockIdx.x, f = blockIdx.y, d = blockIdx.z;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int Py = p.Py;
+  const C<T>* E1 = x + (size_t)d * p.nap;
+  const C<T>* E2 = E1 + p.n1;
+  const bool ycos = (f != 0);
+  for (int t = tid; t < Py; t += nthr) bufA[t] = czero<T>();
+  __syncthreads();
+  for (int k2 = tid; k2 <= p.N; k2 += nthr) {
+    C<T> c = czero<T>();
+    if (f == 0) {
+      if (k2 >= 1) c = E1[k1 * p.N + (k2 - 1)];
+    } else if (f == 1) {
+      if (k1 >= 1) c = E2[(k1 - 1) * (p.N + 1) + k2];
+    } else {
+      if (k2 >= 1) c = cscale<T>(E1[k1 * p.N + (k2 - 1)], (T)(k2 * M_PI / p.b));
+      if (k1 >= 1) c = csub<T>(c, cscale<T>(E2[(k1 - 1) * (p.N + 1) + k2], (T)(k1 * M_PI / p.a)));
+    }
+    if (ycos) {
+      if (k2 == 0) bufA[0] = cscale<T>(c, (T)2);
+      else { bufA[k2] = c; bufA[Py - k2] = c; }
+    } else if (k2 >= 1) {
+      bufA[k2] = c;
+      bufA[Py - k2] = mk<T>(-c.x, -c.y);
+    }
+  }
+  __syncthreads();
+  C<T>* S = fft_lines<T, false>(bufA, bufB, Py, p.lPy, 1, tw, p.twlog);
+  C<T>* O = (S == bufA) ? bufB : bufA;
+  const C<T>* eh = ycos ? eh_c : eh_s;
+  for (int t = tid; t < 2 * Py; t += nthr) O[t] = cmul<T>(S[t & (Py - 1)], eh[t]);
+  __syncthreads();
+  C<T>* v = fft_lines<T, true>(O, S, 2 * Py, p.lPy + 1, 1, tw, p.twlog);
+  C<T>* dst = Vy + ((size_t)(d * 3 + f) * p.nx + k1) * Py;
+  for (int j = tid; j < Py; j += nthr) {
+    C<T> r = czero<T>();
+    if (j != Py / 2) {
+      int j2 = j < Py / 2 ? j : j - Py;
+      r = v[j2 & (2 * Py - 1)];
+    }
+    dst[j] = r;
+  }
+}
+
+// ------------------------------------------------------------------ pass B
+// grid (Py columns j, 3 fields, ndir)
+template <typename T>
+__global__ void __launch_bounds__(256) k_tbcB(const C<T>* __restrict__ Vy, C<T>* __restrict__ W,
+                                              TbcP p, const C<T>* __restrict__ tw,
+                                              const C<T>* __restrict__ eh_c,
+                                              const C<T>* __restrict__ eh_s,
+                                              const C<T>* __restrict__ kh) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  C<T>* bufA = (C<T>*)sm_raw;
+  C<T>* bufB = bufA + 2 * p.Px;
+  const int j = blockIdx.x, f = blockIdx.y, d = blockIdx.z;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int Px = p.Px, Py = p.Py;
+  C<T>* dst = W + (size_t)(d * 3 + f) * (p.nx + 1) * Py + j;
+  if (j == Py / 2) {
+    for (int q = tid; q <= p.nx; q += nthr) dst[(size_t)q * Py] = czero<T>();
+    return;
+  }
+  const bool xcos = (f != 1);
+  const C<T>* src = Vy + (size_t)(d * 3 + f) * p.nx * Py + j;
+  for (int t = tid; t < Px; t += nthr) bufA[t] = czero<T>();
+  __syncthreads();
+  for (int k1 = tid; k1 < p.nx; k1 += nthr) {
+    C<T> c = src[(size_t)k1 * Py];
+    if (xcos) {
+      if (k1 == 0) bufA[0] = cscale<T>(c, (T)2);
+      else { bufA[k1] = c; bufA[Px - k1] = c; }
+    } else if (k1 >= 1) {
+      bufA[k1] = c;
+      bufA[Px - k1] = mk<T>(-c.x, -c.y);
+    }
+  }
+  __syncthreads();
+  C<T>* S = fft_lines<T, false>(bufA, bufB, Px, p.lPx, 1, tw, p.twlog);
+  C<T>* O = (S == bufA) ? bufB : bufA;
+  const C<T>* eh = xcos ? eh_c : eh_s;
+  for (int t = tid; t < 2 * Px; t += nthr) O[t] = cmul<T>(S[t & (Px - 1)], eh[t]);
+  __syncthreads();
+  C<T>* v = fft_lines<T, true>(O, S, 2 * Px, p.lPx + 1, 1, tw, p.twlog);
+  C<T>* L = (v == O) ? S : O;
+  const int j2a = j < Py / 2 ? j : Py - j;
+  const int hq = Py / 2;
+  for (int i = tid; i < Px; i += nthr) {
+    C<T> r = czero<T>();
+    if (i != Px / 2) {
+      int j1 = i < Px / 2 ? i : i - Px;
+      int j1a = j1 < 0 ? -j1 : j1;
+      r = cmul<T>(v[j1 & (2 * Px - 1)], kh[(size_t)j1a * hq + j2a]);
+    }
+    L[i] = r;
+  }
+  __syncthreads();
+  C<T>* U = fft_lines<T, true>(L, v, Px, p.lPx, 1, tw, p.twlog);
+  for (int q = tid; q <= p.nx; q += nthr) dst[(size_t)q * Py] = U[q];
+}
+
+// ------------------------------------------------------------------ pass C
+// grid (nx+1 rows p, 3 fields, ndir)
+template <typename T>
+__global__ void __launch_bounds__(256) k_tbcC(const C<T>* __restrict__ W, C<T>* __restrict__ Z,
+                                              TbcP p, const C<T>* __restrict__ tw) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  const int Py = p.Py;
+  C<T>* bufA = (C<T>*)sm_raw;
+  C<T>* bufB = bufA + Py;
+  const int row = blockIdx.x, f = blockIdx.y, d = blockIdx.z;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const C<T>* src = W + ((size_t)(d * 3 + f) * (p.nx + 1) + row) * Py;
+  for (int t = tid; t < Py; t += nthr) bufA[t] = src[t];
+  __syncthreads();
+  C<T>* U = fft_lines<T, true>(bufA, bufB, Py, p.lPy, 1, tw, p.twlog);
+  C<T>* E = (U == bufA) ? bufB : bufA;
+  const int ny = p.ny, n2 = 2 * p.ny;
+  const bool ycos = (f != 0);
+  // extension of U(q), q = 0..ny, to length 2 ny (even for cos, odd for sin)
+  __syncthreads();
+  for (int t = tid; t < n2; t += nthr) {
+    C<T> r;
+    if (t <= ny) {
+      r = U[t];
+      if (!ycos && (t == 0 || t == ny)) r = czero<T>();
+    } else {
+      r = U[n2 - t];
+      if (!ycos) r = mk<T>(-r.x, -r.y);
+    }
+    E[t] = r;
+  }
+  __syncthreads();
+  C<T>* D = fft_lines<T, false>(E, U, n2, p.lny + 1, 1, tw, p.twlog);
+  C<T>* dst = Z + ((size_t)(d * 3 + f) * (p.nx + 1) + row) * (ny + 1);
+  const T w = (T)(0.5 * p.b / ny);
+  for (int n = tid; n <= ny; n += nthr) {
+    C<T> v = D[n];
+    dst[n] = ycos ? cscale<T>(v, w) : cscale<T>(cmul_i<T>(v), w);
+  }
+}
+
+// ------------------------------------------------------------------ pass D
+// grid (ny+1 columns n, 3 fields, ndir)
+template <typename T>
+__global__ void __launch_bounds__(256) k_tbcD(const C<T>* __restrict__ Z, C<T>* __restrict__ O,
+                                              TbcP p, const C<T>* __restrict__ tw) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  const int nx = p.nx, n2 = 2 * p.nx, ny = p.ny;
+  C<T>* bufA = (C<T>*)sm_raw;
+  C<T>* bufB = bufA + n2;
+  const int col = blockIdx.x, f = blockIdx.y, d = blockIdx.z;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const bool xcos = (f != 1);
+  const C<T>* src = Z + (size_t)(d * 3 + f) * (nx + 1) * (ny + 1) + col;
+  for (int t = tid; t < n2; t += nthr) {
+    C<T> r;
+    if (t <= nx) {
+      r = src[(size_t)t * (ny + 1)];
+      if (!xcos && (t == 0 || t == nx)) r = czero<T>();
+    } else {
+      r = src[(size_t)(n2 - t) * (ny + 1)];
+      if (!xcos) r = mk<T>(-r.x, -r.y);
+    }
+    bufA[t] = r;
+  }
+  __syncthreads();
+  C<T>* D = fft_lines<T, false>(bufA, bufB, n2, p.lnx + 1, 1, tw, p.twlog);
+  C<T>* dst = O + (size_t)(d * 3 + f) * nx * (ny + 1) + col;
+  const T w = (T)(0.5 * p.a / nx);
+  for (int m = tid; m < nx; m += nthr) {
+    C<T> v = D[m];
+    dst[(size_t)m * (ny + 1)] = xcos ? cscale<T>(v, w) : cscale<T>(cmul_i<T>(v), w);
+  }
+}
+
+// ------------------------------------------------------------------ combine
+// y = local part of (EJ1)/(uT1) + TBC rows (with the sign of the exterior
+// admittance, see the design notes):
+//  row 1: (-1+tau1)E1 + (m pi h/a + vs1)E3 + (h/q)(2k^2 U1 - 2(n pi/b) W)
+//  row 2: (-1+tau2)E2 + (n pi h/b + vs2)E3 + (h/c)(2k^2 U2 + 2(m pi/a) W)
+//  row 3: (m pi h/a)E1 + (n pi h/b)E2 + (-1+tau3)E3
+template <typename T>
+__global__ void k_combine(const C<T>* __restrict__ x, const C<T>* __restrict__ O,
+                          const C<T>* __restrict__ top, C<T>* __restrict__ y, TbcP p, int ndir) {
+  const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (gid >= (long long)ndir * p.nap) return;
+  const int d = (int)(gid / p.nap), i = (int)(gid - (long long)d * p.nap);
+  const C<T>* xd = x + (size_t)d * p.nap;
+  const C<T>* E1 = xd;
+  const C<T>* E2 = xd + p.n1;
+  const C<T>* E3 = xd + p.n1 + p.n2;
+  const int N = p.N, nyp = p.ny + 1;
+  const size_t fs = (size_t)p.nx * nyp;
+  const C<T>* Ocs = O + (size_t)(d * 3 + 0) * fs;
+  const C<T>* Osc = O + (size_t)(d * 3 + 1) * fs;
+  const C<T>* Occ = O + (size_t)(d * 3 + 2) * fs;
+  const T pa = (T)(M_PI / p.a), pb = (T)(M_PI / p.b), h = (T)p.h, ab = (T)(p.a * p.b);
+  const T k2 = (T)p.k2x2;
+  C<T> r;
+  if (i < p.n1) {
+    const int m = i / N, n = i - m * N + 1;
+    r = cmul<T>(cadd<T>(mk<T>(-1, 0), top[i]), E1[i]);
+    if (m >= 1) {
+      C<T> cf = cadd<T>(mk<T>(m * pa * h, 0), top[p.nap + i]);
+      r = cadd<T>(r, cmul<T>(cf, E3[(m - 1) * N + (n - 1)]));
+    }
+    const T s = h / (m == 0 ? ab / 2 : ab / 4);
+    C<T> t = csub<T>(cscale<T>(Ocs[(size_t)m * nyp + n], k2),
+                     cscale<T>(Occ[(size_t)m * nyp + n], 2 * n * pb));
+    r = cadd<T>(r, cscale<T>(t, s));
+  } else if (i < p.n1 + p.n2) {
+    const int ii = i - p.n1;
+    const int m = ii / (N + 1) + 1, n = ii - (m - 1) * (N + 1);
+    r = cmul<T>(cadd<T>(mk<T>(-1, 0), top[i]), E2[ii]);
+    if (n >= 1) {
+      C<T> cf = cadd<T>(mk<T>(n * pb * h, 0), top[p.nap + i]);
+      r = cadd<T>(r, cmul<T>(cf, E3[(m - 1) * N + (n - 1)]));
+    }
+    const T s = h / (n == 0 ? ab / 2 : ab / 4);
+    C<T> t = cadd<T>(cscale<T>(Osc[(size_t)m * nyp + n], k2),
+                     cscale<T>(Occ[(size_t)m * nyp + n], 2 * m * pa));
+    r = cadd<T>(r, cscale<T>(t, s));
+  } else {
+    const int ii = i - p.n1 - p.n2;
+    const int m = ii / N + 1, n = ii - (m - 1) * N + 1;
+    r = cscale<T>(E1[m * N + (n - 1)], m * pa * h);
+    r = cadd<T>(r, cscale<T>(E2[(m - 1) * (N + 1) + n], n * pb * h));
+    r = cadd<T>(r, cmul<T>(cadd<T>(mk<T>(-1, 0), top[i]), E3[ii]));
+  }
+  y[gid] = r;
+}
+
+size_t apply_work_bytes(const Geo& g, int ndir, int eb) {
+  size_t vy = (size_t)ndir * 3 * g.nx * g.Py;
+  size_t w = (size_t)ndir * 3 * (g.nx + 1) * g.Py;
+  size_t z = (size_t)ndir * 3 * (g.nx + 1) * (g.ny + 1);
+  size_t o = (size_t)ndir * 3 * g.nx * (g.ny + 1);
+  // Vy and Z share one region, W and O another; eb = bytes of one complex
+  return (std::max(vy, z) + std::max(w, o)) * (size_t)eb;
+}
+
+template <typename T>
+static cavity_status set_smem(cavity_ctx* ctx) {
+  const Geo& g = ctx->g;
+  int mx = (int)(sizeof(C<T>) * 4 * std::max(g.Px, g.Py));
+  CK(cudaFuncSetAttribute(k_tbcA<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+  CK(cudaFuncSetAttribute(k_tbcB<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+  CK(cudaFuncSetAttribute(k_tbcC<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+  CK(cudaFuncSetAttribute(k_tbcD<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+  return CAVITY_OK;
+}
+
+template <typename T> struct Tabs;
+template <> struct Tabs<double> {
+  static const double2* tw(cavity_ctx* c) { return c->tw64; }
+  static const double2* ex(cavity_ctx* c, int k) { return c->ehat_x64[k]; }
+  static const double2* ey(cavity_ctx* c, int k) { return c->ehat_y64[k]; }
+  static const double2* kh(cavity_ctx* c) { return c->khat64; }
+  static const double2* top(cavity_ctx* c) { return c->top64; }
+};
+template <> struct Tabs<float> {
+  static const float2* tw(cavity_ctx* c) { return c->tw32; }
+  static const float2* ex(cavity_ctx* c, int k) { return c->ehat_x32[k]; }
+  static const float2* ey(cavity_ctx* c, int k) { return c->ehat_y32[k]; }
+  static const float2* kh(cavity_ctx* c) { return c->khat32; }
+  static const float2* top(cavity_ctx* c) { return c->top32; }
+};
+
+template <typename T>
+cavity_status launch_apply(cavity_ctx* ctx, int ndir, const C<T>* x, C<T>* y, void* work) {
+  static int smem_set[2] = {0, 0};
+  const int ti = sizeof(T) == 8 ? 0 : 1;
+  const int need = (int)(sizeof(C<T>) * 4 * std::max(ctx->g.Px, ctx->g.Py));
+  if (smem_set[ti] < need) {
+    CKS(set_smem<T>(ctx));
+    smem_set[ti] = need;
+  }
+  const Geo& g = ctx->g;
+  TbcP p = make_params(ctx);
+  size_t vy = (size_t)ndir * 3 * g.nx * g.Py;
+  size_t z = (size_t)ndir * 3 * (g.nx + 1) * (g.ny + 1);
+  C<T>* R1 = (C<T>*)work;                      // Vy, later Z
+  C<T>* R2 = R1 + std::max(vy, z);             // W, later O
+  cudaStream_t st = ctx->stream;
+  const C<T>* tw = Tabs<T>::tw(ctx);
+  size_t smA = sizeof(C<T>) * 4 * g.Py, smB = sizeof(C<T>) * 4 * g.Px;
+  size_t smC = sizeof(C<T>) * 2 * std::max(g.Py, 2 * g.ny), smD = sizeof(C<T>) * 4 * g.nx;
+  {
+    KScope ks_(ctx, (sizeof(T) == 8 ? KC_TBC_A64 : KC_TBC_A32));
+    k_tbcA<T><<<dim3(g.nx, 3, ndir), 256, smA, st>>>(x, R1, p, tw, Tabs<T>::ey(ctx, 0),
+                                                     Tabs<T>::ey(ctx, 1));
+  }
+  {
+    KScope ks_(ctx, (sizeof(T) == 8 ? KC_TBC_B64 : KC_TBC_B32));
+    k_tbcB<T><<<dim3(g.Py, 3, ndir), 256, smB, st>>>(R1, R2, p, tw, Tabs<T>::ex(ctx, 0),
+                                                     Tabs<T>::ex(ctx, 1), Tabs<T>::kh(ctx));
+  }
+  {
+    KScope ks_(ctx, (sizeof(T) == 8 ? KC_TBC_C64 : KC_TBC_C32));
+    k_tbcC<T><<<dim3(g.nx + 1, 3, ndir), 256, smC, st>>>(R2, R1, p, tw);
+  }
+  {
+    KScope ks_(ctx, (sizeof(T) == 8 ? KC_TBC_D64 : KC_TBC_D32));
+    k_tbcD<T><<<dim3(g.ny + 1, 3, ndir), 256, smD, st>>>(R1, R2, p, tw);
+  }
+  long long tot = (long long)ndir * g.nap;
+  {
+    KScope ks_(ctx, (sizeof(T) == 8 ? KC_COMB64 : KC_COMB32));
+    k_combine<T><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(x, R2, Tabs<T>::top(ctx), y, p,
+                                                                ndir);
+  }
+  CK(cudaGetLastError());
+  return CAVITY_OK;
+}
+
+template cavity_status launch_apply<double>(cavity_ctx*, int, const double2*, double2*, void*);
+template cavity_status launch_apply<float>(cavity_ctx*, int, const float2*, float2*, void*);

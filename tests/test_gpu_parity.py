@@ -1,0 +1,259 @@
+"""GPU parity: every row of the hot path, called through the C ABI, against
+the CPU oracle on identical seeded inputs.
+
+Tolerances (relative L2 over the compared array):
+  FP64 path   1e-10   (the FP64 tolerance the solver is specified to)
+  MIXED path  1e-5    (complex64 transforms and FP32 inner Krylov iterations)
+Sizes span several FFT lines and thread blocks with ragged tails (Nz not a
+power of two, M = Nx-1 odd, rectangular apertures, layered fills).
+"""
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import workloads
+from oracle.aperture import ApertureSystem
+from oracle.excitation import rhs as oracle_rhs
+from oracle.field import field as oracle_field
+from oracle.geometry import Cavity as OCavity, Layer
+from oracle.khat import khat as oracle_khat
+from oracle.rcs import backscatter
+from oracle.tbc import TBCOperator
+from oracle.zsystem import Profiles
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gb():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2008_01966_gb300 as gb
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return gb
+
+
+def rel(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    return np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-300)
+
+
+def ocav(w, layers=None):
+    lay = [Layer(n, e) for n, e in (layers or w['layers'])]
+    return OCavity(w['a'], w['b'], w['c'], w['nx'], w['ny'], w['nz'], w['kappa0'], layers=lay)
+
+
+def gcav(gb, w, precision="fp64", **kw):
+    return gb.Cavity(w['a'], w['b'], w['c'], w['nx'], w['ny'], w['nz'], precision=precision, **kw)
+
+
+CASES = {
+    "homog": dict(a=1.0, b=1.0, c=0.5, nx=16, ny=16, nz=21, kappa0=2 * np.pi * 16 / 8,
+                  layers=[(21, 1.0 + 0j)]),
+    "rect": dict(a=1.0, b=0.75, c=0.4, nx=16, ny=8, nz=13, kappa0=9.0,
+                 layers=[(13, 2.0 + 0.3j)]),
+    "layer3": dict(a=1.0, b=1.0, c=0.5, nx=16, ny=16, nz=23, kappa0=7.5,
+                   layers=[(7, 4 + 1j), (9, 2 + 0.5j), (7, 1.0 + 0j)]),
+}
+
+
+def oracle_profiles_flat(cav, prof):
+    nz = cav.nz
+    P = np.stack([np.concatenate([prof.P1[:, :, j].ravel(), prof.P2[:, :, j].ravel(),
+                                  prof.P3[:, :, j].ravel()]) for j in range(1, nz)])
+    Q = np.stack([np.concatenate([prof.Q1[:, :, j].ravel(), prof.Q2[:, :, j].ravel()])
+                  for j in range(1, nz)])
+    top = np.concatenate([prof.tau1.ravel(), prof.tau2.ravel(), prof.tau3.ravel(),
+                          prof.vs1.ravel(), prof.vs2.ravel()])
+    return P, Q, top
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_zsweep_matches_banded_lu(gb, case):
+    """a1: the GPU ratio sweep reproduces the oracle's pivoted banded LU: top
+    relations tau, varsigma and all per-level profiles P, Q."""
+    w = CASES[case]
+    cav = ocav(w)
+    prof = Profiles(cav)
+    P, Q, top = oracle_profiles_flat(cav, prof)
+    g = gcav(gb, w)
+    g.prepare(w['kappa0'], w['layers'])
+    gtop, gprof, gq = (t.cpu().numpy() for t in g.export_elimination())
+    assert rel(gtop, top) < 1e-12
+    assert rel(gprof, P) < 1e-12
+    assert rel(gq, Q) < 1e-12 or np.abs(Q).max() == 0 and np.abs(gq).max() == 0
+
+
+@pytest.mark.parametrize("case", ["homog", "rect"])
+def test_kernel_table_matches_quadrature(gb, case):
+    """a3: F(G) on the quarter frequency box vs the oracle's Gauss-Legendre
+    quadrature with scipy's j0."""
+    w = CASES[case]
+    g = gcav(gb, w)
+    g.prepare(w['kappa0'], w['layers'])
+    kh = g.export_khat().cpu().numpy()
+    Lx, Ly = 4 * w['a'], 4 * w['b']
+    j1 = np.arange(2 * w['nx'])[:, None]
+    j2 = np.arange(2 * w['ny'])[None, :]
+    rho = np.sqrt((j1 / Lx) ** 2 + (j2 / Ly) ** 2)
+    ref = oracle_khat(rho, w['kappa0'], np.sqrt(2) * max(w['a'], w['b']))
+    assert np.abs(kh - ref).max() < 1e-13 * np.abs(ref).max()
+
+
+def test_rhs_matches_trapezoid_tests(gb):
+    """a2: g1, g2 for several seeded directions."""
+    w = CASES["rect"]
+    cav = ocav(w)
+    th, ph, al = workloads.directions(5, 11)
+    al = np.array([0.0, 0.3, 1.2, np.pi / 2, 2.0])
+    g = gcav(gb, w)
+    g.prepare(w['kappa0'], w['layers'])
+    got = g.rhs(th, ph, al).cpu().numpy()
+    ref = np.array([oracle_rhs(cav, t, p, a) for t, p, a in zip(th, ph, al)])
+    assert rel(got, ref) < 1e-13
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_operator_matches_fft_rule(gb, case):
+    """a4 operator: y = A x of (EJ1)/(uT1) (cavity part plus the TBC integrals
+    by the FFT rule of Sec. 5) in FP64 and in FP32."""
+    w = CASES[case]
+    cav = ocav(w)
+    sysm = ApertureSystem(cav)
+    rng = np.random.default_rng(5)
+    x = rng.standard_normal((3, cav.n_ap)) + 1j * rng.standard_normal((3, cav.n_ap))
+    ref = np.array([sysm.apply(v) for v in x])
+    g = gcav(gb, w)
+    g.prepare(w['kappa0'], w['layers'])
+    y64 = g.apply(torch.tensor(x, dtype=torch.complex128, device="cuda"), "fp64").cpu().numpy()
+    assert rel(y64, ref) < 1e-12
+    y32 = g.apply(torch.tensor(x, dtype=torch.complex64, device="cuda"), "mixed").cpu().numpy()
+    assert rel(y32, ref) < 1e-5
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_solve_fp64_matches_dense_oracle(gb, case):
+    """Whole path in FP64: aperture coefficients and interior field within 1e-10
+    of the oracle's direct solve."""
+    w = CASES[case]
+    cav = ocav(w)
+    sysm = ApertureSystem(cav)
+    th, ph, al = workloads.directions(3, 7)
+    B = np.array([oracle_rhs(cav, t, p, a) for t, p, a in zip(th, ph, al)])
+    X = sysm.solve_dense(B)
+    g = gcav(gb, w, gmres_tol=1e-13)
+    ap, fl, it, res = g.solve(w['kappa0'], w['layers'], th, ph, al, field=True)
+    ap = ap.cpu().numpy()
+    fl = fl.cpu().numpy()
+    assert np.all(res < 1e-12) and np.all(it > 0)
+    for d in range(3):
+        assert rel(ap[d], X[d]) < 1e-10
+        F = oracle_field(cav, sysm.prof, X[d]).ravel()
+        assert rel(fl[d], F) < 1e-10
+
+
+@pytest.mark.parametrize("case", ["homog", "layer3"])
+def test_solve_mixed_matches_dense_oracle(gb, case):
+    """Mixed path (FP32 transforms and inner iterations, FP64 refinement):
+    within 1e-5 of the FP64 oracle per result."""
+    w = CASES[case]
+    cav = ocav(w)
+    sysm = ApertureSystem(cav)
+    th, ph, al = workloads.directions(2, 9)
+    B = np.array([oracle_rhs(cav, t, p, a) for t, p, a in zip(th, ph, al)])
+    X = sysm.solve_dense(B)
+    g = gcav(gb, w, precision="mixed", gmres_tol=1e-10)
+    ap, fl, it, res = g.solve(w['kappa0'], w['layers'], th, ph, al, field=True)
+    assert fl.dtype == torch.complex64
+    ap = ap.cpu().numpy()
+    fl = fl.cpu().numpy()
+    for d in range(2):
+        assert rel(ap[d], X[d]) < 1e-8
+        F = oracle_field(cav, sysm.prof, X[d]).ravel()
+        assert rel(fl[d], F) < 1e-5
+
+
+def test_small_workload_end_to_end(gb):
+    """The 32x32x32 normal-incidence workload (kappa0 = 8 pi), FP64, with the
+    exact selection rules of the symmetric problem checked on the GPU result."""
+    w = workloads.workload('small')
+    cav = ocav(w)
+    sysm = ApertureSystem(cav)
+    X = sysm.solve_dense(oracle_rhs(cav, 0.0, 0.0, 0.0))
+    g = gcav(gb, w, gmres_tol=1e-13)
+    ap, fl, it, res = g.solve(w['kappa0'], w['layers'], w['theta'], w['phi'], w['alpha'])
+    ap = ap.cpu().numpy()[0]
+    assert rel(ap, X) < 1e-10
+    F = oracle_field(cav, sysm.prof, X).ravel()
+    assert rel(fl.cpu().numpy()[0], F) < 1e-10
+    e1 = ap[:cav.n1].reshape(cav.M + 1, cav.N)
+    m = np.arange(cav.M + 1)[:, None]
+    n = np.arange(1, cav.N + 1)[None, :]
+    assert np.abs(e1[(m % 2 == 1) | (n % 2 == 0)]).max() < 1e-12 * np.abs(ap).max()
+
+
+def test_rcs_matches_far_field_formula(gb):
+    w = CASES["rect"]
+    cav = ocav(w)
+    sysm = ApertureSystem(cav)
+    th, ph, al = workloads.directions(3, 4)
+    B = np.array([oracle_rhs(cav, t, p, a) for t, p, a in zip(th, ph, al)])
+    X = sysm.solve_dense(B)
+    g = gcav(gb, w)
+    g.prepare(w['kappa0'], w['layers'])
+    for pol in ("theta", "phi"):
+        s = g.rcs(torch.tensor(X, device="cuda"), th, ph, pol)
+        ref = np.array([backscatter(cav, X[d], th[d], ph[d], pol) for d in range(3)])
+        assert rel(s, ref) < 1e-11
+        s_host = g.rcs(torch.tensor(X), th, ph, pol)
+        assert rel(s_host, ref) < 1e-11
+
+
+def test_batch_isolation(gb):
+    """A direction's result does not depend on the other directions of the
+    batch (fixed-order reductions, per-direction Krylov bases)."""
+    w = CASES["homog"]
+    th, ph, al = workloads.directions(4, 21)
+    g = gcav(gb, w, gmres_tol=1e-12)
+    ap4, _, _, _ = g.solve(w['kappa0'], w['layers'], th, ph, al, field=False)
+    ap4 = ap4.cpu().numpy()
+    for d in (0, 3):
+        ap1, _, _, _ = g.solve(w['kappa0'], w['layers'], th[d:d + 1], ph[d:d + 1], al[d:d + 1],
+                               field=False)
+        assert rel(ap1.cpu().numpy()[0], ap4[d]) < 1e-11
+
+
+def test_host_buffers_match_device_buffers(gb):
+    w = CASES["layer3"]
+    th, ph, al = workloads.directions(2, 3)
+    g = gcav(gb, w, precision="mixed", gmres_tol=1e-10)
+    apd, fld, _, _ = g.solve(w['kappa0'], w['layers'], th, ph, al)
+    aph, flh, _, _ = g.solve(w['kappa0'], w['layers'], th, ph, al, host=True)
+    assert not aph.is_cuda and not flh.is_cuda
+    assert rel(aph.numpy(), apd.cpu().numpy()) < 1e-14
+    assert rel(flh.numpy(), fld.cpu().numpy()) < 1e-7
+
+
+def test_minimal_grid_and_errors(gb):
+    """Degenerate sizes: 4x4 aperture, two vertical steps; argument errors and
+    the resonance status come back as codes, not crashes."""
+    w = dict(a=1.0, b=1.0, c=0.3, nx=4, ny=4, nz=2, kappa0=3.0, layers=[(2, 1.0 + 0j)])
+    cav = ocav(w)
+    sysm = ApertureSystem(cav)
+    X = sysm.solve_dense(oracle_rhs(cav, 0.2, 0.4, 0.1))
+    g = gcav(gb, w, gmres_tol=1e-13)
+    ap, fl, it, res = g.solve(w['kappa0'], w['layers'], [0.2], [0.4], [0.1])
+    assert rel(ap.cpu().numpy()[0], X) < 1e-10
+    with pytest.raises(gb.CavityError) as e:
+        gb.Cavity(1.0, 1.0, 0.5, 12, 16, 8)
+    assert e.value.status == 1
+    with pytest.raises(gb.CavityError) as e:
+        g.prepare(3.0, [(1, 1.0), (1, 2.0)])
+    assert e.value.status == 1
+    g2 = gcav(gb, w, pivot_tol=1e9)
+    with pytest.raises(gb.CavityError) as e:
+        g2.prepare(3.0, w['layers'])
+    assert e.value.status == 3
