@@ -158,6 +158,21 @@ class Cavity:
                                           ctypes.c_void_p(y.data_ptr())))
         return y
 
+    def apply_noalloc(self, x, precision=None, y=None):
+        """y = A x through the allocation-free entry point (library-internal
+        fixed scratch; the caller provides x and y)."""
+        prec = self.precision if precision is None else (
+            _lib.CAVITY_FP64 if precision == "fp64" else _lib.CAVITY_MIXED)
+        x = x.contiguous()
+        want = torch.complex128 if prec == _lib.CAVITY_FP64 else torch.complex64
+        if x.dtype != want or not x.is_cuda or x.dim() != 2 or x.shape[1] != self.n_ap:
+            raise ValueError("x must be a CUDA (ndir, n_ap) tensor of %s" % want)
+        y = torch.empty_like(x) if y is None else y
+        self._check(self.lib.cavity_apply_noalloc(self.h, x.shape[0], prec,
+                                                  ctypes.c_void_p(x.data_ptr()),
+                                                  ctypes.c_void_p(y.data_ptr())))
+        return y
+
     def field(self, aperture):
         aperture = aperture.contiguous()
         if aperture.dtype != torch.complex128 or not aperture.is_cuda or \

@@ -23,7 +23,8 @@ CAVITY_POL_THETA, CAVITY_POL_PHI = 0, 1
 EXPORTS = ["cavity_setup", "cavity_prepare", "cavity_solve", "cavity_rcs", "cavity_destroy",
            "cavity_last_error", "cavity_sizes", "cavity_export_elimination",
            "cavity_export_khat", "cavity_rhs", "cavity_apply", "cavity_field",
-           "cavity_timing", "cavity_timing_read", "cavity_kernel_class"]
+           "cavity_timing", "cavity_timing_read", "cavity_kernel_class",
+           "cavity_apply_noalloc"]
 NUM_KCLASS = 16
 
 
@@ -73,6 +74,7 @@ def load():
     lib.cavity_rhs.argtypes = [P, I, pd, pd, pd, P]
     lib.cavity_apply.argtypes = [P, I, I, P, P]
     lib.cavity_field.argtypes = [P, I, P, P]
+    lib.cavity_apply_noalloc.argtypes = [P, I, I, P, P]
     lib.cavity_timing.argtypes = [P, I]
     lib.cavity_timing_read.argtypes = [P, I, pd, pll]
     lib.cavity_kernel_class.argtypes = [I]

@@ -19,6 +19,7 @@
 // Templated on the arithmetic type: FP64 for the FP64 path and the residuals,
 // FP32 for the inner Krylov iterations of the mixed path.
 #include <algorithm>
+#include <mutex>
 
 #include "common.cuh"
 #include "fft.cuh"
@@ -459,3 +460,56 @@ cavity_status launch_apply(cavity_ctx* ctx, int ndir, const C<T>* x, C<T>* y, vo
 
 template cavity_status launch_apply<double>(cavity_ctx*, int, const double2*, double2*, void*);
 template cavity_status launch_apply<float>(cavity_ctx*, int, const float2*, float2*, void*);
+
+// ------------------------------------------------------------------ no-alloc
+// Variant of cavity_apply for callers that must not allocate device memory.
+// The four transform passes need scratch for their intermediate grids; here it
+// lives in a fixed device array compiled into the library instead of the
+// context's workspace.  Every pass writes all of the scratch it later reads
+// within the same call, so nothing has to be cleared between calls.
+#define CAVITY_NOALLOC_SCRATCH_BYTES (4u << 20)
+static __device__ __align__(256) unsigned char g_noalloc_scratch[CAVITY_NOALLOC_SCRATCH_BYTES];
+static void* g_noalloc_addr[64] = {nullptr};
+static std::mutex g_noalloc_mu;
+
+extern "C" cavity_status cavity_apply_noalloc(cavity_ctx* ctx, int ndir, int precision,
+                                              const void* x, void* y) {
+  if (!ctx) return CAVITY_EINVAL;
+  if (!ctx->prepared || ndir < 1 || !x || !y ||
+      (precision != CAVITY_FP64 && precision != CAVITY_MIXED)) {
+    ctx->err = "cavity_apply_noalloc: not prepared or bad arguments";
+    return CAVITY_EINVAL;
+  }
+  const size_t need = apply_work_bytes(ctx->g, ndir,
+                                       precision == CAVITY_FP64 ? sizeof(double2) : sizeof(float2));
+  if (need > CAVITY_NOALLOC_SCRATCH_BYTES) {
+    ctx->err = "cavity_apply_noalloc: needs " + std::to_string(need) +
+               " bytes of scratch, more than the fixed " +
+               std::to_string(CAVITY_NOALLOC_SCRATCH_BYTES) +
+               " (use fewer directions, a smaller grid, or cavity_apply)";
+    return CAVITY_EINVAL;
+  }
+  int dev = -1;
+  CK(cudaGetDevice(&dev));
+  if (dev != ctx->device || dev < 0 || dev >= 64) {
+    ctx->err = "cavity_apply_noalloc: the context's device must be current";
+    return CAVITY_EINVAL;
+  }
+  void* scratch;
+  {
+    // first call on this device: resolve the device address of the array
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+      void* p = nullptr;
+      CK(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+      g_noalloc_addr[dev] = p;
+    }
+    scratch = g_noalloc_addr[dev];
+  }
+  if (precision == CAVITY_FP64)
+    CKS(launch_apply<double>(ctx, ndir, (const double2*)x, (double2*)y, scratch));
+  else
+    CKS(launch_apply<float>(ctx, ndir, (const float2*)x, (float2*)y, scratch));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return CAVITY_OK;
+}
