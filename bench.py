@@ -217,6 +217,7 @@ def run_gb300(args, rank, world, local_rank):
     w = workloads.workload(WORKLOAD)
     # each rank: its own batch of 16 directions (seeded by rank)
     th, ph, al = workloads.directions(16, 2 + rank) if rank else (w['theta'], w['phi'], w['alpha'])
+    th, ph, al = th[:args.ndir], ph[:args.ndir], al[:args.ndir]
     ndir = len(th)
     tol = 1e-10
     cav = gb.Cavity(w['a'], w['b'], w['c'], w['nx'], w['ny'], w['nz'], precision="mixed",
@@ -345,6 +346,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ndir", type=int, default=16,
+                    help="directions per GPU (16 is the benchmark; fewer only for profiling)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

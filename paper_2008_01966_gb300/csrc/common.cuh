@@ -110,9 +110,9 @@ struct cavity_ctx {
   bool prepared = false;
   double kappa0 = 0;
   std::vector<LayerDev> layers;
-  double2* khat64 = nullptr;   // (Px/2) x (Py/2) quarter box, scaled by 1/(Lx Ly)
+  double2* khat64 = nullptr;   // quarter box [j2][j1] (Py/2 x Px/2), scaled by 1/(Lx Ly)
   float2* khat32 = nullptr;
-  double2* khat_raw = nullptr; // unscaled copy for export
+  double2* khat_raw = nullptr; // unscaled copy [j1][j2] for export
   double2* prof = nullptr;     // (nz-1) x nap profiles P, level-major
   double2* profq = nullptr;    // (nz-1) x (n1+n2) profiles Q (layered only)
   double2* top64 = nullptr;    // nap tau, then n1+n2 varsigma
@@ -192,6 +192,23 @@ inline int ilog2(int n) {
   int l = 0;
   while ((1 << l) < n) ++l;
   return l;
+}
+
+// opt-in shared memory limit of the current device (bytes)
+inline int smem_optin() {
+  int dev = 0, v = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  return v > 0 ? v : 48 * 1024;
+}
+
+// allow `func` the device's opt-in dynamic shared memory (minus its static part)
+template <typename F> inline cudaError_t allow_max_smem(F func) {
+  cudaFuncAttributes a;
+  cudaError_t e = cudaFuncGetAttributes(&a, func);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              smem_optin() - (int)a.sharedSizeBytes);
 }
 
 // grow a workspace to at least `bytes`

@@ -29,98 +29,115 @@ struct FP {
   long long S;          // samples per level
 };
 
+#define FIELD_THREADS 256
+template <typename T> __host__ __device__ __forceinline__ int field_lines(int n) {
+  int tl = fft_tpl<T>(n);
+  return tl >= FIELD_THREADS ? 1 : FIELD_THREADS / tl;
+}
+
+// pass 1: grid (ceil(nx / L) row groups, 3 components, ndir * lc slabs)
 template <typename T>
-__global__ void __launch_bounds__(128) k_field_y(const C<T>* __restrict__ ap, const C<T>* __restrict__ prof,
-                                                 const C<T>* __restrict__ profq, C<T>* __restrict__ T1,
-                                                 FP p, const C<T>* __restrict__ tw) {
+__global__ void __launch_bounds__(FIELD_THREADS) k_field_y(const C<T>* __restrict__ ap,
+                                                           const C<T>* __restrict__ prof,
+                                                           const C<T>* __restrict__ profq,
+                                                           C<T>* __restrict__ T1, FP p,
+                                                           const C<T>* __restrict__ tw) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
-  const int ny = p.ny, L = 2 * ny;
-  C<T>* A = (C<T>*)sm_raw;
-  C<T>* B = A + L;
-  const int r = blockIdx.x, comp = blockIdx.y, s = blockIdx.z;
+  C<T>* buf = (C<T>*)sm_raw;
+  const int ny = p.ny, n2 = 2 * ny, ls = padded_len(n2);
+  const int L = field_lines<T>(n2);
+  const int comp = blockIdx.y, s = blockIdx.z;
+  const int r0 = blockIdx.x * L;
   const int d = s / p.lc, jj = s - d * p.lc;
   const int j = p.j0 + jj;
   if (j > p.nz) return;
   const int tid = threadIdx.x, nthr = blockDim.x;
-  const int m = comp == 0 ? r : r + 1;
-  const bool valid_row = (comp == 0) || (m <= p.M);
   const C<T>* E = ap + (size_t)d * p.nap;
   const bool top = (j == p.nz);
   const C<T>* Pj = prof + (size_t)(j - 1) * p.nap;
   const C<T>* Qj = profq ? profq + (size_t)(j - 1) * (p.n1 + p.n2) : nullptr;
   const bool ycos = (comp == 1);
-  for (int t = tid; t < L; t += nthr) A[t] = mk<T>(0, 0);
+  for (int t = tid; t < L * ls; t += nthr) buf[t] = mk<T>(0, 0);
   __syncthreads();
-  if (valid_row) {
-    for (int n = tid; n <= p.N; n += nthr) {
-      int i = -1;
-      if (comp == 0) { if (n >= 1) i = m * p.N + (n - 1); }
-      else if (comp == 1) i = p.n1 + (m - 1) * (p.N + 1) + n;
-      else { if (n >= 1) i = p.n1 + p.n2 + (m - 1) * p.N + (n - 1); }
-      if (i < 0) continue;
-      C<T> c = E[i];
-      if (!top) {
-        c = cmul<T>(Pj[i], c);
-        if (p.layered && comp < 2 && m >= 1 && n >= 1)
-          c = cadd<T>(c, cmul<T>(Qj[i], E[p.n1 + p.n2 + (m - 1) * p.N + (n - 1)]));
-      }
-      if (ycos) {
-        if (n == 0) A[0] = cscale<T>(c, (T)2);
-        else { A[n] = c; A[L - n] = c; }
-      } else {
-        A[n] = c;
-        A[L - n] = mk<T>(-c.x, -c.y);
-      }
+  const int nn = p.N + 1;                     // = ny, a power of two
+  for (int idx = tid; idx < L * nn; idx += nthr) {
+    const int l = idx >> p.lny, n = idx & (nn - 1);
+    const int r = r0 + l;
+    const int m = comp == 0 ? r : r + 1;
+    if (r >= p.nx || m > p.M || m < 0) continue;
+    int i = -1;
+    if (comp == 0) { if (n >= 1) i = m * p.N + (n - 1); }
+    else if (comp == 1) i = p.n1 + (m - 1) * (p.N + 1) + n;
+    else { if (n >= 1) i = p.n1 + p.n2 + (m - 1) * p.N + (n - 1); }
+    if (i < 0) continue;
+    C<T> c = E[i];
+    if (!top) {
+      c = cmul<T>(Pj[i], c);
+      if (p.layered && comp < 2 && m >= 1 && n >= 1)
+        c = cadd<T>(c, cmul<T>(Qj[i], E[p.n1 + p.n2 + (m - 1) * p.N + (n - 1)]));
+    }
+    C<T>* line = buf + (size_t)l * ls;
+    if (ycos) {
+      if (n == 0) line[0] = cscale<T>(c, (T)2);
+      else { line[pidx(n)] = c; line[pidx(n2 - n)] = c; }
+    } else {
+      line[pidx(n)] = c;
+      line[pidx(n2 - n)] = mk<T>(-c.x, -c.y);
     }
   }
   __syncthreads();
-  C<T>* Z = fft_lines<T, true>(A, B, L, p.lny + 1, 1, tw, p.twlog);
-  C<T>* dst = T1 + (((size_t)s * 3 + comp) * p.nx + r) * (ny + 1);
-  for (int q = tid; q <= ny; q += nthr) {
-    C<T> v = Z[q];
-    // cos: Z/2 ; sin: Z/(2i)
-    dst[q] = ycos ? mk<T>(v.x * (T)0.5, v.y * (T)0.5) : mk<T>(v.y * (T)0.5, -v.x * (T)0.5);
+  fft_inplace<T, true>(buf, ls, n2, p.lny + 1, L, tw, p.twlog);
+  for (int l = 0; l < L; ++l) {
+    const int r = r0 + l;
+    if (r >= p.nx) break;
+    for (int q = tid; q <= ny; q += nthr) {
+      const C<T> v = buf[(size_t)l * ls + pidx(q)];
+      // cos: Z/2 ; sin: Z/(2i)
+      T1[(((size_t)s * 3 + comp) * p.nx + r) * (ny + 1) + q] =
+          ycos ? mk<T>(v.x * (T)0.5, v.y * (T)0.5) : mk<T>(v.y * (T)0.5, -v.x * (T)0.5);
+    }
   }
 }
 
+// pass 2: grid (ceil((ny+1) / L) column groups, 3 components, ndir * lc slabs)
 template <typename T>
-__global__ void __launch_bounds__(256) k_field_x(const C<T>* __restrict__ T1, C<T>* __restrict__ out, FP p,
-                                                 const C<T>* __restrict__ tw, int CB) {
+__global__ void __launch_bounds__(FIELD_THREADS) k_field_x(const C<T>* __restrict__ T1,
+                                                           C<T>* __restrict__ out, FP p,
+                                                           const C<T>* __restrict__ tw) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
-  const int nx = p.nx, ny = p.ny, L = 2 * nx;
-  C<T>* A = (C<T>*)sm_raw;
-  C<T>* B = A + (size_t)CB * L;
-  const int qt = blockIdx.x, comp = blockIdx.y, s = blockIdx.z;
+  C<T>* buf = (C<T>*)sm_raw;
+  const int nx = p.nx, ny = p.ny, n2 = 2 * nx, ls = padded_len(n2);
+  const int L = field_lines<T>(n2);
+  const int comp = blockIdx.y, s = blockIdx.z;
+  const int q0 = blockIdx.x * L;
   const int d = s / p.lc, jj = s - d * p.lc;
   const int j = p.j0 + jj;
   if (j > p.nz) return;
   const int tid = threadIdx.x, nthr = blockDim.x;
-  const int q0 = qt * CB;
   const bool xcos = (comp == 0);
   const C<T>* src = T1 + ((size_t)s * 3 + comp) * nx * (ny + 1);
-  // A[l * L + t]: line l = column q0 + l
-  for (int t = tid; t < CB * L; t += nthr) A[t] = mk<T>(0, 0);
+  for (int t = tid; t < L * ls; t += nthr) buf[t] = mk<T>(0, 0);
   __syncthreads();
   const int nrows = xcos ? nx : nx - 1;    // E1: m = 0..M; E2/E3: m = 1..M
-  for (int t = tid; t < CB * nrows; t += nthr) {
-    const int r = t / CB, l = t - r * CB;
+  const int lL = __ffs(L) - 1;
+  for (int idx = tid; idx < L * nrows; idx += nthr) {
+    const int r = idx >> lL, l = idx & (L - 1);
     const int q = q0 + l;
     if (q > ny) continue;
-    C<T> c = src[(size_t)r * (ny + 1) + q];
-    C<T>* line = A + (size_t)l * L;
+    const C<T> c = src[(size_t)r * (ny + 1) + q];
+    C<T>* line = buf + (size_t)l * ls;
     if (xcos) {
       const int m = r;
       if (m == 0) line[0] = cscale<T>(c, (T)2);
-      else { line[m] = c; line[L - m] = c; }
+      else { line[pidx(m)] = c; line[pidx(n2 - m)] = c; }
     } else {
       const int m = r + 1;
-      line[m] = c;
-      line[L - m] = mk<T>(-c.x, -c.y);
+      line[pidx(m)] = c;
+      line[pidx(n2 - m)] = mk<T>(-c.x, -c.y);
     }
   }
   __syncthreads();
-  C<T>* Z = fft_lines<T, true>(A, B, L, p.lnx + 1, CB, tw, p.twlog);
-  // output block of this component
+  fft_inplace<T, true>(buf, ls, n2, p.lnx + 1, L, tw, p.twlog);
   long long off;
   int ncol, qlo, qhi, plo, phi;
   if (comp == 0) { off = 0; ncol = ny - 1; qlo = 1; qhi = ny - 1; plo = 0; phi = nx; }
@@ -128,14 +145,13 @@ __global__ void __launch_bounds__(256) k_field_x(const C<T>* __restrict__ T1, C<
   else { off = (long long)(nx + 1) * (ny - 1) + (long long)(nx - 1) * (ny + 1); ncol = ny - 1; qlo = 1; qhi = ny - 1; plo = 1; phi = nx - 1; }
   C<T>* dst = out + ((size_t)d * p.nz + (j - 1)) * p.S + off;
   const int np = phi - plo + 1;
-  for (int t = tid; t < CB * np; t += nthr) {
-    const int pr = t / CB, l = t - pr * CB;
+  for (int idx = tid; idx < L * np; idx += nthr) {
+    const int pr = idx >> lL, l = idx & (L - 1);
     const int q = q0 + l;
     if (q < qlo || q > qhi) continue;
-    const int pp = plo + pr;
-    C<T> v = Z[(size_t)l * L + pp];
-    C<T> o = xcos ? mk<T>(v.x * (T)0.5, v.y * (T)0.5) : mk<T>(v.y * (T)0.5, -v.x * (T)0.5);
-    dst[(size_t)pr * ncol + (q - qlo)] = o;
+    const C<T> v = buf[(size_t)l * ls + pidx(plo + pr)];
+    dst[(size_t)pr * ncol + (q - qlo)] =
+        xcos ? mk<T>(v.x * (T)0.5, v.y * (T)0.5) : mk<T>(v.y * (T)0.5, -v.x * (T)0.5);
   }
 }
 
@@ -174,32 +190,31 @@ cavity_status launch_field(cavity_ctx* ctx, int ndir, const double2* ap, C<T>* o
     profq = layered ? (const C<T>*)ctx->profq32 : nullptr;
   }
   const C<T>* tw = sizeof(T) == 8 ? (const C<T>*)ctx->tw64 : (const C<T>*)ctx->tw32;
-  int CB = (int)std::max<size_t>(1, std::min<size_t>(16, ((size_t)128 << 10) / (4 * g.nx * sizeof(C<T>))));
-  size_t smy = sizeof(C<T>) * 4 * g.ny, smx = sizeof(C<T>) * 2 * (size_t)CB * 2 * g.nx;
-  static size_t set_y[2] = {0, 0}, set_x[2] = {0, 0};
+  const int Ly = field_lines<T>(2 * g.ny), Lx = field_lines<T>(2 * g.nx);
+  size_t smy = sizeof(C<T>) * (size_t)Ly * padded_len(2 * g.ny);
+  size_t smx = sizeof(C<T>) * (size_t)Lx * padded_len(2 * g.nx);
+  static bool set[2] = {false, false};
   const int ti = sizeof(T) == 8 ? 0 : 1;
-  if (smy > set_y[ti]) {
-    CK(cudaFuncSetAttribute(k_field_y<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smy));
-    set_y[ti] = smy;
-  }
-  if (smx > set_x[ti]) {
-    CK(cudaFuncSetAttribute(k_field_x<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smx));
-    set_x[ti] = smx;
+  if (!set[ti]) {
+    CK(allow_max_smem(k_field_y<T>));
+    CK(allow_max_smem(k_field_x<T>));
+    set[ti] = true;
   }
   FP p;
   p.nx = g.nx; p.ny = g.ny; p.nz = g.nz; p.M = g.M; p.N = g.N; p.n1 = g.n1; p.n2 = g.n2;
   p.nap = g.nap; p.lnx = g.lnx; p.lny = g.lny; p.twlog = ilog2(ctx->TW);
   p.lc = lc; p.ndir = ndir; p.layered = layered; p.S = g.field_per_level;
-  const int qtiles = (g.ny + 1 + CB - 1) / CB;
   for (int j0 = 1; j0 <= g.nz; j0 += lc) {
     p.j0 = j0;
     {
       KScope ks_(ctx, KC_FIELD_Y);
-      k_field_y<T><<<dim3(g.nx, 3, ndir * lc), 128, smy, ctx->stream>>>(apT, prof, profq, T1, p, tw);
+      k_field_y<T><<<dim3((g.nx + Ly - 1) / Ly, 3, ndir * lc), FIELD_THREADS, smy, ctx->stream>>>(
+          apT, prof, profq, T1, p, tw);
     }
     {
       KScope ks_(ctx, KC_FIELD_X);
-      k_field_x<T><<<dim3(qtiles, 3, ndir * lc), 256, smx, ctx->stream>>>(T1, out, p, tw, CB);
+      k_field_x<T><<<dim3((g.ny + 1 + Lx - 1) / Lx, 3, ndir * lc), FIELD_THREADS, smx, ctx->stream>>>(
+          T1, out, p, tw);
     }
   }
   CK(cudaGetLastError());

@@ -49,6 +49,71 @@ __global__ void __launch_bounds__(256) k_dots(const C<T>* __restrict__ V, long l
   }
 }
 
+// Multi-dot V^H w in two fixed-order stages: each block keeps one chunk of w
+// in shared memory and forms the partial dots of that chunk with all cnt basis
+// vectors; a second kernel adds the chunk partials in chunk order.
+#define MDOT_CHUNK 2048
+template <typename T>
+__global__ void __launch_bounds__(256) k_mdot_partial(const C<T>* __restrict__ V, long long vs,
+                                                      const C<T>* __restrict__ w, long long ws,
+                                                      double2* __restrict__ part, int cnt, int nap,
+                                                      int nchunk) {
+  __shared__ C<T> sw[MDOT_CHUNK];
+  __shared__ double rr[8], ri[8];
+  const int c = blockIdx.x, d = blockIdx.y, tid = threadIdx.x;
+  const int e0 = c * MDOT_CHUNK;
+  const int ne = min(nap - e0, MDOT_CHUNK);
+  const C<T>* wd = w + (size_t)d * ws + e0;
+  for (int e = tid; e < ne; e += 256) sw[e] = wd[e];
+  __syncthreads();
+  const int warp = tid >> 5, lane = tid & 31;
+  const int nsub = cnt >= 8 ? 1 : 8 / cnt;  // warps per basis vector
+  const int ng = 8 / nsub;                  // basis vectors per round
+  for (int i0 = 0; i0 < cnt; i0 += ng) {
+    const int i = i0 + warp / nsub, sub = warp - (warp / nsub) * nsub;
+    double sr = 0, si = 0;
+    if (i < cnt) {
+      // per-lane partial sums in the vector precision (at most 64 terms in
+      // FP32), then FP64 across lanes, warps and chunks
+      const C<T>* v = V + (size_t)d * vs + (size_t)i * nap + e0;
+      T ar = 0, ai = 0;
+      for (int e = sub * 32 + lane; e < ne; e += nsub * 32) {
+        const C<T> a = v[e], b = sw[e];
+        ar += a.x * b.x + a.y * b.y;
+        ai += a.x * b.y - a.y * b.x;
+      }
+      sr = (double)ar;
+      si = (double)ai;
+      for (int off = 16; off > 0; off >>= 1) {
+        sr += __shfl_xor_sync(0xffffffffu, sr, off);
+        si += __shfl_xor_sync(0xffffffffu, si, off);
+      }
+    }
+    if (lane == 0) { rr[warp] = sr; ri[warp] = si; }
+    __syncthreads();
+    if (tid < ng && i0 + tid < cnt) {
+      double a = 0, b = 0;
+      for (int q = 0; q < nsub; ++q) { a += rr[tid * nsub + q]; b += ri[tid * nsub + q]; }
+      part[((size_t)d * nchunk + c) * cnt + i0 + tid] = make_double2(a, b);
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void k_mdot_final(const double2* __restrict__ part, double2* __restrict__ h, int hstride,
+                             int cnt, int nchunk) {
+  const int d = blockIdx.x;
+  for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+    double a = 0, b = 0;
+    for (int c = 0; c < nchunk; ++c) {
+      const double2 v = part[((size_t)d * nchunk + c) * cnt + i];
+      a += v.x;
+      b += v.y;
+    }
+    h[(size_t)d * hstride + i] = make_double2(a, b);
+  }
+}
+
 // w[d][e] += sgn * sum_{i<cnt} V[d*vs + i*nap + e] c[d*cstride + i]
 template <typename T>
 __global__ void k_basis_axpy(const C<T>* __restrict__ V, long long vs, const double2* __restrict__ c,
@@ -57,15 +122,18 @@ __global__ void k_basis_axpy(const C<T>* __restrict__ V, long long vs, const dou
   if (gid >= (long long)ndir * nap) return;
   const int d = (int)(gid / nap), e = (int)(gid - (long long)d * nap);
   const C<T>* v = V + (size_t)d * vs + e;
-  double ar = 0, ai = 0;
+  // accumulate in the vector precision (FP64 arithmetic is scarce on this GPU)
+  T ar = 0, ai = 0;
   for (int i = 0; i < cnt; ++i) {
-    C<T> a = v[(size_t)i * nap];
-    double2 b = c[(size_t)d * cstride + i];
-    ar += (double)a.x * b.x - (double)a.y * b.y;
-    ai += (double)a.x * b.y + (double)a.y * b.x;
+    const C<T> a = v[(size_t)i * nap];
+    const double2 bd = c[(size_t)d * cstride + i];
+    const T bx = (T)bd.x, by = (T)bd.y;
+    ar += a.x * bx - a.y * by;
+    ai += a.x * by + a.y * bx;
   }
-  C<T> o = w[gid];
-  w[gid] = mk<T>((T)(o.x + sgn * ar), (T)(o.y + sgn * ai));
+  const C<T> o = w[gid];
+  const T sg = (T)sgn;
+  w[gid] = mk<T>(o.x + sg * ar, o.y + sg * ai);
 }
 
 // out[d*os + e] = s[d] * in[d*is + e]
@@ -131,8 +199,11 @@ template <typename T> struct GW {
   double2* h2;  // ndir x (m+1)
   double2* y;   // ndir x (m+1)
   double* s;    // ndir
+  double2* part;  // ndir x nchunk x (m+1) multi-dot partials
   void* apw;    // operator workspace
 };
+
+static inline int mdot_chunks(int nap) { return (nap + MDOT_CHUNK - 1) / MDOT_CHUNK; }
 
 template <typename T>
 static size_t gw_bytes(const Geo& g, int ndir, int m) {
@@ -142,6 +213,7 @@ static size_t gw_bytes(const Geo& g, int ndir, int m) {
   b += 2 * al(sizeof(C<T>) * (size_t)ndir * g.nap);
   b += 3 * al(sizeof(double2) * (size_t)ndir * (m + 1));
   b += al(sizeof(double) * ndir);
+  b += al(sizeof(double2) * (size_t)ndir * mdot_chunks(g.nap) * (m + 1));
   b += al(apply_work_bytes(g, ndir, sizeof(C<T>)));
   return b;
 }
@@ -158,19 +230,33 @@ static GW<T> gw_carve(void* base, const Geo& g, int ndir, int m) {
   W.h2 = (double2*)p; p += al(sizeof(double2) * (size_t)ndir * (m + 1));
   W.y = (double2*)p; p += al(sizeof(double2) * (size_t)ndir * (m + 1));
   W.s = (double*)p; p += al(sizeof(double) * ndir);
+  W.part = (double2*)p; p += al(sizeof(double2) * (size_t)ndir * mdot_chunks(g.nap) * (m + 1));
   W.apw = p;
   return W;
+}
+
+// out[d*ostride + i] = <V_i, w> for i < cnt, all directions
+template <typename T>
+static void mdot(cavity_ctx* ctx, const C<T>* V, long long vs, const C<T>* w, long long ws, int cnt,
+                 double2* out, int ostride, double2* part, int ndir) {
+  const int nap = ctx->g.nap, nchunk = mdot_chunks(nap);
+  {
+    KScope ks_(ctx, KC_KRYLOV);
+    k_mdot_partial<T><<<dim3(nchunk, ndir), 256, 0, ctx->stream>>>(V, vs, w, ws, part, cnt, nap,
+                                                                   nchunk);
+  }
+  {
+    KScope ks_(ctx, KC_KRYLOV);
+    k_mdot_final<<<ndir, 64, 0, ctx->stream>>>(part, out, ostride, cnt, nchunk);
+  }
 }
 
 // norms of ndir contiguous vectors (host result)
 template <typename T>
 static cavity_status norms(cavity_ctx* ctx, const C<T>* v, int ndir, double2* scratch, int sstride,
-                           std::vector<double>& out) {
+                           std::vector<double>& out, double2* part) {
   const int nap = ctx->g.nap;
-  {
-    KScope ks_(ctx, KC_KRYLOV);
-    k_dots<T><<<dim3(1, ndir), 256, 0, ctx->stream>>>(v, nap, v, nap, scratch, sstride, nap);
-  }
+  mdot<T>(ctx, v, nap, v, nap, 1, scratch, sstride, part, ndir);
   std::vector<double2> hh((size_t)ndir);
   CK(cudaMemcpy2DAsync(hh.data(), sizeof(double2), scratch, sizeof(double2) * sstride,
                        sizeof(double2), ndir, cudaMemcpyDeviceToHost, ctx->stream));
@@ -193,7 +279,7 @@ static cavity_status gmres_core(cavity_ctx* ctx, int ndir, const C<T>* b, C<T>* 
   const long long vs = (long long)(m + 1) * nap;
   cudaStream_t st = ctx->stream;
   std::vector<double> bnorm, rn;
-  CKS(norms<T>(ctx, b, ndir, W.h, m + 1, bnorm));
+  CKS(norms<T>(ctx, b, ndir, W.h, m + 1, bnorm, W.part));
   rn = bnorm;
   est.assign(ndir, 0.0);
   CK(cudaMemsetAsync(x, 0, sizeof(C<T>) * nv, st));
@@ -239,26 +325,17 @@ static cavity_status gmres_core(cavity_ctx* ctx, int ndir, const C<T>* b, C<T>* 
       CKS(launch_precond_apply<T>(ctx, ndir, W.w, W.z));
       CKS(launch_apply<T>(ctx, ndir, W.z, W.w, W.apw));
       // CGS2
-      {
-        KScope ks_(ctx, KC_KRYLOV);
-        k_dots<T><<<dim3(k + 1, ndir), 256, 0, st>>>(W.V, vs, W.w, nap, W.h, m + 1, nap);
-      }
+      mdot<T>(ctx, W.V, vs, W.w, nap, k + 1, W.h, m + 1, W.part, ndir);
       {
         KScope ks_(ctx, KC_KRYLOV);
         k_basis_axpy<T><<<nblk(nv, 256), 256, 0, st>>>(W.V, vs, W.h, m + 1, k + 1, W.w, nap, ndir, -1.0);
       }
-      {
-        KScope ks_(ctx, KC_KRYLOV);
-        k_dots<T><<<dim3(k + 1, ndir), 256, 0, st>>>(W.V, vs, W.w, nap, W.h2, m + 1, nap);
-      }
+      mdot<T>(ctx, W.V, vs, W.w, nap, k + 1, W.h2, m + 1, W.part, ndir);
       {
         KScope ks_(ctx, KC_KRYLOV);
         k_basis_axpy<T><<<nblk(nv, 256), 256, 0, st>>>(W.V, vs, W.h2, m + 1, k + 1, W.w, nap, ndir, -1.0);
       }
-      {
-        KScope ks_(ctx, KC_KRYLOV);
-        k_dots<T><<<dim3(1, ndir), 256, 0, st>>>(W.w, nap, W.w, nap, W.y, m + 1, nap);
-      }
+      mdot<T>(ctx, W.w, nap, W.w, nap, 1, W.y, m + 1, W.part, ndir);
       CK(cudaMemcpyAsync(h1.data(), W.h, sizeof(double2) * ndir * (m + 1), cudaMemcpyDeviceToHost, st));
       CK(cudaMemcpyAsync(h2v.data(), W.h2, sizeof(double2) * ndir * (m + 1), cudaMemcpyDeviceToHost, st));
       CK(cudaMemcpyAsync(nw.data(), W.y, sizeof(double2) * ndir * (m + 1), cudaMemcpyDeviceToHost, st));
@@ -362,7 +439,7 @@ static cavity_status gmres_core(cavity_ctx* ctx, int ndir, const C<T>* b, C<T>* 
       KScope ks_(ctx, KC_KRYLOV);
       k_bminus<T><<<nblk(nv, 256), 256, 0, st>>>(b, W.w, nv);
     }
-    CKS(norms<T>(ctx, W.w, ndir, W.h, m + 1, rn));
+    CKS(norms<T>(ctx, W.w, ndir, W.h, m + 1, rn, W.part));
     for (int d = 0; d < ndir; ++d) {
       if (bnorm[d] > 0) est[d] = rn[d] / bnorm[d];
       if (est[d] <= tol[d]) done[d] = 1;
@@ -400,8 +477,8 @@ cavity_status run_gmres64(cavity_ctx* ctx, int ndir, const double2* b, double2* 
     k_bminus<double><<<nblk(nv, 256), 256, 0, ctx->stream>>>(b, W.w, nv);
   }
   std::vector<double> rn, bn;
-  CKS(norms<double>(ctx, W.w, ndir, W.h, m + 1, rn));
-  CKS(norms<double>(ctx, b, ndir, W.h, m + 1, bn));
+  CKS(norms<double>(ctx, W.w, ndir, W.h, m + 1, rn, W.part));
+  CKS(norms<double>(ctx, b, ndir, W.h, m + 1, bn, W.part));
   bool ok = true;
   for (int d = 0; d < ndir; ++d) {
     double r = bn[d] > 0 ? rn[d] / bn[d] : 0.0;
@@ -444,7 +521,7 @@ cavity_status run_mixed_solve(cavity_ctx* ctx, int ndir, const double2* b, doubl
   std::vector<double> bn, rn;
   CK(cudaMemsetAsync(x, 0, sizeof(double2) * nv, st));
   CK(cudaMemcpyAsync(r64, b, sizeof(double2) * nv, cudaMemcpyDeviceToDevice, st));
-  CKS(norms<double>(ctx, b, ndir, sc2, 1, bn));
+  CKS(norms<double>(ctx, b, ndir, sc2, 1, bn, W.part));
   rn = bn;
   std::vector<int> it(ndir, 0);
   std::vector<double> est, s(ndir), tin(ndir);
@@ -483,7 +560,7 @@ cavity_status run_mixed_solve(cavity_ctx* ctx, int ndir, const double2* b, doubl
       k_bminus<double><<<nblk(nv, 256), 256, 0, st>>>(b, tmp64, nv);
     }
     CK(cudaMemcpyAsync(r64, tmp64, sizeof(double2) * nv, cudaMemcpyDeviceToDevice, st));
-    CKS(norms<double>(ctx, r64, ndir, sc2, 1, rn));
+    CKS(norms<double>(ctx, r64, ndir, sc2, 1, rn, W.part));
   }
   bool all = true;
   for (int d = 0; d < ndir; ++d) {

@@ -86,8 +86,10 @@ __global__ void k_khat(double2* __restrict__ raw, double2* __restrict__ s64, flo
   }
   if (lane == 0) {
     double2 v = make_double2(0.5 * sr, 0.5 * si);
-    size_t o = (size_t)j1 * hy + j2;
-    raw[o] = v;
+    raw[(size_t)j1 * hy + j2] = v;
+    // scaled copies are stored transposed, [j2][j1]: the operator reads them
+    // along j1 for fixed j2
+    const size_t o = (size_t)j2 * hx + j1;
     s64[o] = make_double2(v.x * scale, v.y * scale);
     s32[o] = make_float2((float)(v.x * scale), (float)(v.y * scale));
   }

@@ -62,7 +62,7 @@ __global__ void k_pc_ax(double2* __restrict__ out, int nint, int Pn, double side
   }
 }
 
-// T[xk][m][j2a] = sum_j Ax[xk][m][j] khat(|j1|, j2a)
+// T[xk][m][j2a] = sum_j Ax[xk][m][j] khat(|j1|, j2a)   (khat stored [j2a][j1a])
 __global__ void k_pc_t(const double2* __restrict__ ax, const double2* __restrict__ kh,
                        double2* __restrict__ out, int nx, int Px, int hy) {
   const int xk = blockIdx.z, m = blockIdx.y;
@@ -73,7 +73,7 @@ __global__ void k_pc_t(const double2* __restrict__ ax, const double2* __restrict
   for (int j = 0; j < Px; ++j) {
     if (j == Px / 2) continue;
     int j1a = j < Px / 2 ? j : Px - j;
-    s = cadd<double>(s, cmul<double>(a[j], kh[(size_t)j1a * hy + j2a]));
+    s = cadd<double>(s, cmul<double>(a[j], kh[(size_t)j2a * (Px / 2) + j1a]));
   }
   out[((size_t)xk * nx + m) * hy + j2a] = s;
 }
@@ -225,7 +225,8 @@ __global__ void k_pc_apply(const C<T>* __restrict__ x, C<T>* __restrict__ y,
   if (gid >= per * ndir) return;
   const int d = (int)(gid / per);
   const int mn = (int)(gid - (long long)d * per);
-  const int m = mn / ny, n = mn - m * ny;
+  const int lny = __ffs(ny) - 1;                 // ny is a power of two
+  const int m = mn >> lny, n = mn & (ny - 1);
   const int N = ny - 1;
   const bool has1 = n >= 1, has2 = m >= 1, has3 = m >= 1 && n >= 1;
   const int i1 = m * N + (n - 1), i2 = n1 + (m - 1) * (N + 1) + n;

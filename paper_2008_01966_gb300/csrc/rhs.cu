@@ -229,7 +229,7 @@ cavity_status launch_rcs(cavity_ctx* ctx, int ndir, const double2* ap, const dou
   double* sg = (double*)((char*)ctx->ws2 + ((sizeof(ObsPar) * ndir + 255) / 256) * 256);
   CK(cudaMemcpyAsync(op, hp.data(), sizeof(ObsPar) * ndir, cudaMemcpyHostToDevice, ctx->stream));
   size_t sm = sizeof(double2) * (2 * g.nx + 2 * g.ny);
-  CK(cudaFuncSetAttribute(k_rcs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  CK(allow_max_smem(k_rcs));
   {
     KScope ks_(ctx, KC_RHS);
     k_rcs<<<ndir, 256, sm, ctx->stream>>>(ap, op, sg, g.nx, g.ny, g.n1, g.n2, g.nap, g.a, g.b,

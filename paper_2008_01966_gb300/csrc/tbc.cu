@@ -73,7 +73,6 @@ __global__ void k_ehat(double2* out64, float2* out32, int P, int lP, double side
   extern __shared__ double2 sm_e[];
   const int Q = 2 * P;
   double2* A = sm_e;
-  double2* B = sm_e + Q;
   for (int t = threadIdx.x; t < Q; t += blockDim.x) {
     int d = t < P ? t : t - Q;
     double2 v;
@@ -91,12 +90,12 @@ __global__ void k_ehat(double2* out64, float2* out32, int P, int lP, double side
       // num / i = (num.y, -num.x)
       v = make_double2(num.y * f, -num.x * f);
     }
-    A[t] = v;
+    A[pidx(t)] = v;
   }
   __syncthreads();
-  double2* R = fft_lines<double, false>(A, B, Q, lP + 1, 1, tw, twlog);
+  fft_inplace<double, false>(A, padded_len(Q), Q, lP + 1, 1, tw, twlog);
   for (int t = threadIdx.x; t < Q; t += blockDim.x) {
-    double2 v = R[t];
+    double2 v = A[pidx(t)];
     double sc = 1.0 / (double)Q;
     double2 r;
     if (kind == 0) r = make_double2(0.5 * sc * v.x, 0.5 * sc * v.y);   // * 1/2
@@ -114,17 +113,16 @@ cavity_status launch_ehat(cavity_ctx* ctx) {
     CK(cudaMalloc(&ctx->ehat_x32[kind], sizeof(float2) * 2 * g.Px));
     CK(cudaMalloc(&ctx->ehat_y64[kind], sizeof(double2) * 2 * g.Py));
     CK(cudaMalloc(&ctx->ehat_y32[kind], sizeof(float2) * 2 * g.Py));
-    size_t smx = sizeof(double2) * 4 * g.Px, smy = sizeof(double2) * 4 * g.Py;
-    CK(cudaFuncSetAttribute(k_ehat, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                            (int)std::max(smx, smy)));
+    size_t smx = sizeof(double2) * padded_len(2 * g.Px), smy = sizeof(double2) * padded_len(2 * g.Py);
+    CK(allow_max_smem(k_ehat));
     {
       KScope ks_(ctx, KC_SETUP);
-      k_ehat<<<1, 512, smx, ctx->stream>>>(ctx->ehat_x64[kind], ctx->ehat_x32[kind], g.Px,
+      k_ehat<<<1, std::max(32, fft_tpl<double>(2 * g.Px)), smx, ctx->stream>>>(ctx->ehat_x64[kind], ctx->ehat_x32[kind], g.Px,
                                             g.lPx, g.a, g.pad, kind, ctx->tw64, twlog);
     }
     {
       KScope ks_(ctx, KC_SETUP);
-      k_ehat<<<1, 512, smy, ctx->stream>>>(ctx->ehat_y64[kind], ctx->ehat_y32[kind], g.Py,
+      k_ehat<<<1, std::max(32, fft_tpl<double>(2 * g.Py)), smy, ctx->stream>>>(ctx->ehat_y64[kind], ctx->ehat_y32[kind], g.Py,
                                             g.lPy, g.b, g.pad, kind, ctx->tw64, twlog);
     }
     CK(cudaGetLastError());
@@ -132,25 +130,42 @@ cavity_status launch_ehat(cavity_ctx* ctx) {
   return CAVITY_OK;
 }
 
+// Lines per CTA: enough lines that a pass of the longest transform in the
+// kernel occupies LINES_THREADS threads (nlong = that length).
+#define LINES_THREADS 256
+template <typename T> __host__ __device__ __forceinline__ int lines_per_cta(int nlong) {
+  int tl = fft_tpl<T>(nlong);
+  return tl >= LINES_THREADS ? 1 : LINES_THREADS / tl;
+}
+
 // ------------------------------------------------------------------ pass A
-// grid (nx rows k1, 3 fields, ndir); field 0: cs (E1), 1: sc (E2), 2: cc (w)
+// grid (ceil(nx / L) row groups, 3 fields, ndir); field 0: cs (E1), 1: sc (E2),
+// 2: cc (w).  Per row k1: the mirrored coefficient sequence along x2 is
+// transformed (length Py), multiplied by the transform of the 1-D kernel
+// (length 2 Py, periodic extension) and transformed back: a linear
+// convolution giving the basis transform at j2 in the symmetric box.
 template <typename T>
-__global__ void __launch_bounds__(256) k_tbcA(const C<T>* __restrict__ x, C<T>* __restrict__ Vy,
-                                              TbcP p, const C<T>* __restrict__ tw,
-                                              const C<T>* __restrict__ eh_c,
-                                              const C<T>* __restrict__ eh_s) {
+__global__ void __launch_bounds__(LINES_THREADS, sizeof(T) == 4 ? 3 : 2) k_tbcA(const C<T>* __restrict__ x, C<T>* __restrict__ Vy,
+                                                        TbcP p, const C<T>* __restrict__ tw,
+                                                        const C<T>* __restrict__ eh_c,
+                                                        const C<T>* __restrict__ eh_s) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
-  C<T>* bufA = (C<T>*)sm_raw;
-  C<T>* bufB = bufA + 2 * p.Py;
-  const int k1 = blockIdx.x, f = blockIdx.y, d = blockIdx.z;
+  C<T>* buf = (C<T>*)sm_raw;
+  const int Py = p.Py, Q = 2 * Py, ls = padded_len(Q);
+  const int L = lines_per_cta<T>(Q);
+  const int f = blockIdx.y, d = blockIdx.z;
+  const int row0 = blockIdx.x * L;
   const int tid = threadIdx.x, nthr = blockDim.x;
-  const int Py = p.Py;
   const C<T>* E1 = x + (size_t)d * p.nap;
   const C<T>* E2 = E1 + p.n1;
   const bool ycos = (f != 0);
-  for (int t = tid; t < Py; t += nthr) bufA[t] = czero<T>();
+  for (int t = tid; t < L * ls; t += nthr) buf[t] = czero<T>();
   __syncthreads();
-  for (int k2 = tid; k2 <= p.N; k2 += nthr) {
+  const int nk = p.N + 1;                     // = ny, a power of two
+  for (int idx = tid; idx < L * nk; idx += nthr) {
+    const int l = idx >> p.lny, k2 = idx & (nk - 1);
+    const int k1 = row0 + l;
+    if (k1 >= p.nx) continue;
     C<T> c = czero<T>();
     if (f == 0) {
       if (k2 >= 1) c = E1[k1 * p.N + (k2 - 1)];
@@ -160,161 +175,205 @@ __global__ void __launch_bounds__(256) k_tbcA(const C<T>* __restrict__ x, C<T>* 
       if (k2 >= 1) c = cscale<T>(E1[k1 * p.N + (k2 - 1)], (T)(k2 * M_PI / p.b));
       if (k1 >= 1) c = csub<T>(c, cscale<T>(E2[(k1 - 1) * (p.N + 1) + k2], (T)(k1 * M_PI / p.a)));
     }
+    C<T>* line = buf + (size_t)l * ls;
     if (ycos) {
-      if (k2 == 0) bufA[0] = cscale<T>(c, (T)2);
-      else { bufA[k2] = c; bufA[Py - k2] = c; }
+      if (k2 == 0) line[0] = cscale<T>(c, (T)2);
+      else { line[pidx(k2)] = c; line[pidx(Py - k2)] = c; }
     } else if (k2 >= 1) {
-      bufA[k2] = c;
-      bufA[Py - k2] = mk<T>(-c.x, -c.y);
+      line[pidx(k2)] = c;
+      line[pidx(Py - k2)] = mk<T>(-c.x, -c.y);
     }
   }
   __syncthreads();
-  C<T>* S = fft_lines<T, false>(bufA, bufB, Py, p.lPy, 1, tw, p.twlog);
-  C<T>* O = (S == bufA) ? bufB : bufA;
+  fft_inplace<T, false>(buf, ls, Py, p.lPy, L, tw, p.twlog);
   const C<T>* eh = ycos ? eh_c : eh_s;
-  for (int t = tid; t < 2 * Py; t += nthr) O[t] = cmul<T>(S[t & (Py - 1)], eh[t]);
+  for (int idx = tid; idx < L * Py; idx += nthr) {
+    const int l = idx >> p.lPy, t = idx & (Py - 1);
+    C<T>* line = buf + (size_t)l * ls;
+    const C<T> sv = line[pidx(t)];
+    line[pidx(t)] = cmul<T>(sv, eh[t]);
+    line[pidx(t + Py)] = cmul<T>(sv, eh[t + Py]);
+  }
   __syncthreads();
-  C<T>* v = fft_lines<T, true>(O, S, 2 * Py, p.lPy + 1, 1, tw, p.twlog);
-  C<T>* dst = Vy + ((size_t)(d * 3 + f) * p.nx + k1) * Py;
-  for (int j = tid; j < Py; j += nthr) {
+  fft_inplace<T, true>(buf, ls, Q, p.lPy + 1, L, tw, p.twlog);
+  for (int idx = tid; idx < L * Py; idx += nthr) {
+    const int l = idx >> p.lPy, j = idx & (Py - 1);
+    const int k1 = row0 + l;
+    if (k1 >= p.nx) continue;
     C<T> r = czero<T>();
     if (j != Py / 2) {
-      int j2 = j < Py / 2 ? j : j - Py;
-      r = v[j2 & (2 * Py - 1)];
+      const int j2 = j < Py / 2 ? j : j - Py;
+      r = buf[(size_t)l * ls + pidx(j2 & (Q - 1))];
     }
-    dst[j] = r;
+    Vy[((size_t)(d * 3 + f) * p.nx + k1) * Py + j] = r;
   }
 }
 
 // ------------------------------------------------------------------ pass B
-// grid (Py columns j, 3 fields, ndir)
+// grid (Py / L column groups, 3 fields, ndir).  Per column j2: the basis
+// transform along x1 (as in pass A), times F(G)(|j1|, |j2|)/(Lx Ly), then the
+// inverse torus transform along x1 evaluated at the nodes p = 0..nx.
 template <typename T>
-__global__ void __launch_bounds__(256) k_tbcB(const C<T>* __restrict__ Vy, C<T>* __restrict__ W,
-                                              TbcP p, const C<T>* __restrict__ tw,
-                                              const C<T>* __restrict__ eh_c,
-                                              const C<T>* __restrict__ eh_s,
-                                              const C<T>* __restrict__ kh) {
+__global__ void __launch_bounds__(LINES_THREADS, sizeof(T) == 4 ? 3 : 2) k_tbcB(const C<T>* __restrict__ Vy, C<T>* __restrict__ W,
+                                                        TbcP p, const C<T>* __restrict__ tw,
+                                                        const C<T>* __restrict__ eh_c,
+                                                        const C<T>* __restrict__ eh_s,
+                                                        const C<T>* __restrict__ kh) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
-  C<T>* bufA = (C<T>*)sm_raw;
-  C<T>* bufB = bufA + 2 * p.Px;
-  const int j = blockIdx.x, f = blockIdx.y, d = blockIdx.z;
+  C<T>* buf = (C<T>*)sm_raw;
+  const int Px = p.Px, Py = p.Py, Q = 2 * Px, ls = padded_len(Q);
+  const int L = lines_per_cta<T>(Q);
+  const int f = blockIdx.y, d = blockIdx.z;
+  const int j0 = blockIdx.x * L;
   const int tid = threadIdx.x, nthr = blockDim.x;
-  const int Px = p.Px, Py = p.Py;
-  C<T>* dst = W + (size_t)(d * 3 + f) * (p.nx + 1) * Py + j;
-  if (j == Py / 2) {
-    for (int q = tid; q <= p.nx; q += nthr) dst[(size_t)q * Py] = czero<T>();
-    return;
-  }
   const bool xcos = (f != 1);
-  const C<T>* src = Vy + (size_t)(d * 3 + f) * p.nx * Py + j;
-  for (int t = tid; t < Px; t += nthr) bufA[t] = czero<T>();
+  const C<T>* src = Vy + (size_t)(d * 3 + f) * p.nx * Py;
+  for (int t = tid; t < L * ls; t += nthr) buf[t] = czero<T>();
   __syncthreads();
-  for (int k1 = tid; k1 < p.nx; k1 += nthr) {
-    C<T> c = src[(size_t)k1 * Py];
+  const int lL = __ffs(L) - 1;
+  for (int idx = tid; idx < L * p.nx; idx += nthr) {
+    const int k1 = idx >> lL, l = idx & (L - 1);
+    const int j = j0 + l;
+    if (j >= Py) continue;
+    const C<T> c = src[(size_t)k1 * Py + j];
+    C<T>* line = buf + (size_t)l * ls;
     if (xcos) {
-      if (k1 == 0) bufA[0] = cscale<T>(c, (T)2);
-      else { bufA[k1] = c; bufA[Px - k1] = c; }
+      if (k1 == 0) line[0] = cscale<T>(c, (T)2);
+      else { line[pidx(k1)] = c; line[pidx(Px - k1)] = c; }
     } else if (k1 >= 1) {
-      bufA[k1] = c;
-      bufA[Px - k1] = mk<T>(-c.x, -c.y);
+      line[pidx(k1)] = c;
+      line[pidx(Px - k1)] = mk<T>(-c.x, -c.y);
     }
   }
   __syncthreads();
-  C<T>* S = fft_lines<T, false>(bufA, bufB, Px, p.lPx, 1, tw, p.twlog);
-  C<T>* O = (S == bufA) ? bufB : bufA;
+  fft_inplace<T, false>(buf, ls, Px, p.lPx, L, tw, p.twlog);
   const C<T>* eh = xcos ? eh_c : eh_s;
-  for (int t = tid; t < 2 * Px; t += nthr) O[t] = cmul<T>(S[t & (Px - 1)], eh[t]);
-  __syncthreads();
-  C<T>* v = fft_lines<T, true>(O, S, 2 * Px, p.lPx + 1, 1, tw, p.twlog);
-  C<T>* L = (v == O) ? S : O;
-  const int j2a = j < Py / 2 ? j : Py - j;
-  const int hq = Py / 2;
-  for (int i = tid; i < Px; i += nthr) {
-    C<T> r = czero<T>();
-    if (i != Px / 2) {
-      int j1 = i < Px / 2 ? i : i - Px;
-      int j1a = j1 < 0 ? -j1 : j1;
-      r = cmul<T>(v[j1 & (2 * Px - 1)], kh[(size_t)j1a * hq + j2a]);
-    }
-    L[i] = r;
+  for (int idx = tid; idx < L * Px; idx += nthr) {
+    const int l = idx >> p.lPx, t = idx & (Px - 1);
+    C<T>* line = buf + (size_t)l * ls;
+    const C<T> sv = line[pidx(t)];
+    line[pidx(t)] = cmul<T>(sv, eh[t]);
+    line[pidx(t + Px)] = cmul<T>(sv, eh[t + Px]);
   }
   __syncthreads();
-  C<T>* U = fft_lines<T, true>(L, v, Px, p.lPx, 1, tw, p.twlog);
-  for (int q = tid; q <= p.nx; q += nthr) dst[(size_t)q * Py] = U[q];
+  fft_inplace<T, true>(buf, ls, Q, p.lPx + 1, L, tw, p.twlog);
+  // K-hat line of length Px in place (sources never overlap other threads'
+  // destinations: i < Px/2 reads i, i > Px/2 reads Px + i)
+  const int hp = Px / 2;
+  for (int idx = tid; idx < L * Px; idx += nthr) {
+    const int l = idx >> p.lPx, i = idx & (Px - 1);
+    const int j = j0 + l;
+    C<T>* line = buf + (size_t)l * ls;
+    C<T> r = czero<T>();
+    if (i != Px / 2 && j < Py && j != Py / 2) {
+      const int j1 = i < Px / 2 ? i : i - Px;
+      const int j1a = j1 < 0 ? -j1 : j1;
+      const int j2a = j < Py / 2 ? j : Py - j;
+      r = cmul<T>(line[pidx(j1 & (Q - 1))], kh[(size_t)j2a * hp + j1a]);
+    }
+    line[pidx(i)] = r;
+  }
+  __syncthreads();
+  fft_inplace<T, true>(buf, ls, Px, p.lPx, L, tw, p.twlog);
+  C<T>* dst = W + (size_t)(d * 3 + f) * (p.nx + 1) * Py;
+  for (int idx = tid; idx < L * (p.nx + 1); idx += nthr) {
+    const int q = idx >> lL, l = idx & (L - 1);
+    const int j = j0 + l;
+    if (j >= Py) continue;
+    dst[(size_t)q * Py + j] = buf[(size_t)l * ls + pidx(q)];
+  }
 }
 
 // ------------------------------------------------------------------ pass C
-// grid (nx+1 rows p, 3 fields, ndir)
+// grid (ceil((nx+1)/L) row groups, 3 fields, ndir).  Per node row p: inverse
+// torus transform along x2 at q = 0..ny, then the trapezoid projection onto
+// cos/sin(n pi q/ny) as an extended FFT of length 2 ny.
 template <typename T>
-__global__ void __launch_bounds__(256) k_tbcC(const C<T>* __restrict__ W, C<T>* __restrict__ Z,
-                                              TbcP p, const C<T>* __restrict__ tw) {
+__global__ void __launch_bounds__(LINES_THREADS, sizeof(T) == 4 ? 3 : 2) k_tbcC(const C<T>* __restrict__ W, C<T>* __restrict__ Z,
+                                                        TbcP p, const C<T>* __restrict__ tw) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
-  const int Py = p.Py;
-  C<T>* bufA = (C<T>*)sm_raw;
-  C<T>* bufB = bufA + Py;
-  const int row = blockIdx.x, f = blockIdx.y, d = blockIdx.z;
+  C<T>* buf = (C<T>*)sm_raw;
+  const int Py = p.Py, ls = padded_len(Py);
+  const int L = lines_per_cta<T>(Py);
+  const int f = blockIdx.y, d = blockIdx.z;
+  const int r0 = blockIdx.x * L;
   const int tid = threadIdx.x, nthr = blockDim.x;
-  const C<T>* src = W + ((size_t)(d * 3 + f) * (p.nx + 1) + row) * Py;
-  for (int t = tid; t < Py; t += nthr) bufA[t] = src[t];
-  __syncthreads();
-  C<T>* U = fft_lines<T, true>(bufA, bufB, Py, p.lPy, 1, tw, p.twlog);
-  C<T>* E = (U == bufA) ? bufB : bufA;
-  const int ny = p.ny, n2 = 2 * p.ny;
+  const int ny = p.ny, n2 = 2 * ny;
   const bool ycos = (f != 0);
-  // extension of U(q), q = 0..ny, to length 2 ny (even for cos, odd for sin)
-  __syncthreads();
-  for (int t = tid; t < n2; t += nthr) {
-    C<T> r;
-    if (t <= ny) {
-      r = U[t];
-      if (!ycos && (t == 0 || t == ny)) r = czero<T>();
-    } else {
-      r = U[n2 - t];
-      if (!ycos) r = mk<T>(-r.x, -r.y);
-    }
-    E[t] = r;
+  const C<T>* src = W + (size_t)(d * 3 + f) * (p.nx + 1) * Py;
+  for (int idx = tid; idx < L * Py; idx += nthr) {
+    const int l = idx >> p.lPy, t = idx & (Py - 1);
+    const int row = r0 + l;
+    buf[(size_t)l * ls + pidx(t)] = row <= p.nx ? src[(size_t)row * Py + t] : czero<T>();
   }
   __syncthreads();
-  C<T>* D = fft_lines<T, false>(E, U, n2, p.lny + 1, 1, tw, p.twlog);
-  C<T>* dst = Z + ((size_t)(d * 3 + f) * (p.nx + 1) + row) * (ny + 1);
+  fft_inplace<T, true>(buf, ls, Py, p.lPy, L, tw, p.twlog);
+  // even (cos) / odd (sin) extension of U(q), q = 0..ny, to length 2 ny in place
+  for (int idx = tid; idx < L * n2; idx += nthr) {
+    const int l = idx >> (p.lny + 1), t = idx & (n2 - 1);
+    C<T>* line = buf + (size_t)l * ls;
+    if (t <= ny) {
+      if (!ycos && (t == 0 || t == ny)) line[pidx(t)] = czero<T>();
+    } else {
+      C<T> v = line[pidx(n2 - t)];
+      line[pidx(t)] = ycos ? v : mk<T>(-v.x, -v.y);
+    }
+  }
+  __syncthreads();
+  fft_inplace<T, false>(buf, ls, n2, p.lny + 1, L, tw, p.twlog);
   const T w = (T)(0.5 * p.b / ny);
-  for (int n = tid; n <= ny; n += nthr) {
-    C<T> v = D[n];
-    dst[n] = ycos ? cscale<T>(v, w) : cscale<T>(cmul_i<T>(v), w);
+  for (int l = 0; l < L; ++l) {
+    const int row = r0 + l;
+    if (row > p.nx) break;
+    for (int n = tid; n <= ny; n += nthr) {
+      const C<T> v = buf[(size_t)l * ls + pidx(n)];
+      Z[((size_t)(d * 3 + f) * (p.nx + 1) + row) * (ny + 1) + n] =
+          ycos ? cscale<T>(v, w) : cscale<T>(cmul_i<T>(v), w);
+    }
   }
 }
 
 // ------------------------------------------------------------------ pass D
-// grid (ny+1 columns n, 3 fields, ndir)
+// grid (ceil((ny+1)/L) column groups, 3 fields, ndir).  Per column n: the
+// trapezoid projection along x1 (extended FFT of length 2 nx).
 template <typename T>
-__global__ void __launch_bounds__(256) k_tbcD(const C<T>* __restrict__ Z, C<T>* __restrict__ O,
-                                              TbcP p, const C<T>* __restrict__ tw) {
+__global__ void __launch_bounds__(LINES_THREADS, sizeof(T) == 4 ? 3 : 2) k_tbcD(const C<T>* __restrict__ Z, C<T>* __restrict__ O,
+                                                        TbcP p, const C<T>* __restrict__ tw) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
-  const int nx = p.nx, n2 = 2 * p.nx, ny = p.ny;
-  C<T>* bufA = (C<T>*)sm_raw;
-  C<T>* bufB = bufA + n2;
-  const int col = blockIdx.x, f = blockIdx.y, d = blockIdx.z;
+  C<T>* buf = (C<T>*)sm_raw;
+  const int nx = p.nx, n2 = 2 * p.nx, ny = p.ny, ls = padded_len(n2);
+  const int L = lines_per_cta<T>(n2);
+  const int f = blockIdx.y, d = blockIdx.z;
+  const int c0 = blockIdx.x * L;
   const int tid = threadIdx.x, nthr = blockDim.x;
   const bool xcos = (f != 1);
-  const C<T>* src = Z + (size_t)(d * 3 + f) * (nx + 1) * (ny + 1) + col;
-  for (int t = tid; t < n2; t += nthr) {
-    C<T> r;
-    if (t <= nx) {
-      r = src[(size_t)t * (ny + 1)];
-      if (!xcos && (t == 0 || t == nx)) r = czero<T>();
-    } else {
-      r = src[(size_t)(n2 - t) * (ny + 1)];
-      if (!xcos) r = mk<T>(-r.x, -r.y);
+  const C<T>* src = Z + (size_t)(d * 3 + f) * (nx + 1) * (ny + 1);
+  const int lL = __ffs(L) - 1;
+  for (int idx = tid; idx < L * n2; idx += nthr) {
+    const int t = idx >> lL, l = idx & (L - 1);
+    const int col = c0 + l;
+    C<T> r = czero<T>();
+    if (col <= ny) {
+      if (t <= nx) {
+        r = src[(size_t)t * (ny + 1) + col];
+        if (!xcos && (t == 0 || t == nx)) r = czero<T>();
+      } else {
+        r = src[(size_t)(n2 - t) * (ny + 1) + col];
+        if (!xcos) r = mk<T>(-r.x, -r.y);
+      }
     }
-    bufA[t] = r;
+    buf[(size_t)l * ls + pidx(t)] = r;
   }
   __syncthreads();
-  C<T>* D = fft_lines<T, false>(bufA, bufB, n2, p.lnx + 1, 1, tw, p.twlog);
-  C<T>* dst = O + (size_t)(d * 3 + f) * nx * (ny + 1) + col;
+  fft_inplace<T, false>(buf, ls, n2, p.lnx + 1, L, tw, p.twlog);
+  C<T>* dst = O + (size_t)(d * 3 + f) * nx * (ny + 1);
   const T w = (T)(0.5 * p.a / nx);
-  for (int m = tid; m < nx; m += nthr) {
-    C<T> v = D[m];
-    dst[(size_t)m * (ny + 1)] = xcos ? cscale<T>(v, w) : cscale<T>(cmul_i<T>(v), w);
+  for (int idx = tid; idx < L * nx; idx += nthr) {
+    const int m = idx >> lL, l = idx & (L - 1);
+    const int col = c0 + l;
+    if (col > ny) continue;
+    const C<T> v = buf[(size_t)l * ls + pidx(m)];
+    dst[(size_t)m * (ny + 1) + col] = xcos ? cscale<T>(v, w) : cscale<T>(cmul_i<T>(v), w);
   }
 }
 
@@ -384,14 +443,31 @@ size_t apply_work_bytes(const Geo& g, int ndir, int eb) {
   return (std::max(vy, z) + std::max(w, o)) * (size_t)eb;
 }
 
+template <typename T> struct SmemCfg {
+  size_t a, b, c, d;
+  int La, Lb, Lc, Ld;
+};
+
+template <typename T> static SmemCfg<T> smem_cfg(const Geo& g) {
+  SmemCfg<T> s;
+  s.La = lines_per_cta<T>(2 * g.Py);
+  s.Lb = lines_per_cta<T>(2 * g.Px);
+  s.Lc = lines_per_cta<T>(g.Py);
+  s.Ld = lines_per_cta<T>(2 * g.nx);
+  s.a = sizeof(C<T>) * (size_t)s.La * padded_len(2 * g.Py);
+  s.b = sizeof(C<T>) * (size_t)s.Lb * padded_len(2 * g.Px);
+  s.c = sizeof(C<T>) * (size_t)s.Lc * padded_len(g.Py);
+  s.d = sizeof(C<T>) * (size_t)s.Ld * padded_len(2 * g.nx);
+  return s;
+}
+
+// every pass kernel may use up to the device's opt-in shared memory
 template <typename T>
 static cavity_status set_smem(cavity_ctx* ctx) {
-  const Geo& g = ctx->g;
-  int mx = (int)(sizeof(C<T>) * 4 * std::max(g.Px, g.Py));
-  CK(cudaFuncSetAttribute(k_tbcA<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
-  CK(cudaFuncSetAttribute(k_tbcB<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
-  CK(cudaFuncSetAttribute(k_tbcC<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
-  CK(cudaFuncSetAttribute(k_tbcD<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+  CK(allow_max_smem(k_tbcA<T>));
+  CK(allow_max_smem(k_tbcB<T>));
+  CK(allow_max_smem(k_tbcC<T>));
+  CK(allow_max_smem(k_tbcD<T>));
   return CAVITY_OK;
 }
 
@@ -413,14 +489,19 @@ template <> struct Tabs<float> {
 
 template <typename T>
 cavity_status launch_apply(cavity_ctx* ctx, int ndir, const C<T>* x, C<T>* y, void* work) {
-  static int smem_set[2] = {0, 0};
-  const int ti = sizeof(T) == 8 ? 0 : 1;
-  const int need = (int)(sizeof(C<T>) * 4 * std::max(ctx->g.Px, ctx->g.Py));
-  if (smem_set[ti] < need) {
-    CKS(set_smem<T>(ctx));
-    smem_set[ti] = need;
-  }
   const Geo& g = ctx->g;
+  const SmemCfg<T> sc = smem_cfg<T>(g);
+  static bool smem_set[2] = {false, false};
+  const int ti = sizeof(T) == 8 ? 0 : 1;
+  const size_t need = std::max(std::max(sc.a, sc.b), std::max(sc.c, sc.d));
+  if (need > (size_t)smem_optin()) {
+    ctx->err = "grid too large for the shared-memory transforms";
+    return CAVITY_EINVAL;
+  }
+  if (!smem_set[ti]) {
+    CKS(set_smem<T>(ctx));
+    smem_set[ti] = true;
+  }
   TbcP p = make_params(ctx);
   size_t vy = (size_t)ndir * 3 * g.nx * g.Py;
   size_t z = (size_t)ndir * 3 * (g.nx + 1) * (g.ny + 1);
@@ -428,25 +509,24 @@ cavity_status launch_apply(cavity_ctx* ctx, int ndir, const C<T>* x, C<T>* y, vo
   C<T>* R2 = R1 + std::max(vy, z);             // W, later O
   cudaStream_t st = ctx->stream;
   const C<T>* tw = Tabs<T>::tw(ctx);
-  size_t smA = sizeof(C<T>) * 4 * g.Py, smB = sizeof(C<T>) * 4 * g.Px;
-  size_t smC = sizeof(C<T>) * 2 * std::max(g.Py, 2 * g.ny), smD = sizeof(C<T>) * 4 * g.nx;
+  const int T_ = LINES_THREADS;
   {
     KScope ks_(ctx, (sizeof(T) == 8 ? KC_TBC_A64 : KC_TBC_A32));
-    k_tbcA<T><<<dim3(g.nx, 3, ndir), 256, smA, st>>>(x, R1, p, tw, Tabs<T>::ey(ctx, 0),
-                                                     Tabs<T>::ey(ctx, 1));
+    k_tbcA<T><<<dim3((g.nx + sc.La - 1) / sc.La, 3, ndir), T_, sc.a, st>>>(
+        x, R1, p, tw, Tabs<T>::ey(ctx, 0), Tabs<T>::ey(ctx, 1));
   }
   {
     KScope ks_(ctx, (sizeof(T) == 8 ? KC_TBC_B64 : KC_TBC_B32));
-    k_tbcB<T><<<dim3(g.Py, 3, ndir), 256, smB, st>>>(R1, R2, p, tw, Tabs<T>::ex(ctx, 0),
-                                                     Tabs<T>::ex(ctx, 1), Tabs<T>::kh(ctx));
+    k_tbcB<T><<<dim3((g.Py + sc.Lb - 1) / sc.Lb, 3, ndir), T_, sc.b, st>>>(
+        R1, R2, p, tw, Tabs<T>::ex(ctx, 0), Tabs<T>::ex(ctx, 1), Tabs<T>::kh(ctx));
   }
   {
     KScope ks_(ctx, (sizeof(T) == 8 ? KC_TBC_C64 : KC_TBC_C32));
-    k_tbcC<T><<<dim3(g.nx + 1, 3, ndir), 256, smC, st>>>(R2, R1, p, tw);
+    k_tbcC<T><<<dim3((g.nx + 1 + sc.Lc - 1) / sc.Lc, 3, ndir), T_, sc.c, st>>>(R2, R1, p, tw);
   }
   {
     KScope ks_(ctx, (sizeof(T) == 8 ? KC_TBC_D64 : KC_TBC_D32));
-    k_tbcD<T><<<dim3(g.ny + 1, 3, ndir), 256, smD, st>>>(R1, R2, p, tw);
+    k_tbcD<T><<<dim3((g.ny + 1 + sc.Ld - 1) / sc.Ld, 3, ndir), T_, sc.d, st>>>(R1, R2, p, tw);
   }
   long long tot = (long long)ndir * g.nap;
   {
