@@ -237,11 +237,15 @@ cavity_status launch_zsweep(cavity_ctx* ctx, double kappa0);
 cavity_status launch_precond(cavity_ctx* ctx);
 cavity_status launch_rhs(cavity_ctx* ctx, int ndir, const double* theta,
                          const double* phi, const double* alpha, double2* out);
+// y = A x; direction d of y starts at y + d * ystride (ystride < 0: n_ap)
 template <typename T>
-cavity_status launch_apply(cavity_ctx* ctx, int ndir, const C<T>* x, C<T>* y, void* work);
+cavity_status launch_apply(cavity_ctx* ctx, int ndir, const C<T>* x, C<T>* y, void* work,
+                           long long ystride = -1);
 size_t apply_work_bytes(const Geo& g, int ndir, int elem_bytes);
+// y = M^{-1} x with per-direction strides (< 0: n_ap)
 template <typename T>
-cavity_status launch_precond_apply(cavity_ctx* ctx, int ndir, const C<T>* x, C<T>* y);
+cavity_status launch_precond_apply(cavity_ctx* ctx, int ndir, const C<T>* x, C<T>* y,
+                                   long long xs = -1, long long ys = -1);
 cavity_status run_gmres64(cavity_ctx* ctx, int ndir, const double2* b, double2* x,
                           int* iters, double* resid);
 cavity_status run_mixed_solve(cavity_ctx* ctx, int ndir, const double2* b, double2* x,

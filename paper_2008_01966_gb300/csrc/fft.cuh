@@ -90,35 +90,28 @@ __device__ __forceinline__ void dft8(C<T>* v) {
   }
 }
 
+// 16-point DFT in place, output in transposed order: on return v[4 r + s]
+// holds X[r + 4 s] (dft16_out maps an output index to its slot).
 template <typename T, bool INV>
 __device__ __forceinline__ void dft16(C<T>* v) {
   // n = c + 4 t, k = r + 4 s:  u_c[r] = DFT4_t(v[c + 4t]);  u_c[r] *= w16^{c r};
   // X[r + 4 s] = DFT4_c(u_c[r])
-  C<T> u[16];
 #pragma unroll
-  for (int i = 0; i < 16; ++i) u[i] = v[i];
-#pragma unroll
-  for (int c = 0; c < 4; ++c) dft4s<T, INV>(u + c, 4);   // u[c + 4 r] = u_c[r]
+  for (int c = 0; c < 4; ++c) dft4s<T, INV>(v + c, 4);   // v[c + 4 r] = u_c[r]
   const T c1 = (T)FFT_C16, s1 = (T)FFT_S16, c2 = (T)FFT_C8;
-  // c = 1: w^r, r = 1, 2, 3
-  u[5] = mulw<T, INV>(u[5], c1, s1);
-  u[9] = mulw<T, INV>(u[9], c2, c2);
-  u[13] = mulw<T, INV>(u[13], s1, c1);
-  // c = 2: w^{2r} = w8^r
-  u[6] = mulw<T, INV>(u[6], c2, c2);
-  u[10] = mulmi<T, INV>(u[10]);
-  u[14] = mulw<T, INV>(u[14], -c2, c2);
-  // c = 3: w^{3r}, r = 1, 2, 3 -> exponents 3, 6, 9
-  u[7] = mulw<T, INV>(u[7], s1, c1);
-  u[11] = mulw<T, INV>(u[11], -c2, c2);
-  u[15] = mulw<T, INV>(u[15], -c1, -s1);
+  v[5] = mulw<T, INV>(v[5], c1, s1);
+  v[9] = mulw<T, INV>(v[9], c2, c2);
+  v[13] = mulw<T, INV>(v[13], s1, c1);
+  v[6] = mulw<T, INV>(v[6], c2, c2);
+  v[10] = mulmi<T, INV>(v[10]);
+  v[14] = mulw<T, INV>(v[14], -c2, c2);
+  v[7] = mulw<T, INV>(v[7], s1, c1);
+  v[11] = mulw<T, INV>(v[11], -c2, c2);
+  v[15] = mulw<T, INV>(v[15], -c1, -s1);
 #pragma unroll
-  for (int r = 0; r < 4; ++r) dft4s<T, INV>(u + 4 * r, 1);  // over c -> s
-#pragma unroll
-  for (int r = 0; r < 4; ++r)
-#pragma unroll
-    for (int s = 0; s < 4; ++s) v[r + 4 * s] = u[4 * r + s];
+  for (int r = 0; r < 4; ++r) dft4s<T, INV>(v + 4 * r, 1);  // v[4 r + s] = X[r + 4 s]
 }
+__host__ __device__ constexpr int dft16_slot(int k) { return 4 * (k & 3) + (k >> 2); }
 
 template <typename T, bool INV>
 __device__ __forceinline__ C<T> twid(const C<T>* __restrict__ tw, int idx) {
@@ -169,13 +162,18 @@ __device__ __forceinline__ void fft_pass(C<T>* line, int n, int s, int t, int tp
       const int j = t + q * tpl;
       const int k = j & (Ns - 1);
       C<T>* w = v + q * R;
-      if constexpr (LR == 4) dft16<T, INV>(w);
-      else if constexpr (LR == 3) dft8<T, INV>(w);
-      else if constexpr (LR == 2) dft4<T, INV>(w);
-      else dft2<T, INV>(w);
       const int base = ((j - k) << LR) + k;
+      if constexpr (LR == 4) {
+        dft16<T, INV>(w);
 #pragma unroll
-      for (int r = 0; r < R; ++r) line[pidx(base + r * Ns)] = w[r];
+        for (int r = 0; r < R; ++r) line[pidx(base + r * Ns)] = w[dft16_slot(r)];
+      } else {
+        if constexpr (LR == 3) dft8<T, INV>(w);
+        else if constexpr (LR == 2) dft4<T, INV>(w);
+        else dft2<T, INV>(w);
+#pragma unroll
+        for (int r = 0; r < R; ++r) line[pidx(base + r * Ns)] = w[r];
+      }
     }
   }
   __syncthreads();

@@ -4,8 +4,9 @@
 //
 // The paper solves the aperture system directly and notes that large
 // apertures need an iterative solver (Sec. 6); GMRES is that solver here.
-// Orthogonalisation: classical Gram-Schmidt applied twice (CGS2): two batched
-// dot-product passes and two basis updates per Arnoldi step.  All reductions
+// Orthogonalisation: classical Gram-Schmidt with a second pass where the first
+// removed more than half of ||w||^2 ("twice is enough"): batched dot-product
+// passes and basis updates, the second skipped per direction.  All reductions
 // are fixed-order block trees, so a direction's result does not depend on the
 // other directions in the batch.  The small Hessenberg least-squares problems
 // (complex Givens rotations) are solved on the host from the coefficients
@@ -57,10 +58,16 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_mdot_partial(const C<T>* __restrict__ V, long long vs,
                                                       const C<T>* __restrict__ w, long long ws,
                                                       double2* __restrict__ part, int cnt, int nap,
-                                                      int nchunk) {
+                                                      int nchunk, const int* __restrict__ flag) {
   __shared__ C<T> sw[MDOT_CHUNK];
   __shared__ double rr[8], ri[8];
   const int c = blockIdx.x, d = blockIdx.y, tid = threadIdx.x;
+  if (flag && !flag[d]) {
+    // pass skipped for this direction: zero partials
+    for (int i = tid; i < cnt; i += blockDim.x)
+      part[((size_t)d * nchunk + c) * cnt + i] = make_double2(0.0, 0.0);
+    return;
+  }
   const int e0 = c * MDOT_CHUNK;
   const int ne = min(nap - e0, MDOT_CHUNK);
   const C<T>* wd = w + (size_t)d * ws + e0;
@@ -117,10 +124,13 @@ __global__ void k_mdot_final(const double2* __restrict__ part, double2* __restri
 // w[d][e] += sgn * sum_{i<cnt} V[d*vs + i*nap + e] c[d*cstride + i]
 template <typename T>
 __global__ void k_basis_axpy(const C<T>* __restrict__ V, long long vs, const double2* __restrict__ c,
-                             int cstride, int cnt, C<T>* __restrict__ w, int nap, int ndir, double sgn) {
+                             int cstride, int cnt, C<T>* __restrict__ w, int nap, int ndir, double sgn,
+                             const int* __restrict__ flag = nullptr, long long wstride = -1) {
   long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (gid >= (long long)ndir * nap) return;
   const int d = (int)(gid / nap), e = (int)(gid - (long long)d * nap);
+  if (flag && !flag[d]) return;
+  if (wstride >= 0) gid = (long long)d * wstride + e;
   const C<T>* v = V + (size_t)d * vs + e;
   // accumulate in the vector precision (FP64 arithmetic is scarce on this GPU)
   T ar = 0, ai = 0;
@@ -146,6 +156,23 @@ __global__ void k_copy_scale(const C<T>* __restrict__ in, long long is, C<T>* __
   C<T> a = in[(size_t)d * is + e];
   T f = (T)s[d];
   out[(size_t)d * os + e] = mk<T>(a.x * f, a.y * f);
+}
+
+// Second Gram-Schmidt pass needed?  ("twice is enough": reorthogonalise when
+// the first pass removed more than half of ||w||^2.)  ||w - V h||^2 is
+// estimated as ||w||^2 - sum |h_i|^2 (V orthonormal).
+__global__ void k_reorth_flag(const double2* __restrict__ h, int hstride, int cnt,
+                              const double2* __restrict__ wn2, int wstride, int* __restrict__ flag,
+                              int ndir) {
+  const int d = blockIdx.x * blockDim.x + threadIdx.x;
+  if (d >= ndir) return;
+  double s = 0;
+  for (int i = 0; i < cnt; ++i) {
+    const double2 v = h[(size_t)d * hstride + i];
+    s += v.x * v.x + v.y * v.y;
+  }
+  const double w0 = wn2[(size_t)d * wstride].x;
+  flag[d] = (w0 - s < 0.5 * w0) ? 1 : 0;
 }
 
 // y += x  (contiguous [d][nap])
@@ -200,6 +227,8 @@ template <typename T> struct GW {
   double2* y;   // ndir x (m+1)
   double* s;    // ndir
   double2* part;  // ndir x nchunk x (m+1) multi-dot partials
+  double2* wn;    // ndir: ||w||^2 before orthogonalisation
+  int* flag;      // ndir: second Gram-Schmidt pass needed
   void* apw;    // operator workspace
 };
 
@@ -214,6 +243,7 @@ static size_t gw_bytes(const Geo& g, int ndir, int m) {
   b += 3 * al(sizeof(double2) * (size_t)ndir * (m + 1));
   b += al(sizeof(double) * ndir);
   b += al(sizeof(double2) * (size_t)ndir * mdot_chunks(g.nap) * (m + 1));
+  b += al(sizeof(double2) * ndir) + al(sizeof(int) * ndir);
   b += al(apply_work_bytes(g, ndir, sizeof(C<T>)));
   return b;
 }
@@ -231,6 +261,8 @@ static GW<T> gw_carve(void* base, const Geo& g, int ndir, int m) {
   W.y = (double2*)p; p += al(sizeof(double2) * (size_t)ndir * (m + 1));
   W.s = (double*)p; p += al(sizeof(double) * ndir);
   W.part = (double2*)p; p += al(sizeof(double2) * (size_t)ndir * mdot_chunks(g.nap) * (m + 1));
+  W.wn = (double2*)p; p += al(sizeof(double2) * ndir);
+  W.flag = (int*)p; p += al(sizeof(int) * ndir);
   W.apw = p;
   return W;
 }
@@ -238,12 +270,12 @@ static GW<T> gw_carve(void* base, const Geo& g, int ndir, int m) {
 // out[d*ostride + i] = <V_i, w> for i < cnt, all directions
 template <typename T>
 static void mdot(cavity_ctx* ctx, const C<T>* V, long long vs, const C<T>* w, long long ws, int cnt,
-                 double2* out, int ostride, double2* part, int ndir) {
+                 double2* out, int ostride, double2* part, int ndir, const int* flag = nullptr) {
   const int nap = ctx->g.nap, nchunk = mdot_chunks(nap);
   {
     KScope ks_(ctx, KC_KRYLOV);
     k_mdot_partial<T><<<dim3(nchunk, ndir), 256, 0, ctx->stream>>>(V, vs, w, ws, part, cnt, nap,
-                                                                   nchunk);
+                                                                   nchunk, flag);
   }
   {
     KScope ks_(ctx, KC_KRYLOV);
@@ -315,27 +347,30 @@ static cavity_status gmres_core(cavity_ctx* ctx, int ndir, const C<T>* b, C<T>* 
       gv[d][0] = make_double2(rn[d], 0);
     }
     for (int k = 0; k < m && total < maxit; ++k, ++total) {
-      // w = A M^{-1} V_k
-      std::fill(sc.begin(), sc.end(), 1.0);
-      CK(cudaMemcpyAsync(W.s, sc.data(), sizeof(double) * ndir, cudaMemcpyHostToDevice, st));
+      // V_{k+1} <- A M^{-1} V_k, written straight into the next basis slot
+      C<T>* Vn = W.V + (size_t)(k + 1) * nap;
+      CKS(launch_precond_apply<T>(ctx, ndir, W.V + (size_t)k * nap, W.z, vs, nap));
+      CKS(launch_apply<T>(ctx, ndir, W.z, Vn, W.apw, vs));
+      // classical Gram-Schmidt: <V_i, w> for i <= k and ||w||^2 (i = k+1) in
+      // one pass; a second pass only where the first cancelled
+      mdot<T>(ctx, W.V, vs, Vn, vs, k + 2, W.h, m + 1, W.part, ndir);
       {
         KScope ks_(ctx, KC_KRYLOV);
-        k_copy_scale<T><<<nblk(nv, 256), 256, 0, st>>>(W.V + (size_t)k * nap, vs, W.w, nap, W.s, nap, ndir);
+        k_basis_axpy<T><<<nblk(nv, 256), 256, 0, st>>>(W.V, vs, W.h, m + 1, k + 1, Vn, nap, ndir, -1.0,
+                                                        nullptr, vs);
       }
-      CKS(launch_precond_apply<T>(ctx, ndir, W.w, W.z));
-      CKS(launch_apply<T>(ctx, ndir, W.z, W.w, W.apw));
-      // CGS2
-      mdot<T>(ctx, W.V, vs, W.w, nap, k + 1, W.h, m + 1, W.part, ndir);
       {
         KScope ks_(ctx, KC_KRYLOV);
-        k_basis_axpy<T><<<nblk(nv, 256), 256, 0, st>>>(W.V, vs, W.h, m + 1, k + 1, W.w, nap, ndir, -1.0);
+        k_reorth_flag<<<1, std::max(32, ndir), 0, st>>>(W.h, m + 1, k + 1, W.h + (k + 1), m + 1,
+                                                        W.flag, ndir);
       }
-      mdot<T>(ctx, W.V, vs, W.w, nap, k + 1, W.h2, m + 1, W.part, ndir);
+      mdot<T>(ctx, W.V, vs, Vn, vs, k + 1, W.h2, m + 1, W.part, ndir, W.flag);
       {
         KScope ks_(ctx, KC_KRYLOV);
-        k_basis_axpy<T><<<nblk(nv, 256), 256, 0, st>>>(W.V, vs, W.h2, m + 1, k + 1, W.w, nap, ndir, -1.0);
+        k_basis_axpy<T><<<nblk(nv, 256), 256, 0, st>>>(W.V, vs, W.h2, m + 1, k + 1, Vn, nap, ndir, -1.0,
+                                                        W.flag, vs);
       }
-      mdot<T>(ctx, W.w, nap, W.w, nap, 1, W.y, m + 1, W.part, ndir);
+      mdot<T>(ctx, Vn, vs, Vn, vs, 1, W.y, m + 1, W.part, ndir);
       CK(cudaMemcpyAsync(h1.data(), W.h, sizeof(double2) * ndir * (m + 1), cudaMemcpyDeviceToHost, st));
       CK(cudaMemcpyAsync(h2v.data(), W.h2, sizeof(double2) * ndir * (m + 1), cudaMemcpyDeviceToHost, st));
       CK(cudaMemcpyAsync(nw.data(), W.y, sizeof(double2) * ndir * (m + 1), cudaMemcpyDeviceToHost, st));
@@ -392,9 +427,9 @@ static cavity_status gmres_core(cavity_ctx* ctx, int ndir, const C<T>* b, C<T>* 
       }
       CK(cudaMemcpyAsync(W.s, sc.data(), sizeof(double) * ndir, cudaMemcpyHostToDevice, st));
       {
+        // normalise V_{k+1} in place (zero for directions that stopped)
         KScope ks_(ctx, KC_KRYLOV);
-        k_copy_scale<T><<<nblk(nv, 256), 256, 0, st>>>(W.w, nap, W.V + (size_t)(k + 1) * nap, vs, W.s,
-                                                        nap, ndir);
+        k_copy_scale<T><<<nblk(nv, 256), 256, 0, st>>>(Vn, vs, Vn, vs, W.s, nap, ndir);
       }
       if (!any) { ++total; break; }
     }

@@ -217,9 +217,9 @@ cavity_status launch_precond(cavity_ctx* ctx) {
 
 // y = (block diagonal)^{-1} x for ndir vectors
 template <typename T>
-__global__ void k_pc_apply(const C<T>* __restrict__ x, C<T>* __restrict__ y,
-                           const C<T>* __restrict__ pinv, int nx, int ny, int n1, int n2, int nap,
-                           int ndir) {
+__global__ void k_pc_apply(const C<T>* __restrict__ x, long long xs, C<T>* __restrict__ y,
+                           long long ys, const C<T>* __restrict__ pinv, int nx, int ny, int n1,
+                           int n2, int nap, int ndir) {
   long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long per = (long long)nx * ny;
   if (gid >= per * ndir) return;
@@ -231,8 +231,8 @@ __global__ void k_pc_apply(const C<T>* __restrict__ x, C<T>* __restrict__ y,
   const bool has1 = n >= 1, has2 = m >= 1, has3 = m >= 1 && n >= 1;
   const int i1 = m * N + (n - 1), i2 = n1 + (m - 1) * (N + 1) + n;
   const int i3 = n1 + n2 + (m - 1) * N + (n - 1);
-  const C<T>* xd = x + (size_t)d * nap;
-  C<T>* yd = y + (size_t)d * nap;
+  const C<T>* xd = x + (size_t)d * xs;
+  C<T>* yd = y + (size_t)d * ys;
   C<T> v[3] = {mk<T>(0, 0), mk<T>(0, 0), mk<T>(0, 0)};
   if (has1) v[0] = xd[i1];
   if (has2) v[1] = xd[i2];
@@ -250,7 +250,10 @@ __global__ void k_pc_apply(const C<T>* __restrict__ x, C<T>* __restrict__ y,
 }
 
 template <typename T>
-cavity_status launch_precond_apply(cavity_ctx* ctx, int ndir, const C<T>* x, C<T>* y) {
+cavity_status launch_precond_apply(cavity_ctx* ctx, int ndir, const C<T>* x, C<T>* y,
+                                   long long xs, long long ys) {
+  if (xs < 0) xs = ctx->g.nap;
+  if (ys < 0) ys = ctx->g.nap;
   const Geo& g = ctx->g;
   const C<T>* pinv;
   if (sizeof(T) == 8) pinv = (const C<T>*)ctx->pinv64;
@@ -258,12 +261,14 @@ cavity_status launch_precond_apply(cavity_ctx* ctx, int ndir, const C<T>* x, C<T
   long long tot = (long long)g.nx * g.ny * ndir;
   {
     KScope ks_(ctx, KC_PRECOND);
-    k_pc_apply<T><<<(unsigned)((tot + 255) / 256), 256, 0, ctx->stream>>>(x, y, pinv, g.nx, g.ny, g.n1,
-                                                                          g.n2, g.nap, ndir);
+    k_pc_apply<T><<<(unsigned)((tot + 255) / 256), 256, 0, ctx->stream>>>(x, xs, y, ys, pinv, g.nx,
+        g.ny, g.n1, g.n2, g.nap, ndir);
   }
   CK(cudaGetLastError());
   return CAVITY_OK;
 }
 
-template cavity_status launch_precond_apply<double>(cavity_ctx*, int, const double2*, double2*);
-template cavity_status launch_precond_apply<float>(cavity_ctx*, int, const float2*, float2*);
+template cavity_status launch_precond_apply<double>(cavity_ctx*, int, const double2*, double2*,
+                                                    long long, long long);
+template cavity_status launch_precond_apply<float>(cavity_ctx*, int, const float2*, float2*,
+                                                   long long, long long);

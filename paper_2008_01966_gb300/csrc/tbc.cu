@@ -385,7 +385,8 @@ __global__ void __launch_bounds__(LINES_THREADS, sizeof(T) == 4 ? 3 : 2) k_tbcD(
 //  row 3: (m pi h/a)E1 + (n pi h/b)E2 + (-1+tau3)E3
 template <typename T>
 __global__ void k_combine(const C<T>* __restrict__ x, const C<T>* __restrict__ O,
-                          const C<T>* __restrict__ top, C<T>* __restrict__ y, TbcP p, int ndir) {
+                          const C<T>* __restrict__ top, C<T>* __restrict__ y, long long ys, TbcP p,
+                          int ndir) {
   const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (gid >= (long long)ndir * p.nap) return;
   const int d = (int)(gid / p.nap), i = (int)(gid - (long long)d * p.nap);
@@ -431,7 +432,7 @@ __global__ void k_combine(const C<T>* __restrict__ x, const C<T>* __restrict__ O
     r = cadd<T>(r, cscale<T>(E2[(m - 1) * (N + 1) + n], n * pb * h));
     r = cadd<T>(r, cmul<T>(cadd<T>(mk<T>(-1, 0), top[i]), E3[ii]));
   }
-  y[gid] = r;
+  y[(size_t)d * ys + i] = r;
 }
 
 size_t apply_work_bytes(const Geo& g, int ndir, int eb) {
@@ -488,7 +489,9 @@ template <> struct Tabs<float> {
 };
 
 template <typename T>
-cavity_status launch_apply(cavity_ctx* ctx, int ndir, const C<T>* x, C<T>* y, void* work) {
+cavity_status launch_apply(cavity_ctx* ctx, int ndir, const C<T>* x, C<T>* y, void* work,
+                           long long ystride) {
+  if (ystride < 0) ystride = ctx->g.nap;
   const Geo& g = ctx->g;
   const SmemCfg<T> sc = smem_cfg<T>(g);
   static bool smem_set[2] = {false, false};
@@ -531,15 +534,17 @@ cavity_status launch_apply(cavity_ctx* ctx, int ndir, const C<T>* x, C<T>* y, vo
   long long tot = (long long)ndir * g.nap;
   {
     KScope ks_(ctx, (sizeof(T) == 8 ? KC_COMB64 : KC_COMB32));
-    k_combine<T><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(x, R2, Tabs<T>::top(ctx), y, p,
-                                                                ndir);
+    k_combine<T><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(x, R2, Tabs<T>::top(ctx), y, ystride,
+                                                                p, ndir);
   }
   CK(cudaGetLastError());
   return CAVITY_OK;
 }
 
-template cavity_status launch_apply<double>(cavity_ctx*, int, const double2*, double2*, void*);
-template cavity_status launch_apply<float>(cavity_ctx*, int, const float2*, float2*, void*);
+template cavity_status launch_apply<double>(cavity_ctx*, int, const double2*, double2*, void*,
+                                           long long);
+template cavity_status launch_apply<float>(cavity_ctx*, int, const float2*, float2*, void*,
+                                          long long);
 
 // ------------------------------------------------------------------ no-alloc
 // Variant of cavity_apply for callers that must not allocate device memory.
