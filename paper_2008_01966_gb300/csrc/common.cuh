@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string>
+#include <type_traits>
+#include <utility>
 #include <vector>
 
 #include "../../include/cavity.h"
@@ -182,9 +184,9 @@ struct KScope {
     }                                                                            \
   } while (0)
 
-#define CKS(st)                                                                  \
+#define CKS(...)                                                                 \
   do {                                                                           \
-    cavity_status s_ = (st);                                                     \
+    cavity_status s_ = (__VA_ARGS__);                                            \
     if (s_ != CAVITY_OK) return s_;                                              \
   } while (0)
 
@@ -254,3 +256,20 @@ template <typename T>
 cavity_status launch_field(cavity_ctx* ctx, int ndir, const double2* ap, C<T>* out);
 cavity_status launch_rcs(cavity_ctx* ctx, int ndir, const double2* ap,
                          const double* th, const double* ph, int pol, double* sigma);
+
+// Kernels whose line transforms have compile-time lengths are instantiated for
+// log2 sizes LO..HI; dispatch_log calls f(std::integral_constant<int, v>).
+template <int LO, int HI, typename F>
+inline cavity_status dispatch_log(int v, F&& f) {
+  if constexpr (LO > HI) {
+    (void)v;
+    return CAVITY_EINVAL;
+  } else {
+    if (v == LO) return f(std::integral_constant<int, LO>{});
+    return dispatch_log<LO + 1, HI>(v, std::forward<F>(f));
+  }
+}
+__host__ __device__ constexpr int clog2(int v) { return v <= 1 ? 0 : 1 + clog2(v >> 1); }
+// log2 of the grid sizes nx, ny accepted by cavity_setup (4 .. 512)
+#define CAV_LOG_MIN 2
+#define CAV_LOG_MAX 9

@@ -4,32 +4,49 @@
 // trapezoid projections and the torus convolution of Sec. 5.2 -- are batches
 // of 1-D transforms of lines held in shared memory.
 //
-// Algorithm: Stockham auto-sort in at most three passes for n <= 4096: each
-// thread owns 16 consecutive "slots" of a line and, per pass, one radix-16
-// butterfly (or two radix-8, four radix-4, eight radix-2), whose inputs are
-// read from shared memory into registers, twiddled, transformed in registers
-// and written back in place after a barrier.  Lines use a padded layout
-// (one pad word per 16 elements, see pidx) so that the strided writes of the
-// first pass do not collide in the shared-memory banks.  Twiddles come from a
-// table tw[k] = exp(-2 pi i k / TW) computed once in FP64 (rounded for the
-// FP32 table): in FP32 a butterfly reads w^k and forms its powers by
-// multiplication (at most 7 products, ~5e-7 relative); in FP64 it reads every
+// Two algorithms:
+//  * warp transform (FP32, 64 <= n <= 1024): the line is split as n = LW x RV
+//    (LW lanes, RV values per lane, RV = LW or 2 LW); each lane does an RV-point
+//    DFT in registers, the twiddle w_n^{l k1}, one transpose through shared
+//    memory and an LW-point DFT in registers (the "four-step" factorisation).
+//    Only warp-level synchronisation inside the transform.
+//  * block transform (FP64, and FP32 lines outside that range): Stockham
+//    auto-sort with radix-8 passes, each thread owning 8 slots of a line per
+//    pass; inputs are read from shared memory into registers, twiddled,
+//    transformed and written back in place after a CTA barrier.
+// Lines use a padded layout (one pad word per 16 elements, see pidx) so that
+// strided accesses do not collide in the shared-memory banks.  Twiddles come
+// from a table tw[k] = exp(-2 pi i k / TW) computed once in FP64 (rounded for
+// the FP32 table); the block transform forms FP32 powers of the table value by
+// multiplication (at most 7 products, ~5e-7 relative) and reads every FP64
 // power from the table.  Forward = exp(-...), inverse = exp(+...),
 // unnormalised.
 //
 // Contract: a CTA transforms `nlines` lines of length n = 2^logn stored at
-// line_base + l * lstride (padded indices).  Threads 0 .. nlines*tpl-1 do the
-// work, tpl = max(1, n/16); all threads of the CTA must call (barriers).
+// line_base + l * lstride (padded indices, lstride >= padded_len(n)).  Threads
+// 0 .. nlines*tpl-1 do the work, tpl = fft_tpl<T>(n); all threads of the CTA
+// must call (barriers).
 #pragma once
 #include "common.cuh"
 
-__host__ __device__ __forceinline__ int pidx(int i) { return i + (i >> 4); }
-__host__ __device__ __forceinline__ int padded_len(int n) { return n + (n >> 4) + 1; }
-// elements per thread: 16 (radix up to 16) in FP32, 8 (radix up to 8) in FP64,
-// which keeps a butterfly's operands in registers without spilling
+__host__ __device__ constexpr int pidx(int i) { return i + (i >> 4); }
+// line length in shared memory: room for the padded layout and for the
+// transposed tile of the warp transform (n + n/8 for n >= 64)
+__host__ __device__ constexpr int padded_len(int n) { return n + (n >> 3) + 2; }
+// block transform: elements per thread (radix up to 8)
 template <typename T> struct FftE { static constexpr int E = 8, LRMAX = 3; };
-template <> struct FftE<double> { static constexpr int E = 8, LRMAX = 3; };
-template <typename T> __host__ __device__ __forceinline__ int fft_tpl(int n) {
+// warp transform (FP32, 64 <= n <= 1024): n = LW * RV lanes x values per lane
+__host__ __device__ constexpr bool warp_fft_ok(int n, int elem_bytes) {
+  return elem_bytes == 8 && n >= 64 && n <= 1024;
+}
+__host__ __device__ constexpr int warp_lanes(int n) {
+  int lg = 0;
+  while ((1 << lg) < n) ++lg;
+  return 1 << (lg >> 1);
+}
+// threads cooperating on one line (same as LineShape<T, log2 n>::TPL)
+template <typename T> __host__ __device__ constexpr int fft_tpl(int n) {
+  if (warp_fft_ok(n, (int)sizeof(C<T>))) return warp_lanes(n);
   return n >= FftE<T>::E ? n / FftE<T>::E : 1;
 }
 
@@ -113,6 +130,55 @@ __device__ __forceinline__ void dft16(C<T>* v) {
 }
 __host__ __device__ constexpr int dft16_slot(int k) { return 4 * (k & 3) + (k >> 2); }
 
+// 32-point DFT in place (natural order): even/odd 16-point halves + w32^k
+template <typename T, bool INV>
+__device__ __forceinline__ void dft32(C<T>* v) {
+  C<T> e[16], o[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    e[i] = v[2 * i];
+    o[i] = v[2 * i + 1];
+  }
+  dft16<T, INV>(e);
+  dft16<T, INV>(o);
+  // cos(k pi / 16), sin(k pi / 16), k = 0..15
+  const T cs[16] = {(T)1.0, (T)0.98078528040323044913, (T)0.92387953251128675613,
+                    (T)0.83146961230254523708, (T)0.70710678118654752440, (T)0.55557023301960222474,
+                    (T)0.38268343236508977173, (T)0.19509032201612826785, (T)0.0,
+                    (T)-0.19509032201612826785, (T)-0.38268343236508977173, (T)-0.55557023301960222474,
+                    (T)-0.70710678118654752440, (T)-0.83146961230254523708, (T)-0.92387953251128675613,
+                    (T)-0.98078528040323044913};
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const T c = cs[k], sn = cs[k < 8 ? 8 - k : k - 8];  // sin(k pi/16) = cos((8-k) pi/16)
+    const C<T> t = mulw<T, INV>(o[dft16_slot(k)], c, sn);
+    const C<T> ev = e[dft16_slot(k)];
+    v[k] = cadd<T>(ev, t);
+    v[k + 16] = csub<T>(ev, t);
+  }
+}
+
+// in-register DFT of size R with natural-order output
+template <typename T, bool INV, int R>
+__device__ __forceinline__ void dft_nat(C<T>* v) {
+  if constexpr (R == 32) {
+    dft32<T, INV>(v);
+  } else if constexpr (R == 16) {
+    C<T> u[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) u[i] = v[i];
+    dft16<T, INV>(u);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) v[k] = u[dft16_slot(k)];
+  } else if constexpr (R == 8) {
+    dft8<T, INV>(v);
+  } else if constexpr (R == 4) {
+    dft4<T, INV>(v);
+  } else {
+    dft2<T, INV>(v);
+  }
+}
+
 template <typename T, bool INV>
 __device__ __forceinline__ C<T> twid(const C<T>* __restrict__ tw, int idx) {
   C<T> w = tw[idx];
@@ -179,45 +245,145 @@ __device__ __forceinline__ void fft_pass(C<T>* line, int n, int s, int t, int tp
   __syncthreads();
 }
 
-// In-place FFT of `nlines` padded lines (stride lstride) of length n = 2^logn.
+// Warp transform of one line of length n = LW * RV (RV = LW or 2 LW) by LW lanes
+// (several lines per warp when LW < 32).  Lane l holds x[l + LW r], r < RV:
+//   X1[k1] = DFT_RV over r;  X1[k1] *= w_n^{l k1};  transposed through the
+//   line's own shared memory;  lane l then owns k1 = l + LW q and forms the
+//   LW-point DFT over the lanes:  X[k1 + RV k2].
+// One shared-memory round trip and warp-level synchronisation only.
+template <typename T, bool INV, int LW, int RV>
+__device__ __forceinline__ void fft_warp(C<T>* line, int n, int logn, int l, bool active,
+                                         const C<T>* __restrict__ tw, int twlog) {
+  C<T> v[RV];
+  if (active) {
+#pragma unroll
+    for (int r = 0; r < RV; ++r) v[r] = line[pidx(l + LW * r)];
+  }
+  __syncwarp();
+  if (active) {
+    dft_nat<T, INV, RV>(v);
+    const int shift = twlog - logn;
+#pragma unroll
+    for (int k1 = 1; k1 < RV; ++k1) v[k1] = cmul<T>(v[k1], twid<T, INV>(tw, ((l * k1) & (n - 1)) << shift));
+#pragma unroll
+    for (int k1 = 0; k1 < RV; ++k1) line[k1 * (LW + 1) + l] = v[k1];
+  }
+  __syncwarp();
+  constexpr int Q = RV / LW;
+  if (active) {
+#pragma unroll
+    for (int q = 0; q < Q; ++q)
+#pragma unroll
+      for (int ll = 0; ll < LW; ++ll) v[q * LW + ll] = line[(l + LW * q) * (LW + 1) + ll];
+  }
+  __syncwarp();
+  if (active) {
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      dft_nat<T, INV, LW>(v + q * LW);
+      const int k1 = l + LW * q;
+#pragma unroll
+      for (int k2 = 0; k2 < LW; ++k2) line[pidx(k1 + RV * k2)] = v[q * LW + k2];
+    }
+  }
+  __syncwarp();
+}
+
+// Block transform of `nlines` lines of runtime length n = 2^logn (setup
+// kernels only; the hot passes use the compile-time fft_lines below).
+// Must be called by all threads of the CTA; ends with a CTA barrier.  Lines
+// beyond what the CTA covers at once (blockDim / tpl) are done in groups.
 template <typename T, bool INV>
 __device__ void fft_inplace(C<T>* base, int lstride, int n, int logn, int nlines,
                             const C<T>* __restrict__ tw, int twlog) {
   constexpr int E = FftE<T>::E, LRMAX = FftE<T>::LRMAX;
   const int tid = threadIdx.x + threadIdx.y * blockDim.x;
-  const int tpl = fft_tpl<T>(n);
-  const int l = tid / tpl, t = tid - l * tpl;
-  const bool active = l < nlines;
-  C<T>* line = base + (size_t)(active ? l : 0) * lstride;
-  if (n < E) {
-    // one pass of radix n
-    switch (logn) {
-      case 3: fft_pass<T, INV, 3, 1>(line, n, 0, t, tpl, tw, twlog, active); break;
-      case 2: fft_pass<T, INV, 2, 1>(line, n, 0, t, tpl, tw, twlog, active); break;
-      case 1: fft_pass<T, INV, 1, 1>(line, n, 0, t, tpl, tw, twlog, active); break;
-      default: break;
-    }
-    return;
-  }
-  // pass schedule: ceil(logn / LRMAX) passes with balanced radices
-  const int k = (logn + LRMAX - 1) / LRMAX;
-  int s = 0;
-  for (int p = 0; p < k; ++p) {
-    const int lr = logn / k + (p < logn % k ? 1 : 0);
-    if constexpr (E == 16) {
-      switch (lr) {
-        case 4: fft_pass<T, INV, 4, 1>(line, n, s, t, tpl, tw, twlog, active); break;
-        case 3: fft_pass<T, INV, 3, 2>(line, n, s, t, tpl, tw, twlog, active); break;
-        case 2: fft_pass<T, INV, 2, 4>(line, n, s, t, tpl, tw, twlog, active); break;
-        default: fft_pass<T, INV, 1, 8>(line, n, s, t, tpl, tw, twlog, active); break;
+  const int nthr = blockDim.x * blockDim.y;
+  const int tpl = n >= E ? n / E : 1;
+  const int lpg = nthr >= tpl ? nthr / tpl : 1;
+  const int lg = tid / tpl, t = tid - lg * tpl;
+  for (int l0 = 0; l0 < nlines; l0 += lpg) {
+    const int l = l0 + lg;
+    const bool active = lg < lpg && l < nlines;
+    C<T>* line = base + (size_t)(active ? l : 0) * lstride;
+    if (n < E) {
+      switch (logn) {
+        case 3: fft_pass<T, INV, 3, 1>(line, n, 0, t, tpl, tw, twlog, active); break;
+        case 2: fft_pass<T, INV, 2, 1>(line, n, 0, t, tpl, tw, twlog, active); break;
+        case 1: fft_pass<T, INV, 1, 1>(line, n, 0, t, tpl, tw, twlog, active); break;
+        default: break;
       }
-    } else {
+      continue;
+    }
+    const int k = (logn + LRMAX - 1) / LRMAX;
+    int s = 0;
+    for (int p = 0; p < k; ++p) {
+      const int lr = logn / k + (p < logn % k ? 1 : 0);
       switch (lr) {
         case 3: fft_pass<T, INV, 3, 1>(line, n, s, t, tpl, tw, twlog, active); break;
         case 2: fft_pass<T, INV, 2, 2>(line, n, s, t, tpl, tw, twlog, active); break;
         default: fft_pass<T, INV, 1, 4>(line, n, s, t, tpl, tw, twlog, active); break;
       }
+      s += lr;
     }
-    s += lr;
   }
+  __syncthreads();
+}
+
+// radix (log2) of pass P of the balanced schedule for a length 2^LOGN
+template <int LOGN, int P> struct BlockRadix {
+  static constexpr int K = (LOGN + 2) / 3;
+  static constexpr int LR = LOGN / K + (P < LOGN % K ? 1 : 0);
+  static constexpr int S = P == 0 ? 0 : BlockRadix<LOGN, (P > 0 ? P - 1 : 0)>::S + BlockRadix<LOGN, (P > 0 ? P - 1 : 0)>::LR;
+};
+template <int LOGN> struct BlockRadix<LOGN, 0> {
+  static constexpr int K = (LOGN + 2) / 3;
+  static constexpr int LR = LOGN / K + (0 < LOGN % K ? 1 : 0);
+  static constexpr int S = 0;
+};
+
+template <typename T, bool INV, int LOGN, int P>
+__device__ __forceinline__ void block_passes(C<T>* line, int t, int tpl, const C<T>* __restrict__ tw,
+                                             int twlog, bool active) {
+  if constexpr (P < BlockRadix<LOGN, 0>::K) {
+    constexpr int LR = BlockRadix<LOGN, P>::LR;
+    constexpr int PER = 8 >> LR;
+    fft_pass<T, INV, LR, PER>(line, 1 << LOGN, BlockRadix<LOGN, P>::S, t, tpl, tw, twlog, active);
+    block_passes<T, INV, LOGN, P + 1>(line, t, tpl, tw, twlog, active);
+  }
+}
+
+// threads cooperating on one line of length 2^LOGN
+template <typename T, int LOGN> struct LineShape {
+  static constexpr bool WARP = sizeof(T) == 4 && LOGN >= 6 && LOGN <= 10;
+  static constexpr int LW = 1 << (LOGN / 2);
+  static constexpr int RV = (1 << LOGN) / LW;
+  static constexpr int TPL = WARP ? LW : (LOGN >= 3 ? (1 << LOGN) / 8 : 1);
+};
+
+// In-place FFT of `nlines` padded lines (stride lstride) of the compile-time
+// length 2^LOGN: the warp transform where it applies, else the block
+// transform.  Called by all threads of the CTA; ends with a CTA barrier.
+template <typename T, bool INV, int LOGN>
+__device__ __forceinline__ void fft_lines(C<T>* base, int lstride, int nlines,
+                                          const C<T>* __restrict__ tw, int twlog) {
+  using S = LineShape<T, LOGN>;
+  constexpr int n = 1 << LOGN, tpl = S::TPL;
+  const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+  const int nthr = blockDim.x * blockDim.y;
+  const int lpg = nthr >= tpl ? nthr / tpl : 1;
+  const int lg = tid / tpl, t = tid - lg * tpl;
+  for (int l0 = 0; l0 < nlines; l0 += lpg) {
+    const int l = l0 + lg;
+    const bool active = lg < lpg && l < nlines;
+    C<T>* line = base + (size_t)(active ? l : 0) * lstride;
+    if constexpr (S::WARP) {
+      fft_warp<T, INV, S::LW, S::RV>(line, n, LOGN, t, active, tw, twlog);
+    } else if constexpr (LOGN <= 3) {
+      if constexpr (LOGN >= 1) fft_pass<T, INV, LOGN, 1>(line, n, 0, t, tpl, tw, twlog, active);
+    } else {
+      block_passes<T, INV, LOGN, 0>(line, t, tpl, tw, twlog, active);
+    }
+  }
+  __syncthreads();
 }

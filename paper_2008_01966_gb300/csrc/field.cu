@@ -30,22 +30,22 @@ struct FP {
 };
 
 #define FIELD_THREADS 256
-template <typename T> __host__ __device__ __forceinline__ int field_lines(int n) {
-  int tl = fft_tpl<T>(n);
-  return tl >= FIELD_THREADS ? 1 : FIELD_THREADS / tl;
+template <typename T> __host__ __device__ constexpr int field_lines(int n) {
+  return fft_tpl<T>(n) >= FIELD_THREADS ? 1 : FIELD_THREADS / fft_tpl<T>(n);
 }
 
-// pass 1: grid (ceil(nx / L) row groups, 3 components, ndir * lc slabs)
-template <typename T>
-__global__ void __launch_bounds__(FIELD_THREADS) k_field_y(const C<T>* __restrict__ ap,
+// pass 1: grid (ceil(nx / L) row groups, 3 components, ndir * lc slabs);
+// instantiated per LNY = log2 ny
+template <typename T, int LNY>
+__global__ void __launch_bounds__(FIELD_THREADS, 2) k_field_y(const C<T>* __restrict__ ap,
                                                            const C<T>* __restrict__ prof,
                                                            const C<T>* __restrict__ profq,
                                                            C<T>* __restrict__ T1, FP p,
                                                            const C<T>* __restrict__ tw) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   C<T>* buf = (C<T>*)sm_raw;
-  const int ny = p.ny, n2 = 2 * ny, ls = padded_len(n2);
-  const int L = field_lines<T>(n2);
+  constexpr int ny = 1 << LNY, n2 = 2 * ny, ls = padded_len(n2);
+  constexpr int L = field_lines<T>(n2);
   const int comp = blockIdx.y, s = blockIdx.z;
   const int r0 = blockIdx.x * L;
   const int d = s / p.lc, jj = s - d * p.lc;
@@ -59,9 +59,8 @@ __global__ void __launch_bounds__(FIELD_THREADS) k_field_y(const C<T>* __restric
   const bool ycos = (comp == 1);
   for (int t = tid; t < L * ls; t += nthr) buf[t] = mk<T>(0, 0);
   __syncthreads();
-  const int nn = p.N + 1;                     // = ny, a power of two
-  for (int idx = tid; idx < L * nn; idx += nthr) {
-    const int l = idx >> p.lny, n = idx & (nn - 1);
+  for (int idx = tid; idx < L * ny; idx += nthr) {
+    const int l = idx >> LNY, n = idx & (ny - 1);
     const int r = r0 + l;
     const int m = comp == 0 ? r : r + 1;
     if (r >= p.nx || m > p.M || m < 0) continue;
@@ -86,7 +85,7 @@ __global__ void __launch_bounds__(FIELD_THREADS) k_field_y(const C<T>* __restric
     }
   }
   __syncthreads();
-  fft_inplace<T, true>(buf, ls, n2, p.lny + 1, L, tw, p.twlog);
+  fft_lines<T, true, LNY + 1>(buf, ls, L, tw, p.twlog);
   for (int l = 0; l < L; ++l) {
     const int r = r0 + l;
     if (r >= p.nx) break;
@@ -99,15 +98,17 @@ __global__ void __launch_bounds__(FIELD_THREADS) k_field_y(const C<T>* __restric
   }
 }
 
-// pass 2: grid (ceil((ny+1) / L) column groups, 3 components, ndir * lc slabs)
-template <typename T>
-__global__ void __launch_bounds__(FIELD_THREADS) k_field_x(const C<T>* __restrict__ T1,
+// pass 2: grid (ceil((ny+1) / L) column groups, 3 components, ndir * lc
+// slabs); instantiated per LNX = log2 nx
+template <typename T, int LNX>
+__global__ void __launch_bounds__(FIELD_THREADS, 2) k_field_x(const C<T>* __restrict__ T1,
                                                            C<T>* __restrict__ out, FP p,
                                                            const C<T>* __restrict__ tw) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   C<T>* buf = (C<T>*)sm_raw;
-  const int nx = p.nx, ny = p.ny, n2 = 2 * nx, ls = padded_len(n2);
-  const int L = field_lines<T>(n2);
+  constexpr int nx = 1 << LNX, n2 = 2 * nx, ls = padded_len(n2);
+  constexpr int L = field_lines<T>(n2), lL = clog2(L);
+  const int ny = p.ny;
   const int comp = blockIdx.y, s = blockIdx.z;
   const int q0 = blockIdx.x * L;
   const int d = s / p.lc, jj = s - d * p.lc;
@@ -119,7 +120,6 @@ __global__ void __launch_bounds__(FIELD_THREADS) k_field_x(const C<T>* __restric
   for (int t = tid; t < L * ls; t += nthr) buf[t] = mk<T>(0, 0);
   __syncthreads();
   const int nrows = xcos ? nx : nx - 1;    // E1: m = 0..M; E2/E3: m = 1..M
-  const int lL = __ffs(L) - 1;
   for (int idx = tid; idx < L * nrows; idx += nthr) {
     const int r = idx >> lL, l = idx & (L - 1);
     const int q = q0 + l;
@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(FIELD_THREADS) k_field_x(const C<T>* __restric
     }
   }
   __syncthreads();
-  fft_inplace<T, true>(buf, ls, n2, p.lnx + 1, L, tw, p.twlog);
+  fft_lines<T, true, LNX + 1>(buf, ls, L, tw, p.twlog);
   long long off;
   int ncol, qlo, qhi, plo, phi;
   if (comp == 0) { off = 0; ncol = ny - 1; qlo = 1; qhi = ny - 1; plo = 0; phi = nx; }
@@ -190,32 +190,38 @@ cavity_status launch_field(cavity_ctx* ctx, int ndir, const double2* ap, C<T>* o
     profq = layered ? (const C<T>*)ctx->profq32 : nullptr;
   }
   const C<T>* tw = sizeof(T) == 8 ? (const C<T>*)ctx->tw64 : (const C<T>*)ctx->tw32;
-  const int Ly = field_lines<T>(2 * g.ny), Lx = field_lines<T>(2 * g.nx);
-  size_t smy = sizeof(C<T>) * (size_t)Ly * padded_len(2 * g.ny);
-  size_t smx = sizeof(C<T>) * (size_t)Lx * padded_len(2 * g.nx);
-  static bool set[2] = {false, false};
-  const int ti = sizeof(T) == 8 ? 0 : 1;
-  if (!set[ti]) {
-    CK(allow_max_smem(k_field_y<T>));
-    CK(allow_max_smem(k_field_x<T>));
-    set[ti] = true;
-  }
   FP p;
   p.nx = g.nx; p.ny = g.ny; p.nz = g.nz; p.M = g.M; p.N = g.N; p.n1 = g.n1; p.n2 = g.n2;
   p.nap = g.nap; p.lnx = g.lnx; p.lny = g.lny; p.twlog = ilog2(ctx->TW);
   p.lc = lc; p.ndir = ndir; p.layered = layered; p.S = g.field_per_level;
   for (int j0 = 1; j0 <= g.nz; j0 += lc) {
     p.j0 = j0;
-    {
+    CKS(dispatch_log<CAV_LOG_MIN, CAV_LOG_MAX>(g.lny, [&](auto c) -> cavity_status {
+      constexpr int LN = decltype(c)::value, L = field_lines<T>(2 << LN);
+      static bool done = false;
+      if (!done) {
+        CK(allow_max_smem(k_field_y<T, LN>));
+        done = true;
+      }
       KScope ks_(ctx, KC_FIELD_Y);
-      k_field_y<T><<<dim3((g.nx + Ly - 1) / Ly, 3, ndir * lc), FIELD_THREADS, smy, ctx->stream>>>(
+      k_field_y<T, LN><<<dim3((g.nx + L - 1) / L, 3, ndir * lc), FIELD_THREADS,
+                         sizeof(C<T>) * (size_t)L * padded_len(2 << LN), ctx->stream>>>(
           apT, prof, profq, T1, p, tw);
-    }
-    {
+      return CAVITY_OK;
+    }));
+    CKS(dispatch_log<CAV_LOG_MIN, CAV_LOG_MAX>(g.lnx, [&](auto c) -> cavity_status {
+      constexpr int LN = decltype(c)::value, L = field_lines<T>(2 << LN);
+      static bool done = false;
+      if (!done) {
+        CK(allow_max_smem(k_field_x<T, LN>));
+        done = true;
+      }
       KScope ks_(ctx, KC_FIELD_X);
-      k_field_x<T><<<dim3((g.ny + 1 + Lx - 1) / Lx, 3, ndir * lc), FIELD_THREADS, smx, ctx->stream>>>(
+      k_field_x<T, LN><<<dim3((g.ny + 1 + L - 1) / L, 3, ndir * lc), FIELD_THREADS,
+                         sizeof(C<T>) * (size_t)L * padded_len(2 << LN), ctx->stream>>>(
           T1, out, p, tw);
-    }
+      return CAVITY_OK;
+    }));
   }
   CK(cudaGetLastError());
   return CAVITY_OK;

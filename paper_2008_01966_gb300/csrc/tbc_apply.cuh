@@ -1,0 +1,465 @@
+// The aperture operator of (EJ1)/(uT1): the cavity (local) part and the TBC
+// part whose singular integrals follow Sec. 5 (discrete rule: periodised FFT
+// convolution with the exact transform of the truncated basis, the kernel
+// table F(G), inverse transform on the torus grid, trapezoid outer rule).
+//
+// For each right-hand side the TBC needs three convolution-projections,
+//   U1 = <cs_mn, G*u1>,  U2 = <sc_mn, G*u2>,  W = <cc_mn, G*w>,
+// u1 = sum E1 cs, u2 = sum E2 sc, w = div_Gamma(z x E) = sum (k2 pi/b) E1 cc -
+// sum (k1 pi/a) E2 cc (Sec. 5.1 reduces every coefficient to I1, I2, I3).
+// Each one is four passes of batched line transforms in shared memory:
+//   A  (rows k1)   basis transform along x2: FFT convolution of the mirrored
+//                  coefficients with the 1-D kernel E(nu) of F(F)
+//   B  (cols j2)   basis transform along x1, times F(G)/(Lx Ly), inverse DFT
+//                  along x1 evaluated at the nodes p = 0..Nx
+//   C  (rows p)    inverse DFT along x2 at q = 0..Ny, trapezoid projection
+//                  onto cos/sin(n pi q/Ny) (an extended FFT of length 2Ny)
+//   D  (cols n)    trapezoid projection along x1 (extended FFT of length 2Nx)
+// and a final elementwise pass adds the local part of (EJ1)/(uT1).
+// Templated on the arithmetic type: FP64 for the FP64 path and the residuals,
+// FP32 for the inner Krylov iterations of the mixed path.  Every pass kernel
+// is instantiated per grid size so that its line transforms have compile-time
+// lengths; tbc.cu instantiates the FP64 operator, tbc_f32.cu the FP32 one.
+#pragma once
+#include <algorithm>
+
+#include "common.cuh"
+#include "fft.cuh"
+
+struct TbcP {
+  int nx, ny, M, N, Px, Py, lPx, lPy, lnx, lny, nap, n1, n2;
+  double a, b, h, k2x2;  // k2x2 = 2 kappa0^2
+  int twlog;
+};
+
+static TbcP make_params(const cavity_ctx* ctx) {
+  const Geo& g = ctx->g;
+  TbcP p;
+  p.nx = g.nx; p.ny = g.ny; p.M = g.M; p.N = g.N; p.Px = g.Px; p.Py = g.Py;
+  p.lPx = g.lPx; p.lPy = g.lPy; p.lnx = g.lnx; p.lny = g.lny;
+  p.nap = g.nap; p.n1 = g.n1; p.n2 = g.n2;
+  p.a = g.a; p.b = g.b; p.h = g.h; p.k2x2 = 2.0 * ctx->kappa0 * ctx->kappa0;
+  p.twlog = ilog2(ctx->TW);
+  return p;
+}
+
+template <typename T> __device__ __forceinline__ C<T> czero() { return mk<T>(0, 0); }
+
+// Lines per CTA: enough lines that a pass of the longest transform in the
+// kernel occupies LINES_THREADS threads (nlong = that length).
+#define LINES_THREADS 256
+template <typename T> __host__ __device__ constexpr int lines_per_cta(int nlong) {
+  return fft_tpl<T>(nlong) >= LINES_THREADS ? 1 : LINES_THREADS / fft_tpl<T>(nlong);
+}
+// passes A and B hold two lines (parities r = 0, 1) per row / column
+template <typename T> __host__ __device__ constexpr int pairs_per_cta(int n) {
+  return 2 * fft_tpl<T>(n) >= LINES_THREADS ? 1 : LINES_THREADS / (2 * fft_tpl<T>(n));
+}
+// registers: FP32 and FP64 kernels run two CTAs of LINES_THREADS per SM
+#define TBC_BOUNDS __launch_bounds__(LINES_THREADS, 2)
+
+// The pass kernels are instantiated per grid size: LNY = log2 ny (passes A,
+// C), LNX = log2 nx (passes B, D).  With the period pad = 4: Px = 4 nx,
+// Py = 4 ny.
+
+// ------------------------------------------------------------------ pass A
+// grid (ceil(nx / L) row groups, 3 fields, ndir); field 0: cs (E1), 1: sc (E2),
+// 2: cc (w).  Per row k1: the mirrored coefficient sequence along x2 (period
+// Py) is transformed, multiplied by the transforms of the two parity kernels
+// eps_r and transformed back: the linear convolutions give the basis
+// transform at j2 = 2t + r of the symmetric box.  Lines: [parity][row].
+template <typename T, int LNY>
+__global__ void TBC_BOUNDS k_tbcA(const C<T>* __restrict__ x, C<T>* __restrict__ Vy, TbcP p,
+                                  const C<T>* __restrict__ tw, const C<T>* __restrict__ eh_c,
+                                  const C<T>* __restrict__ eh_s) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  C<T>* buf = (C<T>*)sm_raw;
+  constexpr int LPY = LNY + 2, Py = 1 << LPY, ny = 1 << LNY, ls = padded_len(Py);
+  constexpr int L = pairs_per_cta<T>(Py);
+  const int f = blockIdx.y, d = blockIdx.z;
+  const int row0 = blockIdx.x * L;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const C<T>* E1 = x + (size_t)d * p.nap;
+  const C<T>* E2 = E1 + p.n1;
+  const int N = ny - 1;
+  const bool ycos = (f != 0);
+  for (int t = tid; t < L * ls; t += nthr) buf[t] = czero<T>();
+  __syncthreads();
+  for (int idx = tid; idx < L * ny; idx += nthr) {
+    const int l = idx >> LNY, k2 = idx & (ny - 1);
+    const int k1 = row0 + l;
+    if (k1 >= p.nx) continue;
+    C<T> c = czero<T>();
+    if (f == 0) {
+      if (k2 >= 1) c = E1[k1 * N + (k2 - 1)];
+    } else if (f == 1) {
+      if (k1 >= 1) c = E2[(k1 - 1) * ny + k2];
+    } else {
+      if (k2 >= 1) c = cscale<T>(E1[k1 * N + (k2 - 1)], (T)(k2 * M_PI / p.b));
+      if (k1 >= 1) c = csub<T>(c, cscale<T>(E2[(k1 - 1) * ny + k2], (T)(k1 * M_PI / p.a)));
+    }
+    C<T>* line = buf + (size_t)l * ls;
+    if (ycos) {
+      if (k2 == 0) line[0] = cscale<T>(c, (T)2);
+      else { line[pidx(k2)] = c; line[pidx(Py - k2)] = c; }
+    } else if (k2 >= 1) {
+      line[pidx(k2)] = c;
+      line[pidx(Py - k2)] = mk<T>(-c.x, -c.y);
+    }
+  }
+  __syncthreads();
+  fft_lines<T, false, LPY>(buf, ls, L, tw, p.twlog);
+  const C<T>* eh = ycos ? eh_c : eh_s;
+  for (int idx = tid; idx < L * Py; idx += nthr) {
+    const int l = idx >> LPY, t = idx & (Py - 1);
+    C<T>* line = buf + (size_t)l * ls;
+    const C<T> sv = line[pidx(t)];
+    line[pidx(t)] = cmul<T>(sv, eh[t]);
+    buf[(size_t)(L + l) * ls + pidx(t)] = cmul<T>(sv, eh[Py + t]);
+  }
+  __syncthreads();
+  fft_lines<T, true, LPY>(buf, ls, 2 * L, tw, p.twlog);
+  for (int idx = tid; idx < L * Py; idx += nthr) {
+    const int l = idx >> LPY, j = idx & (Py - 1);
+    const int k1 = row0 + l;
+    if (k1 >= p.nx) continue;
+    C<T> r = czero<T>();
+    if (j != Py / 2) {
+      const int j2 = j < Py / 2 ? j : j - Py;
+      const int t = j2 >> 1, par = j2 & 1;     // j2 = 2 t + par (floor)
+      r = buf[(size_t)(par * L + l) * ls + pidx(t & (Py - 1))];
+    }
+    Vy[((size_t)(d * 3 + f) * p.nx + k1) * Py + j] = r;
+  }
+}
+
+// ------------------------------------------------------------------ pass B
+// grid (Py / L column groups, 3 fields, ndir).  Per column j2: the basis
+// transform along x1 split by the parity of j1 = 2t + r (as in pass A), times
+// F(G)(|j1|, |j2|)/(Lx Ly), then the inverse torus transform along x1 at the
+// nodes p = 0..nx:  sum_j1 Y(j1) e^{2 pi i j1 p/Px} = Z_0(p) + e^{2 pi i p/Px} Z_1(p),
+// Z_r = inverse transform of length Px/2 of Y(2t + r) over t.
+template <typename T, int LNX>
+__global__ void TBC_BOUNDS k_tbcB(const C<T>* __restrict__ Vy, C<T>* __restrict__ W, TbcP p,
+                                  const C<T>* __restrict__ tw, const C<T>* __restrict__ eh_c,
+                                  const C<T>* __restrict__ eh_s, const C<T>* __restrict__ kh) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  C<T>* buf = (C<T>*)sm_raw;
+  constexpr int LPX = LNX + 2, Px = 1 << LPX, nx = 1 << LNX, ls = padded_len(Px);
+  constexpr int L = pairs_per_cta<T>(Px), lL = clog2(L);
+  constexpr int hp = Px / 2, qp = Px / 4;
+  const int Py = p.Py;
+  const int f = blockIdx.y, d = blockIdx.z;
+  const int j0 = blockIdx.x * L;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const bool xcos = (f != 1);
+  const C<T>* src = Vy + (size_t)(d * 3 + f) * nx * Py;
+  for (int t = tid; t < L * ls; t += nthr) buf[t] = czero<T>();
+  __syncthreads();
+  for (int idx = tid; idx < L * nx; idx += nthr) {
+    const int k1 = idx >> lL, l = idx & (L - 1);
+    const int j = j0 + l;
+    if (j >= Py) continue;
+    const C<T> c = src[(size_t)k1 * Py + j];
+    C<T>* line = buf + (size_t)l * ls;
+    if (xcos) {
+      if (k1 == 0) line[0] = cscale<T>(c, (T)2);
+      else { line[pidx(k1)] = c; line[pidx(Px - k1)] = c; }
+    } else if (k1 >= 1) {
+      line[pidx(k1)] = c;
+      line[pidx(Px - k1)] = mk<T>(-c.x, -c.y);
+    }
+  }
+  __syncthreads();
+  fft_lines<T, false, LPX>(buf, ls, L, tw, p.twlog);
+  const C<T>* eh = xcos ? eh_c : eh_s;
+  for (int idx = tid; idx < L * Px; idx += nthr) {
+    const int l = idx >> LPX, t = idx & (Px - 1);
+    C<T>* line = buf + (size_t)l * ls;
+    const C<T> sv = line[pidx(t)];
+    line[pidx(t)] = cmul<T>(sv, eh[t]);
+    buf[(size_t)(L + l) * ls + pidx(t)] = cmul<T>(sv, eh[Px + t]);
+  }
+  __syncthreads();
+  fft_lines<T, true, LPX>(buf, ls, 2 * L, tw, p.twlog);
+  // K-hat in place: slot u < Px/2 of line (r, l) receives t = u (u < Px/4) or
+  // t = u - Px/2, read from slot t mod Px.  Sources and destinations of
+  // different slots never overlap (u >= Px/4 reads u + Px/2).
+  for (int idx = tid; idx < 2 * L * hp; idx += nthr) {
+    const int lr = idx >> (LPX - 1), u = idx & (hp - 1);
+    const int r = lr >= L ? 1 : 0, l = lr - r * L;
+    const int j = j0 + l;
+    const int t = u < qp ? u : u - hp;
+    const int j1 = 2 * t + r;
+    C<T>* line = buf + (size_t)lr * ls;
+    C<T> v = czero<T>();
+    if (j1 != -hp && j < Py && j != Py / 2) {
+      const int j1a = j1 < 0 ? -j1 : j1;
+      const int j2a = j < Py / 2 ? j : Py - j;
+      v = cmul<T>(line[pidx(t & (Px - 1))], kh[(size_t)j2a * hp + j1a]);
+    }
+    line[pidx(u)] = v;
+  }
+  __syncthreads();
+  fft_lines<T, true, LPX - 1>(buf, ls, 2 * L, tw, p.twlog);
+  C<T>* dst = W + (size_t)(d * 3 + f) * (nx + 1) * Py;
+  const int sh = p.twlog - LPX;
+  for (int idx = tid; idx < L * (nx + 1); idx += nthr) {
+    const int q = idx >> lL, l = idx & (L - 1);
+    const int j = j0 + l;
+    if (j >= Py) continue;
+    const C<T> z0 = buf[(size_t)l * ls + pidx(q)];
+    const C<T> z1 = buf[(size_t)(L + l) * ls + pidx(q)];
+    dst[(size_t)q * Py + j] = cadd<T>(z0, cmul<T>(z1, twid<T, true>(tw, q << sh)));
+  }
+}
+
+// ------------------------------------------------------------------ pass C
+// grid (ceil((nx+1)/L) row groups, 3 fields, ndir).  Per node row p: inverse
+// torus transform along x2 at q = 0..ny, then the trapezoid projection onto
+// cos/sin(n pi q/ny) as an extended FFT of length 2 ny.
+template <typename T, int LNY>
+__global__ void TBC_BOUNDS k_tbcC(const C<T>* __restrict__ W, C<T>* __restrict__ Z, TbcP p,
+                                  const C<T>* __restrict__ tw) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  C<T>* buf = (C<T>*)sm_raw;
+  constexpr int LPY = LNY + 2, Py = 1 << LPY, ny = 1 << LNY, n2 = 2 * ny, ls = padded_len(Py);
+  constexpr int L = lines_per_cta<T>(Py);
+  const int f = blockIdx.y, d = blockIdx.z;
+  const int r0 = blockIdx.x * L;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const bool ycos = (f != 0);
+  const C<T>* src = W + (size_t)(d * 3 + f) * (p.nx + 1) * Py;
+  for (int idx = tid; idx < L * Py; idx += nthr) {
+    const int l = idx >> LPY, t = idx & (Py - 1);
+    const int row = r0 + l;
+    buf[(size_t)l * ls + pidx(t)] = row <= p.nx ? src[(size_t)row * Py + t] : czero<T>();
+  }
+  __syncthreads();
+  fft_lines<T, true, LPY>(buf, ls, L, tw, p.twlog);
+  // even (cos) / odd (sin) extension of U(q), q = 0..ny, to length 2 ny in place
+  for (int idx = tid; idx < L * n2; idx += nthr) {
+    const int l = idx >> (LNY + 1), t = idx & (n2 - 1);
+    C<T>* line = buf + (size_t)l * ls;
+    if (t <= ny) {
+      if (!ycos && (t == 0 || t == ny)) line[pidx(t)] = czero<T>();
+    } else {
+      C<T> v = line[pidx(n2 - t)];
+      line[pidx(t)] = ycos ? v : mk<T>(-v.x, -v.y);
+    }
+  }
+  __syncthreads();
+  fft_lines<T, false, LNY + 1>(buf, ls, L, tw, p.twlog);
+  const T w = (T)(0.5 * p.b / ny);
+  for (int idx = tid; idx < L * (ny + 1); idx += nthr) {
+    const int l = idx / (ny + 1), n = idx - l * (ny + 1);
+    const int row = r0 + l;
+    if (row > p.nx) continue;
+    const C<T> v = buf[(size_t)l * ls + pidx(n)];
+    Z[((size_t)(d * 3 + f) * (p.nx + 1) + row) * (ny + 1) + n] =
+        ycos ? cscale<T>(v, w) : cscale<T>(cmul_i<T>(v), w);
+  }
+}
+
+// ------------------------------------------------------------------ pass D
+// grid (ceil((ny+1)/L) column groups, 3 fields, ndir).  Per column n: the
+// trapezoid projection along x1 (extended FFT of length 2 nx).
+template <typename T, int LNX>
+__global__ void TBC_BOUNDS k_tbcD(const C<T>* __restrict__ Z, C<T>* __restrict__ O, TbcP p,
+                                  const C<T>* __restrict__ tw) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  C<T>* buf = (C<T>*)sm_raw;
+  constexpr int nx = 1 << LNX, n2 = 2 * nx, ls = padded_len(n2);
+  constexpr int L = lines_per_cta<T>(n2), lL = clog2(L);
+  const int ny = p.ny;
+  const int f = blockIdx.y, d = blockIdx.z;
+  const int c0 = blockIdx.x * L;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const bool xcos = (f != 1);
+  const C<T>* src = Z + (size_t)(d * 3 + f) * (nx + 1) * (ny + 1);
+  for (int idx = tid; idx < L * n2; idx += nthr) {
+    const int t = idx >> lL, l = idx & (L - 1);
+    const int col = c0 + l;
+    C<T> r = czero<T>();
+    if (col <= ny) {
+      if (t <= nx) {
+        r = src[(size_t)t * (ny + 1) + col];
+        if (!xcos && (t == 0 || t == nx)) r = czero<T>();
+      } else {
+        r = src[(size_t)(n2 - t) * (ny + 1) + col];
+        if (!xcos) r = mk<T>(-r.x, -r.y);
+      }
+    }
+    buf[(size_t)l * ls + pidx(t)] = r;
+  }
+  __syncthreads();
+  fft_lines<T, false, LNX + 1>(buf, ls, L, tw, p.twlog);
+  C<T>* dst = O + (size_t)(d * 3 + f) * nx * (ny + 1);
+  const T w = (T)(0.5 * p.a / nx);
+  for (int idx = tid; idx < L * nx; idx += nthr) {
+    const int m = idx >> lL, l = idx & (L - 1);
+    const int col = c0 + l;
+    if (col > ny) continue;
+    const C<T> v = buf[(size_t)l * ls + pidx(m)];
+    dst[(size_t)m * (ny + 1) + col] = xcos ? cscale<T>(v, w) : cscale<T>(cmul_i<T>(v), w);
+  }
+}
+
+// ------------------------------------------------------------------ combine
+// y = local part of (EJ1)/(uT1) + TBC rows, with the TBC sign that makes T
+// the exterior admittance z x curl E^s of (EGa2):
+//  row 1: (-1+tau1)E1 + (m pi h/a + vs1)E3 + (h/q)(2k^2 U1 - 2(n pi/b) W)
+//  row 2: (-1+tau2)E2 + (n pi h/b + vs2)E3 + (h/c)(2k^2 U2 + 2(m pi/a) W)
+//  row 3: (m pi h/a)E1 + (n pi h/b)E2 + (-1+tau3)E3
+template <typename T>
+__global__ void k_combine(const C<T>* __restrict__ x, const C<T>* __restrict__ O,
+                          const C<T>* __restrict__ top, C<T>* __restrict__ y, long long ys, TbcP p,
+                          int ndir) {
+  const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (gid >= (long long)ndir * p.nap) return;
+  const int d = (int)(gid / p.nap), i = (int)(gid - (long long)d * p.nap);
+  const C<T>* xd = x + (size_t)d * p.nap;
+  const C<T>* E1 = xd;
+  const C<T>* E2 = xd + p.n1;
+  const C<T>* E3 = xd + p.n1 + p.n2;
+  const int N = p.N, nyp = p.ny + 1;
+  const size_t fs = (size_t)p.nx * nyp;
+  const C<T>* Ocs = O + (size_t)(d * 3 + 0) * fs;
+  const C<T>* Osc = O + (size_t)(d * 3 + 1) * fs;
+  const C<T>* Occ = O + (size_t)(d * 3 + 2) * fs;
+  const T pa = (T)(M_PI / p.a), pb = (T)(M_PI / p.b), h = (T)p.h, ab = (T)(p.a * p.b);
+  const T k2 = (T)p.k2x2;
+  C<T> r;
+  if (i < p.n1) {
+    const int m = i / N, n = i - m * N + 1;
+    r = cmul<T>(cadd<T>(mk<T>(-1, 0), top[i]), E1[i]);
+    if (m >= 1) {
+      C<T> cf = cadd<T>(mk<T>(m * pa * h, 0), top[p.nap + i]);
+      r = cadd<T>(r, cmul<T>(cf, E3[(m - 1) * N + (n - 1)]));
+    }
+    const T s = h / (m == 0 ? ab / 2 : ab / 4);
+    C<T> t = csub<T>(cscale<T>(Ocs[(size_t)m * nyp + n], k2),
+                     cscale<T>(Occ[(size_t)m * nyp + n], 2 * n * pb));
+    r = cadd<T>(r, cscale<T>(t, s));
+  } else if (i < p.n1 + p.n2) {
+    const int ii = i - p.n1;
+    const int m = ii / (N + 1) + 1, n = ii - (m - 1) * (N + 1);
+    r = cmul<T>(cadd<T>(mk<T>(-1, 0), top[i]), E2[ii]);
+    if (n >= 1) {
+      C<T> cf = cadd<T>(mk<T>(n * pb * h, 0), top[p.nap + i]);
+      r = cadd<T>(r, cmul<T>(cf, E3[(m - 1) * N + (n - 1)]));
+    }
+    const T s = h / (n == 0 ? ab / 2 : ab / 4);
+    C<T> t = cadd<T>(cscale<T>(Osc[(size_t)m * nyp + n], k2),
+                     cscale<T>(Occ[(size_t)m * nyp + n], 2 * m * pa));
+    r = cadd<T>(r, cscale<T>(t, s));
+  } else {
+    const int ii = i - p.n1 - p.n2;
+    const int m = ii / N + 1, n = ii - (m - 1) * N + 1;
+    r = cscale<T>(E1[m * N + (n - 1)], m * pa * h);
+    r = cadd<T>(r, cscale<T>(E2[(m - 1) * (N + 1) + n], n * pb * h));
+    r = cadd<T>(r, cmul<T>(cadd<T>(mk<T>(-1, 0), top[i]), E3[ii]));
+  }
+  y[(size_t)d * ys + i] = r;
+}
+
+template <typename T> struct Tabs;
+template <> struct Tabs<double> {
+  static const double2* tw(cavity_ctx* c) { return c->tw64; }
+  static const double2* ex(cavity_ctx* c, int k) { return c->ehat_x64[k]; }
+  static const double2* ey(cavity_ctx* c, int k) { return c->ehat_y64[k]; }
+  static const double2* kh(cavity_ctx* c) { return c->khat64; }
+  static const double2* top(cavity_ctx* c) { return c->top64; }
+};
+template <> struct Tabs<float> {
+  static const float2* tw(cavity_ctx* c) { return c->tw32; }
+  static const float2* ex(cavity_ctx* c, int k) { return c->ehat_x32[k]; }
+  static const float2* ey(cavity_ctx* c, int k) { return c->ehat_y32[k]; }
+  static const float2* kh(cavity_ctx* c) { return c->khat32; }
+  static const float2* top(cavity_ctx* c) { return c->top32; }
+};
+
+// shared memory of each pass (bytes) for the grid sizes of g
+template <typename T> static size_t smem_a(int ny) { return sizeof(C<T>) * 2 * pairs_per_cta<T>(4 * ny) * (size_t)padded_len(4 * ny); }
+template <typename T> static size_t smem_b(int nx) { return sizeof(C<T>) * 2 * pairs_per_cta<T>(4 * nx) * (size_t)padded_len(4 * nx); }
+template <typename T> static size_t smem_c(int ny) { return sizeof(C<T>) * lines_per_cta<T>(4 * ny) * (size_t)padded_len(4 * ny); }
+template <typename T> static size_t smem_d(int nx) { return sizeof(C<T>) * lines_per_cta<T>(2 * nx) * (size_t)padded_len(2 * nx); }
+
+// opt every instantiation of kernel K into the device's shared-memory maximum
+// once per process
+template <typename K> static cavity_status smem_once(cavity_ctx* ctx, K kern, bool& done) {
+  if (!done) {
+    CK(allow_max_smem(kern));
+    done = true;
+  }
+  return CAVITY_OK;
+}
+
+template <typename T>
+cavity_status launch_apply(cavity_ctx* ctx, int ndir, const C<T>* x, C<T>* y, void* work,
+                           long long ystride) {
+  if (ystride < 0) ystride = ctx->g.nap;
+  const Geo& g = ctx->g;
+  const size_t need = std::max(std::max(smem_a<T>(g.ny), smem_b<T>(g.nx)),
+                               std::max(smem_c<T>(g.ny), smem_d<T>(g.nx)));
+  if (need > (size_t)smem_optin()) {
+    ctx->err = "grid too large for the shared-memory transforms";
+    return CAVITY_EINVAL;
+  }
+  TbcP p = make_params(ctx);
+  size_t vy = (size_t)ndir * 3 * g.nx * g.Py;
+  size_t z = (size_t)ndir * 3 * (g.nx + 1) * (g.ny + 1);
+  C<T>* R1 = (C<T>*)work;                      // Vy, later Z
+  C<T>* R2 = R1 + std::max(vy, z);             // W, later O
+  cudaStream_t st = ctx->stream;
+  const C<T>* tw = Tabs<T>::tw(ctx);
+  const int T_ = LINES_THREADS;
+  constexpr bool f64 = sizeof(T) == 8;
+  CKS(dispatch_log<CAV_LOG_MIN, CAV_LOG_MAX>(g.lny, [&](auto c) -> cavity_status {
+    constexpr int LN = decltype(c)::value;
+    constexpr int L = pairs_per_cta<T>(4 << LN);
+    static bool done = false;
+    CKS(smem_once(ctx, k_tbcA<T, LN>, done));
+    KScope ks_(ctx, f64 ? KC_TBC_A64 : KC_TBC_A32);
+    k_tbcA<T, LN><<<dim3((g.nx + L - 1) / L, 3, ndir), T_, smem_a<T>(g.ny), st>>>(
+        x, R1, p, tw, Tabs<T>::ey(ctx, 0), Tabs<T>::ey(ctx, 1));
+    return CAVITY_OK;
+  }));
+  CKS(dispatch_log<CAV_LOG_MIN, CAV_LOG_MAX>(g.lnx, [&](auto c) -> cavity_status {
+    constexpr int LN = decltype(c)::value;
+    constexpr int L = pairs_per_cta<T>(4 << LN);
+    static bool done = false;
+    CKS(smem_once(ctx, k_tbcB<T, LN>, done));
+    KScope ks_(ctx, f64 ? KC_TBC_B64 : KC_TBC_B32);
+    k_tbcB<T, LN><<<dim3((g.Py + L - 1) / L, 3, ndir), T_, smem_b<T>(g.nx), st>>>(
+        R1, R2, p, tw, Tabs<T>::ex(ctx, 0), Tabs<T>::ex(ctx, 1), Tabs<T>::kh(ctx));
+    return CAVITY_OK;
+  }));
+  CKS(dispatch_log<CAV_LOG_MIN, CAV_LOG_MAX>(g.lny, [&](auto c) -> cavity_status {
+    constexpr int LN = decltype(c)::value;
+    constexpr int L = lines_per_cta<T>(4 << LN);
+    static bool done = false;
+    CKS(smem_once(ctx, k_tbcC<T, LN>, done));
+    KScope ks_(ctx, f64 ? KC_TBC_C64 : KC_TBC_C32);
+    k_tbcC<T, LN><<<dim3((g.nx + 1 + L - 1) / L, 3, ndir), T_, smem_c<T>(g.ny), st>>>(R2, R1, p, tw);
+    return CAVITY_OK;
+  }));
+  CKS(dispatch_log<CAV_LOG_MIN, CAV_LOG_MAX>(g.lnx, [&](auto c) -> cavity_status {
+    constexpr int LN = decltype(c)::value;
+    constexpr int L = lines_per_cta<T>(2 << LN);
+    static bool done = false;
+    CKS(smem_once(ctx, k_tbcD<T, LN>, done));
+    KScope ks_(ctx, f64 ? KC_TBC_D64 : KC_TBC_D32);
+    k_tbcD<T, LN><<<dim3((g.ny + 1 + L - 1) / L, 3, ndir), T_, smem_d<T>(g.nx), st>>>(R1, R2, p, tw);
+    return CAVITY_OK;
+  }));
+  long long tot = (long long)ndir * g.nap;
+  {
+    KScope ks_(ctx, f64 ? KC_COMB64 : KC_COMB32);
+    k_combine<T><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(x, R2, Tabs<T>::top(ctx), y, ystride,
+                                                                p, ndir);
+  }
+  CK(cudaGetLastError());
+  return CAVITY_OK;
+}
+

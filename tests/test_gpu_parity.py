@@ -134,6 +134,33 @@ def test_operator_matches_fft_rule(gb, case):
     assert rel(y32, ref) < 1e-5
 
 
+# grid sizes covering log2 nx and log2 ny = 2..9: every per-size instantiation
+# of the transform passes (line lengths 8 .. 2048, warp and block transforms)
+SIZES = [(4, 256), (256, 4), (8, 512), (512, 8), (32, 64), (64, 32), (128, 128)]
+
+
+@pytest.mark.parametrize("nx,ny", SIZES)
+def test_operator_and_field_every_size(gb, nx, ny):
+    """a4 operator and a5+a6 field synthesis at every supported line length,
+    FP64 (1e-12) and FP32 (1e-5), against the oracle on random inputs."""
+    w = dict(a=1.0, b=0.8, c=0.3, nx=nx, ny=ny, nz=5, kappa0=9.0,
+             layers=[(2, 3.0 + 0.5j), (3, 1.0 + 0j)])
+    cav = ocav(w)
+    sysm = ApertureSystem(cav)
+    rng = np.random.default_rng(nx * 1000 + ny)
+    x = rng.standard_normal((2, cav.n_ap)) + 1j * rng.standard_normal((2, cav.n_ap))
+    ref = np.array([sysm.apply(v) for v in x])
+    F = np.array([oracle_field(cav, sysm.prof, v).ravel() for v in x])
+    for prec, tol in (("fp64", 1e-12), ("mixed", 1e-5)):
+        g = gcav(gb, w, precision=prec)
+        g.prepare(w['kappa0'], w['layers'])
+        dt = torch.complex128 if prec == "fp64" else torch.complex64
+        y = g.apply(torch.tensor(x, dtype=dt, device="cuda"), prec).cpu().numpy()
+        assert rel(y, ref) < tol, (prec, rel(y, ref))
+        fl = g.field(torch.tensor(x, dtype=torch.complex128, device="cuda")).cpu().numpy()
+        assert rel(fl, F) < tol, (prec, rel(fl, F))
+
+
 @pytest.mark.parametrize("case", list(CASES))
 def test_solve_fp64_matches_dense_oracle(gb, case):
     """Whole path in FP64: aperture coefficients and interior field within 1e-10
