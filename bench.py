@@ -16,6 +16,7 @@ time over ranks is reported.
 """
 
 import argparse
+import math
 import json
 import os
 import subprocess
@@ -31,7 +32,17 @@ sys.path.insert(0, ROOT)
 import workloads  # noqa: E402
 
 WORKLOAD = "dirs16"
-METRIC = "cavity field DOF/s at rel err <=1e-5 vs FP64 oracle"
+METRIC = "cavity field DOF/s at rel err \u22641e-5 vs FP64 oracle; p50/p99 solve latency"
+# Aperture residual target of the timed mixed-precision solve.  Measured on
+# this workload against the FP64 path solved to 1e-12: the field error is at
+# the complex64 synthesis floor (1.6e-7) from tol 1e-8 down, 1.7e-7 at 1e-7,
+# 5.8e-7 at 1e-6 and 1.1e-5 (over the 1e-5 bound) at 1e-5.  1e-7 keeps the
+# error at the floor; every run re-measures it (the "accuracy" entry).
+TOL = 1e-7
+# DRAM traffic of one launch of the FP64 transform pass B (k_tbcB<double, 8>),
+# from `ncu --set full` on 8 directions (105.0 MB read + 67.3 MB written),
+# scaled to the 16 directions of a launch here (traffic is proportional)
+NCU_TRAFFIC = {"tbc_B_fp64": 2 * (105.042688e6 + 67.337472e6)}
 
 
 def peaks():
@@ -101,10 +112,13 @@ def alg_flops_per_launch(cls, w, ndir):
     fft = lambda n: 5.0 * n * lg(n)  # noqa: E731
     lines = 3 * ndir
     if cls.startswith("tbc_B"):
-        per = fft(Px) + 6 * 2 * Px + fft(2 * Px) + 6 * Px + fft(Px)
+        # forward transform, two parity products, two inverse transforms of
+        # length Px, kernel-table products, two of length Px/2, the twiddled
+        # combination of the two parities at the nx + 1 nodes
+        per = fft(Px) + 6 * 2 * Px + 2 * fft(Px) + 6 * Px + 2 * fft(Px // 2) + 8 * (nx + 1)
         return per * Py * lines
     if cls.startswith("tbc_A"):
-        per = fft(Py) + 6 * 2 * Py + fft(2 * Py)
+        per = fft(Py) + 6 * 2 * Py + 2 * fft(Py)
         return per * nx * lines
     if cls.startswith("tbc_C"):
         return (fft(Py) + fft(2 * ny)) * (nx + 1) * lines
@@ -219,7 +233,7 @@ def run_gb300(args, rank, world, local_rank):
     th, ph, al = workloads.directions(16, 2 + rank) if rank else (w['theta'], w['phi'], w['alpha'])
     th, ph, al = th[:args.ndir], ph[:args.ndir], al[:args.ndir]
     ndir = len(th)
-    tol = 1e-10
+    tol = TOL
     cav = gb.Cavity(w['a'], w['b'], w['c'], w['nx'], w['ny'], w['nz'], precision="mixed",
                     gmres_tol=tol)
     torch.cuda.synchronize()
@@ -240,15 +254,17 @@ def run_gb300(args, rank, world, local_rank):
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     with ClockSampler(local_rank) as clk:
-        e0.record(stream)
-        for _ in range(args.steps):
+        ev[0].record(stream)
+        for k in range(args.steps):
             _, _, iters, res = step()
-        e1.record(stream)
+            ev[k + 1].record(stream)
         torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
+    e0, e1 = ev[0], ev[-1]
+    step_ms = sorted(ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps))
     ms = e0.elapsed_time(e1)
     counts = cav.timing_read()
     launches = sum(c for _, c in counts.values())
@@ -283,6 +299,22 @@ def run_gb300(args, rank, world, local_rank):
     h2d = ndir * 6 * 8
     d2h = ndir * cav.n_ap * 16 + ndir * cav.field_per_dir * 8
 
+    # accuracy of the timed result: the same directions through the FP64 path
+    # (FP64 transforms and GMRES to 1e-12, itself matched to the oracle to
+    # 1e-10 by the parity tests), outside the timed region
+    ref = gb.Cavity(w['a'], w['b'], w['c'], w['nx'], w['ny'], w['nz'], precision="fp64",
+                    gmres_tol=1e-12)
+    ap64, fl64, _, res64 = ref.solve(w['kappa0'], w['layers'], th, ph, al, field=True)
+    err_ap = (torch.linalg.vector_norm(ap - ap64, dim=1) /
+              torch.linalg.vector_norm(ap64, dim=1)).max().item()
+    err_fl = max((torch.linalg.vector_norm(fl[d].to(torch.complex128) - fl64[d]) /
+                  torch.linalg.vector_norm(fl64[d])).item() for d in range(ndir))
+    accuracy = {"vs": "FP64 GPU path, GMRES tol 1e-12 (max resid %.1e)" % float(res64.max()),
+                "aperture_rel_err_max": err_ap, "field_rel_err_max": err_fl,
+                "bound": 1e-5, "ok": bool(err_fl <= 1e-5 and err_ap <= 1e-5)}
+    del ref, ap64, fl64
+    torch.cuda.empty_cache()
+
     hbm, hbm_kind, _ = peaks()
     csum = clk.summary()
     # dominant kernel class and its roofline
@@ -295,7 +327,8 @@ def run_gb300(args, rank, world, local_rank):
         ach = flops / per_launch_s / 1e12
         pk, pk_kind = fp_peak_tflops(cls, csum.get("sm_mhz"))
         roof = {"kernel": cls, "bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
-                "frac": ach / pk, "traffic": None, "peak_source": pk_kind,
+                "frac": ach / pk, "traffic": NCU_TRAFFIC.get(cls) if ndir == 16 else None,
+                "peak_source": pk_kind,
                 "launch_ms": cms / ccnt, "algorithmic_flops_per_launch": flops}
     # HBM view of the field path (write of the field; profile read amortised)
     fx_ms, fx_n = kt.get("field_x", (0, 0))
@@ -314,10 +347,15 @@ def run_gb300(args, rank, world, local_rank):
             "config": {"workload": WORKLOAD + ": 256x256x128 grid, a=b=1, c=0.5, eps=1, "
                                    "kappa0=2pi*25.6 (10 points per wavelength), 16 seeded "
                                    "incident directions per GPU, mixed precision, "
-                                   "aperture tol 1e-10",
+                                   "aperture tol %.0e" % tol,
                        "dof_per_step_per_gpu": dof_step,
                        "l2": "working set larger than L2 (3.2 GB field written per step)",
                        "setup": "resident per (kappa0, eps); timed separately"},
+            "latency_ms": {"p50": step_ms[(len(step_ms) - 1) // 2],
+                           "p99": step_ms[min(len(step_ms) - 1,
+                                              int(math.ceil(0.99 * len(step_ms))) - 1)],
+                           "per": "one cavity_solve of the 16-direction batch"},
+            "accuracy": accuracy,
             "setup_ms": setup_ms, "gmres_iters": [int(i) for i in iters],
             "resid": [float(r) for r in res],
             "gpu_launches": int(launches // args.steps) * args.steps,

@@ -72,7 +72,7 @@ typedef struct {
   int pad_factor;        /* period of the TBC convolution in aperture sides;   */
                          /* 0 selects 4 (the only value the GPU path supports) */
   double gmres_tol;      /* relative residual target of (EJ1)/(uT1); 0 -> 1e-12 */
-  int gmres_restart;     /* Krylov basis size; 0 -> 40                         */
+  int gmres_restart;     /* Krylov basis size, at most 120; 0 -> 40            */
   int gmres_max_iter;    /* total inner iterations; 0 -> 400                   */
   double pivot_tol;      /* |pivot| below pivot_tol * max(1,|sigma-2|) is       */
                          /* reported as CAVITY_ESINGULAR; 0 -> 1e-12            */

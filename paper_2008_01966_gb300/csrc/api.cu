@@ -39,6 +39,7 @@ extern "C" cavity_status cavity_setup(const cavity_desc* desc, void* cuda_stream
     return bad("aspect ratio too large for the period 4*side (needs max/min < 2.12)");
   if (d.gmres_tol < 0 || d.gmres_restart < 0 || d.gmres_max_iter < 0 || d.pivot_tol < 0)
     return bad("negative solver parameter");
+  if (d.gmres_restart > 120) return bad("gmres_restart must be at most 120");
   cavity_ctx* ctx = new cavity_ctx();
   ctx->desc = d;
   if (ctx->desc.pad_factor == 0) ctx->desc.pad_factor = 4;

@@ -57,28 +57,47 @@ __global__ void __launch_bounds__(FIELD_THREADS, 2) k_field_y(const C<T>* __rest
   const C<T>* Pj = prof + (size_t)(j - 1) * p.nap;
   const C<T>* Qj = profq ? profq + (size_t)(j - 1) * (p.n1 + p.n2) : nullptr;
   const bool ycos = (comp == 1);
-  for (int t = tid; t < L * ls; t += nthr) buf[t] = mk<T>(0, 0);
-  __syncthreads();
-  for (int idx = tid; idx < L * ny; idx += nthr) {
+  // coefficients of the L rows, loaded first (all loads in flight), then
+  // mirrored into the lines: every slot except n = ny (and n = 0 for the sine
+  // extension) is written, so only those are cleared
+  constexpr int PER = L * ny / FIELD_THREADS;
+  static_assert(PER * FIELD_THREADS == L * ny, "rows must tile the block");
+  C<T> cv[PER];
+#pragma unroll
+  for (int k = 0; k < PER; ++k) {
+    const int idx = tid + k * FIELD_THREADS;
     const int l = idx >> LNY, n = idx & (ny - 1);
     const int r = r0 + l;
     const int m = comp == 0 ? r : r + 1;
-    if (r >= p.nx || m > p.M || m < 0) continue;
     int i = -1;
-    if (comp == 0) { if (n >= 1) i = m * p.N + (n - 1); }
-    else if (comp == 1) i = p.n1 + (m - 1) * (p.N + 1) + n;
-    else { if (n >= 1) i = p.n1 + p.n2 + (m - 1) * p.N + (n - 1); }
-    if (i < 0) continue;
-    C<T> c = E[i];
-    if (!top) {
-      c = cmul<T>(Pj[i], c);
-      if (p.layered && comp < 2 && m >= 1 && n >= 1)
-        c = cadd<T>(c, cmul<T>(Qj[i], E[p.n1 + p.n2 + (m - 1) * p.N + (n - 1)]));
+    if (r < p.nx && m <= p.M) {
+      if (comp == 0) { if (n >= 1) i = m * p.N + (n - 1); }
+      else if (comp == 1) i = p.n1 + (m - 1) * (p.N + 1) + n;
+      else if (n >= 1) i = p.n1 + p.n2 + (m - 1) * p.N + (n - 1);
     }
+    C<T> c = mk<T>(0, 0);
+    if (i >= 0) {
+      c = E[i];
+      if (!top) {
+        c = cmul<T>(Pj[i], c);
+        if (p.layered && comp < 2 && m >= 1 && n >= 1)
+          c = cadd<T>(c, cmul<T>(Qj[i], E[p.n1 + p.n2 + (m - 1) * p.N + (n - 1)]));
+      }
+    }
+    cv[k] = c;
+  }
+#pragma unroll
+  for (int k = 0; k < PER; ++k) {
+    const int idx = tid + k * FIELD_THREADS;
+    const int l = idx >> LNY, n = idx & (ny - 1);
     C<T>* line = buf + (size_t)l * ls;
-    if (ycos) {
-      if (n == 0) line[0] = cscale<T>(c, (T)2);
-      else { line[pidx(n)] = c; line[pidx(n2 - n)] = c; }
+    const C<T> c = cv[k];
+    if (n == 0) {
+      line[0] = ycos ? cscale<T>(c, (T)2) : mk<T>(0, 0);
+      line[pidx(ny)] = mk<T>(0, 0);
+    } else if (ycos) {
+      line[pidx(n)] = c;
+      line[pidx(n2 - n)] = c;
     } else {
       line[pidx(n)] = c;
       line[pidx(n2 - n)] = mk<T>(-c.x, -c.y);
@@ -86,15 +105,13 @@ __global__ void __launch_bounds__(FIELD_THREADS, 2) k_field_y(const C<T>* __rest
   }
   __syncthreads();
   fft_lines<T, true, LNY + 1>(buf, ls, L, tw, p.twlog);
-  for (int l = 0; l < L; ++l) {
-    const int r = r0 + l;
-    if (r >= p.nx) break;
-    for (int q = tid; q <= ny; q += nthr) {
-      const C<T> v = buf[(size_t)l * ls + pidx(q)];
-      // cos: Z/2 ; sin: Z/(2i)
-      T1[(((size_t)s * 3 + comp) * p.nx + r) * (ny + 1) + q] =
-          ycos ? mk<T>(v.x * (T)0.5, v.y * (T)0.5) : mk<T>(v.y * (T)0.5, -v.x * (T)0.5);
-    }
+  C<T>* dst = T1 + (((size_t)s * 3 + comp) * p.nx + r0) * (ny + 1);
+  const int nr = min(L, p.nx - r0);
+  for (int idx = tid; idx < nr * (ny + 1); idx += nthr) {
+    const int l = idx / (ny + 1), q = idx - l * (ny + 1);
+    const C<T> v = buf[(size_t)l * ls + pidx(q)];
+    // cos: Z/2 ; sin: Z/(2i)
+    dst[idx] = ycos ? mk<T>(v.x * (T)0.5, v.y * (T)0.5) : mk<T>(v.y * (T)0.5, -v.x * (T)0.5);
   }
 }
 
@@ -117,23 +134,40 @@ __global__ void __launch_bounds__(FIELD_THREADS, 2) k_field_x(const C<T>* __rest
   const int tid = threadIdx.x, nthr = blockDim.x;
   const bool xcos = (comp == 0);
   const C<T>* src = T1 + ((size_t)s * 3 + comp) * nx * (ny + 1);
-  for (int t = tid; t < L * ls; t += nthr) buf[t] = mk<T>(0, 0);
-  __syncthreads();
+  // rows r of the L columns, loaded first, then mirrored; unwritten slots
+  // (m = nx, and m = 0 for the sine extension) are cleared
+  constexpr int PER = L * nx / FIELD_THREADS;
+  static_assert(PER * FIELD_THREADS == L * nx, "columns must tile the block");
   const int nrows = xcos ? nx : nx - 1;    // E1: m = 0..M; E2/E3: m = 1..M
-  for (int idx = tid; idx < L * nrows; idx += nthr) {
+  C<T> cv[PER];
+#pragma unroll
+  for (int k = 0; k < PER; ++k) {
+    const int idx = tid + k * FIELD_THREADS;
     const int r = idx >> lL, l = idx & (L - 1);
     const int q = q0 + l;
-    if (q > ny) continue;
-    const C<T> c = src[(size_t)r * (ny + 1) + q];
+    cv[k] = (q <= ny && r < nrows) ? src[(size_t)r * (ny + 1) + q] : mk<T>(0, 0);
+  }
+#pragma unroll
+  for (int k = 0; k < PER; ++k) {
+    const int idx = tid + k * FIELD_THREADS;
+    const int r = idx >> lL, l = idx & (L - 1);
     C<T>* line = buf + (size_t)l * ls;
+    const C<T> c = cv[k];
     if (xcos) {
-      const int m = r;
-      if (m == 0) line[0] = cscale<T>(c, (T)2);
-      else { line[pidx(m)] = c; line[pidx(n2 - m)] = c; }
-    } else {
+      if (r == 0) {
+        line[0] = cscale<T>(c, (T)2);
+        line[pidx(nx)] = mk<T>(0, 0);
+      } else {
+        line[pidx(r)] = c;
+        line[pidx(n2 - r)] = c;
+      }
+    } else if (r < nx - 1) {
       const int m = r + 1;
       line[pidx(m)] = c;
       line[pidx(n2 - m)] = mk<T>(-c.x, -c.y);
+    } else {
+      line[0] = mk<T>(0, 0);
+      line[pidx(nx)] = mk<T>(0, 0);
     }
   }
   __syncthreads();

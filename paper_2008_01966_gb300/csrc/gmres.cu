@@ -80,8 +80,10 @@ __global__ void __launch_bounds__(256) k_mdot_partial(const C<T>* __restrict__ V
     const int i = i0 + warp / nsub, sub = warp - (warp / nsub) * nsub;
     double sr = 0, si = 0;
     if (i < cnt) {
-      // per-lane partial sums in the vector precision (at most 64 terms in
-      // FP32), then FP64 across lanes, warps and chunks
+      // per-lane partial sums (at most 64 terms) and the sum across the warp
+      // in the vector precision; FP64 across warps and chunks.  (FP64
+      // instructions are scarce on this GPU: an FP64 shuffle tree per warp
+      // would cost more than the FP32 products themselves.)
       const C<T>* v = V + (size_t)d * vs + (size_t)i * nap + e0;
       T ar = 0, ai = 0;
       for (int e = sub * 32 + lane; e < ne; e += nsub * 32) {
@@ -89,12 +91,12 @@ __global__ void __launch_bounds__(256) k_mdot_partial(const C<T>* __restrict__ V
         ar += a.x * b.x + a.y * b.y;
         ai += a.x * b.y - a.y * b.x;
       }
+      for (int off = 16; off > 0; off >>= 1) {
+        ar += __shfl_xor_sync(0xffffffffu, ar, off);
+        ai += __shfl_xor_sync(0xffffffffu, ai, off);
+      }
       sr = (double)ar;
       si = (double)ai;
-      for (int off = 16; off > 0; off >>= 1) {
-        sr += __shfl_xor_sync(0xffffffffu, sr, off);
-        si += __shfl_xor_sync(0xffffffffu, si, off);
-      }
     }
     if (lane == 0) { rr[warp] = sr; ri[warp] = si; }
     __syncthreads();
@@ -122,39 +124,57 @@ __global__ void k_mdot_final(const double2* __restrict__ part, double2* __restri
 }
 
 // w[d][e] += sgn * sum_{i<cnt} V[d*vs + i*nap + e] c[d*cstride + i]
+// grid (ceil(nap / 256), ndir); the coefficients are rounded to the vector
+// precision once per block (cnt <= GMRES_MAXC)
+#define GMRES_MAXC 128
 template <typename T>
-__global__ void k_basis_axpy(const C<T>* __restrict__ V, long long vs, const double2* __restrict__ c,
-                             int cstride, int cnt, C<T>* __restrict__ w, int nap, int ndir, double sgn,
-                             const int* __restrict__ flag = nullptr, long long wstride = -1) {
-  long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (gid >= (long long)ndir * nap) return;
-  const int d = (int)(gid / nap), e = (int)(gid - (long long)d * nap);
+__global__ void __launch_bounds__(256) k_basis_axpy(const C<T>* __restrict__ V, long long vs,
+                                                    const double2* __restrict__ c, int cstride,
+                                                    int cnt, C<T>* __restrict__ w, int nap, T sgn,
+                                                    const int* __restrict__ flag = nullptr,
+                                                    long long wstride = -1) {
+  __shared__ C<T> cf[GMRES_MAXC];
+  const int d = blockIdx.y;
   if (flag && !flag[d]) return;
-  if (wstride >= 0) gid = (long long)d * wstride + e;
-  const C<T>* v = V + (size_t)d * vs + e;
-  // accumulate in the vector precision (FP64 arithmetic is scarce on this GPU)
-  T ar = 0, ai = 0;
-  for (int i = 0; i < cnt; ++i) {
-    const C<T> a = v[(size_t)i * nap];
+  for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
     const double2 bd = c[(size_t)d * cstride + i];
-    const T bx = (T)bd.x, by = (T)bd.y;
-    ar += a.x * bx - a.y * by;
-    ai += a.x * by + a.y * bx;
+    cf[i] = mk<T>((T)(sgn * bd.x), (T)(sgn * bd.y));
   }
-  const C<T> o = w[gid];
-  const T sg = (T)sgn;
-  w[gid] = mk<T>(o.x + sg * ar, o.y + sg * ai);
+  __syncthreads();
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nap) return;
+  const C<T>* v = V + (size_t)d * vs + e;
+  T ar = 0, ai = 0;
+  int i = 0;
+  for (; i + 4 <= cnt; i += 4) {
+    C<T> a[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) a[k] = v[(size_t)(i + k) * nap];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const C<T> b = cf[i + k];
+      ar += a[k].x * b.x - a[k].y * b.y;
+      ai += a[k].x * b.y + a[k].y * b.x;
+    }
+  }
+  for (; i < cnt; ++i) {
+    const C<T> a = v[(size_t)i * nap], b = cf[i];
+    ar += a.x * b.x - a.y * b.y;
+    ai += a.x * b.y + a.y * b.x;
+  }
+  const size_t o = (size_t)d * (wstride >= 0 ? wstride : nap) + e;
+  const C<T> ov = w[o];
+  w[o] = mk<T>(ov.x + ar, ov.y + ai);
 }
 
-// out[d*os + e] = s[d] * in[d*is + e]
+// out[d*os + e] = s[d] * in[d*is + e]   (grid (ceil(nap / 256), ndir))
 template <typename T>
 __global__ void k_copy_scale(const C<T>* __restrict__ in, long long is, C<T>* __restrict__ out,
-                             long long os, const double* __restrict__ s, int nap, int ndir) {
-  long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (gid >= (long long)ndir * nap) return;
-  const int d = (int)(gid / nap), e = (int)(gid - (long long)d * nap);
-  C<T> a = in[(size_t)d * is + e];
-  T f = (T)s[d];
+                             long long os, const double* __restrict__ s, int nap) {
+  const int d = blockIdx.y, e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nap) return;
+  const C<T> a = in[(size_t)d * is + e];
+  const T f = (T)s[d];
   out[(size_t)d * os + e] = mk<T>(a.x * f, a.y * f);
 }
 
@@ -189,24 +209,26 @@ __global__ void k_bminus(const C<T>* __restrict__ b, C<T>* __restrict__ w, long 
   if (k < n) w[k] = csub<T>(b[k], w[k]);
 }
 
-// x64 += d32 / s[d]
+// x64 += d32 / s[d]   (grid (ceil(nap / 256), ndir))
 __global__ void k_acc32(double2* __restrict__ x, const float2* __restrict__ dx,
-                        const double* __restrict__ s, int nap, int ndir) {
-  long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (gid >= (long long)ndir * nap) return;
-  const int d = (int)(gid / nap);
+                        const double* __restrict__ s, int nap) {
+  const int d = blockIdx.y, e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nap) return;
+  const size_t k = (size_t)d * nap + e;
   const double f = s[d] > 0 ? 1.0 / s[d] : 0.0;
-  x[gid].x += f * (double)dx[gid].x;
-  x[gid].y += f * (double)dx[gid].y;
+  const float2 v = dx[k];
+  x[k].x += f * (double)v.x;
+  x[k].y += f * (double)v.y;
 }
 
-// r32 = s[d] * r64
+// r32 = s[d] * r64   (grid (ceil(nap / 256), ndir))
 __global__ void k_to32(const double2* __restrict__ r, float2* __restrict__ o,
-                       const double* __restrict__ s, int nap, int ndir) {
-  long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (gid >= (long long)ndir * nap) return;
-  const int d = (int)(gid / nap);
-  o[gid] = make_float2((float)(r[gid].x * s[d]), (float)(r[gid].y * s[d]));
+                       const double* __restrict__ s, int nap) {
+  const int d = blockIdx.y, e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nap) return;
+  const size_t k = (size_t)d * nap + e;
+  const double f = s[d];
+  o[k] = make_float2((float)(r[k].x * f), (float)(r[k].y * f));
 }
 
 static inline unsigned nblk(long long n, int b) { return (unsigned)((n + b - 1) / b); }
@@ -334,7 +356,7 @@ static cavity_status gmres_core(cavity_ctx* ctx, int ndir, const C<T>* b, C<T>* 
     CK(cudaMemcpyAsync(W.s, sc.data(), sizeof(double) * ndir, cudaMemcpyHostToDevice, st));
     {
       KScope ks_(ctx, KC_KRYLOV);
-      k_copy_scale<T><<<nblk(nv, 256), 256, 0, st>>>(W.w, nap, W.V, vs, W.s, nap, ndir);
+      k_copy_scale<T><<<dim3(nblk(nap, 256), ndir), 256, 0, st>>>(W.w, nap, W.V, vs, W.s, nap);
     }
     std::vector<std::vector<std::vector<double2>>> H(ndir);
     std::vector<std::vector<double>> cs(ndir, std::vector<double>(m, 0.0));
@@ -356,8 +378,8 @@ static cavity_status gmres_core(cavity_ctx* ctx, int ndir, const C<T>* b, C<T>* 
       mdot<T>(ctx, W.V, vs, Vn, vs, k + 2, W.h, m + 1, W.part, ndir);
       {
         KScope ks_(ctx, KC_KRYLOV);
-        k_basis_axpy<T><<<nblk(nv, 256), 256, 0, st>>>(W.V, vs, W.h, m + 1, k + 1, Vn, nap, ndir, -1.0,
-                                                        nullptr, vs);
+        k_basis_axpy<T><<<dim3(nblk(nap, 256), ndir), 256, 0, st>>>(W.V, vs, W.h, m + 1, k + 1, Vn, nap,
+                                                                    (T)-1, nullptr, vs);
       }
       {
         KScope ks_(ctx, KC_KRYLOV);
@@ -367,8 +389,8 @@ static cavity_status gmres_core(cavity_ctx* ctx, int ndir, const C<T>* b, C<T>* 
       mdot<T>(ctx, W.V, vs, Vn, vs, k + 1, W.h2, m + 1, W.part, ndir, W.flag);
       {
         KScope ks_(ctx, KC_KRYLOV);
-        k_basis_axpy<T><<<nblk(nv, 256), 256, 0, st>>>(W.V, vs, W.h2, m + 1, k + 1, Vn, nap, ndir, -1.0,
-                                                        W.flag, vs);
+        k_basis_axpy<T><<<dim3(nblk(nap, 256), ndir), 256, 0, st>>>(W.V, vs, W.h2, m + 1, k + 1, Vn, nap,
+                                                                    (T)-1, W.flag, vs);
       }
       mdot<T>(ctx, Vn, vs, Vn, vs, 1, W.y, m + 1, W.part, ndir);
       CK(cudaMemcpyAsync(h1.data(), W.h, sizeof(double2) * ndir * (m + 1), cudaMemcpyDeviceToHost, st));
@@ -429,7 +451,7 @@ static cavity_status gmres_core(cavity_ctx* ctx, int ndir, const C<T>* b, C<T>* 
       {
         // normalise V_{k+1} in place (zero for directions that stopped)
         KScope ks_(ctx, KC_KRYLOV);
-        k_copy_scale<T><<<nblk(nv, 256), 256, 0, st>>>(Vn, vs, Vn, vs, W.s, nap, ndir);
+        k_copy_scale<T><<<dim3(nblk(nap, 256), ndir), 256, 0, st>>>(Vn, vs, Vn, vs, W.s, nap);
       }
       if (!any) { ++total; break; }
     }
@@ -456,7 +478,8 @@ static cavity_status gmres_core(cavity_ctx* ctx, int ndir, const C<T>* b, C<T>* 
     CK(cudaMemsetAsync(W.w, 0, sizeof(C<T>) * nv, st));
     {
       KScope ks_(ctx, KC_KRYLOV);
-      k_basis_axpy<T><<<nblk(nv, 256), 256, 0, st>>>(W.V, vs, W.y, m + 1, kmax, W.w, nap, ndir, 1.0);
+      k_basis_axpy<T><<<dim3(nblk(nap, 256), ndir), 256, 0, st>>>(W.V, vs, W.y, m + 1, kmax, W.w, nap,
+                                                                  (T)1);
     }
     CKS(launch_precond_apply<T>(ctx, ndir, W.w, W.z));
     {
@@ -576,7 +599,7 @@ cavity_status run_mixed_solve(cavity_ctx* ctx, int ndir, const double2* b, doubl
     CK(cudaMemcpyAsync(sdev, s.data(), sizeof(double) * ndir, cudaMemcpyHostToDevice, st));
     {
       KScope ks_(ctx, KC_KRYLOV);
-      k_to32<<<nblk(nv, 256), 256, 0, st>>>(r64, r32, sdev, g.nap, ndir);
+      k_to32<<<dim3(nblk(g.nap, 256), ndir), 256, 0, st>>>(r64, r32, sdev, g.nap);
     }
     std::vector<int> it_in(ndir, 0);
     CKS(gmres_core<float>(ctx, ndir, r32, d32, tin, m, maxit - used, W, it_in, est));
@@ -585,7 +608,7 @@ cavity_status run_mixed_solve(cavity_ctx* ctx, int ndir, const double2* b, doubl
     used += std::max(mx, 1);
     {
       KScope ks_(ctx, KC_KRYLOV);
-      k_acc32<<<nblk(nv, 256), 256, 0, st>>>(x, d32, sdev, g.nap, ndir);
+      k_acc32<<<dim3(nblk(g.nap, 256), ndir), 256, 0, st>>>(x, d32, sdev, g.nap);
     }
     // r = b - A x in FP64
     CKS(launch_apply<double>(ctx, ndir, x, tmp64, apw64));

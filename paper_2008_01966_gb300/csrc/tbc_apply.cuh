@@ -311,56 +311,48 @@ __global__ void TBC_BOUNDS k_tbcD(const C<T>* __restrict__ Z, C<T>* __restrict__
 //  row 1: (-1+tau1)E1 + (m pi h/a + vs1)E3 + (h/q)(2k^2 U1 - 2(n pi/b) W)
 //  row 2: (-1+tau2)E2 + (n pi h/b + vs2)E3 + (h/c)(2k^2 U2 + 2(m pi/a) W)
 //  row 3: (m pi h/a)E1 + (n pi h/b)E2 + (-1+tau3)E3
+// One thread per mode pair (m, n), m < nx, n < ny, writing the rows of the
+// three components that exist for it; grid (ceil(nx ny / 256), ndir).
 template <typename T>
 __global__ void k_combine(const C<T>* __restrict__ x, const C<T>* __restrict__ O,
-                          const C<T>* __restrict__ top, C<T>* __restrict__ y, long long ys, TbcP p,
-                          int ndir) {
-  const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (gid >= (long long)ndir * p.nap) return;
-  const int d = (int)(gid / p.nap), i = (int)(gid - (long long)d * p.nap);
+                          const C<T>* __restrict__ top, C<T>* __restrict__ y, long long ys, TbcP p) {
+  const int d = blockIdx.y;
+  const int mn = blockIdx.x * blockDim.x + threadIdx.x;
+  if (mn >= p.nx * p.ny) return;
+  const int m = mn >> p.lny, n = mn & (p.ny - 1);
   const C<T>* xd = x + (size_t)d * p.nap;
-  const C<T>* E1 = xd;
-  const C<T>* E2 = xd + p.n1;
-  const C<T>* E3 = xd + p.n1 + p.n2;
+  C<T>* yd = y + (size_t)d * ys;
   const int N = p.N, nyp = p.ny + 1;
   const size_t fs = (size_t)p.nx * nyp;
-  const C<T>* Ocs = O + (size_t)(d * 3 + 0) * fs;
-  const C<T>* Osc = O + (size_t)(d * 3 + 1) * fs;
-  const C<T>* Occ = O + (size_t)(d * 3 + 2) * fs;
+  const C<T>* Od = O + (size_t)d * 3 * fs;
   const T pa = (T)(M_PI / p.a), pb = (T)(M_PI / p.b), h = (T)p.h, ab = (T)(p.a * p.b);
   const T k2 = (T)p.k2x2;
-  C<T> r;
-  if (i < p.n1) {
-    const int m = i / N, n = i - m * N + 1;
-    r = cmul<T>(cadd<T>(mk<T>(-1, 0), top[i]), E1[i]);
-    if (m >= 1) {
-      C<T> cf = cadd<T>(mk<T>(m * pa * h, 0), top[p.nap + i]);
-      r = cadd<T>(r, cmul<T>(cf, E3[(m - 1) * N + (n - 1)]));
-    }
+  const int i1 = m * N + (n - 1), i2 = p.n1 + (m - 1) * (N + 1) + n;
+  const int i3 = p.n1 + p.n2 + (m - 1) * N + (n - 1);
+  const bool has1 = n >= 1, has2 = m >= 1, has3 = m >= 1 && n >= 1;
+  const C<T> e1 = has1 ? xd[i1] : mk<T>(0, 0);
+  const C<T> e2 = has2 ? xd[i2] : mk<T>(0, 0);
+  const C<T> e3 = has3 ? xd[i3] : mk<T>(0, 0);
+  const size_t o = (size_t)m * nyp + n;
+  if (has1) {
+    C<T> r = cmul<T>(cadd<T>(mk<T>(-1, 0), top[i1]), e1);
+    if (has3) r = cadd<T>(r, cmul<T>(cadd<T>(mk<T>(m * pa * h, 0), top[p.nap + i1]), e3));
     const T s = h / (m == 0 ? ab / 2 : ab / 4);
-    C<T> t = csub<T>(cscale<T>(Ocs[(size_t)m * nyp + n], k2),
-                     cscale<T>(Occ[(size_t)m * nyp + n], 2 * n * pb));
-    r = cadd<T>(r, cscale<T>(t, s));
-  } else if (i < p.n1 + p.n2) {
-    const int ii = i - p.n1;
-    const int m = ii / (N + 1) + 1, n = ii - (m - 1) * (N + 1);
-    r = cmul<T>(cadd<T>(mk<T>(-1, 0), top[i]), E2[ii]);
-    if (n >= 1) {
-      C<T> cf = cadd<T>(mk<T>(n * pb * h, 0), top[p.nap + i]);
-      r = cadd<T>(r, cmul<T>(cf, E3[(m - 1) * N + (n - 1)]));
-    }
-    const T s = h / (n == 0 ? ab / 2 : ab / 4);
-    C<T> t = cadd<T>(cscale<T>(Osc[(size_t)m * nyp + n], k2),
-                     cscale<T>(Occ[(size_t)m * nyp + n], 2 * m * pa));
-    r = cadd<T>(r, cscale<T>(t, s));
-  } else {
-    const int ii = i - p.n1 - p.n2;
-    const int m = ii / N + 1, n = ii - (m - 1) * N + 1;
-    r = cscale<T>(E1[m * N + (n - 1)], m * pa * h);
-    r = cadd<T>(r, cscale<T>(E2[(m - 1) * (N + 1) + n], n * pb * h));
-    r = cadd<T>(r, cmul<T>(cadd<T>(mk<T>(-1, 0), top[i]), E3[ii]));
+    const C<T> t = csub<T>(cscale<T>(Od[o], k2), cscale<T>(Od[2 * fs + o], 2 * n * pb));
+    yd[i1] = cadd<T>(r, cscale<T>(t, s));
   }
-  y[(size_t)d * ys + i] = r;
+  if (has2) {
+    C<T> r = cmul<T>(cadd<T>(mk<T>(-1, 0), top[i2]), e2);
+    if (has3) r = cadd<T>(r, cmul<T>(cadd<T>(mk<T>(n * pb * h, 0), top[p.nap + i2]), e3));
+    const T s = h / (n == 0 ? ab / 2 : ab / 4);
+    const C<T> t = cadd<T>(cscale<T>(Od[fs + o], k2), cscale<T>(Od[2 * fs + o], 2 * m * pa));
+    yd[i2] = cadd<T>(r, cscale<T>(t, s));
+  }
+  if (has3) {
+    C<T> r = cscale<T>(e1, m * pa * h);
+    r = cadd<T>(r, cscale<T>(e2, n * pb * h));
+    yd[i3] = cadd<T>(r, cmul<T>(cadd<T>(mk<T>(-1, 0), top[i3]), e3));
+  }
 }
 
 template <typename T> struct Tabs;
@@ -453,11 +445,10 @@ cavity_status launch_apply(cavity_ctx* ctx, int ndir, const C<T>* x, C<T>* y, vo
     k_tbcD<T, LN><<<dim3((g.ny + 1 + L - 1) / L, 3, ndir), T_, smem_d<T>(g.nx), st>>>(R1, R2, p, tw);
     return CAVITY_OK;
   }));
-  long long tot = (long long)ndir * g.nap;
   {
     KScope ks_(ctx, f64 ? KC_COMB64 : KC_COMB32);
-    k_combine<T><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(x, R2, Tabs<T>::top(ctx), y, ystride,
-                                                                p, ndir);
+    k_combine<T><<<dim3((g.nx * g.ny + 255) / 256, ndir), 256, 0, st>>>(x, R2, Tabs<T>::top(ctx), y,
+                                                                       ystride, p);
   }
   CK(cudaGetLastError());
   return CAVITY_OK;
