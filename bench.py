@@ -217,6 +217,29 @@ def run_reference(args, rank, world):
     return 0
 
 
+def rank_directions(w, rank, ndir):
+    """Incident directions of one rank: rank 0 takes the workload's own
+    seeded batch, rank r > 0 an independent batch seeded 2 + r (weak scaling:
+    every rank solves its own 16 directions, no data exchange)."""
+    th, ph, al = workloads.directions(16, 2 + rank) if rank else (w['theta'], w['phi'], w['alpha'])
+    return th[:ndir], ph[:ndir], al[:ndir]
+
+
+def max_over_ranks(ms, world, device):
+    """The job's time: the slowest rank's (identity for one rank)."""
+    if world == 1:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(dof_per_rank_step, steps, world, ms):
+    """Whole-job DOF/s: every rank's DOF of every timed step over the job time."""
+    return dof_per_rank_step * steps * world / (ms / 1e3)
+
+
 def run_gb300(args, rank, world, local_rank):
     import torch
     import __graft_entry__
@@ -229,9 +252,7 @@ def run_gb300(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     w = workloads.workload(WORKLOAD)
-    # each rank: its own batch of 16 directions (seeded by rank)
-    th, ph, al = workloads.directions(16, 2 + rank) if rank else (w['theta'], w['phi'], w['alpha'])
-    th, ph, al = th[:args.ndir], ph[:args.ndir], al[:args.ndir]
+    th, ph, al = rank_directions(w, rank, args.ndir)
     ndir = len(th)
     tol = TOL
     cav = gb.Cavity(w['a'], w['b'], w['c'], w['nx'], w['ny'], w['nz'], precision="mixed",
@@ -268,12 +289,9 @@ def run_gb300(args, rank, world, local_rank):
     ms = e0.elapsed_time(e1)
     counts = cav.timing_read()
     launches = sum(c for _, c in counts.values())
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world, dev)
     dof_step = w['nz'] * cav.n_ap * ndir
-    value = dof_step * args.steps * world / (ms / 1e3)
+    value = job_value(dof_step, args.steps, world, ms)
 
     # instrumented pass: per-kernel-class event times (separate from `value`)
     cav.timing(True)
@@ -289,13 +307,15 @@ def run_gb300(args, rank, world, local_rank):
     cav.solve(w['kappa0'], w['layers'], th, ph, al, field=True, host=True, aperture_out=aph,
               field_out=flh)
     torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
     t0 = time.perf_counter()
     for _ in range(args.steps):
         cav.solve(w['kappa0'], w['layers'], th, ph, al, field=True, host=True, aperture_out=aph,
                   field_out=flh)
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    e2e = dof_step * args.steps * world / e2e_s
+    e2e_ms = max_over_ranks(1e3 * (time.perf_counter() - t0), world, dev)
+    e2e = job_value(dof_step, args.steps, world, e2e_ms)
     h2d = ndir * 6 * 8
     d2h = ndir * cav.n_ap * 16 + ndir * cav.field_per_dir * 8
 
