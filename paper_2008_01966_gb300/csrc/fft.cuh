@@ -179,6 +179,15 @@ __device__ __forceinline__ void dft_nat(C<T>* v) {
   }
 }
 
+// Line access of the first read and the last write of a transform.  The
+// default reads and writes the line in place; kernels pass their own to fuse
+// a gather into the first read or a product / scatter into the last write.
+// ld(l, line, n): input n of line l;  st(l, line, k, v): output k of line l.
+template <typename T> struct LineId {
+  __device__ __forceinline__ C<T> ld(int, const C<T>* line, int n) const { return line[pidx(n)]; }
+  __device__ __forceinline__ void st(int, C<T>* line, int k, C<T> v) const { line[pidx(k)] = v; }
+};
+
 template <typename T, bool INV>
 __device__ __forceinline__ C<T> twid(const C<T>* __restrict__ tw, int idx) {
   C<T> w = tw[idx];
@@ -187,9 +196,11 @@ __device__ __forceinline__ C<T> twid(const C<T>* __restrict__ tw, int idx) {
 }
 
 // radix-R pass (R = 2^LR), PER butterflies per thread (PER * R = E, or 1 for n < E)
-template <typename T, bool INV, int LR, int PER>
+template <typename T, bool INV, int LR, int PER, bool FIRST = false, bool LAST = false,
+          typename Op = LineId<T>>
 __device__ __forceinline__ void fft_pass(C<T>* line, int n, int s, int t, int tpl,
-                                         const C<T>* __restrict__ tw, int twlog, bool active) {
+                                         const C<T>* __restrict__ tw, int twlog, bool active,
+                                         int lidx = 0, const Op& op = Op()) {
   constexpr int R = 1 << LR;
   const int Ns = 1 << s;
   const int nb = n >> LR;
@@ -200,7 +211,8 @@ __device__ __forceinline__ void fft_pass(C<T>* line, int n, int s, int t, int tp
       const int j = t + q * tpl;
       const int k = j & (Ns - 1);
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[q * R + r] = line[pidx(j + r * nb)];
+      for (int r = 0; r < R; ++r)
+        v[q * R + r] = FIRST ? op.ld(lidx, line, j + r * nb) : line[pidx(j + r * nb)];
       if (s > 0) {
         const int shift = twlog - (s + LR);
         if constexpr (sizeof(T) == 4) {
@@ -232,13 +244,19 @@ __device__ __forceinline__ void fft_pass(C<T>* line, int n, int s, int t, int tp
       if constexpr (LR == 4) {
         dft16<T, INV>(w);
 #pragma unroll
-        for (int r = 0; r < R; ++r) line[pidx(base + r * Ns)] = w[dft16_slot(r)];
+        for (int r = 0; r < R; ++r) {
+          if constexpr (LAST) op.st(lidx, line, base + r * Ns, w[dft16_slot(r)]);
+          else line[pidx(base + r * Ns)] = w[dft16_slot(r)];
+        }
       } else {
         if constexpr (LR == 3) dft8<T, INV>(w);
         else if constexpr (LR == 2) dft4<T, INV>(w);
         else dft2<T, INV>(w);
 #pragma unroll
-        for (int r = 0; r < R; ++r) line[pidx(base + r * Ns)] = w[r];
+        for (int r = 0; r < R; ++r) {
+          if constexpr (LAST) op.st(lidx, line, base + r * Ns, w[r]);
+          else line[pidx(base + r * Ns)] = w[r];
+        }
       }
     }
   }
@@ -251,13 +269,14 @@ __device__ __forceinline__ void fft_pass(C<T>* line, int n, int s, int t, int tp
 //   line's own shared memory;  lane l then owns k1 = l + LW q and forms the
 //   LW-point DFT over the lanes:  X[k1 + RV k2].
 // One shared-memory round trip and warp-level synchronisation only.
-template <typename T, bool INV, int LW, int RV>
+template <typename T, bool INV, int LW, int RV, typename Op = LineId<T>>
 __device__ __forceinline__ void fft_warp(C<T>* line, int n, int logn, int l, bool active,
-                                         const C<T>* __restrict__ tw, int twlog) {
+                                         const C<T>* __restrict__ tw, int twlog, int lidx = 0,
+                                         const Op& op = Op()) {
   C<T> v[RV];
   if (active) {
 #pragma unroll
-    for (int r = 0; r < RV; ++r) v[r] = line[pidx(l + LW * r)];
+    for (int r = 0; r < RV; ++r) v[r] = op.ld(lidx, line, l + LW * r);
   }
   __syncwarp();
   if (active) {
@@ -283,7 +302,7 @@ __device__ __forceinline__ void fft_warp(C<T>* line, int n, int logn, int l, boo
       dft_nat<T, INV, LW>(v + q * LW);
       const int k1 = l + LW * q;
 #pragma unroll
-      for (int k2 = 0; k2 < LW; ++k2) line[pidx(k1 + RV * k2)] = v[q * LW + k2];
+      for (int k2 = 0; k2 < LW; ++k2) op.st(lidx, line, k1 + RV * k2, v[q * LW + k2]);
     }
   }
   __syncwarp();
@@ -342,14 +361,16 @@ template <int LOGN> struct BlockRadix<LOGN, 0> {
   static constexpr int S = 0;
 };
 
-template <typename T, bool INV, int LOGN, int P>
+template <typename T, bool INV, int LOGN, int P, typename Op>
 __device__ __forceinline__ void block_passes(C<T>* line, int t, int tpl, const C<T>* __restrict__ tw,
-                                             int twlog, bool active) {
-  if constexpr (P < BlockRadix<LOGN, 0>::K) {
+                                             int twlog, bool active, int lidx, const Op& op) {
+  constexpr int K = BlockRadix<LOGN, 0>::K;
+  if constexpr (P < K) {
     constexpr int LR = BlockRadix<LOGN, P>::LR;
     constexpr int PER = 8 >> LR;
-    fft_pass<T, INV, LR, PER>(line, 1 << LOGN, BlockRadix<LOGN, P>::S, t, tpl, tw, twlog, active);
-    block_passes<T, INV, LOGN, P + 1>(line, t, tpl, tw, twlog, active);
+    fft_pass<T, INV, LR, PER, P == 0, P == K - 1, Op>(line, 1 << LOGN, BlockRadix<LOGN, P>::S, t,
+                                                      tpl, tw, twlog, active, lidx, op);
+    block_passes<T, INV, LOGN, P + 1, Op>(line, t, tpl, tw, twlog, active, lidx, op);
   }
 }
 
@@ -364,9 +385,10 @@ template <typename T, int LOGN> struct LineShape {
 // In-place FFT of `nlines` padded lines (stride lstride) of the compile-time
 // length 2^LOGN: the warp transform where it applies, else the block
 // transform.  Called by all threads of the CTA; ends with a CTA barrier.
-template <typename T, bool INV, int LOGN>
+template <typename T, bool INV, int LOGN, typename Op = LineId<T>>
 __device__ __forceinline__ void fft_lines(C<T>* base, int lstride, int nlines,
-                                          const C<T>* __restrict__ tw, int twlog) {
+                                          const C<T>* __restrict__ tw, int twlog,
+                                          const Op& op = Op()) {
   using S = LineShape<T, LOGN>;
   constexpr int n = 1 << LOGN, tpl = S::TPL;
   const int tid = threadIdx.x + threadIdx.y * blockDim.x;
@@ -378,11 +400,12 @@ __device__ __forceinline__ void fft_lines(C<T>* base, int lstride, int nlines,
     const bool active = lg < lpg && l < nlines;
     C<T>* line = base + (size_t)(active ? l : 0) * lstride;
     if constexpr (S::WARP) {
-      fft_warp<T, INV, S::LW, S::RV>(line, n, LOGN, t, active, tw, twlog);
+      fft_warp<T, INV, S::LW, S::RV, Op>(line, n, LOGN, t, active, tw, twlog, l, op);
     } else if constexpr (LOGN <= 3) {
-      if constexpr (LOGN >= 1) fft_pass<T, INV, LOGN, 1>(line, n, 0, t, tpl, tw, twlog, active);
+      if constexpr (LOGN >= 1)
+        fft_pass<T, INV, LOGN, 1, true, true, Op>(line, n, 0, t, tpl, tw, twlog, active, l, op);
     } else {
-      block_passes<T, INV, LOGN, 0>(line, t, tpl, tw, twlog, active);
+      block_passes<T, INV, LOGN, 0, Op>(line, t, tpl, tw, twlog, active, l, op);
     }
   }
   __syncthreads();

@@ -35,7 +35,60 @@ template <typename T> __host__ __device__ constexpr int field_lines(int n) {
 }
 
 // pass 1: grid (ceil(nx / L) row groups, 3 components, ndir * lc slabs);
-// instantiated per LNY = log2 ny
+// instantiated per LNY = log2 ny.  The coefficient formation (profile times
+// aperture value) and the mirroring are the transform's first read, the
+// scaled store of T1 (q <= ny) its last write.
+template <typename T, int LNY>
+struct FieldY {
+  const C<T>* E;                  // aperture coefficients of this direction
+  const C<T>* Pj;                 // profiles of level j
+  const C<T>* Qj;                 // E3-driven profiles of level j (layered) or null
+  C<T>* dst;                      // T1 rows of this (slab, component)
+  int r0, nx, M, N, n1, n2, comp;
+  bool top, layered;
+  __device__ __forceinline__ C<T> coef(int r, int n) const {
+    const int m = comp == 0 ? r : r + 1;
+    if (r >= nx || m > M) return mk<T>(0, 0);
+    int i;
+    if (comp == 0) {
+      if (n < 1) return mk<T>(0, 0);
+      i = m * N + (n - 1);
+    } else if (comp == 1) {
+      i = n1 + (m - 1) * (N + 1) + n;
+    } else {
+      if (n < 1) return mk<T>(0, 0);
+      i = n1 + n2 + (m - 1) * N + (n - 1);
+    }
+    C<T> c = E[i];
+    if (!top) {
+      c = cmul<T>(Pj[i], c);
+      if (layered && comp < 2 && m >= 1 && n >= 1)
+        c = cadd<T>(c, cmul<T>(Qj[i], E[n1 + n2 + (m - 1) * N + (n - 1)]));
+    }
+    return c;
+  }
+  __device__ __forceinline__ C<T> ld(int l, const C<T>*, int k) const {
+    constexpr int ny = 1 << LNY, n2x = 2 * ny;
+    const bool ycos = comp == 1;
+    const int r = r0 + l;
+    if (k < ny) {
+      if (k == 0) return ycos ? cscale<T>(coef(r, 0), (T)2) : mk<T>(0, 0);
+      return coef(r, k);
+    }
+    if (k == ny) return mk<T>(0, 0);
+    const C<T> c = coef(r, n2x - k);
+    return ycos ? c : mk<T>(-c.x, -c.y);
+  }
+  __device__ __forceinline__ void st(int l, C<T>*, int q, C<T> v) const {
+    constexpr int ny = 1 << LNY;
+    const int r = r0 + l;
+    if (q > ny || r >= nx) return;
+    // cos: Z/2 ; sin: Z/(2i)
+    dst[(size_t)r * (ny + 1) + q] =
+        comp == 1 ? mk<T>(v.x * (T)0.5, v.y * (T)0.5) : mk<T>(v.y * (T)0.5, -v.x * (T)0.5);
+  }
+};
+
 template <typename T, int LNY>
 __global__ void __launch_bounds__(FIELD_THREADS, 2) k_field_y(const C<T>* __restrict__ ap,
                                                            const C<T>* __restrict__ prof,
@@ -47,76 +100,57 @@ __global__ void __launch_bounds__(FIELD_THREADS, 2) k_field_y(const C<T>* __rest
   constexpr int ny = 1 << LNY, n2 = 2 * ny, ls = padded_len(n2);
   constexpr int L = field_lines<T>(n2);
   const int comp = blockIdx.y, s = blockIdx.z;
-  const int r0 = blockIdx.x * L;
   const int d = s / p.lc, jj = s - d * p.lc;
   const int j = p.j0 + jj;
   if (j > p.nz) return;
-  const int tid = threadIdx.x, nthr = blockDim.x;
-  const C<T>* E = ap + (size_t)d * p.nap;
-  const bool top = (j == p.nz);
-  const C<T>* Pj = prof + (size_t)(j - 1) * p.nap;
-  const C<T>* Qj = profq ? profq + (size_t)(j - 1) * (p.n1 + p.n2) : nullptr;
-  const bool ycos = (comp == 1);
-  // coefficients of the L rows, loaded first (all loads in flight), then
-  // mirrored into the lines: every slot except n = ny (and n = 0 for the sine
-  // extension) is written, so only those are cleared
-  constexpr int PER = L * ny / FIELD_THREADS;
-  static_assert(PER * FIELD_THREADS == L * ny, "rows must tile the block");
-  C<T> cv[PER];
-#pragma unroll
-  for (int k = 0; k < PER; ++k) {
-    const int idx = tid + k * FIELD_THREADS;
-    const int l = idx >> LNY, n = idx & (ny - 1);
-    const int r = r0 + l;
-    const int m = comp == 0 ? r : r + 1;
-    int i = -1;
-    if (r < p.nx && m <= p.M) {
-      if (comp == 0) { if (n >= 1) i = m * p.N + (n - 1); }
-      else if (comp == 1) i = p.n1 + (m - 1) * (p.N + 1) + n;
-      else if (n >= 1) i = p.n1 + p.n2 + (m - 1) * p.N + (n - 1);
-    }
-    C<T> c = mk<T>(0, 0);
-    if (i >= 0) {
-      c = E[i];
-      if (!top) {
-        c = cmul<T>(Pj[i], c);
-        if (p.layered && comp < 2 && m >= 1 && n >= 1)
-          c = cadd<T>(c, cmul<T>(Qj[i], E[p.n1 + p.n2 + (m - 1) * p.N + (n - 1)]));
-      }
-    }
-    cv[k] = c;
-  }
-#pragma unroll
-  for (int k = 0; k < PER; ++k) {
-    const int idx = tid + k * FIELD_THREADS;
-    const int l = idx >> LNY, n = idx & (ny - 1);
-    C<T>* line = buf + (size_t)l * ls;
-    const C<T> c = cv[k];
-    if (n == 0) {
-      line[0] = ycos ? cscale<T>(c, (T)2) : mk<T>(0, 0);
-      line[pidx(ny)] = mk<T>(0, 0);
-    } else if (ycos) {
-      line[pidx(n)] = c;
-      line[pidx(n2 - n)] = c;
-    } else {
-      line[pidx(n)] = c;
-      line[pidx(n2 - n)] = mk<T>(-c.x, -c.y);
-    }
-  }
-  __syncthreads();
-  fft_lines<T, true, LNY + 1>(buf, ls, L, tw, p.twlog);
-  C<T>* dst = T1 + (((size_t)s * 3 + comp) * p.nx + r0) * (ny + 1);
-  const int nr = min(L, p.nx - r0);
-  for (int idx = tid; idx < nr * (ny + 1); idx += nthr) {
-    const int l = idx / (ny + 1), q = idx - l * (ny + 1);
-    const C<T> v = buf[(size_t)l * ls + pidx(q)];
-    // cos: Z/2 ; sin: Z/(2i)
-    dst[idx] = ycos ? mk<T>(v.x * (T)0.5, v.y * (T)0.5) : mk<T>(v.y * (T)0.5, -v.x * (T)0.5);
-  }
+  FieldY<T, LNY> op;
+  op.E = ap + (size_t)d * p.nap;
+  op.Pj = prof + (size_t)(j - 1) * p.nap;
+  op.Qj = profq ? profq + (size_t)(j - 1) * (p.n1 + p.n2) : nullptr;
+  op.dst = T1 + ((size_t)s * 3 + comp) * p.nx * (ny + 1);
+  op.r0 = blockIdx.x * L;
+  op.nx = p.nx;
+  op.M = p.M;
+  op.N = p.N;
+  op.n1 = p.n1;
+  op.n2 = p.n2;
+  op.comp = comp;
+  op.top = (j == p.nz);
+  op.layered = p.layered;
+  fft_lines<T, true, LNY + 1>(buf, ls, L, tw, p.twlog, op);
 }
 
 // pass 2: grid (ceil((ny+1) / L) column groups, 3 components, ndir * lc
-// slabs); instantiated per LNX = log2 nx
+// slabs); instantiated per LNX = log2 nx.  The column gather of T1 and the
+// mirroring are the transform's first read, the scaled store of the output
+// rows its last write.
+template <typename T, int LNX>
+struct FieldX {
+  const C<T>* src;                // T1 rows of this (slab, component)
+  C<T>* dst;                      // this component's output block of level j
+  int q0, ny, comp, ncol, qlo, qhi, plo, phi;
+  __device__ __forceinline__ C<T> ld(int l, const C<T>*, int t) const {
+    constexpr int nx = 1 << LNX, n2 = 2 * nx;
+    const int q = q0 + l;
+    if (q > ny || t == nx) return mk<T>(0, 0);
+    const bool xcos = comp == 0;
+    // E1: rows r = m (m = 0..nx-1); E2, E3: rows r = m - 1 (m = 1..nx-1)
+    if (t < nx) {
+      if (t == 0) return xcos ? cscale<T>(src[q], (T)2) : mk<T>(0, 0);
+      return src[(size_t)(xcos ? t : t - 1) * (ny + 1) + q];
+    }
+    const int m = n2 - t;
+    const C<T> c = src[(size_t)(xcos ? m : m - 1) * (ny + 1) + q];
+    return xcos ? c : mk<T>(-c.x, -c.y);
+  }
+  __device__ __forceinline__ void st(int l, C<T>*, int pp, C<T> v) const {
+    const int q = q0 + l;
+    if (pp < plo || pp > phi || q < qlo || q > qhi) return;
+    dst[(size_t)(pp - plo) * ncol + (q - qlo)] =
+        comp == 0 ? mk<T>(v.x * (T)0.5, v.y * (T)0.5) : mk<T>(v.y * (T)0.5, -v.x * (T)0.5);
+  }
+};
+
 template <typename T, int LNX>
 __global__ void __launch_bounds__(FIELD_THREADS, 2) k_field_x(const C<T>* __restrict__ T1,
                                                            C<T>* __restrict__ out, FP p,
@@ -124,69 +158,29 @@ __global__ void __launch_bounds__(FIELD_THREADS, 2) k_field_x(const C<T>* __rest
   extern __shared__ __align__(16) unsigned char sm_raw[];
   C<T>* buf = (C<T>*)sm_raw;
   constexpr int nx = 1 << LNX, n2 = 2 * nx, ls = padded_len(n2);
-  constexpr int L = field_lines<T>(n2), lL = clog2(L);
+  constexpr int L = field_lines<T>(n2);
   const int ny = p.ny;
   const int comp = blockIdx.y, s = blockIdx.z;
-  const int q0 = blockIdx.x * L;
   const int d = s / p.lc, jj = s - d * p.lc;
   const int j = p.j0 + jj;
   if (j > p.nz) return;
-  const int tid = threadIdx.x, nthr = blockDim.x;
-  const bool xcos = (comp == 0);
-  const C<T>* src = T1 + ((size_t)s * 3 + comp) * nx * (ny + 1);
-  // rows r of the L columns, loaded first, then mirrored; unwritten slots
-  // (m = nx, and m = 0 for the sine extension) are cleared
-  constexpr int PER = L * nx / FIELD_THREADS;
-  static_assert(PER * FIELD_THREADS == L * nx, "columns must tile the block");
-  const int nrows = xcos ? nx : nx - 1;    // E1: m = 0..M; E2/E3: m = 1..M
-  C<T> cv[PER];
-#pragma unroll
-  for (int k = 0; k < PER; ++k) {
-    const int idx = tid + k * FIELD_THREADS;
-    const int r = idx >> lL, l = idx & (L - 1);
-    const int q = q0 + l;
-    cv[k] = (q <= ny && r < nrows) ? src[(size_t)r * (ny + 1) + q] : mk<T>(0, 0);
-  }
-#pragma unroll
-  for (int k = 0; k < PER; ++k) {
-    const int idx = tid + k * FIELD_THREADS;
-    const int r = idx >> lL, l = idx & (L - 1);
-    C<T>* line = buf + (size_t)l * ls;
-    const C<T> c = cv[k];
-    if (xcos) {
-      if (r == 0) {
-        line[0] = cscale<T>(c, (T)2);
-        line[pidx(nx)] = mk<T>(0, 0);
-      } else {
-        line[pidx(r)] = c;
-        line[pidx(n2 - r)] = c;
-      }
-    } else if (r < nx - 1) {
-      const int m = r + 1;
-      line[pidx(m)] = c;
-      line[pidx(n2 - m)] = mk<T>(-c.x, -c.y);
-    } else {
-      line[0] = mk<T>(0, 0);
-      line[pidx(nx)] = mk<T>(0, 0);
-    }
-  }
-  __syncthreads();
-  fft_lines<T, true, LNX + 1>(buf, ls, L, tw, p.twlog);
+  FieldX<T, LNX> op;
+  op.src = T1 + ((size_t)s * 3 + comp) * nx * (ny + 1);
+  op.q0 = blockIdx.x * L;
+  op.ny = ny;
+  op.comp = comp;
   long long off;
-  int ncol, qlo, qhi, plo, phi;
-  if (comp == 0) { off = 0; ncol = ny - 1; qlo = 1; qhi = ny - 1; plo = 0; phi = nx; }
-  else if (comp == 1) { off = (long long)(nx + 1) * (ny - 1); ncol = ny + 1; qlo = 0; qhi = ny; plo = 1; phi = nx - 1; }
-  else { off = (long long)(nx + 1) * (ny - 1) + (long long)(nx - 1) * (ny + 1); ncol = ny - 1; qlo = 1; qhi = ny - 1; plo = 1; phi = nx - 1; }
-  C<T>* dst = out + ((size_t)d * p.nz + (j - 1)) * p.S + off;
-  const int np = phi - plo + 1;
-  for (int idx = tid; idx < L * np; idx += nthr) {
-    const int pr = idx >> lL, l = idx & (L - 1);
-    const int q = q0 + l;
-    if (q < qlo || q > qhi) continue;
-    const C<T> v = buf[(size_t)l * ls + pidx(plo + pr)];
-    dst[(size_t)pr * ncol + (q - qlo)] =
-        xcos ? mk<T>(v.x * (T)0.5, v.y * (T)0.5) : mk<T>(v.y * (T)0.5, -v.x * (T)0.5);
+  if (comp == 0) {
+    off = 0; op.ncol = ny - 1; op.qlo = 1; op.qhi = ny - 1; op.plo = 0; op.phi = nx;
+  } else if (comp == 1) {
+    off = (long long)(nx + 1) * (ny - 1);
+    op.ncol = ny + 1; op.qlo = 0; op.qhi = ny; op.plo = 1; op.phi = nx - 1;
+  } else {
+    off = (long long)(nx + 1) * (ny - 1) + (long long)(nx - 1) * (ny + 1);
+    op.ncol = ny - 1; op.qlo = 1; op.qhi = ny - 1; op.plo = 1; op.phi = nx - 1;
   }
+  op.dst = out + ((size_t)d * p.nz + (j - 1)) * p.S + off;
+  fft_lines<T, true, LNX + 1>(buf, ls, L, tw, p.twlog, op);
 }
 
 __global__ void k_ap32(const double2* __restrict__ a, float2* __restrict__ b, long long n) {

@@ -29,6 +29,8 @@
 struct TbcP {
   int nx, ny, M, N, Px, Py, lPx, lPy, lnx, lny, nap, n1, n2;
   double a, b, h, k2x2;  // k2x2 = 2 kappa0^2
+  double pia, pib, ab;   // pi / a, pi / b, a b
+  double wy, wx;         // trapezoid weights / 2: b / (2 ny), a / (2 nx)
   int twlog;
 };
 
@@ -39,6 +41,8 @@ static TbcP make_params(const cavity_ctx* ctx) {
   p.lPx = g.lPx; p.lPy = g.lPy; p.lnx = g.lnx; p.lny = g.lny;
   p.nap = g.nap; p.n1 = g.n1; p.n2 = g.n2;
   p.a = g.a; p.b = g.b; p.h = g.h; p.k2x2 = 2.0 * ctx->kappa0 * ctx->kappa0;
+  p.pia = M_PI / g.a; p.pib = M_PI / g.b; p.ab = g.a * g.b;
+  p.wy = 0.5 * g.b / g.ny; p.wx = 0.5 * g.a / g.nx;
   p.twlog = ilog2(ctx->TW);
   return p;
 }
@@ -68,69 +72,107 @@ template <typename T> __host__ __device__ constexpr int pairs_per_cta(int n) {
 // Py) is transformed, multiplied by the transforms of the two parity kernels
 // eps_r and transformed back: the linear convolutions give the basis
 // transform at j2 = 2t + r of the symmetric box.  Lines: [parity][row].
+// The gather of the coefficients is the forward transform's first read, the
+// kernel products its last write, and the scatter to Vy the inverse
+// transforms' last write: shared memory holds only the transforms.
+
+// coefficient k2 (0 <= k2 < ny) of row k1 for field f, mirrored to the input
+// n of a line of length Py
 template <typename T, int LNY>
-__global__ void TBC_BOUNDS k_tbcA(const C<T>* __restrict__ x, C<T>* __restrict__ Vy, TbcP p,
-                                  const C<T>* __restrict__ tw, const C<T>* __restrict__ eh_c,
-                                  const C<T>* __restrict__ eh_s) {
-  extern __shared__ __align__(16) unsigned char sm_raw[];
-  C<T>* buf = (C<T>*)sm_raw;
-  constexpr int LPY = LNY + 2, Py = 1 << LPY, ny = 1 << LNY, ls = padded_len(Py);
-  constexpr int L = pairs_per_cta<T>(Py);
-  const int f = blockIdx.y, d = blockIdx.z;
-  const int row0 = blockIdx.x * L;
-  const int tid = threadIdx.x, nthr = blockDim.x;
-  const C<T>* E1 = x + (size_t)d * p.nap;
-  const C<T>* E2 = E1 + p.n1;
-  const int N = ny - 1;
-  const bool ycos = (f != 0);
-  for (int t = tid; t < L * ls; t += nthr) buf[t] = czero<T>();
-  __syncthreads();
-  for (int idx = tid; idx < L * ny; idx += nthr) {
-    const int l = idx >> LNY, k2 = idx & (ny - 1);
-    const int k1 = row0 + l;
-    if (k1 >= p.nx) continue;
+struct GatherA {
+  const C<T>* E1;
+  const C<T>* E2;
+  int row0, nx, f;
+  T pib, pia;                     // pi / b, pi / a
+  __device__ __forceinline__ C<T> coef(int k1, int k2) const {
+    constexpr int ny = 1 << LNY, N = ny - 1;
     C<T> c = czero<T>();
     if (f == 0) {
       if (k2 >= 1) c = E1[k1 * N + (k2 - 1)];
     } else if (f == 1) {
       if (k1 >= 1) c = E2[(k1 - 1) * ny + k2];
     } else {
-      if (k2 >= 1) c = cscale<T>(E1[k1 * N + (k2 - 1)], (T)(k2 * M_PI / p.b));
-      if (k1 >= 1) c = csub<T>(c, cscale<T>(E2[(k1 - 1) * ny + k2], (T)(k1 * M_PI / p.a)));
+      if (k2 >= 1) c = cscale<T>(E1[k1 * N + (k2 - 1)], (T)k2 * pib);
+      if (k1 >= 1) c = csub<T>(c, cscale<T>(E2[(k1 - 1) * ny + k2], (T)k1 * pia));
     }
-    C<T>* line = buf + (size_t)l * ls;
-    if (ycos) {
-      if (k2 == 0) line[0] = cscale<T>(c, (T)2);
-      else { line[pidx(k2)] = c; line[pidx(Py - k2)] = c; }
-    } else if (k2 >= 1) {
-      line[pidx(k2)] = c;
-      line[pidx(Py - k2)] = mk<T>(-c.x, -c.y);
-    }
+    return c;
   }
-  __syncthreads();
-  fft_lines<T, false, LPY>(buf, ls, L, tw, p.twlog);
-  const C<T>* eh = ycos ? eh_c : eh_s;
-  for (int idx = tid; idx < L * Py; idx += nthr) {
-    const int l = idx >> LPY, t = idx & (Py - 1);
-    C<T>* line = buf + (size_t)l * ls;
-    const C<T> sv = line[pidx(t)];
-    line[pidx(t)] = cmul<T>(sv, eh[t]);
-    buf[(size_t)(L + l) * ls + pidx(t)] = cmul<T>(sv, eh[Py + t]);
-  }
-  __syncthreads();
-  fft_lines<T, true, LPY>(buf, ls, 2 * L, tw, p.twlog);
-  for (int idx = tid; idx < L * Py; idx += nthr) {
-    const int l = idx >> LPY, j = idx & (Py - 1);
+  __device__ __forceinline__ C<T> ld(int l, const C<T>*, int n) const {
+    constexpr int ny = 1 << LNY, Py = 4 * ny;
     const int k1 = row0 + l;
-    if (k1 >= p.nx) continue;
-    C<T> r = czero<T>();
-    if (j != Py / 2) {
-      const int j2 = j < Py / 2 ? j : j - Py;
-      const int t = j2 >> 1, par = j2 & 1;     // j2 = 2 t + par (floor)
-      r = buf[(size_t)(par * L + l) * ls + pidx(t & (Py - 1))];
+    if (k1 >= nx) return czero<T>();
+    const bool ycos = f != 0;
+    if (n < ny) {
+      if (n == 0) return ycos ? cscale<T>(coef(k1, 0), (T)2) : czero<T>();
+      return coef(k1, n);
     }
-    Vy[((size_t)(d * 3 + f) * p.nx + k1) * Py + j] = r;
+    if (n > Py - ny) {
+      const C<T> c = coef(k1, Py - n);
+      return ycos ? c : mk<T>(-c.x, -c.y);
+    }
+    return czero<T>();
   }
+};
+
+// last write of the forward transform: the products with the two parity
+// kernels, into line l (r = 0) and line L + l (r = 1)
+template <typename T, typename G>
+struct ParityProducts : G {
+  const C<T>* eh;                 // [r][P]
+  int P, L, ls;
+  C<T>* buf;
+  __device__ __forceinline__ void st(int l, C<T>*, int k, C<T> v) const {
+    buf[(size_t)l * ls + pidx(k)] = cmul<T>(v, eh[k]);
+    buf[(size_t)(L + l) * ls + pidx(k)] = cmul<T>(v, eh[P + k]);
+  }
+};
+
+// last write of the inverse transforms of pass A: Vy(k1, j), j = 2t + r mod Py
+template <typename T, int LNY>
+struct ScatterA : LineId<T> {
+  C<T>* Vy;                       // this field's [nx][Py] block
+  int row0, nx, L;
+  __device__ __forceinline__ void st(int lr, C<T>*, int k, C<T> v) const {
+    constexpr int Py = 4 << LNY;
+    const int r = lr >= L ? 1 : 0, l = lr - r * L;
+    const int k1 = row0 + l;
+    const int t = k < Py / 2 ? k : k - Py;
+    if (k1 >= nx || t < -Py / 4 || t >= Py / 4) return;
+    const int j2 = 2 * t + r;
+    Vy[(size_t)k1 * Py + (j2 & (Py - 1))] = (j2 == -Py / 2) ? czero<T>() : v;
+  }
+};
+
+template <typename T, int LNY>
+__global__ void TBC_BOUNDS k_tbcA(const C<T>* __restrict__ x, C<T>* __restrict__ Vy, TbcP p,
+                                  const C<T>* __restrict__ tw, const C<T>* __restrict__ eh_c,
+                                  const C<T>* __restrict__ eh_s) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  C<T>* buf = (C<T>*)sm_raw;
+  constexpr int LPY = LNY + 2, Py = 1 << LPY, ls = padded_len(Py);
+  constexpr int L = pairs_per_cta<T>(Py);
+  const int f = blockIdx.y, d = blockIdx.z;
+  const int row0 = blockIdx.x * L;
+  ParityProducts<T, GatherA<T, LNY>> fwd;
+  fwd.E1 = x + (size_t)d * p.nap;
+  fwd.E2 = fwd.E1 + p.n1;
+  fwd.row0 = row0;
+  fwd.nx = p.nx;
+  fwd.f = f;
+  fwd.pib = (T)p.pib;
+  fwd.pia = (T)p.pia;
+  fwd.eh = f != 0 ? eh_c : eh_s;
+  fwd.P = Py;
+  fwd.L = L;
+  fwd.ls = ls;
+  fwd.buf = buf;
+  fft_lines<T, false, LPY>(buf, ls, L, tw, p.twlog, fwd);
+  ScatterA<T, LNY> sc;
+  sc.Vy = Vy + (size_t)(d * 3 + f) * p.nx * Py;
+  sc.row0 = row0;
+  sc.nx = p.nx;
+  sc.L = L;
+  fft_lines<T, true, LPY>(buf, ls, 2 * L, tw, p.twlog, sc);
 }
 
 // ------------------------------------------------------------------ pass B
@@ -139,6 +181,58 @@ __global__ void TBC_BOUNDS k_tbcA(const C<T>* __restrict__ x, C<T>* __restrict__
 // F(G)(|j1|, |j2|)/(Lx Ly), then the inverse torus transform along x1 at the
 // nodes p = 0..nx:  sum_j1 Y(j1) e^{2 pi i j1 p/Px} = Z_0(p) + e^{2 pi i p/Px} Z_1(p),
 // Z_r = inverse transform of length Px/2 of Y(2t + r) over t.
+// Fused: the column gather (first read of the forward transform), the parity
+// products (its last write), the kernel-table products with the move of
+// t to slot t mod Px/2 (last write of the first inverse transforms).
+
+// column j0 + l of Vy along k1, mirrored to the input n of a line of length Px
+template <typename T, int LNX>
+struct GatherB {
+  const C<T>* src;                // this field's [nx][Py] block
+  int j0, Py;
+  bool xcos;
+  __device__ __forceinline__ C<T> ld(int l, const C<T>*, int n) const {
+    constexpr int nx = 1 << LNX, Px = 4 * nx;
+    const int j = j0 + l;
+    if (j >= Py) return czero<T>();
+    if (n < nx) {
+      if (n == 0) return xcos ? cscale<T>(src[j], (T)2) : czero<T>();
+      return src[(size_t)n * Py + j];
+    }
+    if (n > Px - nx) {
+      const C<T> c = src[(size_t)(Px - n) * Py + j];
+      return xcos ? c : mk<T>(-c.x, -c.y);
+    }
+    return czero<T>();
+  }
+};
+
+// last write of the first inverse transforms of pass B: output t (k = t mod
+// Px) of line (r, l), |t| < Px/4, times the kernel table at (|2t + r|, |j2|),
+// written to slot t mod Px/2 (other outputs are not needed)
+template <typename T, int LNX>
+struct KhatB : LineId<T> {
+  const C<T>* kh;                 // [j2 < Py/2][j1 < Px/2]
+  int j0, Py, L;
+  __device__ __forceinline__ void st(int lr, C<T>* line, int k, C<T> v) const {
+    constexpr int Px = 4 << LNX, hp = Px / 2, qp = Px / 4;
+    int t, u;
+    if (k < qp) { t = k; u = k; }
+    else if (k >= Px - qp) { t = k - Px; u = k - hp; }
+    else return;
+    const int r = lr >= L ? 1 : 0, l = lr - r * L;
+    const int j = j0 + l;
+    const int j1 = 2 * t + r;
+    C<T> o = czero<T>();
+    if (j1 != -hp && j < Py && j != Py / 2) {
+      const int j1a = j1 < 0 ? -j1 : j1;
+      const int j2a = j < Py / 2 ? j : Py - j;
+      o = cmul<T>(v, kh[(size_t)j2a * hp + j1a]);
+    }
+    line[pidx(u)] = o;
+  }
+};
+
 template <typename T, int LNX>
 __global__ void TBC_BOUNDS k_tbcB(const C<T>* __restrict__ Vy, C<T>* __restrict__ W, TbcP p,
                                   const C<T>* __restrict__ tw, const C<T>* __restrict__ eh_c,
@@ -147,60 +241,28 @@ __global__ void TBC_BOUNDS k_tbcB(const C<T>* __restrict__ Vy, C<T>* __restrict_
   C<T>* buf = (C<T>*)sm_raw;
   constexpr int LPX = LNX + 2, Px = 1 << LPX, nx = 1 << LNX, ls = padded_len(Px);
   constexpr int L = pairs_per_cta<T>(Px), lL = clog2(L);
-  constexpr int hp = Px / 2, qp = Px / 4;
   const int Py = p.Py;
   const int f = blockIdx.y, d = blockIdx.z;
   const int j0 = blockIdx.x * L;
   const int tid = threadIdx.x, nthr = blockDim.x;
   const bool xcos = (f != 1);
-  const C<T>* src = Vy + (size_t)(d * 3 + f) * nx * Py;
-  for (int t = tid; t < L * ls; t += nthr) buf[t] = czero<T>();
-  __syncthreads();
-  for (int idx = tid; idx < L * nx; idx += nthr) {
-    const int k1 = idx >> lL, l = idx & (L - 1);
-    const int j = j0 + l;
-    if (j >= Py) continue;
-    const C<T> c = src[(size_t)k1 * Py + j];
-    C<T>* line = buf + (size_t)l * ls;
-    if (xcos) {
-      if (k1 == 0) line[0] = cscale<T>(c, (T)2);
-      else { line[pidx(k1)] = c; line[pidx(Px - k1)] = c; }
-    } else if (k1 >= 1) {
-      line[pidx(k1)] = c;
-      line[pidx(Px - k1)] = mk<T>(-c.x, -c.y);
-    }
-  }
-  __syncthreads();
-  fft_lines<T, false, LPX>(buf, ls, L, tw, p.twlog);
-  const C<T>* eh = xcos ? eh_c : eh_s;
-  for (int idx = tid; idx < L * Px; idx += nthr) {
-    const int l = idx >> LPX, t = idx & (Px - 1);
-    C<T>* line = buf + (size_t)l * ls;
-    const C<T> sv = line[pidx(t)];
-    line[pidx(t)] = cmul<T>(sv, eh[t]);
-    buf[(size_t)(L + l) * ls + pidx(t)] = cmul<T>(sv, eh[Px + t]);
-  }
-  __syncthreads();
-  fft_lines<T, true, LPX>(buf, ls, 2 * L, tw, p.twlog);
-  // K-hat in place: slot u < Px/2 of line (r, l) receives t = u (u < Px/4) or
-  // t = u - Px/2, read from slot t mod Px.  Sources and destinations of
-  // different slots never overlap (u >= Px/4 reads u + Px/2).
-  for (int idx = tid; idx < 2 * L * hp; idx += nthr) {
-    const int lr = idx >> (LPX - 1), u = idx & (hp - 1);
-    const int r = lr >= L ? 1 : 0, l = lr - r * L;
-    const int j = j0 + l;
-    const int t = u < qp ? u : u - hp;
-    const int j1 = 2 * t + r;
-    C<T>* line = buf + (size_t)lr * ls;
-    C<T> v = czero<T>();
-    if (j1 != -hp && j < Py && j != Py / 2) {
-      const int j1a = j1 < 0 ? -j1 : j1;
-      const int j2a = j < Py / 2 ? j : Py - j;
-      v = cmul<T>(line[pidx(t & (Px - 1))], kh[(size_t)j2a * hp + j1a]);
-    }
-    line[pidx(u)] = v;
-  }
-  __syncthreads();
+  ParityProducts<T, GatherB<T, LNX>> fwd;
+  fwd.src = Vy + (size_t)(d * 3 + f) * nx * Py;
+  fwd.j0 = j0;
+  fwd.Py = Py;
+  fwd.xcos = xcos;
+  fwd.eh = xcos ? eh_c : eh_s;
+  fwd.P = Px;
+  fwd.L = L;
+  fwd.ls = ls;
+  fwd.buf = buf;
+  fft_lines<T, false, LPX>(buf, ls, L, tw, p.twlog, fwd);
+  KhatB<T, LNX> kb;
+  kb.kh = kh;
+  kb.j0 = j0;
+  kb.Py = Py;
+  kb.L = L;
+  fft_lines<T, true, LPX>(buf, ls, 2 * L, tw, p.twlog, kb);
   fft_lines<T, true, LPX - 1>(buf, ls, 2 * L, tw, p.twlog);
   C<T>* dst = W + (size_t)(d * 3 + f) * (nx + 1) * Py;
   const int sh = p.twlog - LPX;
@@ -217,92 +279,118 @@ __global__ void TBC_BOUNDS k_tbcB(const C<T>* __restrict__ Vy, C<T>* __restrict_
 // ------------------------------------------------------------------ pass C
 // grid (ceil((nx+1)/L) row groups, 3 fields, ndir).  Per node row p: inverse
 // torus transform along x2 at q = 0..ny, then the trapezoid projection onto
-// cos/sin(n pi q/ny) as an extended FFT of length 2 ny.
+// cos/sin(n pi q/ny) as an extended FFT of length 2 ny.  Fused: the row load
+// (first read), the even / odd extension of U(q), q <= ny (last write of the
+// inverse transform), the weighted store of Z (last write of the projection).
+
+template <typename T, int LNY>
+struct RowC {
+  const C<T>* src;                // this field's [nx+1][Py] block
+  int r0, nx;
+  bool ycos;
+  __device__ __forceinline__ C<T> ld(int l, const C<T>*, int n) const {
+    constexpr int Py = 4 << LNY;
+    const int row = r0 + l;
+    return row <= nx ? src[(size_t)row * Py + n] : czero<T>();
+  }
+  __device__ __forceinline__ void st(int, C<T>* line, int k, C<T> v) const {
+    constexpr int ny = 1 << LNY, n2 = 2 * ny;
+    if (k > ny) return;
+    if (!ycos && (k == 0 || k == ny)) {
+      line[pidx(k)] = czero<T>();
+      return;
+    }
+    line[pidx(k)] = v;
+    if (k > 0 && k < ny) line[pidx(n2 - k)] = ycos ? v : mk<T>(-v.x, -v.y);
+  }
+};
+
+template <typename T, int LNY>
+struct StoreZ : LineId<T> {
+  C<T>* Z;                        // this field's [nx+1][ny+1] block
+  int r0, nx;
+  bool ycos;
+  T w;
+  __device__ __forceinline__ void st(int l, C<T>*, int k, C<T> v) const {
+    constexpr int ny = 1 << LNY;
+    const int row = r0 + l;
+    if (k > ny || row > nx) return;
+    Z[(size_t)row * (ny + 1) + k] = ycos ? cscale<T>(v, w) : cscale<T>(cmul_i<T>(v), w);
+  }
+};
+
 template <typename T, int LNY>
 __global__ void TBC_BOUNDS k_tbcC(const C<T>* __restrict__ W, C<T>* __restrict__ Z, TbcP p,
                                   const C<T>* __restrict__ tw) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   C<T>* buf = (C<T>*)sm_raw;
-  constexpr int LPY = LNY + 2, Py = 1 << LPY, ny = 1 << LNY, n2 = 2 * ny, ls = padded_len(Py);
+  constexpr int LPY = LNY + 2, Py = 1 << LPY, ny = 1 << LNY, ls = padded_len(Py);
   constexpr int L = lines_per_cta<T>(Py);
   const int f = blockIdx.y, d = blockIdx.z;
   const int r0 = blockIdx.x * L;
-  const int tid = threadIdx.x, nthr = blockDim.x;
   const bool ycos = (f != 0);
-  const C<T>* src = W + (size_t)(d * 3 + f) * (p.nx + 1) * Py;
-  for (int idx = tid; idx < L * Py; idx += nthr) {
-    const int l = idx >> LPY, t = idx & (Py - 1);
-    const int row = r0 + l;
-    buf[(size_t)l * ls + pidx(t)] = row <= p.nx ? src[(size_t)row * Py + t] : czero<T>();
-  }
-  __syncthreads();
-  fft_lines<T, true, LPY>(buf, ls, L, tw, p.twlog);
-  // even (cos) / odd (sin) extension of U(q), q = 0..ny, to length 2 ny in place
-  for (int idx = tid; idx < L * n2; idx += nthr) {
-    const int l = idx >> (LNY + 1), t = idx & (n2 - 1);
-    C<T>* line = buf + (size_t)l * ls;
-    if (t <= ny) {
-      if (!ycos && (t == 0 || t == ny)) line[pidx(t)] = czero<T>();
-    } else {
-      C<T> v = line[pidx(n2 - t)];
-      line[pidx(t)] = ycos ? v : mk<T>(-v.x, -v.y);
-    }
-  }
-  __syncthreads();
-  fft_lines<T, false, LNY + 1>(buf, ls, L, tw, p.twlog);
-  const T w = (T)(0.5 * p.b / ny);
-  for (int idx = tid; idx < L * (ny + 1); idx += nthr) {
-    const int l = idx / (ny + 1), n = idx - l * (ny + 1);
-    const int row = r0 + l;
-    if (row > p.nx) continue;
-    const C<T> v = buf[(size_t)l * ls + pidx(n)];
-    Z[((size_t)(d * 3 + f) * (p.nx + 1) + row) * (ny + 1) + n] =
-        ycos ? cscale<T>(v, w) : cscale<T>(cmul_i<T>(v), w);
-  }
+  RowC<T, LNY> rc;
+  rc.src = W + (size_t)(d * 3 + f) * (p.nx + 1) * Py;
+  rc.r0 = r0;
+  rc.nx = p.nx;
+  rc.ycos = ycos;
+  fft_lines<T, true, LPY>(buf, ls, L, tw, p.twlog, rc);
+  StoreZ<T, LNY> sz;
+  sz.Z = Z + (size_t)(d * 3 + f) * (p.nx + 1) * (ny + 1);
+  sz.r0 = r0;
+  sz.nx = p.nx;
+  sz.ycos = ycos;
+  sz.w = (T)p.wy;
+  fft_lines<T, false, LNY + 1>(buf, ls, L, tw, p.twlog, sz);
 }
 
 // ------------------------------------------------------------------ pass D
 // grid (ceil((ny+1)/L) column groups, 3 fields, ndir).  Per column n: the
-// trapezoid projection along x1 (extended FFT of length 2 nx).
+// trapezoid projection along x1 (extended FFT of length 2 nx), with the
+// column gather and extension as the first read and the weighted store of O
+// as the last write.
+template <typename T, int LNX>
+struct ColD {
+  const C<T>* src;                // this field's [nx+1][ny+1] block
+  C<T>* dst;                      // this field's [nx][ny+1] block
+  int c0, ny;
+  bool xcos;
+  T w;
+  __device__ __forceinline__ C<T> ld(int l, const C<T>*, int t) const {
+    constexpr int nx = 1 << LNX, n2 = 2 * nx;
+    const int col = c0 + l;
+    if (col > ny) return czero<T>();
+    if (t <= nx) {
+      if (!xcos && (t == 0 || t == nx)) return czero<T>();
+      return src[(size_t)t * (ny + 1) + col];
+    }
+    const C<T> r = src[(size_t)(n2 - t) * (ny + 1) + col];
+    return xcos ? r : mk<T>(-r.x, -r.y);
+  }
+  __device__ __forceinline__ void st(int l, C<T>*, int m, C<T> v) const {
+    constexpr int nx = 1 << LNX;
+    const int col = c0 + l;
+    if (m >= nx || col > ny) return;
+    dst[(size_t)m * (ny + 1) + col] = xcos ? cscale<T>(v, w) : cscale<T>(cmul_i<T>(v), w);
+  }
+};
+
 template <typename T, int LNX>
 __global__ void TBC_BOUNDS k_tbcD(const C<T>* __restrict__ Z, C<T>* __restrict__ O, TbcP p,
                                   const C<T>* __restrict__ tw) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   C<T>* buf = (C<T>*)sm_raw;
   constexpr int nx = 1 << LNX, n2 = 2 * nx, ls = padded_len(n2);
-  constexpr int L = lines_per_cta<T>(n2), lL = clog2(L);
-  const int ny = p.ny;
+  constexpr int L = lines_per_cta<T>(n2);
   const int f = blockIdx.y, d = blockIdx.z;
-  const int c0 = blockIdx.x * L;
-  const int tid = threadIdx.x, nthr = blockDim.x;
-  const bool xcos = (f != 1);
-  const C<T>* src = Z + (size_t)(d * 3 + f) * (nx + 1) * (ny + 1);
-  for (int idx = tid; idx < L * n2; idx += nthr) {
-    const int t = idx >> lL, l = idx & (L - 1);
-    const int col = c0 + l;
-    C<T> r = czero<T>();
-    if (col <= ny) {
-      if (t <= nx) {
-        r = src[(size_t)t * (ny + 1) + col];
-        if (!xcos && (t == 0 || t == nx)) r = czero<T>();
-      } else {
-        r = src[(size_t)(n2 - t) * (ny + 1) + col];
-        if (!xcos) r = mk<T>(-r.x, -r.y);
-      }
-    }
-    buf[(size_t)l * ls + pidx(t)] = r;
-  }
-  __syncthreads();
-  fft_lines<T, false, LNX + 1>(buf, ls, L, tw, p.twlog);
-  C<T>* dst = O + (size_t)(d * 3 + f) * nx * (ny + 1);
-  const T w = (T)(0.5 * p.a / nx);
-  for (int idx = tid; idx < L * nx; idx += nthr) {
-    const int m = idx >> lL, l = idx & (L - 1);
-    const int col = c0 + l;
-    if (col > ny) continue;
-    const C<T> v = buf[(size_t)l * ls + pidx(m)];
-    dst[(size_t)m * (ny + 1) + col] = xcos ? cscale<T>(v, w) : cscale<T>(cmul_i<T>(v), w);
-  }
+  ColD<T, LNX> cd;
+  cd.src = Z + (size_t)(d * 3 + f) * (nx + 1) * (p.ny + 1);
+  cd.dst = O + (size_t)(d * 3 + f) * nx * (p.ny + 1);
+  cd.c0 = blockIdx.x * L;
+  cd.ny = p.ny;
+  cd.xcos = (f != 1);
+  cd.w = (T)p.wx;
+  fft_lines<T, false, LNX + 1>(buf, ls, L, tw, p.twlog, cd);
 }
 
 // ------------------------------------------------------------------ combine
@@ -325,7 +413,7 @@ __global__ void k_combine(const C<T>* __restrict__ x, const C<T>* __restrict__ O
   const int N = p.N, nyp = p.ny + 1;
   const size_t fs = (size_t)p.nx * nyp;
   const C<T>* Od = O + (size_t)d * 3 * fs;
-  const T pa = (T)(M_PI / p.a), pb = (T)(M_PI / p.b), h = (T)p.h, ab = (T)(p.a * p.b);
+  const T pa = (T)p.pia, pb = (T)p.pib, h = (T)p.h, ab = (T)p.ab;
   const T k2 = (T)p.k2x2;
   const int i1 = m * N + (n - 1), i2 = p.n1 + (m - 1) * (N + 1) + n;
   const int i3 = p.n1 + p.n2 + (m - 1) * N + (n - 1);
