@@ -39,10 +39,10 @@ METRIC = "cavity field DOF/s at rel err \u22641e-5 vs FP64 oracle; p50/p99 solve
 # 5.8e-7 at 1e-6 and 1.1e-5 (over the 1e-5 bound) at 1e-5.  1e-7 keeps the
 # error at the floor; every run re-measures it (the "accuracy" entry).
 TOL = 1e-7
-# DRAM traffic of one launch of the FP64 transform pass B (k_tbcB<double, 8>),
-# from `ncu --set full` on 8 directions (105.0 MB read + 67.3 MB written),
-# scaled to the 16 directions of a launch here (traffic is proportional)
-NCU_TRAFFIC = {"tbc_B_fp64": 2 * (105.042688e6 + 67.337472e6)}
+# DRAM traffic of one launch of a kernel class from one `ncu --set full`
+# capture on 8 directions, scaled to the 16 directions of a launch here
+# (traffic is proportional to the directions); filled in per capture
+NCU_TRAFFIC = {}
 
 
 def peaks():
@@ -365,7 +365,7 @@ def run_gb300(args, rank, world, local_rank):
     line = {"metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": world,
             "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "c64 transforms / f64 elimination and residuals", "data": "synthetic",
+            "dtype": "c64 transforms and Krylov; f64 elimination and refinement; f32-pair residual operator", "data": "synthetic",
             "config": {"workload": WORKLOAD + ": 256x256x128 grid, a=b=1, c=0.5, eps=1, "
                                    "kappa0=2pi*25.6 (10 points per wavelength), 16 seeded "
                                    "incident directions per GPU, mixed precision, "

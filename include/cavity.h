@@ -56,6 +56,9 @@ typedef enum {
 } cavity_status;
 
 enum { CAVITY_FP64 = 0, CAVITY_MIXED = 1 };          /* precision modes       */
+/* cavity_apply only: the operator in pair-of-FP32 arithmetic (relative error
+ * ~1e-12, complex128 vectors), the residual operator of CAVITY_MIXED solves */
+enum { CAVITY_PAIR32 = 2 };
 enum { CAVITY_OUT_APERTURE = 0, CAVITY_OUT_FIELD = 1 };
 enum { CAVITY_MEM_DEVICE = 0, CAVITY_MEM_HOST = 1 };
 enum { CAVITY_POL_THETA = 0, CAVITY_POL_PHI = 1 };
@@ -167,8 +170,9 @@ cavity_status cavity_export_khat(cavity_ctx* ctx, void* khat);
 cavity_status cavity_rhs(cavity_ctx* ctx, int ndir, const double* theta,
                          const double* phi, const double* alpha, void* out);
 
-/* y = A x for the reduced aperture matrix of (EJ1)/(uT1): x, y ndir x n_ap,
- * complex128 when precision == CAVITY_FP64 and complex64 when CAVITY_MIXED. */
+/* y = A x for the reduced aperture matrix of (EJ1)/(uT1): x, y ndir x n_ap
+ * (device), complex128 when precision == CAVITY_FP64 or CAVITY_PAIR32 and
+ * complex64 when CAVITY_MIXED.  Other precision values: CAVITY_EINVAL. */
 cavity_status cavity_apply(cavity_ctx* ctx, int ndir, int precision,
                            const void* x, void* y);
 
@@ -205,7 +209,7 @@ cavity_status cavity_field(cavity_ctx* ctx, int ndir, const void* aperture,
  * returns, per class, the summed event time in ms (0 when timing was off) and
  * the number of launches since the last reset; ms and launches are host arrays
  * of length nclass (<= CAVITY_NUM_KCLASS), either may be NULL. */
-#define CAVITY_NUM_KCLASS 16
+#define CAVITY_NUM_KCLASS 21
 cavity_status cavity_timing(cavity_ctx* ctx, int enable);
 cavity_status cavity_timing_read(cavity_ctx* ctx, int nclass, double* ms,
                                  long long* launches);

@@ -147,10 +147,14 @@ class Cavity:
         return out
 
     def apply(self, x, precision=None):
-        prec = self.precision if precision is None else (
-            _lib.CAVITY_FP64 if precision == "fp64" else _lib.CAVITY_MIXED)
+        """y = A x.  precision: None (the context's), "fp64", "mixed" (FP32
+        operator, complex64 vectors) or "pair32" (pair-of-FP32 arithmetic,
+        complex128 vectors: the residual operator of the mixed solve)."""
+        prec = self.precision if precision is None else {
+            "fp64": _lib.CAVITY_FP64, "mixed": _lib.CAVITY_MIXED,
+            "pair32": _lib.CAVITY_PAIR32}[precision]
         x = x.contiguous()
-        want = torch.complex128 if prec == _lib.CAVITY_FP64 else torch.complex64
+        want = torch.complex64 if prec == _lib.CAVITY_MIXED else torch.complex128
         if x.dtype != want or not x.is_cuda or x.dim() != 2 or x.shape[1] != self.n_ap:
             raise ValueError("x must be a CUDA (ndir, n_ap) tensor of %s" % want)
         y = torch.empty_like(x)

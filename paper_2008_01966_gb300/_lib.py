@@ -14,7 +14,7 @@ CAVITY_OK, CAVITY_EINVAL, CAVITY_ENOMEM, CAVITY_ESINGULAR, CAVITY_ENOCONV, CAVIT
     CAVITY_ECUDA = range(7)
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ESINGULAR", 4: "ENOCONV", 5: "ETIMEOUT",
                 6: "ECUDA"}
-CAVITY_FP64, CAVITY_MIXED = 0, 1
+CAVITY_FP64, CAVITY_MIXED, CAVITY_PAIR32 = 0, 1, 2
 CAVITY_OUT_APERTURE, CAVITY_OUT_FIELD = 0, 1
 CAVITY_MEM_DEVICE, CAVITY_MEM_HOST = 0, 1
 CAVITY_POL_THETA, CAVITY_POL_PHI = 0, 1
@@ -25,7 +25,7 @@ EXPORTS = ["cavity_setup", "cavity_prepare", "cavity_solve", "cavity_rcs", "cavi
            "cavity_export_khat", "cavity_rhs", "cavity_apply", "cavity_field",
            "cavity_timing", "cavity_timing_read", "cavity_kernel_class",
            "cavity_apply_noalloc"]
-NUM_KCLASS = 16
+NUM_KCLASS = 21
 
 
 class CavityDesc(ctypes.Structure):

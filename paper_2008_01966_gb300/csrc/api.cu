@@ -84,7 +84,8 @@ extern "C" void cavity_destroy(cavity_ctx* ctx) {
                   ctx->ehat_y64[1], ctx->ehat_x32[0], ctx->ehat_x32[1], ctx->ehat_y32[0],
                   ctx->ehat_y32[1], ctx->khat64, ctx->khat32, ctx->khat_raw, ctx->prof, ctx->profq,
                   ctx->top64, ctx->top32, ctx->pinv64, ctx->pinv32, ctx->prof32, ctx->profq32,
-                  ctx->minpiv, ctx->ws, ctx->ws2, ctx->stage};
+                  ctx->minpiv, ctx->ws, ctx->ws2, ctx->stage, ctx->tw_p, ctx->ehat_xp[0],
+                  ctx->ehat_xp[1], ctx->ehat_yp[0], ctx->ehat_yp[1], ctx->khat_p, ctx->top_p};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto& e : ctx->evs) {
@@ -157,6 +158,7 @@ extern "C" cavity_status cavity_prepare(cavity_ctx* ctx, double kappa0, int nlay
   if (!kappa_same) CKS(launch_khat(ctx, kappa0));
   CKS(launch_zsweep(ctx, kappa0));
   CKS(launch_precond(ctx));
+  CKS(launch_pair_tables(ctx));
   CK(cudaStreamSynchronize(ctx->stream));
   ctx->prepared = true;
   return CAVITY_OK;
@@ -191,6 +193,9 @@ extern "C" cavity_status cavity_apply(cavity_ctx* ctx, int ndir, int precision, 
   } else if (precision == CAVITY_MIXED) {
     CKS(ensure_ws(ctx, &ctx->ws, &ctx->ws_bytes, apply_work_bytes(ctx->g, ndir, sizeof(float2))));
     CKS(launch_apply<float>(ctx, ndir, (const float2*)x, (float2*)y, ctx->ws));
+  } else if (precision == CAVITY_PAIR32) {
+    CKS(ensure_ws(ctx, &ctx->ws, &ctx->ws_bytes, apply_pair_work_bytes(ctx->g, ndir)));
+    CKS(launch_apply_pair(ctx, ndir, (const double2*)x, (double2*)y, ctx->ws));
   } else {
     ctx->err = "unknown precision";
     return CAVITY_EINVAL;
@@ -335,7 +340,8 @@ extern "C" cavity_status cavity_rcs(cavity_ctx* ctx, int ndir, const void* apert
 static const char* kclass_names[KC_N] = {
     "tbc_A_fp64", "tbc_B_fp64", "tbc_C_fp64", "tbc_D_fp64", "tbc_combine_fp64",
     "tbc_A_fp32", "tbc_B_fp32", "tbc_C_fp32", "tbc_D_fp32", "tbc_combine_fp32",
-    "krylov", "precond", "field_y", "field_x", "rhs_rcs", "setup"};
+    "krylov", "precond", "field_y", "field_x", "rhs_rcs", "setup",
+    "tbc_A_pair32", "tbc_B_pair32", "tbc_C_pair32", "tbc_D_pair32", "tbc_combine_pair32"};
 static_assert(KC_N == CAVITY_NUM_KCLASS, "class count");
 
 extern "C" const char* cavity_kernel_class(int k) {

@@ -81,7 +81,8 @@ struct Geo {
 enum KClass {
   KC_TBC_A64, KC_TBC_B64, KC_TBC_C64, KC_TBC_D64, KC_COMB64,
   KC_TBC_A32, KC_TBC_B32, KC_TBC_C32, KC_TBC_D32, KC_COMB32,
-  KC_KRYLOV, KC_PRECOND, KC_FIELD_Y, KC_FIELD_X, KC_RHS, KC_SETUP, KC_N
+  KC_KRYLOV, KC_PRECOND, KC_FIELD_Y, KC_FIELD_X, KC_RHS, KC_SETUP,
+  KC_TBC_AP, KC_TBC_BP, KC_TBC_CP, KC_TBC_DP, KC_COMBP, KC_N
 };
 
 // one layer of the fill, top to bottom
@@ -107,6 +108,10 @@ struct cavity_ctx {
   // convolution scale folded in
   double2 *ehat_x64[2] = {nullptr, nullptr}, *ehat_y64[2] = {nullptr, nullptr};
   float2 *ehat_x32[2] = {nullptr, nullptr}, *ehat_y32[2] = {nullptr, nullptr};
+  // the same tables in pair-of-FP32 form (struct cdf, 16 bytes per entry) for
+  // the residual operator of the mixed solve
+  void* tw_p = nullptr;
+  void *ehat_xp[2] = {nullptr, nullptr}, *ehat_yp[2] = {nullptr, nullptr};
 
   // ---- state of the last prepare (kappa0, layers)
   bool prepared = false;
@@ -119,6 +124,8 @@ struct cavity_ctx {
   double2* profq = nullptr;    // (nz-1) x (n1+n2) profiles Q (layered only)
   double2* top64 = nullptr;    // nap tau, then n1+n2 varsigma
   float2* top32 = nullptr;
+  void* khat_p = nullptr;      // pair-of-FP32 copies of khat64 and top64
+  void* top_p = nullptr;
   double2* pinv64 = nullptr;   // (M+1)(N+1) x 9 inverse diagonal blocks
   float2* pinv32 = nullptr;
   float2* prof32 = nullptr;    // FP32 copies of the profiles for the mixed field path
@@ -244,6 +251,12 @@ template <typename T>
 cavity_status launch_apply(cavity_ctx* ctx, int ndir, const C<T>* x, C<T>* y, void* work,
                            long long ystride = -1);
 size_t apply_work_bytes(const Geo& g, int ndir, int elem_bytes);
+// y = A x in pair-of-FP32 arithmetic (~1e-12), FP64 vectors in and out;
+// work: apply_pair_work_bytes
+cavity_status launch_apply_pair(cavity_ctx* ctx, int ndir, const double2* x, double2* y,
+                                void* work);
+size_t apply_pair_work_bytes(const Geo& g, int ndir);
+cavity_status launch_pair_tables(cavity_ctx* ctx);
 // y = M^{-1} x with per-direction strides (< 0: n_ap)
 template <typename T>
 cavity_status launch_precond_apply(cavity_ctx* ctx, int ndir, const C<T>* x, C<T>* y,

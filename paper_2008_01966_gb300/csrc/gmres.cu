@@ -16,7 +16,9 @@
 // GMRES:  solve A d = r with FP32 GMRES to ~1e-5;  x += d (FP64);  update r;
 // repeat until ||r|| <= tol ||b||.  The residual is updated two ways:
 //   while the correction is large (||r|| > RES32_MAX ||b||, always after the
-//   first solve): r = b - A x with the FP64 operator;
+//   first solve): r = b - A x with the operator in pair-of-FP32 arithmetic
+//   (relative error ~1e-12: FP64-grade for a residual, at FP32 instruction
+//   rates; see df64.cuh);
 //   afterwards:    r = r - A d with the FP32 operator applied to the (scaled)
 //   correction, subtracted in FP64.
 // The second form is exact algebra (b - A(x + d) = r - A d); its only error is
@@ -24,7 +26,7 @@
 // parity tests bound eps32 (relative error of the FP32 operator) far below
 // 1e-5, so with ||r|| <= 1e-4 ||b|| the updated residual is within 2e-9 ||b||
 // of the true one.  One FP64 operator application per solve instead of one per
-// refinement step.
+// refinement step, and that one in pair-of-FP32 arithmetic.
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -587,7 +589,7 @@ cavity_status run_mixed_solve(cavity_ctx* ctx, int ndir, const double2* b, doubl
   const long long nv = (long long)ndir * g.nap;
   size_t n32 = gw_bytes<float>(g, ndir, m);
   size_t extra = 3 * al(sizeof(double2) * nv) + 2 * al(sizeof(float2) * nv) +
-                 al(apply_work_bytes(g, ndir, sizeof(double2))) + al(sizeof(double) * ndir) +
+                 al(apply_pair_work_bytes(g, ndir)) + al(sizeof(double) * ndir) +
                  al(sizeof(double2) * ndir);
   CKS(ensure_ws(ctx, &ctx->ws, &ctx->ws_bytes, n32 + extra));
   GW<float> W = gw_carve<float>(ctx->ws, g, ndir, m);
@@ -597,7 +599,7 @@ cavity_status run_mixed_solve(cavity_ctx* ctx, int ndir, const double2* b, doubl
   p += al(sizeof(double2) * nv);
   float2* r32 = (float2*)p; p += al(sizeof(float2) * nv);
   float2* d32 = (float2*)p; p += al(sizeof(float2) * nv);
-  void* apw64 = p; p += al(apply_work_bytes(g, ndir, sizeof(double2)));
+  void* apw64 = p; p += al(apply_pair_work_bytes(g, ndir));
   double* sdev = (double*)p; p += al(sizeof(double) * ndir);
   double2* sc2 = (double2*)p;
   cudaStream_t st = ctx->stream;
@@ -638,8 +640,8 @@ cavity_status run_mixed_solve(cavity_ctx* ctx, int ndir, const double2* b, doubl
     bool big = false;
     for (int d = 0; d < ndir; ++d) big = big || (bn[d] > 0 && rn[d] > RES32_MAX * bn[d]);
     if (big) {
-      // r = b - A x with the FP64 operator
-      CKS(launch_apply<double>(ctx, ndir, x, tmp64, apw64));
+      // r = b - A x with the pair-of-FP32 operator (~1e-12 relative)
+      CKS(launch_apply_pair(ctx, ndir, x, tmp64, apw64));
       {
         KScope ks_(ctx, KC_KRYLOV);
         k_bminus<double><<<nblk(nv, 256), 256, 0, st>>>(b, tmp64, nv);

@@ -22,6 +22,7 @@
 // lengths; tbc.cu instantiates the FP64 operator, tbc_f32.cu the FP32 one.
 #pragma once
 #include <algorithm>
+#include <type_traits>
 
 #include "common.cuh"
 #include "fft.cuh"
@@ -181,31 +182,10 @@ __global__ void TBC_BOUNDS k_tbcA(const C<T>* __restrict__ x, C<T>* __restrict__
 // F(G)(|j1|, |j2|)/(Lx Ly), then the inverse torus transform along x1 at the
 // nodes p = 0..nx:  sum_j1 Y(j1) e^{2 pi i j1 p/Px} = Z_0(p) + e^{2 pi i p/Px} Z_1(p),
 // Z_r = inverse transform of length Px/2 of Y(2t + r) over t.
-// Fused: the column gather (first read of the forward transform), the parity
-// products (its last write), the kernel-table products with the move of
-// t to slot t mod Px/2 (last write of the first inverse transforms).
-
-// column j0 + l of Vy along k1, mirrored to the input n of a line of length Px
-template <typename T, int LNX>
-struct GatherB {
-  const C<T>* src;                // this field's [nx][Py] block
-  int j0, Py;
-  bool xcos;
-  __device__ __forceinline__ C<T> ld(int l, const C<T>*, int n) const {
-    constexpr int nx = 1 << LNX, Px = 4 * nx;
-    const int j = j0 + l;
-    if (j >= Py) return czero<T>();
-    if (n < nx) {
-      if (n == 0) return xcos ? cscale<T>(src[j], (T)2) : czero<T>();
-      return src[(size_t)n * Py + j];
-    }
-    if (n > Px - nx) {
-      const C<T> c = src[(size_t)(Px - n) * Py + j];
-      return xcos ? c : mk<T>(-c.x, -c.y);
-    }
-    return czero<T>();
-  }
-};
+// Fused: the parity products (last write of the forward transform), the
+// kernel-table products with the move of t to slot t mod Px/2 (last write of
+// the first inverse transforms).  The column gather stays a cooperative pass:
+// as a per-line first read it would load one element per 32-byte sector.
 
 // last write of the first inverse transforms of pass B: output t (k = t mod
 // Px) of line (r, l), |t| < Px/4, times the kernel table at (|2t + r|, |j2|),
@@ -246,11 +226,31 @@ __global__ void TBC_BOUNDS k_tbcB(const C<T>* __restrict__ Vy, C<T>* __restrict_
   const int j0 = blockIdx.x * L;
   const int tid = threadIdx.x, nthr = blockDim.x;
   const bool xcos = (f != 1);
-  ParityProducts<T, GatherB<T, LNX>> fwd;
-  fwd.src = Vy + (size_t)(d * 3 + f) * nx * Py;
-  fwd.j0 = j0;
-  fwd.Py = Py;
-  fwd.xcos = xcos;
+  // cooperative, coalesced gather of the L columns (consecutive threads take
+  // consecutive columns of a row); the mirrored lines cover every slot but
+  // [nx, Px - nx], which is cleared
+  {
+    const C<T>* src = Vy + (size_t)(d * 3 + f) * nx * Py;
+#pragma unroll 4
+    for (int idx = tid; idx < L * nx; idx += nthr) {
+      const int k1 = idx >> lL, l = idx & (L - 1);
+      const int j = j0 + l;
+      const C<T> c = j < Py ? src[(size_t)k1 * Py + j] : czero<T>();
+      C<T>* line = buf + (size_t)l * ls;
+      if (k1 == 0) {
+        line[0] = xcos ? cscale<T>(c, (T)2) : czero<T>();
+      } else {
+        line[pidx(k1)] = c;
+        line[pidx(Px - k1)] = xcos ? c : mk<T>(-c.x, -c.y);
+      }
+    }
+    for (int idx = tid; idx < L * (2 * nx + 1); idx += nthr) {
+      const int l = idx / (2 * nx + 1), k = nx + idx - l * (2 * nx + 1);
+      buf[(size_t)l * ls + pidx(k)] = czero<T>();
+    }
+    __syncthreads();
+  }
+  ParityProducts<T, LineId<T>> fwd;
   fwd.eh = xcos ? eh_c : eh_s;
   fwd.P = Px;
   fwd.L = L;
@@ -475,6 +475,13 @@ template <typename K> static cavity_status smem_once(cavity_ctx* ctx, K kern, bo
   return CAVITY_OK;
 }
 
+// launch-accounting class of pass `k` (0..4: A, B, C, D, combine) for type T
+template <typename T> static int kclass(int k) {
+  if (sizeof(C<T>) == 8) return KC_TBC_A32 + k;
+  if (std::is_same<T, double>::value) return KC_TBC_A64 + k;
+  return KC_TBC_AP + k;
+}
+
 template <typename T>
 cavity_status launch_apply(cavity_ctx* ctx, int ndir, const C<T>* x, C<T>* y, void* work,
                            long long ystride) {
@@ -494,13 +501,12 @@ cavity_status launch_apply(cavity_ctx* ctx, int ndir, const C<T>* x, C<T>* y, vo
   cudaStream_t st = ctx->stream;
   const C<T>* tw = Tabs<T>::tw(ctx);
   const int T_ = LINES_THREADS;
-  constexpr bool f64 = sizeof(T) == 8;
   CKS(dispatch_log<CAV_LOG_MIN, CAV_LOG_MAX>(g.lny, [&](auto c) -> cavity_status {
     constexpr int LN = decltype(c)::value;
     constexpr int L = pairs_per_cta<T>(4 << LN);
     static bool done = false;
     CKS(smem_once(ctx, k_tbcA<T, LN>, done));
-    KScope ks_(ctx, f64 ? KC_TBC_A64 : KC_TBC_A32);
+    KScope ks_(ctx, kclass<T>(0));
     k_tbcA<T, LN><<<dim3((g.nx + L - 1) / L, 3, ndir), T_, smem_a<T>(g.ny), st>>>(
         x, R1, p, tw, Tabs<T>::ey(ctx, 0), Tabs<T>::ey(ctx, 1));
     return CAVITY_OK;
@@ -510,7 +516,7 @@ cavity_status launch_apply(cavity_ctx* ctx, int ndir, const C<T>* x, C<T>* y, vo
     constexpr int L = pairs_per_cta<T>(4 << LN);
     static bool done = false;
     CKS(smem_once(ctx, k_tbcB<T, LN>, done));
-    KScope ks_(ctx, f64 ? KC_TBC_B64 : KC_TBC_B32);
+    KScope ks_(ctx, kclass<T>(1));
     k_tbcB<T, LN><<<dim3((g.Py + L - 1) / L, 3, ndir), T_, smem_b<T>(g.nx), st>>>(
         R1, R2, p, tw, Tabs<T>::ex(ctx, 0), Tabs<T>::ex(ctx, 1), Tabs<T>::kh(ctx));
     return CAVITY_OK;
@@ -520,7 +526,7 @@ cavity_status launch_apply(cavity_ctx* ctx, int ndir, const C<T>* x, C<T>* y, vo
     constexpr int L = lines_per_cta<T>(4 << LN);
     static bool done = false;
     CKS(smem_once(ctx, k_tbcC<T, LN>, done));
-    KScope ks_(ctx, f64 ? KC_TBC_C64 : KC_TBC_C32);
+    KScope ks_(ctx, kclass<T>(2));
     k_tbcC<T, LN><<<dim3((g.nx + 1 + L - 1) / L, 3, ndir), T_, smem_c<T>(g.ny), st>>>(R2, R1, p, tw);
     return CAVITY_OK;
   }));
@@ -529,12 +535,12 @@ cavity_status launch_apply(cavity_ctx* ctx, int ndir, const C<T>* x, C<T>* y, vo
     constexpr int L = lines_per_cta<T>(2 << LN);
     static bool done = false;
     CKS(smem_once(ctx, k_tbcD<T, LN>, done));
-    KScope ks_(ctx, f64 ? KC_TBC_D64 : KC_TBC_D32);
+    KScope ks_(ctx, kclass<T>(3));
     k_tbcD<T, LN><<<dim3((g.ny + 1 + L - 1) / L, 3, ndir), T_, smem_d<T>(g.nx), st>>>(R1, R2, p, tw);
     return CAVITY_OK;
   }));
   {
-    KScope ks_(ctx, f64 ? KC_COMB64 : KC_COMB32);
+    KScope ks_(ctx, kclass<T>(4));
     k_combine<T><<<dim3((g.nx * g.ny + 255) / 256, ndir), 256, 0, st>>>(x, R2, Tabs<T>::top(ctx), y,
                                                                        ystride, p);
   }

@@ -159,6 +159,10 @@ def test_operator_and_field_every_size(gb, nx, ny):
         assert rel(y, ref) < tol, (prec, rel(y, ref))
         fl = g.field(torch.tensor(x, dtype=torch.complex128, device="cuda")).cpu().numpy()
         assert rel(fl, F) < tol, (prec, rel(fl, F))
+        if prec == "mixed":
+            # the residual operator of the mixed solve: pair-of-FP32 arithmetic
+            yp = g.apply(torch.tensor(x, device="cuda"), "pair32").cpu().numpy()
+            assert rel(yp, ref) < 1e-11, rel(yp, ref)
 
 
 @pytest.mark.parametrize("case", list(CASES))
