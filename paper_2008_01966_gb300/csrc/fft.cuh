@@ -282,8 +282,20 @@ __device__ __forceinline__ void fft_warp(C<T>* line, int n, int logn, int l, boo
   if (active) {
     dft_nat<T, INV, RV>(v);
     const int shift = twlog - logn;
+    // w^{l k1} = w^{8 g l} w^{i l} for k1 = 8 g + i: 7 + RV/8 - 1 table reads
+    // instead of RV - 1 (each product adds at most ~2 ulp)
+    C<T> wi[8];
 #pragma unroll
-    for (int k1 = 1; k1 < RV; ++k1) v[k1] = cmul<T>(v[k1], twid<T, INV>(tw, ((l * k1) & (n - 1)) << shift));
+    for (int i = 1; i < 8 && i < RV; ++i) wi[i] = twid<T, INV>(tw, ((l * i) & (n - 1)) << shift);
+#pragma unroll
+    for (int i = 1; i < 8 && i < RV; ++i) v[i] = cmul<T>(v[i], wi[i]);
+#pragma unroll
+    for (int g = 1; g < RV / 8; ++g) {
+      const C<T> wg = twid<T, INV>(tw, ((l * 8 * g) & (n - 1)) << shift);
+      v[8 * g] = cmul<T>(v[8 * g], wg);
+#pragma unroll
+      for (int i = 1; i < 8; ++i) v[8 * g + i] = cmul<T>(v[8 * g + i], cmul<T>(wg, wi[i]));
+    }
 #pragma unroll
     for (int k1 = 0; k1 < RV; ++k1) line[k1 * (LW + 1) + l] = v[k1];
   }

@@ -98,10 +98,24 @@ __global__ void __launch_bounds__(256) k_mdot_partial(const C<T>* __restrict__ V
       // would cost more than the FP32 products themselves.)
       const C<T>* v = V + (size_t)d * vs + (size_t)i * nap + e0;
       T ar = 0, ai = 0;
-      for (int e = sub * 32 + lane; e < ne; e += nsub * 32) {
-        const C<T> a = v[e], b = sw[e];
-        ar += a.x * b.x + a.y * b.y;
-        ai += a.x * b.y - a.y * b.x;
+      if (nsub == 1 && ne == MDOT_CHUNK) {
+        // full chunk, one warp per vector: 8 loads in flight, 4 partial sums
+        T pr[4] = {0, 0, 0, 0}, pi[4] = {0, 0, 0, 0};
+#pragma unroll 8
+        for (int k = 0; k < MDOT_CHUNK / 32; ++k) {
+          const int e = lane + 32 * k;
+          const C<T> a = v[e], b = sw[e];
+          pr[k & 3] += a.x * b.x + a.y * b.y;
+          pi[k & 3] += a.x * b.y - a.y * b.x;
+        }
+        ar = (pr[0] + pr[1]) + (pr[2] + pr[3]);
+        ai = (pi[0] + pi[1]) + (pi[2] + pi[3]);
+      } else {
+        for (int e = sub * 32 + lane; e < ne; e += nsub * 32) {
+          const C<T> a = v[e], b = sw[e];
+          ar += a.x * b.x + a.y * b.y;
+          ai += a.x * b.y - a.y * b.x;
+        }
       }
       for (int off = 16; off > 0; off >>= 1) {
         ar += __shfl_xor_sync(0xffffffffu, ar, off);
@@ -158,12 +172,12 @@ __global__ void __launch_bounds__(256) k_basis_axpy(const C<T>* __restrict__ V, 
   const C<T>* v = V + (size_t)d * vs + e;
   T ar = 0, ai = 0;
   int i = 0;
-  for (; i + 4 <= cnt; i += 4) {
-    C<T> a[4];
+  for (; i + 8 <= cnt; i += 8) {
+    C<T> a[8];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) a[k] = v[(size_t)(i + k) * nap];
+    for (int k = 0; k < 8; ++k) a[k] = v[(size_t)(i + k) * nap];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < 8; ++k) {
       const C<T> b = cf[i + k];
       ar += a[k].x * b.x - a[k].y * b.y;
       ai += a[k].x * b.y + a[k].y * b.x;

@@ -41,6 +41,30 @@ static DirPar dir_params(double kappa0, double t, double f, double al) {
 // fac layout per direction: [cx (nx) | sx (nx) | cy (ny+1) | sy (ny+1)]
 // cx[m] = sum_p w_p cos(m pi p/nx) e^{i a1 x_p}, m = 0..nx-1;  sx[m] likewise
 // with sin (index m, m = 1..nx-1 used); cy, sy over n = 0..ny.
+// With cos = (e^{+} + e^{-})/2 both reduce to the trapezoid sum of a geometric
+// progression, in closed form:
+//   T(th) = 1/2 + z + ... + z^{N-1} + z^N/2 = (i/2) cot(th/2) (1 - z^N),  z = e^{i th},
+//   th = (alpha side +- pi m)/N,  z^N = (-1)^m e^{i alpha side};
+// where |sin(th/2)| < 1e-3 the progression is summed term by term instead
+// (the closed form would cancel there).
+__device__ double2 trap_progression(double th, int N, double2 zN) {
+  double s, c;
+  sincos(0.5 * th, &s, &c);
+  if (fabs(s) < 1e-3) {
+    double sr = 0, si = 0;
+    for (int p = 0; p <= N; ++p) {
+      const double w = (p == 0 || p == N) ? 0.5 : 1.0;
+      double es, ec;
+      sincos(th * p, &es, &ec);
+      sr += w * ec;
+      si += w * es;
+    }
+    return make_double2(sr, si);
+  }
+  const double ct = 0.5 * c / s;
+  return make_double2(ct * zN.y, ct * (1.0 - zN.x));
+}
+
 __global__ void k_rhs_factors(const DirPar* __restrict__ dp, double2* __restrict__ fac, int nx,
                               int ny, double a, double b) {
   const int d = blockIdx.y, which = blockIdx.z;
@@ -52,20 +76,18 @@ __global__ void k_rhs_factors(const DirPar* __restrict__ dp, double2* __restrict
   const double al = xdir ? dp[d].a1 : dp[d].a2;
   const bool isc = (which == 0 || which == 2);
   const int off = which == 0 ? 0 : which == 1 ? nx : which == 2 ? 2 * nx : 2 * nx + ny + 1;
+  double es, ec;
+  sincos(al * side, &es, &ec);
+  const double w = side / nint;
   for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < count; m += gridDim.x * blockDim.x) {
-    double sr = 0, si = 0;
-    for (int p = 0; p <= nint; ++p) {
-      double w = side / nint;
-      if (p == 0 || p == nint) w *= 0.5;
-      double ts, tc;
-      sincospi((double)((long long)m * p % (2 * nint)) / nint, &ts, &tc);
-      double tr = isc ? tc : ts;
-      double es, ec;
-      sincos(al * (p * side / nint), &es, &ec);
-      sr += w * tr * ec;
-      si += w * tr * es;
-    }
-    fac[(size_t)d * per + off + m] = make_double2(sr, si);
+    const double sg = (m & 1) ? -1.0 : 1.0;
+    const double2 zN = make_double2(sg * ec, sg * es);
+    const double2 gp = trap_progression((al * side + M_PI * m) / nint, nint, zN);
+    const double2 gm = trap_progression((al * side - M_PI * m) / nint, nint, zN);
+    double2 r;
+    if (isc) r = make_double2(0.5 * w * (gp.x + gm.x), 0.5 * w * (gp.y + gm.y));
+    else r = make_double2(0.5 * w * (gp.y - gm.y), -0.5 * w * (gp.x - gm.x));
+    fac[(size_t)d * per + off + m] = r;
   }
 }
 

@@ -192,7 +192,7 @@ __global__ void TBC_BOUNDS k_tbcA(const C<T>* __restrict__ x, C<T>* __restrict__
 // written to slot t mod Px/2 (other outputs are not needed)
 template <typename T, int LNX>
 struct KhatB : LineId<T> {
-  const C<T>* kh;                 // [j2 < Py/2][j1 < Px/2]
+  const C<T>* kh;                 // rows |j2| of the block's columns, [l][j1 < Px/2]
   int j0, Py, L;
   __device__ __forceinline__ void st(int lr, C<T>* line, int k, C<T> v) const {
     constexpr int Px = 4 << LNX, hp = Px / 2, qp = Px / 4;
@@ -206,8 +206,7 @@ struct KhatB : LineId<T> {
     C<T> o = czero<T>();
     if (j1 != -hp && j < Py && j != Py / 2) {
       const int j1a = j1 < 0 ? -j1 : j1;
-      const int j2a = j < Py / 2 ? j : Py - j;
-      o = cmul<T>(v, kh[(size_t)j2a * hp + j1a]);
+      o = cmul<T>(v, kh[l * hp + j1a]);
     }
     line[pidx(u)] = o;
   }
@@ -226,6 +225,21 @@ __global__ void TBC_BOUNDS k_tbcB(const C<T>* __restrict__ Vy, C<T>* __restrict_
   const int j0 = blockIdx.x * L;
   const int tid = threadIdx.x, nthr = blockDim.x;
   const bool xcos = (f != 1);
+  // shared memory: 2L lines, then the two parity kernels [2][Px], then the
+  // kernel-table rows |j2| of the L columns [L][Px/2] (staged once per block,
+  // so the fused products read shared memory instead of waiting on loads)
+  C<T>* eh_sm = buf + (size_t)2 * L * ls;
+  C<T>* kh_sm = eh_sm + 2 * Px;
+  {
+    const C<T>* eh = xcos ? eh_c : eh_s;
+    for (int t = tid; t < 2 * Px; t += nthr) eh_sm[t] = eh[t];
+    for (int idx = tid; idx < L * (Px / 2); idx += nthr) {
+      const int l = idx >> (LPX - 1), j1 = idx & (Px / 2 - 1);
+      const int j = j0 + l;
+      const int j2a = j < Py / 2 ? j : Py - j;
+      kh_sm[idx] = (j < Py && j != Py / 2) ? kh[(size_t)j2a * (Px / 2) + j1] : czero<T>();
+    }
+  }
   // cooperative, coalesced gather of the L columns (consecutive threads take
   // consecutive columns of a row); the mirrored lines cover every slot but
   // [nx, Px - nx], which is cleared
@@ -251,14 +265,14 @@ __global__ void TBC_BOUNDS k_tbcB(const C<T>* __restrict__ Vy, C<T>* __restrict_
     __syncthreads();
   }
   ParityProducts<T, LineId<T>> fwd;
-  fwd.eh = xcos ? eh_c : eh_s;
+  fwd.eh = eh_sm;
   fwd.P = Px;
   fwd.L = L;
   fwd.ls = ls;
   fwd.buf = buf;
   fft_lines<T, false, LPX>(buf, ls, L, tw, p.twlog, fwd);
   KhatB<T, LNX> kb;
-  kb.kh = kh;
+  kb.kh = kh_sm;
   kb.j0 = j0;
   kb.Py = Py;
   kb.L = L;
@@ -461,7 +475,10 @@ template <> struct Tabs<float> {
 
 // shared memory of each pass (bytes) for the grid sizes of g
 template <typename T> static size_t smem_a(int ny) { return sizeof(C<T>) * 2 * pairs_per_cta<T>(4 * ny) * (size_t)padded_len(4 * ny); }
-template <typename T> static size_t smem_b(int nx) { return sizeof(C<T>) * 2 * pairs_per_cta<T>(4 * nx) * (size_t)padded_len(4 * nx); }
+template <typename T> static size_t smem_b(int nx) {
+  const size_t L = pairs_per_cta<T>(4 * nx);
+  return sizeof(C<T>) * (2 * L * (size_t)padded_len(4 * nx) + 2 * 4 * (size_t)nx + L * 2 * (size_t)nx);
+}
 template <typename T> static size_t smem_c(int ny) { return sizeof(C<T>) * lines_per_cta<T>(4 * ny) * (size_t)padded_len(4 * ny); }
 template <typename T> static size_t smem_d(int nx) { return sizeof(C<T>) * lines_per_cta<T>(2 * nx) * (size_t)padded_len(2 * nx); }
 
