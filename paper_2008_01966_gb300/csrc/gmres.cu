@@ -135,18 +135,22 @@ __global__ void __launch_bounds__(256) k_mdot_partial(const C<T>* __restrict__ V
   }
 }
 
+// h[d][i] = sum over chunks of the partials, in chunk order within each lane
+// and a fixed shuffle tree across lanes: one warp per (i, d), grid (cnt, ndir)
 __global__ void k_mdot_final(const double2* __restrict__ part, double2* __restrict__ h, int hstride,
                              int cnt, int nchunk) {
-  const int d = blockIdx.x;
-  for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
-    double a = 0, b = 0;
-    for (int c = 0; c < nchunk; ++c) {
-      const double2 v = part[((size_t)d * nchunk + c) * cnt + i];
-      a += v.x;
-      b += v.y;
-    }
-    h[(size_t)d * hstride + i] = make_double2(a, b);
+  const int i = blockIdx.x, d = blockIdx.y, lane = threadIdx.x;
+  double a = 0, b = 0;
+  for (int c = lane; c < nchunk; c += 32) {
+    const double2 v = part[((size_t)d * nchunk + c) * cnt + i];
+    a += v.x;
+    b += v.y;
   }
+  for (int off = 16; off > 0; off >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, off);
+    b += __shfl_xor_sync(0xffffffffu, b, off);
+  }
+  if (lane == 0) h[(size_t)d * hstride + i] = make_double2(a, b);
 }
 
 // w[d][e] += sgn * sum_{i<cnt} V[d*vs + i*nap + e] c[d*cstride + i]
@@ -327,7 +331,7 @@ static void mdot(cavity_ctx* ctx, const C<T>* V, long long vs, const C<T>* w, lo
   }
   {
     KScope ks_(ctx, KC_KRYLOV);
-    k_mdot_final<<<ndir, 64, 0, ctx->stream>>>(part, out, ostride, cnt, nchunk);
+    k_mdot_final<<<dim3(cnt, ndir), 32, 0, ctx->stream>>>(part, out, ostride, cnt, nchunk);
   }
 }
 
