@@ -79,7 +79,16 @@ typedef struct {
   int gmres_max_iter;    /* total inner iterations; 0 -> 400                   */
   double pivot_tol;      /* |pivot| below pivot_tol * max(1,|sigma-2|) is       */
                          /* reported as CAVITY_ESINGULAR; 0 -> 1e-12            */
+  int khat_scheme;       /* kernel table F(G) of Sec. 5.2:                      */
+                         /* CAVITY_KHAT_QUADRATURE (0): Gauss-Legendre, ~1e-13  */
+                         /* CAVITY_KHAT_PAPER (1): the paper's scheme -- the    */
+                         /*   same quadrature where 2 pi rho R <= 20 pi sqrt 2, */
+                         /*   else the closed-form integral to infinity minus   */
+                         /*   the asymptotic tail (two-term J0 and Fresnel      */
+                         /*   expansions); an approximation, inaccurate near    */
+                         /*   2 pi rho = kappa0                                 */
 } cavity_desc;
+enum { CAVITY_KHAT_QUADRATURE = 0, CAVITY_KHAT_PAPER = 1 };
 
 /* Create a context for one cavity geometry and grid.  `cuda_stream` is a
  * cudaStream_t (NULL = legacy default stream).  Validates the descriptor;

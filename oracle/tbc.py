@@ -35,7 +35,7 @@ Each step is a dense matrix here (numpy matmul as the only library step).
 import numpy as np
 
 from .geometry import Cavity
-from .khat import khat
+from .khat import khat, khat_paper
 
 
 def freq_index(P):
@@ -92,8 +92,11 @@ class TBCOperator:
     out[m, n] = sum_k I^{mn}_k C[k] over the same index ranges.
     """
 
-    def __init__(self, cav: Cavity, kh=None):
+    def __init__(self, cav: Cavity, kh=None, scheme='quadrature'):
+        """scheme: 'quadrature' (the reference F(G)) or 'paper' (the
+        approximate large-frequency scheme of Sec. 5.2, `khat_paper`)."""
         self.cav = cav
+        self._khat = khat if scheme == 'quadrature' else khat_paper
         a, b, nx, ny, pad = cav.a, cav.b, cav.nx, cav.ny, cav.pad
         self.Px, self.Py = pad * nx, pad * ny
         self.jx, self.jy = freq_index(self.Px), freq_index(self.Py)
@@ -127,12 +130,12 @@ class TBCOperator:
         if self.Lx == self.Ly:
             key = ax[:, None] ** 2 + ay[None, :] ** 2
             uniq, inv = np.unique(key, return_inverse=True)
-            vals = khat(np.sqrt(uniq) / self.Lx, self.cav.kappa0, R)
+            vals = self._khat(np.sqrt(uniq) / self.Lx, self.cav.kappa0, R)
             return vals[inv].reshape(key.shape)
         ux, ix = np.unique(ax, return_inverse=True)
         uy, iy = np.unique(ay, return_inverse=True)
         rho = np.sqrt((ux[:, None] / self.Lx) ** 2 + (uy[None, :] / self.Ly) ** 2)
-        q = khat(rho, self.cav.kappa0, R)
+        q = self._khat(rho, self.cav.kappa0, R)
         return q[ix][:, iy]
 
     def factors(self, kind):

@@ -33,7 +33,8 @@ class CavityDesc(ctypes.Structure):
                 ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
                 ("precision", ctypes.c_int), ("pad_factor", ctypes.c_int),
                 ("gmres_tol", ctypes.c_double), ("gmres_restart", ctypes.c_int),
-                ("gmres_max_iter", ctypes.c_int), ("pivot_tol", ctypes.c_double)]
+                ("gmres_max_iter", ctypes.c_int), ("pivot_tol", ctypes.c_double),
+                ("khat_scheme", ctypes.c_int)]
 
 
 class CavityError(RuntimeError):

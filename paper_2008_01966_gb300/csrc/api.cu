@@ -40,6 +40,8 @@ extern "C" cavity_status cavity_setup(const cavity_desc* desc, void* cuda_stream
   if (d.gmres_tol < 0 || d.gmres_restart < 0 || d.gmres_max_iter < 0 || d.pivot_tol < 0)
     return bad("negative solver parameter");
   if (d.gmres_restart > 120) return bad("gmres_restart must be at most 120");
+  if (d.khat_scheme != CAVITY_KHAT_QUADRATURE && d.khat_scheme != CAVITY_KHAT_PAPER)
+    return bad("khat_scheme must be CAVITY_KHAT_QUADRATURE or CAVITY_KHAT_PAPER");
   cavity_ctx* ctx = new cavity_ctx();
   ctx->desc = d;
   if (ctx->desc.pad_factor == 0) ctx->desc.pad_factor = 4;

@@ -101,8 +101,64 @@ __device__ double bessel_j0(double x) {
   return sqrt(2.0 / (M_PI * x)) * (P * cchi - Q * schi);
 }
 
+// ---- the paper's large-frequency scheme (CAVITY_KHAT_PAPER), Sec. 5.2:
+//   int_0^R J0(c r) e^{i k r} dr = int_0^inf - (1/c) int_{cR}^inf J0(z) e^{i k z/c} dz,
+// int_0^inf = 1/sqrt(c^2 - k^2) (c > k) or i/sqrt(k^2 - c^2) (c < k); in the tail
+// J0(z) ~ sqrt(2/(pi z)) (cos(z - pi/4) + sin(z - pi/4)/(8z)), the exponentials
+// e^{+-i(z - pi/4)} combine with e^{i k z/c} into
+//   A(p) = int_Z^inf e^{ipz} z^{-1/2} dz = sqrt(pi/(2|p|)) (1 + i - 2C(T) - 2iS(T)),
+//   T = sqrt(2|p|Z/pi) (complex conjugate for p < 0), and
+//   B(p) = int_Z^inf e^{ipz} z^{-3/2} dz = 2 e^{ipZ}/sqrt(Z) + 2ip A(p),
+// p = k/c +- 1, with the Fresnel integrals C, S from their two-term asymptotic
+// expansions.  (The paper prints 1/(c^2 - k^2) for the integral to infinity and
+// sqrt(pi)/(2p) in front of A; the forms above are the corrected ones.)
+#define KHAT_PAPER_CR (20.0 * M_PI * 1.41421356237309504880)
+
+__device__ double2 kp_tail_half(double p, double Z) {
+  const double ap = fabs(p);
+  const double T = sqrt(2.0 * ap * Z / M_PI);
+  const double u = M_PI * T * T;
+  const double f = (1.0 - 3.0 / (u * u)) / (M_PI * T);
+  const double g = (1.0 - 15.0 / (u * u)) / (M_PI * M_PI * T * T * T);
+  double sp, cp;
+  sincos(0.5 * u, &sp, &cp);
+  const double C = 0.5 + f * sp - g * cp;
+  const double S = 0.5 - f * cp - g * sp;
+  const double pre = sqrt(M_PI / (2.0 * ap));
+  double2 v = make_double2(pre * (1.0 - 2.0 * C), pre * (1.0 - 2.0 * S));
+  if (p < 0) v.y = -v.y;
+  return v;
+}
+
+__device__ double2 kp_tail_3half(double p, double Z) {
+  const double2 A = kp_tail_half(p, Z);
+  double s, c;
+  sincos(p * Z, &s, &c);
+  const double w = 2.0 / sqrt(Z);
+  // 2 e^{ipZ}/sqrt(Z) + 2 i p A
+  return make_double2(w * c - 2.0 * p * A.y, w * s + 2.0 * p * A.x);
+}
+
+__device__ double2 khat_paper_tail(double c, double k, double R) {
+  const double d = c * c - k * k;
+  const double2 inf = d > 0 ? make_double2(1.0 / sqrt(d), 0.0) : make_double2(0.0, 1.0 / sqrt(-d));
+  const double Z = c * R;
+  const double pp = k / c + 1.0, pm = k / c - 1.0;
+  const double r2 = 0.70710678118654752440;
+  const double2 e4 = make_double2(r2, -r2), e4c = make_double2(r2, r2);  // e^{-i pi/4}, e^{+i pi/4}
+  const double2 ap = kp_tail_half(pp, Z), am = kp_tail_half(pm, Z);
+  const double2 bp = kp_tail_3half(pp, Z), bm = kp_tail_3half(pm, Z);
+  const double2 cosp = cscale<double>(cadd<double>(cmul<double>(e4, ap), cmul<double>(e4c, am)), 0.5);
+  const double2 dsin = csub<double>(cmul<double>(e4, bp), cmul<double>(e4c, bm));
+  const double2 sinp = make_double2(0.5 * dsin.y, -0.5 * dsin.x);     // / (2i)
+  const double2 tail = cscale<double>(cadd<double>(cosp, cscale<double>(sinp, 0.125)),
+                                      sqrt(2.0 / M_PI) / c);
+  return cscale<double>(csub<double>(inf, tail), 0.5);
+}
+
 __global__ void k_khat(double2* __restrict__ raw, double2* __restrict__ s64, float2* __restrict__ s32,
-                       int hx, int hy, double Lx, double Ly, double kappa0, double R, double scale) {
+                       int hx, int hy, double Lx, double Ly, double kappa0, double R, double scale,
+                       int scheme) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (warp >= hx * hy) return;
@@ -110,6 +166,16 @@ __global__ void k_khat(double2* __restrict__ raw, double2* __restrict__ s64, flo
   const double r1 = j1 / Lx, r2 = j2 / Ly;
   const double rho = sqrt(r1 * r1 + r2 * r2);
   const double c = 2.0 * M_PI * rho;
+  if (scheme == CAVITY_KHAT_PAPER && c * R > KHAT_PAPER_CR) {
+    if (lane == 0) {
+      const double2 v = khat_paper_tail(c, kappa0, R);
+      raw[(size_t)j1 * hy + j2] = v;
+      const size_t o = (size_t)j2 * hx + j1;
+      s64[o] = make_double2(v.x * scale, v.y * scale);
+      s32[o] = make_float2((float)(v.x * scale), (float)(v.y * scale));
+    }
+    return;
+  }
   const double omega = c + fabs(kappa0);
   int npan = (int)ceil(omega * R / M_PI);
   if (npan < 1) npan = 1;
@@ -167,7 +233,7 @@ cavity_status launch_khat(cavity_ctx* ctx, double kappa0) {
     KScope ks_(ctx, KC_SETUP);
     k_khat<<<(unsigned)((threads + 255) / 256), 256, 0, ctx->stream>>>(
         ctx->khat_raw, ctx->khat64, ctx->khat32, hx, hy, g.Lx, g.Ly, kappa0, g.R,
-        1.0 / (g.Lx * g.Ly));
+        1.0 / (g.Lx * g.Ly), ctx->desc.khat_scheme);
   }
   CK(cudaGetLastError());
   return CAVITY_OK;

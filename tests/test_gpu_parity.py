@@ -18,7 +18,7 @@ from oracle.aperture import ApertureSystem
 from oracle.excitation import rhs as oracle_rhs
 from oracle.field import field as oracle_field
 from oracle.geometry import Cavity as OCavity, Layer
-from oracle.khat import khat as oracle_khat
+from oracle.khat import khat as oracle_khat, khat_paper as oracle_khat_paper
 from oracle.rcs import backscatter
 from oracle.tbc import TBCOperator
 from oracle.zsystem import Profiles
@@ -101,6 +101,46 @@ def test_kernel_table_matches_quadrature(gb, case):
     rho = np.sqrt((j1 / Lx) ** 2 + (j2 / Ly) ** 2)
     ref = oracle_khat(rho, w['kappa0'], np.sqrt(2) * max(w['a'], w['b']))
     assert np.abs(kh - ref).max() < 1e-13 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("nx,kappa0", [(64, 2 * np.pi * 6.4), (32, 2 * np.pi * 15.3)])
+def test_kernel_table_paper_scheme(gb, nx, kappa0):
+    """f1: the table by the paper's Sec. 5.2 scheme (khat_scheme="paper")
+    against the oracle's restatement of the same scheme.  At 64 x 64 the box
+    reaches c R = 400 with the ridge 2 pi rho = kappa0 in the quadrature range;
+    at 32 x 32 with kappa0 = 30.6 pi the ridge lies in the asymptotic range."""
+    w = dict(a=1.0, b=1.0, c=0.5, nx=nx, ny=nx, nz=8, layers=[(8, 1.0 + 0j)])
+    g = gcav(gb, w, khat_scheme="paper")
+    g.prepare(kappa0, w['layers'])
+    kh = g.export_khat().cpu().numpy()
+    j1 = np.arange(2 * nx)[:, None]
+    j2 = np.arange(2 * nx)[None, :]
+    rho = np.sqrt((j1 / 4.0) ** 2 + (j2 / 4.0) ** 2)
+    ref = oracle_khat_paper(rho, kappa0, np.sqrt(2.0))
+    # the scheme's integral to infinity, 1/sqrt(c^2 - kappa0^2), amplifies the
+    # rounding of c by c^2/|c^2 - kappa0^2| next to the ridge
+    c = 2 * np.pi * rho
+    cond = 1.0 + c * c / np.abs(c * c - kappa0 ** 2)
+    assert np.all(np.abs(kh - ref) <= 1e-12 * cond * np.abs(ref)), \
+        (np.abs(kh - ref) / (cond * np.abs(ref))).max()
+
+
+def test_solve_with_paper_scheme(gb):
+    """f1: whole FP64 solve with the paper's table against the oracle's direct
+    solve with the same table (64 x 64, ten points per wavelength: the
+    asymptotic range starts beyond the ridge)."""
+    w = dict(a=1.0, b=1.0, c=0.5, nx=64, ny=64, nz=12, kappa0=2 * np.pi * 6.4,
+             layers=[(12, 1.0 + 0j)])
+    cav = ocav(w)
+    sysm = ApertureSystem(cav, tbc=TBCOperator(cav, scheme='paper'))
+    th, ph, al = workloads.directions(2, 12)
+    B = np.array([oracle_rhs(cav, t, p, a) for t, p, a in zip(th, ph, al)])
+    X, ores = sysm.solve_gmres(B)
+    assert np.all(ores < 1e-12)
+    g = gcav(gb, w, gmres_tol=1e-13, khat_scheme="paper")
+    ap, fl, it, res = g.solve(w['kappa0'], w['layers'], th, ph, al, field=False)
+    for d in range(2):
+        assert rel(ap[d].cpu().numpy(), X[d]) < 1e-10
 
 
 def test_rhs_matches_trapezoid_tests(gb):
