@@ -9,7 +9,11 @@ coarse (16 points per wavelength horizontally) so the oracle finishes in
 seconds; lengths in wavelengths (kappa0 = 2 pi).
 
   Example 1 (small): a = b = 1, c = 3, empty cavity
-  Example 2:         a = 1, b = c = 0.25, eps_r = 7 + 1.5i
+  Example 2:         a = 1, b = c = 0.25, eps_r = 7 + 1.5i.  Under the discrete
+                     rule of the TBC integrals (period 4 a x 4 b, truncation
+                     radius sqrt(2) max(a, b)) a 4:1 aperture wraps around the
+                     short period, so setup rejects it (checked below); the
+                     fill is run in a square aperture a = b = 0.5 instead
   Example 3:         a = b = 1, top layer eps_r = 7 + 1.5i of depth 1 over
                      eps_r = 3 + 0.05i of depth 2
 """
@@ -28,7 +32,7 @@ pytestmark = pytest.mark.gpu
 
 EXAMPLES = {
     "example1_small": dict(a=1.0, b=1.0, c=3.0, nx=16, ny=16, nz=48, layers=[(48, 1.0 + 0j)]),
-    "example2": dict(a=1.0, b=0.25, c=0.25, nx=16, ny=4, nz=4, layers=[(4, 7 + 1.5j)]),
+    "example2_fill": dict(a=0.5, b=0.5, c=0.25, nx=8, ny=8, nz=4, layers=[(4, 7 + 1.5j)]),
     "example3": dict(a=1.0, b=1.0, c=3.0, nx=16, ny=16, nz=48,
                      layers=[(16, 7 + 1.5j), (32, 3 + 0.05j)]),
 }
@@ -65,3 +69,11 @@ def test_example_rcs_sweep(gb, name):
         # relative to the sweep's peak (the curves have deep nulls)
         assert np.abs(sig - ref).max() <= 1e-9 * ref.max(), (pol, np.abs(sig - ref).max() / ref.max())
         assert np.all(np.isfinite(sig)) and np.all(sig >= 0)
+
+
+def test_example2_aperture_is_rejected(gb):
+    """The 4:1 aperture of Example 2 needs a longer period along its short side
+    than the operator's fixed 4 a x 4 b: setup returns CAVITY_EINVAL."""
+    with pytest.raises(gb.CavityError) as e:
+        gb.Cavity(1.0, 0.25, 0.25, 16, 4, 4)
+    assert e.value.status == 1
