@@ -39,15 +39,21 @@ def report(name, w, ndir=3):
              np.linalg.norm(field(cav, s_ref.prof, X[d])) for d in range(ndir))
     er = max(abs(backscatter(cav, Xp[d], th[d], ph[d]) / backscatter(cav, X[d], th[d], ph[d]) - 1)
              for d in range(ndir))
-    print("%-10s table: max rel %.1e (max rel off the ridge band %.1e, max abs / max|K| %.1e); "
-          "aperture %.1e, field %.1e, RCS %.1e (max over %d directions)"
-          % (name, rel.max(), rel[~band].max(), err.max() / np.abs(K).max(), ea, ef, er, ndir))
+    print("%-10s table: max rel %.1e (off the ridge band %.1e, max abs / max|K| %.1e, "
+          "max|K_paper| / max|K| %.1e); aperture %.1e, field %.1e, RCS %.1e (max over %d "
+          "directions)" % (name, rel.max(), rel[~band].max() if np.any(~band) else 0.0,
+                           err.max() / np.abs(K).max(), np.abs(Kp).max() / np.abs(K).max(),
+                           ea, ef, er, ndir))
 
 
 if __name__ == "__main__":
     report("small", workloads.workload("small"), ndir=1)
     report("dirs16@64", workloads.scaled("dirs16", 64, nz=32, ndir=3))
     report("layer4@64", workloads.scaled("layered4", 64, nz=32, ndir=3))
+    th, ph, al = workloads.directions(2, 12)
+    ridge = dict(a=1.0, b=1.0, c=0.5, nx=32, ny=32, nz=12, kappa0=2 * np.pi * 15.3,
+                 layers=[(12, 1.0 + 0j)], theta=th, phi=ph, alpha=al)
+    report("ridge@32", ridge, ndir=2)
     import sys
     if "--full" in sys.argv:
         report("dirs16", workloads.scaled("dirs16", 256, nz=128, ndir=1), ndir=1)

@@ -15,6 +15,12 @@ Workloads (all a = b = 1, c = 0.5 in the same length unit):
              permutation of {4+1i, 2+0.5i, 6+0.1i, 1} (top to bottom),
              kappa0 = 2 pi / (10 h sqrt(6)) (10 points per wavelength in the
              densest layer), 8 directions, seed 3
+  rcs_sweep48()  48 cavities of uneven sizes (seed 4): side s in {64, 128,
+             256, 512}, Nz = s/2, a = b = 1, c = 0.5; homogeneous with
+             probability 1/2, else 2-4 layers of equal depth with
+             Re eps ~ U[1, 6], Im eps ~ U[0, 1]; four wavenumbers f kappa_10,
+             f in {0.25, 0.5, 0.75, 1}, kappa_10 at 10 points per wavelength in
+             the densest layer; 64 directions each
 """
 
 import numpy as np
@@ -77,3 +83,30 @@ def scaled(name, nx, ny=None, nz=None, ndir=None):
         for k in ('theta', 'phi', 'alpha'):
             w[k] = np.resize(w[k], ndir)
     return w
+
+
+def rcs_sweep48(seed=4):
+    """The 48-cavity backscatter sweep: a list of dicts with keys a, b, c, nx,
+    ny, nz, layers, kappas (four wavenumbers), theta, phi, alpha (64 each)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for i in range(48):
+        s = int(rng.choice([64, 128, 256, 512]))
+        nz = s // 2
+        if rng.uniform() < 0.5:
+            layers = [(nz, 1.0 + 0j)]
+        else:
+            k = int(rng.integers(2, 5))
+            base = nz // k
+            lev = [base] * k
+            lev[0] += nz - base * k
+            eps = rng.uniform(1.0, 6.0, k) + 1j * rng.uniform(0.0, 1.0, k)
+            layers = [(l, complex(e)) for l, e in zip(lev, eps)]
+        h = 0.5 / nz
+        emax = max(abs(e.real) for _, e in layers)
+        k10 = 2 * np.pi / (10 * h * np.sqrt(emax))
+        th, ph, al = directions(64, 1000 * seed + i)
+        out.append(dict(a=1.0, b=1.0, c=0.5, nx=s, ny=s, nz=nz, layers=layers,
+                        kappas=[f * k10 for f in (0.25, 0.5, 0.75, 1.0)],
+                        theta=th, phi=ph, alpha=al))
+    return out
