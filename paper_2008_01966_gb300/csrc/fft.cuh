@@ -422,3 +422,24 @@ __device__ __forceinline__ void fft_lines(C<T>* base, int lstride, int nlines,
   }
   __syncthreads();
 }
+
+// Warp-resident transform of the lines [first, first + cnt) that belong to the
+// calling warp (FP32, LineShape<T, LOGN>::WARP): 32 / LW lines at a time, each
+// on LW lanes.  Warp-level synchronisation only -- no block barrier, so the
+// warps of a block can run their chains of transforms independently.
+template <typename T, bool INV, int LOGN, typename Op = LineId<T>>
+__device__ __forceinline__ void fft_warp_lines(C<T>* base, int lstride, int first, int cnt,
+                                               const C<T>* __restrict__ tw, int twlog,
+                                               const Op& op = Op()) {
+  using S = LineShape<T, LOGN>;
+  static_assert(S::WARP, "warp transform lengths only");
+  constexpr int LW = S::LW, LPW = 32 / LW;
+  const int lane = threadIdx.x & 31;
+  const int sub = lane / LW, t = lane - sub * LW;
+  for (int l0 = 0; l0 < cnt; l0 += LPW) {
+    const int l = first + l0 + sub;
+    const bool active = l0 + sub < cnt;
+    C<T>* line = base + (size_t)(active ? l : first) * lstride;
+    fft_warp<T, INV, LW, S::RV, Op>(line, 1 << LOGN, LOGN, t, active, tw, twlog, l, op);
+  }
+}

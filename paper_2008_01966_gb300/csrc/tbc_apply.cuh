@@ -128,6 +128,33 @@ struct ParityProducts : G {
   }
 };
 
+// last write of the forward transform when each parity line transforms its
+// own copy of the column: the product with its parity's kernel, in place
+template <typename T>
+struct OwnParity : LineId<T> {
+  const C<T>* eh;                 // [r][P]
+  int P, L;
+  __device__ __forceinline__ void st(int l, C<T>* line, int k, C<T> v) const {
+    const int r = l >= L ? 1 : 0;
+    line[pidx(k)] = cmul<T>(v, eh[r * P + k]);
+  }
+};
+
+// pass A with one copy of the row per parity line: gather of row (l mod L),
+// product with the kernel of parity (l >= L), in place
+template <typename T, int LNY>
+struct GatherOwnA : GatherA<T, LNY> {
+  const C<T>* eh;                 // [r][P]
+  int P, L;
+  __device__ __forceinline__ C<T> ld(int l, const C<T>* line, int n) const {
+    return GatherA<T, LNY>::ld(l >= L ? l - L : l, line, n);
+  }
+  __device__ __forceinline__ void st(int l, C<T>* line, int k, C<T> v) const {
+    const int r = l >= L ? 1 : 0;
+    line[pidx(k)] = cmul<T>(v, eh[r * P + k]);
+  }
+};
+
 // last write of the inverse transforms of pass A: Vy(k1, j), j = 2t + r mod Py
 template <typename T, int LNY>
 struct ScatterA : LineId<T> {
@@ -154,26 +181,47 @@ __global__ void TBC_BOUNDS k_tbcA(const C<T>* __restrict__ x, C<T>* __restrict__
   constexpr int L = pairs_per_cta<T>(Py);
   const int f = blockIdx.y, d = blockIdx.z;
   const int row0 = blockIdx.x * L;
-  ParityProducts<T, GatherA<T, LNY>> fwd;
-  fwd.E1 = x + (size_t)d * p.nap;
-  fwd.E2 = fwd.E1 + p.n1;
-  fwd.row0 = row0;
-  fwd.nx = p.nx;
-  fwd.f = f;
-  fwd.pib = (T)p.pib;
-  fwd.pia = (T)p.pia;
-  fwd.eh = f != 0 ? eh_c : eh_s;
-  fwd.P = Py;
-  fwd.L = L;
-  fwd.ls = ls;
-  fwd.buf = buf;
-  fft_lines<T, false, LPY>(buf, ls, L, tw, p.twlog, fwd);
   ScatterA<T, LNY> sc;
   sc.Vy = Vy + (size_t)(d * 3 + f) * p.nx * Py;
   sc.row0 = row0;
   sc.nx = p.nx;
   sc.L = L;
-  fft_lines<T, true, LPY>(buf, ls, 2 * L, tw, p.twlog, sc);
+  if constexpr (LineShape<T, LPY>::WARP && 2 * L * LineShape<T, LPY>::TPL == LINES_THREADS) {
+    // every warp transforms its own lines (parity 0 or 1 of a row) from the
+    // gather to the scatter, the row's forward transform done by both of its
+    // lines' warps: no idle warps and no block barrier
+    GatherOwnA<T, LNY> fwd;
+    fwd.E1 = x + (size_t)d * p.nap;
+    fwd.E2 = fwd.E1 + p.n1;
+    fwd.row0 = row0;
+    fwd.nx = p.nx;
+    fwd.f = f;
+    fwd.pib = (T)p.pib;
+    fwd.pia = (T)p.pia;
+    fwd.eh = f != 0 ? eh_c : eh_s;
+    fwd.P = Py;
+    fwd.L = L;
+    constexpr int LPW = 32 / LineShape<T, LPY>::TPL;
+    const int first = (threadIdx.x >> 5) * LPW;
+    fft_warp_lines<T, false, LPY>(buf, ls, first, LPW, tw, p.twlog, fwd);
+    fft_warp_lines<T, true, LPY>(buf, ls, first, LPW, tw, p.twlog, sc);
+  } else {
+    ParityProducts<T, GatherA<T, LNY>> fwd;
+    fwd.E1 = x + (size_t)d * p.nap;
+    fwd.E2 = fwd.E1 + p.n1;
+    fwd.row0 = row0;
+    fwd.nx = p.nx;
+    fwd.f = f;
+    fwd.pib = (T)p.pib;
+    fwd.pia = (T)p.pia;
+    fwd.eh = f != 0 ? eh_c : eh_s;
+    fwd.P = Py;
+    fwd.L = L;
+    fwd.ls = ls;
+    fwd.buf = buf;
+    fft_lines<T, false, LPY>(buf, ls, L, tw, p.twlog, fwd);
+    fft_lines<T, true, LPY>(buf, ls, 2 * L, tw, p.twlog, sc);
+  }
 }
 
 // ------------------------------------------------------------------ pass B
@@ -225,6 +273,9 @@ __global__ void TBC_BOUNDS k_tbcB(const C<T>* __restrict__ Vy, C<T>* __restrict_
   const int j0 = blockIdx.x * L;
   const int tid = threadIdx.x, nthr = blockDim.x;
   const bool xcos = (f != 1);
+  // the per-warp chain (below) needs the column in both of its lines
+  constexpr int NCOPY = (LineShape<T, LPX>::WARP && LineShape<T, LPX - 1>::WARP &&
+                         2 * L * LineShape<T, LPX>::TPL == LINES_THREADS) ? 2 : 1;
   // shared memory: 2L lines, then the two parity kernels [2][Px], then the
   // kernel-table rows |j2| of the L columns [L][Px/2] (staged once per block,
   // so the fused products read shared memory instead of waiting on loads)
@@ -250,34 +301,53 @@ __global__ void TBC_BOUNDS k_tbcB(const C<T>* __restrict__ Vy, C<T>* __restrict_
       const int k1 = idx >> lL, l = idx & (L - 1);
       const int j = j0 + l;
       const C<T> c = j < Py ? src[(size_t)k1 * Py + j] : czero<T>();
-      C<T>* line = buf + (size_t)l * ls;
-      if (k1 == 0) {
-        line[0] = xcos ? cscale<T>(c, (T)2) : czero<T>();
-      } else {
-        line[pidx(k1)] = c;
-        line[pidx(Px - k1)] = xcos ? c : mk<T>(-c.x, -c.y);
+      const C<T> c0 = k1 == 0 ? (xcos ? cscale<T>(c, (T)2) : czero<T>()) : c;
+      const C<T> cm = xcos ? c : mk<T>(-c.x, -c.y);
+#pragma unroll
+      for (int r = 0; r < NCOPY; ++r) {
+        C<T>* line = buf + (size_t)(r * L + l) * ls;
+        line[pidx(k1)] = c0;
+        if (k1 > 0) line[pidx(Px - k1)] = cm;
       }
     }
-    for (int idx = tid; idx < L * (2 * nx + 1); idx += nthr) {
+    for (int idx = tid; idx < NCOPY * L * (2 * nx + 1); idx += nthr) {
       const int l = idx / (2 * nx + 1), k = nx + idx - l * (2 * nx + 1);
       buf[(size_t)l * ls + pidx(k)] = czero<T>();
     }
     __syncthreads();
   }
-  ParityProducts<T, LineId<T>> fwd;
-  fwd.eh = eh_sm;
-  fwd.P = Px;
-  fwd.L = L;
-  fwd.ls = ls;
-  fwd.buf = buf;
-  fft_lines<T, false, LPX>(buf, ls, L, tw, p.twlog, fwd);
   KhatB<T, LNX> kb;
   kb.kh = kh_sm;
   kb.j0 = j0;
   kb.Py = Py;
   kb.L = L;
-  fft_lines<T, true, LPX>(buf, ls, 2 * L, tw, p.twlog, kb);
-  fft_lines<T, true, LPX - 1>(buf, ls, 2 * L, tw, p.twlog);
+  if constexpr (LineShape<T, LPX>::WARP && LineShape<T, LPX - 1>::WARP &&
+                2 * L * LineShape<T, LPX>::TPL == LINES_THREADS) {
+    // every warp runs the whole chain on its own lines (a parity-0 or a
+    // parity-1 line of a column): the forward transform of the column is done
+    // by both of its lines' warps, so no warp idles and no block barrier is
+    // needed until the two parities are combined
+    constexpr int LPW = 32 / LineShape<T, LPX>::TPL;
+    const int first = (tid >> 5) * LPW;
+    OwnParity<T> fwd;
+    fwd.eh = eh_sm;
+    fwd.P = Px;
+    fwd.L = L;
+    fft_warp_lines<T, false, LPX>(buf, ls, first, LPW, tw, p.twlog, fwd);
+    fft_warp_lines<T, true, LPX>(buf, ls, first, LPW, tw, p.twlog, kb);
+    fft_warp_lines<T, true, LPX - 1>(buf, ls, first, LPW, tw, p.twlog);
+    __syncthreads();
+  } else {
+    ParityProducts<T, LineId<T>> fwd;
+    fwd.eh = eh_sm;
+    fwd.P = Px;
+    fwd.L = L;
+    fwd.ls = ls;
+    fwd.buf = buf;
+    fft_lines<T, false, LPX>(buf, ls, L, tw, p.twlog, fwd);
+    fft_lines<T, true, LPX>(buf, ls, 2 * L, tw, p.twlog, kb);
+    fft_lines<T, true, LPX - 1>(buf, ls, 2 * L, tw, p.twlog);
+  }
   C<T>* dst = W + (size_t)(d * 3 + f) * (nx + 1) * Py;
   const int sh = p.twlog - LPX;
   for (int idx = tid; idx < L * (nx + 1); idx += nthr) {
