@@ -16,7 +16,7 @@ from .rcs import backscatter
 from .tbc import TBCOperator
 
 
-def report(name, w, ndir=3):
+def report(name, w, ndir=3, dense=False):
     cav = Cavity(w['a'], w['b'], w['c'], w['nx'], w['ny'], w['nz'], w['kappa0'],
                  layers=[Layer(n, e) for n, e in w['layers']])
     ref_t = TBCOperator(cav)
@@ -32,8 +32,11 @@ def report(name, w, ndir=3):
     B = np.array([rhs(cav, t, p, a) for t, p, a in zip(th, ph, al)])
     s_ref = ApertureSystem(cav, tbc=ref_t)
     s_pap = ApertureSystem(cav, tbc=pap_t, prof=s_ref.prof)
-    X, _ = s_ref.solve_gmres(B)
-    Xp, _ = s_pap.solve_gmres(B)
+    if dense:
+        X, Xp = s_ref.solve_dense(B), s_pap.solve_dense(B)
+    else:
+        X, _ = s_ref.solve_gmres(B)
+        Xp, _ = s_pap.solve_gmres(B)
     ea = max(np.linalg.norm(Xp[d] - X[d]) / np.linalg.norm(X[d]) for d in range(ndir))
     ef = max(np.linalg.norm(field(cav, s_ref.prof, Xp[d]) - field(cav, s_ref.prof, X[d])) /
              np.linalg.norm(field(cav, s_ref.prof, X[d])) for d in range(ndir))
@@ -53,7 +56,7 @@ if __name__ == "__main__":
     th, ph, al = workloads.directions(2, 12)
     ridge = dict(a=1.0, b=1.0, c=0.5, nx=32, ny=32, nz=12, kappa0=2 * np.pi * 15.3,
                  layers=[(12, 1.0 + 0j)], theta=th, phi=ph, alpha=al)
-    report("ridge@32", ridge, ndir=2)
+    report("ridge@32", ridge, ndir=2, dense=True)
     import sys
     if "--full" in sys.argv:
         report("dirs16", workloads.scaled("dirs16", 256, nz=128, ndir=1), ndir=1)
