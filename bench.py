@@ -40,10 +40,10 @@ METRIC = "cavity field DOF/s at rel err \u22641e-5 vs FP64 oracle; p50/p99 solve
 # error at the floor; every run re-measures it (the "accuracy" entry).
 TOL = 1e-7
 # DRAM traffic of one launch of a kernel class from one `ncu --set full`
-# capture on 8 directions (profiles/tbc_B_fp32_dirs16.txt: 52.6 MB read +
-# 19.8 MB written), scaled to the 16 directions of a launch here (traffic is
-# proportional to the directions).  Only valid for the kernel as captured.
-NCU_TRAFFIC = {"tbc_B_fp32": 2 * (52.559104e6 + 19.846144e6)}
+# capture on 8 directions, scaled to the 16 directions of a launch here
+# (traffic is proportional to the directions).  Only valid for the kernel as
+# captured: emptied whenever the kernel changes, refilled from the next capture.
+NCU_TRAFFIC = {}
 
 
 def peaks():
