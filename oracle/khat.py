@@ -11,8 +11,11 @@ transform at frequency xi = (xi1, xi2), which depends on rho = |xi| only:
 The paper prints the prefactor 1/(4 pi) in front of the radial integral; the
 angular integral contributes 2 pi J0, so the prefactor is 1/2.  The integrand is
 entire in r, so composite Gauss-Legendre quadrature on panels no wider than
-pi / (2 pi rho + kappa0) converges geometrically; 16 nodes per panel leave an
-error far below 1e-14 relative: `khat` is the reference table.
+pi / (2 pi rho + kappa0) converges geometrically (16 nodes per panel).  What
+is left is the conditioning of the sum: the rounding of the arguments c r
+(c = 2 pi rho) shifts every oscillation coherently, a relative error of about
+c R * 1e-16 (1.4e-13 at c R = 1440, measured against a 30-digit evaluation):
+`khat` is the reference table to that accuracy.
 
 `khat_paper` is the paper's own scheme of Sec. 5.2, an approximation, kept as a
 measured variant: quadrature for small frequencies and, for large c = 2 pi rho,
