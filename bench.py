@@ -21,7 +21,6 @@ import json
 import os
 import subprocess
 import sys
-import threading
 import time
 
 import numpy as np
@@ -43,7 +42,7 @@ TOL = 1e-7
 # capture on 8 directions, scaled to the 16 directions of a launch here
 # (traffic is proportional to the directions).  Only valid for the kernel as
 # captured: emptied whenever the kernel changes, refilled from the next capture.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {"tbc_B_fp32": 2 * (52.560896e6 + 20.722944e6)}   # profiles/tbc_B_fp32_dirs16.txt
 
 
 def peaks():
@@ -56,35 +55,41 @@ def peaks():
 
 # ---------------------------------------------------------------- clocks
 class ClockSampler:
+    """nvidia-smi's own sampling loop (every 50 ms) running while the timed
+    steps run; rows are collected when the region ends."""
+
     def __init__(self, index):
         self.index = index
         self.rows = []
-        self.stop_ev = threading.Event()
-        self.th = None
+        self.proc = None
 
-    def _run(self):
+    def __enter__(self):
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
-        while not self.stop_ev.is_set():
-            try:
-                out = subprocess.run(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
-                                      "--format=csv,noheader,nounits"], capture_output=True,
-                                     text=True, timeout=5).stdout.strip()
-                if out:
-                    self.rows.append([x.strip() for x in out.split(",")])
-            except Exception:
-                pass
-            self.stop_ev.wait(0.2)
-
-    def __enter__(self):
-        self.th = threading.Thread(target=self._run, daemon=True)
-        self.th.start()
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                         text=True)
+            time.sleep(0.1)
+        except Exception:
+            self.proc = None
         return self
 
     def __exit__(self, *a):
-        self.stop_ev.set()
-        self.th.join(timeout=10)
+        if self.proc is None:
+            return
+        time.sleep(0.06)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=10)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        for line in out.splitlines():
+            if line.strip():
+                self.rows.append([x.strip() for x in line.split(",")])
 
     def summary(self):
         if not self.rows:
@@ -403,7 +408,7 @@ def run_gb300(args, rank, world, local_rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
