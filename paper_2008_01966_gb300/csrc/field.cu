@@ -37,9 +37,9 @@ template <typename T> __host__ __device__ constexpr int field_lines(int n) {
 }
 
 // pass 1: grid (ceil(nx / L) row groups, 3 components, ndir * lc slabs);
-// instantiated per LNY = log2 ny.  The coefficient formation (profile times
-// aperture value) and the mirroring are the transform's first read, the
-// scaled store of T1 (q <= ny) its last write.
+// instantiated per LNY = log2 ny.  A cooperative gather forms the
+// coefficients (profile times aperture value) and mirrors them into the lines;
+// the scaled store of T1 (q <= ny) is the transform's last write.
 template <typename T, int LNY>
 struct FieldY {
   const C<T>* E;                  // aperture coefficients of this direction
@@ -91,6 +91,12 @@ struct FieldY {
   }
 };
 
+// the gathered line as the first read, FieldY's store as the last write
+template <typename T, int LNY>
+struct FieldYStore : FieldY<T, LNY> {
+  __device__ __forceinline__ C<T> ld(int, const C<T>* line, int t) const { return line[pidx(t)]; }
+};
+
 template <typename T, int LNY>
 __global__ void __launch_bounds__(FIELD_THREADS, 2) k_field_y(const C<T>* __restrict__ ap,
                                                            const C<T>* __restrict__ prof,
@@ -119,7 +125,36 @@ __global__ void __launch_bounds__(FIELD_THREADS, 2) k_field_y(const C<T>* __rest
   op.comp = comp;
   op.top = (j == p.nz);
   op.layered = p.layered;
-  fft_lines<T, true, LNY + 1>(buf, ls, L, tw, p.twlog, op);
+  // cooperative gather: consecutive threads take consecutive n of a row, all
+  // of a thread's loads are issued before its first store, and the mirrored
+  // coefficients go straight into the lines (every slot is written)
+  constexpr int PER = L * ny / FIELD_THREADS;
+  static_assert(PER * FIELD_THREADS == L * ny, "rows must tile the block");
+  C<T> cv[PER];
+#pragma unroll
+  for (int k = 0; k < PER; ++k) {
+    const int idx = threadIdx.x + k * FIELD_THREADS;
+    cv[k] = op.coef(op.r0 + (idx >> LNY), idx & (ny - 1));
+  }
+  const bool ycos = comp == 1;
+#pragma unroll
+  for (int k = 0; k < PER; ++k) {
+    const int idx = threadIdx.x + k * FIELD_THREADS;
+    const int l = idx >> LNY, n = idx & (ny - 1);
+    C<T>* line = buf + (size_t)l * ls;
+    const C<T> c = cv[k];
+    if (n == 0) {
+      line[0] = ycos ? cscale<T>(c, (T)2) : mk<T>(0, 0);
+      line[pidx(ny)] = mk<T>(0, 0);
+    } else {
+      line[pidx(n)] = c;
+      line[pidx(n2 - n)] = ycos ? c : mk<T>(-c.x, -c.y);
+    }
+  }
+  __syncthreads();
+  FieldYStore<T, LNY> st;
+  static_cast<FieldY<T, LNY>&>(st) = op;
+  fft_lines<T, true, LNY + 1>(buf, ls, L, tw, p.twlog, st);
 }
 
 // pass 2: grid (ceil((ny+1) / L) column groups, 3 components, ndir * lc
