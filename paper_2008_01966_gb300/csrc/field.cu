@@ -188,6 +188,12 @@ struct FieldX {
   }
 };
 
+// the gathered line as the first read, FieldX's store as the last write
+template <typename T, int LNX>
+struct FieldXStore : FieldX<T, LNX> {
+  __device__ __forceinline__ C<T> ld(int, const C<T>* line, int t) const { return line[pidx(t)]; }
+};
+
 template <typename T, int LNX>
 __global__ void __launch_bounds__(FIELD_THREADS, 2) k_field_x(const C<T>* __restrict__ T1,
                                                            C<T>* __restrict__ out, FP p,
@@ -217,7 +223,48 @@ __global__ void __launch_bounds__(FIELD_THREADS, 2) k_field_x(const C<T>* __rest
     op.ncol = ny - 1; op.qlo = 1; op.qhi = ny - 1; op.plo = 1; op.phi = nx - 1;
   }
   op.dst = out + ((size_t)d * p.nz + (j - 1)) * p.S + off;
-  fft_lines<T, true, LNX + 1>(buf, ls, L, tw, p.twlog, op);
+  // cooperative gather of the L columns of T1: consecutive threads take
+  // consecutive columns of a row, all loads of a thread in flight before its
+  // first store; mirrored into the lines (slots m = nx, and m = 0 for the sine
+  // extension, cleared)
+  constexpr int lL = clog2(L);
+  constexpr int PER = L * nx / FIELD_THREADS;
+  static_assert(PER * FIELD_THREADS == L * nx, "columns must tile the block");
+  const bool xcos = comp == 0;
+  const int nrows = xcos ? nx : nx - 1;    // E1: m = 0..M; E2/E3: m = 1..M
+  C<T> cv[PER];
+#pragma unroll
+  for (int k = 0; k < PER; ++k) {
+    const int idx = threadIdx.x + k * FIELD_THREADS;
+    const int r = idx >> lL, q = op.q0 + (idx & (L - 1));
+    cv[k] = (q <= ny && r < nrows) ? op.src[(size_t)r * (ny + 1) + q] : mk<T>(0, 0);
+  }
+#pragma unroll
+  for (int k = 0; k < PER; ++k) {
+    const int idx = threadIdx.x + k * FIELD_THREADS;
+    const int r = idx >> lL, l = idx & (L - 1);
+    C<T>* line = buf + (size_t)l * ls;
+    const C<T> c = cv[k];
+    if (xcos) {
+      if (r == 0) {
+        line[0] = cscale<T>(c, (T)2);
+        line[pidx(nx)] = mk<T>(0, 0);
+      } else {
+        line[pidx(r)] = c;
+        line[pidx(n2 - r)] = c;
+      }
+    } else if (r < nx - 1) {
+      line[pidx(r + 1)] = c;
+      line[pidx(n2 - r - 1)] = mk<T>(-c.x, -c.y);
+    } else {
+      line[0] = mk<T>(0, 0);
+      line[pidx(nx)] = mk<T>(0, 0);
+    }
+  }
+  __syncthreads();
+  FieldXStore<T, LNX> st;
+  static_cast<FieldX<T, LNX>&>(st) = op;
+  fft_lines<T, true, LNX + 1>(buf, ls, L, tw, p.twlog, st);
 }
 
 __global__ void k_ap32(const double2* __restrict__ a, float2* __restrict__ b, long long n) {
