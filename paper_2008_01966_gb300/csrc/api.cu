@@ -90,6 +90,7 @@ extern "C" void cavity_destroy(cavity_ctx* ctx) {
                   ctx->ehat_xp[1], ctx->ehat_yp[0], ctx->ehat_yp[1], ctx->khat_p, ctx->top_p};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  if (ctx->pin) cudaFreeHost(ctx->pin);
   for (auto& e : ctx->evs) {
     cudaEventDestroy(e.a);
     cudaEventDestroy(e.b);

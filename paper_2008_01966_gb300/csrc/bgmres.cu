@@ -1,0 +1,973 @@
+// Block GMRES in FP32 for the inner solves of the mixed-precision refinement.
+//
+// All incident directions of a solve share the operator, so their Krylov
+// spaces are built together (block Arnoldi): the directions are split into
+// groups of at most BG_MAX, and step k of a group extends its basis by the
+// block A M^{-1} V_k of all its directions at once.  A direction's correction
+// is then sought in the whole block space, which contains its own
+// single-direction Krylov space of the same step count; the block solve reaches
+// the inner tolerance in fewer operator applications (measured with the oracle
+// on the 16-direction 64^2 and 128^2 workloads: 10-11 block steps against
+// 13-14 per-direction steps to 1e-5).
+//
+// Orthogonalisation of the new block W against the basis V: classical
+// Gram-Schmidt in two passes, each a pair of GEMM-shaped kernels -- V^H W by a
+// split reduction over the rows (k_bproj, k_bproj_final) and W -= V H with one
+// row per thread (k_bnn).  The block itself is then orthonormalised by SVQB
+// (Stathopoulos and Wu, 2002): W = V' S with V' = W U Lambda^{-1/2} from the
+// eigendecomposition G = W^H W = U Lambda U^H; eigenvalues below a floor are
+// raised to it, so nearly dependent directions (repeated incident directions,
+// converged columns) never divide by ~0 and W = V' S holds exactly, and the
+// step is repeated until V'^H V' is the identity to FP32 accuracy.
+//
+// The least-squares problems min || E_1 S_0 - Hbar Y || (block upper Hessenberg,
+// one right-hand side per direction of the group) are solved on the host in
+// FP64 by Householder reflections, one new column at a time; the norm of the
+// tail of each transformed right-hand side is that direction's residual.
+//
+// Reductions are fixed-order trees, so the result is deterministic for a given
+// batch; unlike per-direction GMRES it depends (within the tolerance) on which
+// directions share a group.
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <vector>
+
+#include "common.cuh"
+
+#define BG_MAX 16         // directions per group (columns of a block)
+#define BG_GROUPS 32      // groups per call (BG_GROUPS * BG_MAX directions)
+#define BG_PART_CTAS 608  // bound on groups x row chunks of one projection
+
+typedef std::complex<double> cd;
+
+struct BGrp {
+  const float2* V;  // Kv basis columns, stride nap
+  const float2* W;  // r block columns, stride nap
+  float2* O;        // output columns, stride nap (k_bnn)
+  int Kv;           // columns taken from V (k_bnn multiplies these)
+  int K;            // projected columns (k_bproj): V_0..V_{Kv-1}, then W_0..W_{K-Kv-1}
+  int r;
+  int coff;         // offset of this group's coefficient matrix (BG_MAX wide)
+};
+struct BGSet {
+  BGrp g[BG_GROUPS];
+};
+
+// Partial projections: part[z][x][i][j] = sum over the rows e of slab x of
+// conj(X_i[e]) W_j[e] for group z, i < K, j < r, where X_i is basis column i
+// for i < Kv and block column i - Kv after that (so the block's own Gram matrix
+// comes out of the same pass).  grid (nslab, ceil(K/16), groups), 256 threads:
+// a CTA owns the 16 x 16 output tile of columns 16 y .. 16 y + 15 over its slab
+// of rows, which it walks in tiles of 128 rows staged in shared memory (the next
+// tile is fetched into registers while the current one is used).  Thread t
+// computes a 4 x 4 block of the tile, i = 4 ((t & 15) >> 2) + a,
+// j = 4 (t & 3) + b, over the rows e = t >> 4 (mod 16) of each tile; the 16 row
+// classes are summed through shared memory at the end.
+#define BP_ROWS 128
+// Staged tiles are [row][16 columns] without padding; column c of row e is
+// stored at c ^ (e & 15), so the staging stores (consecutive rows, one column)
+// and the 16-byte reads of column pairs (one row) are both free of bank
+// conflicts.  A pair (c, c + 1), c even, sits at the aligned pair
+// c ^ (e & 14), swapped when e is odd.
+__device__ __forceinline__ void bp_pair(const float2* row, int c0, int s, float2& x0, float2& x1) {
+  const float4 v = *(const float4*)(row + (c0 ^ (s & 14)));
+  if (s & 1) {
+    x0 = make_float2(v.z, v.w);
+    x1 = make_float2(v.x, v.y);
+  } else {
+    x0 = make_float2(v.x, v.y);
+    x1 = make_float2(v.z, v.w);
+  }
+}
+__device__ __forceinline__ void cp_async8(float2* dst, const float2* src, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  const int n = valid ? 8 : 0;  // 0: the 8 bytes are zero-filled
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(n));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
+}
+
+// Tiles are copied global -> shared asynchronously into two buffers, the
+// next tile in flight while the current one is used.
+__global__ void __launch_bounds__(256, 2) k_bproj(BGSet set, double2* __restrict__ part, int nap,
+                                                  int rs, int nct, int kcap) {
+  extern __shared__ __align__(16) float2 sm[];  // 2 x (V tile, W tile); later the row-class sums
+  const BGrp& gd = set.g[blockIdx.z];
+  const int t = threadIdx.x;
+  const int tij = t & 15, ti = tij >> 2, tj = tij & 3, rcl = t >> 4;
+  const int ib = blockIdx.y * 16, K = gd.K, Kv = gd.Kv, r = gd.r;
+  const int e0 = blockIdx.x * rs, e1 = min(nap, e0 + rs);
+  // staging: element q = t + 256 u (u < 8) of a 128 x 16 tile is row q % 128, column q / 128
+  auto stage = [&](int buf, int eb) {
+    float2* vs = sm + buf * (2 * BP_ROWS * 16);
+    float2* ws = vs + BP_ROWS * 16;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int q = t + 256 * u, c = q >> 7, el = q & 127, e = eb + el, i = ib + c;
+      const bool in = e < e1;
+      const float2* src = i < Kv ? gd.V + (size_t)i * nap : gd.W + (size_t)(i - Kv) * nap;
+      const int o = el * 16 + (c ^ (el & 15));
+      cp_async8(vs + o, (in && i < K) ? src + e : gd.W, in && i < K);
+      cp_async8(ws + o, (in && c < r) ? gd.W + (size_t)c * nap + e : gd.W, in && c < r);
+    }
+    cp_async_commit();
+  };
+  float2 acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = make_float2(0.f, 0.f);
+  const int ntile = (e1 - e0 + BP_ROWS - 1) / BP_ROWS;
+  if (ntile > 0) stage(0, e0);
+  if (ntile > 1) stage(1, e0 + BP_ROWS);
+  for (int it = 0; it < ntile; ++it) {
+    if (it + 1 < ntile) cp_async_wait<1>();
+    else cp_async_wait<0>();
+    __syncthreads();
+    const float2* vs = sm + (it & 1) * (2 * BP_ROWS * 16);
+    const float2* ws = vs + BP_ROWS * 16;
+#pragma unroll
+    for (int e = rcl; e < BP_ROWS; e += 16) {
+      const int sw = e & 15;
+      float2 av[4], wv[4];
+      bp_pair(vs + e * 16, 4 * ti, sw, av[0], av[1]);
+      bp_pair(vs + e * 16, 4 * ti + 2, sw, av[2], av[3]);
+      bp_pair(ws + e * 16, 4 * tj, sw, wv[0], wv[1]);
+      bp_pair(ws + e * 16, 4 * tj + 2, sw, wv[2], wv[3]);
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          acc[a][b].x += av[a].x * wv[b].x + av[a].y * wv[b].y;
+          acc[a][b].y += av[a].x * wv[b].y - av[a].y * wv[b].x;
+        }
+    }
+    __syncthreads();
+    if (it + 2 < ntile) stage(it & 1, e0 + (it + 2) * BP_ROWS);
+  }
+  // sum the 16 row classes: output (i, j) of the tile at sm[class * 256 + i * 16 + j]
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) sm[rcl * 256 + (4 * ti + a) * 16 + 4 * tj + b] = acc[a][b];
+  __syncthreads();
+  const int li = t >> 4, lj = t & 15;
+  if (ib + li < K && lj < r) {
+    double sx = 0, sy = 0;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) { sx += (double)sm[q * 256 + t].x; sy += (double)sm[q * 256 + t].y; }
+    part[((size_t)(blockIdx.z * nct + blockIdx.x) * kcap + ib + li) * BG_MAX + lj] = make_double2(sx, sy);
+  }
+}
+#define BP_SMEM (sizeof(float2) * 4 * BP_ROWS * 16)
+
+// h[z][i][j] = sum over the nct slabs of part[z][x][i][j] in a fixed order.
+// grid (ceil(K/16), groups), 1024 threads: output (i, j) of the 16-row tile is
+// t & 255; the four thread quarters take slabs x = t >> 8 (mod 4) in order and
+// are added in quarter order.
+__global__ void __launch_bounds__(1024) k_bproj_final(BGSet set, const double2* __restrict__ part,
+                                                      double2* __restrict__ h, int nct, int kcap) {
+  __shared__ double2 q4[4][256];
+  const BGrp& gd = set.g[blockIdx.y];
+  const int t = threadIdx.x, o = t & 255, qg = t >> 8;
+  const int i = blockIdx.x * 16 + (o >> 4), j = o & 15;
+  double sx = 0, sy = 0;
+  if (i < gd.K && j < gd.r) {
+    for (int x = qg; x < nct; x += 4) {
+      const double2 v = part[((size_t)(blockIdx.y * nct + x) * kcap + i) * BG_MAX + j];
+      sx += v.x;
+      sy += v.y;
+    }
+  }
+  q4[qg][o] = make_double2(sx, sy);
+  __syncthreads();
+  if (qg == 0 && i < gd.K && j < gd.r) {
+    double ax = 0, ay = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) { ax += q4[q][o].x; ay += q4[q][o].y; }
+    h[((size_t)blockIdx.y * kcap + i) * BG_MAX + j] = make_double2(ax, ay);
+  }
+}
+
+// O_j[e] = beta O_j[e] + sgn sum_{i<Kv} V_i[e] C[i][j]  for j < r; C is the
+// group's coefficient matrix at cmat + coff (FP64, BG_MAX wide), rounded to
+// FP32 into dynamic shared memory once (rows padded to a multiple of 4 with
+// zeros).  Each of the 128 threads takes the rows e and e + 128 of its block's
+// 256, so each coefficient read from shared memory serves two rows, and the
+// loads of the next four basis columns are in flight while the current four
+// are used.  (Small blocks keep the last partial wave of blocks short.)  All
+// inputs of a row are read before its outputs are written, so O may alias V.
+// grid (ceil(nap / 256), 1, groups); dynamic shared memory bnn_smem(Kv).
+__host__ __device__ constexpr size_t bnn_smem(int kv) {
+  return sizeof(float2) * BG_MAX * (size_t)((kv + 3) / 4 * 4);
+}
+#define BNN_THREADS 128
+__global__ void __launch_bounds__(BNN_THREADS) k_bnn(BGSet set, const double2* __restrict__ cmat, int nap,
+                                             float beta, float sgn) {
+  extern __shared__ __align__(16) float4 cs[];  // [Kv4][BG_MAX / 2]
+  const BGrp& gd = set.g[blockIdx.z];
+  const double2* Cm = cmat + gd.coff;
+  const int Kv = gd.Kv, K4 = (Kv + 3) / 4 * 4;
+  const int e = blockIdx.x * (2 * BNN_THREADS) + threadIdx.x, f = e + BNN_THREADS;
+  const bool ie = e < nap, jf = f < nap;
+  for (int t = threadIdx.x; t < K4 * BG_MAX; t += BNN_THREADS) {
+    const int ii = t / BG_MAX, j = t - ii * BG_MAX;
+    double2 c = make_double2(0.0, 0.0);
+    if (ii < Kv && j < gd.r) c = Cm[(size_t)ii * BG_MAX + j];
+    ((float2*)cs)[t] = make_float2((float)(sgn * c.x), (float)(sgn * c.y));
+  }
+  __syncthreads();
+  float2 p[BG_MAX], q[BG_MAX];
+#pragma unroll
+  for (int j = 0; j < BG_MAX; ++j) p[j] = q[j] = make_float2(0.f, 0.f);
+  float2 a[4], b[4];
+  auto load4 = [&](int i0) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const bool in = i0 + u < Kv;
+      const float2* vp = gd.V + (size_t)(i0 + u) * nap;
+      a[u] = (in && ie) ? vp[e] : make_float2(0.f, 0.f);
+      b[u] = (in && jf) ? vp[f] : make_float2(0.f, 0.f);
+    }
+  };
+  load4(0);
+  for (int i0 = 0; i0 < Kv; i0 += 4) {
+    float2 ca[4], cb[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) { ca[u] = a[u]; cb[u] = b[u]; }
+    if (i0 + 4 < Kv) load4(i0 + 4);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const float4* cr = cs + (size_t)(i0 + u) * (BG_MAX / 2);
+#pragma unroll
+      for (int h = 0; h < BG_MAX / 2; ++h) {
+        const float4 c2 = cr[h];
+        p[2 * h].x += ca[u].x * c2.x - ca[u].y * c2.y;
+        p[2 * h].y += ca[u].x * c2.y + ca[u].y * c2.x;
+        p[2 * h + 1].x += ca[u].x * c2.z - ca[u].y * c2.w;
+        p[2 * h + 1].y += ca[u].x * c2.w + ca[u].y * c2.z;
+        q[2 * h].x += cb[u].x * c2.x - cb[u].y * c2.y;
+        q[2 * h].y += cb[u].x * c2.y + cb[u].y * c2.x;
+        q[2 * h + 1].x += cb[u].x * c2.z - cb[u].y * c2.w;
+        q[2 * h + 1].y += cb[u].x * c2.w + cb[u].y * c2.z;
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < BG_MAX; ++j) {
+    if (j < gd.r) {
+      if (ie) {
+        float2* o = gd.O + (size_t)j * nap + e;
+        float2 ov = make_float2(0.f, 0.f);
+        if (beta != 0.f) ov = *o;
+        *o = make_float2(beta * ov.x + p[j].x, beta * ov.y + p[j].y);
+      }
+      if (jf) {
+        float2* o = gd.O + (size_t)j * nap + f;
+        float2 ov = make_float2(0.f, 0.f);
+        if (beta != 0.f) ov = *o;
+        *o = make_float2(beta * ov.x + q[j].x, beta * ov.y + q[j].y);
+      }
+    }
+  }
+}
+
+// dst[map[c]] += src[c]  (column c of a contiguous block; grid (ceil(nap/256), ncol))
+__global__ void k_scatter_add(const float2* __restrict__ src, float2* __restrict__ dst,
+                              const int* __restrict__ map, int nap) {
+  const int c = blockIdx.y, e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nap) return;
+  const float2 a = src[(size_t)c * nap + e];
+  float2* o = dst + (size_t)map[c] * nap + e;
+  *o = make_float2(o->x + a.x, o->y + a.y);
+}
+
+// dst[c] = src[map[c]]  (gather into a contiguous block)
+__global__ void k_gather_cols(const float2* __restrict__ src, float2* __restrict__ dst,
+                              const int* __restrict__ map, int nap) {
+  const int c = blockIdx.y, e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nap) return;
+  dst[(size_t)c * nap + e] = src[(size_t)map[c] * nap + e];
+}
+
+// dst[c] -= src[c]  (contiguous blocks; grid (ceil(nap/256), ncol))
+__global__ void k_sub_cols(const float2* __restrict__ src, float2* __restrict__ dst, int nap) {
+  const size_t k = (size_t)blockIdx.y * nap + blockIdx.x * blockDim.x + threadIdx.x;
+  if (blockIdx.x * blockDim.x + threadIdx.x >= (unsigned)nap) return;
+  dst[k] = make_float2(dst[k].x - src[k].x, dst[k].y - src[k].y);
+}
+
+static inline unsigned bg_blocks(long long n, int b) { return (unsigned)((n + b - 1) / b); }
+
+// ------------------------------------------------------------------ host side
+
+// Eigendecomposition of a Hermitian n x n matrix (row-major) by cyclic Jacobi
+// rotations: a = U diag(lam) U^H.  The rotation for entry (p, q) is computed
+// from t = tan(theta) of the 2 x 2 problem without trigonometric calls.
+static void herm_eig(std::vector<cd> a, int n, std::vector<double>& lam, std::vector<cd>& U) {
+  U.assign((size_t)n * n, cd(0, 0));
+  for (int i = 0; i < n; ++i) U[(size_t)i * n + i] = 1.0;
+  auto A = [&](int i, int j) -> cd& { return a[(size_t)i * n + j]; };
+  for (int sweep = 0; sweep < 40; ++sweep) {
+    double off = 0, dia = 0;
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) (i == j ? dia : off) += std::norm(A(i, j));
+    if (off <= 1e-30 * std::max(dia, 1e-300)) break;
+    for (int p = 0; p < n - 1; ++p) {
+      for (int q = p + 1; q < n; ++q) {
+        const cd apq = A(p, q);
+        const double m2 = std::norm(apq);
+        if (m2 <= 1e-34 * std::abs(A(p, p).real() * A(q, q).real()) || m2 == 0.0) continue;
+        const double m = std::sqrt(m2);
+        const cd ph = apq / m;
+        // zero the (p, q) entry: tan(2 theta) = 2 m / (a_qq - a_pp), |theta| <= pi/4
+        const double tau = (A(q, q).real() - A(p, p).real()) / (2 * m);
+        const double t = (tau >= 0 ? 1.0 : -1.0) / (std::fabs(tau) + std::sqrt(1.0 + tau * tau));
+        const double c = 1.0 / std::sqrt(1.0 + t * t), s = t * c;
+        // J: columns p, q of the identity replaced by (c, -s conj(ph)) and (s ph, c)
+        const cd jpq = s * ph, jqp = -s * std::conj(ph);
+        for (int k = 0; k < n; ++k) {  // a <- a J
+          const cd x = A(k, p), y = A(k, q);
+          A(k, p) = x * c + y * jqp;
+          A(k, q) = x * jpq + y * c;
+        }
+        for (int k = 0; k < n; ++k) {  // a <- J^H a
+          const cd x = A(p, k), y = A(q, k);
+          A(p, k) = c * x + std::conj(jqp) * y;
+          A(q, k) = std::conj(jpq) * x + c * y;
+        }
+        A(p, q) = A(q, p) = 0.0;
+        A(p, p) = A(p, p).real();
+        A(q, q) = A(q, q).real();
+        for (int k = 0; k < n; ++k) {  // U <- U J
+          const cd x = U[(size_t)k * n + p], y = U[(size_t)k * n + q];
+          U[(size_t)k * n + p] = x * c + y * jqp;
+          U[(size_t)k * n + q] = x * jpq + y * c;
+        }
+      }
+    }
+  }
+  lam.resize(n);
+  for (int i = 0; i < n; ++i) lam[i] = A(i, i).real();
+}
+
+// Cholesky QR step: G = L L^H, T = L^{-H} (the block transform, BG_MAX wide),
+// S = L^H (old block = new block * S).  Returns false when a pivot falls below
+// 1e-10 of the largest diagonal entry; cond receives an upper bound of the
+// condition number of G, ||G||_F ||L^{-1}||_F^2.
+static bool cholqr(const std::vector<cd>& G, int n, std::vector<cd>& T, std::vector<cd>& S,
+                   double& cond) {
+  std::vector<cd> L((size_t)n * n, cd(0, 0));
+  double dmax = 0, gf = 0;
+  for (int i = 0; i < n; ++i) dmax = std::max(dmax, G[(size_t)i * n + i].real());
+  for (const cd& x : G) gf += std::norm(x);
+  if (!(dmax > 0)) return false;
+  for (int j = 0; j < n; ++j) {
+    double d = G[(size_t)j * n + j].real();
+    for (int k = 0; k < j; ++k) d -= std::norm(L[(size_t)j * n + k]);
+    if (!(d > 1e-10 * dmax)) return false;
+    const double ljj = std::sqrt(d);
+    L[(size_t)j * n + j] = ljj;
+    for (int i = j + 1; i < n; ++i) {
+      cd v = G[(size_t)i * n + j];
+      for (int k = 0; k < j; ++k) v -= L[(size_t)i * n + k] * std::conj(L[(size_t)j * n + k]);
+      L[(size_t)i * n + j] = v / ljj;
+    }
+  }
+  // Li = L^{-1} (lower triangular)
+  std::vector<cd> Li((size_t)n * n, cd(0, 0));
+  for (int c = 0; c < n; ++c) {
+    Li[(size_t)c * n + c] = 1.0 / L[(size_t)c * n + c];
+    for (int i = c + 1; i < n; ++i) {
+      cd v = 0;
+      for (int k = c; k < i; ++k) v -= L[(size_t)i * n + k] * Li[(size_t)k * n + c];
+      Li[(size_t)i * n + c] = v / L[(size_t)i * n + i];
+    }
+  }
+  double lf = 0;
+  for (const cd& x : Li) lf += std::norm(x);
+  cond = std::sqrt(gf) * lf;
+  T.assign((size_t)n * BG_MAX, cd(0, 0));
+  S.assign((size_t)n * n, cd(0, 0));
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      T[(size_t)i * BG_MAX + j] = std::conj(Li[(size_t)j * n + i]);  // (L^{-1})^H
+      S[(size_t)i * n + j] = std::conj(L[(size_t)j * n + i]);        // L^H
+    }
+  return true;
+}
+
+// One SVQB step on the Gram matrix G (n x n): T = U Lambda_c^{-1/2} (the
+// transform of the block, stored BG_MAX wide as the k_bnn coefficient matrix),
+// S = Lambda_c^{1/2} U^H (W = (W T) S); Lambda_c = max(Lambda, floor).
+// Returns the deviation of G from the identity (max |G - I|); ratio receives
+// min(Lambda) / max(Lambda).
+static double svqb(const std::vector<cd>& G, int n, std::vector<cd>& T, std::vector<cd>& S,
+                   double& ratio) {
+  double dev = 0;
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) dev = std::max(dev, std::abs(G[(size_t)i * n + j] - (i == j ? 1.0 : 0.0)));
+  std::vector<double> lam;
+  std::vector<cd> U;
+  herm_eig(G, n, lam, U);
+  double lmax = 0, lmin = 1e300;
+  for (double l : lam) {
+    lmax = std::max(lmax, l);
+    lmin = std::min(lmin, l);
+  }
+  ratio = lmax > 0 ? lmin / lmax : 0.0;
+  T.assign((size_t)n * BG_MAX, cd(0, 0));
+  S.assign((size_t)n * n, cd(0, 0));
+  if (!(lmax > 1e-300)) return dev;  // the block vanished (exact breakdown): zero block
+  const double fl = lmax * 1e-12;
+  for (int c = 0; c < n; ++c) {
+    const double l = std::max(lam[c], fl), sl = std::sqrt(l);
+    for (int i = 0; i < n; ++i) {
+      T[(size_t)i * BG_MAX + c] = U[(size_t)i * n + c] / sl;
+      S[(size_t)c * n + i] = sl * std::conj(U[(size_t)i * n + c]);
+    }
+  }
+  return dev;
+}
+
+// S <- S2 S  (n x n, row-major)
+static void matmul_left(const std::vector<cd>& S2, std::vector<cd>& S, int n) {
+  std::vector<cd> o((size_t)n * n, cd(0, 0));
+  for (int i = 0; i < n; ++i)
+    for (int k = 0; k < n; ++k) {
+      const cd a = S2[(size_t)i * n + k];
+      for (int j = 0; j < n; ++j) o[(size_t)i * n + j] += a * S[(size_t)k * n + j];
+    }
+  S.swap(o);
+}
+
+// Householder QR of the block Hessenberg matrix of one group, one column at a time.
+struct BlockLS {
+  int r = 0;                         // block width = right-hand sides
+  int rows = 0, cols = 0;            // current size of Hbar
+  std::vector<std::vector<cd>> v;    // reflector c acts on rows c .. c + v[c].size() - 1
+  std::vector<std::vector<cd>> R;    // column c of the triangular factor (rows 0..c)
+  std::vector<cd> g;                 // rows x r transformed right-hand sides (row-major)
+  void start(int r_, const std::vector<cd>& S0) {
+    r = r_;
+    rows = r;
+    cols = 0;
+    v.clear();
+    R.clear();
+    g = S0;
+  }
+  // append block column: col[c] has rows_new entries (rows 0..rows_new-1)
+  void add(const std::vector<std::vector<cd>>& newcols, int rows_new) {
+    g.resize((size_t)rows_new * r, cd(0, 0));
+    rows = rows_new;
+    // the reflectors so far, each applied to all new columns at once
+    std::vector<std::vector<cd>> nc(newcols.size());
+    for (size_t c = 0; c < newcols.size(); ++c) {
+      nc[c] = newcols[c];
+      nc[c].resize(rows, cd(0, 0));
+    }
+    for (int p = 0; p < cols; ++p) {
+      const auto& vp = v[p];
+      const size_t L = vp.size();
+      for (auto& col : nc) {
+        cd* x = col.data() + p;
+        double sr = 0, si = 0;
+        for (size_t t = 0; t < L; ++t) {  // s = v^H x
+          sr += vp[t].real() * x[t].real() + vp[t].imag() * x[t].imag();
+          si += vp[t].real() * x[t].imag() - vp[t].imag() * x[t].real();
+        }
+        sr *= 2;
+        si *= 2;
+        for (size_t t = 0; t < L; ++t)  // x -= 2 v s
+          x[t] -= cd(vp[t].real() * sr - vp[t].imag() * si, vp[t].real() * si + vp[t].imag() * sr);
+      }
+    }
+    for (size_t cix = 0; cix < nc.size(); ++cix) {
+      std::vector<cd>& col = nc[cix];
+      // reflectors of the earlier new columns of this block
+      for (int p = cols - (int)cix; p < cols; ++p) {
+        const auto& vp = v[p];
+        cd s = 0;
+        for (size_t t = 0; t < vp.size(); ++t) s += std::conj(vp[t]) * col[p + t];
+        for (size_t t = 0; t < vp.size(); ++t) col[p + t] -= 2.0 * vp[t] * s;
+      }
+      const int ci = cols;
+      double alpha = 0;
+      for (int t = ci; t < rows; ++t) alpha += std::norm(col[t]);
+      alpha = std::sqrt(alpha);
+      const double a0 = std::abs(col[ci]);
+      const cd ph = a0 > 0 ? col[ci] / a0 : cd(1, 0);
+      std::vector<cd> u(col.begin() + ci, col.end());
+      u[0] += ph * alpha;
+      double un = 0;
+      for (const cd& x : u) un += std::norm(x);
+      un = std::sqrt(un);
+      if (un > 0)
+        for (cd& x : u) x /= un;
+      for (int t = ci; t < rows; ++t) col[t] = 0;
+      col[ci] = -ph * alpha;
+      R.emplace_back(col.begin(), col.begin() + ci + 1);
+      for (int j = 0; j < r; ++j) {
+        cd s = 0;
+        for (size_t t = 0; t < u.size(); ++t) s += std::conj(u[t]) * g[(size_t)(ci + t) * r + j];
+        for (size_t t = 0; t < u.size(); ++t) g[(size_t)(ci + t) * r + j] -= 2.0 * u[t] * s;
+      }
+      v.push_back(std::move(u));
+      ++cols;
+    }
+  }
+  double resid(int j) const {
+    double s = 0;
+    for (int t = cols; t < rows; ++t) s += std::norm(g[(size_t)t * r + j]);
+    return std::sqrt(s);
+  }
+  // Y = R^{-1} g[0:cols]  (cols x r, stored BG_MAX wide)
+  void solve(std::vector<cd>& Y) const {
+    Y.assign((size_t)cols * BG_MAX, cd(0, 0));
+    for (int j = 0; j < r; ++j) {
+      for (int i = cols - 1; i >= 0; --i) {
+        cd s = g[(size_t)i * r + j];
+        for (int k = i + 1; k < cols; ++k) s -= R[k][i] * Y[(size_t)k * BG_MAX + j];
+        const cd d = R[i][i];
+        Y[(size_t)i * BG_MAX + j] = std::abs(d) > 0 ? s / d : cd(0, 0);
+      }
+    }
+  }
+};
+
+struct BWork {
+  float2 *V, *Rc, *Z, *Wb, *Tt;
+  double2 *part, *hb, *cb;
+  int* map;
+  void* apw;
+  int kcap, gmax;
+};
+
+static size_t al256(size_t x) { return (x + 255) / 256 * 256; }
+
+size_t block_inner_work_bytes(const Geo& g, int ndir, int mb) {
+  const int nd = std::min(ndir, BG_GROUPS * BG_MAX);
+  const int gm = (nd + BG_MAX - 1) / BG_MAX;
+  const size_t kcap = (size_t)(mb + 1) * BG_MAX;
+  const size_t col = sizeof(float2) * (size_t)g.nap;
+  size_t b = 0;
+  b += al256(col * gm * kcap);                              // V
+  b += 4 * al256(col * nd);                                 // Rc, Z, Wb, Tt
+  b += al256(sizeof(double2) * BG_PART_CTAS * kcap * BG_MAX);  // part
+  b += al256(sizeof(double2) * 3 * gm * kcap * BG_MAX);      // hb
+  b += al256(sizeof(double2) * gm * kcap * BG_MAX);          // cb
+  b += al256(sizeof(int) * nd);                              // map
+  b += al256(apply_work_bytes(g, nd, sizeof(float2)));
+  return b;
+}
+
+static BWork bwork_carve(void* base, const Geo& g, int ndir, int mb) {
+  const int nd = std::min(ndir, BG_GROUPS * BG_MAX);
+  const int gm = (nd + BG_MAX - 1) / BG_MAX;
+  const size_t kcap = (size_t)(mb + 1) * BG_MAX;
+  const size_t col = sizeof(float2) * (size_t)g.nap;
+  char* p = (char*)base;
+  BWork w;
+  w.V = (float2*)p; p += al256(col * gm * kcap);
+  w.Rc = (float2*)p; p += al256(col * nd);
+  w.Z = (float2*)p; p += al256(col * nd);
+  w.Wb = (float2*)p; p += al256(col * nd);
+  w.Tt = (float2*)p; p += al256(col * nd);
+  w.part = (double2*)p; p += al256(sizeof(double2) * BG_PART_CTAS * kcap * BG_MAX);
+  w.hb = (double2*)p; p += al256(sizeof(double2) * 3 * gm * kcap * BG_MAX);
+  w.cb = (double2*)p; p += al256(sizeof(double2) * gm * kcap * BG_MAX);
+  w.map = (int*)p; p += al256(sizeof(int) * nd);
+  w.apw = p;
+  w.kcap = (int)kcap;
+  w.gmax = gm;
+  return w;
+}
+
+// V^H W for every group of `set` (ng groups, K and r per group) into
+// hb + slot * gmax * kcap * BG_MAX, laid out [z][i][j].
+static void bproj(cavity_ctx* ctx, const BGSet& set, int ng, int kmax, const BWork& w, int slot) {
+  const int nap = ctx->g.nap;
+  const int ytiles = (kmax + 15) / 16;
+  // one slab of rows per SM over the groups (few, long slabs keep the final
+  // sum short; the column tiles multiply the CTAs)
+  int nct = std::max(1, std::min(BG_PART_CTAS / ng, 152 / ng));
+  nct = std::min(nct, (nap + BP_ROWS - 1) / BP_ROWS);
+  int rs = (nap + nct - 1) / nct;
+  rs = (rs + BP_ROWS - 1) / BP_ROWS * BP_ROWS;
+  nct = (nap + rs - 1) / rs;
+  double2* h = w.hb + (size_t)slot * w.gmax * w.kcap * BG_MAX;
+  static bool done = false;
+  if (!done) {
+    cudaFuncSetAttribute(k_bproj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BP_SMEM);
+    done = true;
+  }
+  {
+    KScope ks_(ctx, KC_KRYLOV);
+    k_bproj<<<dim3(nct, ytiles, ng), 256, BP_SMEM, ctx->stream>>>(set, w.part, nap, rs, nct, w.kcap);
+  }
+  {
+    KScope ks_(ctx, KC_KRYLOV);
+    k_bproj_final<<<dim3(ytiles, ng), 1024, 0, ctx->stream>>>(set, w.part, h, nct, w.kcap);
+  }
+}
+
+static cavity_status bnn(cavity_ctx* ctx, const BGSet& set, int ng, const double2* cmat, float beta,
+                         float sgn) {
+  const int nap = ctx->g.nap;
+  int kv = 0;
+  for (int z = 0; z < ng; ++z) kv = std::max(kv, set.g[z].Kv);
+  static bool done = false;
+  if (!done) {
+    CK(cudaFuncSetAttribute(k_bnn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)bnn_smem(BG_MAX * 40)));
+    done = true;
+  }
+  KScope ks_(ctx, KC_KRYLOV);
+  k_bnn<<<dim3(bg_blocks(nap, 2 * BNN_THREADS), 1, ng), BNN_THREADS, bnn_smem(kv), ctx->stream>>>(
+      set, cmat, nap, beta, sgn);
+  return CAVITY_OK;
+}
+
+// Solves A M^{-1} y = r_d for the directions with active[d] (r: ndir scaled
+// FP32 residual columns), accumulating d = M^{-1} y into the d columns (zeroed
+// first).  tol[d] is the relative target (the columns have unit norm); iters[d]
+// is increased by the block steps taken, est[d] is the final least-squares
+// residual.  Groups still above tolerance after mb steps restart from their
+// true inner residual.
+cavity_status run_block_inner(cavity_ctx* ctx, int ndir, const float2* r, float2* d,
+                              const std::vector<double>& tol, const std::vector<char>& active, int mb,
+                              int maxit, void* work, std::vector<int>& iters,
+                              std::vector<double>& est) {
+  const Geo& g = ctx->g;
+  const int nap = g.nap;
+  cudaStream_t st = ctx->stream;
+  CK(cudaMemsetAsync(d, 0, sizeof(float2) * (size_t)ndir * nap, st));
+  std::vector<int> all;
+  for (int q = 0; q < ndir; ++q)
+    if (active[q]) all.push_back(q);
+  est.assign(ndir, 0.0);
+  // directions beyond one call's capacity are solved in further batches
+  for (size_t b0 = 0; b0 < all.size(); b0 += BG_GROUPS * BG_MAX) {
+    const int na = (int)std::min(all.size() - b0, (size_t)BG_GROUPS * BG_MAX);
+    std::vector<int> dirs(all.begin() + b0, all.begin() + b0 + na);
+    BWork w = bwork_carve(work, g, ndir, mb);
+    const int ng = (na + BG_MAX - 1) / BG_MAX;
+    // balanced groups: group z holds directions [goff[z], goff[z] + gr[z])
+    std::vector<int> gr(ng), goff(ng);
+    for (int z = 0, o = 0; z < ng; ++z) {
+      gr[z] = na / ng + (z < na % ng ? 1 : 0);
+      goff[z] = o;
+      o += gr[z];
+    }
+    CK(cudaMemcpyAsync(w.map, dirs.data(), sizeof(int) * na, cudaMemcpyHostToDevice, st));
+    {
+      KScope ks_(ctx, KC_KRYLOV);
+      k_gather_cols<<<dim3(bg_blocks(nap, 256), na), 256, 0, st>>>(r, w.Rc, w.map, nap);
+    }
+    std::vector<char> gdone(ng, 0);
+    int used = 0;
+    auto Vg = [&](int z) { return w.V + (size_t)z * w.kcap * nap; };
+    auto hptr = [&](int slot, int z) {
+      return w.hb + ((size_t)slot * w.gmax + z) * w.kcap * BG_MAX;
+    };
+    const size_t hsz = (size_t)w.kcap * BG_MAX;
+    // pinned staging: three fetched coefficient slots, then the upload slot;
+    // an upload is rewritten only after a stream synchronisation that follows
+    // the previous one
+    CKS(ensure_pin(ctx, sizeof(double2) * 4 * w.gmax * hsz));
+    double2* hh = (double2*)ctx->pin;
+    double2* cup = hh + (size_t)3 * w.gmax * hsz;
+    bool upl_pending = false;  // an upload may still be queued behind GPU work
+    auto sync = [&]() -> cavity_status {
+      CK(cudaStreamSynchronize(st));
+      upl_pending = false;
+      return CAVITY_OK;
+    };
+    auto fetch = [&](int slot) -> cavity_status {
+      CK(cudaMemcpyAsync(hh + (size_t)slot * w.gmax * hsz, hptr(slot, 0),
+                         sizeof(double2) * ng * hsz, cudaMemcpyDeviceToHost, st));
+      return CAVITY_OK;
+    };
+    auto hval = [&](int slot, int z, int i, int j) {
+      const double2 t = hh[(size_t)slot * w.gmax * hsz + (size_t)z * hsz + (size_t)i * BG_MAX + j];
+      return cd(t.x, t.y);
+    };
+    auto upload = [&](const std::vector<std::vector<cd>>& mats, const std::vector<int>& zs) -> cavity_status {
+      if (upl_pending) CKS(sync());
+      for (size_t q = 0; q < zs.size(); ++q) {
+        const auto& m = mats[q];
+        for (size_t t = 0; t < m.size(); ++t)
+          cup[(size_t)zs[q] * hsz + t] = make_double2(m[t].real(), m[t].imag());
+      }
+      CK(cudaMemcpyAsync(w.cb, cup, sizeof(double2) * ng * hsz, cudaMemcpyHostToDevice, st));
+      upl_pending = true;
+      return CAVITY_OK;
+    };
+    // Orthonormalise block columns [col0, col0 + r) of each listed group's
+    // basis in place by repeated SVQB; S[z] receives the r x r factor with
+    // old block = new block * S.  G0, when given, holds the Gram matrices of
+    // the blocks as they are (first pass without a device Gram).
+    auto orthonormalise = [&](const std::vector<int>& zs, const std::vector<int>& col0,
+                              std::vector<std::vector<cd>>& S,
+                              const std::vector<std::vector<cd>>* G0) -> cavity_status {
+      const int nz = (int)zs.size();
+      S.assign(nz, {});
+      std::vector<char> ok(nz, 0);
+      for (int pass = 0; pass < 4; ++pass) {
+        std::vector<int> todo;
+        for (int q = 0; q < nz; ++q)
+          if (!ok[q]) todo.push_back(q);
+        if (todo.empty()) break;
+        if (pass > 0 || !G0) {
+          BGSet set;
+          for (size_t t = 0; t < todo.size(); ++t) {
+            const int q = todo[t], z = zs[q];
+            float2* blk = Vg(z) + (size_t)col0[q] * nap;
+            set.g[t] = BGrp{blk, blk, blk, 0, gr[z], gr[z], 0};
+          }
+          bproj(ctx, set, (int)todo.size(), BG_MAX, w, 2);
+          CKS(fetch(2));
+          CKS(sync());
+        }
+        std::vector<std::vector<cd>> Ts(todo.size());
+        std::vector<int> tz;
+        BGSet set2;
+        int n2 = 0;
+        for (size_t t = 0; t < todo.size(); ++t) {
+          const int q = todo[t], z = zs[q], n = gr[z];
+          std::vector<cd> G((size_t)n * n);
+          if (pass == 0 && G0) G = (*G0)[q];
+          else
+            for (int i = 0; i < n; ++i)
+              for (int j = 0; j < n; ++j) G[(size_t)i * n + j] = hval(2, (int)t, i, j);
+          double dev = 0;
+          for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j)
+              dev = std::max(dev, std::abs(G[(size_t)i * n + j] - (i == j ? 1.0 : 0.0)));
+          if (pass > 0 && dev <= 2e-6) {
+            ok[q] = 1;
+            continue;
+          }
+          // Cholesky QR; its FP32 transform leaves an orthogonality error
+          // within the block of ~ eps32 cond(G), accepted without a check for
+          // cond(G) <= 1e3: it perturbs the least-squares residual norms by
+          // that relative amount, far below the inner tolerance, while the
+          // orthogonality to the earlier blocks comes from the two
+          // Gram-Schmidt passes.  Nearly dependent blocks take the
+          // eigendecomposition and further passes.
+          std::vector<cd> T, Sk;
+          double cond = 1e300, ratio;
+          if (cholqr(G, n, T, Sk, cond)) {
+            if (cond <= 1e3) ok[q] = 1;
+          } else {
+            svqb(G, n, T, Sk, ratio);
+          }
+          if (S[q].empty()) S[q] = Sk;
+          else matmul_left(Sk, S[q], n);
+          Ts[n2] = T;
+          tz.push_back(n2);
+          float2* blk = Vg(z) + (size_t)col0[q] * nap;
+          set2.g[n2] = BGrp{blk, blk, blk, n, n, n, n2 * (int)hsz};
+          ++n2;
+        }
+        if (n2 == 0) break;
+        Ts.resize(n2);
+        CKS(upload(Ts, tz));
+        CKS(bnn(ctx, set2, n2, w.cb, 0.f, 1.f));
+      }
+      for (int q = 0; q < nz; ++q)
+        if (S[q].empty()) {  // first pass always transforms, so this is unreachable
+          const int n = gr[zs[q]];
+          S[q].assign((size_t)n * n, cd(0, 0));
+          for (int i = 0; i < n; ++i) S[q][(size_t)i * n + i] = 1.0;
+        }
+      return CAVITY_OK;
+    };
+
+    while (true) {
+      std::vector<int> act;
+      for (int z = 0; z < ng; ++z)
+        if (!gdone[z]) act.push_back(z);
+      if (act.empty() || used >= maxit) break;
+      // cycle start: V_0 = orthonormalised residual block of each active group
+      for (int z : act)
+        CK(cudaMemcpyAsync(Vg(z), w.Rc + (size_t)goff[z] * nap, sizeof(float2) * gr[z] * nap,
+                           cudaMemcpyDeviceToDevice, st));
+      std::vector<std::vector<cd>> S0;
+      CKS(orthonormalise(act, std::vector<int>(act.size(), 0), S0, nullptr));
+      std::vector<BlockLS> ls(ng);
+      for (size_t q = 0; q < act.size(); ++q) ls[act[q]].start(gr[act[q]], S0[q]);
+      std::vector<int> cyc = act;  // groups of this cycle
+      std::vector<char> cdone(ng, 0);
+      // GPU work of block step k for the groups in `run`: W = A M^{-1} V_k,
+      // one classical Gram-Schmidt pass, the Gram matrix of the result, W into
+      // basis slot k + 1, and the coefficients on their way to the host
+      std::vector<int> woff(ng, 0);
+      auto launch_step = [&](int k, const std::vector<int>& run) -> cavity_status {
+        int nc = 0;
+        for (int z : run) {
+          woff[z] = nc;
+          CKS(launch_precond_apply<float>(ctx, gr[z], Vg(z) + (size_t)k * gr[z] * nap,
+                                          w.Z + (size_t)nc * nap));
+          nc += gr[z];
+        }
+        CKS(launch_apply<float>(ctx, nc, w.Z, w.Wb, w.apw));
+        BGSet set;
+        int kmax = 0;
+        for (size_t t = 0; t < run.size(); ++t) {
+          const int z = run[t], kv = (k + 1) * gr[z];
+          float2* wz = w.Wb + (size_t)woff[z] * nap;
+          set.g[t] = BGrp{Vg(z), wz, wz, kv, kv, gr[z], (int)(t * hsz)};
+          kmax = std::max(kmax, kv);
+        }
+        const int nr = (int)run.size();
+        bproj(ctx, set, nr, kmax, w, 0);
+        CKS(bnn(ctx, set, nr, hptr(0, 0), 1.f, -1.f));
+        // Gram matrix of the projected block, formed from it directly (the
+        // difference G(W) - H^H H cancels when W lies almost in the basis)
+        BGSet gs;
+        for (size_t t = 0; t < run.size(); ++t) {
+          float2* wz = w.Wb + (size_t)woff[run[t]] * nap;
+          gs.g[t] = BGrp{wz, wz, wz, 0, gr[run[t]], gr[run[t]], 0};
+        }
+        bproj(ctx, gs, nr, BG_MAX, w, 1);
+        for (int z : run)
+          CK(cudaMemcpyAsync(Vg(z) + (size_t)(k + 1) * gr[z] * nap, w.Wb + (size_t)woff[z] * nap,
+                             sizeof(float2) * gr[z] * nap, cudaMemcpyDeviceToDevice, st));
+        CKS(fetch(0));
+        CKS(fetch(1));
+        return CAVITY_OK;
+      };
+      // residual estimates of the last two steps per direction (convergence
+      // forecast for launching the next step before the least squares)
+      std::vector<double> e1(ndir, 1.0), e2(ndir, 1.0);
+      // run: the groups of the step being processed, in launch (slot) order;
+      // a group that converged under a step launched ahead stays in it but
+      // takes no further least-squares columns
+      std::vector<int> run = cyc, lnext;
+      bool launched = false;
+      int k = 0;
+      for (; k < mb && used < maxit; ++k) {
+        if (run.empty()) break;
+        if (!launched) CKS(launch_step(k, run));
+        launched = false;
+        CKS(sync());
+        // Gram matrix of the projected block (slot 1)
+        std::vector<std::vector<cd>> G0(run.size()), Hc(run.size());
+        for (size_t t = 0; t < run.size(); ++t) {
+          const int n = gr[run[t]], K = (k + 1) * n;
+          auto& G = G0[t];
+          G.assign((size_t)n * n, cd(0, 0));
+          for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) G[(size_t)i * n + j] = hval(1, (int)t, i, j);
+          for (int i = 0; i < n; ++i)  // exactly Hermitian
+            for (int j = 0; j < i; ++j) {
+              const cd m = 0.5 * (G[(size_t)i * n + j] + std::conj(G[(size_t)j * n + i]));
+              G[(size_t)i * n + j] = m;
+              G[(size_t)j * n + i] = std::conj(m);
+            }
+          Hc[t].resize((size_t)K * n);  // H, kept before the slots are reused
+          for (int i = 0; i < K; ++i)
+            for (int j = 0; j < n; ++j) Hc[t][(size_t)i * n + j] = hval(0, (int)t, i, j);
+        }
+        std::vector<std::vector<cd>> S;
+        std::vector<int> c0;
+        for (int z : run) c0.push_back((k + 1) * gr[z]);
+        CKS(orthonormalise(run, c0, S, &G0));
+        ++used;
+        // launch step k + 1 now unless some group is forecast to converge at
+        // step k (geometric extrapolation of its estimates)
+        std::vector<int> active;
+        for (int z : run)
+          if (!cdone[z]) active.push_back(z);
+        bool soon = false;
+        for (int z : active)
+          for (int j = 0; j < gr[z]; ++j) {
+            const int dd = dirs[goff[z] + j];
+            const double f = e2[dd] > 0 ? e1[dd] * std::min(1.0, e1[dd] / e2[dd]) : e1[dd];
+            soon = soon || f <= 2.0 * tol[dd];
+          }
+        if (!soon && k + 1 < mb && used < maxit) {
+          CKS(launch_step(k + 1, active));
+          launched = true;
+          lnext = active;
+        }
+        // least squares of step k (overlaps the GPU work just launched)
+        std::vector<int> next;
+        for (size_t t = 0; t < run.size(); ++t) {
+          const int z = run[t], n = gr[z], K = (k + 1) * n;
+          if (cdone[z]) continue;
+          std::vector<std::vector<cd>> cols(n, std::vector<cd>((size_t)K + n, cd(0, 0)));
+          for (int j = 0; j < n; ++j) {
+            for (int i = 0; i < K; ++i) cols[j][i] = Hc[t][(size_t)i * n + j];
+            for (int i = 0; i < n; ++i) cols[j][K + i] = S[t][(size_t)i * n + j];
+          }
+          ls[z].add(cols, K + n);
+          bool conv = true;
+          for (int j = 0; j < n; ++j) {
+            const int dd = dirs[goff[z] + j];
+            iters[dd] += 1;
+            est[dd] = ls[z].resid(j);
+            e2[dd] = e1[dd];
+            e1[dd] = est[dd];
+            conv = conv && est[dd] <= tol[dd];
+          }
+          if (conv) cdone[z] = 1;
+          else next.push_back(z);
+        }
+        if (next.empty()) break;
+        run = launched ? lnext : next;
+      }
+      // corrections of this cycle: d += M^{-1} V Y per group
+      std::vector<std::vector<cd>> Ys;
+      std::vector<int> yz;
+      BGSet set;
+      int n = 0;
+      for (int z : cyc) {
+        std::vector<cd> Y;
+        ls[z].solve(Y);
+        if (ls[z].cols == 0) continue;
+        Ys.push_back(Y);
+        yz.push_back(n);
+        set.g[n] = BGrp{Vg(z), nullptr, w.Tt + (size_t)goff[z] * nap, ls[z].cols, ls[z].cols, gr[z],
+                        n * (int)hsz};
+        ++n;
+      }
+      if (n > 0) {
+        CKS(upload(Ys, yz));
+        CKS(bnn(ctx, set, n, w.cb, 0.f, 1.f));
+      }
+      // T -> Z = M^{-1} T, scattered into the direction columns of d
+      std::vector<int> done_now;
+      for (int z : cyc) {
+        if (ls[z].cols == 0) continue;
+        CKS(launch_precond_apply<float>(ctx, gr[z], w.Tt + (size_t)goff[z] * nap,
+                                        w.Z + (size_t)goff[z] * nap));
+        KScope ks_(ctx, KC_KRYLOV);
+        k_scatter_add<<<dim3(bg_blocks(nap, 256), gr[z]), 256, 0, st>>>(
+            w.Z + (size_t)goff[z] * nap, d, w.map + goff[z], nap);
+      }
+      for (int z : cyc)
+        if (cdone[z]) gdone[z] = 1;
+      bool rest = false;
+      for (int z : cyc) rest = rest || !gdone[z];
+      if (!rest || used >= maxit) break;
+      // restart: R_c <- R_c - A M^{-1} (V Y) for the groups still running
+      for (int z : cyc) {
+        if (gdone[z]) continue;
+        CKS(launch_precond_apply<float>(ctx, gr[z], w.Tt + (size_t)goff[z] * nap,
+                                        w.Z + (size_t)goff[z] * nap));
+        CKS(launch_apply<float>(ctx, gr[z], w.Z + (size_t)goff[z] * nap,
+                                w.Wb + (size_t)goff[z] * nap, w.apw));
+        KScope ks_(ctx, KC_KRYLOV);
+        k_sub_cols<<<dim3(bg_blocks(nap, 256), gr[z]), 256, 0, st>>>(
+            w.Wb + (size_t)goff[z] * nap, w.Rc + (size_t)goff[z] * nap, nap);
+      }
+    }
+  }
+  CK(cudaGetLastError());
+  return CAVITY_OK;
+}

@@ -139,6 +139,8 @@ struct cavity_ctx {
   void* ws2 = nullptr;
   size_t stage_bytes = 0;   // device staging of cavity_solve (right-hand sides,
   void* stage = nullptr;    // and outputs that go to host memory)
+  size_t pin_bytes = 0;     // pinned host staging of the block Krylov
+  void* pin = nullptr;      // coefficient matrices (asynchronous copies)
 
   // ---- launch accounting: counts always, CUDA-event times while timing is on
   long long nlaunch[KC_N] = {0};
@@ -220,6 +222,23 @@ template <typename F> inline cudaError_t allow_max_smem(F func) {
                               smem_optin() - (int)a.sharedSizeBytes);
 }
 
+// grow the pinned host staging to at least `bytes`
+inline cavity_status ensure_pin(cavity_ctx* ctx, size_t bytes) {
+  if (ctx->pin_bytes >= bytes) return CAVITY_OK;
+  if (ctx->pin) cudaFreeHost(ctx->pin);
+  ctx->pin = nullptr;
+  ctx->pin_bytes = 0;
+  cudaError_t e = cudaMallocHost(&ctx->pin, bytes);
+  if (e != cudaSuccess) {
+    ctx->pin = nullptr;
+    ctx->err = "pinned staging allocation of " + std::to_string(bytes) + " bytes failed: " +
+               cudaGetErrorString(e);
+    return CAVITY_ENOMEM;
+  }
+  ctx->pin_bytes = bytes;
+  return CAVITY_OK;
+}
+
 // grow a workspace to at least `bytes`
 inline cavity_status ensure_ws(cavity_ctx* ctx, void** p, size_t* have, size_t bytes) {
   if (*have >= bytes) return CAVITY_OK;
@@ -265,6 +284,13 @@ cavity_status run_gmres64(cavity_ctx* ctx, int ndir, const double2* b, double2* 
                           int* iters, double* resid);
 cavity_status run_mixed_solve(cavity_ctx* ctx, int ndir, const double2* b, double2* x,
                               int* iters, double* resid);
+// FP32 block GMRES for the inner solves of the mixed refinement (bgmres.cu):
+// solves A M^{-1} y = r_d for the directions with active[d], d = M^{-1} y.
+cavity_status run_block_inner(cavity_ctx* ctx, int ndir, const float2* r, float2* d,
+                              const std::vector<double>& tol, const std::vector<char>& active,
+                              int mb, int maxit, void* work, std::vector<int>& iters,
+                              std::vector<double>& est);
+size_t block_inner_work_bytes(const Geo& g, int ndir, int mb);
 template <typename T>
 cavity_status launch_field(cavity_ctx* ctx, int ndir, const double2* ap, C<T>* out);
 cavity_status launch_rcs(cavity_ctx* ctx, int ndir, const double2* ap,

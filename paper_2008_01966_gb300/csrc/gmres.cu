@@ -13,7 +13,8 @@
 // copied back once per iteration.
 //
 // Mixed precision (CAVITY_MIXED): iterative refinement in FP64 around FP32
-// GMRES:  solve A d = r with FP32 GMRES to ~1e-5;  x += d (FP64);  update r;
+// block GMRES (bgmres.cu; all directions of a group share one Krylov basis):
+// solve A d = r with FP32 block GMRES to ~1e-5;  x += d (FP64);  update r;
 // repeat until ||r|| <= tol ||b||.  The residual is updated two ways:
 //   while the correction is large (||r|| > RES32_MAX ||b||, always after the
 //   first solve): r = b - A x with the operator in pair-of-FP32 arithmetic
@@ -596,35 +597,40 @@ __global__ void k_sub32(double2* __restrict__ r, const float2* __restrict__ y,
 // residuals above this fraction of ||b|| are recomputed with the FP64 operator
 #define RES32_MAX 1e-4
 
-// MIXED path: FP64 iterative refinement around FP32 GMRES.
+// MIXED path: FP64 iterative refinement around FP32 block GMRES (bgmres.cu).
 cavity_status run_mixed_solve(cavity_ctx* ctx, int ndir, const double2* b, double2* x, int* iters,
                               double* resid) {
   const Geo& g = ctx->g;
   double tol;
   int m, maxit;
   solver_params(ctx, tol, m, maxit);
+  // block steps per cycle: the block basis grows by one column per direction
+  // and step, and the inner solves converge in about a dozen steps
+  const int mb = std::max(2, std::min(m, 30));
   auto al = [](size_t v) { return (v + 255) / 256 * 256; };
   const long long nv = (long long)ndir * g.nap;
-  size_t n32 = gw_bytes<float>(g, ndir, m);
-  size_t extra = 3 * al(sizeof(double2) * nv) + 2 * al(sizeof(float2) * nv) +
-                 al(apply_pair_work_bytes(g, ndir)) + al(sizeof(double) * ndir) +
-                 al(sizeof(double2) * ndir);
-  CKS(ensure_ws(ctx, &ctx->ws, &ctx->ws_bytes, n32 + extra));
-  GW<float> W = gw_carve<float>(ctx->ws, g, ndir, m);
-  char* p = (char*)ctx->ws + n32;
+  const size_t nb = al(block_inner_work_bytes(g, ndir, mb));
+  size_t extra = 2 * al(sizeof(double2) * nv) + 2 * al(sizeof(float2) * nv) +
+                 al(apply_pair_work_bytes(g, ndir)) + al(apply_work_bytes(g, ndir, sizeof(float2))) +
+                 al(sizeof(double) * ndir) + al(sizeof(double2) * ndir) +
+                 al(sizeof(double2) * (size_t)ndir * mdot_chunks(g.nap));
+  CKS(ensure_ws(ctx, &ctx->ws, &ctx->ws_bytes, nb + extra));
+  void* bw = ctx->ws;
+  char* p = (char*)ctx->ws + nb;
   double2* r64 = (double2*)p; p += al(sizeof(double2) * nv);
   double2* tmp64 = (double2*)p; p += al(sizeof(double2) * nv);
-  p += al(sizeof(double2) * nv);
   float2* r32 = (float2*)p; p += al(sizeof(float2) * nv);
   float2* d32 = (float2*)p; p += al(sizeof(float2) * nv);
   void* apw64 = p; p += al(apply_pair_work_bytes(g, ndir));
+  void* apw32 = p; p += al(apply_work_bytes(g, ndir, sizeof(float2)));
   double* sdev = (double*)p; p += al(sizeof(double) * ndir);
-  double2* sc2 = (double2*)p;
+  double2* sc2 = (double2*)p; p += al(sizeof(double2) * ndir);
+  double2* part = (double2*)p;
   cudaStream_t st = ctx->stream;
   std::vector<double> bn, rn;
   CK(cudaMemsetAsync(x, 0, sizeof(double2) * nv, st));
   CK(cudaMemcpyAsync(r64, b, sizeof(double2) * nv, cudaMemcpyDeviceToDevice, st));
-  CKS(norms<double>(ctx, b, ndir, sc2, 1, bn, W.part));
+  CKS(norms<double>(ctx, b, ndir, sc2, 1, bn, part));
   rn = bn;
   std::vector<int> it(ndir, 0);
   std::vector<double> est, s(ndir), tin(ndir);
@@ -647,7 +653,9 @@ cavity_status run_mixed_solve(cavity_ctx* ctx, int ndir, const double2* b, doubl
       k_to32<<<dim3(nblk(g.nap, 256), ndir), 256, 0, st>>>(r64, r32, sdev, g.nap);
     }
     std::vector<int> it_in(ndir, 0);
-    CKS(gmres_core<float>(ctx, ndir, r32, d32, tin, m, maxit - used, W, it_in, est));
+    std::vector<char> act(ndir, 0);
+    for (int d = 0; d < ndir; ++d) act[d] = s[d] > 0;
+    CKS(run_block_inner(ctx, ndir, r32, d32, tin, act, mb, maxit - used, bw, it_in, est));
     int mx = 0;
     for (int d = 0; d < ndir; ++d) { it[d] += it_in[d]; mx = std::max(mx, it_in[d]); }
     used += std::max(mx, 1);
@@ -667,13 +675,13 @@ cavity_status run_mixed_solve(cavity_ctx* ctx, int ndir, const double2* b, doubl
       CK(cudaMemcpyAsync(r64, tmp64, sizeof(double2) * nv, cudaMemcpyDeviceToDevice, st));
     } else {
       // r = r - A d with the FP32 operator on the scaled correction
-      CKS(launch_apply<float>(ctx, ndir, d32, r32, W.apw));
+      CKS(launch_apply<float>(ctx, ndir, d32, r32, apw32));
       {
         KScope ks_(ctx, KC_KRYLOV);
         k_sub32<<<dim3(nblk(g.nap, 256), ndir), 256, 0, st>>>(r64, r32, sdev, g.nap);
       }
     }
-    CKS(norms<double>(ctx, r64, ndir, sc2, 1, rn, W.part));
+    CKS(norms<double>(ctx, r64, ndir, sc2, 1, rn, part));
   }
   bool all = true;
   for (int d = 0; d < ndir; ++d) {

@@ -328,3 +328,43 @@ def test_minimal_grid_and_errors(gb):
     with pytest.raises(gb.CavityError) as e:
         g2.prepare(3.0, w['layers'])
     assert e.value.status == 3
+
+
+def test_mixed_block_solver_groups_duplicates_restarts(gb):
+    """The mixed path's inner solves run block GMRES over groups of at most 16
+    directions.  21 directions (groups of 11 and 10) with two repeated pairs,
+    solved with the default block length and with restarts after every 2
+    block steps: every aperture within 1e-8 of the oracle's dense solve, and
+    the repeated directions give the same result."""
+    w = CASES["layer3"]
+    cav = ocav(w)
+    sysm = ApertureSystem(cav)
+    th, ph, al = workloads.directions(19, 41)
+    th = np.concatenate([th, th[[3, 11]]])
+    ph = np.concatenate([ph, ph[[3, 11]]])
+    al = np.concatenate([al, al[[3, 11]]])
+    B = np.array([oracle_rhs(cav, t, p, a) for t, p, a in zip(th, ph, al)])
+    X = sysm.solve_dense(B)
+    for restart in (40, 2):
+        g = gcav(gb, w, precision="mixed", gmres_tol=1e-10, gmres_restart=restart,
+                 gmres_max_iter=400)
+        ap, _, it, res = g.solve(w['kappa0'], w['layers'], th, ph, al, field=False)
+        assert np.all(res <= 1e-10), (restart, res.max())
+        ap = ap.cpu().numpy()
+        for d in range(len(th)):
+            assert rel(ap[d], X[d]) < 1e-8, (restart, d)
+        assert rel(ap[19], ap[3]) < 1e-9 and rel(ap[20], ap[11]) < 1e-9
+
+
+def test_mixed_result_alone_and_in_the_mix(gb):
+    """A direction solved alone and inside a batch (where it shares a Krylov
+    block with the others) agrees within the solver tolerance."""
+    w = CASES["homog"]
+    th, ph, al = workloads.directions(6, 23)
+    g = gcav(gb, w, precision="mixed", gmres_tol=1e-10)
+    ap6, _, _, _ = g.solve(w['kappa0'], w['layers'], th, ph, al, field=False)
+    ap6 = ap6.cpu().numpy()
+    for d in (0, 5):
+        ap1, _, _, _ = g.solve(w['kappa0'], w['layers'], th[d:d + 1], ph[d:d + 1], al[d:d + 1],
+                               field=False)
+        assert rel(ap1.cpu().numpy()[0], ap6[d]) < 1e-8
