@@ -165,30 +165,32 @@ __global__ void __launch_bounds__(256, 2) k_bproj(BGSet set, double2* __restrict
 #define BP_SMEM (sizeof(float2) * 4 * BP_ROWS * 16)
 
 // h[z][i][j] = sum over the nct slabs of part[z][x][i][j] in a fixed order.
-// grid (ceil(K/16), groups), 1024 threads: output (i, j) of the 16-row tile is
-// t & 255; the four thread quarters take slabs x = t >> 8 (mod 4) in order and
-// are added in quarter order.
-__global__ void __launch_bounds__(1024) k_bproj_final(BGSet set, const double2* __restrict__ part,
-                                                      double2* __restrict__ h, int nct, int kcap) {
-  __shared__ double2 q4[4][256];
+// grid (K, groups), 256 threads: thread t adds the slabs x = t >> 4 (mod 16)
+// of column j = t & 15 (16 consecutive threads read one 256-byte row of
+// partials), and the 16 slab classes are added in class order.
+__global__ void __launch_bounds__(256) k_bproj_final(BGSet set, const double2* __restrict__ part,
+                                                     double2* __restrict__ h, int nct, int kcap) {
+  __shared__ double2 q16[16][16];
   const BGrp& gd = set.g[blockIdx.y];
-  const int t = threadIdx.x, o = t & 255, qg = t >> 8;
-  const int i = blockIdx.x * 16 + (o >> 4), j = o & 15;
+  const int i = blockIdx.x;
+  if (i >= gd.K) return;  // uniform over the block
+  const int t = threadIdx.x, j = t & 15, xg = t >> 4;
   double sx = 0, sy = 0;
-  if (i < gd.K && j < gd.r) {
-    for (int x = qg; x < nct; x += 4) {
+  if (j < gd.r) {
+#pragma unroll 4
+    for (int x = xg; x < nct; x += 16) {
       const double2 v = part[((size_t)(blockIdx.y * nct + x) * kcap + i) * BG_MAX + j];
       sx += v.x;
       sy += v.y;
     }
   }
-  q4[qg][o] = make_double2(sx, sy);
+  q16[xg][j] = make_double2(sx, sy);
   __syncthreads();
-  if (qg == 0 && i < gd.K && j < gd.r) {
+  if (t < 16 && t < gd.r) {
     double ax = 0, ay = 0;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) { ax += q4[q][o].x; ay += q4[q][o].y; }
-    h[((size_t)blockIdx.y * kcap + i) * BG_MAX + j] = make_double2(ax, ay);
+    for (int q = 0; q < 16; ++q) { ax += q16[q][t].x; ay += q16[q][t].y; }
+    h[((size_t)blockIdx.y * kcap + i) * BG_MAX + t] = make_double2(ax, ay);
   }
 }
 
@@ -610,7 +612,7 @@ static void bproj(cavity_ctx* ctx, const BGSet& set, int ng, int kmax, const BWo
   }
   {
     KScope ks_(ctx, KC_KRYLOV);
-    k_bproj_final<<<dim3(ytiles, ng), 1024, 0, ctx->stream>>>(set, w.part, h, nct, w.kcap);
+    k_bproj_final<<<dim3(kmax, ng), 256, 0, ctx->stream>>>(set, w.part, h, nct, w.kcap);
   }
 }
 
