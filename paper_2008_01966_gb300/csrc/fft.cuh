@@ -195,6 +195,25 @@ __device__ __forceinline__ C<T> twid(const C<T>* __restrict__ tw, int idx) {
   return w;
 }
 
+// Barrier of the threads that transform one line (tpl consecutive threads,
+// several lines per call): the warp when tpl <= 32, else a named barrier per
+// group of tpl threads (ids 1..15; id 0 is __syncthreads), so the groups of a
+// block do not wait for each other between passes.  Lines of different groups
+// never share shared memory within a transform call, and every transform call
+// ends with a block barrier.  The branch depends only on tpl and the block
+// size, so all threads of a block take the same one.
+__device__ __forceinline__ void line_group_sync(int tpl) {
+  const int nthr = blockDim.x * blockDim.y;
+  if (tpl <= 32) {
+    __syncwarp();
+  } else if (tpl >= nthr || (tpl & 31) != 0 || nthr % tpl != 0 || nthr / tpl > 15) {
+    __syncthreads();
+  } else {
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + tid / tpl), "r"(tpl) : "memory");
+  }
+}
+
 // radix-R pass (R = 2^LR), PER butterflies per thread (PER * R = E, or 1 for n < E)
 template <typename T, bool INV, int LR, int PER, bool FIRST = false, bool LAST = false,
           typename Op = LineId<T>>
@@ -233,7 +252,7 @@ __device__ __forceinline__ void fft_pass(C<T>* line, int n, int s, int t, int tp
       }
     }
   }
-  __syncthreads();
+  line_group_sync(tpl);
   if (active) {
 #pragma unroll
     for (int q = 0; q < PER; ++q) {
@@ -260,7 +279,7 @@ __device__ __forceinline__ void fft_pass(C<T>* line, int n, int s, int t, int tp
       }
     }
   }
-  __syncthreads();
+  line_group_sync(tpl);
 }
 
 // Warp transform of one line of length n = LW * RV (RV = LW or 2 LW) by LW lanes

@@ -36,67 +36,50 @@ template <typename T> __host__ __device__ constexpr int field_lines(int n) {
   return fft_tpl<T>(n) >= FIELD_THREADS ? 1 : FIELD_THREADS / fft_tpl<T>(n);
 }
 
-// pass 1: grid (ceil(nx / L) row groups, 3 components, ndir * lc slabs);
-// instantiated per LNY = log2 ny.  A cooperative gather forms the
-// coefficients (profile times aperture value) and mirrors them into the lines;
-// the scaled store of T1 (q <= ny) is the transform's last write.
-template <typename T, int LNY>
-struct FieldY {
+// Pairing.  The cosine synthesis of one coefficient row and the sine synthesis
+// of another share one complex FFT: the extended line of the cosine row is
+// even, that of the sine row odd, so the transform Z of their sum splits into
+// the two syntheses as the even and odd parts,
+//   C(q) = (Z(q) + Z(-q)) / 2,   S(q) = (Z(q) - Z(-q)) / 2.
+// Along x2, E2 (cos) row m pairs with E1 (sin) row m; along x1, E1 (cos)
+// column q pairs with E2 (sin) column q.  E3 (sin, sin) lines stay single.
+// Group g = blockIdx.y: 0 the pairs, 1 the E3 lines.
+
+// modal coefficient of component c (0, 1, 2) at (m, n) for level j, zero
+// outside the component's index set: profile times aperture value, plus the
+// E3-driven term for E1, E2 in a layered fill
+template <typename T>
+struct FieldCoef {
   const C<T>* E;                  // aperture coefficients of this direction
   const C<T>* Pj;                 // profiles of level j
   const C<T>* Qj;                 // E3-driven profiles of level j (layered) or null
-  C<T>* dst;                      // T1 rows of this (slab, component)
-  int r0, nx, M, N, n1, n2, comp;
+  int M, N, n1, n2;
   bool top, layered;
-  __device__ __forceinline__ C<T> coef(int r, int n) const {
-    const int m = comp == 0 ? r : r + 1;
-    if (r >= nx || m > M) return mk<T>(0, 0);
+  __device__ __forceinline__ C<T> operator()(int c, int m, int n) const {
     int i;
-    if (comp == 0) {
-      if (n < 1) return mk<T>(0, 0);
+    if (c == 0) {
+      if (m > M || n < 1 || n > N) return mk<T>(0, 0);
       i = m * N + (n - 1);
-    } else if (comp == 1) {
+    } else if (c == 1) {
+      if (m < 1 || m > M || n > N) return mk<T>(0, 0);
       i = n1 + (m - 1) * (N + 1) + n;
     } else {
-      if (n < 1) return mk<T>(0, 0);
+      if (m < 1 || m > M || n < 1 || n > N) return mk<T>(0, 0);
       i = n1 + n2 + (m - 1) * N + (n - 1);
     }
-    C<T> c = E[i];
+    C<T> v = E[i];
     if (!top) {
-      c = cmul<T>(Pj[i], c);
-      if (layered && comp < 2 && m >= 1 && n >= 1)
-        c = cadd<T>(c, cmul<T>(Qj[i], E[n1 + n2 + (m - 1) * N + (n - 1)]));
+      v = cmul<T>(Pj[i], v);
+      if (layered && c < 2 && m >= 1 && n >= 1)
+        v = cadd<T>(v, cmul<T>(Qj[i], E[n1 + n2 + (m - 1) * N + (n - 1)]));
     }
-    return c;
-  }
-  __device__ __forceinline__ C<T> ld(int l, const C<T>*, int k) const {
-    constexpr int ny = 1 << LNY, n2x = 2 * ny;
-    const bool ycos = comp == 1;
-    const int r = r0 + l;
-    if (k < ny) {
-      if (k == 0) return ycos ? cscale<T>(coef(r, 0), (T)2) : mk<T>(0, 0);
-      return coef(r, k);
-    }
-    if (k == ny) return mk<T>(0, 0);
-    const C<T> c = coef(r, n2x - k);
-    return ycos ? c : mk<T>(-c.x, -c.y);
-  }
-  __device__ __forceinline__ void st(int l, C<T>*, int q, C<T> v) const {
-    constexpr int ny = 1 << LNY;
-    const int r = r0 + l;
-    if (q > ny || r >= nx) return;
-    // cos: Z/2 ; sin: Z/(2i)
-    dst[(size_t)r * (ny + 1) + q] =
-        comp == 1 ? mk<T>(v.x * (T)0.5, v.y * (T)0.5) : mk<T>(v.y * (T)0.5, -v.x * (T)0.5);
+    return v;
   }
 };
 
-// the gathered line as the first read, FieldY's store as the last write
-template <typename T, int LNY>
-struct FieldYStore : FieldY<T, LNY> {
-  __device__ __forceinline__ C<T> ld(int, const C<T>* line, int t) const { return line[pidx(t)]; }
-};
-
+// pass 1: grid (ceil(nx / L), 2 groups, ndir * lc slabs); instantiated per
+// LNY = log2 ny.  Line l of group 0 is row m = r0 + l (E2 even + E1 odd), of
+// group 1 row m = r0 + l + 1 (E3 odd).  T1 rows: E1 at m, E2 and E3 at m - 1.
 template <typename T, int LNY>
 __global__ void __launch_bounds__(FIELD_THREADS, 2) k_field_y(const C<T>* __restrict__ ap,
                                                            const C<T>* __restrict__ prof,
@@ -107,93 +90,78 @@ __global__ void __launch_bounds__(FIELD_THREADS, 2) k_field_y(const C<T>* __rest
   C<T>* buf = (C<T>*)sm_raw;
   constexpr int ny = 1 << LNY, n2 = 2 * ny, ls = padded_len(n2);
   constexpr int L = field_lines<T>(n2);
-  const int comp = blockIdx.y, s = blockIdx.z;
-  const int d = s / p.lc, jj = s - d * p.lc;
+  const int grp = blockIdx.y, s = blockIdx.z;
+  const int jj = s / p.ndir, d = s - jj * p.ndir;  // directions fastest: a level's profile is reused from L2
   const int j = p.j0 + jj;
   if (j > p.nz) return;
-  FieldY<T, LNY> op;
-  op.E = ap + (size_t)d * p.nap;
-  op.Pj = prof + (size_t)(j - 1) * p.nap;
-  op.Qj = profq ? profq + (size_t)(j - 1) * (p.n1 + p.n2) : nullptr;
-  op.dst = T1 + ((size_t)s * 3 + comp) * p.nx * (ny + 1);
-  op.r0 = blockIdx.x * L;
-  op.nx = p.nx;
-  op.M = p.M;
-  op.N = p.N;
-  op.n1 = p.n1;
-  op.n2 = p.n2;
-  op.comp = comp;
-  op.top = (j == p.nz);
-  op.layered = p.layered;
-  // cooperative gather: consecutive threads take consecutive n of a row, all
-  // of a thread's loads are issued before its first store, and the mirrored
-  // coefficients go straight into the lines (every slot is written)
+  FieldCoef<T> cf;
+  cf.E = ap + (size_t)d * p.nap;
+  cf.Pj = prof + (size_t)(j - 1) * p.nap;
+  cf.Qj = profq ? profq + (size_t)(j - 1) * (p.n1 + p.n2) : nullptr;
+  cf.M = p.M;
+  cf.N = p.N;
+  cf.n1 = p.n1;
+  cf.n2 = p.n2;
+  cf.top = (j == p.nz);
+  cf.layered = p.layered;
+  const int r0 = blockIdx.x * L;
+  const int mo = grp == 0 ? 0 : 1;  // row m of line l is r0 + l + mo
+  // cooperative gather: consecutive threads take consecutive n of a row; all
+  // loads of a thread are issued before its first store into the lines
   constexpr int PER = L * ny / FIELD_THREADS;
   static_assert(PER * FIELD_THREADS == L * ny, "rows must tile the block");
-  C<T> cv[PER];
+  C<T> ce[PER], so[PER];
 #pragma unroll
   for (int k = 0; k < PER; ++k) {
     const int idx = threadIdx.x + k * FIELD_THREADS;
-    cv[k] = op.coef(op.r0 + (idx >> LNY), idx & (ny - 1));
+    const int m = r0 + (idx >> LNY) + mo, n = idx & (ny - 1);
+    if (grp == 0) {
+      ce[k] = cf(1, m, n);
+      so[k] = cf(0, m, n);
+    } else {
+      ce[k] = mk<T>(0, 0);
+      so[k] = cf(2, m, n);
+    }
   }
-  const bool ycos = comp == 1;
 #pragma unroll
   for (int k = 0; k < PER; ++k) {
     const int idx = threadIdx.x + k * FIELD_THREADS;
     const int l = idx >> LNY, n = idx & (ny - 1);
     C<T>* line = buf + (size_t)l * ls;
-    const C<T> c = cv[k];
     if (n == 0) {
-      line[0] = ycos ? cscale<T>(c, (T)2) : mk<T>(0, 0);
+      line[0] = cscale<T>(ce[k], (T)2);
       line[pidx(ny)] = mk<T>(0, 0);
     } else {
-      line[pidx(n)] = c;
-      line[pidx(n2 - n)] = ycos ? c : mk<T>(-c.x, -c.y);
+      line[pidx(n)] = cadd<T>(ce[k], so[k]);
+      line[pidx(n2 - n)] = csub<T>(ce[k], so[k]);
     }
   }
   __syncthreads();
-  FieldYStore<T, LNY> st;
-  static_cast<FieldY<T, LNY>&>(st) = op;
-  fft_lines<T, true, LNY + 1>(buf, ls, L, tw, p.twlog, st);
+  fft_lines<T, true, LNY + 1>(buf, ls, L, tw, p.twlog);
+  // split and store: cos part scaled by 1/2, sine part by 1/(2i)
+  C<T>* t1 = T1 + (size_t)s * 3 * p.nx * (ny + 1);
+  for (int idx = threadIdx.x; idx < L * (ny + 1); idx += FIELD_THREADS) {
+    const int l = idx / (ny + 1), q = idx - l * (ny + 1);
+    const int m = r0 + l + mo;
+    if (m > p.M) continue;
+    const C<T>* line = buf + (size_t)l * ls;
+    const C<T> zq = line[pidx(q)];
+    const C<T> zm = line[pidx((n2 - q) & (n2 - 1))];
+    if (grp == 0) {
+      const C<T> c = cscale<T>(cadd<T>(zq, zm), (T)0.25);
+      const C<T> sn = cscale<T>(csub<T>(zq, zm), (T)0.25);
+      t1[(size_t)m * (ny + 1) + q] = mk<T>(sn.y, -sn.x);  // E1 row m
+      if (m >= 1) t1[((size_t)p.nx + m - 1) * (ny + 1) + q] = c;  // E2 row m - 1
+    } else {
+      t1[((size_t)2 * p.nx + m - 1) * (ny + 1) + q] = mk<T>(zq.y * (T)0.5, -zq.x * (T)0.5);
+    }
+  }
 }
 
-// pass 2: grid (ceil((ny+1) / L) column groups, 3 components, ndir * lc
-// slabs); instantiated per LNX = log2 nx.  The column gather of T1 and the
-// mirroring are the transform's first read, the scaled store of the output
-// rows its last write.
-template <typename T, int LNX>
-struct FieldX {
-  const C<T>* src;                // T1 rows of this (slab, component)
-  C<T>* dst;                      // this component's output block of level j
-  int q0, ny, comp, ncol, qlo, qhi, plo, phi;
-  __device__ __forceinline__ C<T> ld(int l, const C<T>*, int t) const {
-    constexpr int nx = 1 << LNX, n2 = 2 * nx;
-    const int q = q0 + l;
-    if (q > ny || t == nx) return mk<T>(0, 0);
-    const bool xcos = comp == 0;
-    // E1: rows r = m (m = 0..nx-1); E2, E3: rows r = m - 1 (m = 1..nx-1)
-    if (t < nx) {
-      if (t == 0) return xcos ? cscale<T>(src[q], (T)2) : mk<T>(0, 0);
-      return src[(size_t)(xcos ? t : t - 1) * (ny + 1) + q];
-    }
-    const int m = n2 - t;
-    const C<T> c = src[(size_t)(xcos ? m : m - 1) * (ny + 1) + q];
-    return xcos ? c : mk<T>(-c.x, -c.y);
-  }
-  __device__ __forceinline__ void st(int l, C<T>*, int pp, C<T> v) const {
-    const int q = q0 + l;
-    if (pp < plo || pp > phi || q < qlo || q > qhi) return;
-    dst[(size_t)(pp - plo) * ncol + (q - qlo)] =
-        comp == 0 ? mk<T>(v.x * (T)0.5, v.y * (T)0.5) : mk<T>(v.y * (T)0.5, -v.x * (T)0.5);
-  }
-};
-
-// the gathered line as the first read, FieldX's store as the last write
-template <typename T, int LNX>
-struct FieldXStore : FieldX<T, LNX> {
-  __device__ __forceinline__ C<T> ld(int, const C<T>* line, int t) const { return line[pidx(t)]; }
-};
-
+// pass 2: grid (ceil((ny+1) / L) column groups, 2 groups, ndir * lc slabs);
+// instantiated per LNX = log2 nx.  Line l of group 0 is column q = q0 + l
+// (E1 even + E2 odd), of group 1 column q = q0 + l + 1 (E3 odd).  The split
+// samples are written a row segment of L columns at a time.
 template <typename T, int LNX>
 __global__ void __launch_bounds__(FIELD_THREADS, 2) k_field_x(const C<T>* __restrict__ T1,
                                                            C<T>* __restrict__ out, FP p,
@@ -203,68 +171,72 @@ __global__ void __launch_bounds__(FIELD_THREADS, 2) k_field_x(const C<T>* __rest
   constexpr int nx = 1 << LNX, n2 = 2 * nx, ls = padded_len(n2);
   constexpr int L = field_lines<T>(n2);
   const int ny = p.ny;
-  const int comp = blockIdx.y, s = blockIdx.z;
-  const int d = s / p.lc, jj = s - d * p.lc;
+  const int grp = blockIdx.y, s = blockIdx.z;
+  const int jj = s / p.ndir, d = s - jj * p.ndir;  // directions fastest: a level's profile is reused from L2
   const int j = p.j0 + jj;
   if (j > p.nz) return;
-  FieldX<T, LNX> op;
-  op.src = T1 + ((size_t)s * 3 + comp) * nx * (ny + 1);
-  op.q0 = blockIdx.x * L;
-  op.ny = ny;
-  op.comp = comp;
-  long long off;
-  if (comp == 0) {
-    off = 0; op.ncol = ny - 1; op.qlo = 1; op.qhi = ny - 1; op.plo = 0; op.phi = nx;
-  } else if (comp == 1) {
-    off = (long long)(nx + 1) * (ny - 1);
-    op.ncol = ny + 1; op.qlo = 0; op.qhi = ny; op.plo = 1; op.phi = nx - 1;
-  } else {
-    off = (long long)(nx + 1) * (ny - 1) + (long long)(nx - 1) * (ny + 1);
-    op.ncol = ny - 1; op.qlo = 1; op.qhi = ny - 1; op.plo = 1; op.phi = nx - 1;
-  }
-  op.dst = out + ((size_t)d * p.nz + (j - 1)) * p.S + off;
-  // cooperative gather of the L columns of T1: consecutive threads take
-  // consecutive columns of a row, all loads of a thread in flight before its
-  // first store; mirrored into the lines (slots m = nx, and m = 0 for the sine
-  // extension, cleared)
+  const C<T>* t1 = T1 + (size_t)s * 3 * nx * (ny + 1);
+  const int q0 = blockIdx.x * L + (grp == 0 ? 0 : 1);
+  const int qhi = grp == 0 ? ny : ny - 1;  // last column of the group
   constexpr int lL = clog2(L);
   constexpr int PER = L * nx / FIELD_THREADS;
   static_assert(PER * FIELD_THREADS == L * nx, "columns must tile the block");
-  const bool xcos = comp == 0;
-  const int nrows = xcos ? nx : nx - 1;    // E1: m = 0..M; E2/E3: m = 1..M
-  C<T> cv[PER];
+  // cooperative gather of the L columns: consecutive threads take consecutive
+  // columns of a T1 row (row t of the cos part is E1 row t, of the sine part
+  // E2 / E3 row t - 1)
+  C<T> ce[PER], so[PER];
 #pragma unroll
   for (int k = 0; k < PER; ++k) {
     const int idx = threadIdx.x + k * FIELD_THREADS;
-    const int r = idx >> lL, q = op.q0 + (idx & (L - 1));
-    cv[k] = (q <= ny && r < nrows) ? op.src[(size_t)r * (ny + 1) + q] : mk<T>(0, 0);
+    const int t = idx >> lL, q = q0 + (idx & (L - 1));
+    const bool in = q <= qhi;
+    if (grp == 0) {
+      ce[k] = (in && q >= 1 && q < ny) ? t1[(size_t)t * (ny + 1) + q] : mk<T>(0, 0);
+      so[k] = (in && t >= 1) ? t1[((size_t)nx + t - 1) * (ny + 1) + q] : mk<T>(0, 0);
+    } else {
+      ce[k] = mk<T>(0, 0);
+      so[k] = (in && t >= 1) ? t1[((size_t)2 * nx + t - 1) * (ny + 1) + q] : mk<T>(0, 0);
+    }
   }
 #pragma unroll
   for (int k = 0; k < PER; ++k) {
     const int idx = threadIdx.x + k * FIELD_THREADS;
-    const int r = idx >> lL, l = idx & (L - 1);
+    const int t = idx >> lL, l = idx & (L - 1);
     C<T>* line = buf + (size_t)l * ls;
-    const C<T> c = cv[k];
-    if (xcos) {
-      if (r == 0) {
-        line[0] = cscale<T>(c, (T)2);
-        line[pidx(nx)] = mk<T>(0, 0);
-      } else {
-        line[pidx(r)] = c;
-        line[pidx(n2 - r)] = c;
-      }
-    } else if (r < nx - 1) {
-      line[pidx(r + 1)] = c;
-      line[pidx(n2 - r - 1)] = mk<T>(-c.x, -c.y);
-    } else {
-      line[0] = mk<T>(0, 0);
+    if (t == 0) {
+      line[0] = cscale<T>(ce[k], (T)2);
       line[pidx(nx)] = mk<T>(0, 0);
+    } else {
+      line[pidx(t)] = cadd<T>(ce[k], so[k]);
+      line[pidx(n2 - t)] = csub<T>(ce[k], so[k]);
     }
   }
   __syncthreads();
-  FieldXStore<T, LNX> st;
-  static_cast<FieldX<T, LNX>&>(st) = op;
-  fft_lines<T, true, LNX + 1>(buf, ls, L, tw, p.twlog, st);
+  fft_lines<T, true, LNX + 1>(buf, ls, L, tw, p.twlog);
+  // split and store, consecutive threads on consecutive columns of a row
+  C<T>* o = out + ((size_t)d * p.nz + (j - 1)) * p.S;
+  const long long offE2 = (long long)(nx + 1) * (ny - 1);
+  const long long offE3 = offE2 + (long long)(nx - 1) * (ny + 1);
+  for (int idx = threadIdx.x; idx < (nx + 1) * L; idx += FIELD_THREADS) {
+    const int pp = idx >> lL, l = idx & (L - 1);
+    const int q = q0 + l;
+    if (q > qhi) continue;
+    const C<T>* line = buf + (size_t)l * ls;
+    const C<T> zq = line[pidx(pp)];
+    if (grp == 0) {
+      const C<T> zm = line[pidx((n2 - pp) & (n2 - 1))];
+      if (q >= 1 && q < ny) {  // E1 (cos in x1) on p = 0..nx
+        const C<T> c = cscale<T>(cadd<T>(zq, zm), (T)0.25);
+        o[(size_t)pp * (ny - 1) + (q - 1)] = c;
+      }
+      if (pp >= 1 && pp < nx) {  // E2 (sin in x1) on p = 1..nx-1
+        const C<T> sn = cscale<T>(csub<T>(zq, zm), (T)0.25);
+        o[offE2 + (size_t)(pp - 1) * (ny + 1) + q] = mk<T>(sn.y, -sn.x);
+      }
+    } else if (pp >= 1 && pp < nx) {  // E3 on p = 1..nx-1, q = 1..ny-1
+      o[offE3 + (size_t)(pp - 1) * (ny - 1) + (q - 1)] = mk<T>(zq.y * (T)0.5, -zq.x * (T)0.5);
+    }
+  }
 }
 
 __global__ void k_ap32(const double2* __restrict__ a, float2* __restrict__ b, long long n) {
@@ -316,7 +288,7 @@ cavity_status launch_field(cavity_ctx* ctx, int ndir, const double2* ap, C<T>* o
         done = true;
       }
       KScope ks_(ctx, KC_FIELD_Y);
-      k_field_y<T, LN><<<dim3((g.nx + L - 1) / L, 3, ndir * lc), FIELD_THREADS,
+      k_field_y<T, LN><<<dim3((g.nx + L - 1) / L, 2, ndir * lc), FIELD_THREADS,
                          sizeof(C<T>) * (size_t)L * padded_len(2 << LN), ctx->stream>>>(
           apT, prof, profq, T1, p, tw);
       return CAVITY_OK;
@@ -329,7 +301,7 @@ cavity_status launch_field(cavity_ctx* ctx, int ndir, const double2* ap, C<T>* o
         done = true;
       }
       KScope ks_(ctx, KC_FIELD_X);
-      k_field_x<T, LN><<<dim3((g.ny + 1 + L - 1) / L, 3, ndir * lc), FIELD_THREADS,
+      k_field_x<T, LN><<<dim3((g.ny + 1 + L - 1) / L, 2, ndir * lc), FIELD_THREADS,
                          sizeof(C<T>) * (size_t)L * padded_len(2 << LN), ctx->stream>>>(
           T1, out, p, tw);
       return CAVITY_OK;
