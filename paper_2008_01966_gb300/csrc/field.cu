@@ -88,7 +88,8 @@ __global__ void __launch_bounds__(FIELD_THREADS, 2) k_field_y(const C<T>* __rest
                                                            const C<T>* __restrict__ tw) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   C<T>* buf = (C<T>*)sm_raw;
-  constexpr int ny = 1 << LNY, n2 = 2 * ny, ls = padded_len(n2);
+  // odd line pitch: accesses across the lines of a block hit distinct banks
+  constexpr int ny = 1 << LNY, n2 = 2 * ny, ls = padded_len(n2) | 1;
   constexpr int L = field_lines<T>(n2);
   const int grp = blockIdx.y, s = blockIdx.z;
   const int jj = s / p.ndir, d = s - jj * p.ndir;  // directions fastest: a level's profile is reused from L2
@@ -168,7 +169,7 @@ __global__ void __launch_bounds__(FIELD_THREADS, 2) k_field_x(const C<T>* __rest
                                                            const C<T>* __restrict__ tw) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   C<T>* buf = (C<T>*)sm_raw;
-  constexpr int nx = 1 << LNX, n2 = 2 * nx, ls = padded_len(n2);
+  constexpr int nx = 1 << LNX, n2 = 2 * nx, ls = padded_len(n2) | 1;
   constexpr int L = field_lines<T>(n2);
   const int ny = p.ny;
   const int grp = blockIdx.y, s = blockIdx.z;
@@ -289,7 +290,7 @@ cavity_status launch_field(cavity_ctx* ctx, int ndir, const double2* ap, C<T>* o
       }
       KScope ks_(ctx, KC_FIELD_Y);
       k_field_y<T, LN><<<dim3((g.nx + L - 1) / L, 2, ndir * lc), FIELD_THREADS,
-                         sizeof(C<T>) * (size_t)L * padded_len(2 << LN), ctx->stream>>>(
+                         sizeof(C<T>) * (size_t)L * (padded_len(2 << LN) | 1), ctx->stream>>>(
           apT, prof, profq, T1, p, tw);
       return CAVITY_OK;
     }));
@@ -302,7 +303,7 @@ cavity_status launch_field(cavity_ctx* ctx, int ndir, const double2* ap, C<T>* o
       }
       KScope ks_(ctx, KC_FIELD_X);
       k_field_x<T, LN><<<dim3((g.ny + 1 + L - 1) / L, 2, ndir * lc), FIELD_THREADS,
-                         sizeof(C<T>) * (size_t)L * padded_len(2 << LN), ctx->stream>>>(
+                         sizeof(C<T>) * (size_t)L * (padded_len(2 << LN) | 1), ctx->stream>>>(
           T1, out, p, tw);
       return CAVITY_OK;
     }));
