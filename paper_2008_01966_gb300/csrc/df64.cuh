@@ -15,7 +15,7 @@
 #pragma once
 #include "common.cuh"
 
-struct df {
+struct __align__(8) df {
   float hi, lo;
   df() = default;
   __host__ __device__ constexpr df(float h, float l) : hi(h), lo(l) {}
@@ -26,7 +26,8 @@ struct df {
   __host__ __device__ explicit operator double() const { return (double)hi + (double)lo; }
 };
 
-struct cdf {
+// 16-byte aligned so that a complex value moves as one vector access
+struct __align__(16) cdf {
   df x, y;
 };
 template <> struct cplx_t<df> { typedef cdf type; };

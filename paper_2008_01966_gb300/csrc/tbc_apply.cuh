@@ -60,7 +60,9 @@ template <typename T> __host__ __device__ constexpr int lines_per_cta(int nlong)
 template <typename T> __host__ __device__ constexpr int pairs_per_cta(int n) {
   return 2 * fft_tpl<T>(n) >= LINES_THREADS ? 1 : LINES_THREADS / (2 * fft_tpl<T>(n));
 }
-// registers: FP32 and FP64 kernels run two CTAs of LINES_THREADS per SM
+// registers: the pass kernels run two CTAs of LINES_THREADS per SM (the
+// pair-of-FP32 ones spill ~450 bytes per thread at this bound, but one CTA per
+// SM without spills was slower: pass B 10.6 ms against 7.6 ms)
 #define TBC_BOUNDS __launch_bounds__(LINES_THREADS, 2)
 
 // The pass kernels are instantiated per grid size: LNY = log2 ny (passes A,
