@@ -87,6 +87,12 @@ typedef struct {
                          /*   the asymptotic tail (two-term J0 and Fresnel      */
                          /*   expansions); an approximation, inaccurate near    */
                          /*   2 pi rho = kappa0                                 */
+  int modes_m, modes_n;  /* aperture expansion truncated to the modes m <=      */
+                         /* modes_m, n <= modes_n (Galerkin restriction of      */
+                         /* (EJ1)/(uT1): the other aperture unknowns are zero    */
+                         /* and their rows dropped), as in the paper's runs with */
+                         /* few modes (Sec. 7, Table 2: M ~ 2a/lambda); 0 -> all */
+                         /* (M = nx-1, N = ny-1); must not exceed M, N          */
 } cavity_desc;
 enum { CAVITY_KHAT_QUADRATURE = 0, CAVITY_KHAT_PAPER = 1 };
 
@@ -181,7 +187,8 @@ cavity_status cavity_rhs(cavity_ctx* ctx, int ndir, const double* theta,
 
 /* y = A x for the reduced aperture matrix of (EJ1)/(uT1): x, y ndir x n_ap
  * (device), complex128 when precision == CAVITY_FP64 or CAVITY_PAIR32 and
- * complex64 when CAVITY_MIXED.  Other precision values: CAVITY_EINVAL. */
+ * complex64 when CAVITY_MIXED.  Other precision values: CAVITY_EINVAL.  With a
+ * truncated mode set (modes_m, modes_n) the rows of the dropped modes are 0. */
 cavity_status cavity_apply(cavity_ctx* ctx, int ndir, int precision,
                            const void* x, void* y);
 

@@ -177,6 +177,27 @@ class ApertureSystem:
         A = self.dense()
         return sla.solve(A, np.asarray(b).T).T
 
+    def kept_modes(self, mm, nn):
+        """Unknowns of the modes (m, n) with m <= mm and n <= nn: the truncated
+        aperture expansion of the paper's runs (Sec. 7, Table 2 keeps
+        M ~ 2a/lambda modes).  Boolean mask in Appendix A order."""
+        M, N = self.cav.M, self.cav.N
+        def keep(m0, n0):
+            m, n = np.meshgrid(np.arange(m0, M + 1), np.arange(n0, N + 1), indexing='ij')
+            return ((m <= mm) & (n <= nn)).ravel()
+        return np.concatenate([keep(0, 1), keep(1, 0), keep(1, 1)])
+
+    def solve_truncated(self, b, mm, nn):
+        """Galerkin restriction of (EJ1)/(uT1) to the kept modes: the rows and
+        columns of the dropped modes removed, a dense solve of the rest, zeros
+        for the dropped unknowns."""
+        A = self.dense()
+        k = self.kept_modes(mm, nn)
+        b = np.atleast_2d(b)
+        X = np.zeros(b.shape, dtype=complex)
+        X[:, k] = sla.solve(A[np.ix_(k, k)], b[:, k].T).T
+        return X
+
     def solve_gmres(self, b, rtol=1e-13, restart=200, maxiter=200):
         """Restarted GMRES (SciPy) on the matrix-free operator with the block
         diagonal as preconditioner; the true residual is recomputed afterwards.

@@ -40,7 +40,7 @@ class Cavity:
 
     def __init__(self, a, b, c, nx, ny, nz, precision="fp64", gmres_tol=0.0, gmres_restart=0,
                  gmres_max_iter=0, pivot_tol=0.0, stream=None, device=None,
-                 khat_scheme="quadrature"):
+                 khat_scheme="quadrature", modes_m=0, modes_n=0):
         self.lib = _lib.load()
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
         torch.cuda.set_device(self.device)
@@ -48,7 +48,7 @@ class Cavity:
         self.precision = _lib.CAVITY_FP64 if precision == "fp64" else _lib.CAVITY_MIXED
         d = _lib.CavityDesc(a, b, c, nx, ny, nz, self.precision, 4, gmres_tol, gmres_restart,
                             gmres_max_iter, pivot_tol,
-                            {"quadrature": 0, "paper": 1}[khat_scheme])
+                            {"quadrature": 0, "paper": 1}[khat_scheme], modes_m, modes_n)
         h = ctypes.c_void_p()
         st = self.lib.cavity_setup(ctypes.byref(d), ctypes.c_void_p(self.stream.cuda_stream),
                                    ctypes.byref(h))

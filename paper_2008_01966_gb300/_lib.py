@@ -34,7 +34,7 @@ class CavityDesc(ctypes.Structure):
                 ("precision", ctypes.c_int), ("pad_factor", ctypes.c_int),
                 ("gmres_tol", ctypes.c_double), ("gmres_restart", ctypes.c_int),
                 ("gmres_max_iter", ctypes.c_int), ("pivot_tol", ctypes.c_double),
-                ("khat_scheme", ctypes.c_int)]
+                ("khat_scheme", ctypes.c_int), ("modes_m", ctypes.c_int), ("modes_n", ctypes.c_int)]
 
 
 class CavityError(RuntimeError):

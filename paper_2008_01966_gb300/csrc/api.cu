@@ -42,6 +42,8 @@ extern "C" cavity_status cavity_setup(const cavity_desc* desc, void* cuda_stream
   if (d.gmres_restart > 120) return bad("gmres_restart must be at most 120");
   if (d.khat_scheme != CAVITY_KHAT_QUADRATURE && d.khat_scheme != CAVITY_KHAT_PAPER)
     return bad("khat_scheme must be CAVITY_KHAT_QUADRATURE or CAVITY_KHAT_PAPER");
+  if (d.modes_m < 0 || d.modes_m > d.nx - 1 || d.modes_n < 0 || d.modes_n > d.ny - 1)
+    return bad("modes_m, modes_n must be in [0, nx-1], [0, ny-1]");
   cavity_ctx* ctx = new cavity_ctx();
   ctx->desc = d;
   if (ctx->desc.pad_factor == 0) ctx->desc.pad_factor = 4;
@@ -291,6 +293,7 @@ extern "C" cavity_status cavity_solve(cavity_ctx* ctx, double kappa0, int nlayer
   if (host) p += al(sizeof(double2) * nv);
   void* fld = host ? (void*)p : field_out;
   CKS(launch_rhs(ctx, ndir, theta, phi, alpha, b));
+  CKS(launch_mode_mask(ctx, ndir, b));  // truncated expansion: the kept rows only
   cavity_status st;
   if (ctx->desc.precision == CAVITY_FP64)
     st = run_gmres64(ctx, ndir, b, x, iters_out, resid_out);

@@ -291,6 +291,9 @@ cavity_status run_block_inner(cavity_ctx* ctx, int ndir, const float2* r, float2
                               int mb, int maxit, void* work, std::vector<int>& iters,
                               std::vector<double>& est);
 size_t block_inner_work_bytes(const Geo& g, int ndir, int mb);
+// zero the aperture unknowns outside the truncated mode set (modes_m, modes_n
+// of the descriptor; no-op without truncation), ndir contiguous FP64 vectors
+cavity_status launch_mode_mask(cavity_ctx* ctx, int ndir, double2* v);
 template <typename T>
 cavity_status launch_field(cavity_ctx* ctx, int ndir, const double2* ap, C<T>* out);
 cavity_status launch_rcs(cavity_ctx* ctx, int ndir, const double2* ap,

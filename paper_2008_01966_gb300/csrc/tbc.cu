@@ -167,3 +167,7 @@ extern "C" cavity_status cavity_apply_noalloc(cavity_ctx* ctx, int ndir, int pre
   CK(cudaStreamSynchronize(ctx->stream));
   return CAVITY_OK;
 }
+
+cavity_status launch_mode_mask(cavity_ctx* ctx, int ndir, double2* v) {
+  return launch_mode_mask_t<double>(ctx, ndir, v, ctx->g.nap, KC_RHS);
+}

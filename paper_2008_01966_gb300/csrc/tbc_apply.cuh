@@ -571,6 +571,45 @@ template <typename T> static int kclass(int k) {
   return KC_TBC_AP + k;
 }
 
+// Truncated aperture expansion (Sec. 7, Table 2: the paper's runs keep the
+// modes m <= ~2a/lambda): y_i = 0 for unknowns i of a mode (m, n) with
+// m > mm or n > nn.  Unknown order (Appendix A): E1 over m = 0..M, n = 1..N;
+// E2 over m = 1..M, n = 0..N; E3 over m = 1..M, n = 1..N.
+// grid (ceil(nap / 256), ndir)
+template <typename T>
+__global__ void k_mode_mask(C<T>* __restrict__ y, long long ystride, int nap, int N, int n1, int n2,
+                            int mm, int nn) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nap) return;
+  int m, n;
+  if (i < n1) {
+    m = i / N;
+    n = i - m * N + 1;
+  } else if (i < n1 + n2) {
+    const int j = i - n1;
+    m = j / (N + 1) + 1;
+    n = j - (m - 1) * (N + 1);
+  } else {
+    const int j = i - n1 - n2;
+    m = j / N + 1;
+    n = j - (m - 1) * N + 1;
+  }
+  if (m > mm || n > nn) y[(size_t)blockIdx.y * ystride + i] = czero<T>();
+}
+
+template <typename T>
+cavity_status launch_mode_mask_t(cavity_ctx* ctx, int ndir, C<T>* y, long long ystride, int cls) {
+  const cavity_desc& d = ctx->desc;
+  if (d.modes_m <= 0 && d.modes_n <= 0) return CAVITY_OK;
+  const Geo& g = ctx->g;
+  const int mm = d.modes_m > 0 ? d.modes_m : g.M, nn = d.modes_n > 0 ? d.modes_n : g.N;
+  KScope ks_(ctx, cls);
+  k_mode_mask<T><<<dim3((g.nap + 255) / 256, ndir), 256, 0, ctx->stream>>>(y, ystride, g.nap, g.N, g.n1,
+                                                                          g.n2, mm, nn);
+  CK(cudaGetLastError());
+  return CAVITY_OK;
+}
+
 template <typename T>
 cavity_status launch_apply(cavity_ctx* ctx, int ndir, const C<T>* x, C<T>* y, void* work,
                            long long ystride) {
@@ -634,6 +673,9 @@ cavity_status launch_apply(cavity_ctx* ctx, int ndir, const C<T>* x, C<T>* y, vo
                                                                        ystride, p);
   }
   CK(cudaGetLastError());
+  // truncated expansion: the rows of the dropped modes (the operator then
+  // maps the kept subspace to itself, as does the mode-wise preconditioner)
+  CKS(launch_mode_mask_t<T>(ctx, ndir, y, ystride, kclass<T>(4)));
   return CAVITY_OK;
 }
 

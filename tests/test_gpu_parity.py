@@ -368,3 +368,27 @@ def test_mixed_result_alone_and_in_the_mix(gb):
         ap1, _, _, _ = g.solve(w['kappa0'], w['layers'], th[d:d + 1], ph[d:d + 1], al[d:d + 1],
                                field=False)
         assert rel(ap1.cpu().numpy()[0], ap6[d]) < 1e-8
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_truncated_expansion_matches_oracle(gb, precision):
+    """Aperture expansion truncated to m <= 6, n <= 9 (the paper's runs keep
+    few modes, Sec. 7): aperture and field against the oracle's restricted
+    dense solve, per result; the dropped unknowns are exactly zero."""
+    w = CASES["layer3"]
+    cav = ocav(w)
+    sysm = ApertureSystem(cav)
+    th, ph, al = workloads.directions(3, 17)
+    B = np.array([oracle_rhs(cav, t, p, a) for t, p, a in zip(th, ph, al)])
+    X = sysm.solve_truncated(B, 6, 9)
+    keep = sysm.kept_modes(6, 9)
+    fp64 = precision == "fp64"
+    g = gcav(gb, w, precision=precision, gmres_tol=1e-12 if fp64 else 1e-10, modes_m=6, modes_n=9)
+    ap, fl, it, res = g.solve(w['kappa0'], w['layers'], th, ph, al)
+    ap = ap.cpu().numpy()
+    fl = fl.cpu().numpy()
+    for d in range(3):
+        assert np.all(ap[d][~keep] == 0)
+        assert rel(ap[d], X[d]) < (1e-10 if fp64 else 1e-8)
+        F = oracle_field(cav, sysm.prof, X[d]).ravel()
+        assert rel(fl[d], F) < (1e-10 if fp64 else 1e-5)

@@ -11,6 +11,7 @@ import pytest
 import scipy.fft as sfft
 from scipy import integrate, special
 
+import workloads
 from oracle.aperture import ApertureSystem
 from oracle.brute import solve_unreduced
 from oracle.excitation import g_tilde, incident, rhs
@@ -335,3 +336,28 @@ def test_field_top_level_is_aperture_synthesis():
     ref = np.concatenate([(cosx @ e1 @ siny.T).ravel(), (sinx @ e2 @ cosy.T).ravel(),
                           (sinx @ e3 @ siny.T).ravel()])
     assert np.allclose(f, ref, atol=1e-13)
+
+
+def test_truncated_expansion_limits():
+    """The truncated aperture expansion (Sec. 7: the paper's runs keep few
+    modes): keeping every mode is the full solve; the kept set is counted
+    right (3 mm nn + mm + nn unknowns for mm < M, nn < N); the dropped
+    unknowns are zero; and the error against the full solution falls as
+    modes are added (rows of the dense system restricted, so the limit is
+    fixed by the full solve)."""
+    w = workloads.scaled('dirs16', 16, nz=8, ndir=1)
+    cav = Cavity(w['a'], w['b'], w['c'], w['nx'], w['ny'], w['nz'], w['kappa0'],
+                 layers=[Layer(n, e) for n, e in w['layers']])
+    s = ApertureSystem(cav)
+    b = rhs(cav, w['theta'][0], w['phi'][0], w['alpha'][0])
+    full = s.solve_dense(b)
+    assert np.allclose(s.solve_truncated(b, cav.M, cav.N)[0], full, rtol=0, atol=1e-13 * np.abs(full).max())
+    for mm, nn in ((3, 5), (7, 2)):
+        k = s.kept_modes(mm, nn)
+        assert k.sum() == 3 * mm * nn + mm + nn
+        X = s.solve_truncated(b, mm, nn)[0]
+        assert np.all(X[~k] == 0)
+    errs = [np.linalg.norm(s.solve_truncated(b, m, m)[0] - full) / np.linalg.norm(full)
+            for m in (2, 4, 8, 12)]
+    assert all(e1 > e2 for e1, e2 in zip(errs, errs[1:])), errs
+    assert errs[-1] < 0.2 * errs[0]
