@@ -93,6 +93,12 @@ extern "C" void cavity_destroy(cavity_ctx* ctx) {
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (ctx->pin) cudaFreeHost(ctx->pin);
+  for (auto e : ctx->copy_evs) cudaEventDestroy(e);
+  if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+  for (int k = 0; k < 3; ++k) {
+    if (ctx->copy_join[k]) cudaEventDestroy(ctx->copy_join[k]);
+    if (ctx->copy_more[k]) cudaStreamDestroy(ctx->copy_more[k]);
+  }
   for (auto& e : ctx->evs) {
     cudaEventDestroy(e.a);
     cudaEventDestroy(e.b);
@@ -300,16 +306,29 @@ extern "C" cavity_status cavity_solve(cavity_ctx* ctx, double kappa0, int nlayer
   else
     st = run_mixed_solve(ctx, ndir, b, x, iters_out, resid_out);
   if (st != CAVITY_OK && st != CAVITY_ENOCONV) return st;
+  if (host) {
+    // host outputs go out on the copy stream, overlapped with the field
+    // synthesis: the aperture now, the field chunk by chunk (launch_field)
+    CKS(ensure_copy_stream(ctx, 2));
+    CK(cudaEventRecord(ctx->copy_evs[0], ctx->stream));
+    CK(cudaStreamWaitEvent(ctx->copy_stream, ctx->copy_evs[0], 0));
+    CK(cudaMemcpyAsync(aperture_out, x, sizeof(double2) * nv, cudaMemcpyDeviceToHost,
+                       ctx->copy_stream));
+  }
   if (out_mode == CAVITY_OUT_FIELD) {
+    void* hf = host ? field_out : nullptr;
     if (ctx->desc.precision == CAVITY_FP64)
-      CKS(launch_field<double>(ctx, ndir, x, (double2*)fld));
+      CKS(launch_field<double>(ctx, ndir, x, (double2*)fld, hf));
     else
-      CKS(launch_field<float>(ctx, ndir, x, (float2*)fld));
+      CKS(launch_field<float>(ctx, ndir, x, (float2*)fld, hf));
   }
   if (host) {
-    CK(cudaMemcpyAsync(aperture_out, x, sizeof(double2) * nv, cudaMemcpyDeviceToHost, ctx->stream));
-    if (out_mode == CAVITY_OUT_FIELD)
-      CK(cudaMemcpyAsync(field_out, fld, fbytes, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaEventRecord(ctx->copy_evs[1], ctx->copy_stream));
+    CK(cudaStreamWaitEvent(ctx->stream, ctx->copy_evs[1], 0));
+    for (int k = 0; k < 3; ++k) {
+      CK(cudaEventRecord(ctx->copy_join[k], ctx->copy_more[k]));
+      CK(cudaStreamWaitEvent(ctx->stream, ctx->copy_join[k], 0));
+    }
   }
   CK(cudaStreamSynchronize(ctx->stream));
   return st;

@@ -141,6 +141,10 @@ struct cavity_ctx {
   void* stage = nullptr;    // and outputs that go to host memory)
   size_t pin_bytes = 0;     // pinned host staging of the block Krylov
   void* pin = nullptr;      // coefficient matrices (asynchronous copies)
+  cudaStream_t copy_stream = nullptr;   // device-to-host copies of host outputs,
+  std::vector<cudaEvent_t> copy_evs;    // overlapped with the field synthesis
+  cudaStream_t copy_more[3] = {nullptr, nullptr, nullptr};  // further copy engines
+  cudaEvent_t copy_join[3] = {nullptr, nullptr, nullptr};
 
   // ---- launch accounting: counts always, CUDA-event times while timing is on
   long long nlaunch[KC_N] = {0};
@@ -294,8 +298,41 @@ size_t block_inner_work_bytes(const Geo& g, int ndir, int mb);
 // zero the aperture unknowns outside the truncated mode set (modes_m, modes_n
 // of the descriptor; no-op without truncation), ndir contiguous FP64 vectors
 cavity_status launch_mode_mask(cavity_ctx* ctx, int ndir, double2* v);
+// host_out (optional): a host buffer of the field's layout; each chunk of
+// levels is copied there on ctx->copy_stream as soon as it is written (the
+// caller joins the copy stream)
 template <typename T>
-cavity_status launch_field(cavity_ctx* ctx, int ndir, const double2* ap, C<T>* out);
+cavity_status launch_field(cavity_ctx* ctx, int ndir, const double2* ap, C<T>* out,
+                           void* host_out = nullptr);
+// the copy stream and at least n events for it (created once per context)
+inline cavity_status ensure_copy_stream(cavity_ctx* ctx, size_t n) {
+  if (!ctx->copy_stream) {
+    cudaError_t e = cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      ctx->copy_stream = nullptr;
+      ctx->err = cudaGetErrorString(e);
+      return CAVITY_ECUDA;
+    }
+  }
+  for (int k = 0; k < 3; ++k) {
+    if (ctx->copy_more[k]) continue;
+    if (cudaStreamCreateWithFlags(&ctx->copy_more[k], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->copy_join[k], cudaEventDisableTiming) != cudaSuccess) {
+      ctx->err = "copy stream creation failed";
+      return CAVITY_ECUDA;
+    }
+  }
+  while (ctx->copy_evs.size() < n) {
+    cudaEvent_t ev;
+    cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      ctx->err = cudaGetErrorString(e);
+      return CAVITY_ECUDA;
+    }
+    ctx->copy_evs.push_back(ev);
+  }
+  return CAVITY_OK;
+}
 cavity_status launch_rcs(cavity_ctx* ctx, int ndir, const double2* ap,
                          const double* th, const double* ph, int pol, double* sigma);
 

@@ -246,7 +246,8 @@ __global__ void k_ap32(const double2* __restrict__ a, float2* __restrict__ b, lo
 }
 
 template <typename T>
-cavity_status launch_field(cavity_ctx* ctx, int ndir, const double2* ap, C<T>* out) {
+cavity_status launch_field(cavity_ctx* ctx, int ndir, const double2* ap, C<T>* out,
+                           void* host_out) {
   const Geo& g = ctx->g;
   const bool layered = ctx->layers.size() > 1;
   const size_t slab = (size_t)3 * g.nx * (g.ny + 1) * sizeof(C<T>);
@@ -279,7 +280,10 @@ cavity_status launch_field(cavity_ctx* ctx, int ndir, const double2* ap, C<T>* o
   p.nx = g.nx; p.ny = g.ny; p.nz = g.nz; p.M = g.M; p.N = g.N; p.n1 = g.n1; p.n2 = g.n2;
   p.nap = g.nap; p.lnx = g.lnx; p.lny = g.lny; p.twlog = ilog2(ctx->TW);
   p.lc = lc; p.ndir = ndir; p.layered = layered; p.S = g.field_per_level;
-  for (int j0 = 1; j0 <= g.nz; j0 += lc) {
+  const int nchunk = (g.nz + lc - 1) / lc;
+  if (host_out) CKS(ensure_copy_stream(ctx, (size_t)nchunk + 2));
+  int chunk = 0;
+  for (int j0 = 1; j0 <= g.nz; j0 += lc, ++chunk) {
     p.j0 = j0;
     CKS(dispatch_log<CAV_LOG_MIN, CAV_LOG_MAX>(g.lny, [&](auto c) -> cavity_status {
       constexpr int LN = decltype(c)::value, L = field_lines<T>(2 << LN);
@@ -307,10 +311,27 @@ cavity_status launch_field(cavity_ctx* ctx, int ndir, const double2* ap, C<T>* o
           T1, out, p, tw);
       return CAVITY_OK;
     }));
+    if (host_out) {
+      // this chunk's levels of every direction to the host while the next
+      // chunk is synthesised (one contiguous segment per direction)
+      // segments round-robin over four copy streams (several copy engines)
+      cudaEvent_t ev = ctx->copy_evs[2 + chunk];
+      CK(cudaEventRecord(ev, ctx->stream));
+      cudaStream_t cs[4] = {ctx->copy_stream, ctx->copy_more[0], ctx->copy_more[1],
+                            ctx->copy_more[2]};
+      for (int k = 0; k < 4; ++k) CK(cudaStreamWaitEvent(cs[k], ev, 0));
+      const int nl = std::min(lc, g.nz - j0 + 1);
+      for (int d = 0; d < ndir; ++d) {
+        const size_t off = ((size_t)d * g.nz + (j0 - 1)) * (size_t)g.field_per_level;
+        CK(cudaMemcpyAsync((C<T>*)host_out + off, out + off,
+                           sizeof(C<T>) * (size_t)nl * g.field_per_level, cudaMemcpyDeviceToHost,
+                           cs[d & 3]));
+      }
+    }
   }
   CK(cudaGetLastError());
   return CAVITY_OK;
 }
 
-template cavity_status launch_field<double>(cavity_ctx*, int, const double2*, double2*);
-template cavity_status launch_field<float>(cavity_ctx*, int, const double2*, float2*);
+template cavity_status launch_field<double>(cavity_ctx*, int, const double2*, double2*, void*);
+template cavity_status launch_field<float>(cavity_ctx*, int, const double2*, float2*, void*);
