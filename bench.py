@@ -42,7 +42,7 @@ TOL = 1e-7
 # capture on 8 directions, scaled to the 16 directions of a launch here
 # (traffic is proportional to the directions).  Only valid for the kernel as
 # captured: emptied whenever the kernel changes, refilled from the next capture.
-NCU_TRAFFIC = {"tbc_B_fp32": 2 * (52.560896e6 + 20.722944e6)}   # profiles/tbc_B_fp32_dirs16.txt
+NCU_TRAFFIC = {"tbc_B_fp32": 2 * (52.550656e6 + 21.679616e6)}   # profiles/tbc_B_fp32_dirs16.txt
 
 
 def peaks():
