@@ -10,15 +10,17 @@
 // on the 16-direction 64^2 and 128^2 workloads: 10-11 block steps against
 // 13-14 per-direction steps to 1e-5).
 //
-// Orthogonalisation of the new block W against the basis V: classical
-// Gram-Schmidt in two passes, each a pair of GEMM-shaped kernels -- V^H W by a
-// split reduction over the rows (k_bproj, k_bproj_final) and W -= V H with one
-// row per thread (k_bnn).  The block itself is then orthonormalised by SVQB
-// (Stathopoulos and Wu, 2002): W = V' S with V' = W U Lambda^{-1/2} from the
-// eigendecomposition G = W^H W = U Lambda U^H; eigenvalues below a floor are
-// raised to it, so nearly dependent directions (repeated incident directions,
-// converged columns) never divide by ~0 and W = V' S holds exactly, and the
-// step is repeated until V'^H V' is the identity to FP32 accuracy.
+// Orthogonalisation of the new block W against the basis V: one classical
+// Gram-Schmidt pass as two GEMM-shaped kernels on the tensor pipe (warp-level
+// mma.sync, TF32 operands split into three products for FP32 accuracy):
+// V^H W by a split reduction over the rows (k_bproj_tc, then k_bproj_final in
+// a fixed order) and W -= V H (k_bnn_tc).  The Gram matrix of the projected
+// block is then formed (k_bproj_tc with W against itself) and the block is
+// orthonormalised by Cholesky QR, or by SVQB (Stathopoulos and Wu, 2002:
+// W = V' S with V' = W U Lambda^{-1/2} from G = W^H W = U Lambda U^H,
+// eigenvalues below a floor raised to it) when it is nearly dependent
+// (repeated incident directions, converged columns), so W = V' S holds
+// exactly and nothing divides by ~0; a vanished block is an exact breakdown.
 //
 // The least-squares problems min || E_1 S_0 - Hbar Y || (block upper Hessenberg,
 // one right-hand side per direction of the group) are solved on the host in
@@ -44,9 +46,9 @@ typedef std::complex<double> cd;
 struct BGrp {
   const float2* V;  // Kv basis columns, stride nap
   const float2* W;  // r block columns, stride nap
-  float2* O;        // output columns, stride nap (k_bnn)
-  int Kv;           // columns taken from V (k_bnn multiplies these)
-  int K;            // projected columns (k_bproj): V_0..V_{Kv-1}, then W_0..W_{K-Kv-1}
+  float2* O;        // output columns, stride nap (k_bnn_tc)
+  int Kv;           // columns taken from V (k_bnn_tc multiplies these)
+  int K;            // projected columns (k_bproj_tc): V_0..V_{Kv-1}, then W_0..W_{K-Kv-1}
   int r;
   int coff;         // offset of this group's coefficient matrix (BG_MAX wide)
 };
@@ -54,32 +56,8 @@ struct BGSet {
   BGrp g[BG_GROUPS];
 };
 
-// Partial projections: part[z][x][i][j] = sum over the rows e of slab x of
-// conj(X_i[e]) W_j[e] for group z, i < K, j < r, where X_i is basis column i
-// for i < Kv and block column i - Kv after that (so the block's own Gram matrix
-// comes out of the same pass).  grid (nslab, ceil(K/16), groups), 256 threads:
-// a CTA owns the 16 x 16 output tile of columns 16 y .. 16 y + 15 over its slab
-// of rows, which it walks in tiles of 128 rows staged in shared memory (the next
-// tile is fetched into registers while the current one is used).  Thread t
-// computes a 4 x 4 block of the tile, i = 4 ((t & 15) >> 2) + a,
-// j = 4 (t & 3) + b, over the rows e = t >> 4 (mod 16) of each tile; the 16 row
-// classes are summed through shared memory at the end.
-#define BP_ROWS 128
-// Staged tiles are [row][16 columns] without padding; column c of row e is
-// stored at c ^ (e & 15), so the staging stores (consecutive rows, one column)
-// and the 16-byte reads of column pairs (one row) are both free of bank
-// conflicts.  A pair (c, c + 1), c even, sits at the aligned pair
-// c ^ (e & 14), swapped when e is odd.
-__device__ __forceinline__ void bp_pair(const float2* row, int c0, int s, float2& x0, float2& x1) {
-  const float4 v = *(const float4*)(row + (c0 ^ (s & 14)));
-  if (s & 1) {
-    x0 = make_float2(v.z, v.w);
-    x1 = make_float2(v.x, v.y);
-  } else {
-    x0 = make_float2(v.x, v.y);
-    x1 = make_float2(v.z, v.w);
-  }
-}
+#define BP_ROWS 128  // rows per staged tile (slabs are whole tiles)
+
 __device__ __forceinline__ void cp_async8(float2* dst, const float2* src, bool valid) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
   const int n = valid ? 8 : 0;  // 0: the 8 bytes are zero-filled
@@ -89,80 +67,6 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N> __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
 }
-
-// Tiles are copied global -> shared asynchronously into two buffers, the
-// next tile in flight while the current one is used.
-__global__ void __launch_bounds__(256, 2) k_bproj(BGSet set, double2* __restrict__ part, int nap,
-                                                  int rs, int nct, int kcap) {
-  extern __shared__ __align__(16) float2 sm[];  // 2 x (V tile, W tile); later the row-class sums
-  const BGrp& gd = set.g[blockIdx.z];
-  const int t = threadIdx.x;
-  const int tij = t & 15, ti = tij >> 2, tj = tij & 3, rcl = t >> 4;
-  const int ib = blockIdx.y * 16, K = gd.K, Kv = gd.Kv, r = gd.r;
-  const int e0 = blockIdx.x * rs, e1 = min(nap, e0 + rs);
-  // staging: element q = t + 256 u (u < 8) of a 128 x 16 tile is row q % 128, column q / 128
-  auto stage = [&](int buf, int eb) {
-    float2* vs = sm + buf * (2 * BP_ROWS * 16);
-    float2* ws = vs + BP_ROWS * 16;
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int q = t + 256 * u, c = q >> 7, el = q & 127, e = eb + el, i = ib + c;
-      const bool in = e < e1;
-      const float2* src = i < Kv ? gd.V + (size_t)i * nap : gd.W + (size_t)(i - Kv) * nap;
-      const int o = el * 16 + (c ^ (el & 15));
-      cp_async8(vs + o, (in && i < K) ? src + e : gd.W, in && i < K);
-      cp_async8(ws + o, (in && c < r) ? gd.W + (size_t)c * nap + e : gd.W, in && c < r);
-    }
-    cp_async_commit();
-  };
-  float2 acc[4][4];
-#pragma unroll
-  for (int a = 0; a < 4; ++a)
-#pragma unroll
-    for (int b = 0; b < 4; ++b) acc[a][b] = make_float2(0.f, 0.f);
-  const int ntile = (e1 - e0 + BP_ROWS - 1) / BP_ROWS;
-  if (ntile > 0) stage(0, e0);
-  if (ntile > 1) stage(1, e0 + BP_ROWS);
-  for (int it = 0; it < ntile; ++it) {
-    if (it + 1 < ntile) cp_async_wait<1>();
-    else cp_async_wait<0>();
-    __syncthreads();
-    const float2* vs = sm + (it & 1) * (2 * BP_ROWS * 16);
-    const float2* ws = vs + BP_ROWS * 16;
-#pragma unroll
-    for (int e = rcl; e < BP_ROWS; e += 16) {
-      const int sw = e & 15;
-      float2 av[4], wv[4];
-      bp_pair(vs + e * 16, 4 * ti, sw, av[0], av[1]);
-      bp_pair(vs + e * 16, 4 * ti + 2, sw, av[2], av[3]);
-      bp_pair(ws + e * 16, 4 * tj, sw, wv[0], wv[1]);
-      bp_pair(ws + e * 16, 4 * tj + 2, sw, wv[2], wv[3]);
-#pragma unroll
-      for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-          acc[a][b].x += av[a].x * wv[b].x + av[a].y * wv[b].y;
-          acc[a][b].y += av[a].x * wv[b].y - av[a].y * wv[b].x;
-        }
-    }
-    __syncthreads();
-    if (it + 2 < ntile) stage(it & 1, e0 + (it + 2) * BP_ROWS);
-  }
-  // sum the 16 row classes: output (i, j) of the tile at sm[class * 256 + i * 16 + j]
-#pragma unroll
-  for (int a = 0; a < 4; ++a)
-#pragma unroll
-    for (int b = 0; b < 4; ++b) sm[rcl * 256 + (4 * ti + a) * 16 + 4 * tj + b] = acc[a][b];
-  __syncthreads();
-  const int li = t >> 4, lj = t & 15;
-  if (ib + li < K && lj < r) {
-    double sx = 0, sy = 0;
-#pragma unroll
-    for (int q = 0; q < 16; ++q) { sx += (double)sm[q * 256 + t].x; sy += (double)sm[q * 256 + t].y; }
-    part[((size_t)(blockIdx.z * nct + blockIdx.x) * kcap + ib + li) * BG_MAX + lj] = make_double2(sx, sy);
-  }
-}
-#define BP_SMEM (sizeof(float2) * 4 * BP_ROWS * 16)
 
 // h[z][i][j] = sum over the nct slabs of part[z][x][i][j] in a fixed order.
 // grid (K, groups), 256 threads: thread t adds the slabs x = t >> 4 (mod 16)
@@ -194,86 +98,239 @@ __global__ void __launch_bounds__(256) k_bproj_final(BGSet set, const double2* _
   }
 }
 
-// O_j[e] = beta O_j[e] + sgn sum_{i<Kv} V_i[e] C[i][j]  for j < r; C is the
-// group's coefficient matrix at cmat + coff (FP64, BG_MAX wide), rounded to
-// FP32 into dynamic shared memory once (rows padded to a multiple of 4 with
-// zeros).  Each of the 128 threads takes the rows e and e + 128 of its block's
-// 256, so each coefficient read from shared memory serves two rows, and the
-// loads of the next four basis columns are in flight while the current four
-// are used.  (Small blocks keep the last partial wave of blocks short.)  All
-// inputs of a row are read before its outputs are written, so O may alias V.
-// grid (ceil(nap / 256), 1, groups); dynamic shared memory bnn_smem(Kv).
-__host__ __device__ constexpr size_t bnn_smem(int kv) {
-  return sizeof(float2) * BG_MAX * (size_t)((kv + 3) / 4 * 4);
+// O_j[e] = beta O_j[e] + sgn sum_{i<Kv} V_i[e] C[i][j] for j < r (C: the group's
+// coefficient matrix at cmat + coff, FP64, BG_MAX wide), on the tensor pipe
+// (warp-level mma.sync m16n8k8 with TF32 operands, FP32 accumulation).  The
+// complex product is a real GEMM,
+//   [Re O_j, Im O_j] = sum_i [Re V_i, Im V_i] [[Re C_ij, Im C_ij], [-Im C_ij, Re C_ij]],
+// of n_ap rows, 2 Kv inner terms and 32 outputs.  FP32 accuracy comes from the
+// three-product split of each operand into TF32 parts, x = hi + lo:
+// x y ~ hi_x hi_y + hi_x lo_y + lo_x hi_y (the dropped lo lo term is below 2^-22 |x y|).
+__device__ __forceinline__ unsigned tf32_of(float x) {
+  unsigned r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
 }
-#define BNN_THREADS 128
-__global__ void __launch_bounds__(BNN_THREADS) k_bnn(BGSet set, const double2* __restrict__ cmat, int nap,
-                                             float beta, float sgn) {
-  extern __shared__ __align__(16) float4 cs[];  // [Kv4][BG_MAX / 2]
+__device__ __forceinline__ void tf32_split(float x, unsigned& hi, unsigned& lo) {
+  hi = tf32_of(x);
+  lo = tf32_of(x - __uint_as_float(hi));
+}
+// D += A B for one 16 x 8 x 8 tile; fragments as in the PTX ISA for .tf32:
+// lane = 4 g + t; a0 (g, t), a1 (g + 8, t), a2 (g, t + 4), a3 (g + 8, t + 4);
+// b0 (t, g), b1 (t + 4, g); d0 (g, 2t), d1 (g, 2t + 1), d2 (g + 8, 2t), d3 (g + 8, 2t + 1)
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const unsigned (&a)[4], unsigned b0,
+                                         unsigned b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+#define TC_KC 32   // complex rows of C staged per chunk (64 real rows)
+#define TC_BLD 40  // row pitch (words) of the staged real C: the b-fragment loads hit distinct banks
+
+// grid (ceil(nap / 128), 1, groups), 128 threads; warp w owns the rows
+// 128 x + 32 w .. + 31 (two m16 tiles) and all 32 real outputs (four n8 tiles)
+__global__ void __launch_bounds__(128) k_bnn_tc(BGSet set, const double2* __restrict__ cmat,
+                                                int nap, float beta, float sgn) {
+  __shared__ unsigned bhi[2 * TC_KC][TC_BLD], blo[2 * TC_KC][TC_BLD];
   const BGrp& gd = set.g[blockIdx.z];
   const double2* Cm = cmat + gd.coff;
-  const int Kv = gd.Kv, K4 = (Kv + 3) / 4 * 4;
-  const int e = blockIdx.x * (2 * BNN_THREADS) + threadIdx.x, f = e + BNN_THREADS;
-  const bool ie = e < nap, jf = f < nap;
-  for (int t = threadIdx.x; t < K4 * BG_MAX; t += BNN_THREADS) {
-    const int ii = t / BG_MAX, j = t - ii * BG_MAX;
-    double2 c = make_double2(0.0, 0.0);
-    if (ii < Kv && j < gd.r) c = Cm[(size_t)ii * BG_MAX + j];
-    ((float2*)cs)[t] = make_float2((float)(sgn * c.x), (float)(sgn * c.y));
-  }
-  __syncthreads();
-  float2 p[BG_MAX], q[BG_MAX];
+  const int Kv = gd.Kv, r = gd.r;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = lane >> 2, t = lane & 3;
+  const int rbase = blockIdx.x * 128 + warp * 32;
+  float acc[2][4][4];
 #pragma unroll
-  for (int j = 0; j < BG_MAX; ++j) p[j] = q[j] = make_float2(0.f, 0.f);
-  float2 a[4], b[4];
-  auto load4 = [&](int i0) {
+  for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const bool in = i0 + u < Kv;
-      const float2* vp = gd.V + (size_t)(i0 + u) * nap;
-      a[u] = (in && ie) ? vp[e] : make_float2(0.f, 0.f);
-      b[u] = (in && jf) ? vp[f] : make_float2(0.f, 0.f);
+    for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[mt][nt][q] = 0.f;
+  for (int i0 = 0; i0 < Kv; i0 += TC_KC) {
+    __syncthreads();
+    for (int u = threadIdx.x; u < TC_KC * 16; u += 128) {
+      const int ii = u >> 4, j = u & 15;
+      double2 c = make_double2(0.0, 0.0);
+      if (i0 + ii < Kv && j < r) c = Cm[(size_t)(i0 + ii) * BG_MAX + j];
+      const float cr = (float)(sgn * c.x), ci = (float)(sgn * c.y);
+      tf32_split(cr, bhi[2 * ii][2 * j], blo[2 * ii][2 * j]);
+      tf32_split(ci, bhi[2 * ii][2 * j + 1], blo[2 * ii][2 * j + 1]);
+      tf32_split(-ci, bhi[2 * ii + 1][2 * j], blo[2 * ii + 1][2 * j]);
+      tf32_split(cr, bhi[2 * ii + 1][2 * j + 1], blo[2 * ii + 1][2 * j + 1]);
     }
+    __syncthreads();
+    const int kend = min(TC_KC, Kv - i0);
+    for (int kk = 0; kk < kend; kk += 4) {
+      // real inner index 2 kk + t is component (t & 1) of complex column kk + t / 2;
+      // 2 kk + t + 4 the same component of column kk + 2 + t / 2 (no prefetch:
+      // its registers cost more resident warps than it hid latency)
+      const int ca = i0 + kk + (t >> 1), cb = ca + 2;
+      const bool cpt = t & 1;
+      unsigned ahi[2][4], alo[2][4];
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt) {
+        const int r0 = rbase + mt * 16 + g, r1 = r0 + 8;
+        float x[4];
+        const float2 v0 = (r0 < nap && ca < Kv) ? gd.V[(size_t)ca * nap + r0] : make_float2(0.f, 0.f);
+        const float2 v1 = (r1 < nap && ca < Kv) ? gd.V[(size_t)ca * nap + r1] : make_float2(0.f, 0.f);
+        const float2 v2 = (r0 < nap && cb < Kv) ? gd.V[(size_t)cb * nap + r0] : make_float2(0.f, 0.f);
+        const float2 v3 = (r1 < nap && cb < Kv) ? gd.V[(size_t)cb * nap + r1] : make_float2(0.f, 0.f);
+        x[0] = cpt ? v0.y : v0.x;
+        x[1] = cpt ? v1.y : v1.x;
+        x[2] = cpt ? v2.y : v2.x;
+        x[3] = cpt ? v3.y : v3.x;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) tf32_split(x[q], ahi[mt][q], alo[mt][q]);
+      }
+      const int kr = 2 * kk + t;
+#pragma unroll
+      for (int nt = 0; nt < 4; ++nt) {
+        const int n = nt * 8 + g;
+        const unsigned bh0 = bhi[kr][n], bh1 = bhi[kr + 4][n];
+        const unsigned bl0 = blo[kr][n], bl1 = blo[kr + 4][n];
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+          mma_tf32(acc[mt][nt], alo[mt], bh0, bh1);
+          mma_tf32(acc[mt][nt], ahi[mt], bl0, bl1);
+          mma_tf32(acc[mt][nt], ahi[mt], bh0, bh1);
+        }
+      }
+    }
+  }
+  // d0, d1: (row g, complex output 4 nt + t); d2, d3: row g + 8
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt) {
+      const int j = 4 * nt + t;
+      if (j >= r) continue;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int row = rbase + mt * 16 + g + 8 * h;
+        if (row >= nap) continue;
+        float2* o = gd.O + (size_t)j * nap + row;
+        float2 ov = make_float2(0.f, 0.f);
+        if (beta != 0.f) ov = *o;
+        *o = make_float2(beta * ov.x + acc[mt][nt][2 * h], beta * ov.y + acc[mt][nt][2 * h + 1]);
+      }
+    }
+}
+
+// Partial projections: part[z][x][i][j] = sum over the rows e of slab x of
+// conj(X_i[e]) W_j[e] for group z, i < K, j < r, where X_i is basis column i
+// for i < Kv and block column i - Kv after that, on the tensor pipe.
+// With real columns m = 2 i + c of V (component c of column i) and n = 2 j + c'
+// of W, the real product P = Vr^T Wr over the rows of a slab gives
+//   Re H_ij = P(2i, 2j) + P(2i+1, 2j+1),   Im H_ij = P(2i, 2j+1) - P(2i+1, 2j)
+// (H = V^H W), with the same three-product TF32 split as k_bnn_tc.  grid (nslab,
+// ceil(K / 16), groups), 128 threads: the block owns 16 complex V columns (32
+// real rows of P, two m16 tiles) against all 16 W columns (32 real, four n8
+// tiles) over its slab, walked in 128-row tiles staged by cp.async into two
+// buffers (row pitch 40 words: the fragment loads of a warp hit distinct
+// banks); warp w takes rows 32 w .. 32 w + 31 of each tile, and the four
+// warps' sums are added in warp order at the end.
+#define TP_ROWS 128
+#define TP_LD 40
+#define TP_SMEM (sizeof(float) * 2 * 2 * TP_ROWS * TP_LD)
+__global__ void __launch_bounds__(128) k_bproj_tc(BGSet set, double2* __restrict__ part, int nap,
+                                                  int rs, int nct, int kcap) {
+  extern __shared__ __align__(16) float tsm[];  // [buf][V | W][row][TP_LD]
+  const BGrp& gd = set.g[blockIdx.z];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int g = lane >> 2, t = lane & 3;
+  const int ib = blockIdx.y * 16, K = gd.K, Kv = gd.Kv, r = gd.r;
+  const int e0 = blockIdx.x * rs, e1 = min(nap, e0 + rs);
+  // staging: element q = tid + 128 u (u < 16) of a 128 x 16 tile: row q % 128, column q / 128
+  auto stage = [&](int buf, int eb) {
+    float* vs = tsm + (size_t)buf * 2 * TP_ROWS * TP_LD;
+    float* ws = vs + TP_ROWS * TP_LD;
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const int q = tid + 128 * u, c = q >> 7, el = q & 127, e = eb + el, i = ib + c;
+      const bool in = e < e1;
+      const float2* src = i < Kv ? gd.V + (size_t)i * nap : gd.W + (size_t)(i - Kv) * nap;
+      cp_async8((float2*)(vs + el * TP_LD + 2 * c), (in && i < K) ? src + e : gd.W, in && i < K);
+      cp_async8((float2*)(ws + el * TP_LD + 2 * c), (in && c < r) ? gd.W + (size_t)c * nap + e : gd.W,
+                in && c < r);
+    }
+    cp_async_commit();
   };
-  load4(0);
-  for (int i0 = 0; i0 < Kv; i0 += 4) {
-    float2 ca[4], cb[4];
+  float acc[2][4][4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) { ca[u] = a[u]; cb[u] = b[u]; }
-    if (i0 + 4 < Kv) load4(i0 + 4);
+  for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const float4* cr = cs + (size_t)(i0 + u) * (BG_MAX / 2);
+    for (int nt = 0; nt < 4; ++nt)
 #pragma unroll
-      for (int h = 0; h < BG_MAX / 2; ++h) {
-        const float4 c2 = cr[h];
-        p[2 * h].x += ca[u].x * c2.x - ca[u].y * c2.y;
-        p[2 * h].y += ca[u].x * c2.y + ca[u].y * c2.x;
-        p[2 * h + 1].x += ca[u].x * c2.z - ca[u].y * c2.w;
-        p[2 * h + 1].y += ca[u].x * c2.w + ca[u].y * c2.z;
-        q[2 * h].x += cb[u].x * c2.x - cb[u].y * c2.y;
-        q[2 * h].y += cb[u].x * c2.y + cb[u].y * c2.x;
-        q[2 * h + 1].x += cb[u].x * c2.z - cb[u].y * c2.w;
-        q[2 * h + 1].y += cb[u].x * c2.w + cb[u].y * c2.z;
+      for (int q = 0; q < 4; ++q) acc[mt][nt][q] = 0.f;
+  const int ntile = (e1 - e0 + TP_ROWS - 1) / TP_ROWS;
+  if (ntile > 0) stage(0, e0);
+  if (ntile > 1) stage(1, e0 + TP_ROWS);
+  for (int it = 0; it < ntile; ++it) {
+    if (it + 1 < ntile) cp_async_wait<1>();
+    else cp_async_wait<0>();
+    __syncthreads();
+    const float* vs = tsm + (size_t)(it & 1) * 2 * TP_ROWS * TP_LD;
+    const float* ws = vs + TP_ROWS * TP_LD;
+#pragma unroll
+    for (int ks = 0; ks < 4; ++ks) {
+      const int ea = warp * 32 + ks * 8 + t, eb = ea + 4;  // rows of the k8 step
+      unsigned ahi[2][4], alo[2][4];
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt) {
+        // real rows m = 16 mt + g (+ 8): word 16 mt + g (+ 8) of a staged row
+        const int w0 = 16 * mt + g;
+        tf32_split(vs[ea * TP_LD + w0], ahi[mt][0], alo[mt][0]);
+        tf32_split(vs[ea * TP_LD + w0 + 8], ahi[mt][1], alo[mt][1]);
+        tf32_split(vs[eb * TP_LD + w0], ahi[mt][2], alo[mt][2]);
+        tf32_split(vs[eb * TP_LD + w0 + 8], ahi[mt][3], alo[mt][3]);
+      }
+#pragma unroll
+      for (int nt = 0; nt < 4; ++nt) {
+        unsigned bh0, bl0, bh1, bl1;
+        tf32_split(ws[ea * TP_LD + 8 * nt + g], bh0, bl0);
+        tf32_split(ws[eb * TP_LD + 8 * nt + g], bh1, bl1);
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+          mma_tf32(acc[mt][nt], alo[mt], bh0, bh1);
+          mma_tf32(acc[mt][nt], ahi[mt], bl0, bl1);
+          mma_tf32(acc[mt][nt], ahi[mt], bh0, bh1);
+        }
       }
     }
+    __syncthreads();
+    if (it + 2 < ntile) stage(it & 1, e0 + (it + 2) * TP_ROWS);
   }
+  // P tiles of the four warps into shared memory: warp w's P(m, n) at
+  // red[w][m][n] (32 x 33 floats), d0 (m = 16 mt + g, n = 8 nt + 2t), d1 n + 1,
+  // d2, d3 at m + 8
+  float* red = tsm;
 #pragma unroll
-  for (int j = 0; j < BG_MAX; ++j) {
-    if (j < gd.r) {
-      if (ie) {
-        float2* o = gd.O + (size_t)j * nap + e;
-        float2 ov = make_float2(0.f, 0.f);
-        if (beta != 0.f) ov = *o;
-        *o = make_float2(beta * ov.x + p[j].x, beta * ov.y + p[j].y);
-      }
-      if (jf) {
-        float2* o = gd.O + (size_t)j * nap + f;
-        float2 ov = make_float2(0.f, 0.f);
-        if (beta != 0.f) ov = *o;
-        *o = make_float2(beta * ov.x + q[j].x, beta * ov.y + q[j].y);
-      }
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt) {
+      const int m = 16 * mt + g, n = 8 * nt + 2 * t;
+      float* rw = red + warp * 32 * 33;
+      rw[m * 33 + n] = acc[mt][nt][0];
+      rw[m * 33 + n + 1] = acc[mt][nt][1];
+      rw[(m + 8) * 33 + n] = acc[mt][nt][2];
+      rw[(m + 8) * 33 + n + 1] = acc[mt][nt][3];
     }
+  __syncthreads();
+  // thread -> 2 of the 256 complex outputs (i, j) of the tile
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int o = tid + 128 * h, li = o >> 4, lj = o & 15;
+    if (ib + li >= K || lj >= r) continue;
+    double pr = 0, pi = 0;
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+      const float* rw = red + w * 32 * 33;
+      pr += (double)rw[(2 * li) * 33 + 2 * lj] + (double)rw[(2 * li + 1) * 33 + 2 * lj + 1];
+      pi += (double)rw[(2 * li) * 33 + 2 * lj + 1] - (double)rw[(2 * li + 1) * 33 + 2 * lj];
+    }
+    part[((size_t)(blockIdx.z * nct + blockIdx.x) * kcap + ib + li) * BG_MAX + lj] = make_double2(pr, pi);
   }
 }
 
@@ -403,7 +460,7 @@ static bool cholqr(const std::vector<cd>& G, int n, std::vector<cd>& T, std::vec
 }
 
 // One SVQB step on the Gram matrix G (n x n): T = U Lambda_c^{-1/2} (the
-// transform of the block, stored BG_MAX wide as the k_bnn coefficient matrix),
+// transform of the block, stored BG_MAX wide as the k_bnn_tc coefficient matrix),
 // S = Lambda_c^{1/2} U^H (W = (W T) S); Lambda_c = max(Lambda, floor).
 // Returns the deviation of G from the identity (max |G - I|); ratio receives
 // min(Lambda) / max(Lambda).
@@ -603,12 +660,13 @@ static void bproj(cavity_ctx* ctx, const BGSet& set, int ng, int kmax, const BWo
   double2* h = w.hb + (size_t)slot * w.gmax * w.kcap * BG_MAX;
   static bool done = false;
   if (!done) {
-    cudaFuncSetAttribute(k_bproj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BP_SMEM);
+    cudaFuncSetAttribute(k_bproj_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TP_SMEM);
     done = true;
   }
   {
     KScope ks_(ctx, KC_KRYLOV);
-    k_bproj<<<dim3(nct, ytiles, ng), 256, BP_SMEM, ctx->stream>>>(set, w.part, nap, rs, nct, w.kcap);
+    k_bproj_tc<<<dim3(nct, ytiles, ng), 128, TP_SMEM, ctx->stream>>>(set, w.part, nap, rs, nct,
+                                                                     w.kcap);
   }
   {
     KScope ks_(ctx, KC_KRYLOV);
@@ -619,17 +677,8 @@ static void bproj(cavity_ctx* ctx, const BGSet& set, int ng, int kmax, const BWo
 static cavity_status bnn(cavity_ctx* ctx, const BGSet& set, int ng, const double2* cmat, float beta,
                          float sgn) {
   const int nap = ctx->g.nap;
-  int kv = 0;
-  for (int z = 0; z < ng; ++z) kv = std::max(kv, set.g[z].Kv);
-  static bool done = false;
-  if (!done) {
-    CK(cudaFuncSetAttribute(k_bnn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                            (int)bnn_smem(BG_MAX * 40)));
-    done = true;
-  }
   KScope ks_(ctx, KC_KRYLOV);
-  k_bnn<<<dim3(bg_blocks(nap, 2 * BNN_THREADS), 1, ng), BNN_THREADS, bnn_smem(kv), ctx->stream>>>(
-      set, cmat, nap, beta, sgn);
+  k_bnn_tc<<<dim3(bg_blocks(nap, 128), 1, ng), 128, 0, ctx->stream>>>(set, cmat, nap, beta, sgn);
   return CAVITY_OK;
 }
 
