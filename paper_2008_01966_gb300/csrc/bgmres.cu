@@ -31,6 +31,7 @@
 // batch; unlike per-direction GMRES it depends (within the tolerance) on which
 // directions share a group.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <complex>
 #include <vector>
@@ -658,7 +659,7 @@ static void bproj(cavity_ctx* ctx, const BGSet& set, int ng, int kmax, const BWo
   rs = (rs + BP_ROWS - 1) / BP_ROWS * BP_ROWS;
   nct = (nap + rs - 1) / rs;
   double2* h = w.hb + (size_t)slot * w.gmax * w.kcap * BG_MAX;
-  static bool done = false;
+  static std::atomic<bool> done{false};  // set once; host threads may race
   if (!done) {
     cudaFuncSetAttribute(k_bproj_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TP_SMEM);
     done = true;

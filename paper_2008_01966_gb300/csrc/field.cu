@@ -19,6 +19,7 @@
 // Output per direction and level j = 1..Nz: E1 on p = 0..Nx, q = 1..Ny-1,
 // E2 on p = 1..Nx-1, q = 0..Ny, E3 on p = 1..Nx-1, q = 1..Ny-1, row-major.
 #include <algorithm>
+#include <atomic>
 
 #include "common.cuh"
 #include "fft.cuh"
@@ -287,7 +288,7 @@ cavity_status launch_field(cavity_ctx* ctx, int ndir, const double2* ap, C<T>* o
     p.j0 = j0;
     CKS(dispatch_log<CAV_LOG_MIN, CAV_LOG_MAX>(g.lny, [&](auto c) -> cavity_status {
       constexpr int LN = decltype(c)::value, L = field_lines<T>(2 << LN);
-      static bool done = false;
+      static std::atomic<bool> done{false};  // set once; host threads may race
       if (!done) {
         CK(allow_max_smem(k_field_y<T, LN>));
         done = true;
@@ -300,7 +301,7 @@ cavity_status launch_field(cavity_ctx* ctx, int ndir, const double2* ap, C<T>* o
     }));
     CKS(dispatch_log<CAV_LOG_MIN, CAV_LOG_MAX>(g.lnx, [&](auto c) -> cavity_status {
       constexpr int LN = decltype(c)::value, L = field_lines<T>(2 << LN);
-      static bool done = false;
+      static std::atomic<bool> done{false};  // set once; host threads may race
       if (!done) {
         CK(allow_max_smem(k_field_x<T, LN>));
         done = true;

@@ -22,6 +22,7 @@
 // lengths; tbc.cu instantiates the FP64 operator, tbc_f32.cu the FP32 one.
 #pragma once
 #include <algorithm>
+#include <atomic>
 #include <type_traits>
 
 #include "common.cuh"
@@ -556,7 +557,7 @@ template <typename T> static size_t smem_d(int nx) { return sizeof(C<T>) * lines
 
 // opt every instantiation of kernel K into the device's shared-memory maximum
 // once per process
-template <typename K> static cavity_status smem_once(cavity_ctx* ctx, K kern, bool& done) {
+template <typename K> static cavity_status smem_once(cavity_ctx* ctx, K kern, std::atomic<bool>& done) {
   if (!done) {
     CK(allow_max_smem(kern));
     done = true;
@@ -632,7 +633,7 @@ cavity_status launch_apply(cavity_ctx* ctx, int ndir, const C<T>* x, C<T>* y, vo
   CKS(dispatch_log<CAV_LOG_MIN, CAV_LOG_MAX>(g.lny, [&](auto c) -> cavity_status {
     constexpr int LN = decltype(c)::value;
     constexpr int L = pairs_per_cta<T>(4 << LN);
-    static bool done = false;
+    static std::atomic<bool> done{false};  // set once; host threads may race
     CKS(smem_once(ctx, k_tbcA<T, LN>, done));
     KScope ks_(ctx, kclass<T>(0));
     k_tbcA<T, LN><<<dim3((g.nx + L - 1) / L, 3, ndir), T_, smem_a<T>(g.ny), st>>>(
@@ -642,7 +643,7 @@ cavity_status launch_apply(cavity_ctx* ctx, int ndir, const C<T>* x, C<T>* y, vo
   CKS(dispatch_log<CAV_LOG_MIN, CAV_LOG_MAX>(g.lnx, [&](auto c) -> cavity_status {
     constexpr int LN = decltype(c)::value;
     constexpr int L = pairs_per_cta<T>(4 << LN);
-    static bool done = false;
+    static std::atomic<bool> done{false};  // set once; host threads may race
     CKS(smem_once(ctx, k_tbcB<T, LN>, done));
     KScope ks_(ctx, kclass<T>(1));
     k_tbcB<T, LN><<<dim3((g.Py + L - 1) / L, 3, ndir), T_, smem_b<T>(g.nx), st>>>(
@@ -652,7 +653,7 @@ cavity_status launch_apply(cavity_ctx* ctx, int ndir, const C<T>* x, C<T>* y, vo
   CKS(dispatch_log<CAV_LOG_MIN, CAV_LOG_MAX>(g.lny, [&](auto c) -> cavity_status {
     constexpr int LN = decltype(c)::value;
     constexpr int L = lines_per_cta<T>(4 << LN);
-    static bool done = false;
+    static std::atomic<bool> done{false};  // set once; host threads may race
     CKS(smem_once(ctx, k_tbcC<T, LN>, done));
     KScope ks_(ctx, kclass<T>(2));
     k_tbcC<T, LN><<<dim3((g.nx + 1 + L - 1) / L, 3, ndir), T_, smem_c<T>(g.ny), st>>>(R2, R1, p, tw);
@@ -661,7 +662,7 @@ cavity_status launch_apply(cavity_ctx* ctx, int ndir, const C<T>* x, C<T>* y, vo
   CKS(dispatch_log<CAV_LOG_MIN, CAV_LOG_MAX>(g.lnx, [&](auto c) -> cavity_status {
     constexpr int LN = decltype(c)::value;
     constexpr int L = lines_per_cta<T>(2 << LN);
-    static bool done = false;
+    static std::atomic<bool> done{false};  // set once; host threads may race
     CKS(smem_once(ctx, k_tbcD<T, LN>, done));
     KScope ks_(ctx, kclass<T>(3));
     k_tbcD<T, LN><<<dim3((g.ny + 1 + L - 1) / L, 3, ndir), T_, smem_d<T>(g.nx), st>>>(R1, R2, p, tw);
