@@ -130,18 +130,37 @@ __device__ __forceinline__ void mma_tf32(float (&d)[4], const unsigned (&a)[4], 
 
 #define TC_KC 32   // complex rows of C staged per chunk (64 real rows)
 #define TC_BLD 40  // row pitch (words) of the staged real C: the b-fragment loads hit distinct banks
+#define TC_AK 8    // complex basis columns per staged A tile (two k8 steps)
+#define TC_ALD 20  // row pitch (words) of the staged A tile: the a-fragment loads hit distinct banks
 
 // grid (ceil(nap / 128), 1, groups), 128 threads; warp w owns the rows
-// 128 x + 32 w .. + 31 (two m16 tiles) and all 32 real outputs (four n8 tiles)
+// 128 x + 32 w .. + 31 (two m16 tiles) and all 32 real outputs (four n8 tiles).
+// The basis columns come through shared memory: tiles of 128 rows x 8 complex
+// columns (row-major real words, word 2 i + c = component c of column i),
+// copied by cp.async into two buffers, the next tile in flight while the
+// current one is multiplied.
 __global__ void __launch_bounds__(128) k_bnn_tc(BGSet set, const double2* __restrict__ cmat,
                                                 int nap, float beta, float sgn) {
   __shared__ unsigned bhi[2 * TC_KC][TC_BLD], blo[2 * TC_KC][TC_BLD];
+  __shared__ __align__(16) float as[2][128 * TC_ALD];
   const BGrp& gd = set.g[blockIdx.z];
   const double2* Cm = cmat + gd.coff;
   const int Kv = gd.Kv, r = gd.r;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int g = lane >> 2, t = lane & 3;
-  const int rbase = blockIdx.x * 128 + warp * 32;
+  const int row0 = blockIdx.x * 128;
+  const int lrow = warp * 32;  // this warp's first row within the block
+  // staging: element u of thread tid is column i0 + u, row row0 + tid
+  auto stage_a = [&](int buf, int i0) {
+    const int e = row0 + tid;
+#pragma unroll
+    for (int u = 0; u < TC_AK; ++u) {
+      const int i = i0 + u;
+      const bool ok = e < nap && i < Kv;
+      cp_async8((float2*)(as[buf] + tid * TC_ALD + 2 * u), ok ? gd.V + (size_t)i * nap + e : gd.V, ok);
+    }
+    cp_async_commit();
+  };
   float acc[2][4][4];
 #pragma unroll
   for (int mt = 0; mt < 2; ++mt)
@@ -149,43 +168,43 @@ __global__ void __launch_bounds__(128) k_bnn_tc(BGSet set, const double2* __rest
     for (int nt = 0; nt < 4; ++nt)
 #pragma unroll
       for (int q = 0; q < 4; ++q) acc[mt][nt][q] = 0.f;
-  for (int i0 = 0; i0 < Kv; i0 += TC_KC) {
-    __syncthreads();
-    for (int u = threadIdx.x; u < TC_KC * 16; u += 128) {
-      const int ii = u >> 4, j = u & 15;
-      double2 c = make_double2(0.0, 0.0);
-      if (i0 + ii < Kv && j < r) c = Cm[(size_t)(i0 + ii) * BG_MAX + j];
-      const float cr = (float)(sgn * c.x), ci = (float)(sgn * c.y);
-      tf32_split(cr, bhi[2 * ii][2 * j], blo[2 * ii][2 * j]);
-      tf32_split(ci, bhi[2 * ii][2 * j + 1], blo[2 * ii][2 * j + 1]);
-      tf32_split(-ci, bhi[2 * ii + 1][2 * j], blo[2 * ii + 1][2 * j]);
-      tf32_split(cr, bhi[2 * ii + 1][2 * j + 1], blo[2 * ii + 1][2 * j + 1]);
+  const int ntile = (Kv + TC_AK - 1) / TC_AK;
+  if (ntile > 0) stage_a(0, 0);
+  if (ntile > 1) stage_a(1, TC_AK);
+  for (int it = 0; it < ntile; ++it) {
+    const int ia = it * TC_AK;  // first complex column of this A tile
+    if (ia % TC_KC == 0) {
+      // next chunk of C: all threads are past the previous chunk's reads
+      __syncthreads();
+      for (int u = tid; u < TC_KC * 16; u += 128) {
+        const int ii = u >> 4, j = u & 15;
+        double2 c = make_double2(0.0, 0.0);
+        if (ia + ii < Kv && j < r) c = Cm[(size_t)(ia + ii) * BG_MAX + j];
+        const float cr = (float)(sgn * c.x), ci = (float)(sgn * c.y);
+        tf32_split(cr, bhi[2 * ii][2 * j], blo[2 * ii][2 * j]);
+        tf32_split(ci, bhi[2 * ii][2 * j + 1], blo[2 * ii][2 * j + 1]);
+        tf32_split(-ci, bhi[2 * ii + 1][2 * j], blo[2 * ii + 1][2 * j]);
+        tf32_split(cr, bhi[2 * ii + 1][2 * j + 1], blo[2 * ii + 1][2 * j + 1]);
+      }
     }
+    if (it + 1 < ntile) cp_async_wait<1>();
+    else cp_async_wait<0>();
     __syncthreads();
-    const int kend = min(TC_KC, Kv - i0);
-    for (int kk = 0; kk < kend; kk += 4) {
-      // real inner index 2 kk + t is component (t & 1) of complex column kk + t / 2;
-      // 2 kk + t + 4 the same component of column kk + 2 + t / 2 (no prefetch:
-      // its registers cost more resident warps than it hid latency)
-      const int ca = i0 + kk + (t >> 1), cb = ca + 2;
-      const bool cpt = t & 1;
+    const float* at = as[it & 1];
+    const int cb0 = 2 * (ia % TC_KC);  // first real row of C for this tile
+#pragma unroll
+    for (int ks = 0; ks < 2; ++ks) {
+      const int kb = 8 * ks;  // real inner index within the tile
       unsigned ahi[2][4], alo[2][4];
 #pragma unroll
       for (int mt = 0; mt < 2; ++mt) {
-        const int r0 = rbase + mt * 16 + g, r1 = r0 + 8;
-        float x[4];
-        const float2 v0 = (r0 < nap && ca < Kv) ? gd.V[(size_t)ca * nap + r0] : make_float2(0.f, 0.f);
-        const float2 v1 = (r1 < nap && ca < Kv) ? gd.V[(size_t)ca * nap + r1] : make_float2(0.f, 0.f);
-        const float2 v2 = (r0 < nap && cb < Kv) ? gd.V[(size_t)cb * nap + r0] : make_float2(0.f, 0.f);
-        const float2 v3 = (r1 < nap && cb < Kv) ? gd.V[(size_t)cb * nap + r1] : make_float2(0.f, 0.f);
-        x[0] = cpt ? v0.y : v0.x;
-        x[1] = cpt ? v1.y : v1.x;
-        x[2] = cpt ? v2.y : v2.x;
-        x[3] = cpt ? v3.y : v3.x;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) tf32_split(x[q], ahi[mt][q], alo[mt][q]);
+        const int rr = lrow + mt * 16 + g;
+        tf32_split(at[rr * TC_ALD + kb + t], ahi[mt][0], alo[mt][0]);
+        tf32_split(at[(rr + 8) * TC_ALD + kb + t], ahi[mt][1], alo[mt][1]);
+        tf32_split(at[rr * TC_ALD + kb + t + 4], ahi[mt][2], alo[mt][2]);
+        tf32_split(at[(rr + 8) * TC_ALD + kb + t + 4], ahi[mt][3], alo[mt][3]);
       }
-      const int kr = 2 * kk + t;
+      const int kr = cb0 + kb + t;
 #pragma unroll
       for (int nt = 0; nt < 4; ++nt) {
         const int n = nt * 8 + g;
@@ -199,6 +218,8 @@ __global__ void __launch_bounds__(128) k_bnn_tc(BGSet set, const double2* __rest
         }
       }
     }
+    __syncthreads();
+    if (it + 2 < ntile) stage_a(it & 1, (it + 2) * TC_AK);
   }
   // d0, d1: (row g, complex output 4 nt + t); d2, d3: row g + 8
 #pragma unroll
@@ -209,7 +230,7 @@ __global__ void __launch_bounds__(128) k_bnn_tc(BGSet set, const double2* __rest
       if (j >= r) continue;
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
-        const int row = rbase + mt * 16 + g + 8 * h;
+        const int row = row0 + lrow + mt * 16 + g + 8 * h;
         if (row >= nap) continue;
         float2* o = gd.O + (size_t)j * nap + row;
         float2 ov = make_float2(0.f, 0.f);
