@@ -249,14 +249,14 @@ __global__ void __launch_bounds__(128) k_bnn_tc(BGSet set, const double2* __rest
 // (H = V^H W), with the same three-product TF32 split as k_bnn_tc.  grid (nslab,
 // ceil(K / 16), groups), 128 threads: the block owns 16 complex V columns (32
 // real rows of P, two m16 tiles) against all 16 W columns (32 real, four n8
-// tiles) over its slab, walked in 128-row tiles staged by cp.async into two
+// tiles) over its slab, walked in 64-row tiles staged by cp.async into two
 // buffers (row pitch 40 words: the fragment loads of a warp hit distinct
-// banks); warp w takes rows 32 w .. 32 w + 31 of each tile, and the four
+// banks); warp w takes rows 16 w .. 16 w + 15 of each tile, and the four
 // warps' sums are added in warp order at the end.
-#define TP_ROWS 128
+#define TP_ROWS 64
 #define TP_LD 40
 #define TP_SMEM (sizeof(float) * 2 * 2 * TP_ROWS * TP_LD)
-__global__ void __launch_bounds__(128) k_bproj_tc(BGSet set, double2* __restrict__ part, int nap,
+__global__ void __launch_bounds__(128, 4) k_bproj_tc(BGSet set, double2* __restrict__ part, int nap,
                                                   int rs, int nct, int kcap) {
   extern __shared__ __align__(16) float tsm[];  // [buf][V | W][row][TP_LD]
   const BGrp& gd = set.g[blockIdx.z];
@@ -264,13 +264,13 @@ __global__ void __launch_bounds__(128) k_bproj_tc(BGSet set, double2* __restrict
   const int g = lane >> 2, t = lane & 3;
   const int ib = blockIdx.y * 16, K = gd.K, Kv = gd.Kv, r = gd.r;
   const int e0 = blockIdx.x * rs, e1 = min(nap, e0 + rs);
-  // staging: element q = tid + 128 u (u < 16) of a 128 x 16 tile: row q % 128, column q / 128
+  // staging: element q = tid + 128 u (u < 8) of a 64 x 16 tile: row q % 64, column q / 64
   auto stage = [&](int buf, int eb) {
     float* vs = tsm + (size_t)buf * 2 * TP_ROWS * TP_LD;
     float* ws = vs + TP_ROWS * TP_LD;
 #pragma unroll
-    for (int u = 0; u < 16; ++u) {
-      const int q = tid + 128 * u, c = q >> 7, el = q & 127, e = eb + el, i = ib + c;
+    for (int u = 0; u < 8; ++u) {
+      const int q = tid + 128 * u, c = q >> 6, el = q & 63, e = eb + el, i = ib + c;
       const bool in = e < e1;
       const float2* src = i < Kv ? gd.V + (size_t)i * nap : gd.W + (size_t)(i - Kv) * nap;
       cp_async8((float2*)(vs + el * TP_LD + 2 * c), (in && i < K) ? src + e : gd.W, in && i < K);
@@ -295,9 +295,9 @@ __global__ void __launch_bounds__(128) k_bproj_tc(BGSet set, double2* __restrict
     __syncthreads();
     const float* vs = tsm + (size_t)(it & 1) * 2 * TP_ROWS * TP_LD;
     const float* ws = vs + TP_ROWS * TP_LD;
-#pragma unroll
-    for (int ks = 0; ks < 4; ++ks) {
-      const int ea = warp * 32 + ks * 8 + t, eb = ea + 4;  // rows of the k8 step
+#pragma unroll 1
+    for (int ks = 0; ks < 2; ++ks) {
+      const int ea = warp * 16 + ks * 8 + t, eb = ea + 4;  // rows of the k8 step
       unsigned ahi[2][4], alo[2][4];
 #pragma unroll
       for (int mt = 0; mt < 2; ++mt) {
