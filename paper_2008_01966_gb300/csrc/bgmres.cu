@@ -150,7 +150,10 @@ __global__ void __launch_bounds__(128) k_bnn_tc(BGSet set, const double2* __rest
   const int g = lane >> 2, t = lane & 3;
   const int row0 = blockIdx.x * 128;
   const int lrow = warp * 32;  // this warp's first row within the block
-  // staging: element u of thread tid is column i0 + u, row row0 + tid
+  // staging: element u of thread tid is column i0 + u, row row0 + tid (a warp
+  // reads 256 contiguous bytes of one column; the 8-byte writes of a half-warp
+  // fall on 8 bank pairs at the 20-word pitch, 2-way, which measured faster
+  // than a conflict-free map that spreads a warp's reads over four columns)
   auto stage_a = [&](int buf, int i0) {
     const int e = row0 + tid;
 #pragma unroll
@@ -264,13 +267,17 @@ __global__ void __launch_bounds__(128, 4) k_bproj_tc(BGSet set, double2* __restr
   const int g = lane >> 2, t = lane & 3;
   const int ib = blockIdx.y * 16, K = gd.K, Kv = gd.Kv, r = gd.r;
   const int e0 = blockIdx.x * rs, e1 = min(nap, e0 + rs);
-  // staging: element q = tid + 128 u (u < 8) of a 64 x 16 tile: row q % 64, column q / 64
+  // staging: element q = tid + 128 u (u < 8) of a 64 x 16 tile has row bits
+  // 0-1 from q bits 0-1 and bits 2-5 from q bits 6-9, column q bits 2-5; a
+  // half-warp writes 4 rows x 4 columns (distinct banks at the 40-word pitch)
+  // and a warp reads 8 whole 32-byte sectors
   auto stage = [&](int buf, int eb) {
     float* vs = tsm + (size_t)buf * 2 * TP_ROWS * TP_LD;
     float* ws = vs + TP_ROWS * TP_LD;
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
-      const int q = tid + 128 * u, c = q >> 6, el = q & 63, e = eb + el, i = ib + c;
+      const int q = tid + 128 * u, c = (q >> 2) & 15, el = (q & 3) | ((q >> 6) << 2);
+      const int e = eb + el, i = ib + c;
       const bool in = e < e1;
       const float2* src = i < Kv ? gd.V + (size_t)i * nap : gd.W + (size_t)(i - Kv) * nap;
       cp_async8((float2*)(vs + el * TP_LD + 2 * c), (in && i < K) ? src + e : gd.W, in && i < K);
