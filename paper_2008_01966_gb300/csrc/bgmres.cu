@@ -128,7 +128,7 @@ __device__ __forceinline__ void mma_tf32(float (&d)[4], const unsigned (&a)[4], 
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-#define TC_KC 32   // complex rows of C staged per chunk (64 real rows)
+#define TC_KC 16   // complex rows of C staged per chunk (32 real rows)
 #define TC_BLD 40  // row pitch (words) of the staged real C: the b-fragment loads hit distinct banks
 #define TC_AK 8    // complex basis columns per staged A tile (two k8 steps)
 #define TC_ALD 20  // row pitch (words) of the staged A tile: the a-fragment loads hit distinct banks
@@ -138,8 +138,9 @@ __device__ __forceinline__ void mma_tf32(float (&d)[4], const unsigned (&a)[4], 
 // The basis columns come through shared memory: tiles of 128 rows x 8 complex
 // columns (row-major real words, word 2 i + c = component c of column i),
 // copied by cp.async into two buffers, the next tile in flight while the
-// current one is multiplied.
-__global__ void __launch_bounds__(128) k_bnn_tc(BGSet set, const double2* __restrict__ cmat,
+// current one is multiplied.  30 KB of shared memory and at most 80 registers
+// a thread: six blocks per SM.
+__global__ void __launch_bounds__(128, 6) k_bnn_tc(BGSet set, const double2* __restrict__ cmat,
                                                 int nap, float beta, float sgn) {
   __shared__ unsigned bhi[2 * TC_KC][TC_BLD], blo[2 * TC_KC][TC_BLD];
   __shared__ __align__(16) float as[2][128 * TC_ALD];
