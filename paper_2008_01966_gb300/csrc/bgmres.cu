@@ -680,9 +680,10 @@ static BWork bwork_carve(void* base, const Geo& g, int ndir, int mb) {
 static void bproj(cavity_ctx* ctx, const BGSet& set, int ng, int kmax, const BWork& w, int slot) {
   const int nap = ctx->g.nap;
   const int ytiles = (kmax + 15) / 16;
-  // one slab of rows per SM over the groups (few, long slabs keep the final
-  // sum short; the column tiles multiply the CTAs)
-  int nct = std::max(1, std::min(BG_PART_CTAS / ng, 152 / ng));
+  // slabs of rows such that slabs x column tiles x groups fill one wave of
+  // resident blocks (four per SM, BG_PART_CTAS in all): no tail wave, and a
+  // short projection (the Gram matrix, K = 16) still spreads over every SM
+  int nct = std::max(1, BG_PART_CTAS / (ytiles * ng));
   nct = std::min(nct, (nap + BP_ROWS - 1) / BP_ROWS);
   int rs = (nap + nct - 1) / nct;
   rs = (rs + BP_ROWS - 1) / BP_ROWS * BP_ROWS;
