@@ -317,6 +317,94 @@ def test_rcs_square_swap_symmetry():
     assert np.allclose(e1a.T, e2b, atol=1e-12 * np.abs(xa).max())
 
 
+def _te10_sigma(kappa0, a, b, theta, phi, pol):
+    """Backscatter-style cross section 4 pi r^2 |E|^2 of the textbook far field
+    of an aperture of sides a (along x) and b in a ground plane carrying the
+    y-polarised TE10 distribution E0 cos(pi x / a), E0 = 1 (the open-ended
+    waveguide pattern, e.g. Balanis, Antenna Theory, aperture antennas on an
+    infinite ground plane):
+        E_theta = (pi/2) C sin(phi) cos X / (X^2 - (pi/2)^2) sin Y / Y,
+        E_phi   = (pi/2) C cos(theta) cos(phi) (same two factors),
+    C = kappa0 a b / (2 pi r), X = (kappa0 a / 2) sin(theta) cos(phi),
+    Y = (kappa0 b / 2) sin(theta) sin(phi)."""
+    X = 0.5 * kappa0 * a * np.sin(theta) * np.cos(phi)
+    Y = 0.5 * kappa0 * b * np.sin(theta) * np.sin(phi)
+    fx = np.cos(X) / (X ** 2 - (np.pi / 2) ** 2)
+    fy = np.sinc(Y / np.pi)                     # sin Y / Y
+    c = kappa0 * a * b / (2 * np.pi)            # C r
+    ang = np.sin(phi) if pol == 'theta' else np.cos(theta) * np.cos(phi)
+    return 4 * np.pi * (np.pi / 2 * c * ang * fx * fy) ** 2
+
+
+@pytest.mark.parametrize("theta,phi", [(0.0, 0.0), (0.4, 0.3), (0.9, 1.2), (1.3, 2.5), (0.7, 4.0)])
+def test_rcs_single_mode_matches_te10_aperture_pattern(theta, phi):
+    """The RCS functional against a textbook closed form: the aperture field of
+    the single mode E2^(1,0) = sin(pi x1 / a) is the TE10 distribution (shifted
+    by a/2, a phase), so sigma_theta and sigma_phi must equal 4 pi r^2 |E|^2 of
+    the open-ended waveguide pattern; the E1^(0,1) mode is its reflection
+    across the diagonal (a <-> b, phi -> pi/2 - phi).  Checks the closed-form
+    cos/sin integrals, z x E, both polarisation vectors and the kappa0^2 / pi
+    prefactor at oblique angles (a != b)."""
+    a, b, kappa0 = 1.0, 0.7, 3 * np.pi
+    cav = Cavity(a, b, 0.5, 8, 8, 8, kappa0)
+    e1 = np.zeros((cav.M + 1, cav.N), complex)
+    e2 = np.zeros((cav.M, cav.N + 1), complex)
+    e3 = np.zeros((cav.M, cav.N), complex)
+    e2[0, 0] = 1.0                                            # m = 1, n = 0
+    x2 = cav.join(e1, e2, e3)
+    e2[0, 0] = 0.0
+    e1[0, 0] = 1.0                                            # m = 0, n = 1
+    x1 = cav.join(e1, e2, e3)
+    for pol in ('theta', 'phi'):
+        want2 = _te10_sigma(kappa0, a, b, theta, phi, pol)
+        got2 = backscatter(cav, x2, theta, phi, pol)
+        assert abs(got2 - want2) <= 1e-12 * max(want2, 1e-30) + 1e-14, (pol, got2, want2)
+        want1 = _te10_sigma(kappa0, b, a, theta, np.pi / 2 - phi, pol)
+        got1 = backscatter(cav, x1, theta, phi, pol)
+        assert abs(got1 - want1) <= 1e-12 * max(want1, 1e-30) + 1e-14, (pol, got1, want1)
+
+
+@pytest.mark.parametrize("theta,phi", [(0.4, 0.3), (0.9, 1.2), (1.3, 2.5), (0.7, 4.0)])
+def test_rcs_two_modes_interfere_as_te10_patterns(theta, phi):
+    """E2^(1,0) + (0.6 + 0.4i) E1^(0,1): the backscatter RCS of the sum carries
+    the interference of the two modes (through the real part of the relative
+    coefficient: both patterns share the shift phase), so the relative sign
+    of the E1 and E2 terms of z x E matters.  Expected value from the two centred TE10
+    patterns (the textbook factors of _te10_sigma, one per polarisation of the
+    aperture field) times the phase of the shift to [0, a] x [0, b],
+    exp(-i (X + Y)), and the cross products written out:
+        L(E2 mode) = +x (pi a b / 2) cos X / (X^2 - pi^2/4) sin Y / Y e^{-i(X+Y)},
+        L(E1 mode) = -y (pi a b / 2) sin X / X cos Y / (Y^2 - pi^2/4) e^{-i(X+Y)}."""
+    a, b, kappa0 = 1.0, 0.7, 3 * np.pi
+    cav = Cavity(a, b, 0.5, 8, 8, 8, kappa0)
+    e1 = np.zeros((cav.M + 1, cav.N), complex)
+    e2 = np.zeros((cav.M, cav.N + 1), complex)
+    e3 = np.zeros((cav.M, cav.N), complex)
+    e2[0, 0] = 1.0
+    c1 = 0.6 + 0.4j
+    e1[0, 0] = c1
+    x = cav.join(e1, e2, e3)
+    X = 0.5 * kappa0 * a * np.sin(theta) * np.cos(phi)
+    Y = 0.5 * kappa0 * b * np.sin(theta) * np.sin(phi)
+    ph = np.exp(-1j * (X + Y))
+    L2 = np.array([1.0, 0, 0]) * (np.pi * a * b / 2) * np.cos(X) / (X ** 2 - np.pi ** 2 / 4) \
+        * np.sinc(Y / np.pi) * ph
+    L1 = -np.array([0, 1.0, 0]) * (np.pi * a * b / 2) * np.sinc(X / np.pi) \
+        * np.cos(Y) / (Y ** 2 - np.pi ** 2 / 4) * ph
+    L = L2 + c1 * L1
+    r = np.array([np.sin(theta) * np.cos(phi), np.sin(theta) * np.sin(phi), np.cos(theta)])
+    th = np.array([np.cos(theta) * np.cos(phi), np.cos(theta) * np.sin(phi), -np.sin(theta)])
+    fh = np.array([-np.sin(phi), np.cos(phi), 0.0])
+    for pol, e in (('theta', th), ('phi', fh)):
+        want = kappa0 ** 2 / np.pi * abs(np.dot(e, np.cross(r, L))) ** 2
+        got = backscatter(cav, x, theta, phi, pol)
+        assert abs(got - want) <= 1e-12 * want, (pol, got, want)
+        # a flipped relative sign of the two terms is detectably different
+        Lf = L2 - c1 * L1
+        wrong = kappa0 ** 2 / np.pi * abs(np.dot(e, np.cross(r, Lf))) ** 2
+        assert abs(wrong - want) > 1e-3 * want
+
+
 def test_incident_wave_is_transverse():
     """p . q = 0 for the Sec. 7 parametrisation, and beta >= 0 (Sec. 2)."""
     for th, ph, al in ((0.3, 1.2, 0.0), (1.0, 4.0, 0.7), (0.0, 0.0, 0.0)):
