@@ -130,9 +130,18 @@ cavity_status cavity_prepare(cavity_ctx* ctx, double kappa0, int nlayers,
  *  out_mem:      CAVITY_MEM_DEVICE or CAVITY_MEM_HOST for both outputs.
  *  iters_out, resid_out: host arrays of length ndir (may be NULL): Krylov
  *                iterations and final relative residual of (EJ1)/(uT1) per
- *                direction.
+ *                direction.  CAVITY_FP64: GMRES iterations of the direction.
+ *                CAVITY_MIXED: block GMRES steps of the FP32 inner solves,
+ *                summed over the FP64 refinement cycles (one step applies
+ *                the operator to the whole group of up to 16 directions);
+ *                the residual is the refinement's FP64 residual.
+ * gmres_restart bounds the basis per direction (CAVITY_FP64) or the block
+ * steps per refinement cycle (CAVITY_MIXED: min(gmres_restart, 30), at least
+ * 2); gmres_max_iter bounds the iterations or block steps in total.
  * Returns CAVITY_ENOCONV (outputs filled) when a residual stays above
- * gmres_tol after gmres_max_iter iterations. */
+ * gmres_tol after gmres_max_iter iterations (CAVITY_FP64: when the true
+ * residual, recomputed after GMRES stops on its estimate, exceeds
+ * 10 gmres_tol). */
 cavity_status cavity_solve(cavity_ctx* ctx, double kappa0, int nlayers,
                            const int* layer_levels, const double* eps_re,
                            const double* eps_im, int ndir, const double* theta,
