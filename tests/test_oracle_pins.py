@@ -143,6 +143,46 @@ def test_reduction_matches_unreduced_system(layers):
         assert np.abs(c3.ravel() - bru[3][:, j - 1]).max() < 1e-12 * scale
 
 
+@pytest.mark.parametrize("nsplit", [2, 3])
+def test_equal_eps_layers_converge_to_homogeneous(nsplit):
+    """A homogeneous fill cut into layers of the same permittivity.  The
+    interface rows of Sec. 4 ((con42-2) and its E2 analogue, (con61) with
+    (con32)) are one-sided differences: with eps equal on both sides they read
+    T_{j-1} - 2 T_j + T_{j+1} = 0, the interior row without its h^2 (kappa^2 -
+    lambda) T_j term.  So the E3-driven profiles Q vanish identically (their
+    source carries the factor 1 - eps_U / eps_D), and the profiles P agree
+    with the homogeneous elimination of Sec. 3 to first order in h, not to
+    rounding.  An unbalanced interface stencil (a doubled term in (con61), a
+    factor on one side of (con32), a wrong diagonal of the E1 interface row)
+    leaves an O(1) gap and fails the order check; eps ratios are 1 here and
+    are pinned by the two-layer transmission test instead."""
+    eps, kap = 2 + 0.3j, 5.0
+    modes = [(1, 1), (2, 3), (0, 2), (5, 4)]
+    gaps = []
+    for nz in (24, 48, 96, 192):
+        base = nz // nsplit
+        split = [base] * nsplit
+        split[0] += nz - base * nsplit
+        hom = Cavity(1.0, 0.8, 0.5, 8, 8, nz, kap, layers=[Layer(nz, eps)])
+        lay = Cavity(1.0, 0.8, 0.5, 8, 8, nz, kap, layers=[Layer(n, eps) for n in split])
+        g1 = g3 = 0.0
+        for m, n in modes:
+            if m >= 1:
+                P3h, _ = e3_profile(hom, m, n)
+                P3l, _ = e3_profile(lay, m, n)
+                g3 = max(g3, np.abs(P3h - P3l).max() / np.abs(P3h).max())
+            P1h, _ = tangential_profiles(hom, m, n, m * np.pi / hom.a, None)
+            P1l, Q1l = tangential_profiles(lay, m, n, m * np.pi / lay.a,
+                                           P3l if m >= 1 else None)
+            assert np.all(Q1l == 0)
+            g1 = max(g1, np.abs(P1h - P1l).max() / np.abs(P1h).max())
+        gaps.append((g1, g3))
+    gaps = np.array(gaps)
+    for k in range(2):
+        assert np.all(_order(gaps[:, k]) > 0.85) and np.all(_order(gaps[:, k]) < 1.25)
+    assert gaps[-1, 0] < 0.05 and gaps[-1, 1] < 0.02
+
+
 # ---------------------------------------------------------------- transforms
 def test_synthesis_matches_scipy_dct_dst_type1():
     """T4: the explicit cos/sin synthesis of (E123F) on the grid equals
