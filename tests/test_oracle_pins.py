@@ -357,6 +357,33 @@ def test_rcs_square_swap_symmetry():
     assert np.allclose(e1a.T, e2b, atol=1e-12 * np.abs(xa).max())
 
 
+@pytest.mark.parametrize("theta,phi,alpha", [(0.5, 0.3, 0.4), (1.1, 2.2, -0.7)])
+def test_diagonal_reflection_at_oblique_incidence(theta, phi, alpha):
+    """The reflection x1 <-> x2 of a square cavity on a square grid maps the
+    incident wave (theta, phi, alpha) to (theta, pi/2 - phi, -alpha) (theta_hat
+    goes to theta_hat, phi_hat to -phi_hat) and the field E to S E(S x): the
+    E1 and E2 coefficients trade places with transposed mode indices and E3
+    is transposed.  The discrete problem keeps the symmetry exactly, so the
+    right-hand sides of both rows (their phases at oblique incidence
+    included), the solution of a layered fill and both backscatter
+    polarisations must map into each other to rounding."""
+    cav = Cavity(1.0, 1.0, 0.5, 8, 8, 6, 7.0, layers=[Layer(3, 2 + 0.4j), Layer(3, 1.0)])
+    sysm = ApertureSystem(cav)
+    b = rhs(cav, theta, phi, alpha)
+    b2 = rhs(cav, theta, np.pi / 2 - phi, -alpha)
+    for u, v in ((b, b2), (sysm.solve_dense(b), sysm.solve_dense(b2))):
+        e1, e2, e3 = cav.split(u)
+        f1, f2, f3 = cav.split(v)
+        tol = 1e-13 * np.abs(u).max()
+        assert np.abs(f1 - e2.T).max() < tol and np.abs(f2 - e1.T).max() < tol
+        assert np.abs(f3 - e3.T).max() < tol
+    x, x2 = sysm.solve_dense(b), sysm.solve_dense(b2)
+    for pol in ('theta', 'phi'):
+        s1 = backscatter(cav, x, theta, phi, pol)
+        s2 = backscatter(cav, x2, theta, np.pi / 2 - phi, pol)
+        assert s1 > 0 and abs(s1 - s2) < 1e-12 * s1
+
+
 def _te10_sigma(kappa0, a, b, theta, phi, pol):
     """Backscatter-style cross section 4 pi r^2 |E|^2 of the textbook far field
     of an aperture of sides a (along x) and b in a ground plane carrying the
