@@ -56,12 +56,13 @@ def test_homogeneous_profiles_converge_to_continuous_modes():
     """T2: in an empty homogeneous cavity with unit aperture value the FD
     profiles approach sin(g(x3+c))/sin(g c) (E1, Dirichlet bottom, second order)
     and cos(g(x3+c))/cos(g c) (E3, Neumann bottom imposed as E_{3,0} = E_{3,1},
-    first order), g^2 = kappa^2 - lambda_mn (ode1x3)/(ode3x3)."""
-    kap, m, n = 7.0, 1, 1
+    first order), g^2 = kappa^2 - lambda_mn (ode1x3)/(ode3x3), on a rectangular
+    aperture (a != b) with lambda_mn written out here."""
+    kap, m, n, a, b = 7.0, 1, 1, 1.0, 0.8
     e1, e3 = [], []
     for nz in (16, 32, 64, 128):
-        cav = Cavity(1.0, 1.0, 0.5, 4, 4, nz, kap)
-        g = np.sqrt(kap ** 2 - cav.lam(m, n) + 0j)
+        cav = Cavity(a, b, 0.5, 4, 4, nz, kap)
+        g = np.sqrt(kap ** 2 - (m * np.pi / a) ** 2 - (n * np.pi / b) ** 2 + 0j)
         z = -cav.c + np.arange(nz + 1) * cav.h
         P, _ = tangential_profiles(cav, m, n, 0.0)
         e1.append(np.abs(P - np.sin(g * (z + cav.c)) / np.sin(g * cav.c)).max())
@@ -123,16 +124,17 @@ def test_layered_profiles_converge_to_transmission_solution():
     assert err3[-1] < 0.03 and errq[-1] < 0.003
 
 
-@pytest.mark.parametrize("layers", [[], [Layer(3, 4 + 1j), Layer(3, 2 + .5j), Layer(2, 1.0)]])
-def test_reduction_matches_unreduced_system(layers):
+@pytest.mark.parametrize("layers,b", [([], 1.0), ([Layer(3, 4 + 1j), Layer(3, 2 + .5j), Layer(2, 1.0)], 1.0),
+                                      ([Layer(4, 3 + 0.2j), Layer(4, 1.0)], 0.6)])
+def test_reduction_matches_unreduced_system(layers, b):
     """T3: Gaussian elimination onto the aperture, (EJ1)/(uT1), followed by the
     back-substitution (EInter) reproduces the dense solve of the full unreduced
     system (all levels, all modes, (ENUGa)/(uNUGa) rows)."""
-    cav = Cavity(1.0, 1.0, 0.5, 4, 4, 8, 6.0, layers=layers)
+    cav = Cavity(1.0, b, 0.5, 4, 4, 8, 6.0, layers=layers)
     sysm = ApertureSystem(cav)
-    b = rhs(cav, 0.3, 0.7, 0.2)
-    x = sysm.solve_dense(b)
-    bru = solve_unreduced(cav, sysm.dense_tbc(), b)
+    g = rhs(cav, 0.3, 0.7, 0.2)
+    x = sysm.solve_dense(g)
+    bru = solve_unreduced(cav, sysm.dense_tbc(), g)
     scale = np.abs(x).max()
     ap = np.concatenate([bru[1][:, -1], bru[2][:, -1], bru[3][:, -1]])
     assert np.abs(ap - x).max() < 1e-12 * scale
@@ -204,22 +206,26 @@ def test_synthesis_matches_scipy_dct_dst_type1():
 
 
 def test_gtilde_trapezoid_second_order():
-    """T9: the trapezoid test integral g~ of (nosig) converges at second order
-    to the closed form int_0^a cos(m pi x/a) e^{i a1 x} dx *
-    int_0^b sin(n pi y/b) e^{i a2 y} dy."""
-    a1, a2, m, n = 5.3, -2.1, 3, 2
+    """T9: the trapezoid test integrals g~ of (nosig) converge at second order
+    to the closed forms int_0^a cos(m pi x/a) e^{i a1 x} dx *
+    int_0^b sin(n pi y/b) e^{i a2 y} dy (row 1) and int_0^a sin(m pi x/a)
+    e^{i a1 x} dx * int_0^b cos(n pi y/b) e^{i a2 y} dy (row 2), a != b."""
+    a1, a2, m, n, a, b = 5.3, -2.1, 3, 2, 1.0, 0.7
 
     def exact1(k, al, L, kind):
         s = np.array([al - k * np.pi / L, al + k * np.pi / L])
         f = np.where(s == 0, L, (np.exp(1j * s * L) - 1) / (1j * np.where(s == 0, 1, s)))
         return 0.5 * (f[0] + f[1]) if kind == 'c' else (f[1] - f[0]) / 2j
-    ex = exact1(m, a1, 1.0, 'c') * exact1(n, a2, 1.0, 's')
-    errs = []
+    ex1 = exact1(m, a1, a, 'c') * exact1(n, a2, b, 's')      # row 1: cos x1 sin x2
+    ex2 = exact1(m, a1, a, 's') * exact1(n, a2, b, 'c')      # row 2: sin x1 cos x2
+    errs1, errs2 = [], []
     for nx in (16, 32, 64, 128):
-        cav = Cavity(1.0, 1.0, 0.5, nx, nx, 4, 1.0)
-        gt1, _ = g_tilde(cav, a1, a2)
-        errs.append(abs(gt1[m, n - 1] - ex))
-    assert np.all(_order(errs) > 1.9)
+        cav = Cavity(a, b, 0.5, nx, nx, 4, 1.0)
+        gt1, gt2 = g_tilde(cav, a1, a2)
+        errs1.append(abs(gt1[m, n - 1] - ex1))
+        errs2.append(abs(gt2[m - 1, n] - ex2))
+    assert np.all(_order(errs1) > 1.9) and np.all(_order(errs2) > 1.9)
+    assert errs1[-1] < 5e-4 * abs(ex1) and errs2[-1] < 5e-4 * abs(ex2)
 
 
 # ---------------------------------------------------------------- kernel
@@ -274,25 +280,48 @@ def test_static_self_potential_of_the_square():
     assert np.all(_order(errs) > 1.5)
 
 
-def test_tbc_row_is_the_exterior_admittance():
+def test_static_self_potential_of_a_rectangle():
+    """The same limit on a 1 x 0.5 aperture: the electrostatic self-potential
+    of a rectangle, (1/4 pi) [(2/3)(a^3 + b^3 - d^3) + 2 a^2 b ln((b + d)/a) +
+    2 a b^2 ln((a + d)/b)], d = sqrt(a^2 + b^2) (the double integral of
+    1/|x - y| over the rectangle, which reduces to the square's value at
+    a = b).  Fixes the per-axis normalisation of rule D when the periods
+    differ."""
+    a, b = 1.0, 0.5
+    d = np.hypot(a, b)
+    exact = ((2 / 3) * (a ** 3 + b ** 3 - d ** 3) + 2 * a * a * b * np.log((b + d) / a)
+             + 2 * a * b * b * np.log((a + d) / b)) / (4 * np.pi)
+    errs = []
+    for nx in (8, 16, 32):
+        cav = Cavity(a, b, 0.5, nx, nx, 4, 1e-9)
+        errs.append(abs(TBCOperator(cav).diag('cc')[0, 0] - exact) / exact)
+    assert errs[-1] < 2e-3
+    assert np.all(_order(errs) > 1.5)
+
+
+@pytest.mark.parametrize("b", [1.0, 0.6])
+def test_tbc_row_is_the_exterior_admittance(b):
     """For an evanescent mode the TBC part of row 1 of (EJ1) must be -h times
     the half-space admittance z x curl E^s of (ENU1): for E1 alone that is
     h (kappa0^2 - (n pi/b)^2) / gamma, gamma^2 = lambda_mn - kappa0^2 (the field
     above the aperture decays upward).  This fixes the sign of the TBC operator
-    (see the reading in oracle.aperture) and the magnitude of I1 and I3."""
+    (see the reading in oracle.aperture) and the magnitude of I1 and I3; on a
+    rectangle (b = 0.6) it also fixes which frequency axis carries which
+    period (a kernel table with the two axes exchanged is off by 60 %)."""
     nx = 64
     kap = 2 * np.pi * nx / 10
-    cav = Cavity(1.0, 1.0, 0.5, nx, nx, 8, kap)
+    cav = Cavity(1.0, b, 0.5, nx, nx, 8, kap)
     sysm = ApertureSystem(cav)
     tb = sysm.tbc
     d1, d3 = tb.diag('cs'), tb.diag('cc')
     k2 = 2 * kap ** 2
     for (m, n) in ((32, 32), (48, 48), (3, 60)):
-        g = np.sqrt((m * np.pi) ** 2 + (n * np.pi) ** 2 - kap ** 2)
-        q = cav.a * cav.b / 4
-        row = cav.h / q * (k2 * d1[m, n - 1] - 2 * (n * np.pi) ** 2 * d3[m, n])
-        adm = cav.h * (kap ** 2 - (n * np.pi) ** 2) / g
-        assert abs(row / adm - 1) < 0.06
+        km, kn = m * np.pi / cav.a, n * np.pi / b
+        g = np.sqrt(km ** 2 + kn ** 2 - kap ** 2)
+        q = cav.a * b / 4
+        row = cav.h / q * (k2 * d1[m, n - 1] - 2 * kn ** 2 * d3[m, n])
+        adm = cav.h * (kap ** 2 - kn ** 2) / g
+        assert abs(row / adm - 1) < 0.06, (m, n, row / adm)
     # the block diagonal used by the preconditioner is the matrix diagonal
     B = sysm.block_diagonal()
     cav2 = Cavity(1.0, 1.0, 0.5, 8, 8, 8, 9.0)
