@@ -1,0 +1,138 @@
+"""Mutation check of the oracle pins (run by hand; about 15 minutes):
+
+    python tests/mutation_check.py
+
+Plants one plausible mistake at a time -- a flipped sign, a shifted index,
+a dropped factor, an exchanged a and b -- in a scratch copy of oracle/, runs
+the CPU pins (tests/test_oracle_pins.py, tests/test_khat_scheme.py) against
+it, and reports whether some pin fails ("caught").  Two mutations are known
+to survive: they change the discrete rule D only within its discretisation
+error (a shorter kernel truncation radius that still cuts only far corner
+pairs, and a frequency box two lines narrower); the GPU-versus-oracle parity
+tests and the regression fixtures of tests/golden/ fix those choices.
+Exit status 1 if any other mutation survives.
+"""
+
+import os
+import shutil
+import subprocess
+import sys
+import tempfile
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+# (file under oracle/, original text, mutated text)
+MUTATIONS = [
+    ('excitation.py', 'a1 = -kappa0 * st * cf', 'a1 = kappa0 * st * cf'),
+    ('excitation.py', 'beta = kappa0 * ct', 'beta = -kappa0 * ct'),
+    ('excitation.py', 'th_hat = np.array([ct * cf, ct * sf, -st])', 'th_hat = np.array([ct * cf, ct * sf, st])'),
+    ('excitation.py', '(a1 * p[2] + beta * p[0])', '(a1 * p[2] - beta * p[0])'),
+    ('excitation.py', '(a2 * p[2] + beta * p[1])', '(a2 * p[2] + beta * p[0])'),
+    ('excitation.py', 'q[0] = ab / 2.0', 'q[0] = ab / 4.0'),
+    ('excitation.py', 'cn[0] = ab / 2.0', 'cn[0] = ab / 4.0'),
+    ('excitation.py', 'ex = np.exp(1j * a1 * x)', 'ex = np.exp(-1j * a1 * x)'),
+    ('excitation.py', 'return np.outer(cx, sy), np.outer(sx, cy)', 'return np.outer(cx, sy), np.outer(sx, cy).conj()'),
+    ('tbc.py', 'val = (1.0 - np.exp(-2j * np.pi * safe * a)) / (2j * np.pi * safe)', 'val = (1.0 - np.exp(2j * np.pi * safe * a)) / (2j * np.pi * safe)'),
+    ('tbc.py', "return 0.5 * (em + ep)", "return 0.5 * (em - ep)"),
+    ('tbc.py', "return (em - ep) / 2j", "return (em + ep) / 2j"),
+    ('tbc.py', "w[0] *= 0.5", "w[0] *= 1.0"),
+    ('tbc.py', "return np.exp(2j * np.pi * np.outer(nodes, js) / P)", "return np.exp(-2j * np.pi * np.outer(nodes, js) / P)"),
+    ('tbc.py', "self._ex = idft_matrix(np.arange(nx + 1), self.jx, self.Px) / self.Lx", "self._ex = idft_matrix(np.arange(nx + 1), self.jx, self.Px) / self.Ly / 2"),
+    ('tbc.py', "R = np.sqrt(2.0) * max(a, b)", "R = 1.3 * max(a, b)"),
+    ('aperture.py', "wc[..., :, 1:] += self.ny[None, 1:] * e1", "wc[..., :, 1:] -= self.ny[None, 1:] * e1"),
+    ('aperture.py', "y1 = (-1.0 + p.tau1) * e1", "y1 = (1.0 + p.tau1) * e1"),
+    ('aperture.py', "y1[..., 1:, :] += (self.mx[1:, None] * h + p.vs1[1:, :]) * e3", "y1[..., 1:, :] += (self.mx[1:, None] * h - p.vs1[1:, :]) * e3"),
+    ('aperture.py', "+ (self.ny[None, 1:] * h) * e2[..., :, 1:] + (-1.0 + p.tau3) * e3", "- (self.ny[None, 1:] * h) * e2[..., :, 1:] + (-1.0 + p.tau3) * e3"),
+    ('aperture.py', "k2 = 2.0 * cav.kappa0 ** 2\n        h = cav.h\n        U1", "k2 = -2.0 * cav.kappa0 ** 2\n        h = cav.h\n        U1"),
+    ('aperture.py', "(k2 * U2 + 2.0 * self.mx[1:, None] * W[1:, :])", "(k2 * U2 - 2.0 * self.mx[1:, None] * W[1:, :])"),
+    ('field.py', "c1[1:, :] += prof.Q1[1:, :, j] * e3", "c1[1:, :] -= prof.Q1[1:, :, j] * e3"),
+    ('field.py', "f2 = sinx @ c2 @ cosy.T", "f2 = sinx @ c2 @ cosy[::-1].T"),
+    ('field.py', "siny = np.sin(np.pi * np.outer(py[1:-1], np.arange(1, N + 1)) / cav.ny)", "siny = np.sin(np.pi * np.outer(py[1:-1], np.arange(0, N)) / cav.ny)"),
+    ('khat.py', "ez = np.exp(1j * kappa0 * r) * wt", "ez = np.exp(-1j * kappa0 * r) * wt"),
+    ('khat.py', "out[idx] = 0.5 * (vals @ ez)", "out[idx] = 1.0 * (vals @ ez)"),
+    ('khat.py', "vals = j0(2.0 * np.pi * flat[idx, None] * r[None, :])", "vals = j0(np.pi * flat[idx, None] * r[None, :])"),
+    ('zsystem.py', "diag += 1.0          # Neumann: E_{3,0} = E_{3,1}", "diag += 0.0"),
+    ('zsystem.py', "ab[1, 0] = s - 1.0                       # E_{3,0} = E_{3,1}", "ab[1, 0] = s - 2.0"),
+    ('zsystem.py', "coef = mu * cav.h * (1.0 - cav.layers[up].eps / cav.layers[lo].eps)", "coef = mu * cav.h * (1.0 - cav.layers[lo].eps / cav.layers[up].eps)"),
+    ('geometry.py', "k2 = self.kappa0 ** 2 * self.layers[layer_index].eps", "k2 = self.kappa0 ** 2"),
+    ('geometry.py', "return (m * np.pi / self.a) ** 2 + (n * np.pi / self.b) ** 2", "return (m * np.pi / self.a) ** 2 + (n * np.pi / self.a) ** 2"),
+    ('tbc.py', "rho = np.sqrt((ux[:, None] / self.Lx) ** 2 + (uy[None, :] / self.Ly) ** 2)", "rho = np.sqrt((ux[:, None] / self.Ly) ** 2 + (uy[None, :] / self.Lx) ** 2)"),
+    ('tbc.py', "self._ey = idft_matrix(np.arange(ny + 1), self.jy, self.Py) / self.Ly", "self._ey = idft_matrix(np.arange(ny + 1), self.jy, self.Py) / self.Lx"),
+    ('tbc.py', "h = P // 2 - 1", "h = P // 2 - 3"),
+    ('tbc.py', "em = _E(2 * js - pad * ks, a, pad)", "em = _E(2 * js - pad * ks + 1, a, pad)"),
+    ('excitation.py', "ph_hat = np.array([-sf, cf, 0.0])", "ph_hat = np.array([sf, -cf, 0.0])"),
+    ('excitation.py', "sx = trap_matrix('s', np.arange(1, M + 1), cav.nx, cav.a) @ ex", "sx = trap_matrix('s', np.arange(0, M), cav.nx, cav.a) @ ex"),
+    ('excitation.py', "y = np.arange(cav.ny + 1) * cav.b / cav.ny", "y = np.arange(cav.ny + 1) * cav.a / cav.ny"),
+    ('aperture.py', "wc[..., 1:, :] -= self.mx[1:, None] * e2", "wc[..., 1:, :] += self.mx[1:, None] * e2"),
+    ('aperture.py', "self.ny = np.arange(0, N + 1) * np.pi / cav.b", "self.ny = np.arange(0, N + 1) * np.pi / cav.a"),
+    ('aperture.py', "y2 = (-1.0 + p.tau2) * e2", "y2 = (-1.0 + p.tau1[:p.tau2.shape[0], :p.tau2.shape[1]]) * e2"),
+    ('zsystem.py', "rhs[-1, 0] = -1.0", "rhs[-1, 0] = 1.0"),
+    ('field.py', "f1 = cosx @ c1 @ siny.T", "f1 = 0.5 * cosx @ c1 @ siny.T"),
+    ('field.py', "f3 = sinx @ c3 @ siny.T", "f3 = -(sinx @ c3 @ siny.T)"),
+    ('rcs.py', "return np.array([-I2, I1, 0.0 + 0j])", "return np.array([I2, I1, 0.0 + 0j])"),
+    ('khat.py', "omega = 2.0 * np.pi * flat + abs(kappa0)", "omega = 0.2 * np.pi * flat + abs(kappa0)"),
+    ('field.py', "c2[:, 1:] += prof.Q2[:, 1:, j] * e3", "c2[:, 1:] -= prof.Q2[:, 1:, j] * e3"),
+    ('zsystem.py', "Q[1:nz] = sol[:, 1]", "Q[1:nz] = -sol[:, 1]"),
+    ('zsystem.py', "_band_set(ab, U, ia, ia, -1.0)", "_band_set(ab, U, ia, ia, 1.0)"),
+    ('zsystem.py', "self.vs2 = self.Q2[:, :, j]", "self.vs2 = -self.Q2[:, :, j]"),
+    ('zsystem.py', "self.tau3 = self.P3[:, :, j]", "self.tau3 = self.P3[:, :, j - 1]"),
+    ('zsystem.py', "p3 = self.P3[m - 1, n - 1] if (layered and n >= 1) else None", "p3 = None"),
+    ('aperture.py', "return ((m <= mm) & (n <= nn)).ravel()", "return ((m < mm) & (n <= nn)).ravel()"),
+    ('excitation.py', "q = np.full(cav.M + 1, ab / 4.0)", "q = np.full(cav.M + 1, ab / 2.0)"),
+    ('geometry.py', "res.append((top, li, li + 1))", "res.append((top - 1, li, li + 1))"),
+    ('excitation.py', "p = np.cos(alpha) * th_hat + np.sin(alpha) * ph_hat", "p = np.sin(alpha) * th_hat + np.cos(alpha) * ph_hat"),
+    ('khat.py', "tail = np.sqrt(2.0 / np.pi) / cb * (cos_part + sin_part / 8.0)", "tail = np.sqrt(2.0 / np.pi) / cb * (cos_part - sin_part / 8.0)"),
+    ('khat.py', "pp, pm = k / cb + 1.0, k / cb - 1.0", "pp, pm = k / cb - 1.0, k / cb + 1.0"),
+    ('khat.py', "out[big] = 0.5 * (inf - tail)", "out[big] = 0.5 * (inf + tail)"),
+    ('aperture.py', "y2[..., :, 1:] += (self.ny[None, 1:] * h + p.vs2[:, 1:]) * e3", "y2[..., :, 1:] += (self.ny[None, 1:] * h) * e3"),
+]
+
+KNOWN_SURVIVORS = {
+    "R = np.sqrt(2.0) * max(a, b)",
+    "h = P // 2 - 1",
+}
+
+
+def run_one(f, a, b):
+    tmp = tempfile.mkdtemp(prefix="oracle_mutant_")
+    try:
+        shutil.copytree(os.path.join(ROOT, "oracle"), os.path.join(tmp, "oracle"),
+                        ignore=shutil.ignore_patterns("__pycache__"))
+        shutil.copytree(os.path.join(ROOT, "tests"), os.path.join(tmp, "tests"),
+                        ignore=shutil.ignore_patterns("__pycache__"))
+        shutil.copy(os.path.join(ROOT, "workloads.py"), tmp)
+        path = os.path.join(tmp, "oracle", f)
+        src = open(path).read()
+        if src.count(a) != 1:
+            return "site not found"
+        open(path, "w").write(src.replace(a, b))
+        r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
+                            "tests/test_oracle_pins.py", "tests/test_khat_scheme.py"],
+                           cwd=tmp, capture_output=True, text=True, timeout=900)
+        return "caught" if r.returncode != 0 else "survived"
+    finally:
+        shutil.rmtree(tmp, ignore_errors=True)
+
+
+def main():
+    base = subprocess.run([sys.executable, "-m", "pytest", "-q", "-p", "no:cacheprovider",
+                           "tests/test_oracle_pins.py", "tests/test_khat_scheme.py"],
+                          cwd=ROOT, capture_output=True, text=True)
+    if base.returncode != 0:
+        print("the pins fail on the unmodified oracle; fix that first")
+        return 2
+    bad = 0
+    for f, a, b in MUTATIONS:
+        res = run_one(f, a, b)
+        first = a.splitlines()[0]
+        known = first in KNOWN_SURVIVORS
+        print("%-9s %-14s %s%s" % (res, f, first[:70], "  (known)" if known and res == "survived" else ""),
+              flush=True)
+        if res != "caught" and not (known and res == "survived"):
+            bad += 1
+    print("%d mutations, %d unexpected" % (len(MUTATIONS), bad))
+    return 1 if bad else 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
