@@ -5,7 +5,9 @@
 Plants one plausible mistake at a time -- a flipped sign, a shifted index,
 a dropped factor, an exchanged a and b -- in a scratch copy of oracle/, runs
 the CPU pins (tests/test_oracle_pins.py, tests/test_khat_scheme.py) against
-it, and reports whether some pin fails ("caught").  Two mutations are known
+it, and reports whether some pin fails ("caught"); then the same for the
+block GMRES host numerics (csrc/bgmres_host.h against
+tests/test_block_host.py).  Two mutations are known
 to survive: they change the discrete rule D only within its discretisation
 error (a shorter kernel truncation radius that still cuts only far corner
 pairs, and a frequency box two lines narrower); the GPU-versus-oracle parity
@@ -93,6 +95,45 @@ KNOWN_SURVIVORS = {
 }
 
 
+# (original text, mutated text) in the block GMRES host numerics, checked
+# against tests/test_block_host.py
+HOST_HEADER = "paper_2008_01966_gb300/csrc/bgmres_host.h"
+HOST_MUTATIONS = [
+    ("const cd jpq = s * ph, jqp = -s * std::conj(ph);", "const cd jpq = s * ph, jqp = s * std::conj(ph);"),
+    ("const double t = (tau >= 0 ? 1.0 : -1.0) / (std::fabs(tau) + std::sqrt(1.0 + tau * tau));", "const double t = (tau >= 0 ? -1.0 : 1.0) / (std::fabs(tau) + std::sqrt(1.0 + tau * tau));"),
+    ("for (int k = 0; k < j; ++k) v -= L[(size_t)i * n + k] * std::conj(L[(size_t)j * n + k]);", "for (int k = 0; k < j; ++k) v -= L[(size_t)i * n + k] * L[(size_t)j * n + k];"),
+    ("if (!(d > 1e-10 * dmax)) return false;", "if (!(d > 1e-20 * dmax)) return false;"),
+    ("cond = std::sqrt(gf) * lf;", "cond = std::sqrt(gf * lf);"),
+    ("T[(size_t)i * BG_MAX + j] = std::conj(Li[(size_t)j * n + i]);  // (L^{-1})^H", "T[(size_t)i * BG_MAX + j] = Li[(size_t)j * n + i];"),
+    ("const double fl = lmax * 1e-12;", "const double fl = lmax * 1e-2;"),
+    ("S[(size_t)c * n + i] = sl * std::conj(U[(size_t)i * n + c]);", "S[(size_t)c * n + i] = sl * U[(size_t)i * n + c];"),
+    ("u[0] += ph * alpha;", "u[0] -= ph * alpha;"),
+    ("for (int t = cols; t < rows; ++t) s += std::norm(g[(size_t)t * r + j]);", "for (int t = cols + 1; t < rows; ++t) s += std::norm(g[(size_t)t * r + j]);"),
+    ("for (int k = i + 1; k < cols; ++k) s -= R[k][i] * Y[(size_t)k * BG_MAX + j];", "for (int k = i + 1; k < cols; ++k) s += R[k][i] * Y[(size_t)k * BG_MAX + j];"),
+    ("for (int p = cols - (int)cix; p < cols; ++p) {", "for (int p = cols - (int)cix + 1; p < cols; ++p) {"),
+    ("Y[(size_t)i * BG_MAX + j] = std::abs(d) > 0 ? s / d : cd(0, 0);", "Y[(size_t)i * BG_MAX + j] = s / d;"),
+    ("o[(size_t)i * n + j] += a * S[(size_t)k * n + j];", "o[(size_t)i * n + j] += a * S[(size_t)j * n + k];"),
+]
+
+
+def run_host(a, b):
+    tmp = tempfile.mkdtemp(prefix="host_mutant_")
+    try:
+        os.makedirs(os.path.join(tmp, os.path.dirname(HOST_HEADER)))
+        shutil.copytree(os.path.join(ROOT, "tests"), os.path.join(tmp, "tests"),
+                        ignore=shutil.ignore_patterns("__pycache__"))
+        src = open(os.path.join(ROOT, HOST_HEADER)).read()
+        if src.count(a) != 1:
+            return "site not found"
+        open(os.path.join(tmp, HOST_HEADER), "w").write(src.replace(a, b))
+        r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
+                            "tests/test_block_host.py"], cwd=tmp, capture_output=True, text=True,
+                           timeout=600)
+        return "caught" if r.returncode != 0 else "survived"
+    finally:
+        shutil.rmtree(tmp, ignore_errors=True)
+
+
 def run_one(f, a, b):
     tmp = tempfile.mkdtemp(prefix="oracle_mutant_")
     try:
@@ -130,7 +171,12 @@ def main():
               flush=True)
         if res != "caught" and not (known and res == "survived"):
             bad += 1
-    print("%d mutations, %d unexpected" % (len(MUTATIONS), bad))
+    for a, b in HOST_MUTATIONS:
+        res = run_host(a, b)
+        print("%-9s %-14s %s" % (res, "bgmres_host.h", a[:70]), flush=True)
+        if res != "caught":
+            bad += 1
+    print("%d mutations, %d unexpected" % (len(MUTATIONS) + len(HOST_MUTATIONS), bad))
     return 1 if bad else 0
 
 

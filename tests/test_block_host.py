@@ -126,6 +126,29 @@ def test_cholqr_orthonormalises_a_block(shim, n):
     assert cond >= np.linalg.cond(G) * (1 - 1e-12)           # an upper bound
 
 
+def _rotated(rng, lam):
+    """U diag(lam) U^H with a random unitary U."""
+    n = len(lam)
+    Q, _ = np.linalg.qr(rand_c(rng, n, n))
+    return Q @ np.diag(lam) @ Q.conj().T
+
+
+def test_cholqr_condition_bound_on_ill_conditioned_blocks(shim):
+    """The acceptance test of the solver (Cholesky QR kept without a second
+    pass when the bound is at most 1e3) needs a true upper bound where it
+    matters: on blocks of condition 2e3 and 5e5 the bound must exceed
+    cond_2(G), so such blocks are not accepted."""
+    rng = np.random.default_rng(31)
+    for lam in ([1.0, 0.3, 5e-4], [2.0, 1.0, 0.5, 0.1, 4e-6]):
+        G = _rotated(rng, np.array(lam))
+        G = 0.5 * (G + G.conj().T)
+        ok, T, S, cond = cholqr(shim, G)
+        assert ok
+        c2 = np.linalg.cond(G)
+        assert cond >= c2 * (1 - 1e-9) and cond > 1e3
+        assert np.allclose(T @ S, np.eye(len(lam)), atol=1e-9)
+
+
 def test_cholqr_refuses_dependent_blocks(shim):
     rng = np.random.default_rng(9)
     W = rand_c(rng, 100, 4)
@@ -172,6 +195,23 @@ def test_svqb_well_conditioned_and_vanished(shim):
     # exact breakdown: a zero block stays zero, nothing divides by zero
     dev, T, S, ratio = svqb(shim, np.zeros((3, 3)))
     assert dev == 1.0 and ratio == 0.0 and np.all(T == 0) and np.all(S == 0)
+
+
+def test_svqb_orthonormalises_a_widely_spread_block(shim):
+    """Eigenvalues spread over nine decades (above Cholesky QR's pivot
+    threshold) are all above SVQB's floor of 1e-12 of the largest: the new
+    block must come out orthonormal in every direction, not just the large
+    ones."""
+    rng = np.random.default_rng(32)
+    lam = np.array([1.0, 1e-3, 1e-6, 1e-9])
+    G = _rotated(rng, lam)
+    G = 0.5 * (G + G.conj().T)
+    dev, T, S, ratio = svqb(shim, G)
+    T = T[:, :4]
+    assert ratio == pytest.approx(1e-9, rel=1e-5)
+    ev = np.linalg.eigvalsh(T.conj().T @ G @ T)
+    assert np.allclose(ev, 1.0, atol=1e-5), ev
+    assert np.allclose(T @ S, np.eye(4), atol=1e-6)
 
 
 def test_matmul_left(shim):
