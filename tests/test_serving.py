@@ -72,6 +72,95 @@ def test_batching_split_and_eviction():
     assert s["answered"] == 7 and s["latency_ms"]["p99"] >= s["latency_ms"]["p50"]
 
 
+def _run_bounded(srv, reqs, limit=20.0):
+    """Server.run in a thread: a stalled scheduler fails the test instead of
+    hanging it."""
+    out = {}
+
+    def go():
+        out["res"] = srv.run(reqs)
+    t = threading.Thread(target=go, daemon=True)
+    t.start()
+    t.join(limit)
+    assert not t.is_alive(), "the scheduler stalled"
+    return out["res"]
+
+
+class TrackingBackend(FakeBackend):
+    """Records the order in which contexts close and whether a context was
+    closed while one of its solves was running."""
+
+    def __init__(self, dt=0.02):
+        super().__init__(dt)
+        self.active = set()
+        self.closed = []
+        self.closed_while_busy = False
+
+    def solve(self, handle, key, *args):
+        with self.lock:
+            self.active.add(id(handle))
+        try:
+            return super().solve(handle, key, *args)
+        finally:
+            with self.lock:
+                self.active.discard(id(handle))
+
+    def close(self, handle):
+        with self.lock:
+            if id(handle) in self.active:
+                self.closed_while_busy = True
+            self.closed.append(handle["key"])
+        super().close(handle)
+
+
+def test_batch_fills_max_dirs_exactly_and_oversized_requests_run_alone():
+    """Requests queued behind a busy context are batched while their
+    directions fit max_dirs, up to and including exactly max_dirs; a request
+    larger than max_dirs is still served, as a batch of its own."""
+    be = FakeBackend(dt=0.05)
+    srv = Server(be, budget_bytes=100, footprint=foot, max_dirs=8)
+    reqs = [req(0, 0.0, 16, 1)]
+    reqs += [req(1, 0.010, 16, 4), req(2, 0.011, 16, 4), req(3, 0.012, 16, 4)]
+    reqs += [req(4, 0.6, 16, 11)]
+    res = _run_bounded(srv, reqs)
+    assert all(r.status == 0 for r in res.values())
+    assert [b[2] for b in srv.batches] == [1, 8, 4, 11]
+    for r in reqs:
+        assert res[r.rid].dof == 10 * r.ndir          # dof per direction x directions
+
+
+def test_admission_at_the_budget_and_grid_at_the_size_limit():
+    """A context whose footprint equals the budget is admitted, and a grid at
+    exactly the largest supported side is served."""
+    srv = Server(FakeBackend(dt=0.0), budget_bytes=16, footprint=foot, max_dirs=8, max_side=16)
+    res = _run_bounded(srv, [req(0, 0.0, 16, 2)])
+    assert res[0].status == 0
+
+
+def test_least_recently_used_context_is_evicted_first():
+    """Budget for two contexts: A and B are used in that order, then A again;
+    a third key C must evict B (least recently used), not A."""
+    be = TrackingBackend(dt=0.01)
+    srv = Server(be, budget_bytes=32, footprint=foot, max_dirs=8)
+    reqs = [req(0, 0.0, 16, 1, kappa0=5.0), req(1, 0.15, 16, 1, kappa0=6.0),
+            req(2, 0.30, 16, 1, kappa0=5.0), req(3, 0.45, 16, 1, kappa0=7.0)]
+    res = _run_bounded(srv, reqs)
+    assert all(r.status == 0 for r in res.values())
+    assert be.closed[0][1] == 6.0
+    assert len(be.opened) == 3
+
+
+def test_busy_context_is_never_evicted():
+    """Budget for one context: a second key arriving while the first is
+    solving waits for it instead of closing it under the running solve."""
+    be = TrackingBackend(dt=0.3)
+    srv = Server(be, budget_bytes=16, footprint=foot, max_dirs=8)
+    res = _run_bounded(srv, [req(0, 0.0, 16, 1, kappa0=5.0), req(1, 0.05, 16, 1, kappa0=6.0)])
+    assert all(r.status == 0 for r in res.values())
+    assert not be.closed_while_busy
+    assert res[1].start >= res[0].done - 1e-6
+
+
 def test_rejections():
     be = FakeBackend()
     srv = Server(be, budget_bytes=100, footprint=lambda g, *a: 10 * g[3], max_dirs=8)
