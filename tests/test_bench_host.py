@@ -23,10 +23,10 @@ def _row(sm, mx, hw="Not Active", hwt="Not Active", swt="Not Active", cap="Not A
 def test_clock_summary_median_and_reasons():
     s = bench.ClockSampler(0)
     s.rows = [_row("2070", "2070"), _row("2055", "2070", cap="Active"),
-              _row("2070", "2070"), _row("[N/A]", "2070")]
+              _row("2070", "2040"), _row("[N/A]", "2070"), _row("2070", "2070")]
     out = s.summary()
     assert out["sm_mhz"] == 2070.0 and out["sm_max_mhz"] == 2070.0
-    assert out["reasons"] == ["sw_power_cap"] and out["samples"] == 4
+    assert out["reasons"] == ["sw_power_cap"] and out["samples"] == 5
 
 
 def test_clock_summary_flags_thermal_and_unsampled():
