@@ -30,6 +30,14 @@ CUDA path) is:
   * the outer integral is the trapezoid rule on x1_p = p a/Nx, x2_q = q b/Ny.
 
 Each step is a dense matrix here (numpy matmul as the only library step).
+
+Variant outer='parseval' (the symmetric form of the next rows of the plan,
+not used by the CUDA path): the outer integral is taken exactly as well, by
+Parseval's identity on the torus, <phi_m, I_k> = (Lx Ly)^{-1} sum_j
+conj(F(phi_m))(j/L) F(G)(|j/L|) F(phi_k)(j/L): the same frequency box and
+kernel table, with the test functions transformed exactly like the trial
+functions, so each block is Phi^H diag(F(G)) Phi, complex symmetric, and a
+dense contraction.
 """
 
 import numpy as np
@@ -92,9 +100,13 @@ class TBCOperator:
     out[m, n] = sum_k I^{mn}_k C[k] over the same index ranges.
     """
 
-    def __init__(self, cav: Cavity, kh=None, scheme='quadrature'):
+    def __init__(self, cav: Cavity, kh=None, scheme='quadrature', outer='trapezoid'):
         """scheme: 'quadrature' (the reference F(G)) or 'paper' (the
-        approximate large-frequency scheme of Sec. 5.2, `khat_paper`)."""
+        approximate large-frequency scheme of Sec. 5.2, `khat_paper`).
+        outer: 'trapezoid' (rule D) or 'parseval' (exact outer integral)."""
+        if outer not in ('trapezoid', 'parseval'):
+            raise ValueError("outer must be 'trapezoid' or 'parseval'")
+        self.outer = outer
         self.cav = cav
         self._khat = khat if scheme == 'quadrature' else khat_paper
         a, b, nx, ny, pad = cav.a, cav.b, cav.nx, cav.ny, cav.pad
@@ -141,8 +153,12 @@ class TBCOperator:
     def factors(self, kind):
         """X[m, j1] (projection after inverse DFT) and Phi[j1, k1] per axis."""
         kx, ky = kind[0], kind[1]
-        Xx = self._tx[kx] @ self._ex
-        Xy = self._ty[ky] @ self._ey
+        if self.outer == 'parseval':
+            Xx = self._fx[kx].conj().T / self.Lx
+            Xy = self._fy[ky].conj().T / self.Ly
+        else:
+            Xx = self._tx[kx] @ self._ex
+            Xy = self._ty[ky] @ self._ey
         return (Xx, self._fx[kx]), (Xy, self._fy[ky])
 
     def apply(self, kind, C):
@@ -150,6 +166,8 @@ class TBCOperator:
         kx, ky = kind[0], kind[1]
         V = self._fx[kx] @ C @ self._fy[ky].T           # frequency box
         V = V * self.Kh
+        if self.outer == 'parseval':                       # exact outer integral
+            return (self._fx[kx].conj().T / self.Lx) @ V @ (self._fy[ky].conj() / self.Ly)
         U = self._ex @ V @ self._ey.T                      # aperture nodes
         return self._tx[kx] @ U @ self._ty[ky].T           # trapezoid projection
 

@@ -333,6 +333,59 @@ def test_tbc_row_is_the_exterior_admittance(b):
     assert B.shape == (cav.M + 1, cav.N + 1, 3, 3)
 
 
+# ---------------------------------------------------------------- Parseval form (f2)
+def test_parseval_form_is_complex_symmetric():
+    """With the outer integral taken exactly (Parseval on the torus), every
+    TBC block is Phi^H diag(F(G)) Phi: I^{mn}_k = I^{k}_{mn} to rounding, for
+    the three kinds, on a rectangle.  Rule D's trapezoid outer rule is not
+    symmetric (a few per cent), which is what the variant removes.  The
+    matrix-free apply equals the dense blocks."""
+    cav = Cavity(1.0, 0.7, 0.5, 8, 8, 4, 9.0)
+    par, trap = TBCOperator(cav, outer='parseval'), TBCOperator(cav)
+    rng = np.random.default_rng(4)
+    for kind in ('cc', 'cs', 'sc'):
+        I = par.dense(kind)
+        assert np.abs(I - I.transpose(2, 3, 0, 1)).max() < 1e-14 * np.abs(I).max()
+        It = trap.dense(kind)
+        assert np.abs(It - It.transpose(2, 3, 0, 1)).max() > 1e-2 * np.abs(It).max()
+        C = rng.standard_normal(I.shape[2:]) + 1j * rng.standard_normal(I.shape[2:])
+        assert np.allclose(par.apply(kind, C), np.einsum('mnkq,kq->mn', I, C),
+                           rtol=0, atol=1e-13 * np.abs(I).max() * np.abs(C).sum())
+
+
+@pytest.mark.parametrize("a,b", [(1.0, 1.0), (1.0, 0.5)])
+def test_parseval_form_static_self_potential(a, b):
+    """The kappa0 -> 0 limit of I3^{00}_{00} in the Parseval form converges at
+    second order to the closed-form self-potential of the rectangle (same
+    expression as for rule D), with a smaller constant."""
+    d = np.hypot(a, b)
+    exact = ((2 / 3) * (a ** 3 + b ** 3 - d ** 3) + 2 * a * a * b * np.log((b + d) / a)
+             + 2 * a * b * b * np.log((a + d) / b)) / (4 * np.pi)
+    errs = []
+    for nx in (8, 16, 32):
+        cav = Cavity(a, b, 0.5, nx, nx, 4, 1e-9)
+        errs.append(abs(TBCOperator(cav, outer='parseval').diag('cc')[0, 0] - exact) / exact)
+    assert np.all(_order(errs) > 1.8) and errs[-1] < 3e-4
+
+
+def test_parseval_form_agrees_with_rule_d_as_the_grid_refines():
+    """Both outer rules discretise the same integrals, so the backscatter RCS
+    of a fixed two-layer cavity computed with either approaches the same
+    value: their relative gap shrinks under refinement (8^2, 16^2, 32^2)."""
+    kap, th, ph, al = 2 * np.pi * 2.0, 0.6, 0.8, 0.3
+    gaps = []
+    for nx in (8, 16, 32):
+        cav = Cavity(1.0, 0.8, 0.5, nx, nx, nx, kap,
+                     layers=[Layer(nx // 2, 2 + 0.2j), Layer(nx - nx // 2, 1.0)])
+        sig = []
+        for outer in ('trapezoid', 'parseval'):
+            sysm = ApertureSystem(cav, tbc=TBCOperator(cav, outer=outer))
+            x = sysm.solve_dense(rhs(cav, th, ph, al))
+            sig.append(backscatter(cav, x, th, ph, 'theta'))
+        gaps.append(abs(sig[0] - sig[1]) / sig[1])
+    assert np.all(_order(gaps) > 1.5) and gaps[-1] < 1e-2
+
+
 # ---------------------------------------------------------------- whole solve
 def test_normal_incidence_selection_rules():
     """T6: at normal incidence with p = x_hat on a square aperture the problem
