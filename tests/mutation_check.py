@@ -87,6 +87,9 @@ MUTATIONS = [
     ('khat.py', "pp, pm = k / cb + 1.0, k / cb - 1.0", "pp, pm = k / cb - 1.0, k / cb + 1.0"),
     ('khat.py', "out[big] = 0.5 * (inf - tail)", "out[big] = 0.5 * (inf + tail)"),
     ('aperture.py', "y2[..., :, 1:] += (self.ny[None, 1:] * h + p.vs2[:, 1:]) * e3", "y2[..., :, 1:] += (self.ny[None, 1:] * h) * e3"),
+    ('tbc.py', "return (self._fx[kx].conj().T / self.Lx) @ V @ (self._fy[ky].conj() / self.Ly)", "return (self._fx[kx].T / self.Lx) @ V @ (self._fy[ky] / self.Ly)"),
+    ('tbc.py', "            Xx = self._fx[kx].conj().T / self.Lx\n", "            Xx = self._fx[kx].conj().T\n"),
+    ('tbc.py', "return (self._fx[kx].conj().T / self.Lx) @ V @ (self._fy[ky].conj() / self.Ly)", "return (self._fx[kx].conj().T / self.Lx) @ V @ (self._fy[ky].conj() / self.Lx)"),
 ]
 
 KNOWN_SURVIVORS = {
