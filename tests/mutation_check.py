@@ -26,6 +26,10 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 # (file under oracle/, original text, mutated text)
 MUTATIONS = [
     ('excitation.py', 'a1 = -kappa0 * st * cf', 'a1 = kappa0 * st * cf'),
+    ('excitation.py', 'g1 = (h / q)[:, None] * 2j * (a1', 'g1 = (h / q)[:, None] * -1j * (a1'),
+    ('excitation.py', 'g2 = (h / cn)[None, :] * 2j * (a2', 'g2 = (h / cn)[None, :] * -1j * (a2'),
+    ('excitation.py', 'g1 = (h / q)[:, None] * 2j * (a1', 'g1 = (h / q)[:, None] * -2j * (a1'),
+    ('excitation.py', 'g2 = (h / cn)[None, :] * 2j * (a2', 'g2 = (h / cn)[None, :] * 1j * (a2'),
     ('excitation.py', 'beta = kappa0 * ct', 'beta = -kappa0 * ct'),
     ('excitation.py', 'th_hat = np.array([ct * cf, ct * sf, -st])', 'th_hat = np.array([ct * cf, ct * sf, st])'),
     ('excitation.py', '(a1 * p[2] + beta * p[0])', '(a1 * p[2] - beta * p[0])'),
