@@ -52,6 +52,7 @@ def khat(rho, kappa0, R, nodes=_NODES):
     x, w = _gl(nodes)
     omega = 2.0 * np.pi * flat + abs(kappa0)
     npan = np.maximum(1, np.ceil(omega * R / np.pi)).astype(int)
+    jobs = []
     for npv in np.unique(npan):
         sel = np.nonzero(npan == npv)[0]
         width = R / npv
@@ -62,11 +63,30 @@ def khat(rho, kappa0, R, nodes=_NODES):
         ez = np.exp(1j * kappa0 * r) * wt           # (nr,)
         # chunk over rho to bound memory
         chunk = max(1, int(4_000_000 // r.size))
-        for s in range(0, sel.size, chunk):
-            idx = sel[s:s + chunk]
-            vals = j0(2.0 * np.pi * flat[idx, None] * r[None, :])
-            out[idx] = 0.5 * (vals @ ez)
+        jobs.extend((sel[s:s + chunk], r, ez) for s in range(0, sel.size, chunk))
+
+    def one(job):
+        idx, r, ez = job
+        vals = j0(2.0 * np.pi * flat[idx, None] * r[None, :])
+        out[idx] = 0.5 * (vals @ ez)
+    # chunks are independent (disjoint entries of out); J0 releases the GIL,
+    # so large tables are shared out over threads
+    if len(jobs) > 1 and flat.size > 100_000:
+        from concurrent.futures import ThreadPoolExecutor
+        with ThreadPoolExecutor(_threads()) as ex:
+            list(ex.map(one, jobs))
+    else:
+        for job in jobs:
+            one(job)
     return out.reshape(rho.shape)
+
+
+def _threads():
+    try:
+        import os
+        return max(1, len(os.sched_getaffinity(0)))
+    except Exception:
+        return 1
 
 
 def khat_zero(kappa0, R):

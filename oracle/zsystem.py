@@ -176,6 +176,54 @@ def _e3_profile_homogeneous(cav: Cavity, m: int, n: int):
     return P
 
 
+def _profile_rows(cav: Cavity, ms):
+    """Profiles of every mode in the rows m in `ms` (P3, then P1/Q1 and P2/Q2,
+    which use P3 of the same (m, n) in a layered fill)."""
+    N, nz = cav.N, cav.nz
+    layered = len(cav.layers) > 1
+    out = []
+    for m in ms:
+        p3 = np.zeros((N, nz + 1), dtype=complex) if m >= 1 else None
+        if m >= 1:
+            for n in range(1, N + 1):
+                if layered:
+                    p3[n - 1], _ = e3_profile(cav, m, n)
+                else:
+                    p3[n - 1] = _e3_profile_homogeneous(cav, m, n)
+        p1 = np.zeros((N, nz + 1), dtype=complex)
+        q1 = np.zeros_like(p1)
+        for n in range(1, N + 1):
+            d3 = p3[n - 1] if (layered and m >= 1) else None
+            p1[n - 1], q1[n - 1] = tangential_profiles(cav, m, n, m * np.pi / cav.a, d3)
+        p2 = q2 = None
+        if m >= 1:
+            p2 = np.zeros((N + 1, nz + 1), dtype=complex)
+            q2 = np.zeros_like(p2)
+            for n in range(0, N + 1):
+                d3 = p3[n - 1] if (layered and n >= 1) else None
+                p2[n], q2[n] = tangential_profiles(cav, m, n, n * np.pi / cav.b, d3)
+        out.append((m, p3, p1, q1, p2, q2))
+    return out
+
+
+def _profile_rows_job(args):
+    return _profile_rows(*args)
+
+
+def _workers(cav: Cavity, workers):
+    """Processes for the per-mode solves: one for small grids (where starting
+    a pool costs more than it saves), else every core of this process."""
+    if workers is not None:
+        return max(1, int(workers))
+    if cav.M * cav.N < 128 * 128:
+        return 1
+    try:
+        import os
+        return max(1, len(os.sched_getaffinity(0)))
+    except Exception:
+        return 1
+
+
 class Profiles:
     """All per-mode profiles of a cavity.
 
@@ -183,32 +231,43 @@ class Profiles:
     P2[m-1, n, j], Q2[m-1, n, j]   E2 over N2
     P3[m-1, n-1, j]                E3 over N3 (upper value at interfaces)
     tau1, tau2, tau3, vs1, vs2     top relations (level Nz-1) as 2-D arrays
+
+    Every mode's system is solved on its own (the per-mode problems are
+    independent); on large grids the rows m are shared out over a pool of
+    processes (started with `spawn`), each solving whole rows exactly as a
+    single process would.
     """
 
-    def __init__(self, cav: Cavity):
+    def __init__(self, cav: Cavity, workers=None):
         M, N, nz = cav.M, cav.N, cav.nz
-        layered = len(cav.layers) > 1
         self.P3 = np.zeros((M, N, nz + 1), dtype=complex)
-        for m in range(1, M + 1):
-            for n in range(1, N + 1):
-                if layered:
-                    self.P3[m - 1, n - 1], _ = e3_profile(cav, m, n)
-                else:
-                    self.P3[m - 1, n - 1] = _e3_profile_homogeneous(cav, m, n)
         self.P1 = np.zeros((M + 1, N, nz + 1), dtype=complex)
         self.Q1 = np.zeros_like(self.P1)
-        for m in range(0, M + 1):
-            for n in range(1, N + 1):
-                p3 = self.P3[m - 1, n - 1] if (layered and m >= 1) else None
-                self.P1[m, n - 1], self.Q1[m, n - 1] = tangential_profiles(
-                    cav, m, n, m * np.pi / cav.a, p3)
         self.P2 = np.zeros((M, N + 1, nz + 1), dtype=complex)
         self.Q2 = np.zeros_like(self.P2)
-        for m in range(1, M + 1):
-            for n in range(0, N + 1):
-                p3 = self.P3[m - 1, n - 1] if (layered and n >= 1) else None
-                self.P2[m - 1, n], self.Q2[m - 1, n] = tangential_profiles(
-                    cav, m, n, n * np.pi / cav.b, p3)
+        nw = _workers(cav, workers)
+        rows = list(range(0, M + 1))
+        parts = None
+        if nw > 1:
+            # a spawned worker re-imports the main script, so a script that
+            # builds large profiles needs the usual `if __name__ == "__main__"`
+            # guard; without it the pool fails and the rows are solved here
+            import multiprocessing as mp
+            from concurrent.futures import ProcessPoolExecutor
+            chunks = [rows[k::4 * nw] for k in range(4 * nw)]
+            try:
+                with ProcessPoolExecutor(nw, mp_context=mp.get_context("spawn")) as ex:
+                    parts = list(ex.map(_profile_rows_job, [(cav, c) for c in chunks if c]))
+            except Exception:
+                parts = None
+        if parts is None:
+            parts = [_profile_rows(cav, rows)]
+        for part in parts:
+            for m, p3, p1, q1, p2, q2 in part:
+                self.P1[m], self.Q1[m] = p1, q1
+                if m >= 1:
+                    self.P3[m - 1] = p3
+                    self.P2[m - 1], self.Q2[m - 1] = p2, q2
         j = nz - 1
         self.tau1 = self.P1[:, :, j]
         self.tau2 = self.P2[:, :, j]
