@@ -201,21 +201,27 @@ cavity_status cavity_rhs(cavity_ctx* ctx, int ndir, const double* theta,
 cavity_status cavity_apply(cavity_ctx* ctx, int ndir, int precision,
                            const void* x, void* y);
 
-/* Allocation-free y = A x: the same operator and argument conventions as
- * cavity_apply, for callers that may not allocate device memory -- for
- * example a host application that owns a fixed device memory budget and
- * forbids libraries to call cudaMalloc in its solve loop, where an allocation
- * would also add an implicit device synchronisation.  It needs a context that
- * cavity_setup and cavity_prepare built beforehand; the call itself allocates
- * nothing.  The transform passes use a fixed 4 MiB device array inside the
- * library (held on every device that loads it, until exit) as scratch; sizes
- * whose scratch exceeds 4 MiB (e.g. more than about 2 directions at
- * 64 x 64 in FP64) are rejected with CAVITY_EINVAL and a message.  The first
- * call on a device looks up the array's device address (make that first call
- * before any stream capture); the context's device must be current.  All
- * calls share the one array: calls that overlap on the GPU (other streams,
- * other contexts, other threads) race and must be serialised by the caller.
- * Nothing carries over between calls: each call writes all scratch it reads.
+/* Allocation-free y = A x: the operator of cavity_apply, for callers that
+ * may not allocate device memory -- for example a host application that owns
+ * a fixed device memory budget and forbids libraries to call cudaMalloc in
+ * its solve loop, where an allocation would also add an implicit device
+ * synchronisation.  It needs a context that cavity_setup and cavity_prepare
+ * built beforehand; the call itself allocates nothing.
+ *  precision: CAVITY_FP64 (x, y complex128) or CAVITY_MIXED (FP32 operator,
+ *             x, y complex64) only; CAVITY_PAIR32 and any other value return
+ *             CAVITY_EINVAL.
+ *  x, y:      ndir x n_ap device buffers of the context's device, caller-owned;
+ *             y must not overlap x (the operator reads x while writing y).
+ * The transform passes use a fixed 4 MiB device array inside the library
+ * (held on every device that loads it, until exit) as scratch; sizes whose
+ * scratch exceeds 4 MiB (e.g. more than about 2 directions at 64 x 64 in
+ * FP64) are rejected with CAVITY_EINVAL and a message.  The first call on a
+ * device looks up the array's device address (make that first call before
+ * any stream capture); the context's device must be current.  The call
+ * synchronises the context's stream before it returns.  All calls share the
+ * one array: calls that overlap on the GPU (other streams, other contexts,
+ * other threads) race and must be serialised by the caller.  Nothing carries
+ * over between calls: each call writes all scratch it reads.
  * The paper has no counterpart to this entry point. */
 cavity_status cavity_apply_noalloc(cavity_ctx* ctx, int ndir, int precision,
                                    const void* x, void* y);

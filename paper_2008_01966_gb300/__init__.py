@@ -35,6 +35,34 @@ def _layers(layers):
             ei.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
 
 
+_NOALLOC_PRECISION = {"fp64": _lib.CAVITY_FP64, "mixed": _lib.CAVITY_MIXED}
+
+
+def check_operator_io(x, y, dtype, n_ap, device):
+    """Argument checks of an operator call y = A x that writes through y's raw
+    pointer: both tensors on `device`, of `dtype`, shaped (ndir, n_ap) alike,
+    contiguous, and y not overlapping x.  Raises ValueError before anything
+    reaches the library."""
+    for name, t in (("x", x), ("y", y)):
+        if not isinstance(t, torch.Tensor):
+            raise ValueError("%s must be a tensor" % name)
+        if t.device != device:
+            raise ValueError("%s must be on %s, not %s" % (name, device, t.device))
+        if t.dtype != dtype:
+            raise ValueError("%s must be %s, not %s" % (name, dtype, t.dtype))
+        if t.dim() != 2 or t.shape[1] != n_ap or t.shape[0] < 1:
+            raise ValueError("%s must have shape (ndir, %d), not %s" % (name, n_ap,
+                                                                        tuple(t.shape)))
+        if not t.is_contiguous():
+            raise ValueError("%s must be contiguous" % name)
+    if y.shape != x.shape:
+        raise ValueError("y must have x's shape %s, not %s" % (tuple(x.shape), tuple(y.shape)))
+    nb = x.numel() * x.element_size()
+    x0, y0 = x.data_ptr(), y.data_ptr()
+    if x0 < y0 + nb and y0 < x0 + nb:
+        raise ValueError("y must not overlap x (the operator reads x while it writes y)")
+
+
 class Cavity:
     """One cavity geometry and grid with its resident device state."""
 
@@ -165,15 +193,28 @@ class Cavity:
         return y
 
     def apply_noalloc(self, x, precision=None, y=None):
-        """y = A x through the allocation-free entry point (library-internal
-        fixed scratch; the caller provides x and y)."""
-        prec = self.precision if precision is None else (
-            _lib.CAVITY_FP64 if precision == "fp64" else _lib.CAVITY_MIXED)
-        x = x.contiguous()
+        """y = A x through the allocation-free entry point: the library uses
+        its own fixed scratch array and allocates nothing.  precision: None
+        (the context's), "fp64" (complex128 vectors) or "mixed" (FP32
+        operator, complex64 vectors); the pair-of-FP32 operator has no
+        allocation-free form.  y, if given, must be a contiguous CUDA tensor
+        of x's shape and dtype on the context's device that does not overlap
+        x; otherwise a new tensor is returned (allocated here by torch, not
+        by the library)."""
+        if precision is None:
+            prec = self.precision
+        elif precision in _NOALLOC_PRECISION:
+            prec = _NOALLOC_PRECISION[precision]
+        else:
+            raise ValueError("apply_noalloc precision must be 'fp64' or 'mixed', not %r"
+                             % (precision,))
         want = torch.complex128 if prec == _lib.CAVITY_FP64 else torch.complex64
-        if x.dtype != want or not x.is_cuda or x.dim() != 2 or x.shape[1] != self.n_ap:
-            raise ValueError("x must be a CUDA (ndir, n_ap) tensor of %s" % want)
-        y = torch.empty_like(x) if y is None else y
+        if self.device.type != "cuda":
+            raise ValueError("apply_noalloc needs a CUDA context")
+        x = x.contiguous()
+        if y is None:
+            y = torch.empty_like(x)
+        check_operator_io(x, y, want, self.n_ap, self.device)
         self._check(self.lib.cavity_apply_noalloc(self.h, x.shape[0], prec,
                                                   ctypes.c_void_p(x.data_ptr()),
                                                   ctypes.c_void_p(y.data_ptr())))

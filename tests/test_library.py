@@ -50,3 +50,54 @@ def test_setup_rejects_bad_descriptors_without_a_gpu():
         assert st == _lib.CAVITY_EINVAL, bad
         assert lib.cavity_last_error(None)
     assert lib.cavity_setup(None, None, ctypes.byref(h)) == _lib.CAVITY_EINVAL
+
+
+def test_operator_io_checks_raise_before_the_library_is_called():
+    """The binding checks y (and x) before it hands raw pointers to the
+    library: wrong device, dtype, shape, stride, or y overlapping x."""
+    torch = pytest.importorskip("torch")
+    import paper_2008_01966_gb300 as gb
+    cpu = torch.device("cpu")
+    n = 10
+    x = torch.zeros((2, n), dtype=torch.complex128)
+    gb.check_operator_io(x, torch.empty_like(x), torch.complex128, n, cpu)
+    bad_y = [torch.zeros((2, n), dtype=torch.complex64),          # dtype
+             torch.zeros((3, n), dtype=torch.complex128),         # shape
+             torch.zeros((2, n + 1), dtype=torch.complex128),     # n_ap
+             torch.zeros((n, 2), dtype=torch.complex128).t(),     # not contiguous
+             torch.zeros((2, n), dtype=torch.complex128, device="meta"),  # device
+             x,                                                   # y is x
+             torch.zeros((3, n), dtype=torch.complex128)[1:],     # ok on its own ...
+             "not a tensor"]
+    big = torch.zeros((3, n), dtype=torch.complex128)
+    x_in_big = big[:2]
+    for k, y in enumerate(bad_y):
+        xx = x
+        if k == 6:
+            xx, y = x_in_big, big[1:]                             # ... but overlaps x
+        with pytest.raises(ValueError):
+            gb.check_operator_io(xx, y, torch.complex128, n, cpu)
+    with pytest.raises(ValueError):
+        gb.check_operator_io(x.to(torch.complex64), torch.empty_like(x), torch.complex128, n,
+                             cpu)
+
+
+def test_noalloc_precision_names_are_checked():
+    """Only 'fp64' and 'mixed' reach the allocation-free entry point; any
+    other name raises in the binding (no silent mapping to mixed)."""
+    torch = pytest.importorskip("torch")
+    import paper_2008_01966_gb300 as gb
+
+    class NoLib:
+        def __getattr__(self, name):
+            raise AssertionError("library called: " + name)
+    g = object.__new__(gb.Cavity)
+    g.lib, g.h, g.n_ap, g.precision = NoLib(), None, 4, 0
+    g.device = torch.device("cpu")
+    x = torch.zeros((1, 4), dtype=torch.complex128)
+    for name in ("pair32", "fp32", "FP64", ""):
+        with pytest.raises(ValueError):
+            g.apply_noalloc(x, name)
+    with pytest.raises(ValueError):          # a CPU context never reaches the library
+        g.apply_noalloc(x, "fp64")
+    g.h = None
