@@ -1,17 +1,27 @@
-"""Benchmark: cavity field DOF/s for the 256 x 256 x 128, 16-direction workload.
+"""Benchmark: cavity field DOF/s of the paper's solver on one GB300.
 
-One step = cavity_solve for one batch of 16 incident directions: excitation
-(g1, g2), aperture solve of (EJ1) (FP32 Krylov iterations with FP64 residual
-refinement), back-substitution and inverse transforms for the full interior
-field (complex64).  The per-(kappa0, eps) state -- kernel table, per-mode
-elimination, preconditioner -- is built once before the timed region and
-reused, as the paper reuses its singular integrals for all incident angles;
-its time is reported as setup_ms.
+Default workload (the largest single-GPU configuration): layered4, a
+512 x 512 x 256 grid with four layers of 64 steps (permittivities a seeded
+permutation of {4+1i, 2+0.5i, 6+0.1i, 1}), 10 points per wavelength in the
+densest layer, 8 incident directions.  `--workload dirs16` runs the
+homogeneous 256 x 256 x 128, 16-direction case instead.
+
+One step = cavity_solve for the batch of incident directions: excitation
+(g1, g2), aperture solve of (uT1) (FP32 block Krylov iterations inside FP64
+residual refinement), back-substitution and inverse transforms for the full
+interior field (complex64).  The per-(kappa0, eps) state -- kernel table,
+per-mode elimination, preconditioner -- is built once before the timed region
+and reused, as the paper reuses its singular integrals for all incident
+angles; its time is reported as setup_ms.  The same directions are then
+solved by the plain FP64 path (fp64_path: DOF/s, p50/p99), and, on one GPU,
+by the CPU oracle, against which both GPU results are compared per direction
+(accuracy) and which is timed (cpu_baseline).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+                    [--workload layered4|dirs16]
 
 N > 1 runs under torch.distributed (one rank per GPU); every rank solves its
-own batch of 16 directions (independent problems, weak scaling) and the max
+own batch of directions (independent problems, weak scaling) and the max
 time over ranks is reported.
 """
 
@@ -30,19 +40,37 @@ sys.path.insert(0, ROOT)
 
 import workloads  # noqa: E402
 
-WORKLOAD = "dirs16"
+WORKLOADS = {
+    "layered4": {"desc": "layered4: 512x512x256 grid, a=b=1, c=0.5, four layers of 64 steps "
+                         "(eps a seeded permutation of {4+1i, 2+0.5i, 6+0.1i, 1}, top to "
+                         "bottom), kappa0=2pi/(10h sqrt 6) (10 points per wavelength in the "
+                         "densest layer), 8 seeded incident directions per GPU",
+                 "seed": 3, "oracle_dirs": 1},
+    "dirs16": {"desc": "dirs16: 256x256x128 grid, a=b=1, c=0.5, eps=1, kappa0=2pi*25.6 "
+                       "(10 points per wavelength), 16 seeded incident directions per GPU",
+               "seed": 2, "oracle_dirs": 2},
+}
+DEFAULT_WORKLOAD = "layered4"
 METRIC = "cavity field DOF/s at rel err \u22641e-5 vs FP64 oracle; p50/p99 solve latency"
 # Aperture residual target of the timed mixed-precision solve.  Measured on
-# this workload against the FP64 path solved to 1e-12: the field error is at
-# the complex64 synthesis floor (1.6e-7) from tol 1e-8 down, 1.7e-7 at 1e-7,
-# 5.8e-7 at 1e-6 and 1.1e-5 (over the 1e-5 bound) at 1e-5.  1e-7 keeps the
-# error at the floor; every run re-measures it (the "accuracy" entry).
+# the 256^2 workload against the FP64 path solved to 1e-12: the field error is
+# at the complex64 synthesis floor (1.6e-7) from tol 1e-8 down, 1.7e-7 at
+# 1e-7, 5.8e-7 at 1e-6 and 1.1e-5 (over the 1e-5 bound) at 1e-5.  1e-7 keeps
+# the error at the floor; every run re-measures it against the oracle (the
+# "accuracy" entry).
 TOL = 1e-7
+# Oracle GMRES iterations to a relative residual of 1e-12 (first direction of
+# each workload), used to size the reference arm's bounded steps.
+REF_ITERS = {"layered4": 40, "dirs16": 30}
 # DRAM traffic of one launch of a kernel class from one `ncu --set full`
-# capture on 8 directions, scaled to the 16 directions of a launch here
-# (traffic is proportional to the directions).  Only valid for the kernel as
-# captured: emptied whenever the kernel changes, refilled from the next capture.
-NCU_TRAFFIC = {"tbc_B_fp32": 2 * (52.550656e6 + 21.679616e6)}   # profiles/tbc_B_fp32_dirs16.txt
+# capture, per launch of the benchmark (scaled by directions where the
+# capture had fewer; traffic is proportional to the directions).  Only valid
+# for the kernel as captured: emptied whenever the kernel changes.
+NCU_TRAFFIC = {("dirs16", "tbc_B_fp32"): 2 * (52.550656e6 + 21.679616e6)}
+# FP64 FMA throughput measured on a GB300 with a throughput kernel (16
+# independent FMA chains per thread, 8 blocks of 256 threads per SM, CUDA
+# events, best of 5); None until measured.
+FP64_MEASURED_TFLOPS = None
 
 
 def peaks():
@@ -134,23 +162,37 @@ def alg_flops_per_launch(cls, w, ndir):
 
 
 def fp_peak_tflops(cls, sm_mhz):
-    """ALU peaks: FP64 1.25 TFLOP/s (nominal GB300 figure); FP32 derived as
-    152 SMs x 128 FP32 lanes x 2 flops x SM clock."""
+    """ALU peaks: FP64 from the measured FMA throughput (the nominal GB300
+    figure 1.25 TFLOP/s until measured); FP32 derived as 152 SMs x 128 FP32
+    lanes x 2 flops x SM clock."""
     if cls.endswith("fp64"):
+        if FP64_MEASURED_TFLOPS:
+            return FP64_MEASURED_TFLOPS, "measured FP64 FMA throughput"
         return 1.25, "nominal FP64 1.25 TFLOP/s"
     clk = (sm_mhz or 2070.0) * 1e6
     return 152 * 128 * 2 * clk / 1e12, "derived FP32 152x128x2xclock"
 
 
-# ---------------------------------------------------------------- oracle sample
-def oracle_sample(w, ndir_sample=1, time_budget=None):
-    """The CPU oracle on a bounded sample of the workload: per direction, the
-    aperture solve (block-preconditioned GMRES, FP64) and the full field
-    synthesis.  The oracle's own setup (kernel table, per-mode elimination) is
-    done first and reported separately, like the GPU's."""
+def class_roofline(cls, cms, ccnt, w, ndir, sm_mhz, workload):
+    """ALU roofline of one TBC kernel class from its live event time: the
+    algorithmic flops of one launch over the mean launch duration."""
+    flops = alg_flops_per_launch(cls, w, ndir)
+    if flops is None or ccnt <= 0 or cms <= 0:
+        return None
+    per_launch_s = cms / ccnt / 1e3
+    ach = flops / per_launch_s / 1e12
+    pk, pk_kind = fp_peak_tflops(cls, sm_mhz)
+    return {"kernel": cls, "bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
+            "frac": ach / pk, "traffic": NCU_TRAFFIC.get((workload, cls)),
+            "peak_source": pk_kind, "launch_ms": cms / ccnt,
+            "algorithmic_flops_per_launch": flops}
+
+
+# ---------------------------------------------------------------- oracle leg
+def oracle_system(w):
+    """The oracle's discretised system of the workload, with its setup time
+    (kernel table, per-mode elimination, preconditioner blocks)."""
     from oracle.aperture import ApertureSystem
-    from oracle.excitation import rhs
-    from oracle.field import field
     from oracle.geometry import Cavity, Layer
     from oracle.tbc import TBCOperator
     from oracle.zsystem import Profiles
@@ -158,16 +200,51 @@ def oracle_sample(w, ndir_sample=1, time_budget=None):
                  layers=[Layer(n, e) for n, e in w['layers']])
     t0 = time.perf_counter()
     sysm = ApertureSystem(cav, Profiles(cav), TBCOperator(cav))
-    setup = time.perf_counter() - t0
-    times = []
-    for d in range(ndir_sample):
+    return cav, sysm, time.perf_counter() - t0
+
+
+def oracle_leg(w, th, ph, al, dirs, results):
+    """The CPU oracle on directions `dirs` of the batch: aperture GMRES to a
+    relative residual of 1e-12 and the field on every level, timed (the
+    cpu_baseline), and each GPU result in `results` ({name: (aperture, field)}
+    device tensors of the whole batch) compared with it per direction:
+    rel-L2 of the aperture vector, and of the whole field of the direction,
+    accumulated level by level (plus the worst single level)."""
+    from oracle.excitation import rhs
+    from oracle.field import field_level, synth_mats
+    cav, sysm, setup = oracle_system(w)
+    mats = synth_mats(cav)
+    errs = {k: {"aperture": [], "field": [], "field_worst_level": []} for k in results}
+    t_solve = t_field = 0.0
+    for d in dirs:
         t0 = time.perf_counter()
-        b = rhs(cav, w['theta'][d], w['phi'][d], w['alpha'][d])
-        x, _ = sysm.solve_gmres(b, rtol=1e-10)
-        field(cav, sysm.prof, x[0])
-        times.append(time.perf_counter() - t0)
-    dof = w['nz'] * cav.n_ap
-    return dof, times, setup
+        x, res = sysm.solve_gmres(rhs(cav, th[d], ph[d], al[d]), rtol=1e-12)
+        x = x[0]
+        t_solve += time.perf_counter() - t0
+        for k, (ap, _) in results.items():
+            g = ap[d].cpu().numpy()
+            errs[k]["aperture"].append(float(np.linalg.norm(g - x) / np.linalg.norm(x)))
+        num = {k: 0.0 for k in results}
+        den = 0.0
+        worst = {k: 0.0 for k in results}
+        for j in range(1, cav.nz + 1):
+            t0 = time.perf_counter()
+            F = field_level(cav, sysm.prof, x, j, mats)
+            t_field += time.perf_counter() - t0
+            nF = float(np.vdot(F, F).real)
+            den += nF
+            S = F.size
+            for k, (_, fl) in results.items():
+                G = fl[d, (j - 1) * S:j * S].cpu().numpy().astype(np.complex128)
+                e = float(np.vdot(G - F, G - F).real)
+                num[k] += e
+                worst[k] = max(worst[k], (e / max(nF, 1e-300)) ** 0.5)
+        for k in results:
+            errs[k]["field"].append((num[k] / den) ** 0.5)
+            errs[k]["field_worst_level"].append(worst[k])
+    dof = w['nz'] * cav.n_ap * len(dirs)
+    return {"errors": errs, "setup_s": setup, "solve_s": t_solve, "field_s": t_field,
+            "dof": dof, "dirs": list(dirs), "oracle_resid_max": float(res.max())}
 
 
 def cores():
@@ -181,53 +258,63 @@ def cores():
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
-    w = workloads.workload(WORKLOAD)
+    w = workloads.workload(args.workload)
+    w['name'] = args.workload
     steps, warm = args.steps, args.warmup
-    from oracle.aperture import ApertureSystem
     from oracle.excitation import rhs
-    from oracle.field import field
-    from oracle.geometry import Cavity, Layer
-    from oracle.tbc import TBCOperator
-    from oracle.zsystem import Profiles
-    cav = Cavity(w['a'], w['b'], w['c'], w['nx'], w['ny'], w['nz'], w['kappa0'],
-                 layers=[Layer(n, e) for n, e in w['layers']])
-    t0 = time.perf_counter()
-    sysm = ApertureSystem(cav, Profiles(cav), TBCOperator(cav))
-    setup = time.perf_counter() - t0
+    from oracle.field import field_level, synth_mats
+    cav, sysm, setup = oracle_system(w)
+    mats = synth_mats(cav)
+    pre = sysm.preconditioner()
+    iters = REF_ITERS[args.workload]
+    lev_per_step = max(1, int(round(w['nz'] / iters)))
+    b = rhs(cav, w['theta'][0], w['phi'][0], w['alpha'][0])
+    x = b / np.linalg.norm(b)
+    rng = np.random.Generator(np.random.PCG64(1))
+    xa = rng.standard_normal(cav.n_ap) + 1j * rng.standard_normal(cav.n_ap)
 
-    def step(d):
-        b = rhs(cav, w['theta'][d], w['phi'][d], w['alpha'][d])
-        x, _ = sysm.solve_gmres(b, rtol=1e-10)
-        field(cav, sysm.prof, x[0])
+    def step(k):
+        nonlocal x
+        x = sysm.apply(pre(x))
+        x = x / np.linalg.norm(x)
+        j0 = (k * lev_per_step) % w['nz']
+        for j in range(j0 + 1, min(j0 + lev_per_step, w['nz']) + 1):
+            field_level(cav, sysm.prof, xa, j, mats)
     for k in range(warm):
-        step(k % 16)
+        step(k)
     t0 = time.perf_counter()
     for k in range(steps):
-        step((warm + k) % 16)
+        step(warm + k)
     el = time.perf_counter() - t0
-    dof = w['nz'] * cav.n_ap * steps
-    val = dof / el
+    dof_step = lev_per_step * cav.n_ap
+    val = dof_step * steps / el
     nc = cores()
+    sample = ("per step: one oracle GMRES iteration of one direction (operator + block "
+              "preconditioner on %d unknowns) and the field on %d of %d levels; %d such "
+              "steps make one direction's solve (GMRES to 1e-12 takes %d iterations on this "
+              "workload), so each step is credited %d field DOF; oracle setup %.1f s excluded"
+              % (cav.n_ap, lev_per_step, w['nz'], iters, iters, dof_step, setup))
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "DOF/s",
             "n_gpus": world, "steps": steps, "warmup": warm, "ms_per_step": 1e3 * el / steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
-            "data": "synthetic", "config": {"workload": WORKLOAD + ": 256x256x128 grid, eps=1, "
-                                            "kappa0=2pi*25.6, 1 incident direction per step"},
+            "data": "synthetic", "config": {"workload": WORKLOADS[args.workload]["desc"]},
             "setup_ms": 1e3 * setup,
             "cpu_baseline": {"value": val, "unit": "DOF/s", "cores": nc, "kind": "oracle",
-                             "sample": "one incident direction per step (aperture GMRES + full "
-                                       "field), oracle setup excluded"},
+                             "sample": sample},
             "e2e": {"value": val, "unit": "DOF/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
 
-def rank_directions(w, rank, ndir):
+def rank_directions(w, rank, ndir, seed=2):
     """Incident directions of one rank: rank 0 takes the workload's own
-    seeded batch, rank r > 0 an independent batch seeded 2 + r (weak scaling:
-    every rank solves its own 16 directions, no data exchange)."""
-    th, ph, al = workloads.directions(16, 2 + rank) if rank else (w['theta'], w['phi'], w['alpha'])
+    seeded batch, rank r > 0 an independent batch of the same size seeded
+    seed + r (weak scaling: every rank solves its own directions, no data
+    exchange)."""
+    n = len(w['theta'])
+    th, ph, al = workloads.directions(n, seed + rank) if rank else (w['theta'], w['phi'],
+                                                                      w['alpha'])
     return th[:ndir], ph[:ndir], al[:ndir]
 
 
@@ -246,6 +333,35 @@ def job_value(dof_per_rank_step, steps, world, ms):
     return dof_per_rank_step * steps * world / (ms / 1e3)
 
 
+def percentile(sorted_ms, q):
+    return sorted_ms[min(len(sorted_ms) - 1, max(0, int(math.ceil(q * len(sorted_ms))) - 1))]
+
+
+def field_bytes(w, n_ap, n12, field_per_dir, ndir, elem):
+    """Algorithmic bytes of one field synthesis (a5+a6) of ndir directions:
+    the field written once, the profiles read once (P over n_ap, and Q over
+    N1 + N2 in a layered fill), the aperture vectors read once."""
+    layered = len(w['layers']) > 1
+    prof = (w['nz'] - 1) * (n_ap + (n12 if layered else 0)) * elem
+    return ndir * field_per_dir * elem + prof + ndir * n_ap * elem
+
+
+def timed_steps(step, steps, stream):
+    """Run `steps` calls of step() between CUDA events on `stream`; returns
+    (total ms, sorted per-step ms, last result)."""
+    import torch
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    out = None
+    for k in range(steps):
+        out = step()
+        ev[k + 1].record(stream)
+    torch.cuda.synchronize()
+    per = sorted(ev[k].elapsed_time(ev[k + 1]) for k in range(steps))
+    return ev[0].elapsed_time(ev[-1]), per, out
+
+
 def run_gb300(args, rank, world, local_rank):
     import torch
     import __graft_entry__
@@ -257,8 +373,9 @@ def run_gb300(args, rank, world, local_rank):
     import paper_2008_01966_gb300 as gb
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    w = workloads.workload(WORKLOAD)
-    th, ph, al = rank_directions(w, rank, args.ndir)
+    spec = WORKLOADS[args.workload]
+    w = workloads.workload(args.workload)
+    th, ph, al = rank_directions(w, rank, args.ndir or len(w['theta']), spec["seed"])
     ndir = len(th)
     tol = TOL
     cav = gb.Cavity(w['a'], w['b'], w['c'], w['nx'], w['ny'], w['nz'], precision="mixed",
@@ -280,21 +397,13 @@ def run_gb300(args, rank, world, local_rank):
     cav.timing(False)
     if world > 1:
         torch.distributed.barrier()
-    torch.cuda.synchronize()
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     with ClockSampler(local_rank) as clk:
         torch.cuda.nvtx.range_push("timed")      # lets ncu select the timed steps
-        ev[0].record(stream)
-        for k in range(args.steps):
-            _, _, iters, res = step()
-            ev[k + 1].record(stream)
-        torch.cuda.synchronize()
+        ms, step_ms, out = timed_steps(step, args.steps, stream)
         torch.cuda.nvtx.range_pop()
+    _, _, iters, res = out
     if world > 1:
         torch.distributed.barrier()
-    e0, e1 = ev[0], ev[-1]
-    step_ms = sorted(ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps))
-    ms = e0.elapsed_time(e1)
     counts = cav.timing_read()
     launches = sum(c for _, c in counts.values())
     ms = max_over_ranks(ms, world, dev)
@@ -307,7 +416,6 @@ def run_gb300(args, rank, world, local_rank):
         step()
     kt = cav.timing_read()
     cav.timing(False)
-    instr_launches = sum(c for _, c in kt.values())
 
     # e2e: same metric through the C ABI with host (pinned) output buffers
     aph = torch.empty((ndir, cav.n_ap), dtype=torch.complex128, pin_memory=True)
@@ -326,80 +434,97 @@ def run_gb300(args, rank, world, local_rank):
     e2e = job_value(dof_step, args.steps, world, e2e_ms)
     h2d = ndir * 6 * 8
     d2h = ndir * cav.n_ap * 16 + ndir * cav.field_per_dir * 8
+    del aph, flh
 
-    # accuracy of the timed result: the same directions through the FP64 path
-    # (FP64 transforms and GMRES to 1e-12, itself matched to the oracle to
-    # 1e-10 by the parity tests), outside the timed region
+    # the plain FP64 path on the same configuration and directions: FP64
+    # transforms, FP64 GMRES to 1e-12, complex128 field
     ref = gb.Cavity(w['a'], w['b'], w['c'], w['nx'], w['ny'], w['nz'], precision="fp64",
                     gmres_tol=1e-12)
-    ap64, fl64, _, res64 = ref.solve(w['kappa0'], w['layers'], th, ph, al, field=True)
-    err_ap = (torch.linalg.vector_norm(ap - ap64, dim=1) /
-              torch.linalg.vector_norm(ap64, dim=1)).max().item()
-    err_fl = max((torch.linalg.vector_norm(fl[d].to(torch.complex128) - fl64[d]) /
-                  torch.linalg.vector_norm(fl64[d])).item() for d in range(ndir))
-    accuracy = {"vs": "FP64 GPU path, GMRES tol 1e-12 (max resid %.1e)" % float(res64.max()),
-                "aperture_rel_err_max": err_ap, "field_rel_err_max": err_fl,
-                "bound": 1e-5, "ok": bool(err_fl <= 1e-5 and err_ap <= 1e-5)}
-    del ref, ap64, fl64
-    torch.cuda.empty_cache()
+    ref.prepare(w['kappa0'], w['layers'])
+    ap64 = torch.empty((ndir, cav.n_ap), dtype=torch.complex128, device=dev)
+    fl64 = torch.empty((ndir, cav.field_per_dir), dtype=torch.complex128, device=dev)
+
+    def step64():
+        return ref.solve(w['kappa0'], w['layers'], th, ph, al, field=True, aperture_out=ap64,
+                         field_out=fl64)
+    step64()
+    ms64, step64_ms, out64 = timed_steps(step64, args.fp64_steps, stream)
+    ms64 = max_over_ranks(ms64, world, dev)
+    _, _, it64, res64 = out64
+    ref.timing(True)
+    step64()
+    kt64 = ref.timing_read()
+    ref.timing(False)
+    fp64_path = {"value": job_value(dof_step, args.fp64_steps, world, ms64), "unit": "DOF/s",
+                 "ms_per_step": ms64 / args.fp64_steps, "steps": args.fp64_steps,
+                 "latency_ms": {"p50": percentile(step64_ms, 0.5),
+                                "p99": percentile(step64_ms, 0.99)},
+                 "gmres_iters": [int(i) for i in it64], "resid_max": float(res64.max()),
+                 "kernel_ms_per_step": {k: v[0] for k, v in kt64.items() if v[1]},
+                 "dtype": "f64 throughout, complex128 field"}
 
     hbm, hbm_kind, _ = peaks()
     csum = clk.summary()
-    # dominant kernel class and its roofline
-    dom = max(kt.items(), key=lambda kv: kv[1][0])
-    cls, (cms, ccnt) = dom
-    flops = alg_flops_per_launch(cls, w, ndir)
-    roof = None
-    if flops is not None and ccnt > 0:
-        per_launch_s = cms / ccnt / 1e3
-        ach = flops / per_launch_s / 1e12
-        pk, pk_kind = fp_peak_tflops(cls, csum.get("sm_mhz"))
-        roof = {"kernel": cls, "bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
-                "frac": ach / pk, "traffic": NCU_TRAFFIC.get(cls) if ndir == 16 else None,
-                "peak_source": pk_kind,
-                "launch_ms": cms / ccnt, "algorithmic_flops_per_launch": flops}
-    # HBM view of the field path (write of the field; profile read amortised)
-    fx_ms, fx_n = kt.get("field_x", (0, 0))
-    fy_ms, fy_n = kt.get("field_y", (0, 0))
-    fbytes = ndir * cav.field_per_dir * 8 + (w['nz'] - 1) * cav.n_ap * 8
+    rooflines = {}
+    for cls, (cms, ccnt) in kt.items():
+        r = class_roofline(cls, cms, ccnt, w, ndir, csum.get("sm_mhz"), args.workload)
+        if r is not None:
+            rooflines[cls] = r
+    # the field path (a5+a6) against HBM
+    fcls = [c for c in kt if c.startswith("field")]
+    f_ms = sum(kt[c][0] for c in fcls)
+    fbytes = field_bytes(w, cav.n_ap, cav.n1 + cav.n2, cav.field_per_dir, ndir, 8)
     field_roof = None
-    if fx_ms + fy_ms > 0:
-        ach = fbytes / ((fx_ms + fy_ms) / args.steps / 1e3) / 1e9
-        field_roof = {"kernels": "field_y+field_x", "bound": "hbm", "achieved": ach, "peak": hbm,
+    if f_ms > 0:
+        ach = fbytes / (f_ms / args.steps / 1e3) / 1e9
+        field_roof = {"kernels": "+".join(fcls), "bound": "hbm", "achieved": ach, "peak": hbm,
                       "unit": "GB/s", "frac": ach / hbm, "peak_source": hbm_kind,
-                      "algorithmic_bytes_per_step": fbytes}
+                      "algorithmic_bytes_per_step": fbytes,
+                      "ms_per_step": f_ms / args.steps}
+    dom = max(kt.items(), key=lambda kv: kv[1][0])[0]
+    roof = rooflines.get(dom)
+    if roof is None and dom.startswith("field"):
+        roof = dict(field_roof, kernel=dom)
     line = {"metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": world,
             "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "c64 transforms and Krylov; f64 elimination and refinement; f32-pair residual operator", "data": "synthetic",
-            "config": {"workload": WORKLOAD + ": 256x256x128 grid, a=b=1, c=0.5, eps=1, "
-                                   "kappa0=2pi*25.6 (10 points per wavelength), 16 seeded "
-                                   "incident directions per GPU, mixed precision, "
-                                   "aperture tol %.0e" % tol,
+            "dtype": "c64 transforms and Krylov; f64 elimination and refinement; "
+                     "f32-pair residual operator",
+            "data": "synthetic",
+            "config": {"workload": spec["desc"] + ", mixed precision, aperture tol %.0e" % tol,
                        "dof_per_step_per_gpu": dof_step,
-                       "l2": "working set larger than L2 (3.2 GB field written per step)",
+                       "l2": "working set larger than L2 (%.1f GB field written per step)"
+                             % (ndir * cav.field_per_dir * 8 / 1e9),
                        "setup": "resident per (kappa0, eps); timed separately"},
-            "latency_ms": {"p50": step_ms[(len(step_ms) - 1) // 2],
-                           "p99": step_ms[min(len(step_ms) - 1,
-                                              int(math.ceil(0.99 * len(step_ms))) - 1)],
-                           "per": "one cavity_solve of the 16-direction batch"},
-            "accuracy": accuracy,
+            "latency_ms": {"p50": percentile(step_ms, 0.5), "p99": percentile(step_ms, 0.99),
+                           "per": "one cavity_solve of the %d-direction batch" % ndir},
             "setup_ms": setup_ms, "gmres_iters": [int(i) for i in iters],
             "resid": [float(r) for r in res],
             "gpu_launches": int(launches // args.steps) * args.steps,
             "gpu_launches_per_step": launches / args.steps,
             "kernel_ms_per_step": {k: v[0] / args.steps for k, v in kt.items() if v[1]},
             "roofline": roof, "roofline_field_path": field_roof,
+            "roofline_by_class": rooflines,
+            "fp64_path": fp64_path,
             "e2e": {"value": e2e, "unit": "DOF/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "clocks": csum}
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        dof1, times, osetup = oracle_sample(w, 3)
-        line["cpu_baseline"] = {"value": dof1 / sum(times), "unit": "DOF/s", "cores": cores(),
-                                "kind": "oracle",
-                                "sample": "3 of the 16 directions: aperture GMRES + full field "
-                                          "(%.1f s); oracle setup %.1f s excluded" %
-                                          (sum(times), osetup)}
+    if rank == 0 and world == 1 and not args.no_oracle:
+        dirs = list(range(min(args.oracle_dirs or spec["oracle_dirs"], ndir)))
+        o = oracle_leg(w, th, ph, al, dirs, {"mixed": (ap, fl), "fp64_path": (ap64, fl64)})
+        em, e64 = o["errors"]["mixed"], o["errors"]["fp64_path"]
+        line["accuracy"] = {
+            "vs": "FP64 oracle (CPU, complex128; GMRES to 1e-12, max resid %.1e), directions %s"
+                  % (o["oracle_resid_max"], o["dirs"]),
+            "mixed": em, "fp64_path": e64, "bound_mixed": 1e-5, "bound_fp64": 1e-10,
+            "ok": bool(max(em["aperture"] + em["field"]) <= 1e-5 and
+                       max(e64["aperture"] + e64["field"]) <= 1e-10)}
+        line["cpu_baseline"] = {
+            "value": o["dof"] / (o["solve_s"] + o["field_s"]), "unit": "DOF/s",
+            "cores": cores(), "kind": "oracle",
+            "sample": "%d of the %d directions: aperture GMRES to 1e-12 (%.1f s) + full field "
+                      "(%.1f s); oracle setup %.1f s excluded"
+                      % (len(dirs), ndir, o["solve_s"], o["field_s"], o["setup_s"])}
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0
@@ -411,9 +536,14 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--ndir", type=int, default=16,
-                    help="directions per GPU (16 is the benchmark; fewer only for profiling)")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--no-oracle", "--no-cpu-baseline", dest="no_oracle", action="store_true",
+                    help="skip the oracle leg (accuracy and cpu_baseline)")
+    ap.add_argument("--oracle-dirs", type=int, default=0,
+                    help="directions the oracle solves (default: 1 for layered4, 2 for dirs16)")
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--ndir", type=int, default=0,
+                    help="directions per GPU (0: the workload's batch; fewer only for profiling)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

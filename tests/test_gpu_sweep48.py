@@ -2,10 +2,10 @@
 layered fills, four wavenumbers, 64 directions each) on a seeded subset, as in
 the measurement plan: the first cavity of every size class, all four
 wavenumbers and all 64 directions on the GPU (mixed precision, aperture and
-RCS); against the oracle's direct or GMRES solve for the 64 and 128 classes
-(8 directions at one wavenumber), and by the FP64 residual of the operator
-(itself matched to the oracle at every grid size) and agreement with the FP64
-path for the 256 and 512 classes.
+RCS); against the oracle's GMRES solve at one wavenumber: 8 directions for
+the 64 and 128 classes, 2 for the 256 and 512 classes (whose oracle setup
+and solves take minutes), plus, for those two classes, the FP64 residual of
+every direction and agreement with the FP64 path.
 """
 
 import numpy as np
@@ -53,20 +53,19 @@ def test_sweep48_subset(gb, index, cv):
         assert np.all(np.isfinite(s)) and np.all(s >= 0)
         sig.append((kappa0, ap, s))
     kappa0, ap, s = sig[1]
-    if cv['nx'] <= 128:
-        cav = OCavity(cv['a'], cv['b'], cv['c'], cv['nx'], cv['ny'], cv['nz'], kappa0,
-                      layers=[Layer(n, e) for n, e in cv['layers']])
-        sysm = ApertureSystem(cav)
-        sel = np.arange(0, 64, 8)
-        B = np.array([oracle_rhs(cav, th[d], ph[d], al[d]) for d in sel])
-        X, ores = sysm.solve_gmres(B)
-        assert np.all(ores < 1e-12)
-        ref = np.array([backscatter(cav, X[k], th[d], ph[d]) for k, d in enumerate(sel)])
-        apn = ap.cpu().numpy()
-        for k, d in enumerate(sel):
-            assert np.linalg.norm(apn[d] - X[k]) <= 1e-6 * np.linalg.norm(X[k])
-        assert np.all(np.abs(s[sel] - ref) <= 1e-5 * ref.max())
-    else:
+    cav = OCavity(cv['a'], cv['b'], cv['c'], cv['nx'], cv['ny'], cv['nz'], kappa0,
+                  layers=[Layer(n, e) for n, e in cv['layers']])
+    sysm = ApertureSystem(cav)
+    sel = np.arange(0, 64, 8) if cv['nx'] <= 128 else np.array([0, 32])
+    B = np.array([oracle_rhs(cav, th[d], ph[d], al[d]) for d in sel])
+    X, ores = sysm.solve_gmres(B, rtol=1e-12, restart=300, maxiter=300)
+    assert np.all(ores < 1e-11)
+    ref = np.array([backscatter(cav, X[k], th[d], ph[d]) for k, d in enumerate(sel)])
+    apn = ap.cpu().numpy()
+    for k, d in enumerate(sel):
+        assert np.linalg.norm(apn[d] - X[k]) <= 1e-6 * np.linalg.norm(X[k]), d
+    assert np.all(np.abs(s[sel] - ref) <= 1e-5 * ref.max())
+    if cv['nx'] > 128:
         g.prepare(kappa0, cv['layers'])
         b = g.rhs(th, ph, al)
         r = b - g.apply(ap, "fp64")
