@@ -282,22 +282,17 @@ __device__ __forceinline__ void fft_pass(C<T>* line, int n, int s, int t, int tp
   line_group_sync(tpl);
 }
 
-// Warp transform of one line of length n = LW * RV (RV = LW or 2 LW) by LW lanes
-// (several lines per warp when LW < 32).  Lane l holds x[l + LW r], r < RV:
+// Core of the warp transform: lane l holds v[r] = x[l + LW r], r < RV, of a
+// line of length n = LW * RV (RV = LW or 2 LW).
 //   X1[k1] = DFT_RV over r;  X1[k1] *= w_n^{l k1};  transposed through the
-//   line's own shared memory;  lane l then owns k1 = l + LW q and forms the
-//   LW-point DFT over the lanes:  X[k1 + RV k2].
-// One shared-memory round trip and warp-level synchronisation only.
-template <typename T, bool INV, int LW, int RV, typename Op = LineId<T>>
-__device__ __forceinline__ void fft_warp(C<T>* line, int n, int logn, int l, bool active,
-                                         const C<T>* __restrict__ tw, int twlog, int lidx = 0,
-                                         const Op& op = Op()) {
-  C<T> v[RV];
-  if (active) {
-#pragma unroll
-    for (int r = 0; r < RV; ++r) v[r] = op.ld(lidx, line, l + LW * r);
-  }
-  __syncwarp();
+//   tile (RV x (LW + 1) entries of shared memory);  lane l then owns
+//   k1 = l + LW q and forms the LW-point DFT over the lanes.
+// On return v[q LW + k2] = X[k1 + RV k2] with k1 = l + LW q.  The tile may
+// overlap the line (all inputs are in registers); warp synchronisation only.
+template <typename T, bool INV, int LW, int RV>
+__device__ __forceinline__ void fft_warp_core(C<T>* v, C<T>* tile, int n, int logn, int l,
+                                              bool active, const C<T>* __restrict__ tw,
+                                              int twlog) {
   if (active) {
     dft_nat<T, INV, RV>(v);
     const int shift = twlog - logn;
@@ -316,7 +311,7 @@ __device__ __forceinline__ void fft_warp(C<T>* line, int n, int logn, int l, boo
       for (int i = 1; i < 8; ++i) v[8 * g + i] = cmul<T>(v[8 * g + i], cmul<T>(wg, wi[i]));
     }
 #pragma unroll
-    for (int k1 = 0; k1 < RV; ++k1) line[k1 * (LW + 1) + l] = v[k1];
+    for (int k1 = 0; k1 < RV; ++k1) tile[k1 * (LW + 1) + l] = v[k1];
   }
   __syncwarp();
   constexpr int Q = RV / LW;
@@ -324,13 +319,33 @@ __device__ __forceinline__ void fft_warp(C<T>* line, int n, int logn, int l, boo
 #pragma unroll
     for (int q = 0; q < Q; ++q)
 #pragma unroll
-      for (int ll = 0; ll < LW; ++ll) v[q * LW + ll] = line[(l + LW * q) * (LW + 1) + ll];
+      for (int ll = 0; ll < LW; ++ll) v[q * LW + ll] = tile[(l + LW * q) * (LW + 1) + ll];
   }
   __syncwarp();
   if (active) {
 #pragma unroll
+    for (int q = 0; q < Q; ++q) dft_nat<T, INV, LW>(v + q * LW);
+  }
+}
+
+// Warp transform of one line of length n = LW * RV (RV = LW or 2 LW) by LW lanes
+// (several lines per warp when LW < 32): the core above on the line's own
+// shared memory, with op's first read and last write.
+template <typename T, bool INV, int LW, int RV, typename Op = LineId<T>>
+__device__ __forceinline__ void fft_warp(C<T>* line, int n, int logn, int l, bool active,
+                                         const C<T>* __restrict__ tw, int twlog, int lidx = 0,
+                                         const Op& op = Op()) {
+  C<T> v[RV];
+  if (active) {
+#pragma unroll
+    for (int r = 0; r < RV; ++r) v[r] = op.ld(lidx, line, l + LW * r);
+  }
+  __syncwarp();
+  fft_warp_core<T, INV, LW, RV>(v, line, n, logn, l, active, tw, twlog);
+  constexpr int Q = RV / LW;
+  if (active) {
+#pragma unroll
     for (int q = 0; q < Q; ++q) {
-      dft_nat<T, INV, LW>(v + q * LW);
       const int k1 = l + LW * q;
 #pragma unroll
       for (int k2 = 0; k2 < LW; ++k2) op.st(lidx, line, k1 + RV * k2, v[q * LW + k2]);
@@ -461,4 +476,49 @@ __device__ __forceinline__ void fft_warp_lines(C<T>* base, int lstride, int firs
     C<T>* line = base + (size_t)(active ? l : first) * lstride;
     fft_warp<T, INV, LW, S::RV, Op>(line, 1 << LOGN, LOGN, t, active, tw, twlog, l, op);
   }
+}
+
+// Named barrier of the two warps of a two-warp transform (ids 1..15; 0 is
+// __syncthreads).
+__device__ __forceinline__ void pair_sync(int id) {
+  asm volatile("bar.sync %0, 64;" ::"r"(id) : "memory");
+}
+
+// Two-warp transform of one FP32 line of length n = 2^LOGN (2048): one radix-2
+// step (decimation in frequency) and a warp transform of length n/2 per warp.
+// Warp h (0 or 1) forms u_h[i] = x[i] + x[i + n/2] (h = 0) or
+// (x[i] - x[i + n/2]) w_n^i (h = 1) and transforms it: X[2k + h] = DFT_{n/2}(u_h)[k].
+// Both warps read the whole line (op.ld) before either writes; their tiles
+// lie in disjoint halves of the line (the line's padded length is at least
+// n + n/8); both finish reading their tiles before either stores (op.st with
+// the output index 2k + h).  bar_id: a named barrier owned by the two warps.
+template <typename T, bool INV, int LOGN, typename Op = LineId<T>>
+__device__ __forceinline__ void fft_warp2(C<T>* line, int h, int l, const C<T>* __restrict__ tw,
+                                          int twlog, int bar_id, int lidx = 0,
+                                          const Op& op = Op()) {
+  constexpr int n = 1 << LOGN, nh = n / 2;
+  using S = LineShape<T, LOGN - 1>;
+  static_assert(S::WARP && S::LW == 32, "two-warp transform of 2 x 1024 points");
+  constexpr int LW = S::LW, RV = S::RV;
+  C<T> v[RV];
+  const int shift = twlog - LOGN;
+#pragma unroll
+  for (int r = 0; r < RV; ++r) {
+    const int i = l + LW * r;
+    const C<T> a = op.ld(lidx, line, i), b = op.ld(lidx, line, i + nh);
+    v[r] = h == 0 ? cadd<T>(a, b) : cmul<T>(csub<T>(a, b), twid<T, INV>(tw, i << shift));
+  }
+  pair_sync(bar_id);
+  constexpr int TILE = RV * (LW + 1);
+  static_assert(TILE <= nh + nh / 8, "tiles fit in the two halves of the padded line");
+  fft_warp_core<T, INV, LW, RV>(v, line + h * (nh + nh / 8), nh, LOGN - 1, l, true, tw, twlog);
+  pair_sync(bar_id);
+  constexpr int Q = RV / LW;
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const int k1 = l + LW * q;
+#pragma unroll
+    for (int k2 = 0; k2 < LW; ++k2) op.st(lidx, line, 2 * (k1 + RV * k2) + h, v[q * LW + k2]);
+  }
+  __syncwarp();
 }

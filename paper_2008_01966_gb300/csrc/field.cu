@@ -246,10 +246,59 @@ __global__ void k_ap32(const double2* __restrict__ a, float2* __restrict__ b, lo
   if (k < n) b[k] = make_float2((float)a[k].x, (float)a[k].y);
 }
 
+// the persistent single-kernel synthesis of field_fused.cu (complex64 field)
+bool field_fused_supported(const Geo& g);
+size_t field_fused_work_bytes(const Geo& g);
+cavity_status launch_field_fused(cavity_ctx* ctx, int ndir, const float2* apT, float2* out,
+                                 int j0, int nlev, void* work);
+cavity_status field_fused_check(cavity_ctx* ctx, void* work);
+
+static cavity_status launch_field_fused_all(cavity_ctx* ctx, int ndir, const double2* ap,
+                                            float2* out, void* host_out) {
+  const Geo& g = ctx->g;
+  const size_t apb = ((sizeof(float2) * (size_t)ndir * g.nap + 255) / 256) * 256;
+  CKS(ensure_ws(ctx, &ctx->ws2, &ctx->ws2_bytes, apb + field_fused_work_bytes(g)));
+  float2* a32 = (float2*)ctx->ws2;
+  void* work = (char*)ctx->ws2 + apb;
+  {
+    const long long n = (long long)ndir * g.nap;
+    KScope ks_(ctx, KC_FIELD_Y);
+    k_ap32<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(ap, a32, n);
+  }
+  // device output: one launch over all levels; host output: chunks of levels,
+  // each copied out (one segment per direction, over four copy streams)
+  // while the next is synthesised
+  const int nchunk = host_out ? std::min(g.nz, 8) : 1;
+  const int lc = (g.nz + nchunk - 1) / nchunk;
+  if (host_out) CKS(ensure_copy_stream(ctx, (size_t)nchunk + 2));
+  int chunk = 0;
+  for (int j0 = 1; j0 <= g.nz; j0 += lc, ++chunk) {
+    const int nl = std::min(lc, g.nz - j0 + 1);
+    CKS(launch_field_fused(ctx, ndir, a32, out, j0, nl, work));
+    if (host_out) {
+      cudaEvent_t ev = ctx->copy_evs[2 + chunk];
+      CK(cudaEventRecord(ev, ctx->stream));
+      cudaStream_t cs[4] = {ctx->copy_stream, ctx->copy_more[0], ctx->copy_more[1],
+                            ctx->copy_more[2]};
+      for (int k = 0; k < 4; ++k) CK(cudaStreamWaitEvent(cs[k], ev, 0));
+      for (int d = 0; d < ndir; ++d) {
+        const size_t off = ((size_t)d * g.nz + (j0 - 1)) * (size_t)g.field_per_level;
+        CK(cudaMemcpyAsync((float2*)host_out + off, out + off,
+                           sizeof(float2) * (size_t)nl * g.field_per_level,
+                           cudaMemcpyDeviceToHost, cs[d & 3]));
+      }
+    }
+  }
+  return field_fused_check(ctx, work);
+}
+
 template <typename T>
 cavity_status launch_field(cavity_ctx* ctx, int ndir, const double2* ap, C<T>* out,
                            void* host_out) {
   const Geo& g = ctx->g;
+  if constexpr (sizeof(T) == 4) {
+    if (field_fused_supported(g)) return launch_field_fused_all(ctx, ndir, ap, out, host_out);
+  }
   const bool layered = ctx->layers.size() > 1;
   const size_t slab = (size_t)3 * g.nx * (g.ny + 1) * sizeof(C<T>);
   int lc = (int)std::max<size_t>(1, ((size_t)512 << 20) / (slab * ndir));

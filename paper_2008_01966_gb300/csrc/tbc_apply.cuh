@@ -480,6 +480,182 @@ __global__ void TBC_BOUNDS k_tbcD(const C<T>* __restrict__ Z, C<T>* __restrict__
   fft_lines<T, false, LNX + 1>(buf, ls, L, tw, p.twlog, cd);
 }
 
+// ------------------------------------------------------------------ passes B, C at 2048 points
+// FP32 lines of 2048 points (the 512 x 512 grid: Px = Py = 2048) do not fit
+// one warp's registers; each line is transformed by two warps (fft_warp2:
+// one radix-2 step, then a 1024-point warp transform per warp), so these
+// passes keep the warp transforms of the smaller grids -- no block barrier
+// inside a transform, one shared-memory round trip per 1024-point half.
+// Pass B: two columns per block of eight warps, each parity line on a warp
+// pair; pass C: four rows per block, each on a warp pair; the named barrier
+// of pair g is 1 + g.  (Pass A keeps the block transform at this size: a
+// two-warp version measured 0.46 against 0.29 ms per 8-direction launch.)
+template <int N2> struct W2 {
+  static constexpr int LS = padded_len(N2);
+  static constexpr int L = 2;           // rows / columns per block
+};
+
+// pass B: grid (Py / 2 column pairs, 3 fields, ndir).  The parity kernels
+// are read from global memory (32 KB, L1 resident); shared memory holds the
+// four lines and the kernel-table rows of the two columns.
+template <typename T>
+struct OwnParityG : LineId<T> {
+  const C<T>* __restrict__ eh;    // [r][P], global
+  int P, L;
+  __device__ __forceinline__ void st(int l, C<T>* line, int k, C<T> v) const {
+    const int r = l >= L ? 1 : 0;
+    line[pidx(k)] = cmul<T>(v, __ldg(eh + r * P + k));
+  }
+};
+
+// KhatB for the two-warp pass: the lanes of a warp write outputs 2 apart, so
+// they read the kernel table 4 apart in j1; the rows are staged with
+// j1 -> (j1 mod 4) (Px/8 + 4) + j1 / 4 (row length KH_ROW), which makes
+// those reads consecutive and the staging writes free of bank conflicts
+template <int LNX>
+struct KhatBPerm : LineId<float> {
+  static constexpr int KH_ROW = 4 * ((4 << LNX) / 8 + 4);
+  const float2* kh;               // rows |j2| of the block's columns, permuted
+  int j0, Py, L;
+  __device__ __forceinline__ static int perm(int j1) {
+    constexpr int Px = 4 << LNX;
+    return (j1 & 3) * (Px / 8 + 4) + (j1 >> 2);
+  }
+  __device__ __forceinline__ void st(int lr, float2* line, int k, float2 v) const {
+    constexpr int Px = 4 << LNX, hp = Px / 2, qp = Px / 4;
+    int t, u;
+    if (k < qp) { t = k; u = k; }
+    else if (k >= Px - qp) { t = k - Px; u = k - hp; }
+    else return;
+    const int r = lr >= L ? 1 : 0, l = lr - r * L;
+    const int j = j0 + l;
+    const int j1 = 2 * t + r;
+    float2 o = czero<float>();
+    if (j1 != -hp && j < Py && j != Py / 2) {
+      const int j1a = j1 < 0 ? -j1 : j1;
+      o = cmul<float>(v, kh[l * KH_ROW + perm(j1a)]);
+    }
+    line[pidx(u)] = o;
+  }
+};
+
+template <int LNX>
+__global__ void __launch_bounds__(LINES_THREADS, 2)
+    k_tbcB_w2(const float2* __restrict__ Vy, float2* __restrict__ W, TbcP p,
+              const float2* __restrict__ tw, const float2* __restrict__ eh_c,
+              const float2* __restrict__ eh_s, const float2* __restrict__ kh) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  float2* buf = (float2*)sm_raw;
+  constexpr int LPX = LNX + 2, Px = 1 << LPX, nx = 1 << LNX, ls = W2<Px>::LS, L = W2<Px>::L;
+  const int Py = p.Py;
+  const int f = blockIdx.y, d = blockIdx.z;
+  const int j0 = blockIdx.x * L;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  const bool xcos = (f != 1);
+  float2* kh_sm = buf + (size_t)2 * L * ls;
+  for (int idx = tid; idx < L * (Px / 2); idx += nthr) {
+    const int l = idx >> (LPX - 1), j1 = idx & (Px / 2 - 1);
+    const int j = j0 + l;
+    const int j2a = j < Py / 2 ? j : Py - j;
+    kh_sm[l * KhatBPerm<LNX>::KH_ROW + KhatBPerm<LNX>::perm(j1)] =
+        (j < Py && j != Py / 2) ? kh[(size_t)j2a * (Px / 2) + j1] : czero<float>();
+  }
+  // both parity lines of each column receive the mirrored column; the slots
+  // [nx, Px - nx] are cleared
+  {
+    const float2* src = Vy + (size_t)(d * 3 + f) * nx * Py;
+    for (int idx = tid; idx < L * nx; idx += nthr) {
+      const int k1 = idx >> 1, l = idx & 1;
+      const int j = j0 + l;
+      const float2 c = j < Py ? src[(size_t)k1 * Py + j] : czero<float>();
+      const float2 c0 = k1 == 0 ? (xcos ? cscale<float>(c, 2.f) : czero<float>()) : c;
+      const float2 cm = xcos ? c : mk<float>(-c.x, -c.y);
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        float2* line = buf + (size_t)(r * L + l) * ls;
+        line[pidx(k1)] = c0;
+        if (k1 > 0) line[pidx(Px - k1)] = cm;
+      }
+    }
+    for (int idx = tid; idx < 2 * L * (2 * nx + 1); idx += nthr) {
+      const int l = idx / (2 * nx + 1), k = nx + idx - l * (2 * nx + 1);
+      buf[(size_t)l * ls + pidx(k)] = czero<float>();
+    }
+    __syncthreads();
+  }
+  const int lr = warp >> 1, h = warp & 1;
+  float2* line = buf + (size_t)lr * ls;
+  OwnParityG<float> fwd;
+  fwd.eh = xcos ? eh_c : eh_s;
+  fwd.P = Px;
+  fwd.L = L;
+  fft_warp2<float, false, LPX>(line, h, lane, tw, p.twlog, 1 + lr, lr, fwd);
+  pair_sync(1 + lr);
+  KhatBPerm<LNX> kb;
+  kb.kh = kh_sm;
+  kb.j0 = j0;
+  kb.Py = Py;
+  kb.L = L;
+  fft_warp2<float, true, LPX>(line, h, lane, tw, p.twlog, 1 + lr, lr, kb);
+  pair_sync(1 + lr);
+  if (h == 0) fft_warp<float, true, 32, 32>(line, Px / 2, LPX - 1, lane, true, tw, p.twlog);
+  __syncthreads();
+  float2* dst = W + (size_t)(d * 3 + f) * (nx + 1) * Py;
+  const int sh = p.twlog - LPX;
+  for (int idx = tid; idx < L * (nx + 1); idx += nthr) {
+    const int q = idx >> 1, l = idx & 1;
+    const int j = j0 + l;
+    if (j >= Py) continue;
+    const float2 z0 = buf[(size_t)l * ls + pidx(q)];
+    const float2 z1 = buf[(size_t)(L + l) * ls + pidx(q)];
+    dst[(size_t)q * Py + j] = cadd<float>(z0, cmul<float>(z1, twid<float, true>(tw, q << sh)));
+  }
+}
+
+// pass C: grid (ceil((nx+1) / 4) row groups, 3 fields, ndir); four rows per
+// block, the inverse torus transform of a row (2048 points) on a warp pair,
+// then its projection (1024 points) on the pair's first warp
+template <int LNY>
+__global__ void __launch_bounds__(LINES_THREADS, 2)
+    k_tbcC_w2(const float2* __restrict__ W, float2* __restrict__ Z, TbcP p,
+              const float2* __restrict__ tw) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  float2* buf = (float2*)sm_raw;
+  constexpr int LPY = LNY + 2, Py = 1 << LPY, ny = 1 << LNY, ls = W2<Py>::LS;
+  constexpr int RB = 4;   // rows per block
+  const int f = blockIdx.y, d = blockIdx.z;
+  const int r0 = blockIdx.x * RB;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int l = warp >> 1, h = warp & 1;
+  const bool ycos = (f != 0);
+  RowC<float, LNY> rc;
+  rc.src = W + (size_t)(d * 3 + f) * (p.nx + 1) * Py;
+  rc.r0 = r0;
+  rc.nx = p.nx;
+  rc.ycos = ycos;
+  float2* line = buf + (size_t)l * ls;
+  fft_warp2<float, true, LPY>(line, h, lane, tw, p.twlog, 1 + l, l, rc);
+  pair_sync(1 + l);
+  if (h == 0) {
+    StoreZ<float, LNY> sz;
+    sz.Z = Z + (size_t)(d * 3 + f) * (p.nx + 1) * (ny + 1);
+    sz.r0 = r0;
+    sz.nx = p.nx;
+    sz.ycos = ycos;
+    sz.w = (float)p.wy;
+    fft_warp<float, false, 32, 32>(line, 2 * ny, LNY + 1, lane, true, tw, p.twlog, l, sz);
+  }
+}
+
+template <typename T> __host__ __device__ constexpr bool w2_ok(int ln) {
+  return sizeof(T) == 4 && ln == 9;
+}
+static size_t smem_b_w2(int nx) {
+  return sizeof(float2) * (4 * (size_t)padded_len(4 * nx) + 2 * (size_t)(2 * nx + 16));
+}
+static size_t smem_c_w2(int ny) { return sizeof(float2) * 4 * (size_t)padded_len(4 * ny); }
+
 // ------------------------------------------------------------------ combine
 // y = local part of (EJ1)/(uT1) + TBC rows, with the TBC sign that makes T
 // the exterior admittance z x curl E^s of (EGa2):
@@ -643,21 +819,41 @@ cavity_status launch_apply(cavity_ctx* ctx, int ndir, const C<T>* x, C<T>* y, vo
   CKS(dispatch_log<CAV_LOG_MIN, CAV_LOG_MAX>(g.lnx, [&](auto c) -> cavity_status {
     constexpr int LN = decltype(c)::value;
     constexpr int L = pairs_per_cta<T>(4 << LN);
-    static std::atomic<bool> done{false};  // set once; host threads may race
-    CKS(smem_once(ctx, k_tbcB<T, LN>, done));
-    KScope ks_(ctx, kclass<T>(1));
-    k_tbcB<T, LN><<<dim3((g.Py + L - 1) / L, 3, ndir), T_, smem_b<T>(g.nx), st>>>(
-        R1, R2, p, tw, Tabs<T>::ex(ctx, 0), Tabs<T>::ex(ctx, 1), Tabs<T>::kh(ctx));
-    return CAVITY_OK;
+    if constexpr (w2_ok<T>(LN)) {
+      static std::atomic<bool> done2{false};
+      CKS(smem_once(ctx, k_tbcB_w2<LN>, done2));
+      KScope ks_(ctx, kclass<T>(1));
+      k_tbcB_w2<LN><<<dim3(g.Py / 2, 3, ndir), T_, smem_b_w2(g.nx), st>>>(
+          (const float2*)R1, (float2*)R2, p, (const float2*)tw, (const float2*)Tabs<T>::ex(ctx, 0),
+          (const float2*)Tabs<T>::ex(ctx, 1), (const float2*)Tabs<T>::kh(ctx));
+      return CAVITY_OK;
+    } else {
+      static std::atomic<bool> done{false};  // set once; host threads may race
+      CKS(smem_once(ctx, k_tbcB<T, LN>, done));
+      KScope ks_(ctx, kclass<T>(1));
+      k_tbcB<T, LN><<<dim3((g.Py + L - 1) / L, 3, ndir), T_, smem_b<T>(g.nx), st>>>(
+          R1, R2, p, tw, Tabs<T>::ex(ctx, 0), Tabs<T>::ex(ctx, 1), Tabs<T>::kh(ctx));
+      return CAVITY_OK;
+    }
   }));
   CKS(dispatch_log<CAV_LOG_MIN, CAV_LOG_MAX>(g.lny, [&](auto c) -> cavity_status {
     constexpr int LN = decltype(c)::value;
     constexpr int L = lines_per_cta<T>(4 << LN);
-    static std::atomic<bool> done{false};  // set once; host threads may race
-    CKS(smem_once(ctx, k_tbcC<T, LN>, done));
-    KScope ks_(ctx, kclass<T>(2));
-    k_tbcC<T, LN><<<dim3((g.nx + 1 + L - 1) / L, 3, ndir), T_, smem_c<T>(g.ny), st>>>(R2, R1, p, tw);
-    return CAVITY_OK;
+    if constexpr (w2_ok<T>(LN)) {
+      static std::atomic<bool> done2{false};
+      CKS(smem_once(ctx, k_tbcC_w2<LN>, done2));
+      KScope ks_(ctx, kclass<T>(2));
+      k_tbcC_w2<LN><<<dim3((g.nx + 1 + 3) / 4, 3, ndir), T_, smem_c_w2(g.ny), st>>>(
+          (const float2*)R2, (float2*)R1, p, (const float2*)tw);
+      return CAVITY_OK;
+    } else {
+      static std::atomic<bool> done{false};  // set once; host threads may race
+      CKS(smem_once(ctx, k_tbcC<T, LN>, done));
+      KScope ks_(ctx, kclass<T>(2));
+      k_tbcC<T, LN><<<dim3((g.nx + 1 + L - 1) / L, 3, ndir), T_, smem_c<T>(g.ny), st>>>(R2, R1, p,
+                                                                                       tw);
+      return CAVITY_OK;
+    }
   }));
   CKS(dispatch_log<CAV_LOG_MIN, CAV_LOG_MAX>(g.lnx, [&](auto c) -> cavity_status {
     constexpr int LN = decltype(c)::value;
