@@ -11,11 +11,16 @@
 // 13-14 per-direction steps to 1e-5).
 //
 // Orthogonalisation of the new block W against the basis V: one classical
-// Gram-Schmidt pass as two GEMM-shaped kernels on the tensor pipe (warp-level
-// mma.sync, TF32 operands split into three products for FP32 accuracy):
-// V^H W by a split reduction over the rows (k_bproj_tc, then k_bproj_final in
-// a fixed order) and W -= V H (k_bnn_tc).  The Gram matrix of the projected
-// block is then formed (k_bproj_tc with W against itself) and the block is
+// Gram-Schmidt pass as two GEMM-shaped tensor-core kernels, TF32 operands
+// split into three products for FP32 accuracy.  W -= V H (k_bnn_tc5) runs on
+// the fifth-generation tensor cores (tcgen05.mma kind::tf32, accumulators in
+// tensor memory; tc05.cuh).  V^H W is a split reduction over the rows
+// (k_bproj_tc, then k_bproj_final in a fixed order) on warp-level mma.sync: a
+// tcgen05 version measured 2x slower, its threads having to split and place
+// every element in the core-matrix layout of the reduction dimension, where
+// the mma.sync version splits fragments in registers from tiles staged by
+// cp.async.  The Gram matrix of the projected block is then formed
+// (k_bproj_tc with W against itself) and the block is
 // orthonormalised by Cholesky QR, or by SVQB (Stathopoulos and Wu, 2002:
 // W = V' S with V' = W U Lambda^{-1/2} from G = W^H W = U Lambda U^H,
 // eigenvalues below a floor raised to it) when it is nearly dependent
@@ -38,6 +43,7 @@
 
 #include "bgmres_host.h"
 #include "common.cuh"
+#include "tc05.cuh"
 
 #define BG_GROUPS 32      // groups per call (BG_GROUPS * BG_MAX directions)
 #define BG_PART_CTAS 608  // bound on groups x row chunks of one projection
@@ -45,8 +51,8 @@
 struct BGrp {
   const float2* V;  // Kv basis columns, stride nap
   const float2* W;  // r block columns, stride nap
-  float2* O;        // output columns, stride nap (k_bnn_tc)
-  int Kv;           // columns taken from V (k_bnn_tc multiplies these)
+  float2* O;        // output columns, stride nap (k_bnn_tc5)
+  int Kv;           // columns taken from V (k_bnn_tc5 multiplies these)
   int K;            // projected columns (k_bproj_tc): V_0..V_{Kv-1}, then W_0..W_{K-Kv-1}
   int r;
   int coff;         // offset of this group's coefficient matrix (BG_MAX wide)
@@ -97,14 +103,158 @@ __global__ void __launch_bounds__(256) k_bproj_final(BGSet set, const double2* _
   }
 }
 
-// O_j[e] = beta O_j[e] + sgn sum_{i<Kv} V_i[e] C[i][j] for j < r (C: the group's
-// coefficient matrix at cmat + coff, FP64, BG_MAX wide), on the tensor pipe
-// (warp-level mma.sync m16n8k8 with TF32 operands, FP32 accumulation).  The
+// Block update: O_j[e] = beta O_j[e] + sgn sum_{i<Kv} V_i[e] C[i][j] for j < r
+// (C: the group's coefficient matrix at cmat + coff, FP64, BG_MAX wide).  The
 // complex product is a real GEMM,
 //   [Re O_j, Im O_j] = sum_i [Re V_i, Im V_i] [[Re C_ij, Im C_ij], [-Im C_ij, Re C_ij]],
-// of n_ap rows, 2 Kv inner terms and 32 outputs.  FP32 accuracy comes from the
-// three-product split of each operand into TF32 parts, x = hi + lo:
-// x y ~ hi_x hi_y + hi_x lo_y + lo_x hi_y (the dropped lo lo term is below 2^-22 |x y|).
+// of n_ap rows, 2 Kv inner terms and 32 outputs.
+// It runs on the fifth-generation tensor cores (tcgen05.mma
+// kind::tf32, accumulator in tensor memory; layouts and the TF32 split in
+// tc05.cuh): grid (ceil(nap / 128), 1, groups), 128 threads (one warpgroup),
+// the block's 128 rows x 32 real outputs in 32 columns of tensor memory.
+// Chunks of T5_CH = 8 complex basis columns (16 real inner terms, two MMA
+// k-steps, three products each) pass through two shared-memory buffers: the
+// threads stage chunk c + 1 while the tensor cores multiply chunk c.  The
+// products hi hi and the two corrections go to separate accumulators (32
+// columns each), drained into FP32 registers every TC_DRAIN chunks (see
+// tc05.cuh).  Thread
+// t stages row row0 + t of V (eight 8-byte loads, one per column, a warp's
+// 32 rows contiguous) and one complex coefficient (u, j) = (t / 16, t % 16)
+// as its 2 x 2 real block.  A wait that runs out sets *err and skips the
+// output.
+#define T5_CH 8
+struct T5Buf {
+  float a_hi[2][128 * 8], a_lo[2][128 * 8];  // [k-step][K-major tile]
+  float b_hi[2][32 * 8], b_lo[2][32 * 8];
+};
+__device__ int g_tc_err;  // set when a tensor-core wait ran out
+
+__global__ void __launch_bounds__(128) k_bnn_tc5(BGSet set, const double2* __restrict__ cmat,
+                                                 int nap, float beta, float sgn) {
+  extern __shared__ __align__(128) unsigned char t5raw[];
+  T5Buf* bufs = (T5Buf*)t5raw;
+  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ uint32_t tslot;
+  const BGrp& gd = set.g[blockIdx.z];
+  const double2* Cm = cmat + gd.coff;
+  const int Kv = gd.Kv, r = gd.r;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int row0 = blockIdx.x * 128, e = row0 + tid;
+  const int nch = (Kv + T5_CH - 1) / T5_CH;
+  if (nch == 0) {  // uniform over the block: O = beta O
+    if (e < nap)
+      for (int j = 0; j < r; ++j) {
+        float2* o = gd.O + (size_t)j * nap + e;
+        const float2 ov = beta != 0.f ? *o : make_float2(0.f, 0.f);
+        *o = make_float2(beta * ov.x, beta * ov.y);
+      }
+    return;
+  }
+  if (tid == 0) {
+    tc_mbar_init(&mbar[0]);
+    tc_mbar_init(&mbar[1]);
+  }
+  if (warp == 0) tc_alloc(&tslot, 64);
+  tc_before_sync();
+  __syncthreads();
+  tc_after_sync();
+  const uint32_t tmem = tslot;
+  constexpr uint32_t idesc = tc_idesc_tf32(128, 32);
+  bool ok = true;
+  float racc[32];
+#pragma unroll
+  for (int n = 0; n < 32; ++n) racc[n] = 0.f;
+  float2 v[T5_CH];
+  double2 cnext;
+  auto load_chunk = [&](int cn) {
+#pragma unroll
+    for (int u = 0; u < T5_CH; ++u) {
+      const int i = cn * T5_CH + u;
+      v[u] = (i < Kv && e < nap) ? gd.V[(size_t)i * nap + e] : make_float2(0.f, 0.f);
+    }
+    const int iu = cn * T5_CH + (tid >> 4), j = tid & 15;
+    cnext = (iu < Kv && j < r) ? Cm[(size_t)iu * BG_MAX + j] : make_double2(0.0, 0.0);
+  };
+  load_chunk(0);
+  for (int c = 0; c < nch && ok; ++c) {
+    const int b = c & 1;
+    T5Buf& B = bufs[b];
+    // the MMAs of chunk c - 2 read this buffer
+    if (c >= 2) ok = tc_mbar_wait(&mbar[b], ((c - 2) >> 1) & 1);
+    ok = __syncthreads_and(ok);
+    if (!ok) break;
+    // A: row tid, complex columns i = c T5_CH + u -> real inner terms 2u, 2u + 1
+    // (values loaded one iteration ahead)
+#pragma unroll
+    for (int u = 0; u < T5_CH; ++u) {
+      uint32_t hr, lr, hi, li;
+      tc_split(v[u].x, hr, lr);
+      tc_split(v[u].y, hi, li);
+      const int ks = u >> 2, k8 = (2 * u) & 7, off = tc_koff(tid, k8);
+      *(uint2*)((char*)B.a_hi[ks] + off) = make_uint2(hr, hi);
+      *(uint2*)((char*)B.a_lo[ks] + off) = make_uint2(lr, li);
+    }
+    // B (N x K, K-major): real rows n = 2j + c' against inner terms k = 2u + c
+    {
+      const int u = tid >> 4, j = tid & 15;
+      const double2 cc = cnext;
+      if (c + 1 < nch) load_chunk(c + 1);   // in flight during the barrier and the MMAs
+      const float cr = (float)(sgn * cc.x), ci = (float)(sgn * cc.y);
+      const int ks = u >> 2, k8 = (2 * u) & 7;
+      uint32_t h0, l0, h1, l1, h2, l2;
+      tc_split(cr, h0, l0);
+      tc_split(ci, h1, l1);
+      tc_split(-ci, h2, l2);
+      // (n = 2j: k = 2u -> cr, k = 2u + 1 -> -ci), (n = 2j + 1: ci, cr)
+      *(uint2*)((char*)B.b_hi[ks] + tc_koff(2 * j, k8)) = make_uint2(h0, h2);
+      *(uint2*)((char*)B.b_lo[ks] + tc_koff(2 * j, k8)) = make_uint2(l0, l2);
+      *(uint2*)((char*)B.b_hi[ks] + tc_koff(2 * j + 1, k8)) = make_uint2(h1, h0);
+      *(uint2*)((char*)B.b_lo[ks] + tc_koff(2 * j + 1, k8)) = make_uint2(l1, l0);
+    }
+    tc_fence_smem();
+    tc_before_sync();
+    __syncthreads();
+    tc_after_sync();
+    if (tid == 0) {
+#pragma unroll
+      for (int ks = 0; ks < 2; ++ks) {
+        const uint64_t ah = tc_desc(B.a_hi[ks]), al = tc_desc(B.a_lo[ks]);
+        const uint64_t bh = tc_desc(B.b_hi[ks]), bl = tc_desc(B.b_lo[ks]);
+        const uint32_t acc = (c % TC_DRAIN != 0 || ks > 0) ? 1u : 0u;
+        tc_mma(tmem, ah, bh, idesc, acc);         // hi hi
+        tc_mma(tmem + 32, al, bh, idesc, acc);    // the corrections apart
+        tc_mma(tmem + 32, ah, bl, idesc, 1u);
+      }
+      tc_commit(&mbar[b]);
+    }
+    if (c % TC_DRAIN == TC_DRAIN - 1 || c == nch - 1) {
+      ok = __syncthreads_and(tc_mbar_wait(&mbar[b], (c >> 1) & 1));
+      tc_after_sync();
+      if (ok) tc_drain(tmem + ((uint32_t)(32 * warp) << 16), racc);
+      tc_before_sync();
+      __syncthreads();
+    }
+  }
+  // every MMA done: the last chunk was drained
+  if (ok) {
+    const float* d = racc;
+    if (e < nap) {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        if (j >= r) break;
+        float2* o = gd.O + (size_t)j * nap + e;
+        const float2 ov = beta != 0.f ? *o : make_float2(0.f, 0.f);
+        *o = make_float2(beta * ov.x + d[2 * j], beta * ov.y + d[2 * j + 1]);
+      }
+    }
+  } else if (tid == 0) {
+    atomicExch(&g_tc_err, 1);
+  }
+  tc_before_sync();
+  __syncthreads();
+  if (warp == 0) tc_dealloc(tmem, 64);
+}
+
 __device__ __forceinline__ unsigned tf32_of(float x) {
   unsigned r;
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
@@ -126,129 +276,13 @@ __device__ __forceinline__ void mma_tf32(float (&d)[4], const unsigned (&a)[4], 
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-#define TC_KC 16   // complex rows of C staged per chunk (32 real rows)
-#define TC_BLD 40  // row pitch (words) of the staged real C: the b-fragment loads hit distinct banks
-#define TC_AK 8    // complex basis columns per staged A tile (two k8 steps)
-#define TC_ALD 20  // row pitch (words) of the staged A tile: the a-fragment loads hit distinct banks
-
-// grid (ceil(nap / 128), 1, groups), 128 threads; warp w owns the rows
-// 128 x + 32 w .. + 31 (two m16 tiles) and all 32 real outputs (four n8 tiles).
-// The basis columns come through shared memory: tiles of 128 rows x 8 complex
-// columns (row-major real words, word 2 i + c = component c of column i),
-// copied by cp.async into two buffers, the next tile in flight while the
-// current one is multiplied.  30 KB of shared memory and at most 80 registers
-// a thread: six blocks per SM.
-__global__ void __launch_bounds__(128, 6) k_bnn_tc(BGSet set, const double2* __restrict__ cmat,
-                                                int nap, float beta, float sgn) {
-  __shared__ unsigned bhi[2 * TC_KC][TC_BLD], blo[2 * TC_KC][TC_BLD];
-  __shared__ __align__(16) float as[2][128 * TC_ALD];
-  const BGrp& gd = set.g[blockIdx.z];
-  const double2* Cm = cmat + gd.coff;
-  const int Kv = gd.Kv, r = gd.r;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int g = lane >> 2, t = lane & 3;
-  const int row0 = blockIdx.x * 128;
-  const int lrow = warp * 32;  // this warp's first row within the block
-  // staging: element u of thread tid is column i0 + u, row row0 + tid (a warp
-  // reads 256 contiguous bytes of one column; the 8-byte writes of a half-warp
-  // fall on 8 bank pairs at the 20-word pitch, 2-way, which measured faster
-  // than a conflict-free map that spreads a warp's reads over four columns)
-  auto stage_a = [&](int buf, int i0) {
-    const int e = row0 + tid;
-#pragma unroll
-    for (int u = 0; u < TC_AK; ++u) {
-      const int i = i0 + u;
-      const bool ok = e < nap && i < Kv;
-      cp_async8((float2*)(as[buf] + tid * TC_ALD + 2 * u), ok ? gd.V + (size_t)i * nap + e : gd.V, ok);
-    }
-    cp_async_commit();
-  };
-  float acc[2][4][4];
-#pragma unroll
-  for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-    for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) acc[mt][nt][q] = 0.f;
-  const int ntile = (Kv + TC_AK - 1) / TC_AK;
-  if (ntile > 0) stage_a(0, 0);
-  if (ntile > 1) stage_a(1, TC_AK);
-  for (int it = 0; it < ntile; ++it) {
-    const int ia = it * TC_AK;  // first complex column of this A tile
-    if (ia % TC_KC == 0) {
-      // next chunk of C: all threads are past the previous chunk's reads
-      __syncthreads();
-      for (int u = tid; u < TC_KC * 16; u += 128) {
-        const int ii = u >> 4, j = u & 15;
-        double2 c = make_double2(0.0, 0.0);
-        if (ia + ii < Kv && j < r) c = Cm[(size_t)(ia + ii) * BG_MAX + j];
-        const float cr = (float)(sgn * c.x), ci = (float)(sgn * c.y);
-        tf32_split(cr, bhi[2 * ii][2 * j], blo[2 * ii][2 * j]);
-        tf32_split(ci, bhi[2 * ii][2 * j + 1], blo[2 * ii][2 * j + 1]);
-        tf32_split(-ci, bhi[2 * ii + 1][2 * j], blo[2 * ii + 1][2 * j]);
-        tf32_split(cr, bhi[2 * ii + 1][2 * j + 1], blo[2 * ii + 1][2 * j + 1]);
-      }
-    }
-    if (it + 1 < ntile) cp_async_wait<1>();
-    else cp_async_wait<0>();
-    __syncthreads();
-    const float* at = as[it & 1];
-    const int cb0 = 2 * (ia % TC_KC);  // first real row of C for this tile
-#pragma unroll
-    for (int ks = 0; ks < 2; ++ks) {
-      const int kb = 8 * ks;  // real inner index within the tile
-      unsigned ahi[2][4], alo[2][4];
-#pragma unroll
-      for (int mt = 0; mt < 2; ++mt) {
-        const int rr = lrow + mt * 16 + g;
-        tf32_split(at[rr * TC_ALD + kb + t], ahi[mt][0], alo[mt][0]);
-        tf32_split(at[(rr + 8) * TC_ALD + kb + t], ahi[mt][1], alo[mt][1]);
-        tf32_split(at[rr * TC_ALD + kb + t + 4], ahi[mt][2], alo[mt][2]);
-        tf32_split(at[(rr + 8) * TC_ALD + kb + t + 4], ahi[mt][3], alo[mt][3]);
-      }
-      const int kr = cb0 + kb + t;
-#pragma unroll
-      for (int nt = 0; nt < 4; ++nt) {
-        const int n = nt * 8 + g;
-        const unsigned bh0 = bhi[kr][n], bh1 = bhi[kr + 4][n];
-        const unsigned bl0 = blo[kr][n], bl1 = blo[kr + 4][n];
-#pragma unroll
-        for (int mt = 0; mt < 2; ++mt) {
-          mma_tf32(acc[mt][nt], alo[mt], bh0, bh1);
-          mma_tf32(acc[mt][nt], ahi[mt], bl0, bl1);
-          mma_tf32(acc[mt][nt], ahi[mt], bh0, bh1);
-        }
-      }
-    }
-    __syncthreads();
-    if (it + 2 < ntile) stage_a(it & 1, (it + 2) * TC_AK);
-  }
-  // d0, d1: (row g, complex output 4 nt + t); d2, d3: row g + 8
-#pragma unroll
-  for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-    for (int nt = 0; nt < 4; ++nt) {
-      const int j = 4 * nt + t;
-      if (j >= r) continue;
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int row = row0 + lrow + mt * 16 + g + 8 * h;
-        if (row >= nap) continue;
-        float2* o = gd.O + (size_t)j * nap + row;
-        float2 ov = make_float2(0.f, 0.f);
-        if (beta != 0.f) ov = *o;
-        *o = make_float2(beta * ov.x + acc[mt][nt][2 * h], beta * ov.y + acc[mt][nt][2 * h + 1]);
-      }
-    }
-}
-
 // Partial projections: part[z][x][i][j] = sum over the rows e of slab x of
 // conj(X_i[e]) W_j[e] for group z, i < K, j < r, where X_i is basis column i
 // for i < Kv and block column i - Kv after that, on the tensor pipe.
 // With real columns m = 2 i + c of V (component c of column i) and n = 2 j + c'
 // of W, the real product P = Vr^T Wr over the rows of a slab gives
 //   Re H_ij = P(2i, 2j) + P(2i+1, 2j+1),   Im H_ij = P(2i, 2j+1) - P(2i+1, 2j)
-// (H = V^H W), with the same three-product TF32 split as k_bnn_tc.  grid (nslab,
+// (H = V^H W), with the three-product TF32 split.  grid (nslab,
 // ceil(K / 16), groups), 128 threads: the block owns 16 complex V columns (32
 // real rows of P, two m16 tiles) against all 16 W columns (32 real, four n8
 // tiles) over its slab, walked in 64-row tiles staged by cp.async into two
@@ -474,7 +508,8 @@ static cavity_status bnn(cavity_ctx* ctx, const BGSet& set, int ng, const double
                          float sgn) {
   const int nap = ctx->g.nap;
   KScope ks_(ctx, KC_KRYLOV);
-  k_bnn_tc<<<dim3(bg_blocks(nap, 128), 1, ng), 128, 0, ctx->stream>>>(set, cmat, nap, beta, sgn);
+  k_bnn_tc5<<<dim3(bg_blocks(nap, 128), 1, ng), 128, 2 * sizeof(T5Buf), ctx->stream>>>(
+      set, cmat, nap, beta, sgn);
   return CAVITY_OK;
 }
 
@@ -816,5 +851,14 @@ cavity_status run_block_inner(cavity_ctx* ctx, int ndir, const float2* r, float2
     }
   }
   CK(cudaGetLastError());
+  {
+    int terr = 0;
+    CK(cudaMemcpyFromSymbolAsync(&terr, g_tc_err, sizeof(int), 0, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (terr) {
+      ctx->err = "block Krylov update: a tensor-core completion wait ran out";
+      return CAVITY_ETIMEOUT;
+    }
+  }
   return CAVITY_OK;
 }

@@ -111,7 +111,7 @@ static bool cholqr(const std::vector<cd>& G, int n, std::vector<cd>& T, std::vec
 }
 
 // One SVQB step on the Gram matrix G (n x n): T = U Lambda_c^{-1/2} (the
-// transform of the block, stored BG_MAX wide as the k_bnn_tc coefficient matrix),
+// transform of the block, stored BG_MAX wide as the k_bnn_tc5 coefficient matrix),
 // S = Lambda_c^{1/2} U^H (W = (W T) S); Lambda_c = max(Lambda, floor).
 // Returns the deviation of G from the identity (max |G - I|); ratio receives
 // min(Lambda) / max(Lambda).
