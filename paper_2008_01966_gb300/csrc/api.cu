@@ -89,7 +89,7 @@ extern "C" void cavity_destroy(cavity_ctx* ctx) {
                   ctx->ehat_y32[1], ctx->khat64, ctx->khat32, ctx->khat_raw, ctx->prof, ctx->profq,
                   ctx->top64, ctx->top32, ctx->pinv64, ctx->pinv32, ctx->prof32, ctx->profq32,
                   ctx->minpiv, ctx->ws, ctx->ws2, ctx->stage, ctx->tw_p, ctx->ehat_xp[0],
-                  ctx->ehat_xp[1], ctx->ehat_yp[0], ctx->ehat_yp[1], ctx->khat_p, ctx->top_p};
+                  ctx->ehat_xp[1], ctx->ehat_yp[0], ctx->ehat_yp[1], ctx->khat_p, ctx->top_p, ctx->prof_rec};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (ctx->pin) cudaFreeHost(ctx->pin);

@@ -130,6 +130,12 @@ struct cavity_ctx {
   float2* pinv32 = nullptr;
   float2* prof32 = nullptr;    // FP32 copies of the profiles for the mixed field path
   float2* profq32 = nullptr;
+  // FP32 profiles of the fused field kernel as one record per (level, m, n)
+  // on the full nx x ny mode grid: {P1, P2}, {P3, Q1}, {Q2, 0} (layered, 3
+  // float4) or {P1, P2}, {P3, 0} (homogeneous, 2 float4); entries outside a
+  // component's index set are 0 (field_fused.cu)
+  float4* prof_rec = nullptr;
+  int prof_rec_w = 0;
   double* minpiv = nullptr;    // device scalar: min |pivot| / scale
 
   // ---- workspaces (grown on demand)
@@ -304,6 +310,11 @@ cavity_status launch_mode_mask(cavity_ctx* ctx, int ndir, double2* v);
 template <typename T>
 cavity_status launch_field(cavity_ctx* ctx, int ndir, const double2* ap, C<T>* out,
                            void* host_out = nullptr);
+// the fused field kernel (field_fused.cu): the grids it covers, and the
+// per-(level, m, n) FP32 profile records it reads, built from the FP64
+// profiles at prepare
+bool field_fused_supported(const Geo& g);
+cavity_status launch_prof_records(cavity_ctx* ctx);
 // the copy stream and at least n events for it (created once per context)
 inline cavity_status ensure_copy_stream(cavity_ctx* ctx, size_t n) {
   if (!ctx->copy_stream) {

@@ -249,22 +249,20 @@ __global__ void k_ap32(const double2* __restrict__ a, float2* __restrict__ b, lo
 // the persistent single-kernel synthesis of field_fused.cu (complex64 field)
 bool field_fused_supported(const Geo& g);
 size_t field_fused_work_bytes(const Geo& g);
-cavity_status launch_field_fused(cavity_ctx* ctx, int ndir, const float2* apT, float2* out,
+cavity_status launch_field_fused(cavity_ctx* ctx, int ndir, const float4* apr, float2* out,
                                  int j0, int nlev, void* work);
+size_t ap_records_bytes(const Geo& g, int ndir);
+cavity_status launch_ap_records(cavity_ctx* ctx, int ndir, const double2* ap, float4* rec);
 cavity_status field_fused_check(cavity_ctx* ctx, void* work);
 
 static cavity_status launch_field_fused_all(cavity_ctx* ctx, int ndir, const double2* ap,
                                             float2* out, void* host_out) {
   const Geo& g = ctx->g;
-  const size_t apb = ((sizeof(float2) * (size_t)ndir * g.nap + 255) / 256) * 256;
+  const size_t apb = ((ap_records_bytes(g, ndir) + 255) / 256) * 256;
   CKS(ensure_ws(ctx, &ctx->ws2, &ctx->ws2_bytes, apb + field_fused_work_bytes(g)));
-  float2* a32 = (float2*)ctx->ws2;
+  float4* apr = (float4*)ctx->ws2;
   void* work = (char*)ctx->ws2 + apb;
-  {
-    const long long n = (long long)ndir * g.nap;
-    KScope ks_(ctx, KC_FIELD_Y);
-    k_ap32<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(ap, a32, n);
-  }
+  CKS(launch_ap_records(ctx, ndir, ap, apr));
   // device output: one launch over all levels; host output: chunks of levels,
   // each copied out (one segment per direction, over four copy streams)
   // while the next is synthesised
@@ -274,7 +272,7 @@ static cavity_status launch_field_fused_all(cavity_ctx* ctx, int ndir, const dou
   int chunk = 0;
   for (int j0 = 1; j0 <= g.nz; j0 += lc, ++chunk) {
     const int nl = std::min(lc, g.nz - j0 + 1);
-    CKS(launch_field_fused(ctx, ndir, a32, out, j0, nl, work));
+    CKS(launch_field_fused(ctx, ndir, apr, out, j0, nl, work));
     if (host_out) {
       cudaEvent_t ev = ctx->copy_evs[2 + chunk];
       CK(cudaEventRecord(ev, ctx->stream));

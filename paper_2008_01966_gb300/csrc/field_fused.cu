@@ -64,6 +64,7 @@ constexpr long long SPIN_LIMIT = 1ll << 24;  // ~ seconds with the backoff below
 
 struct FFP {
   int nx, ny, nz, M, N, n1, n2, nap;
+  int recw;                  // float4 per profile record: 2 (homogeneous), 3 (layered)
   int ndir, j0, nslab;       // slabs s = (j - j0) * ndir + d
   int nR, nC, R, Cq;         // items per slab, rows / columns per item
   int lag, twlog;
@@ -90,17 +91,11 @@ __device__ __forceinline__ int ld_acquire(const int* p) {
   asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
-// L2 policies: keep T1 and the aperture vectors, stream the field out
+// L2 policies: keep T1, stream the field out
 __device__ __forceinline__ unsigned long long pol_last() {
   unsigned long long p;
   asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
   return p;
-}
-__device__ __forceinline__ float2 ld_keep(const float2* a, unsigned long long pol) {
-  float2 v;
-  asm("ld.global.nc.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;"
-      : "=f"(v.x), "=f"(v.y) : "l"(a), "l"(pol));
-  return v;
 }
 // T1 is rewritten by other blocks between uses of a ring buffer: read it
 // from L2 (never from a possibly stale L1 line)
@@ -192,9 +187,9 @@ struct FFShape {
 
 template <int LNX, int LNY>
 __global__ void __launch_bounds__(FF_THREADS, 1)
-    k_field_fused(const float2* __restrict__ ap, const float2* __restrict__ prof,
-                  const float2* __restrict__ profq, float2* __restrict__ T1,
-                  float2* __restrict__ out, FFCtl* ctl, FFP p, const float2* __restrict__ tw) {
+    k_field_fused(const float4* __restrict__ apr, const float4* __restrict__ prec,
+                  float2* __restrict__ T1, float2* __restrict__ out, FFCtl* ctl, FFP p,
+                  const float2* __restrict__ tw) {
   using S = FFShape<LNX, LNY>;
   constexpr int nx = S::nx, ny = S::ny, R = S::R, Cq = S::Cq;
   extern __shared__ __align__(16) unsigned char sm_raw[];
@@ -251,65 +246,55 @@ __global__ void __launch_bounds__(FF_THREADS, 1)
       float2* t1 = T1 + (size_t)(m.slab % FF_RING) * p.t1slab;
       if (m.kind == KIND_ROW) {
         // lines 0..R-1: row m (E2 cos + E1 sin), lines R..2R-1: row m (E3 sin).
-        // Batches of U elements per thread: every load of a batch is issued
-        // (indices clamped, values masked) before the first is used.
+        // One record index per mode: the aperture record {E1, E2}, {E3, 0} and
+        // the profile record of level j (entries outside an index set are 0,
+        // so no masks); batches of U elements per thread, every load of a
+        // batch issued before the first is used.
         constexpr int n2 = 2 * ny, ls = S::LSY;
         constexpr int PER = R * ny / (FF_NL * 32);
         constexpr int U = PER < 4 ? PER : 4;
         static_assert(PER % U == 0 && PER * FF_NL * 32 == R * ny, "row items tile the loaders");
-        const float2* E = ap + (size_t)d * p.nap;
+        const float4* A = apr + (size_t)d * 2 * nx * ny;
         const bool top = (j == p.nz);
-        const float2* Pj = prof + (size_t)(top ? 0 : j - 1) * p.nap;
-        const float2* Qj = p.layered && !top ? profq + (size_t)(j - 1) * (p.n1 + p.n2) : nullptr;
-        const int N = p.N, M = p.M, n1 = p.n1, n12 = p.n1 + p.n2;
+        const bool lay = p.recw == 3;
+        const float4* Pj = prec + (size_t)(top ? 0 : j - 1) * p.recw * nx * ny;
+        const int M = p.M;
         const float2 z = make_float2(0.f, 0.f);
 #pragma unroll 1
         for (int k0 = 0; k0 < PER; k0 += U) {
-          float2 a1[U], a2[U], a3[U], p1[U], p2[U], p3[U], q1[U], q2[U];
-          int i1[U], i2[U], i3[U];
-          unsigned mask = 0;
+          float4 a01[U], a3[U], p01[U], p3q1[U], q2[U];
 #pragma unroll
           for (int u = 0; u < U; ++u) {
             const int e = lt + (k0 + u) * (FF_NL * 32);
             const int r = e >> LNY, n = e & (ny - 1);
-            const int mm = m.idx * R + r;
-            const bool in = mm <= M;
-            const bool h1 = in && n >= 1, h2 = in && mm >= 1, h3 = h1 && h2;
-            mask |= (h1 ? 1u : 0u) << (3 * u);
-            mask |= (h2 ? 2u : 0u) << (3 * u);
-            mask |= (h3 ? 4u : 0u) << (3 * u);
-            i1[u] = h1 ? mm * N + (n - 1) : 0;
-            i2[u] = h2 ? n1 + (mm - 1) * (N + 1) + n : 0;
-            i3[u] = h3 ? n12 + (mm - 1) * N + (n - 1) : 0;
-            a1[u] = ld_keep(E + i1[u], keep);
-            a2[u] = ld_keep(E + i2[u], keep);
-            a3[u] = ld_keep(E + i3[u], keep);
+            const int mm = min(m.idx * R + r, M);   // rows beyond M: any record, masked below
+            const int rec = mm * ny + n;
+            a01[u] = __ldg(A + 2 * rec);
+            a3[u] = __ldg(A + 2 * rec + 1);
             if (!top) {
-              p1[u] = Pj[i1[u]];
-              p2[u] = Pj[i2[u]];
-              p3[u] = Pj[i3[u]];
-              if (Qj) {
-                q1[u] = Qj[i1[u]];
-                q2[u] = Qj[i2[u]];
-              }
+              p01[u] = __ldg(Pj + (size_t)p.recw * rec);
+              p3q1[u] = __ldg(Pj + (size_t)p.recw * rec + 1);
+              if (lay) q2[u] = __ldg(Pj + (size_t)p.recw * rec + 2);
             }
           }
 #pragma unroll
           for (int u = 0; u < U; ++u) {
             const int e = lt + (k0 + u) * (FF_NL * 32);
             const int r = e >> LNY, n = e & (ny - 1);
-            const bool h1 = (mask >> (3 * u)) & 1u, h2 = (mask >> (3 * u)) & 2u,
-                       h3 = (mask >> (3 * u)) & 4u;
-            float2 e1 = h1 ? a1[u] : z, e2 = h2 ? a2[u] : z, e3 = h3 ? a3[u] : z;
+            const bool in = m.idx * R + r <= M;
+            float2 e1 = make_float2(a01[u].x, a01[u].y), e2 = make_float2(a01[u].z, a01[u].w);
+            float2 e3 = make_float2(a3[u].x, a3[u].y);
             if (!top) {
-              if (h1) e1 = cmul<float>(p1[u], e1);
-              if (h2) e2 = cmul<float>(p2[u], e2);
-              if (h3) e3 = cmul<float>(p3[u], e3);
-              if (Qj && h3) {
-                e1 = cadd<float>(e1, cmul<float>(q1[u], a3[u]));
-                e2 = cadd<float>(e2, cmul<float>(q2[u], a3[u]));
+              const float2 E3 = e3;
+              e1 = cmul<float>(make_float2(p01[u].x, p01[u].y), e1);
+              e2 = cmul<float>(make_float2(p01[u].z, p01[u].w), e2);
+              e3 = cmul<float>(make_float2(p3q1[u].x, p3q1[u].y), E3);
+              if (lay) {
+                e1 = cadd<float>(e1, cmul<float>(make_float2(p3q1[u].z, p3q1[u].w), E3));
+                e2 = cadd<float>(e2, cmul<float>(make_float2(q2[u].x, q2[u].y), E3));
               }
             }
+            if (!in) e1 = e2 = e3 = z;
             float2* lp = buf + (size_t)r * ls;
             float2* l3 = buf + (size_t)(R + r) * ls;
             if (n == 0) {
@@ -466,8 +451,8 @@ __global__ void __launch_bounds__(FF_THREADS, 1)
 }
 
 template <int LN>
-cavity_status run_fused(cavity_ctx* ctx, const float2* apT, const float2* prof,
-                        const float2* profq, float2* T1, FFCtl* ctl, float2* out, FFP p) {
+cavity_status run_fused(cavity_ctx* ctx, const float4* apr, const float4* prec, float2* T1,
+                        FFCtl* ctl, float2* out, FFP p) {
   using S = FFShape<LN, LN>;
   auto kern = k_field_fused<LN, LN>;
   static std::atomic<bool> done{false};  // set once; host threads may race
@@ -491,7 +476,7 @@ cavity_status run_fused(cavity_ctx* ctx, const float2* apT, const float2* prof,
   const long long grid = std::min<long long>((long long)sms * blocks_per_sm, p.total);
   {
     KScope ks_(ctx, KC_FIELD_X);
-    kern<<<(unsigned)grid, FF_THREADS, S::SMEM, ctx->stream>>>(apT, prof, profq, T1, out, ctl, p,
+    kern<<<(unsigned)grid, FF_THREADS, S::SMEM, ctx->stream>>>(apr, prec, T1, out, ctl, p,
                                                               ctx->tw32);
   }
   CK(cudaGetLastError());
@@ -510,27 +495,105 @@ size_t field_fused_work_bytes(const Geo& g) {
   return sizeof(float2) * (size_t)FF_RING * 3 * g.nx * (g.ny + 1) + 256;
 }
 
-// Levels j0 .. j0 + nlev - 1 of ndir directions; apT: FP32 aperture vectors,
-// work: field_fused_work_bytes (T1 ring, then the control words); ferr: a
-// device word or'ed with 1 when a wait ran out.
-cavity_status launch_field_fused(cavity_ctx* ctx, int ndir, const float2* apT, float2* out,
+// Levels j0 .. j0 + nlev - 1 of ndir directions; apr: the aperture records
+// (ap_records), work: field_fused_work_bytes (T1 ring, then the control words).
+cavity_status launch_field_fused(cavity_ctx* ctx, int ndir, const float4* apr, float2* out,
                                  int j0, int nlev, void* work) {
   const Geo& g = ctx->g;
+  if (!ctx->prof_rec) {
+    ctx->err = "field: profile records missing (not a mixed-precision context)";
+    return CAVITY_EINVAL;
+  }
   FFP p;
   p.nx = g.nx; p.ny = g.ny; p.nz = g.nz; p.M = g.M; p.N = g.N; p.n1 = g.n1; p.n2 = g.n2;
   p.nap = g.nap; p.ndir = ndir; p.j0 = j0; p.nslab = nlev * ndir;
+  p.recw = ctx->prof_rec_w;
   p.twlog = ilog2(ctx->TW);
   p.layered = ctx->layers.size() > 1;
   p.S = g.field_per_level;
   p.t1slab = 3ll * g.nx * (g.ny + 1);
   float2* T1 = (float2*)work;
   FFCtl* ctl = (FFCtl*)((char*)work + sizeof(float2) * (size_t)FF_RING * p.t1slab);
-  const float2* prof = ctx->prof32;
-  const float2* profq = p.layered ? ctx->profq32 : nullptr;
   return dispatch_log<5, 9>(g.lnx, [&](auto c) -> cavity_status {
     constexpr int LN = decltype(c)::value;
-    return run_fused<LN>(ctx, apT, prof, profq, T1, ctl, out, p);
+    return run_fused<LN>(ctx, apr, ctx->prof_rec, T1, ctl, out, p);
   });
+}
+
+// aperture records: {E1, E2}, {E3, 0} per direction and mode (m, n) of the
+// nx x ny mode grid, FP32, zero outside each component's index set
+__global__ void k_ap_records(const double2* __restrict__ ap, float4* __restrict__ rec, int nx,
+                             int ny, int N, int n1, int n2, int nap) {
+  const int mn = blockIdx.x * blockDim.x + threadIdx.x, d = blockIdx.y;
+  if (mn >= nx * ny) return;
+  const int m = mn / ny, n = mn - m * ny;
+  const double2* E = ap + (size_t)d * nap;
+  const double2 z = make_double2(0.0, 0.0);
+  const double2 e1 = n >= 1 ? E[m * N + (n - 1)] : z;
+  const double2 e2 = m >= 1 ? E[n1 + (m - 1) * (N + 1) + n] : z;
+  const double2 e3 = (m >= 1 && n >= 1) ? E[n1 + n2 + (m - 1) * N + (n - 1)] : z;
+  float4* o = rec + ((size_t)d * nx * ny + mn) * 2;
+  o[0] = make_float4((float)e1.x, (float)e1.y, (float)e2.x, (float)e2.y);
+  o[1] = make_float4((float)e3.x, (float)e3.y, 0.f, 0.f);
+}
+
+size_t ap_records_bytes(const Geo& g, int ndir) {
+  return sizeof(float4) * 2 * (size_t)ndir * g.nx * g.ny;
+}
+
+cavity_status launch_ap_records(cavity_ctx* ctx, int ndir, const double2* ap, float4* rec) {
+  const Geo& g = ctx->g;
+  KScope ks_(ctx, KC_FIELD_Y);
+  k_ap_records<<<dim3((g.nx * g.ny + 255) / 256, ndir), 256, 0, ctx->stream>>>(
+      ap, rec, g.nx, g.ny, g.N, g.n1, g.n2, g.nap);
+  CK(cudaGetLastError());
+  return CAVITY_OK;
+}
+
+// profile records of levels 1..nz-1 (see cavity_ctx::prof_rec)
+__global__ void k_prof_records(const double2* __restrict__ prof, const double2* __restrict__ profq,
+                               float4* __restrict__ rec, int nx, int ny, int N, int n1, int n2,
+                               int nap, int nlev, int w) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= (long long)nlev * nx * ny) return;
+  const int jl = (int)(t / (nx * ny)), mn = (int)(t - (long long)jl * nx * ny);
+  const int m = mn / ny, n = mn - m * ny;
+  const double2* P = prof + (size_t)jl * nap;
+  const double2 z = make_double2(0.0, 0.0);
+  const bool h1 = n >= 1, h2 = m >= 1, h3 = h1 && h2;
+  const int i1 = m * N + (n - 1), i2 = n1 + (m - 1) * (N + 1) + n, i3 = n1 + n2 + (m - 1) * N + (n - 1);
+  const double2 p1 = h1 ? P[i1] : z, p2 = h2 ? P[i2] : z, p3 = h3 ? P[i3] : z;
+  float4* o = rec + (size_t)t * w;
+  o[0] = make_float4((float)p1.x, (float)p1.y, (float)p2.x, (float)p2.y);
+  if (w == 3) {
+    const double2* Q = profq + (size_t)jl * (n1 + n2);
+    const double2 q1 = h3 ? Q[i1] : z, q2 = h3 ? Q[i2] : z;
+    o[1] = make_float4((float)p3.x, (float)p3.y, (float)q1.x, (float)q1.y);
+    o[2] = make_float4((float)q2.x, (float)q2.y, 0.f, 0.f);
+  } else {
+    o[1] = make_float4((float)p3.x, (float)p3.y, 0.f, 0.f);
+  }
+}
+
+cavity_status launch_prof_records(cavity_ctx* ctx) {
+  const Geo& g = ctx->g;
+  const bool layered = ctx->layers.size() > 1;
+  const int w = layered ? 3 : 2;
+  const long long n = (long long)(g.nz - 1) * g.nx * g.ny;
+  if (!ctx->prof_rec || ctx->prof_rec_w < w) {
+    if (ctx->prof_rec) cudaFree(ctx->prof_rec);
+    ctx->prof_rec = nullptr;
+    ctx->prof_rec_w = 0;
+    // size for the layered layout, so a later layered prepare reuses it
+    CK(cudaMalloc(&ctx->prof_rec, sizeof(float4) * 3 * (size_t)n));
+  }
+  ctx->prof_rec_w = w;
+  KScope ks_(ctx, KC_SETUP);
+  k_prof_records<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(
+      ctx->prof, layered ? ctx->profq : nullptr, ctx->prof_rec, g.nx, g.ny, g.N, g.n1, g.n2,
+      g.nap, g.nz - 1, w);
+  CK(cudaGetLastError());
+  return CAVITY_OK;
 }
 
 // the error word of the last fused launch (0: every wait ended in time)

@@ -194,14 +194,19 @@ cavity_status launch_zsweep(cavity_ctx* ctx, double kappa0) {
   }
   size_t nprof = (size_t)(g.nz - 1) * g.nap;
   size_t nq = (size_t)(g.nz - 1) * (g.n1 + g.n2);
+  // FP32 copies of the profiles for the complex64 field of mixed contexts:
+  // records for the fused kernel where it runs, else plain copies
+  const bool mixed = ctx->desc.precision == CAVITY_MIXED;
+  const bool recs = mixed && field_fused_supported(g);
+  const bool plain32 = mixed && !recs;
   if (!ctx->prof) CK(cudaMalloc(&ctx->prof, sizeof(double2) * nprof));
-  if (!ctx->prof32) CK(cudaMalloc(&ctx->prof32, sizeof(float2) * nprof));
+  if (plain32 && !ctx->prof32) CK(cudaMalloc(&ctx->prof32, sizeof(float2) * nprof));
   if (!ctx->top64) CK(cudaMalloc(&ctx->top64, sizeof(double2) * (g.nap + g.n1 + g.n2)));
   if (!ctx->top32) CK(cudaMalloc(&ctx->top32, sizeof(float2) * (g.nap + g.n1 + g.n2)));
   if (!ctx->minpiv) CK(cudaMalloc(&ctx->minpiv, sizeof(double)));
   const bool layered = L.nl > 1;
   if (layered && !ctx->profq) CK(cudaMalloc(&ctx->profq, sizeof(double2) * nq));
-  if (layered && !ctx->profq32) CK(cudaMalloc(&ctx->profq32, sizeof(float2) * nq));
+  if (plain32 && layered && !ctx->profq32) CK(cudaMalloc(&ctx->profq32, sizeof(float2) * nq));
   double big = 1e300;
   CK(cudaMemcpyAsync(ctx->minpiv, &big, sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
   CK(cudaMemsetAsync(ctx->top64, 0, sizeof(double2) * (g.nap + g.n1 + g.n2), ctx->stream));
@@ -224,22 +229,22 @@ cavity_status launch_zsweep(cavity_ctx* ctx, double kappa0) {
     }
   }
   CK(cudaGetLastError());
-  {
+  if (plain32) {
     KScope ks_(ctx, KC_SETUP);
     k_f32_copy<<<(unsigned)((nprof + 255) / 256), 256, 0, ctx->stream>>>(ctx->prof, ctx->prof32,
                                                                        (long long)nprof);
   }
+  if (recs) CKS(launch_prof_records(ctx));
   long long ntop = g.nap + g.n1 + g.n2;
   {
     KScope ks_(ctx, KC_SETUP);
     k_f32_copy<<<(unsigned)((ntop + 255) / 256), 256, 0, ctx->stream>>>(ctx->top64, ctx->top32, ntop);
   }
-  if (layered)
-    {
-      KScope ks_(ctx, KC_SETUP);
-      k_f32_copy<<<(unsigned)((nq + 255) / 256), 256, 0, ctx->stream>>>(ctx->profq, ctx->profq32,
-                                                                      (long long)nq);
-    }
+  if (plain32 && layered) {
+    KScope ks_(ctx, KC_SETUP);
+    k_f32_copy<<<(unsigned)((nq + 255) / 256), 256, 0, ctx->stream>>>(ctx->profq, ctx->profq32,
+                                                                    (long long)nq);
+  }
   CK(cudaGetLastError());
   double worst = 0;
   CK(cudaMemcpyAsync(&worst, ctx->minpiv, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
