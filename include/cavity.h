@@ -231,6 +231,24 @@ cavity_status cavity_apply_noalloc(cavity_ctx* ctx, int ndir, int precision,
 cavity_status cavity_field(cavity_ctx* ctx, int ndir, const void* aperture,
                            void* field);
 
+/* ---- implementation options (chosen by the autotuner) ---------------------
+ * Variants of the same arithmetic whose speed depends on the grid, the batch
+ * and the device; results agree within the precision of the path (the FP32
+ * operator variants to ~1e-7 relative, the group width within the solver
+ * tolerance).  Set per context, at any time between calls; the
+ * paper_2008_01966_gb300.autotune module times them and caches its choice.
+ *  CAVITY_OPT_PASS_B_2048, CAVITY_OPT_PASS_C_2048: FP32 operator passes B and
+ *      C on lines of 2048 points (512-point grid sides): 0 = each line on a
+ *      pair of warps (one radix-2 step, then a 1024-point warp transform per
+ *      warp; default), 1 = the block (Stockham) transform.
+ *  CAVITY_OPT_GROUP_WIDTH: directions per group of the mixed solve's block
+ *      Krylov iterations (one basis per group), 1..16; default 16.
+ * CAVITY_EINVAL for an unknown option or a value out of range. */
+enum { CAVITY_OPT_PASS_B_2048 = 0, CAVITY_OPT_PASS_C_2048 = 1, CAVITY_OPT_GROUP_WIDTH = 2,
+       CAVITY_NUM_OPT = 3 };
+cavity_status cavity_set_option(cavity_ctx* ctx, int option, int value);
+cavity_status cavity_get_option(const cavity_ctx* ctx, int option, int* value);
+
 /* ---- launch accounting (benchmark instrumentation, not part of the method) --
  * Every kernel the library launches belongs to one of CAVITY_NUM_KCLASS
  * classes (names from cavity_kernel_class).  Launches are always counted.

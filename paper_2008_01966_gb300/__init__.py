@@ -247,6 +247,18 @@ class Cavity:
         self._check(self.lib.cavity_export_khat(self.h, ctypes.c_void_p(out.data_ptr())))
         return out
 
+    # ------------------------------------------------------------ options
+    def set_option(self, name, value):
+        """Implementation option (include/cavity.h, CAVITY_OPT_*): "pass_b_2048",
+        "pass_c_2048" (0 warp pairs, 1 block transform) or "group_width"
+        (1..16 directions per block Krylov group)."""
+        self._check(self.lib.cavity_set_option(self.h, _lib.OPTIONS[name], int(value)))
+
+    def get_option(self, name):
+        v = ctypes.c_int()
+        self._check(self.lib.cavity_get_option(self.h, _lib.OPTIONS[name], ctypes.byref(v)))
+        return v.value
+
     # ------------------------------------------------------------ instrumentation
     def timing(self, enable=True):
         """Reset launch counters; with enable, time every launch with events."""

@@ -24,7 +24,10 @@ EXPORTS = ["cavity_setup", "cavity_prepare", "cavity_solve", "cavity_rcs", "cavi
            "cavity_last_error", "cavity_sizes", "cavity_export_elimination",
            "cavity_export_khat", "cavity_rhs", "cavity_apply", "cavity_field",
            "cavity_timing", "cavity_timing_read", "cavity_kernel_class",
-           "cavity_apply_noalloc"]
+           "cavity_apply_noalloc", "cavity_set_option", "cavity_get_option"]
+CAVITY_OPT_PASS_B_2048, CAVITY_OPT_PASS_C_2048, CAVITY_OPT_GROUP_WIDTH = range(3)
+OPTIONS = {"pass_b_2048": CAVITY_OPT_PASS_B_2048, "pass_c_2048": CAVITY_OPT_PASS_C_2048,
+           "group_width": CAVITY_OPT_GROUP_WIDTH}
 NUM_KCLASS = 21
 
 
@@ -76,6 +79,8 @@ def load():
     lib.cavity_apply.argtypes = [P, I, I, P, P]
     lib.cavity_field.argtypes = [P, I, P, P]
     lib.cavity_apply_noalloc.argtypes = [P, I, I, P, P]
+    lib.cavity_set_option.argtypes = [P, I, I]
+    lib.cavity_get_option.argtypes = [P, I, ctypes.POINTER(I)]
     lib.cavity_timing.argtypes = [P, I]
     lib.cavity_timing_read.argtypes = [P, I, pd, pll]
     lib.cavity_kernel_class.argtypes = [I]

@@ -406,3 +406,27 @@ extern "C" cavity_status cavity_timing_read(cavity_ctx* ctx, int nclass, double*
   }
   return CAVITY_OK;
 }
+
+extern "C" cavity_status cavity_set_option(cavity_ctx* ctx, int option, int value) {
+  if (!ctx) return CAVITY_EINVAL;
+  bool ok = false;
+  switch (option) {
+    case CAVITY_OPT_PASS_B_2048:
+    case CAVITY_OPT_PASS_C_2048: ok = value == 0 || value == 1; break;
+    case CAVITY_OPT_GROUP_WIDTH: ok = value >= 1 && value <= 16; break;
+    default: break;
+  }
+  if (!ok) {
+    ctx->err = "cavity_set_option: unknown option " + std::to_string(option) + " or value " +
+               std::to_string(value) + " out of range";
+    return CAVITY_EINVAL;
+  }
+  ctx->opt[option] = value;
+  return CAVITY_OK;
+}
+
+extern "C" cavity_status cavity_get_option(const cavity_ctx* ctx, int option, int* value) {
+  if (!ctx || !value || option < 0 || option >= CAVITY_NUM_OPT) return CAVITY_EINVAL;
+  *value = ctx->opt[option];
+  return CAVITY_OK;
+}

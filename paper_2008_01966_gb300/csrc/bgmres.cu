@@ -436,9 +436,10 @@ struct BWork {
 
 static size_t al256(size_t x) { return (x + 255) / 256 * 256; }
 
-size_t block_inner_work_bytes(const Geo& g, int ndir, int mb) {
-  const int nd = std::min(ndir, BG_GROUPS * BG_MAX);
-  const int gm = (nd + BG_MAX - 1) / BG_MAX;
+// gw: directions per group (1..BG_MAX); a call takes up to BG_GROUPS groups
+size_t block_inner_work_bytes(const Geo& g, int ndir, int mb, int gw) {
+  const int nd = std::min(ndir, BG_GROUPS * gw);
+  const int gm = (nd + gw - 1) / gw;
   const size_t kcap = (size_t)(mb + 1) * BG_MAX;
   const size_t col = sizeof(float2) * (size_t)g.nap;
   size_t b = 0;
@@ -452,9 +453,9 @@ size_t block_inner_work_bytes(const Geo& g, int ndir, int mb) {
   return b;
 }
 
-static BWork bwork_carve(void* base, const Geo& g, int ndir, int mb) {
-  const int nd = std::min(ndir, BG_GROUPS * BG_MAX);
-  const int gm = (nd + BG_MAX - 1) / BG_MAX;
+static BWork bwork_carve(void* base, const Geo& g, int ndir, int mb, int gw) {
+  const int nd = std::min(ndir, BG_GROUPS * gw);
+  const int gm = (nd + gw - 1) / gw;
   const size_t kcap = (size_t)(mb + 1) * BG_MAX;
   const size_t col = sizeof(float2) * (size_t)g.nap;
   char* p = (char*)base;
@@ -532,11 +533,12 @@ cavity_status run_block_inner(cavity_ctx* ctx, int ndir, const float2* r, float2
     if (active[q]) all.push_back(q);
   est.assign(ndir, 0.0);
   // directions beyond one call's capacity are solved in further batches
-  for (size_t b0 = 0; b0 < all.size(); b0 += BG_GROUPS * BG_MAX) {
-    const int na = (int)std::min(all.size() - b0, (size_t)BG_GROUPS * BG_MAX);
+  const int gw = std::max(1, std::min(BG_MAX, ctx->opt[CAVITY_OPT_GROUP_WIDTH]));
+  for (size_t b0 = 0; b0 < all.size(); b0 += (size_t)BG_GROUPS * gw) {
+    const int na = (int)std::min(all.size() - b0, (size_t)BG_GROUPS * gw);
     std::vector<int> dirs(all.begin() + b0, all.begin() + b0 + na);
-    BWork w = bwork_carve(work, g, ndir, mb);
-    const int ng = (na + BG_MAX - 1) / BG_MAX;
+    BWork w = bwork_carve(work, g, ndir, mb, gw);
+    const int ng = (na + gw - 1) / gw;
     // balanced groups: group z holds directions [goff[z], goff[z] + gr[z])
     std::vector<int> gr(ng), goff(ng);
     for (int z = 0, o = 0; z < ng; ++z) {

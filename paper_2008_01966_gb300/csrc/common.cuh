@@ -152,6 +152,9 @@ struct cavity_ctx {
   cudaStream_t copy_more[3] = {nullptr, nullptr, nullptr};  // further copy engines
   cudaEvent_t copy_join[3] = {nullptr, nullptr, nullptr};
 
+  // ---- implementation options (cavity_set_option)
+  int opt[CAVITY_NUM_OPT] = {0, 0, 16};
+
   // ---- launch accounting: counts always, CUDA-event times while timing is on
   long long nlaunch[KC_N] = {0};
   bool timing = false;
@@ -300,7 +303,7 @@ cavity_status run_block_inner(cavity_ctx* ctx, int ndir, const float2* r, float2
                               const std::vector<double>& tol, const std::vector<char>& active,
                               int mb, int maxit, void* work, std::vector<int>& iters,
                               std::vector<double>& est);
-size_t block_inner_work_bytes(const Geo& g, int ndir, int mb);
+size_t block_inner_work_bytes(const Geo& g, int ndir, int mb, int gw);
 // zero the aperture unknowns outside the truncated mode set (modes_m, modes_n
 // of the descriptor; no-op without truncation), ndir contiguous FP64 vectors
 cavity_status launch_mode_mask(cavity_ctx* ctx, int ndir, double2* v);

@@ -609,7 +609,7 @@ cavity_status run_mixed_solve(cavity_ctx* ctx, int ndir, const double2* b, doubl
   const int mb = std::max(2, std::min(m, 30));
   auto al = [](size_t v) { return (v + 255) / 256 * 256; };
   const long long nv = (long long)ndir * g.nap;
-  const size_t nb = al(block_inner_work_bytes(g, ndir, mb));
+  const size_t nb = al(block_inner_work_bytes(g, ndir, mb, ctx->opt[CAVITY_OPT_GROUP_WIDTH]));
   size_t extra = 2 * al(sizeof(double2) * nv) + 2 * al(sizeof(float2) * nv) +
                  al(apply_pair_work_bytes(g, ndir)) + al(apply_work_bytes(g, ndir, sizeof(float2))) +
                  al(sizeof(double) * ndir) + al(sizeof(double2) * ndir) +

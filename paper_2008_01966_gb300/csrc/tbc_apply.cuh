@@ -820,14 +820,18 @@ cavity_status launch_apply(cavity_ctx* ctx, int ndir, const C<T>* x, C<T>* y, vo
     constexpr int LN = decltype(c)::value;
     constexpr int L = pairs_per_cta<T>(4 << LN);
     if constexpr (w2_ok<T>(LN)) {
-      static std::atomic<bool> done2{false};
-      CKS(smem_once(ctx, k_tbcB_w2<LN>, done2));
-      KScope ks_(ctx, kclass<T>(1));
-      k_tbcB_w2<LN><<<dim3(g.Py / 2, 3, ndir), T_, smem_b_w2(g.nx), st>>>(
-          (const float2*)R1, (float2*)R2, p, (const float2*)tw, (const float2*)Tabs<T>::ex(ctx, 0),
-          (const float2*)Tabs<T>::ex(ctx, 1), (const float2*)Tabs<T>::kh(ctx));
-      return CAVITY_OK;
-    } else {
+      if (ctx->opt[CAVITY_OPT_PASS_B_2048] == 0) {
+        static std::atomic<bool> done2{false};
+        CKS(smem_once(ctx, k_tbcB_w2<LN>, done2));
+        KScope ks_(ctx, kclass<T>(1));
+        k_tbcB_w2<LN><<<dim3(g.Py / 2, 3, ndir), T_, smem_b_w2(g.nx), st>>>(
+            (const float2*)R1, (float2*)R2, p, (const float2*)tw,
+            (const float2*)Tabs<T>::ex(ctx, 0), (const float2*)Tabs<T>::ex(ctx, 1),
+            (const float2*)Tabs<T>::kh(ctx));
+        return CAVITY_OK;
+      }
+    }
+    {
       static std::atomic<bool> done{false};  // set once; host threads may race
       CKS(smem_once(ctx, k_tbcB<T, LN>, done));
       KScope ks_(ctx, kclass<T>(1));
@@ -840,13 +844,16 @@ cavity_status launch_apply(cavity_ctx* ctx, int ndir, const C<T>* x, C<T>* y, vo
     constexpr int LN = decltype(c)::value;
     constexpr int L = lines_per_cta<T>(4 << LN);
     if constexpr (w2_ok<T>(LN)) {
-      static std::atomic<bool> done2{false};
-      CKS(smem_once(ctx, k_tbcC_w2<LN>, done2));
-      KScope ks_(ctx, kclass<T>(2));
-      k_tbcC_w2<LN><<<dim3((g.nx + 1 + 3) / 4, 3, ndir), T_, smem_c_w2(g.ny), st>>>(
-          (const float2*)R2, (float2*)R1, p, (const float2*)tw);
-      return CAVITY_OK;
-    } else {
+      if (ctx->opt[CAVITY_OPT_PASS_C_2048] == 0) {
+        static std::atomic<bool> done2{false};
+        CKS(smem_once(ctx, k_tbcC_w2<LN>, done2));
+        KScope ks_(ctx, kclass<T>(2));
+        k_tbcC_w2<LN><<<dim3((g.nx + 1 + 3) / 4, 3, ndir), T_, smem_c_w2(g.ny), st>>>(
+            (const float2*)R2, (float2*)R1, p, (const float2*)tw);
+        return CAVITY_OK;
+      }
+    }
+    {
       static std::atomic<bool> done{false};  // set once; host threads may race
       CKS(smem_once(ctx, k_tbcC<T, LN>, done));
       KScope ks_(ctx, kclass<T>(2));

@@ -12,9 +12,14 @@ Nz x n_ap per direction).  The mixed solve synchronises with the host once
 per block step, so the sweep is not one captured launch.
 
     python -m paper_2008_01966_gb300.sweep48 [--subset K] [--precision mixed]
+                                             [--tune CACHE.json]
 
 prints one JSON line: solves, wall time, solves/s, DOF/s, and per side class
-the solves, setup and solve seconds and the largest residual.
+the solves, setup and solve seconds and the largest residual.  With --tune,
+the implementation options (include/cavity.h, CAVITY_OPT_*) are chosen by the
+autotuner on the first cavity of each side class (its first wavenumber, all
+64 directions), cached in CACHE.json and applied to every cavity of the
+class; the tuning time counts in the wall time and the choices are printed.
 """
 
 import argparse
@@ -47,6 +52,17 @@ class GpuBackend:
         cav.prepare(kappa0, cv['layers'])
         self.torch.cuda.synchronize()
 
+    def tune(self, cav, cv, kappa0, cache):
+        from . import autotune
+        out = autotune.tune(cav, kappa0, cv['layers'], cv['theta'], cv['phi'], cv['alpha'],
+                            cache=cache)
+        self.torch.cuda.synchronize()
+        return out["choice"]
+
+    def apply_choice(self, cav, choice):
+        for name, v in choice.items():
+            cav.set_option(name, v)
+
     def solve(self, cav, cv, kappa0, want_field):
         ap, _, it, res = cav.solve(kappa0, cv['layers'], cv['theta'], cv['phi'], cv['alpha'],
                                    field=want_field)
@@ -58,12 +74,20 @@ class GpuBackend:
         cav.close()
 
 
-def run(backend, cavities, clock=time.perf_counter):
-    """Solve every (cavity, wavenumber) pair; one record per pair."""
+def run(backend, cavities, clock=time.perf_counter, tune_cache=None, choices=None):
+    """Solve every (cavity, wavenumber) pair; one record per pair.  With
+    tune_cache, options are tuned once per side class (first cavity, first
+    wavenumber) and applied to the class; `choices` receives them by side."""
     records = []
+    chosen = {} if choices is None else choices
     for ci, cv in enumerate(cavities):
         cav = backend.open(cv)
         try:
+            if tune_cache is not None:
+                side = str(cv['nx'])
+                if side not in chosen:
+                    chosen[side] = backend.tune(cav, cv, cv['kappas'][0], tune_cache)
+                backend.apply_choice(cav, chosen[side])
             for ki, kappa0 in enumerate(cv['kappas']):
                 t0 = clock()
                 backend.prepare(cav, cv, kappa0)
@@ -109,16 +133,21 @@ def main(argv=None):
                     help="only the first K cavities of the sweep (0: all 48)")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--tol", type=float, default=1e-7)
+    ap.add_argument("--tune", default=None, metavar="CACHE.json",
+                    help="autotune the implementation options per side class")
     args = ap.parse_args(argv)
     cavities = workloads.rcs_sweep48()
     if args.subset:
         cavities = cavities[:args.subset]
     backend = GpuBackend(args.precision, args.tol)
     t0 = time.perf_counter()
-    records = run(backend, cavities)
+    choices = {}
+    records = run(backend, cavities, tune_cache=args.tune, choices=choices)
     wall = time.perf_counter() - t0
     out = summary(records, wall)
     out.update(precision=args.precision, tol=args.tol, cavities=len(cavities))
+    if args.tune:
+        out["tuned_options"] = choices
     print(json.dumps(out))
     return out
 

@@ -69,3 +69,40 @@ def test_context_closed_when_a_solve_fails():
     except RuntimeError:
         pass
     assert fb.events[-1] == ("close",)
+
+
+def test_tuning_once_per_side_class():
+    """With a tuning cache, the options are tuned on the first cavity of each
+    side class (its first wavenumber) and applied to every cavity of that
+    class before its solves."""
+    class Tuning(FakeBackend):
+        def tune(self, cav, cv, kappa0, cache):
+            self.events.append(("tune", cv['nx'], kappa0, cache))
+            return {"group_width": cv['nx'] // 64}
+
+        def apply_choice(self, cav, choice):
+            self.events.append(("apply", cav["cv"]['nx'], choice["group_width"]))
+
+    cavities = workloads.rcs_sweep48()
+    fb = Tuning()
+    choices = {}
+    sweep48.run(fb, cavities, tune_cache="c.json", choices=choices)
+    tunes = [e for e in fb.events if e[0] == "tune"]
+    assert sorted(e[1] for e in tunes) == sorted({cv['nx'] for cv in cavities})
+    first = {}
+    for cv in cavities:
+        first.setdefault(cv['nx'], cv['kappas'][0])
+    assert all(e[2] == first[e[1]] and e[3] == "c.json" for e in tunes)
+    applies = [e for e in fb.events if e[0] == "apply"]
+    assert len(applies) == 48 and all(e[2] == e[1] // 64 for e in applies)
+    assert choices == {str(s): {"group_width": s // 64} for s in first}
+    # every apply precedes the cavity's first solve
+    last = None
+    for e in fb.events:
+        if e[0] == "apply":
+            last = "apply"
+        elif e[0] == "solve":
+            assert last in ("apply", "solve")
+            last = "solve"
+        elif e[0] == "open":
+            last = "open"
