@@ -198,6 +198,71 @@ class ApertureSystem:
         X[:, k] = sla.solve(A[np.ix_(k, k)], b[:, k].T).T
         return X
 
+    def dense_kept(self, mm, nn):
+        """The kept block A[k][:, k] of dense() for the modes m <= mm, n <= nn,
+        assembled from restricted pieces: the cavity part couples the three
+        components of one mode only, and each TBC integral is a product of
+        per-axis factors, so the block needs the factor rows and columns of the
+        kept modes alone (TBCOperator.dense with mm, nn).  Rows and columns in
+        the order of kept_modes: E1 (m = 0..mm, n = 1..nn), E2 (m = 1..mm,
+        n = 0..nn), E3 (m = 1..mm, n = 1..nn), m-major."""
+        cav = self.cav
+        h = cav.h
+        k2 = 2.0 * cav.kappa0 ** 2
+        p = self.prof
+        n1, n2, n3 = (mm + 1) * nn, mm * (nn + 1), mm * nn
+        nk = n1 + n2 + n3
+        mx, ny = self.mx[:mm + 1], self.ny[:nn + 1]
+        I1 = self.tbc.dense('cs', mm, nn)            # m, k1 = 0..mm;  n, k2 = 1..nn
+        I2 = self.tbc.dense('sc', mm, nn)            # m, k1 = 1..mm;  n, k2 = 0..nn
+        I3 = self.tbc.dense('cc', mm, nn)            # m, k1 = 0..mm;  n, k2 = 0..nn
+        s1 = (h / self.q[:mm + 1])[:, None]
+        s2 = (h / self.cn[:nn + 1])[None, :]
+        A = np.zeros((nk, nk), dtype=complex)
+        # TBC blocks (the F, G, H blocks of (ENUGa) with w = div_Gamma(z x E))
+        B11 = k2 * s1[:, :, None, None] * I1
+        B11 -= (s1 * 2.0 * ny[None, 1:])[:, :, None, None] * \
+            I3[:, 1:, :, 1:] * ny[None, None, None, 1:]
+        B12 = (s1 * 2.0 * ny[None, 1:])[:, :, None, None] * \
+            I3[:, 1:, 1:, :] * mx[None, None, 1:, None]
+        B21 = (s2 * 2.0 * mx[1:, None])[:, :, None, None] * \
+            I3[1:, :, :, 1:] * ny[None, None, None, 1:]
+        B22 = k2 * s2[:, :, None, None] * I2
+        B22 -= (s2 * 2.0 * mx[1:, None])[:, :, None, None] * \
+            I3[1:, :, 1:, :] * mx[None, None, 1:, None]
+        A[:n1, :n1] = B11.reshape(n1, n1)
+        A[:n1, n1:n1 + n2] = B12.reshape(n1, n2)
+        A[n1:n1 + n2, :n1] = B21.reshape(n2, n1)
+        A[n1:n1 + n2, n1:n1 + n2] = B22.reshape(n2, n2)
+        # cavity part, mode by mode (the rows of local())
+        m1, q1 = np.meshgrid(np.arange(0, mm + 1), np.arange(1, nn + 1), indexing='ij')
+        m2, q2 = np.meshgrid(np.arange(1, mm + 1), np.arange(0, nn + 1), indexing='ij')
+        m3, q3 = np.meshgrid(np.arange(1, mm + 1), np.arange(1, nn + 1), indexing='ij')
+        i1 = (m1 * nn + q1 - 1).ravel()
+        i2 = (n1 + (m2 - 1) * (nn + 1) + q2).ravel()
+        i3 = (n1 + n2 + (m3 - 1) * nn + q3 - 1).ravel()
+        A[i1, i1] += (-1.0 + p.tau1[m1, q1 - 1]).ravel()
+        A[i2, i2] += (-1.0 + p.tau2[m2 - 1, q2]).ravel()
+        A[i3, i3] += (-1.0 + p.tau3[m3 - 1, q3 - 1]).ravel()
+        # E3 columns of rows 1 and 2, and row 3
+        j1 = (m3 * nn + q3 - 1).ravel()                    # E1 unknown of mode (m, n), m, n >= 1
+        j2 = (n1 + (m3 - 1) * (nn + 1) + q3).ravel()       # E2 unknown of the same mode
+        A[j1, i3] += (m3 * np.pi / cav.a * h + p.vs1[m3, q3 - 1]).ravel()
+        A[j2, i3] += (q3 * np.pi / cav.b * h + p.vs2[m3 - 1, q3]).ravel()
+        A[i3, j1] += (m3 * np.pi / cav.a * h).ravel()
+        A[i3, j2] += (q3 * np.pi / cav.b * h).ravel()
+        return A
+
+    def solve_kept(self, b, mm, nn):
+        """solve_truncated with the kept block assembled by dense_kept (the
+        same system; feasible where the full dense matrix is not)."""
+        A = self.dense_kept(mm, nn)
+        k = self.kept_modes(mm, nn)
+        b = np.atleast_2d(b)
+        X = np.zeros(b.shape, dtype=complex)
+        X[:, k] = sla.solve(A, b[:, k].T).T
+        return X
+
     def solve_gmres(self, b, rtol=1e-13, restart=200, maxiter=200):
         """Restarted GMRES (SciPy) on the matrix-free operator with the block
         diagonal as preconditioner; the true residual is recomputed afterwards.

@@ -177,8 +177,15 @@ class TBCOperator:
         (Xx, Fx), (Xy, Fy) = self.factors(kind)
         return (Xx * Fx.T) @ self.Kh @ (Xy * Fy.T).T
 
-    def dense(self, kind):
-        """I[m, n, k1, k2] for the full index ranges of `kind` (small grids)."""
+    def dense(self, kind, mm=None, nn=None):
+        """I[m, n, k1, k2] for the full index ranges of `kind` (small grids),
+        or, with mm, nn, for the modes m, k1 <= mm and n, k2 <= nn only (the
+        factor rows and columns of those modes; the rest of each range is
+        cut off)."""
         (Xx, Fx), (Xy, Fy) = self.factors(kind)
+        if mm is not None:
+            cx = mm + 1 if kind[0] == 'c' else mm      # 'c' ranges start at 0, 's' at 1
+            cy = nn + 1 if kind[1] == 'c' else nn
+            Xx, Fx, Xy, Fy = Xx[:cx], Fx[:, :cx], Xy[:cy], Fy[:, :cy]
         T1 = np.einsum('mj,jl,jk->mkl', Xx, self.Kh, Fx, optimize=True)
         return np.einsum('nl,mkl,lq->mnkq', Xy, T1, Fy, optimize=True)

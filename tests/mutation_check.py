@@ -51,6 +51,10 @@ MUTATIONS = [
     ('aperture.py', "+ (self.ny[None, 1:] * h) * e2[..., :, 1:] + (-1.0 + p.tau3) * e3", "- (self.ny[None, 1:] * h) * e2[..., :, 1:] + (-1.0 + p.tau3) * e3"),
     ('aperture.py', "k2 = 2.0 * cav.kappa0 ** 2\n        h = cav.h\n        U1", "k2 = -2.0 * cav.kappa0 ** 2\n        h = cav.h\n        U1"),
     ('aperture.py', "(k2 * U2 + 2.0 * self.mx[1:, None] * W[1:, :])", "(k2 * U2 - 2.0 * self.mx[1:, None] * W[1:, :])"),
+    ('aperture.py', "A[j1, i3] += (m3 * np.pi / cav.a * h + p.vs1[m3, q3 - 1]).ravel()", "A[j1, i3] += (m3 * np.pi / cav.a * h - p.vs1[m3, q3 - 1]).ravel()"),
+    ('aperture.py', "A[i3, j2] += (q3 * np.pi / cav.b * h).ravel()", "A[i3, j2] += (q3 * np.pi / cav.a * h).ravel()"),
+    ('aperture.py', "B21 = (s2 * 2.0 * mx[1:, None])[:, :, None, None] * \\\n            I3[1:, :, :, 1:]", "B21 = (s2 * 2.0 * mx[1:, None])[:, :, None, None] * \\\n            -I3[1:, :, :, 1:]"),
+    ('tbc.py', "cy = nn + 1 if kind[1] == 'c' else nn", "cy = nn + 1"),
     ('field.py', "c1[1:, :] += prof.Q1[1:, :, j] * e3", "c1[1:, :] -= prof.Q1[1:, :, j] * e3"),
     ('field.py', "f2 = sinx @ c2 @ cosy.T", "f2 = sinx @ c2 @ cosy[::-1].T"),
     ('field.py', "siny = np.sin(np.pi * np.outer(py[1:-1], np.arange(1, N + 1)) / cav.ny)", "siny = np.sin(np.pi * np.outer(py[1:-1], np.arange(0, N)) / cav.ny)"),

@@ -653,6 +653,26 @@ def test_field_top_level_is_aperture_synthesis():
     assert np.allclose(f, ref, atol=1e-13)
 
 
+@pytest.mark.parametrize("name,nx,ny", [("dirs16", 16, 16), ("layered4", 16, 8)])
+def test_kept_block_is_the_restriction_of_the_dense_matrix(name, nx, ny):
+    """dense_kept (the kept modes' block assembled from restricted per-axis
+    factors and the mode-diagonal cavity part) equals the rows and columns of
+    the kept modes cut out of the full dense matrix, for square and oblong
+    mode sets, one or all modes per axis; solve_kept is solve_truncated."""
+    w = workloads.scaled(name, nx, nz=8, ndir=1)
+    cav = Cavity(w['a'], w['b'] * ny / nx, w['c'], nx, ny, w['nz'], w['kappa0'],
+                 layers=[Layer(n, e) for n, e in w['layers']])
+    s = ApertureSystem(cav)
+    A = s.dense()
+    scale = np.abs(A).max()
+    for mm, nn in ((3, 5), (7, 2), (1, 1), (cav.M, 3), (cav.M, cav.N)):
+        k = s.kept_modes(mm, nn)
+        assert np.abs(s.dense_kept(mm, nn) - A[np.ix_(k, k)]).max() <= 1e-14 * scale
+    b = rhs(cav, w['theta'][0], w['phi'][0], w['alpha'][0])
+    X1, X2 = s.solve_truncated(b, 4, 3), s.solve_kept(b, 4, 3)
+    assert np.linalg.norm(X1 - X2) <= 1e-12 * np.linalg.norm(X1)
+
+
 def test_truncated_expansion_limits():
     """The truncated aperture expansion (Sec. 7: the paper's runs keep few
     modes): keeping every mode is the full solve; the kept set is counted
