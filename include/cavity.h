@@ -93,8 +93,24 @@ typedef struct {
                          /* and their rows dropped), as in the paper's runs with */
                          /* few modes (Sec. 7, Table 2: M ~ 2a/lambda); 0 -> all */
                          /* (M = nx-1, N = ny-1); must not exceed M, N          */
+  int aperture_solver;   /* how (EJ1)/(uT1) is solved (Algorithm I/II Step 3):  */
+                         /* CAVITY_SOLVER_KRYLOV (0): matrix-free GMRES with the */
+                         /*   FFT operator (see precision);                     */
+                         /* CAVITY_SOLVER_DENSE (1): the paper's direct solve of */
+                         /*   the kept block (every unknown of the modes m <=   */
+                         /*   modes_m, n <= modes_n), assembled once per        */
+                         /*   cavity_prepare from the per-axis factors of       */
+                         /*   Sec. 5.2 and LU-factored with partial pivoting in */
+                         /*   FP32; each solve refines x in FP64 with the FFT   */
+                         /*   operator's residual (FP64 operator for           */
+                         /*   CAVITY_FP64, pair-of-FP32 for CAVITY_MIXED), so  */
+                         /*   the result meets gmres_tol like the Krylov path. */
+                         /*   The kept block must have at most                 */
+                         /*   CAVITY_DENSE_MAX_N unknowns (3 mm nn + mm + nn)  */
 } cavity_desc;
 enum { CAVITY_KHAT_QUADRATURE = 0, CAVITY_KHAT_PAPER = 1 };
+enum { CAVITY_SOLVER_KRYLOV = 0, CAVITY_SOLVER_DENSE = 1 };
+#define CAVITY_DENSE_MAX_N 16384
 
 /* Create a context for one cavity geometry and grid.  `cuda_stream` is a
  * cudaStream_t (NULL = legacy default stream).  Validates the descriptor;
@@ -231,6 +247,34 @@ cavity_status cavity_apply_noalloc(cavity_ctx* ctx, int ndir, int precision,
 cavity_status cavity_field(cavity_ctx* ctx, int ndir, const void* aperture,
                            void* field);
 
+/* Dense direct solve (Algorithm I/II Step 3) on the kept modes, step by step.
+ *
+ * cavity_dense_size: *n = number of kept unknowns, 3 mm nn + mm + nn with
+ *   mm = modes_m, nn = modes_n (0 -> M, N); the kept block's rows and columns
+ *   are these unknowns in Appendix A order (E1 over m = 0..mm, n = 1..nn, then
+ *   E2 over m = 1..mm, n = 0..nn, then E3 over m = 1..mm, n = 1..nn, m-major).
+ * cavity_dense_assemble (after cavity_prepare): writes the kept block of the
+ *   matrix of (EJ1)/(uT1) -- the cavity part and the TBC integrals of Sec. 5.1
+ *   under the discrete rule of Sec. 5.2 -- as complex64 into the device buffer
+ *   a, row-major with leading dimension lda >= n (elements); entries carry
+ *   FP32 rounding of sums over the frequency box.  CAVITY_EINVAL if n exceeds
+ *   CAVITY_DENSE_MAX_N.
+ * cavity_lu_factor: in-place LU factorisation with partial pivoting, P A = L U
+ *   (L unit lower, U upper, both stored in a), of an n x n complex64 device
+ *   matrix, row-major with leading dimension lda; ipiv (device, n ints)
+ *   receives the row exchanged with row i at step i (0-based, as a sequence of
+ *   exchanges).  *info (host) = -1, or the first step whose pivot column was
+ *   exactly zero (the factors are then complete but U is singular and the call
+ *   returns CAVITY_ESINGULAR).  1 <= n <= CAVITY_DENSE_MAX_N.
+ * cavity_lu_solve: overwrites the nrhs right-hand sides b (device, complex64,
+ *   right-hand side r at b + r ldb, ldb >= n) with the solutions of
+ *   A x = b from cavity_lu_factor's output. */
+cavity_status cavity_dense_size(const cavity_ctx* ctx, int* n);
+cavity_status cavity_dense_assemble(cavity_ctx* ctx, void* a, int lda);
+cavity_status cavity_lu_factor(cavity_ctx* ctx, void* a, int n, int lda, int* ipiv, int* info);
+cavity_status cavity_lu_solve(cavity_ctx* ctx, const void* lu, int n, int lda, const int* ipiv,
+                              int nrhs, void* b, int ldb);
+
 /* ---- implementation options (chosen by the autotuner) ---------------------
  * Variants of the same arithmetic whose speed depends on the grid, the batch
  * and the device; results agree within the precision of the path (the FP32
@@ -258,7 +302,7 @@ cavity_status cavity_get_option(const cavity_ctx* ctx, int option, int* value);
  * returns, per class, the summed event time in ms (0 when timing was off) and
  * the number of launches since the last reset; ms and launches are host arrays
  * of length nclass (<= CAVITY_NUM_KCLASS), either may be NULL. */
-#define CAVITY_NUM_KCLASS 21
+#define CAVITY_NUM_KCLASS 24
 cavity_status cavity_timing(cavity_ctx* ctx, int enable);
 cavity_status cavity_timing_read(cavity_ctx* ctx, int nclass, double* ms,
                                  long long* launches);

@@ -68,7 +68,7 @@ class Cavity:
 
     def __init__(self, a, b, c, nx, ny, nz, precision="fp64", gmres_tol=0.0, gmres_restart=0,
                  gmres_max_iter=0, pivot_tol=0.0, stream=None, device=None,
-                 khat_scheme="quadrature", modes_m=0, modes_n=0):
+                 khat_scheme="quadrature", modes_m=0, modes_n=0, aperture_solver="krylov"):
         self.lib = _lib.load()
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
         torch.cuda.set_device(self.device)
@@ -76,7 +76,8 @@ class Cavity:
         self.precision = _lib.CAVITY_FP64 if precision == "fp64" else _lib.CAVITY_MIXED
         d = _lib.CavityDesc(a, b, c, nx, ny, nz, self.precision, 4, gmres_tol, gmres_restart,
                             gmres_max_iter, pivot_tol,
-                            {"quadrature": 0, "paper": 1}[khat_scheme], modes_m, modes_n)
+                            {"quadrature": 0, "paper": 1}[khat_scheme], modes_m, modes_n,
+                            _lib.SOLVERS[aperture_solver])
         h = ctypes.c_void_p()
         st = self.lib.cavity_setup(ctypes.byref(d), ctypes.c_void_p(self.stream.cuda_stream),
                                    ctypes.byref(h))
@@ -246,6 +247,48 @@ class Cavity:
         out = torch.empty((2 * self.nx, 2 * self.ny), dtype=torch.complex128, device=self.device)
         self._check(self.lib.cavity_export_khat(self.h, ctypes.c_void_p(out.data_ptr())))
         return out
+
+    # ------------------------------------------------------------ dense solve steps
+    def dense_size(self):
+        """Number of kept unknowns (rows of the kept block)."""
+        n = ctypes.c_int()
+        self._check(self.lib.cavity_dense_size(self.h, ctypes.byref(n)))
+        return n.value
+
+    def dense_assemble(self):
+        """The kept block of the aperture matrix (after prepare) as an n x n
+        complex64 device tensor."""
+        n = self.dense_size()
+        a = torch.empty((n, n), dtype=torch.complex64, device=self.device)
+        self._check(self.lib.cavity_dense_assemble(self.h, ctypes.c_void_p(a.data_ptr()), n))
+        return a
+
+    def lu_factor(self, a):
+        """In-place LU with partial pivoting of the square complex64 device
+        tensor a (row-major); returns (ipiv, info) with ipiv an int32 device
+        tensor of row exchanges (info -1 unless a pivot column was zero)."""
+        if a.dtype != torch.complex64 or a.dim() != 2 or a.shape[0] != a.shape[1] or \
+                not a.is_contiguous() or a.device != self.device:
+            raise ValueError("a must be a contiguous square complex64 tensor on %s" % self.device)
+        n = a.shape[0]
+        ipiv = torch.empty(n, dtype=torch.int32, device=self.device)
+        info = ctypes.c_int(-1)
+        st = self.lib.cavity_lu_factor(self.h, ctypes.c_void_p(a.data_ptr()), n, n,
+                                       ctypes.c_void_p(ipiv.data_ptr()), ctypes.byref(info))
+        if st not in (0, _lib.CAVITY_ESINGULAR):
+            self._check(st)
+        return ipiv, info.value
+
+    def lu_solve(self, lu, ipiv, b):
+        """Solve with lu_factor's output for the rows of b (nrhs x n
+        complex64 device tensor, overwritten and returned)."""
+        n = lu.shape[0]
+        if b.dtype != torch.complex64 or b.dim() != 2 or b.shape[1] != n or not b.is_contiguous():
+            raise ValueError("b must be a contiguous nrhs x %d complex64 tensor" % n)
+        self._check(self.lib.cavity_lu_solve(self.h, ctypes.c_void_p(lu.data_ptr()), n, n,
+                                             ctypes.c_void_p(ipiv.data_ptr()), b.shape[0],
+                                             ctypes.c_void_p(b.data_ptr()), n))
+        return b
 
     # ------------------------------------------------------------ options
     def set_option(self, name, value):

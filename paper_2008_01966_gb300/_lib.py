@@ -24,11 +24,15 @@ EXPORTS = ["cavity_setup", "cavity_prepare", "cavity_solve", "cavity_rcs", "cavi
            "cavity_last_error", "cavity_sizes", "cavity_export_elimination",
            "cavity_export_khat", "cavity_rhs", "cavity_apply", "cavity_field",
            "cavity_timing", "cavity_timing_read", "cavity_kernel_class",
-           "cavity_apply_noalloc", "cavity_set_option", "cavity_get_option"]
+           "cavity_apply_noalloc", "cavity_set_option", "cavity_get_option",
+           "cavity_dense_size", "cavity_dense_assemble", "cavity_lu_factor", "cavity_lu_solve"]
+CAVITY_SOLVER_KRYLOV, CAVITY_SOLVER_DENSE = 0, 1
+SOLVERS = {"krylov": CAVITY_SOLVER_KRYLOV, "dense": CAVITY_SOLVER_DENSE}
+DENSE_MAX_N = 16384
 CAVITY_OPT_PASS_B_2048, CAVITY_OPT_PASS_C_2048, CAVITY_OPT_GROUP_WIDTH = range(3)
 OPTIONS = {"pass_b_2048": CAVITY_OPT_PASS_B_2048, "pass_c_2048": CAVITY_OPT_PASS_C_2048,
            "group_width": CAVITY_OPT_GROUP_WIDTH}
-NUM_KCLASS = 21
+NUM_KCLASS = 24
 
 
 class CavityDesc(ctypes.Structure):
@@ -37,7 +41,8 @@ class CavityDesc(ctypes.Structure):
                 ("precision", ctypes.c_int), ("pad_factor", ctypes.c_int),
                 ("gmres_tol", ctypes.c_double), ("gmres_restart", ctypes.c_int),
                 ("gmres_max_iter", ctypes.c_int), ("pivot_tol", ctypes.c_double),
-                ("khat_scheme", ctypes.c_int), ("modes_m", ctypes.c_int), ("modes_n", ctypes.c_int)]
+                ("khat_scheme", ctypes.c_int), ("modes_m", ctypes.c_int), ("modes_n", ctypes.c_int),
+                ("aperture_solver", ctypes.c_int)]
 
 
 class CavityError(RuntimeError):
@@ -81,6 +86,10 @@ def load():
     lib.cavity_apply_noalloc.argtypes = [P, I, I, P, P]
     lib.cavity_set_option.argtypes = [P, I, I]
     lib.cavity_get_option.argtypes = [P, I, ctypes.POINTER(I)]
+    lib.cavity_dense_size.argtypes = [P, pi]
+    lib.cavity_dense_assemble.argtypes = [P, P, I]
+    lib.cavity_lu_factor.argtypes = [P, P, I, I, P, pi]
+    lib.cavity_lu_solve.argtypes = [P, P, I, I, P, I, P, I]
     lib.cavity_timing.argtypes = [P, I]
     lib.cavity_timing_read.argtypes = [P, I, pd, pll]
     lib.cavity_kernel_class.argtypes = [I]

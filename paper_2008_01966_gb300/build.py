@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libcavity.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["api.cu", "tbc.cu", "tbc_f32.cu", "tbc_df.cu", "zsweep.cu", "khat.cu", "rhs.cu", "precond.cu", "gmres.cu", "bgmres.cu",
+SOURCES = ["api.cu", "tbc.cu", "tbc_f32.cu", "tbc_df.cu", "zsweep.cu", "khat.cu", "rhs.cu", "precond.cu", "gmres.cu", "bgmres.cu", "dense.cu",
            "field.cu", "field_fused.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fcx-limited-range",

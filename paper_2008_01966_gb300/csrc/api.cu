@@ -44,6 +44,14 @@ extern "C" cavity_status cavity_setup(const cavity_desc* desc, void* cuda_stream
     return bad("khat_scheme must be CAVITY_KHAT_QUADRATURE or CAVITY_KHAT_PAPER");
   if (d.modes_m < 0 || d.modes_m > d.nx - 1 || d.modes_n < 0 || d.modes_n > d.ny - 1)
     return bad("modes_m, modes_n must be in [0, nx-1], [0, ny-1]");
+  if (d.aperture_solver != CAVITY_SOLVER_KRYLOV && d.aperture_solver != CAVITY_SOLVER_DENSE)
+    return bad("aperture_solver must be CAVITY_SOLVER_KRYLOV or CAVITY_SOLVER_DENSE");
+  if (d.aperture_solver == CAVITY_SOLVER_DENSE) {
+    const long long mm = d.modes_m > 0 ? d.modes_m : d.nx - 1, nn = d.modes_n > 0 ? d.modes_n : d.ny - 1;
+    if (3 * mm * nn + mm + nn > CAVITY_DENSE_MAX_N)
+      return bad("dense aperture solver: the kept block (3 mm nn + mm + nn unknowns) exceeds "
+                 "CAVITY_DENSE_MAX_N; truncate with modes_m, modes_n");
+  }
   cavity_ctx* ctx = new cavity_ctx();
   ctx->desc = d;
   if (ctx->desc.pad_factor == 0) ctx->desc.pad_factor = 4;
@@ -89,7 +97,9 @@ extern "C" void cavity_destroy(cavity_ctx* ctx) {
                   ctx->ehat_y32[1], ctx->khat64, ctx->khat32, ctx->khat_raw, ctx->prof, ctx->profq,
                   ctx->top64, ctx->top32, ctx->pinv64, ctx->pinv32, ctx->prof32, ctx->profq32,
                   ctx->minpiv, ctx->ws, ctx->ws2, ctx->stage, ctx->tw_p, ctx->ehat_xp[0],
-                  ctx->ehat_xp[1], ctx->ehat_yp[0], ctx->ehat_yp[1], ctx->khat_p, ctx->top_p, ctx->prof_rec};
+                  ctx->ehat_xp[1], ctx->ehat_yp[0], ctx->ehat_yp[1], ctx->khat_p, ctx->top_p, ctx->prof_rec,
+                  ctx->dn_a, ctx->dn_ipiv, ctx->dn_perm, ctx->dn_map, ctx->dn_scr,
+                  ctx->dn_dinv};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (ctx->pin) cudaFreeHost(ctx->pin);
@@ -161,6 +171,7 @@ extern "C" cavity_status cavity_prepare(cavity_ctx* ctx, double kappa0, int nlay
              L[l].eps_im == ctx->layers[l].eps_im;
   if (same) return CAVITY_OK;
   ctx->prepared = false;
+  ctx->dn_ready = false;
   bool kappa_same = ctx->khat64 && ctx->kappa0 == kappa0;
   const bool was_layered = ctx->layers.size() > 1;
   ctx->kappa0 = kappa0;
@@ -172,6 +183,22 @@ extern "C" cavity_status cavity_prepare(cavity_ctx* ctx, double kappa0, int nlay
   CKS(launch_pair_tables(ctx));
   CK(cudaStreamSynchronize(ctx->stream));
   ctx->prepared = true;
+  if (ctx->desc.aperture_solver == CAVITY_SOLVER_DENSE) {
+    // Step 3 of Algorithm I/II as a direct solve: the kept block's factors
+    // are part of the resident state of this (kappa0, eps)
+    cavity_status s = launch_dense_factor(ctx);
+    if (s == CAVITY_OK) {
+      cudaError_t e = cudaStreamSynchronize(ctx->stream);
+      if (e != cudaSuccess) {
+        ctx->err = cudaGetErrorString(e);
+        s = CAVITY_ECUDA;
+      }
+    }
+    if (s != CAVITY_OK) {
+      ctx->prepared = false;
+      return s;
+    }
+  }
   return CAVITY_OK;
 }
 
@@ -301,7 +328,9 @@ extern "C" cavity_status cavity_solve(cavity_ctx* ctx, double kappa0, int nlayer
   CKS(launch_rhs(ctx, ndir, theta, phi, alpha, b));
   CKS(launch_mode_mask(ctx, ndir, b));  // truncated expansion: the kept rows only
   cavity_status st;
-  if (ctx->desc.precision == CAVITY_FP64)
+  if (ctx->desc.aperture_solver == CAVITY_SOLVER_DENSE)
+    st = run_dense_solve(ctx, ndir, b, x, iters_out, resid_out);
+  else if (ctx->desc.precision == CAVITY_FP64)
     st = run_gmres64(ctx, ndir, b, x, iters_out, resid_out);
   else
     st = run_mixed_solve(ctx, ndir, b, x, iters_out, resid_out);
@@ -366,7 +395,8 @@ static const char* kclass_names[KC_N] = {
     "tbc_A_fp64", "tbc_B_fp64", "tbc_C_fp64", "tbc_D_fp64", "tbc_combine_fp64",
     "tbc_A_fp32", "tbc_B_fp32", "tbc_C_fp32", "tbc_D_fp32", "tbc_combine_fp32",
     "krylov", "precond", "field_y", "field_x", "rhs_rcs", "setup",
-    "tbc_A_pair32", "tbc_B_pair32", "tbc_C_pair32", "tbc_D_pair32", "tbc_combine_pair32"};
+    "tbc_A_pair32", "tbc_B_pair32", "tbc_C_pair32", "tbc_D_pair32", "tbc_combine_pair32",
+    "dense_assemble", "dense_lu", "dense_solve"};
 static_assert(KC_N == CAVITY_NUM_KCLASS, "class count");
 
 extern "C" const char* cavity_kernel_class(int k) {
@@ -405,6 +435,38 @@ extern "C" cavity_status cavity_timing_read(cavity_ctx* ctx, int nclass, double*
     if (launches) launches[k] = ctx->nlaunch[k];
   }
   return CAVITY_OK;
+}
+
+extern "C" cavity_status cavity_dense_size(const cavity_ctx* ctx, int* n) {
+  if (!ctx || !n) return CAVITY_EINVAL;
+  *n = kept_set(ctx->desc, ctx->g).nk;
+  return CAVITY_OK;
+}
+
+extern "C" cavity_status cavity_dense_assemble(cavity_ctx* ctx, void* a, int lda) {
+  if (!ctx) return CAVITY_EINVAL;
+  if (!a) {
+    ctx->err = "cavity_dense_assemble: a is NULL";
+    return CAVITY_EINVAL;
+  }
+  CKS(dense_assemble(ctx, (float2*)a, lda));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return CAVITY_OK;
+}
+
+extern "C" cavity_status cavity_lu_factor(cavity_ctx* ctx, void* a, int n, int lda, int* ipiv,
+                                          int* info) {
+  if (!ctx) return CAVITY_EINVAL;
+  int inf = -1;
+  cavity_status s = dense_lu(ctx, (float2*)a, n, lda, ipiv, &inf);
+  if (info) *info = inf;
+  return s;
+}
+
+extern "C" cavity_status cavity_lu_solve(cavity_ctx* ctx, const void* lu, int n, int lda,
+                                         const int* ipiv, int nrhs, void* b, int ldb) {
+  if (!ctx) return CAVITY_EINVAL;
+  return dense_lu_solve(ctx, (const float2*)lu, n, lda, ipiv, nullptr, nrhs, (float2*)b, ldb);
 }
 
 extern "C" cavity_status cavity_set_option(cavity_ctx* ctx, int option, int value) {

@@ -4,6 +4,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
 #include <string>
 #include <type_traits>
@@ -82,7 +83,8 @@ enum KClass {
   KC_TBC_A64, KC_TBC_B64, KC_TBC_C64, KC_TBC_D64, KC_COMB64,
   KC_TBC_A32, KC_TBC_B32, KC_TBC_C32, KC_TBC_D32, KC_COMB32,
   KC_KRYLOV, KC_PRECOND, KC_FIELD_Y, KC_FIELD_X, KC_RHS, KC_SETUP,
-  KC_TBC_AP, KC_TBC_BP, KC_TBC_CP, KC_TBC_DP, KC_COMBP, KC_N
+  KC_TBC_AP, KC_TBC_BP, KC_TBC_CP, KC_TBC_DP, KC_COMBP,
+  KC_DENSE_ASM, KC_DENSE_LU, KC_DENSE_TRS, KC_N
 };
 
 // one layer of the fill, top to bottom
@@ -151,6 +153,19 @@ struct cavity_ctx {
   std::vector<cudaEvent_t> copy_evs;    // overlapped with the field synthesis
   cudaStream_t copy_more[3] = {nullptr, nullptr, nullptr};  // further copy engines
   cudaEvent_t copy_join[3] = {nullptr, nullptr, nullptr};
+
+  // ---- dense solve of the kept block (aperture_solver == CAVITY_SOLVER_DENSE):
+  // FP32 LU factors (row-major, leading dimension dn_lda) with the row
+  // permutation, and the map from kept (compact) to full unknown indices
+  int dn_n = 0, dn_lda = 0;
+  bool dn_ready = false;
+  float2* dn_a = nullptr;
+  float2* dn_dinv = nullptr;  // inverted 64 x 64 diagonal blocks of L and U
+  int* dn_ipiv = nullptr;
+  int* dn_perm = nullptr;
+  int* dn_map = nullptr;
+  void* dn_scr = nullptr;     // LU scratch (pivot candidates, barrier counters)
+  size_t dn_scr_bytes = 0;
 
   // ---- implementation options (cavity_set_option)
   int opt[CAVITY_NUM_OPT] = {0, 0, 16};
@@ -347,8 +362,49 @@ inline cavity_status ensure_copy_stream(cavity_ctx* ctx, size_t n) {
   }
   return CAVITY_OK;
 }
+// dense path (dense.cu): the kept set, the FP32 kept block assembled from the
+// per-axis factors of Sec. 5.2, its LU factors, and one inner solve of the
+// refinement: x += s^-1 (LU)^-1 (s r) on the kept unknowns (s[d] per direction)
+struct KeptSet {
+  int mm, nn, n1, n2, n3, nk;
+};
+KeptSet kept_set(const cavity_desc& d, const Geo& g);
+cavity_status dense_assemble(cavity_ctx* ctx, float2* a, int lda);
+cavity_status dense_lu(cavity_ctx* ctx, float2* a, int n, int lda, int* ipiv, int* info);
+cavity_status dense_lu_solve(cavity_ctx* ctx, const float2* lu, int n, int lda, const int* ipiv,
+                             const int* perm, int nrhs, float2* y, int ldy);
+cavity_status launch_dense_factor(cavity_ctx* ctx);
+size_t dense_inner_work_bytes(const cavity_ctx* ctx, int ndir);
+// the barrier-timeout flag inside dense_inner_solve's work area (nonzero after
+// the stream: a substitution gave up)
+int* dense_inner_err(const cavity_ctx* ctx, int ndir, void* work);
+cavity_status dense_inner_solve(cavity_ctx* ctx, int ndir, const double2* r, const double* s,
+                                double2* x, void* work);
+cavity_status run_dense_solve(cavity_ctx* ctx, int ndir, const double2* b, double2* x,
+                              int* iters, double* resid);
 cavity_status launch_rcs(cavity_ctx* ctx, int ndir, const double2* ap,
                          const double* th, const double* ph, int pol, double* sigma);
+
+// exp(-2 pi i k / n) from the twiddle table tw of length TW (n divides TW)
+static __device__ __forceinline__ double2 tw_at(const double2* __restrict__ tw, int TW, long long k,
+                                                int n) {
+  long long r = k % n;
+  if (r < 0) r += n;
+  return tw[r * (TW / n)];
+}
+// E(d / L) of the basis transform (Sec. 5.2) on the torus of period L = 4 side:
+// (1 - (-i)^d) L / (2 pi i d), and side at d = 0
+static __device__ __forceinline__ double2 eps_d(long long d, double side) {
+  if (d == 0) return make_double2(side, 0.0);
+  int r = (int)(((d % 4) + 4) % 4);
+  double2 num;
+  if (r == 0) num = make_double2(0.0, 0.0);
+  else if (r == 1) num = make_double2(1.0, 1.0);    // 1 - (-i)
+  else if (r == 2) num = make_double2(2.0, 0.0);    // 1 - (-1)
+  else num = make_double2(1.0, -1.0);               // 1 - i
+  double f = 4.0 * side / (2.0 * M_PI * (double)d);
+  return make_double2(num.y * f, -num.x * f);       // num / i * f
+}
 
 // Kernels whose line transforms have compile-time lengths are instantiated for
 // log2 sizes LO..HI; dispatch_log calls f(std::integral_constant<int, v>).

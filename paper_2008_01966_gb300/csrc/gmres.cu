@@ -702,3 +702,85 @@ cavity_status run_mixed_solve(cavity_ctx* ctx, int ndir, const double2* b, doubl
   }
   return CAVITY_OK;
 }
+
+// Dense path (aperture_solver == CAVITY_SOLVER_DENSE): FP64 iterative
+// refinement around the FP32 LU factors of the kept block (dense.cu).  Each
+// step solves with the factors for the scaled residual of the kept rows,
+// adds the correction in FP64, and recomputes r = b - A x with the FP64
+// operator (CAVITY_FP64) or the pair-of-FP32 operator (CAVITY_MIXED), whose
+// rows outside the kept set are zero.  iters counts refinement steps.
+cavity_status run_dense_solve(cavity_ctx* ctx, int ndir, const double2* b, double2* x, int* iters,
+                              double* resid) {
+  const Geo& g = ctx->g;
+  double tol;
+  int m, maxit;
+  solver_params(ctx, tol, m, maxit);
+  auto al = [](size_t v) { return (v + 255) / 256 * 256; };
+  const long long nv = (long long)ndir * g.nap;
+  const bool fp64 = ctx->desc.precision == CAVITY_FP64;
+  const size_t apw = fp64 ? apply_work_bytes(g, ndir, sizeof(double2)) : apply_pair_work_bytes(g, ndir);
+  const size_t need = 2 * al(sizeof(double2) * nv) + al(apw) + al(dense_inner_work_bytes(ctx, ndir)) +
+                      al(sizeof(double) * ndir) + al(sizeof(double2) * ndir) +
+                      al(sizeof(double2) * (size_t)ndir * mdot_chunks(g.nap));
+  CKS(ensure_ws(ctx, &ctx->ws, &ctx->ws_bytes, need));
+  char* p = (char*)ctx->ws;
+  double2* r64 = (double2*)p; p += al(sizeof(double2) * nv);
+  double2* tmp = (double2*)p; p += al(sizeof(double2) * nv);
+  void* apwk = p; p += al(apw);
+  void* inner = p; p += al(dense_inner_work_bytes(ctx, ndir));
+  double* sdev = (double*)p; p += al(sizeof(double) * ndir);
+  double2* sc2 = (double2*)p; p += al(sizeof(double2) * ndir);
+  double2* part = (double2*)p;
+  cudaStream_t st = ctx->stream;
+  CK(cudaMemsetAsync(x, 0, sizeof(double2) * nv, st));
+  CK(cudaMemcpyAsync(r64, b, sizeof(double2) * nv, cudaMemcpyDeviceToDevice, st));
+  std::vector<double> bn, rn, prev;
+  CKS(norms<double>(ctx, b, ndir, sc2, 1, bn, part));
+  rn = bn;
+  std::vector<double> s(ndir);
+  int steps = 0;
+  const int max_steps = std::max(1, std::min(maxit, 30));
+  bool conv = false, stalled = false;
+  for (; steps < max_steps; ++steps) {
+    bool all = true;
+    for (int d = 0; d < ndir; ++d) all = all && (bn[d] == 0 || rn[d] <= tol * bn[d]);
+    if (all) { conv = true; break; }
+    if (stalled) break;
+    for (int d = 0; d < ndir; ++d)
+      s[d] = (bn[d] == 0 || rn[d] <= tol * bn[d] || !(rn[d] > 0)) ? 0.0 : 1.0 / rn[d];
+    CK(cudaMemcpyAsync(sdev, s.data(), sizeof(double) * ndir, cudaMemcpyHostToDevice, st));
+    CKS(dense_inner_solve(ctx, ndir, r64, sdev, x, inner));
+    if (fp64) CKS(launch_apply<double>(ctx, ndir, x, tmp, apwk));
+    else CKS(launch_apply_pair(ctx, ndir, x, tmp, apwk));
+    {
+      KScope ks_(ctx, KC_DENSE_TRS);
+      k_bminus<double><<<nblk(nv, 256), 256, 0, st>>>(b, tmp, nv);
+    }
+    std::swap(r64, tmp);
+    prev = rn;
+    CKS(norms<double>(ctx, r64, ndir, sc2, 1, rn, part));
+    // a step that does not halve some unconverged residual: the factors of
+    // the FP32 block are too inaccurate for this system; stop after it
+    for (int d = 0; d < ndir; ++d)
+      if (s[d] > 0 && rn[d] > 0.5 * prev[d]) stalled = true;
+  }
+  int terr = 0;
+  CK(cudaMemcpyAsync(&terr, dense_inner_err(ctx, ndir, inner), sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (terr) {
+    ctx->err = "dense aperture solve: a grid barrier of the substitution timed out";
+    return CAVITY_ETIMEOUT;
+  }
+  bool all = true;
+  for (int d = 0; d < ndir; ++d) {
+    const double r = bn[d] > 0 ? rn[d] / bn[d] : 0.0;
+    if (iters) iters[d] = steps;
+    if (resid) resid[d] = r;
+    all = all && r <= tol;
+  }
+  if (!(conv || all)) {
+    ctx->err = "dense aperture solve: the refinement stopped above tolerance";
+    return CAVITY_ENOCONV;
+  }
+  return CAVITY_OK;
+}

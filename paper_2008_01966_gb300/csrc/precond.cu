@@ -14,26 +14,6 @@
 // iteration count depends on it, never the solution.
 #include "common.cuh"
 
-// exp(-2 pi i k / n) from the table (n divides TW)
-__device__ __forceinline__ double2 tw_at(const double2* __restrict__ tw, int TW, long long k, int n) {
-  long long r = k % n;
-  if (r < 0) r += n;
-  return tw[r * (TW / n)];
-}
-
-// eps(d) = E(d/L), L = 4 side: (1 - (-i)^d) * L / (2 pi i d), side at d = 0
-__device__ __forceinline__ double2 eps_d(long long d, double side) {
-  if (d == 0) return make_double2(side, 0.0);
-  int r = (int)(((d % 4) + 4) % 4);
-  double2 num;
-  if (r == 0) num = make_double2(0.0, 0.0);
-  else if (r == 1) num = make_double2(1.0, 1.0);    // 1 - (-i)
-  else if (r == 2) num = make_double2(2.0, 0.0);    // 1 - (-1)
-  else num = make_double2(1.0, -1.0);               // 1 - i
-  double f = 4.0 * side / (2.0 * M_PI * (double)d);
-  return make_double2(num.y * f, -num.x * f);       // num / i * f
-}
-
 // Ax[kind][m][j], j in FFT order over the box (Nyquist slot zero)
 __global__ void k_pc_ax(double2* __restrict__ out, int nint, int Pn, double side,
                         const double2* __restrict__ tw, int TW) {
