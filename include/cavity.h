@@ -287,9 +287,17 @@ cavity_status cavity_lu_solve(cavity_ctx* ctx, const void* lu, int n, int lda, c
  *      warp; default), 1 = the block (Stockham) transform.
  *  CAVITY_OPT_GROUP_WIDTH: directions per group of the mixed solve's block
  *      Krylov iterations (one basis per group), 1..16; default 16.
+ *  CAVITY_OPT_COARSE_MODES: two-level preconditioner of the mixed solve's
+ *      inner FP32 iterations (Krylov solver): 0 (default) = the 3 x 3 block
+ *      diagonal of each mode alone; mc > 0 = in addition the kept block of
+ *      the modes m, n <= mc solved exactly with its FP32 LU factors (the
+ *      coarse level, the modes that couple most through the TBC), factored
+ *      at the first mixed solve after cavity_prepare or a change of mc; its
+ *      3 mc^2 + 2 mc unknowns must not exceed CAVITY_DENSE_MAX_N.  Changes
+ *      the iteration count, not the result beyond the solver tolerance.
  * CAVITY_EINVAL for an unknown option or a value out of range. */
 enum { CAVITY_OPT_PASS_B_2048 = 0, CAVITY_OPT_PASS_C_2048 = 1, CAVITY_OPT_GROUP_WIDTH = 2,
-       CAVITY_NUM_OPT = 3 };
+       CAVITY_OPT_COARSE_MODES = 3, CAVITY_NUM_OPT = 4 };
 cavity_status cavity_set_option(cavity_ctx* ctx, int option, int value);
 cavity_status cavity_get_option(const cavity_ctx* ctx, int option, int* value);
 

@@ -293,8 +293,10 @@ class Cavity:
     # ------------------------------------------------------------ options
     def set_option(self, name, value):
         """Implementation option (include/cavity.h, CAVITY_OPT_*): "pass_b_2048",
-        "pass_c_2048" (0 warp pairs, 1 block transform) or "group_width"
-        (1..16 directions per block Krylov group)."""
+        "pass_c_2048" (0 warp pairs, 1 block transform), "group_width"
+        (1..16 directions per block Krylov group) or "coarse_modes" (0, or
+        mc > 0: the mixed solve's two-level preconditioner with the exact
+        solve of the modes m, n <= mc as its coarse level)."""
         self._check(self.lib.cavity_set_option(self.h, _lib.OPTIONS[name], int(value)))
 
     def get_option(self, name):

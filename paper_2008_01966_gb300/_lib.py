@@ -29,9 +29,10 @@ EXPORTS = ["cavity_setup", "cavity_prepare", "cavity_solve", "cavity_rcs", "cavi
 CAVITY_SOLVER_KRYLOV, CAVITY_SOLVER_DENSE = 0, 1
 SOLVERS = {"krylov": CAVITY_SOLVER_KRYLOV, "dense": CAVITY_SOLVER_DENSE}
 DENSE_MAX_N = 16384
-CAVITY_OPT_PASS_B_2048, CAVITY_OPT_PASS_C_2048, CAVITY_OPT_GROUP_WIDTH = range(3)
+CAVITY_OPT_PASS_B_2048, CAVITY_OPT_PASS_C_2048, CAVITY_OPT_GROUP_WIDTH, \
+    CAVITY_OPT_COARSE_MODES = range(4)
 OPTIONS = {"pass_b_2048": CAVITY_OPT_PASS_B_2048, "pass_c_2048": CAVITY_OPT_PASS_C_2048,
-           "group_width": CAVITY_OPT_GROUP_WIDTH}
+           "group_width": CAVITY_OPT_GROUP_WIDTH, "coarse_modes": CAVITY_OPT_COARSE_MODES}
 NUM_KCLASS = 24
 
 

@@ -98,10 +98,11 @@ extern "C" void cavity_destroy(cavity_ctx* ctx) {
                   ctx->top64, ctx->top32, ctx->pinv64, ctx->pinv32, ctx->prof32, ctx->profq32,
                   ctx->minpiv, ctx->ws, ctx->ws2, ctx->stage, ctx->tw_p, ctx->ehat_xp[0],
                   ctx->ehat_xp[1], ctx->ehat_yp[0], ctx->ehat_yp[1], ctx->khat_p, ctx->top_p, ctx->prof_rec,
-                  ctx->dn_a, ctx->dn_ipiv, ctx->dn_perm, ctx->dn_map, ctx->dn_scr,
-                  ctx->dn_dinv};
+                  ctx->dn_scr};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  dense_free(ctx->dn);
+  dense_free(ctx->cs);
   if (ctx->pin) cudaFreeHost(ctx->pin);
   for (auto e : ctx->copy_evs) cudaEventDestroy(e);
   if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
@@ -171,7 +172,8 @@ extern "C" cavity_status cavity_prepare(cavity_ctx* ctx, double kappa0, int nlay
              L[l].eps_im == ctx->layers[l].eps_im;
   if (same) return CAVITY_OK;
   ctx->prepared = false;
-  ctx->dn_ready = false;
+  ctx->dn.ready = false;
+  ctx->cs.ready = false;
   bool kappa_same = ctx->khat64 && ctx->kappa0 == kappa0;
   const bool was_layered = ctx->layers.size() > 1;
   ctx->kappa0 = kappa0;
@@ -449,7 +451,7 @@ extern "C" cavity_status cavity_dense_assemble(cavity_ctx* ctx, void* a, int lda
     ctx->err = "cavity_dense_assemble: a is NULL";
     return CAVITY_EINVAL;
   }
-  CKS(dense_assemble(ctx, (float2*)a, lda));
+  CKS(dense_assemble(ctx, kept_set(ctx->desc, ctx->g), (float2*)a, lda));
   CK(cudaStreamSynchronize(ctx->stream));
   return CAVITY_OK;
 }
@@ -476,6 +478,14 @@ extern "C" cavity_status cavity_set_option(cavity_ctx* ctx, int option, int valu
     case CAVITY_OPT_PASS_B_2048:
     case CAVITY_OPT_PASS_C_2048: ok = value == 0 || value == 1; break;
     case CAVITY_OPT_GROUP_WIDTH: ok = value >= 1 && value <= 16; break;
+    case CAVITY_OPT_COARSE_MODES: {
+      const KeptSet all = kept_set(ctx->desc, ctx->g);
+      ok = value == 0 ||
+           (value > 0 && kept_set_of(std::min(value, all.mm), std::min(value, all.nn)).nk <=
+                             CAVITY_DENSE_MAX_N);
+      if (ok && value != ctx->opt[option]) ctx->cs.ready = false;
+      break;
+    }
     default: break;
   }
   if (!ok) {

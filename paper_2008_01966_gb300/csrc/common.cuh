@@ -93,6 +93,27 @@ struct LayerDev {
   double eps_re, eps_im;
 };
 
+// kept block of the aperture system: the modes m <= mm, n <= nn
+struct KeptSet {
+  int mm, nn, n1, n2, n3, nk;
+};
+
+// FP32 LU factors of a kept block (row-major, leading dimension lda), the row
+// permutation, the inverted 64 x 64 diagonal blocks of L and U, the map from
+// kept (compact) to full unknown indices, and a work area for its solves
+struct DenseLU {
+  KeptSet ks{};
+  int n = 0, lda = 0;
+  bool ready = false;
+  float2* a = nullptr;
+  float2* dinv = nullptr;
+  int* ipiv = nullptr;
+  int* perm = nullptr;
+  int* map = nullptr;
+  void* work = nullptr;
+  size_t work_bytes = 0;
+};
+
 // The resident device state of one context.
 struct cavity_ctx {
   Geo g;
@@ -154,21 +175,15 @@ struct cavity_ctx {
   cudaStream_t copy_more[3] = {nullptr, nullptr, nullptr};  // further copy engines
   cudaEvent_t copy_join[3] = {nullptr, nullptr, nullptr};
 
-  // ---- dense solve of the kept block (aperture_solver == CAVITY_SOLVER_DENSE):
-  // FP32 LU factors (row-major, leading dimension dn_lda) with the row
-  // permutation, and the map from kept (compact) to full unknown indices
-  int dn_n = 0, dn_lda = 0;
-  bool dn_ready = false;
-  float2* dn_a = nullptr;
-  float2* dn_dinv = nullptr;  // inverted 64 x 64 diagonal blocks of L and U
-  int* dn_ipiv = nullptr;
-  int* dn_perm = nullptr;
-  int* dn_map = nullptr;
+  // ---- dense LU factors of a kept block: the direct solver's (kept set of
+  // modes_m, modes_n; aperture_solver == CAVITY_SOLVER_DENSE) and the coarse
+  // level of the two-level preconditioner (modes m, n <= CAVITY_OPT_COARSE_MODES)
+  DenseLU dn, cs;
   void* dn_scr = nullptr;     // LU scratch (pivot candidates, barrier counters)
   size_t dn_scr_bytes = 0;
 
   // ---- implementation options (cavity_set_option)
-  int opt[CAVITY_NUM_OPT] = {0, 0, 16};
+  int opt[CAVITY_NUM_OPT] = {0, 0, 16, 0};
 
   // ---- launch accounting: counts always, CUDA-event times while timing is on
   long long nlaunch[KC_N] = {0};
@@ -365,11 +380,18 @@ inline cavity_status ensure_copy_stream(cavity_ctx* ctx, size_t n) {
 // dense path (dense.cu): the kept set, the FP32 kept block assembled from the
 // per-axis factors of Sec. 5.2, its LU factors, and one inner solve of the
 // refinement: x += s^-1 (LU)^-1 (s r) on the kept unknowns (s[d] per direction)
-struct KeptSet {
-  int mm, nn, n1, n2, n3, nk;
-};
 KeptSet kept_set(const cavity_desc& d, const Geo& g);
-cavity_status dense_assemble(cavity_ctx* ctx, float2* a, int lda);
+KeptSet kept_set_of(int mm, int nn);
+cavity_status dense_assemble(cavity_ctx* ctx, const KeptSet& ks, float2* a, int lda);
+// assemble and factor the kept block ks into f (kept resident until destroy)
+cavity_status dense_factor(cavity_ctx* ctx, DenseLU& f, const KeptSet& ks);
+void dense_free(DenseLU& f);
+// the coarse level of the mixed solver's preconditioner: factors it when
+// CAVITY_OPT_COARSE_MODES > 0 and it is missing; y <- A_cc^{-1} x on the
+// coarse unknowns of ndir FP32 vectors (other unknowns untouched)
+cavity_status coarse_prepare(cavity_ctx* ctx);
+cavity_status coarse_correct(cavity_ctx* ctx, int ndir, const float2* x, long long xs, float2* y,
+                             long long ys);
 cavity_status dense_lu(cavity_ctx* ctx, float2* a, int n, int lda, int* ipiv, int* info);
 cavity_status dense_lu_solve(cavity_ctx* ctx, const float2* lu, int n, int lda, const int* ipiv,
                              const int* perm, int nrhs, float2* y, int ldy);

@@ -36,9 +36,12 @@
 
 // ------------------------------------------------------------ kept set
 KeptSet kept_set(const cavity_desc& d, const Geo& g) {
+  return kept_set_of(d.modes_m > 0 ? d.modes_m : g.M, d.modes_n > 0 ? d.modes_n : g.N);
+}
+KeptSet kept_set_of(int mm, int nn) {
   KeptSet k;
-  k.mm = d.modes_m > 0 ? d.modes_m : g.M;
-  k.nn = d.modes_n > 0 ? d.modes_n : g.N;
+  k.mm = mm;
+  k.nn = nn;
   k.n1 = (k.mm + 1) * k.nn;
   k.n2 = k.mm * (k.nn + 1);
   k.n3 = k.mm * k.nn;
@@ -276,13 +279,12 @@ __global__ void k_dn_assemble(const float2* __restrict__ Ics, const float2* __re
 
 static size_t al256(size_t v) { return (v + 255) / 256 * 256; }
 
-cavity_status dense_assemble(cavity_ctx* ctx, float2* a, int lda) {
+cavity_status dense_assemble(cavity_ctx* ctx, const KeptSet& ks, float2* a, int lda) {
   const Geo& g = ctx->g;
   if (!ctx->prepared) {
     ctx->err = "dense assembly: call cavity_prepare first";
     return CAVITY_EINVAL;
   }
-  const KeptSet ks = kept_set(ctx->desc, g);
   if (ks.nk > CAVITY_DENSE_MAX_N || lda < ks.nk) {
     ctx->err = "dense assembly: kept block of " + std::to_string(ks.nk) +
                " unknowns exceeds the limit, or lda too small";
@@ -963,50 +965,55 @@ cavity_status dense_lu_solve(cavity_ctx* ctx, const float2* lu, int n, int lda, 
 }
 
 // ------------------------------------------------------------ the dense path
-cavity_status launch_dense_factor(cavity_ctx* ctx) {
+void dense_free(DenseLU& f) {
+  void* ptrs[] = {f.a, f.dinv, f.ipiv, f.perm, f.map, f.work};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  f = DenseLU();
+}
+
+cavity_status dense_factor(cavity_ctx* ctx, DenseLU& f, const KeptSet& ks) {
   const Geo& g = ctx->g;
-  const KeptSet ks = kept_set(ctx->desc, g);
-  ctx->dn_ready = false;
+  f.ready = false;
   if (ks.nk > CAVITY_DENSE_MAX_N) {
-    ctx->err = "dense aperture solve: the kept block has " + std::to_string(ks.nk) +
+    ctx->err = "dense kept block of " + std::to_string(ks.nk) +
                " unknowns, more than CAVITY_DENSE_MAX_N";
     return CAVITY_EINVAL;
   }
   const int lda = (ks.nk + 3) / 4 * 4;
-  if (ctx->dn_n != ks.nk || !ctx->dn_a) {
-    if (ctx->dn_a) cudaFree(ctx->dn_a);
-    if (ctx->dn_ipiv) cudaFree(ctx->dn_ipiv);
-    if (ctx->dn_perm) cudaFree(ctx->dn_perm);
-    if (ctx->dn_map) cudaFree(ctx->dn_map);
-    if (ctx->dn_dinv) cudaFree(ctx->dn_dinv);
-    ctx->dn_a = ctx->dn_dinv = nullptr;
-    ctx->dn_ipiv = ctx->dn_perm = ctx->dn_map = nullptr;
-    ctx->dn_n = 0;
-    cudaError_t e = cudaMalloc(&ctx->dn_a, sizeof(float2) * (size_t)ks.nk * lda);
-    if (e == cudaSuccess) e = cudaMalloc(&ctx->dn_ipiv, sizeof(int) * ks.nk);
-    if (e == cudaSuccess) e = cudaMalloc(&ctx->dn_perm, sizeof(int) * ks.nk);
-    if (e == cudaSuccess) e = cudaMalloc(&ctx->dn_map, sizeof(int) * ks.nk);
-    if (e == cudaSuccess) e = cudaMalloc(&ctx->dn_dinv, dinv_bytes(ks.nk));
+  if (f.n != ks.nk || f.ks.mm != ks.mm || f.ks.nn != ks.nn || !f.a) {
+    dense_free(f);
+    cudaError_t e = cudaMalloc(&f.a, sizeof(float2) * (size_t)ks.nk * lda);
+    if (e == cudaSuccess) e = cudaMalloc(&f.ipiv, sizeof(int) * ks.nk);
+    if (e == cudaSuccess) e = cudaMalloc(&f.perm, sizeof(int) * ks.nk);
+    if (e == cudaSuccess) e = cudaMalloc(&f.map, sizeof(int) * ks.nk);
+    if (e == cudaSuccess) e = cudaMalloc(&f.dinv, dinv_bytes(ks.nk));
     if (e != cudaSuccess) {
-      ctx->err = std::string("dense aperture solve: allocation failed: ") + cudaGetErrorString(e);
+      dense_free(f);
+      ctx->err = std::string("dense kept block: allocation failed: ") + cudaGetErrorString(e);
       return CAVITY_ENOMEM;
     }
     const std::vector<int> map = kept_map(ks, g);
-    CK(cudaMemcpy(ctx->dn_map, map.data(), sizeof(int) * ks.nk, cudaMemcpyHostToDevice));
-    ctx->dn_n = ks.nk;
-    ctx->dn_lda = lda;
+    CK(cudaMemcpy(f.map, map.data(), sizeof(int) * ks.nk, cudaMemcpyHostToDevice));
+    f.ks = ks;
+    f.n = ks.nk;
+    f.lda = lda;
   }
-  CKS(dense_assemble(ctx, ctx->dn_a, lda));
+  CKS(dense_assemble(ctx, ks, f.a, lda));
   int info = -1;
-  CKS(dense_lu(ctx, ctx->dn_a, ks.nk, lda, ctx->dn_ipiv, &info));
+  CKS(dense_lu(ctx, f.a, ks.nk, lda, f.ipiv, &info));
   {
     KScope ks_(ctx, KC_DENSE_LU);
-    k_lu_perm<<<1, 256, sizeof(int) * ks.nk, ctx->stream>>>(ctx->dn_ipiv, ctx->dn_perm, ks.nk);
+    k_lu_perm<<<1, 256, sizeof(int) * ks.nk, ctx->stream>>>(f.ipiv, f.perm, ks.nk);
   }
   CK(cudaGetLastError());
-  CKS(launch_dinv(ctx, ctx->dn_a, ks.nk, lda, ctx->dn_dinv));
-  ctx->dn_ready = true;
+  CKS(launch_dinv(ctx, f.a, ks.nk, lda, f.dinv));
+  f.ready = true;
   return CAVITY_OK;
+}
+
+cavity_status launch_dense_factor(cavity_ctx* ctx) {
+  return dense_factor(ctx, ctx->dn, kept_set(ctx->desc, ctx->g));
 }
 
 // Y[d][i] = (float) (s[d] r[d][map[perm[i]]])  (grid (ceil(nk/256), ndir))
@@ -1030,6 +1037,48 @@ __global__ void k_dn_scatter(double2* __restrict__ x, int nap, const int* __rest
   o->y += f * (double)v.y;
 }
 
+// y[d][map[perm^-1 ...]]: the coarse correction overwrites the coarse
+// unknowns of y with the solution for the coarse unknowns of x
+__global__ void k_cs_gather(const float2* __restrict__ x, long long xs, const int* __restrict__ map,
+                            const int* __restrict__ perm, float2* __restrict__ Y, int nk) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, d = blockIdx.y;
+  if (i < nk) Y[(size_t)d * nk + i] = x[(size_t)d * xs + map[perm[i]]];
+}
+__global__ void k_cs_put(const float2* __restrict__ Y, const int* __restrict__ map,
+                         float2* __restrict__ y, long long ys, int nk) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, d = blockIdx.y;
+  if (i < nk) y[(size_t)d * ys + map[i]] = Y[(size_t)d * nk + i];
+}
+
+cavity_status coarse_prepare(cavity_ctx* ctx) {
+  const int mc = ctx->opt[CAVITY_OPT_COARSE_MODES];
+  if (mc <= 0 || ctx->cs.ready) return CAVITY_OK;
+  const KeptSet all = kept_set(ctx->desc, ctx->g);
+  return dense_factor(ctx, ctx->cs, kept_set_of(std::min(mc, all.mm), std::min(mc, all.nn)));
+}
+
+cavity_status coarse_correct(cavity_ctx* ctx, int ndir, const float2* x, long long xs, float2* y,
+                             long long ys) {
+  DenseLU& f = ctx->cs;
+  if (!f.ready || ctx->opt[CAVITY_OPT_COARSE_MODES] <= 0) return CAVITY_OK;
+  const size_t need = al256(sizeof(float2) * (size_t)f.n * ndir) + subst_scratch_bytes(ndir);
+  CKS(ensure_ws(ctx, &f.work, &f.work_bytes, need));
+  float2* Y = (float2*)f.work;
+  cudaStream_t st = ctx->stream;
+  {
+    KScope ks_(ctx, KC_DENSE_TRS);
+    k_cs_gather<<<dim3(nblk(f.n, 256), ndir), 256, 0, st>>>(x, xs, f.map, f.perm, Y, f.n);
+  }
+  CKS(lu_substitute(ctx, f.a, f.n, f.lda, f.dinv, ndir, Y, f.n,
+                    (char*)f.work + al256(sizeof(float2) * (size_t)f.n * ndir)));
+  {
+    KScope ks_(ctx, KC_DENSE_TRS);
+    k_cs_put<<<dim3(nblk(f.n, 256), ndir), 256, 0, st>>>(Y, f.map, y, ys, f.n);
+  }
+  CK(cudaGetLastError());
+  return CAVITY_OK;
+}
+
 size_t dense_inner_work_bytes(const cavity_ctx* ctx, int ndir) {
   const KeptSet ks = kept_set(ctx->desc, ctx->g);
   return al256(sizeof(float2) * (size_t)ks.nk * ndir) + subst_scratch_bytes(ndir);
@@ -1043,23 +1092,23 @@ int* dense_inner_err(const cavity_ctx* ctx, int ndir, void* work) {
 
 cavity_status dense_inner_solve(cavity_ctx* ctx, int ndir, const double2* r, const double* s,
                                 double2* x, void* work) {
-  if (!ctx->dn_ready) {
+  if (!ctx->dn.ready) {
     ctx->err = "dense aperture solve: no factorisation (cavity_prepare with the dense solver)";
     return CAVITY_EINVAL;
   }
-  const int nk = ctx->dn_n;
+  const int nk = ctx->dn.n;
   float2* Y = (float2*)work;
   cudaStream_t st = ctx->stream;
   {
     KScope ks_(ctx, KC_DENSE_TRS);
-    k_dn_gather<<<dim3(nblk(nk, 256), ndir), 256, 0, st>>>(r, ctx->g.nap, ctx->dn_map, ctx->dn_perm, s,
+    k_dn_gather<<<dim3(nblk(nk, 256), ndir), 256, 0, st>>>(r, ctx->g.nap, ctx->dn.map, ctx->dn.perm, s,
                                                           Y, nk);
   }
-  CKS(lu_substitute(ctx, ctx->dn_a, nk, ctx->dn_lda, ctx->dn_dinv, ndir, Y, nk,
+  CKS(lu_substitute(ctx, ctx->dn.a, nk, ctx->dn.lda, ctx->dn.dinv, ndir, Y, nk,
                     (char*)work + al256(sizeof(float2) * (size_t)nk * ndir)));
   {
     KScope ks_(ctx, KC_DENSE_TRS);
-    k_dn_scatter<<<dim3(nblk(nk, 256), ndir), 256, 0, st>>>(x, ctx->g.nap, ctx->dn_map, s, Y, nk);
+    k_dn_scatter<<<dim3(nblk(nk, 256), ndir), 256, 0, st>>>(x, ctx->g.nap, ctx->dn.map, s, Y, nk);
   }
   CK(cudaGetLastError());
   return CAVITY_OK;

@@ -628,6 +628,7 @@ cavity_status run_mixed_solve(cavity_ctx* ctx, int ndir, const double2* b, doubl
   double2* part = (double2*)p;
   cudaStream_t st = ctx->stream;
   std::vector<double> bn, rn;
+  CKS(coarse_prepare(ctx));
   CK(cudaMemsetAsync(x, 0, sizeof(double2) * nv, st));
   CK(cudaMemcpyAsync(r64, b, sizeof(double2) * nv, cudaMemcpyDeviceToDevice, st));
   CKS(norms<double>(ctx, b, ndir, sc2, 1, bn, part));

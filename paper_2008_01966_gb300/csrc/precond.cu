@@ -245,6 +245,9 @@ cavity_status launch_precond_apply(cavity_ctx* ctx, int ndir, const C<T>* x, C<T
         g.ny, g.n1, g.n2, g.nap, ndir);
   }
   CK(cudaGetLastError());
+  // two-level variant (FP32 inner solves of the mixed path): the coarse
+  // unknowns take the exact solve of the coarse block instead
+  if constexpr (std::is_same<T, float>::value) CKS(coarse_correct(ctx, ndir, x, xs, y, ys));
   return CAVITY_OK;
 }
 

@@ -180,3 +180,25 @@ def test_dense_and_krylov_agree_on_a_truncated_256_grid(gb):
         g.close()
     for d in range(nd):
         assert rel(sols["dense"][d], sols["krylov"][d]) < 1e-10
+
+
+def test_two_level_preconditioner_same_solution_fewer_steps(gb):
+    """The mixed solve's two-level preconditioner (coarse level: the exact
+    solve of the modes m, n <= 24 by their LU factors) on a layered 128 x 128
+    cavity: the same solution as the one-level preconditioner within the
+    solver tolerance, in fewer block steps."""
+    w = workloads.scaled("layered4", 128, nz=64, ndir=8)
+    out = {}
+    for mc in (0, 24):
+        g = gb.Cavity(w['a'], w['b'], w['c'], w['nx'], w['ny'], w['nz'], precision="mixed",
+                      gmres_tol=1e-10)
+        g.set_option("coarse_modes", mc)
+        assert g.get_option("coarse_modes") == mc
+        ap, _, it, res = g.solve(w['kappa0'], w['layers'], w['theta'], w['phi'], w['alpha'],
+                                 field=False)
+        assert np.all(np.asarray(res) <= 1e-10), (mc, res)
+        out[mc] = (ap.cpu().numpy(), np.asarray(it))
+        g.close()
+    for d in range(len(w['theta'])):
+        assert rel(out[24][0][d], out[0][0][d]) < 1e-8
+    assert out[24][1].max() < out[0][1].max(), (out[0][1], out[24][1])
