@@ -101,15 +101,28 @@ typedef struct {
                          /*   modes_m, n <= modes_n), assembled once per        */
                          /*   cavity_prepare from the per-axis factors of       */
                          /*   Sec. 5.2 and LU-factored with partial pivoting in */
-                         /*   FP32; each solve refines x in FP64 with the FFT   */
-                         /*   operator's residual (FP64 operator for           */
-                         /*   CAVITY_FP64, pair-of-FP32 for CAVITY_MIXED), so  */
-                         /*   the result meets gmres_tol like the Krylov path. */
+                         /*   FP32; each solve refines x in FP64, the residual */
+                         /*   from the block kept in FP64 (CAVITY_FP64, and    */
+                         /*   the Parseval rule) or from the pair-of-FP32 FFT  */
+                         /*   operator (CAVITY_MIXED), so the result meets     */
+                         /*   gmres_tol like the Krylov path.                  */
                          /*   The kept block must have at most                 */
                          /*   CAVITY_DENSE_MAX_N unknowns (3 mm nn + mm + nn)  */
+  int outer_rule;        /* outer integral of the TBC coefficients (Sec. 5.2): */
+                         /* CAVITY_OUTER_TRAPEZOID (0): the trapezoid rule on  */
+                         /*   the aperture nodes (rule D; every solver);       */
+                         /* CAVITY_OUTER_PARSEVAL (1): exact by Parseval's     */
+                         /*   identity on the torus -- each TBC block becomes  */
+                         /*   Phi^H diag(F(G)) Phi, complex symmetric; dense   */
+                         /*   solver only (the block is assembled in FP64 and  */
+                         /*   also supplies the refinement's residual); the    */
+                         /*   operator calls cavity_apply and                  */
+                         /*   cavity_apply_noalloc apply rule D whatever this  */
+                         /*   field says                                       */
 } cavity_desc;
 enum { CAVITY_KHAT_QUADRATURE = 0, CAVITY_KHAT_PAPER = 1 };
 enum { CAVITY_SOLVER_KRYLOV = 0, CAVITY_SOLVER_DENSE = 1 };
+enum { CAVITY_OUTER_TRAPEZOID = 0, CAVITY_OUTER_PARSEVAL = 1 };
 #define CAVITY_DENSE_MAX_N 16384
 
 /* Create a context for one cavity geometry and grid.  `cuda_stream` is a

@@ -68,7 +68,8 @@ class Cavity:
 
     def __init__(self, a, b, c, nx, ny, nz, precision="fp64", gmres_tol=0.0, gmres_restart=0,
                  gmres_max_iter=0, pivot_tol=0.0, stream=None, device=None,
-                 khat_scheme="quadrature", modes_m=0, modes_n=0, aperture_solver="krylov"):
+                 khat_scheme="quadrature", modes_m=0, modes_n=0, aperture_solver="krylov",
+                 outer_rule="trapezoid"):
         self.lib = _lib.load()
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
         torch.cuda.set_device(self.device)
@@ -77,7 +78,7 @@ class Cavity:
         d = _lib.CavityDesc(a, b, c, nx, ny, nz, self.precision, 4, gmres_tol, gmres_restart,
                             gmres_max_iter, pivot_tol,
                             {"quadrature": 0, "paper": 1}[khat_scheme], modes_m, modes_n,
-                            _lib.SOLVERS[aperture_solver])
+                            _lib.SOLVERS[aperture_solver], _lib.OUTER_RULES[outer_rule])
         h = ctypes.c_void_p()
         st = self.lib.cavity_setup(ctypes.byref(d), ctypes.c_void_p(self.stream.cuda_stream),
                                    ctypes.byref(h))

@@ -28,6 +28,7 @@ EXPORTS = ["cavity_setup", "cavity_prepare", "cavity_solve", "cavity_rcs", "cavi
            "cavity_dense_size", "cavity_dense_assemble", "cavity_lu_factor", "cavity_lu_solve"]
 CAVITY_SOLVER_KRYLOV, CAVITY_SOLVER_DENSE = 0, 1
 SOLVERS = {"krylov": CAVITY_SOLVER_KRYLOV, "dense": CAVITY_SOLVER_DENSE}
+OUTER_RULES = {"trapezoid": 0, "parseval": 1}
 DENSE_MAX_N = 16384
 CAVITY_OPT_PASS_B_2048, CAVITY_OPT_PASS_C_2048, CAVITY_OPT_GROUP_WIDTH, \
     CAVITY_OPT_COARSE_MODES = range(4)
@@ -43,7 +44,7 @@ class CavityDesc(ctypes.Structure):
                 ("gmres_tol", ctypes.c_double), ("gmres_restart", ctypes.c_int),
                 ("gmres_max_iter", ctypes.c_int), ("pivot_tol", ctypes.c_double),
                 ("khat_scheme", ctypes.c_int), ("modes_m", ctypes.c_int), ("modes_n", ctypes.c_int),
-                ("aperture_solver", ctypes.c_int)]
+                ("aperture_solver", ctypes.c_int), ("outer_rule", ctypes.c_int)]
 
 
 class CavityError(RuntimeError):

@@ -46,6 +46,10 @@ extern "C" cavity_status cavity_setup(const cavity_desc* desc, void* cuda_stream
     return bad("modes_m, modes_n must be in [0, nx-1], [0, ny-1]");
   if (d.aperture_solver != CAVITY_SOLVER_KRYLOV && d.aperture_solver != CAVITY_SOLVER_DENSE)
     return bad("aperture_solver must be CAVITY_SOLVER_KRYLOV or CAVITY_SOLVER_DENSE");
+  if (d.outer_rule != CAVITY_OUTER_TRAPEZOID && d.outer_rule != CAVITY_OUTER_PARSEVAL)
+    return bad("outer_rule must be CAVITY_OUTER_TRAPEZOID or CAVITY_OUTER_PARSEVAL");
+  if (d.outer_rule == CAVITY_OUTER_PARSEVAL && d.aperture_solver != CAVITY_SOLVER_DENSE)
+    return bad("the Parseval outer rule is implemented by the dense solver only");
   if (d.aperture_solver == CAVITY_SOLVER_DENSE) {
     const long long mm = d.modes_m > 0 ? d.modes_m : d.nx - 1, nn = d.modes_n > 0 ? d.modes_n : d.ny - 1;
     if (3 * mm * nn + mm + nn > CAVITY_DENSE_MAX_N)

@@ -106,6 +106,7 @@ struct DenseLU {
   int n = 0, lda = 0;
   bool ready = false;
   float2* a = nullptr;
+  double2* a64 = nullptr;   // the block in FP64 (residuals of the refinement), or null
   float2* dinv = nullptr;
   int* ipiv = nullptr;
   int* perm = nullptr;
@@ -384,7 +385,11 @@ KeptSet kept_set(const cavity_desc& d, const Geo& g);
 KeptSet kept_set_of(int mm, int nn);
 cavity_status dense_assemble(cavity_ctx* ctx, const KeptSet& ks, float2* a, int lda);
 // assemble and factor the kept block ks into f (kept resident until destroy)
-cavity_status dense_factor(cavity_ctx* ctx, DenseLU& f, const KeptSet& ks);
+cavity_status dense_factor(cavity_ctx* ctx, DenseLU& f, const KeptSet& ks, bool keep64 = false);
+// r = b - A x on the kept rows of the solver's block in FP64 (ndir vectors of
+// length n_ap; rows outside the kept set are not written)
+cavity_status dense_residual(cavity_ctx* ctx, int ndir, const double2* b, const double2* x,
+                             double2* r);
 void dense_free(DenseLU& f);
 // the coarse level of the mixed solver's preconditioner: factors it when
 // CAVITY_OPT_COARSE_MODES > 0 and it is missing; y <- A_cc^{-1} x on the

@@ -104,19 +104,23 @@ __global__ void k_dn_phi(double2* __restrict__ Phi, int mk, int Pn, double side)
   }
 }
 
-// Af[kind][m * mk + k][ja] = sum over j1 = +-ja of X(m, j1) Phi(j1, k), ja < Pn/2
-// (FP32); grid (mk * mk * ceil(Pn/2 / 256), 1, 2)
+// Af[kind][m * mk + k][ja] = sum over j1 = +-ja of X(m, j1) Phi(j1, k), ja < Pn/2;
+// with conj_x, X(m, j1) = conj(Phi(j1, m)) (the outer integral taken exactly by
+// Parseval's identity: the test function transformed like the trial function);
+// grid (mk * mk * ceil(Pn/2 / 256), 1, 2)
+template <typename T>
 __global__ void k_dn_fold(const double2* __restrict__ X, const double2* __restrict__ Phi,
-                          float2* __restrict__ Af, int mk, int Pn) {
+                          C<T>* __restrict__ Af, int mk, int Pn, int conj_x) {
   const int H = Pn / 2, hb = (H + 255) / 256;
   const int kind = blockIdx.z, mkk = blockIdx.x / hb, m = mkk / mk, k = mkk % mk;
   const int ja = (blockIdx.x % hb) * blockDim.x + threadIdx.x;
   if (ja >= H) return;
-  const double2* x = X + ((size_t)kind * mk + m) * Pn;
+  const double2* x = (conj_x ? Phi : X) + ((size_t)kind * mk + m) * Pn;
   const double2* f = Phi + ((size_t)kind * mk + k) * Pn;
-  double2 r = cmul<double>(x[ja], f[ja]);
-  if (ja > 0) r = cadd<double>(r, cmul<double>(x[Pn - ja], f[Pn - ja]));
-  Af[((size_t)kind * mk * mk + mkk) * H + ja] = to_f(r);
+  auto xv = [&](int j) { return conj_x ? cconj<double>(x[j]) : x[j]; };
+  double2 r = cmul<double>(xv(ja), f[ja]);
+  if (ja > 0) r = cadd<double>(r, cmul<double>(xv(Pn - ja), f[Pn - ja]));
+  Af[((size_t)kind * mk * mk + mkk) * H + ja] = conv<T>(r);
 }
 
 // ------------------------------------------------------------ complex GEMM (FP32)
@@ -127,17 +131,18 @@ __global__ void k_dn_fold(const double2* __restrict__ X, const double2* __restri
 #define GM_BM 128
 #define GM_BN 64
 #define GM_BK 16
-struct GemmArgs {
-  const float2* A;
+template <typename T> struct GemmArgsT {
+  const C<T>* A;
   long long sar, sak;
-  const float2* B;
+  const C<T>* B;
   long long sbk, sbc;
-  float2* C;
+  C<T>* C;
   long long ldc;
   int M, N, K;
-  float alpha;
+  T alpha;
   int beta;
 };
+typedef GemmArgsT<float> GemmArgs;
 
 __global__ void __launch_bounds__(256, 2) k_cgemm(GemmArgs g) {
   __shared__ float2 As[GM_BK][GM_BM + 1];
@@ -203,6 +208,74 @@ __global__ void __launch_bounds__(256, 2) k_cgemm(GemmArgs g) {
   }
 }
 
+// The same in FP64: 64 x 64 outputs per CTA of 256 threads (4 x 4 per thread)
+#define GZ_BM 64
+#define GZ_BN 64
+#define GZ_BK 16
+__global__ void __launch_bounds__(256, 2) k_zgemm(GemmArgsT<double> g) {
+  __shared__ double2 As[GZ_BK][GZ_BM + 1];
+  __shared__ double2 Bs[GZ_BK][GZ_BN + 1];
+  const int t = threadIdx.x, tr = t >> 4, tc = t & 15;
+  const int i0 = blockIdx.y * GZ_BM, j0 = blockIdx.x * GZ_BN;
+  double2 acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = make_double2(0.0, 0.0);
+  const bool ak = g.sak == 1, bc = g.sbc == 1;
+  for (int kb = 0; kb < g.K; kb += GZ_BK) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = t + q * 256;
+      const int r = ak ? e >> 4 : e & (GZ_BM - 1), k = ak ? e & 15 : e >> 6;
+      const int gi = i0 + r, gk = kb + k;
+      As[k][r] = (gi < g.M && gk < g.K) ? g.A[gi * g.sar + gk * g.sak] : make_double2(0.0, 0.0);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = t + q * 256;
+      const int c = bc ? e & (GZ_BN - 1) : e >> 4, k = bc ? e >> 6 : e & 15;
+      const int gj = j0 + c, gk = kb + k;
+      Bs[k][c] = (gj < g.N && gk < g.K) ? g.B[gk * g.sbk + gj * g.sbc] : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int k = 0; k < GZ_BK; ++k) {
+      double2 a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[k][tr + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[k][tc + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          acc[i][j].x = fma(a[i].x, b[j].x, fma(-a[i].y, b[j].y, acc[i][j].x));
+          acc[i][j].y = fma(a[i].x, b[j].y, fma(a[i].y, b[j].x, acc[i][j].y));
+        }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int gi = i0 + tr + 16 * i;
+    if (gi >= g.M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int gj = j0 + tc + 16 * j;
+      if (gj >= g.N) continue;
+      double2* c = g.C + gi * g.ldc + gj;
+      double2 v = make_double2(g.alpha * acc[i][j].x, g.alpha * acc[i][j].y);
+      if (g.beta) {
+        const double2 o = *c;
+        v.x += o.x;
+        v.y += o.y;
+      }
+      *c = v;
+    }
+  }
+}
+
 static cavity_status cgemm(cavity_ctx* ctx, const GemmArgs& a, int cls) {
   if (a.M <= 0 || a.N <= 0) return CAVITY_OK;
   KScope ks_(ctx, cls);
@@ -210,8 +283,18 @@ static cavity_status cgemm(cavity_ctx* ctx, const GemmArgs& a, int cls) {
   CK(cudaGetLastError());
   return CAVITY_OK;
 }
+static cavity_status cgemm(cavity_ctx* ctx, const GemmArgsT<double>& a, int cls) {
+  if (a.M <= 0 || a.N <= 0) return CAVITY_OK;
+  KScope ks_(ctx, cls);
+  k_zgemm<<<dim3(nblk(a.N, GZ_BN), nblk(a.M, GZ_BM)), 256, 0, ctx->stream>>>(a);
+  CK(cudaGetLastError());
+  return CAVITY_OK;
+}
 
 // ------------------------------------------------------------ kept block
+__device__ __forceinline__ double2 to_d2(float2 a) { return to_d(a); }
+__device__ __forceinline__ double2 to_d2(double2 a) { return a; }
+
 struct AsmP {
   int nk, n1k, n2k, mk, nkk;   // kept sizes; mk = mm + 1, nkk = nn + 1
   int nn, N, gn1, gn2, nap;    // full-index layout
@@ -221,9 +304,10 @@ struct AsmP {
 // A[r][c] of the kept block: the TBC rows from the integrals Ics, Isc, Icc
 // ([(m, k1)][(n, k2)], FP32) and the cavity part from top (tau of every
 // unknown, then varsigma of the E1 and E2 unknowns); grid (ceil(nk/256), nk)
-__global__ void k_dn_assemble(const float2* __restrict__ Ics, const float2* __restrict__ Isc,
-                              const float2* __restrict__ Icc, const double2* __restrict__ top,
-                              float2* __restrict__ A, int lda, AsmP p) {
+template <typename T>
+__global__ void k_dn_assemble(const C<T>* __restrict__ Ics, const C<T>* __restrict__ Isc,
+                              const C<T>* __restrict__ Icc, const double2* __restrict__ top,
+                              C<T>* __restrict__ A, int lda, AsmP p) {
   const int r = blockIdx.y;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= p.nk) return;
@@ -245,12 +329,12 @@ __global__ void k_dn_assemble(const float2* __restrict__ Ics, const float2* __re
   if (cr == 0) {
     const int i1 = m * p.N + (n - 1);
     if (cc == 0) {
-      const float2 a = Ics[o], w = Icc[o];
+      const double2 a = to_d2(Ics[o]), w = to_d2(Icc[o]);
       v.x = s1 * (p.k2 * a.x - 2 * npb * k2pb * w.x);
       v.y = s1 * (p.k2 * a.y - 2 * npb * k2pb * w.y);
       if (same) v = cadd<double>(v, cadd<double>(make_double2(-1, 0), top[i1]));
     } else if (cc == 1) {
-      const float2 w = Icc[o];
+      const double2 w = to_d2(Icc[o]);
       v = make_double2(s1 * 2 * npb * k1pa * w.x, s1 * 2 * npb * k1pa * w.y);
     } else if (same) {
       v = cadd<double>(make_double2(mpa * p.h, 0), top[p.nap + i1]);
@@ -258,10 +342,10 @@ __global__ void k_dn_assemble(const float2* __restrict__ Ics, const float2* __re
   } else if (cr == 1) {
     const int i2 = p.gn1 + (m - 1) * (p.N + 1) + n;
     if (cc == 0) {
-      const float2 w = Icc[o];
+      const double2 w = to_d2(Icc[o]);
       v = make_double2(s2 * 2 * mpa * k2pb * w.x, s2 * 2 * mpa * k2pb * w.y);
     } else if (cc == 1) {
-      const float2 a = Isc[o], w = Icc[o];
+      const double2 a = to_d2(Isc[o]), w = to_d2(Icc[o]);
       v.x = s2 * (p.k2 * a.x - 2 * mpa * k1pa * w.x);
       v.y = s2 * (p.k2 * a.y - 2 * mpa * k1pa * w.y);
       if (same) v = cadd<double>(v, cadd<double>(make_double2(-1, 0), top[i2]));
@@ -274,12 +358,18 @@ __global__ void k_dn_assemble(const float2* __restrict__ Ics, const float2* __re
     else if (cc == 1) v = make_double2(npb * p.h, 0);
     else v = cadd<double>(make_double2(-1, 0), top[i3]);
   }
-  A[(size_t)r * lda + c] = to_f(v);
+  A[(size_t)r * lda + c] = conv<T>(v);
 }
 
 static size_t al256(size_t v) { return (v + 255) / 256 * 256; }
 
-cavity_status dense_assemble(cavity_ctx* ctx, const KeptSet& ks, float2* a, int lda) {
+template <typename T> static const C<T>* khat_of(const cavity_ctx* ctx);
+template <> const float2* khat_of<float>(const cavity_ctx* ctx) { return ctx->khat32; }
+template <> const double2* khat_of<double>(const cavity_ctx* ctx) { return ctx->khat64; }
+
+// the kept block ks in precision T under the context's outer rule
+template <typename T>
+static cavity_status dense_assemble_t(cavity_ctx* ctx, const KeptSet& ks, C<T>* a, int lda) {
   const Geo& g = ctx->g;
   if (!ctx->prepared) {
     ctx->err = "dense assembly: call cavity_prepare first";
@@ -290,30 +380,31 @@ cavity_status dense_assemble(cavity_ctx* ctx, const KeptSet& ks, float2* a, int 
                " unknowns exceeds the limit, or lda too small";
     return CAVITY_EINVAL;
   }
+  const bool parseval = ctx->desc.outer_rule == CAVITY_OUTER_PARSEVAL;
   const int mk = ks.mm + 1, nkk = ks.nn + 1;
   const int Hx = g.Px / 2, Hy = g.Py / 2;
   const size_t npx = (size_t)mk * mk, npy = (size_t)nkk * nkk;
   // scratch: X, Phi per axis (FP64), folded factors, T per y kind, three I
   const size_t bx = al256(sizeof(double2) * 2 * mk * (size_t)g.Px);
   const size_t by = al256(sizeof(double2) * 2 * nkk * (size_t)g.Py);
-  const size_t bfx = al256(sizeof(float2) * 2 * npx * Hx), bfy = al256(sizeof(float2) * 2 * npy * Hy);
-  const size_t bt = al256(sizeof(float2) * (size_t)Hx * npy);
-  const size_t bi = al256(sizeof(float2) * npx * npy);
+  const size_t bfx = al256(sizeof(C<T>) * 2 * npx * Hx), bfy = al256(sizeof(C<T>) * 2 * npy * Hy);
+  const size_t bt = al256(sizeof(C<T>) * (size_t)Hx * npy);
+  const size_t bi = al256(sizeof(C<T>) * npx * npy);
   CKS(ensure_ws(ctx, &ctx->ws2, &ctx->ws2_bytes, 2 * bx + 2 * by + bfx + bfy + 2 * bt + 3 * bi));
   char* q = (char*)ctx->ws2;
   double2* Xx = (double2*)q; q += bx;
   double2* Fx = (double2*)q; q += bx;
   double2* Xy = (double2*)q; q += by;
   double2* Fy = (double2*)q; q += by;
-  float2* Axf = (float2*)q; q += bfx;
-  float2* Ayf = (float2*)q; q += bfy;
-  float2* T[2];
-  T[0] = (float2*)q; q += bt;
-  T[1] = (float2*)q; q += bt;
-  float2* I[3];
-  for (int f = 0; f < 3; ++f) { I[f] = (float2*)q; q += bi; }
+  C<T>* Axf = (C<T>*)q; q += bfx;
+  C<T>* Ayf = (C<T>*)q; q += bfy;
+  C<T>* Tm[2];
+  Tm[0] = (C<T>*)q; q += bt;
+  Tm[1] = (C<T>*)q; q += bt;
+  C<T>* I[3];
+  for (int f = 0; f < 3; ++f) { I[f] = (C<T>*)q; q += bi; }
   cudaStream_t st = ctx->stream;
-  {
+  if (!parseval) {
     KScope ks_(ctx, KC_DENSE_ASM);
     k_dn_x<<<dim3(nblk(g.Px, 256), mk, 2), 256, 0, st>>>(Xx, mk, g.nx, g.Px, g.a, ctx->tw64, ctx->TW);
   }
@@ -321,7 +412,7 @@ cavity_status dense_assemble(cavity_ctx* ctx, const KeptSet& ks, float2* a, int 
     KScope ks_(ctx, KC_DENSE_ASM);
     k_dn_phi<<<dim3(nblk(g.Px, 256), mk, 2), 256, 0, st>>>(Fx, mk, g.Px, g.a);
   }
-  {
+  if (!parseval) {
     KScope ks_(ctx, KC_DENSE_ASM);
     k_dn_x<<<dim3(nblk(g.Py, 256), nkk, 2), 256, 0, st>>>(Xy, nkk, g.ny, g.Py, g.b, ctx->tw64, ctx->TW);
   }
@@ -331,33 +422,35 @@ cavity_status dense_assemble(cavity_ctx* ctx, const KeptSet& ks, float2* a, int 
   }
   {
     KScope ks_(ctx, KC_DENSE_ASM);
-    k_dn_fold<<<dim3((unsigned)(npx * nblk(Hx, 256)), 1, 2), 256, 0, st>>>(Xx, Fx, Axf, mk, g.Px);
+    k_dn_fold<T><<<dim3((unsigned)(npx * nblk(Hx, 256)), 1, 2), 256, 0, st>>>(Xx, Fx, Axf, mk, g.Px,
+                                                                              parseval);
   }
   {
     KScope ks_(ctx, KC_DENSE_ASM);
-    k_dn_fold<<<dim3((unsigned)(npy * nblk(Hy, 256)), 1, 2), 256, 0, st>>>(Xy, Fy, Ayf, nkk, g.Py);
+    k_dn_fold<T><<<dim3((unsigned)(npy * nblk(Hy, 256)), 1, 2), 256, 0, st>>>(Xy, Fy, Ayf, nkk, g.Py,
+                                                                              parseval);
   }
   CK(cudaGetLastError());
-  // T[yk][j1][(n, k2)] = sum_j2 Kq[j2][j1] Ayf[yk][(n, k2)][j2]   (Kq = khat32, [j2][j1])
+  // T[yk][j1][(n, k2)] = sum_j2 Kq[j2][j1] Ayf[yk][(n, k2)][j2]   (Kq: the quarter box, [j2][j1])
   for (int yk = 0; yk < 2; ++yk) {
-    GemmArgs ga;
-    ga.A = ctx->khat32; ga.sar = 1; ga.sak = Hx;
+    GemmArgsT<T> ga;
+    ga.A = khat_of<T>(ctx); ga.sar = 1; ga.sak = Hx;
     ga.B = Ayf + (size_t)yk * npy * Hy; ga.sbk = 1; ga.sbc = Hy;
-    ga.C = T[yk]; ga.ldc = (long long)npy;
+    ga.C = Tm[yk]; ga.ldc = (long long)npy;
     ga.M = Hx; ga.N = (int)npy; ga.K = Hy;
-    ga.alpha = 1.f; ga.beta = 0;
+    ga.alpha = 1; ga.beta = 0;
     CKS(cgemm(ctx, ga, KC_DENSE_ASM));
   }
   // I_f[(m, k1)][(n, k2)] = sum_j1 Axf[xk][(m, k1)][j1] T[yk][j1][(n, k2)]
   // f = cs (x cos, y sin), sc (x sin, y cos), cc
   const int xk_of[3] = {0, 1, 0}, yk_of[3] = {1, 0, 0};
   for (int f = 0; f < 3; ++f) {
-    GemmArgs ga;
+    GemmArgsT<T> ga;
     ga.A = Axf + (size_t)xk_of[f] * npx * Hx; ga.sar = Hx; ga.sak = 1;
-    ga.B = T[yk_of[f]]; ga.sbk = (long long)npy; ga.sbc = 1;
+    ga.B = Tm[yk_of[f]]; ga.sbk = (long long)npy; ga.sbc = 1;
     ga.C = I[f]; ga.ldc = (long long)npy;
     ga.M = (int)npx; ga.N = (int)npy; ga.K = Hx;
-    ga.alpha = 1.f; ga.beta = 0;
+    ga.alpha = 1; ga.beta = 0;
     CKS(cgemm(ctx, ga, KC_DENSE_ASM));
   }
   AsmP p;
@@ -367,11 +460,15 @@ cavity_status dense_assemble(cavity_ctx* ctx, const KeptSet& ks, float2* a, int 
   p.k2 = 2.0 * ctx->kappa0 * ctx->kappa0;
   {
     KScope ks_(ctx, KC_DENSE_ASM);
-    k_dn_assemble<<<dim3(nblk(ks.nk, 256), ks.nk), 256, 0, st>>>(I[0], I[1], I[2], ctx->top64, a,
-                                                                  lda, p);
+    k_dn_assemble<T><<<dim3(nblk(ks.nk, 256), ks.nk), 256, 0, st>>>(I[0], I[1], I[2], ctx->top64, a,
+                                                                     lda, p);
   }
   CK(cudaGetLastError());
   return CAVITY_OK;
+}
+
+cavity_status dense_assemble(cavity_ctx* ctx, const KeptSet& ks, float2* a, int lda) {
+  return dense_assemble_t<float>(ctx, ks, a, lda);
 }
 
 // ------------------------------------------------------------ LU factorisation
@@ -966,13 +1063,18 @@ cavity_status dense_lu_solve(cavity_ctx* ctx, const float2* lu, int n, int lda, 
 
 // ------------------------------------------------------------ the dense path
 void dense_free(DenseLU& f) {
-  void* ptrs[] = {f.a, f.dinv, f.ipiv, f.perm, f.map, f.work};
+  void* ptrs[] = {f.a, f.a64, f.dinv, f.ipiv, f.perm, f.map, f.work};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   f = DenseLU();
 }
 
-cavity_status dense_factor(cavity_ctx* ctx, DenseLU& f, const KeptSet& ks) {
+__global__ void k_dn_narrow(const double2* __restrict__ a64, float2* __restrict__ a, long long n) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) a[i] = to_f(a64[i]);
+}
+
+cavity_status dense_factor(cavity_ctx* ctx, DenseLU& f, const KeptSet& ks, bool keep64) {
   const Geo& g = ctx->g;
   f.ready = false;
   if (ks.nk > CAVITY_DENSE_MAX_N) {
@@ -981,13 +1083,14 @@ cavity_status dense_factor(cavity_ctx* ctx, DenseLU& f, const KeptSet& ks) {
     return CAVITY_EINVAL;
   }
   const int lda = (ks.nk + 3) / 4 * 4;
-  if (f.n != ks.nk || f.ks.mm != ks.mm || f.ks.nn != ks.nn || !f.a) {
+  if (f.n != ks.nk || f.ks.mm != ks.mm || f.ks.nn != ks.nn || !f.a || (keep64 && !f.a64)) {
     dense_free(f);
     cudaError_t e = cudaMalloc(&f.a, sizeof(float2) * (size_t)ks.nk * lda);
     if (e == cudaSuccess) e = cudaMalloc(&f.ipiv, sizeof(int) * ks.nk);
     if (e == cudaSuccess) e = cudaMalloc(&f.perm, sizeof(int) * ks.nk);
     if (e == cudaSuccess) e = cudaMalloc(&f.map, sizeof(int) * ks.nk);
     if (e == cudaSuccess) e = cudaMalloc(&f.dinv, dinv_bytes(ks.nk));
+    if (e == cudaSuccess && keep64) e = cudaMalloc(&f.a64, sizeof(double2) * (size_t)ks.nk * lda);
     if (e != cudaSuccess) {
       dense_free(f);
       ctx->err = std::string("dense kept block: allocation failed: ") + cudaGetErrorString(e);
@@ -999,7 +1102,14 @@ cavity_status dense_factor(cavity_ctx* ctx, DenseLU& f, const KeptSet& ks) {
     f.n = ks.nk;
     f.lda = lda;
   }
-  CKS(dense_assemble(ctx, ks, f.a, lda));
+  if (keep64) {
+    CKS(dense_assemble_t<double>(ctx, ks, f.a64, lda));
+    const long long tot = (long long)ks.nk * lda;
+    KScope ks_(ctx, KC_DENSE_ASM);
+    k_dn_narrow<<<(unsigned)((tot + 255) / 256), 256, 0, ctx->stream>>>(f.a64, f.a, tot);
+  } else {
+    CKS(dense_assemble(ctx, ks, f.a, lda));
+  }
   int info = -1;
   CKS(dense_lu(ctx, f.a, ks.nk, lda, f.ipiv, &info));
   {
@@ -1012,8 +1122,79 @@ cavity_status dense_factor(cavity_ctx* ctx, DenseLU& f, const KeptSet& ks) {
   return CAVITY_OK;
 }
 
+// The solver keeps the block in FP64 as well where the refinement takes its
+// residual from it: always under the Parseval rule (the FFT operator
+// implements rule D only), and on the FP64 path (one dense FP64 product per
+// step is cheaper than the FP64 FFT operator on the full grid)
 cavity_status launch_dense_factor(cavity_ctx* ctx) {
-  return dense_factor(ctx, ctx->dn, kept_set(ctx->desc, ctx->g));
+  const bool keep64 = ctx->desc.outer_rule == CAVITY_OUTER_PARSEVAL || ctx->desc.precision == CAVITY_FP64;
+  return dense_factor(ctx, ctx->dn, kept_set(ctx->desc, ctx->g), keep64);
+}
+
+// r[d][map[i]] = b[d][map[i]] - sum_k A64[i][k] x[d][map[k]]: 64 rows x 16
+// right-hand sides per CTA, k in tiles of 32 through shared memory
+#define RS_R 64
+#define RS_K 32
+__global__ void __launch_bounds__(256) k_dn_resid(const double2* __restrict__ A, int lda, int nk,
+                                                  const int* __restrict__ map, const double2* __restrict__ b,
+                                                  const double2* __restrict__ x, double2* __restrict__ r,
+                                                  int nap, int ndir) {
+  __shared__ double2 As[RS_R][RS_K + 1];
+  __shared__ double2 Xs[TS_D][RS_K + 1];
+  const int t = threadIdx.x, row = t >> 2, g = t & 3;
+  const int i0 = blockIdx.x * RS_R, d0 = blockIdx.y * TS_D;
+  double2 acc[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) acc[u] = make_double2(0.0, 0.0);
+  for (int kb = 0; kb < nk; kb += RS_K) {
+#pragma unroll
+    for (int u = 0; u < RS_R * RS_K / 256; ++u) {
+      const int e = t + u * 256, i = e / RS_K, k = e % RS_K;
+      As[i][k] = (i0 + i < nk && kb + k < nk) ? A[(size_t)(i0 + i) * lda + kb + k] : make_double2(0.0, 0.0);
+    }
+#pragma unroll
+    for (int u = 0; u < TS_D * RS_K / 256; ++u) {
+      const int e = t + u * 256, d = e / RS_K, k = e % RS_K;
+      Xs[d][k] = (d0 + d < ndir && kb + k < nk) ? x[(size_t)(d0 + d) * nap + map[kb + k]]
+                                                 : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int k = 0; k < RS_K; ++k) {
+      const double2 a = As[row][k];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const double2 v = Xs[g + 4 * u][k];
+        acc[u].x = fma(a.x, v.x, fma(-a.y, v.y, acc[u].x));
+        acc[u].y = fma(a.x, v.y, fma(a.y, v.x, acc[u].y));
+      }
+    }
+    __syncthreads();
+  }
+  const int i = i0 + row;
+  if (i >= nk) return;
+  const int mi = map[i];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int d = d0 + g + 4 * u;
+    if (d >= ndir) continue;
+    const double2 bv = b[(size_t)d * nap + mi];
+    r[(size_t)d * nap + mi] = make_double2(bv.x - acc[u].x, bv.y - acc[u].y);
+  }
+}
+
+cavity_status dense_residual(cavity_ctx* ctx, int ndir, const double2* b, const double2* x,
+                             double2* r) {
+  const DenseLU& f = ctx->dn;
+  if (!f.ready || !f.a64) {
+    ctx->err = "dense residual: no FP64 kept block";
+    return CAVITY_EINVAL;
+  }
+  KScope ks_(ctx, KC_DENSE_TRS);
+  k_dn_resid<<<dim3(nblk(f.n, RS_R), nblk(ndir, TS_D)), 256, 0, ctx->stream>>>(
+      f.a64, f.lda, f.n, f.map, b, x, r, ctx->g.nap, ndir);
+  CK(cudaGetLastError());
+  return CAVITY_OK;
 }
 
 // Y[d][i] = (float) (s[d] r[d][map[perm[i]]])  (grid (ceil(nk/256), ndir))

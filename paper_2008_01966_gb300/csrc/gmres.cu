@@ -707,9 +707,10 @@ cavity_status run_mixed_solve(cavity_ctx* ctx, int ndir, const double2* b, doubl
 // Dense path (aperture_solver == CAVITY_SOLVER_DENSE): FP64 iterative
 // refinement around the FP32 LU factors of the kept block (dense.cu).  Each
 // step solves with the factors for the scaled residual of the kept rows,
-// adds the correction in FP64, and recomputes r = b - A x with the FP64
-// operator (CAVITY_FP64) or the pair-of-FP32 operator (CAVITY_MIXED), whose
-// rows outside the kept set are zero.  iters counts refinement steps.
+// adds the correction in FP64, and recomputes r = b - A x: with the FP64 kept
+// block where it is resident (the Parseval rule; the FP64 path), else with
+// the pair-of-FP32 FFT operator (rule D, CAVITY_MIXED), whose rows outside
+// the kept set are zero.  iters counts refinement steps.
 cavity_status run_dense_solve(cavity_ctx* ctx, int ndir, const double2* b, double2* x, int* iters,
                               double* resid) {
   const Geo& g = ctx->g;
@@ -751,13 +752,18 @@ cavity_status run_dense_solve(cavity_ctx* ctx, int ndir, const double2* b, doubl
       s[d] = (bn[d] == 0 || rn[d] <= tol * bn[d] || !(rn[d] > 0)) ? 0.0 : 1.0 / rn[d];
     CK(cudaMemcpyAsync(sdev, s.data(), sizeof(double) * ndir, cudaMemcpyHostToDevice, st));
     CKS(dense_inner_solve(ctx, ndir, r64, sdev, x, inner));
-    if (fp64) CKS(launch_apply<double>(ctx, ndir, x, tmp, apwk));
-    else CKS(launch_apply_pair(ctx, ndir, x, tmp, apwk));
-    {
-      KScope ks_(ctx, KC_DENSE_TRS);
-      k_bminus<double><<<nblk(nv, 256), 256, 0, st>>>(b, tmp, nv);
+    if (ctx->dn.a64) {
+      // r = b - A x with the FP64 kept block (rows outside the kept set stay 0)
+      CKS(dense_residual(ctx, ndir, b, x, r64));
+    } else {
+      if (fp64) CKS(launch_apply<double>(ctx, ndir, x, tmp, apwk));
+      else CKS(launch_apply_pair(ctx, ndir, x, tmp, apwk));
+      {
+        KScope ks_(ctx, KC_DENSE_TRS);
+        k_bminus<double><<<nblk(nv, 256), 256, 0, st>>>(b, tmp, nv);
+      }
+      std::swap(r64, tmp);
     }
-    std::swap(r64, tmp);
     prev = rn;
     CKS(norms<double>(ctx, r64, ndir, sc2, 1, rn, part));
     // a step that does not halve some unconverged residual: the factors of

@@ -24,6 +24,7 @@ from oracle.aperture import ApertureSystem
 from oracle.excitation import rhs as oracle_rhs
 from oracle.field import field as oracle_field
 from oracle.geometry import Cavity as OCavity, Layer
+from oracle.tbc import TBCOperator
 
 pytestmark = pytest.mark.gpu
 
@@ -202,3 +203,52 @@ def test_two_level_preconditioner_same_solution_fewer_steps(gb):
     for d in range(len(w['theta'])):
         assert rel(out[24][0][d], out[0][0][d]) < 1e-8
     assert out[24][1].max() < out[0][1].max(), (out[0][1], out[24][1])
+
+
+@pytest.mark.parametrize("case,mm,nn", [("homog", 5, 7), ("rect", 15, 7), ("layer3", 15, 15)])
+def test_parseval_kept_block_matches_oracle(gb, case, mm, nn):
+    """The Parseval form of the TBC blocks (Sec. 5.2 with the outer integral
+    taken exactly: Phi^H diag(F(G)) Phi) assembled on the GPU against the
+    oracle's dense_kept under outer='parseval', entry by entry."""
+    w = CASES[case]
+    cav = ocav(w)
+    ref = ApertureSystem(cav, tbc=TBCOperator(cav, outer='parseval')).dense_kept(mm, nn)
+    g = gcav(gb, w, modes_m=mm if mm < w['nx'] - 1 else 0, modes_n=nn if nn < w['ny'] - 1 else 0,
+             aperture_solver="dense", outer_rule="parseval")
+    g.prepare(w['kappa0'], w['layers'])
+    A = g.dense_assemble().cpu().numpy()
+    err = np.abs(A - ref).max() / np.abs(ref).max()
+    assert err < 2e-6, err
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("case,mm,nn", [("layer3", 6, 9), ("rect", 0, 0)])
+def test_parseval_dense_solve_matches_oracle(gb, precision, case, mm, nn):
+    """Whole solves under the Parseval rule (dense solver: FP32 factors, FP64
+    residuals from the FP64 kept block) against the oracle's direct solve of
+    the same system, aperture and field per direction."""
+    w = CASES[case]
+    cav = ocav(w)
+    sysm = ApertureSystem(cav, tbc=TBCOperator(cav, outer='parseval'))
+    mmo, nno = mm or cav.M, nn or cav.N
+    th, ph, al = workloads.directions(3, 37)
+    B = np.array([oracle_rhs(cav, t, p, a) for t, p, a in zip(th, ph, al)])
+    X = sysm.solve_kept(B, mmo, nno)
+    fp64 = precision == "fp64"
+    g = gcav(gb, w, precision=precision, gmres_tol=1e-12 if fp64 else 1e-10,
+             modes_m=mm if mm < cav.M else 0, modes_n=nn if nn < cav.N else 0,
+             aperture_solver="dense", outer_rule="parseval")
+    ap, fl, it, res = g.solve(w['kappa0'], w['layers'], th, ph, al)
+    ap = ap.cpu().numpy()
+    fl = fl.cpu().numpy()
+    assert np.all(np.asarray(it) <= 6), it
+    for d in range(3):
+        assert rel(ap[d], X[d]) < (1e-10 if fp64 else 1e-8)
+        F = oracle_field(cav, sysm.prof, X[d]).ravel()
+        assert rel(fl[d], F) < (1e-10 if fp64 else 1e-5)
+
+
+def test_parseval_needs_the_dense_solver(gb):
+    w = CASES["homog"]
+    with pytest.raises(gb.CavityError):
+        gcav(gb, w, outer_rule="parseval")
