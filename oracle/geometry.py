@@ -42,7 +42,10 @@ class Cavity:
     kappa0    free-space wavenumber (Sec. 2)
     layers    top-to-bottom list of Layer; default one layer with eps = 1
     pad       period of the frequency-domain convolution in units of the
-              aperture side (L = pad * a); part of the discrete TBC operator
+              aperture side (Lx = pad * a); part of the discrete TBC operator
+    pad_y     the same along x2 (Ly = pad_y * b); 0 = pad.  A period must
+              exceed the side plus the kernel's truncation radius, so a long
+              narrow aperture needs a longer period along its short side
     """
     a: float
     b: float
@@ -53,8 +56,11 @@ class Cavity:
     kappa0: float
     layers: List[Layer] = field(default_factory=list)
     pad: int = 4
+    pad_y: int = 0
 
     def __post_init__(self):
+        if not self.pad_y:
+            self.pad_y = self.pad
         if not self.layers:
             self.layers = [Layer(self.nz, 1.0 + 0j)]
         self.layers = [Layer(int(l.nlev), complex(l.eps)) for l in self.layers]

@@ -13,13 +13,16 @@ integral I_k(x) = int F(y) G(x-y) dy as F^{-1}(F(F) F(G)) and the outer integral
 by the trapezoid rule.  The discrete rule written out here (and binding for the
 CUDA path) is:
 
-  * the convolution is periodised with period Lx = pad*a, Ly = pad*b; for x, y in
-    Gamma and the truncation radius R = sqrt(2) max(a,b) no image contributes
-    while pad*min(a,b) > min(a,b) + R;
+  * the convolution is periodised with period Lx = pad*a, Ly = pad_y*b; for
+    x, y in Gamma and the truncation radius R = sqrt(2) max(a,b) no image
+    contributes while pad*a > a + R and pad_y*b > b + R (pad_y = pad = 4 for
+    apertures up to about 2:1; a 4:1 aperture needs pad_y = 8 along its short
+    side);
   * the inverse transform is the Fourier series on that torus truncated to the
     symmetric box |j1| <= Px/2 - 1, |j2| <= Py/2 - 1 with Px = pad*Nx,
-    Py = pad*Ny (so the torus grid of spacing a/Nx contains the aperture
-    nodes):  I_k(x) = (Lx Ly)^{-1} sum_j F(F)(j/L) F(G)(|j/L|) exp(2 pi i j.x/L);
+    Py = pad_y*Ny (so the torus grid of spacing a/Nx, b/Ny contains the
+    aperture nodes):
+    I_k(x) = (Lx Ly)^{-1} sum_j F(F)(j/L) F(G)(|j/L|) exp(2 pi i j.x/L);
   * F(F) is the exact transform of the truncated basis function, separable into
     1-D factors  f^c_k(xi) = [E(xi - k/2a) + E(xi + k/2a)]/2 and
     f^s_k(xi) = [E(xi - k/2a) - E(xi + k/2a)]/(2i) with
@@ -109,12 +112,13 @@ class TBCOperator:
         self.outer = outer
         self.cav = cav
         self._khat = khat if scheme == 'quadrature' else khat_paper
-        a, b, nx, ny, pad = cav.a, cav.b, cav.nx, cav.ny, cav.pad
-        self.Px, self.Py = pad * nx, pad * ny
+        a, b, nx, ny = cav.a, cav.b, cav.nx, cav.ny
+        padx, pady = cav.pad, cav.pad_y
+        self.Px, self.Py = padx * nx, pady * ny
         self.jx, self.jy = freq_index(self.Px), freq_index(self.Py)
-        self.Lx, self.Ly = pad * a, pad * b
+        self.Lx, self.Ly = padx * a, pady * b
         R = np.sqrt(2.0) * max(a, b)
-        if pad * min(a, b) <= min(a, b) + R:
+        if padx * a <= a + R or pady * b <= b + R:
             raise ValueError("period too short for the truncated kernel")
         if kh is None:
             kh = self._kernel_table(R)
@@ -127,8 +131,8 @@ class TBCOperator:
         for kind in 'cs':
             kx = rng[kind][0]
             ky = rng[kind][1]
-            self._fx[kind] = phi_matrix(kind, kx, self.jx, a, pad)
-            self._fy[kind] = phi_matrix(kind, ky, self.jy, b, pad)
+            self._fx[kind] = phi_matrix(kind, kx, self.jx, a, padx)
+            self._fy[kind] = phi_matrix(kind, ky, self.jy, b, pady)
             self._tx[kind] = trap_matrix(kind, kx, nx, a)
             self._ty[kind] = trap_matrix(kind, ky, ny, b)
         self._ex = idft_matrix(np.arange(nx + 1), self.jx, self.Px) / self.Lx

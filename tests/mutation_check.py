@@ -44,6 +44,9 @@ MUTATIONS = [
     ('tbc.py', "w[0] *= 0.5", "w[0] *= 1.0"),
     ('tbc.py', "return np.exp(2j * np.pi * np.outer(nodes, js) / P)", "return np.exp(-2j * np.pi * np.outer(nodes, js) / P)"),
     ('tbc.py', "self._ex = idft_matrix(np.arange(nx + 1), self.jx, self.Px) / self.Lx", "self._ex = idft_matrix(np.arange(nx + 1), self.jx, self.Px) / self.Ly / 2"),
+    ('tbc.py', "padx, pady = cav.pad, cav.pad_y", "padx, pady = cav.pad, 2 * cav.pad_y"),
+    ('tbc.py', "self._fy[kind] = phi_matrix(kind, ky, self.jy, b, pady)", "self._fy[kind] = phi_matrix(kind, ky, self.jy, b, padx)"),
+    ('tbc.py', "self.Lx, self.Ly = padx * a, pady * b", "self.Lx, self.Ly = padx * a, padx * b"),
     ('tbc.py', "R = np.sqrt(2.0) * max(a, b)", "R = 1.3 * max(a, b)"),
     ('aperture.py', "wc[..., :, 1:] += self.ny[None, 1:] * e1", "wc[..., :, 1:] -= self.ny[None, 1:] * e1"),
     ('aperture.py', "y1 = (-1.0 + p.tau1) * e1", "y1 = (1.0 + p.tau1) * e1"),

@@ -299,6 +299,27 @@ def test_static_self_potential_of_a_rectangle():
     assert np.all(_order(errs) > 1.5)
 
 
+def test_static_self_potential_of_a_4_to_1_rectangle_with_period_8b():
+    """A 1 x 0.25 aperture (Example 2 of Sec. 7) with M = N: the period along
+    the short side must exceed b + sqrt(2) a, so it is 8 b there (pad_y = 8);
+    the kappa0 -> 0 limit of I3^{00}_{00} then converges at about second order
+    to the rectangle's electrostatic self-potential (closed form as above),
+    which fixes the per-axis period in E(nu), the frequency box and 1/(Lx Ly).
+    With the period 4 b setup refuses the aperture."""
+    a, b = 1.0, 0.25
+    d = np.hypot(a, b)
+    exact = ((2 / 3) * (a ** 3 + b ** 3 - d ** 3) + 2 * a * a * b * np.log((b + d) / a)
+             + 2 * a * b * b * np.log((a + d) / b)) / (4 * np.pi)
+    errs = []
+    for nx in (8, 16, 32):
+        cav = Cavity(a, b, 0.25, nx, nx, 4, 1e-9, pad_y=8)
+        errs.append(abs(TBCOperator(cav).diag('cc')[0, 0] - exact) / exact)
+    assert errs[-1] < 2e-3, errs
+    assert np.all(_order(errs) > 1.5), errs
+    with pytest.raises(ValueError):
+        TBCOperator(Cavity(a, b, 0.25, 8, 8, 4, 1e-9))
+
+
 @pytest.mark.parametrize("b", [1.0, 0.6])
 def test_tbc_row_is_the_exterior_admittance(b):
     """For an evanescent mode the TBC part of row 1 of (EJ1) must be -h times
