@@ -72,8 +72,13 @@ typedef struct {
                          /*   aperture solve (FP32 inner Krylov iterations with */
                          /*   FP64 residual refinement); FP32 transforms and a  */
                          /*   complex64 field                                  */
-  int pad_factor;        /* period of the TBC convolution in aperture sides;   */
-                         /* 0 selects 4 (the only value the GPU path supports) */
+  int pad_factor;        /* period of the TBC convolution in aperture sides    */
+                         /* (Sec. 5.2; it must exceed side + sqrt 2 max(a, b)  */
+                         /* on each axis): 0 = per axis, 4 where that suffices */
+                         /* (max/min < 2.12), else 8 or 16 (max/min < 11);    */
+                         /* 4 = 4 on both axes (EINVAL if too short).  The FFT */
+                         /* operator, and with it the Krylov solver, needs 4   */
+                         /* on both axes; longer periods take the dense solver */
   double gmres_tol;      /* relative residual target of (EJ1)/(uT1); 0 -> 1e-12 */
   int gmres_restart;     /* Krylov basis size, at most 120; 0 -> 40            */
   int gmres_max_iter;    /* total inner iterations; 0 -> 400                   */
@@ -217,6 +222,11 @@ cavity_status cavity_export_elimination(cavity_ctx* ctx, void* top, void* prof,
 /* The kernel table F(G)(rho) of Sec. 5.2 at rho = |(j1/Lx, j2/Ly)| for
  * j1 = 0..Px/2-1, j2 = 0..Py/2-1 (row-major, complex128), Px = 4 nx. */
 cavity_status cavity_export_khat(cavity_ctx* ctx, void* khat);
+
+/* The convolution periods chosen at setup, in aperture sides: Lx = pad_x a,
+ * Ly = pad_y b; the kernel table of cavity_export_khat is
+ * (pad_x nx / 2) x (pad_y ny / 2). */
+cavity_status cavity_periods(const cavity_ctx* ctx, int* pad_x, int* pad_y);
 
 /* Right-hand sides [g1; g2; 0] of (EJ1) for ndir directions (host angle
  * arrays) into out (ndir x n_ap complex128, device). */

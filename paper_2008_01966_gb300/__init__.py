@@ -75,7 +75,7 @@ class Cavity:
         torch.cuda.set_device(self.device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         self.precision = _lib.CAVITY_FP64 if precision == "fp64" else _lib.CAVITY_MIXED
-        d = _lib.CavityDesc(a, b, c, nx, ny, nz, self.precision, 4, gmres_tol, gmres_restart,
+        d = _lib.CavityDesc(a, b, c, nx, ny, nz, self.precision, 0, gmres_tol, gmres_restart,
                             gmres_max_iter, pivot_tol,
                             {"quadrature": 0, "paper": 1}[khat_scheme], modes_m, modes_n,
                             _lib.SOLVERS[aperture_solver], _lib.OUTER_RULES[outer_rule])
@@ -92,6 +92,9 @@ class Cavity:
         self.n_ap, self.field_per_dir = n_ap.value, fpd.value
         self.n1 = nx * (ny - 1)
         self.n2 = (nx - 1) * ny
+        px, py = ctypes.c_int(), ctypes.c_int()
+        self.lib.cavity_periods(self.h, ctypes.byref(px), ctypes.byref(py))
+        self.pad_x, self.pad_y = px.value, py.value
 
     def _check(self, st, allow_noconv=False):
         if st == 0 or (allow_noconv and st == _lib.CAVITY_ENOCONV):
@@ -245,7 +248,8 @@ class Cavity:
         return top, prof, profq
 
     def export_khat(self):
-        out = torch.empty((2 * self.nx, 2 * self.ny), dtype=torch.complex128, device=self.device)
+        out = torch.empty((self.pad_x * self.nx // 2, self.pad_y * self.ny // 2), dtype=torch.complex128,
+                          device=self.device)
         self._check(self.lib.cavity_export_khat(self.h, ctypes.c_void_p(out.data_ptr())))
         return out
 

@@ -25,7 +25,8 @@ EXPORTS = ["cavity_setup", "cavity_prepare", "cavity_solve", "cavity_rcs", "cavi
            "cavity_export_khat", "cavity_rhs", "cavity_apply", "cavity_field",
            "cavity_timing", "cavity_timing_read", "cavity_kernel_class",
            "cavity_apply_noalloc", "cavity_set_option", "cavity_get_option",
-           "cavity_dense_size", "cavity_dense_assemble", "cavity_lu_factor", "cavity_lu_solve"]
+           "cavity_dense_size", "cavity_dense_assemble", "cavity_lu_factor", "cavity_lu_solve",
+           "cavity_periods"]
 CAVITY_SOLVER_KRYLOV, CAVITY_SOLVER_DENSE = 0, 1
 SOLVERS = {"krylov": CAVITY_SOLVER_KRYLOV, "dense": CAVITY_SOLVER_DENSE}
 OUTER_RULES = {"trapezoid": 0, "parseval": 1}
@@ -88,6 +89,7 @@ def load():
     lib.cavity_apply_noalloc.argtypes = [P, I, I, P, P]
     lib.cavity_set_option.argtypes = [P, I, I]
     lib.cavity_get_option.argtypes = [P, I, ctypes.POINTER(I)]
+    lib.cavity_periods.argtypes = [P, pi, pi]
     lib.cavity_dense_size.argtypes = [P, pi]
     lib.cavity_dense_assemble.argtypes = [P, P, I]
     lib.cavity_lu_factor.argtypes = [P, P, I, I, P, pi]

@@ -34,8 +34,18 @@ extern "C" cavity_status cavity_setup(const cavity_desc* desc, void* cuda_stream
   if (d.nz < 2 || d.nz > 1 << 20) return bad("nz must be in [2, 2^20]");
   if (d.precision != CAVITY_FP64 && d.precision != CAVITY_MIXED) return bad("unknown precision");
   if (d.pad_factor != 0 && d.pad_factor != 4) return bad("pad_factor must be 0 or 4");
+  // period of the TBC convolution per axis (Sec. 5.2): it must exceed the
+  // side plus the kernel's truncation radius R; 4 sides where that suffices
+  // (apertures up to about 2:1), else the next power of two (0 = automatic)
   const double R = std::sqrt(2.0) * std::max(d.a, d.b);
-  if (!(4.0 * std::min(d.a, d.b) > std::min(d.a, d.b) + R))
+  auto period = [&](double side) {
+    int p = 4;
+    while (p <= 16 && !(p * side > side + R)) p *= 2;
+    return p;
+  };
+  const int padx = period(d.a), pady = period(d.b);
+  if (padx > 16 || pady > 16) return bad("aspect ratio too large (needs max/min < 11)");
+  if (d.pad_factor == 4 && (padx != 4 || pady != 4))
     return bad("aspect ratio too large for the period 4*side (needs max/min < 2.12)");
   if (d.gmres_tol < 0 || d.gmres_restart < 0 || d.gmres_max_iter < 0 || d.pivot_tol < 0)
     return bad("negative solver parameter");
@@ -50,6 +60,9 @@ extern "C" cavity_status cavity_setup(const cavity_desc* desc, void* cuda_stream
     return bad("outer_rule must be CAVITY_OUTER_TRAPEZOID or CAVITY_OUTER_PARSEVAL");
   if (d.outer_rule == CAVITY_OUTER_PARSEVAL && d.aperture_solver != CAVITY_SOLVER_DENSE)
     return bad("the Parseval outer rule is implemented by the dense solver only");
+  if ((padx != 4 || pady != 4) && d.aperture_solver != CAVITY_SOLVER_DENSE)
+    return bad("this aperture needs a convolution period of more than 4 sides (max/min >= "
+               "2.12); the FFT operator has period 4, so use the dense solver");
   if (d.aperture_solver == CAVITY_SOLVER_DENSE) {
     const long long mm = d.modes_m > 0 ? d.modes_m : d.nx - 1, nn = d.modes_n > 0 ? d.modes_n : d.ny - 1;
     if (3 * mm * nn + mm + nn > CAVITY_DENSE_MAX_N)
@@ -68,16 +81,17 @@ extern "C" cavity_status cavity_setup(const cavity_desc* desc, void* cuda_stream
   g.M = d.nx - 1; g.N = d.ny - 1;
   g.n1 = (g.M + 1) * g.N; g.n2 = g.M * (g.N + 1); g.n3 = g.M * g.N;
   g.nap = g.n1 + g.n2 + g.n3;
-  g.pad = 4;
-  g.Px = 4 * d.nx; g.Py = 4 * d.ny;
-  g.Lx = 4 * d.a; g.Ly = 4 * d.b; g.R = R;
+  g.padx = padx; g.pady = pady;
+  g.fft_ok = padx == 4 && pady == 4;
+  g.Px = padx * d.nx; g.Py = pady * d.ny;
+  g.Lx = padx * d.a; g.Ly = pady * d.b; g.R = R;
   g.lnx = ilog2(d.nx); g.lny = ilog2(d.ny); g.lPx = ilog2(g.Px); g.lPy = ilog2(g.Py);
   g.field_per_level = (long long)(d.nx + 1) * (d.ny - 1) + (long long)(d.nx - 1) * (d.ny + 1) +
                       (long long)(d.nx - 1) * (d.ny - 1);
   g.field_per_dir = g.field_per_level * d.nz;
   ctx->TW = 2 * std::max(g.Px, g.Py);
   cavity_status s = launch_twiddles(ctx);
-  if (s == CAVITY_OK) s = launch_ehat(ctx);
+  if (s == CAVITY_OK && g.fft_ok) s = launch_ehat(ctx);
   if (s == CAVITY_OK) {
     cudaError_t e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) {
@@ -133,6 +147,13 @@ extern "C" cavity_status cavity_sizes(const cavity_ctx* ctx, long long* n_ap, lo
   return CAVITY_OK;
 }
 
+extern "C" cavity_status cavity_periods(const cavity_ctx* ctx, int* pad_x, int* pad_y) {
+  if (!ctx || !pad_x || !pad_y) return CAVITY_EINVAL;
+  *pad_x = ctx->g.padx;
+  *pad_y = ctx->g.pady;
+  return CAVITY_OK;
+}
+
 static cavity_status check_layers(cavity_ctx* ctx, int nlayers, const int* lev, const double* er,
                                   const double* ei) {
   if (nlayers < 1 || nlayers > 16 || !lev || !er || !ei) {
@@ -185,8 +206,10 @@ extern "C" cavity_status cavity_prepare(cavity_ctx* ctx, double kappa0, int nlay
   (void)was_layered;
   if (!kappa_same) CKS(launch_khat(ctx, kappa0));
   CKS(launch_zsweep(ctx, kappa0));
-  CKS(launch_precond(ctx));
-  CKS(launch_pair_tables(ctx));
+  if (ctx->g.fft_ok) {   // the Krylov path's preconditioner and operator tables
+    CKS(launch_precond(ctx));
+    CKS(launch_pair_tables(ctx));
+  }
   CK(cudaStreamSynchronize(ctx->stream));
   ctx->prepared = true;
   if (ctx->desc.aperture_solver == CAVITY_SOLVER_DENSE) {

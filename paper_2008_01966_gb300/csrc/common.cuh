@@ -72,7 +72,8 @@ struct Geo {
   double a, b, c, h;
   int nx, ny, nz, M, N;
   int n1, n2, n3, nap;     // sizes of the aperture blocks (Appendix A)
-  int pad, Px, Py;         // TBC torus: Px = pad*nx points, period Lx = pad*a
+  int padx, pady, Px, Py;  // TBC torus: Px = padx*nx points, period Lx = padx*a (y alike)
+  bool fft_ok;             // padx = pady = 4: the FFT operator's layout (else dense solver only)
   double Lx, Ly, R;        // R = sqrt(2) max(a,b): truncation of the kernel
   int lnx, lny, lPx, lPy;  // log2 of nx, ny, Px, Py
   long long field_per_level, field_per_dir;
@@ -419,17 +420,24 @@ static __device__ __forceinline__ double2 tw_at(const double2* __restrict__ tw, 
   if (r < 0) r += n;
   return tw[r * (TW / n)];
 }
-// E(d / L) of the basis transform (Sec. 5.2) on the torus of period L = 4 side:
-// (1 - (-i)^d) L / (2 pi i d), and side at d = 0
-static __device__ __forceinline__ double2 eps_d(long long d, double side) {
+// E(d / L) of the basis transform (Sec. 5.2) on the torus of period
+// L = pad side: (1 - exp(-2 pi i d / pad)) L / (2 pi i d), and side at d = 0
+// (pad = 4: exp(-2 pi i d / 4) = (-i)^d taken exactly)
+static __device__ __forceinline__ double2 eps_d(long long d, double side, int pad = 4) {
   if (d == 0) return make_double2(side, 0.0);
-  int r = (int)(((d % 4) + 4) % 4);
   double2 num;
-  if (r == 0) num = make_double2(0.0, 0.0);
-  else if (r == 1) num = make_double2(1.0, 1.0);    // 1 - (-i)
-  else if (r == 2) num = make_double2(2.0, 0.0);    // 1 - (-1)
-  else num = make_double2(1.0, -1.0);               // 1 - i
-  double f = 4.0 * side / (2.0 * M_PI * (double)d);
+  if (pad == 4) {
+    int r = (int)(((d % 4) + 4) % 4);
+    if (r == 0) num = make_double2(0.0, 0.0);
+    else if (r == 1) num = make_double2(1.0, 1.0);    // 1 - (-i)
+    else if (r == 2) num = make_double2(2.0, 0.0);    // 1 - (-1)
+    else num = make_double2(1.0, -1.0);               // 1 - i
+  } else {
+    double sn, cs;
+    sincospi(-2.0 * (double)(d % pad) / (double)pad, &sn, &cs);
+    num = make_double2(1.0 - cs, -sn);
+  }
+  double f = pad * side / (2.0 * M_PI * (double)d);
   return make_double2(num.y * f, -num.x * f);       // num / i * f
 }
 

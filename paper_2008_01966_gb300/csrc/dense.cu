@@ -88,15 +88,17 @@ __global__ void k_dn_x(double2* __restrict__ X, int mk, int nint, int Pn, double
   }
 }
 
-// Phi[kind][k][j]: exact transform at j1 / (4 side) of cos (kind 0) or sin
-// (kind 1) (k pi y / side) on [0, side]: [E(j1 - 2k) +- E(j1 + 2k)] / (2 or 2i)
-__global__ void k_dn_phi(double2* __restrict__ Phi, int mk, int Pn, double side) {
+// Phi[kind][k][j]: exact transform at j1 / (pad side) of cos (kind 0) or sin
+// (kind 1) (k pi y / side) on [0, side]; the basis frequency k / (2 side) is
+// (pad / 2) k on the torus grid: [E(j1 - pad k / 2) +- E(j1 + pad k / 2)] / (2 or 2i)
+__global__ void k_dn_phi(double2* __restrict__ Phi, int mk, int Pn, double side, int pad) {
   const int kind = blockIdx.z, k = blockIdx.y;
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < Pn; j += gridDim.x * blockDim.x) {
     double2 r = make_double2(0, 0);
     if (j != Pn / 2 && !(kind == 1 && k == 0)) {
       const long long j1 = j < Pn / 2 ? j : j - Pn;
-      const double2 em = eps_d(j1 - 2 * k, side), ep = eps_d(j1 + 2 * k, side);
+      const long long sh = (long long)(pad / 2) * k;
+      const double2 em = eps_d(j1 - sh, side, pad), ep = eps_d(j1 + sh, side, pad);
       if (kind == 0) r = make_double2(0.5 * (em.x + ep.x), 0.5 * (em.y + ep.y));
       else r = make_double2(0.5 * (em.y - ep.y), -0.5 * (em.x - ep.x));
     }
@@ -410,7 +412,7 @@ static cavity_status dense_assemble_t(cavity_ctx* ctx, const KeptSet& ks, C<T>* 
   }
   {
     KScope ks_(ctx, KC_DENSE_ASM);
-    k_dn_phi<<<dim3(nblk(g.Px, 256), mk, 2), 256, 0, st>>>(Fx, mk, g.Px, g.a);
+    k_dn_phi<<<dim3(nblk(g.Px, 256), mk, 2), 256, 0, st>>>(Fx, mk, g.Px, g.a, g.padx);
   }
   if (!parseval) {
     KScope ks_(ctx, KC_DENSE_ASM);
@@ -418,7 +420,7 @@ static cavity_status dense_assemble_t(cavity_ctx* ctx, const KeptSet& ks, C<T>* 
   }
   {
     KScope ks_(ctx, KC_DENSE_ASM);
-    k_dn_phi<<<dim3(nblk(g.Py, 256), nkk, 2), 256, 0, st>>>(Fy, nkk, g.Py, g.b);
+    k_dn_phi<<<dim3(nblk(g.Py, 256), nkk, 2), 256, 0, st>>>(Fy, nkk, g.Py, g.b, g.pady);
   }
   {
     KScope ks_(ctx, KC_DENSE_ASM);
@@ -1124,10 +1126,12 @@ cavity_status dense_factor(cavity_ctx* ctx, DenseLU& f, const KeptSet& ks, bool 
 
 // The solver keeps the block in FP64 as well where the refinement takes its
 // residual from it: always under the Parseval rule (the FFT operator
-// implements rule D only), and on the FP64 path (one dense FP64 product per
-// step is cheaper than the FP64 FFT operator on the full grid)
+// implements rule D only) and for periods other than 4 sides (the FFT
+// operator's layout), and on the FP64 path (one dense FP64 product per step
+// is cheaper than the FP64 FFT operator on the full grid)
 cavity_status launch_dense_factor(cavity_ctx* ctx) {
-  const bool keep64 = ctx->desc.outer_rule == CAVITY_OUTER_PARSEVAL || ctx->desc.precision == CAVITY_FP64;
+  const bool keep64 = ctx->desc.outer_rule == CAVITY_OUTER_PARSEVAL ||
+                      ctx->desc.precision == CAVITY_FP64 || !ctx->g.fft_ok;
   return dense_factor(ctx, ctx->dn, kept_set(ctx->desc, ctx->g), keep64);
 }
 

@@ -15,7 +15,7 @@
 #include "common.cuh"
 
 // Ax[kind][m][j], j in FFT order over the box (Nyquist slot zero)
-__global__ void k_pc_ax(double2* __restrict__ out, int nint, int Pn, double side,
+__global__ void k_pc_ax(double2* __restrict__ out, int nint, int Pn, double side, int pad,
                         const double2* __restrict__ tw, int TW) {
   const int kind = blockIdx.z;  // 0 cos, 1 sin
   const int m = blockIdx.y;
@@ -32,7 +32,8 @@ __global__ void k_pc_ax(double2* __restrict__ out, int nint, int Pn, double side
         double2 e = cconj<double>(tw_at(tw, TW, j1 * p, Pn));      // exp(2 pi i j1 p / Pn)
         X = cadd<double>(X, cscale<double>(e, w * tr));
       }
-      double2 em = eps_d(j1 - 2 * m, side), ep = eps_d(j1 + 2 * m, side);
+      const long long sh = (long long)(pad / 2) * m;
+      double2 em = eps_d(j1 - sh, side, pad), ep = eps_d(j1 + sh, side, pad);
       double2 phi;
       if (kind == 0) phi = make_double2(0.5 * (em.x + ep.x), 0.5 * (em.y + ep.y));
       else phi = make_double2(0.5 * (em.y - ep.y), -0.5 * (em.x - ep.x));   // /(2i)
@@ -171,11 +172,13 @@ cavity_status launch_precond(cavity_ctx* ctx) {
   cudaStream_t st = ctx->stream;
   {
     KScope ks_(ctx, KC_SETUP);
-    k_pc_ax<<<dim3((g.Px + 255) / 256, g.nx, 2), 256, 0, st>>>(ax, g.nx, g.Px, g.a, ctx->tw64, ctx->TW);
+    k_pc_ax<<<dim3((g.Px + 255) / 256, g.nx, 2), 256, 0, st>>>(ax, g.nx, g.Px, g.a, g.padx, ctx->tw64,
+                                                               ctx->TW);
   }
   {
     KScope ks_(ctx, KC_SETUP);
-    k_pc_ax<<<dim3((g.Py + 255) / 256, g.ny, 2), 256, 0, st>>>(ay, g.ny, g.Py, g.b, ctx->tw64, ctx->TW);
+    k_pc_ax<<<dim3((g.Py + 255) / 256, g.ny, 2), 256, 0, st>>>(ay, g.ny, g.Py, g.b, g.pady, ctx->tw64,
+                                                               ctx->TW);
   }
   {
     KScope ks_(ctx, KC_SETUP);

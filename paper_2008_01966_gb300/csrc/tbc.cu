@@ -90,12 +90,12 @@ cavity_status launch_ehat(cavity_ctx* ctx) {
     {
       KScope ks_(ctx, KC_SETUP);
       k_ehat<<<2, std::max(32, fft_tpl<double>(g.Px)), smx, ctx->stream>>>(
-          ctx->ehat_x64[kind], ctx->ehat_x32[kind], g.Px, g.lPx, g.a, g.pad, kind, ctx->tw64, twlog);
+          ctx->ehat_x64[kind], ctx->ehat_x32[kind], g.Px, g.lPx, g.a, g.padx, kind, ctx->tw64, twlog);
     }
     {
       KScope ks_(ctx, KC_SETUP);
       k_ehat<<<2, std::max(32, fft_tpl<double>(g.Py)), smy, ctx->stream>>>(
-          ctx->ehat_y64[kind], ctx->ehat_y32[kind], g.Py, g.lPy, g.b, g.pad, kind, ctx->tw64, twlog);
+          ctx->ehat_y64[kind], ctx->ehat_y32[kind], g.Py, g.lPy, g.b, g.pady, kind, ctx->tw64, twlog);
     }
     CK(cudaGetLastError());
   }

@@ -790,6 +790,10 @@ cavity_status launch_mode_mask_t(cavity_ctx* ctx, int ndir, C<T>* y, long long y
 template <typename T>
 cavity_status launch_apply(cavity_ctx* ctx, int ndir, const C<T>* x, C<T>* y, void* work,
                            long long ystride) {
+  if (!ctx->g.fft_ok) {
+    ctx->err = "the FFT operator needs the convolution period 4 on both axes";
+    return CAVITY_EINVAL;
+  }
   if (ystride < 0) ystride = ctx->g.nap;
   const Geo& g = ctx->g;
   const size_t need = std::max(std::max(smem_a<T>(g.ny), smem_b<T>(g.nx)),

@@ -55,6 +55,10 @@ size_t apply_pair_work_bytes(const Geo& g, int ndir) {
 
 cavity_status launch_apply_pair(cavity_ctx* ctx, int ndir, const double2* x, double2* y,
                                 void* work) {
+  if (!ctx->g.fft_ok) {
+    ctx->err = "the FFT operator needs the convolution period 4 on both axes";
+    return CAVITY_EINVAL;
+  }
   const Geo& g = ctx->g;
   const long long n = (long long)ndir * g.nap;
   const size_t v = ((sizeof(cdf) * (size_t)n + 255) / 256) * 256;

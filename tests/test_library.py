@@ -39,7 +39,8 @@ def test_setup_rejects_bad_descriptors_without_a_gpu():
     h = ctypes.c_void_p()
     for bad in (dict(nx=12), dict(nz=1), dict(a=-1.0), dict(precision=7), dict(pad_factor=3),
                 dict(a=1.0, b=0.3), dict(restart=121), dict(khat_scheme=2), dict(modes_m=-1),
-                dict(modes_m=16), dict(modes_n=16)):
+                dict(modes_m=16), dict(modes_n=16), dict(a=1.0, b=0.05),
+                dict(a=1.0, b=0.25, pad_factor=4)):
         kw = dict(a=1.0, b=1.0, c=0.5, nx=16, ny=16, nz=8, precision=0, pad_factor=0,
                   restart=0, khat_scheme=0, modes_m=0, modes_n=0)
         kw.update(bad)
