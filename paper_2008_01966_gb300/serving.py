@@ -73,7 +73,7 @@ class Result:
     rcs: np.ndarray = None
     iters: np.ndarray = None
     resid: np.ndarray = None
-    aperture: object = None         # device tensor when keep_aperture
+    aperture: object = None         # host tensor when keep_aperture
     dof: int = 0
 
     @property
@@ -81,19 +81,29 @@ class Result:
         return self.done - self.arrival
 
 
-def workload_requests(n, rate, seed=5, a=1.0, c=0.5):
+def workload_requests(n, rate, seed=5, a=1.0, c=0.5, catalogue=0, keep_every=0):
     """Seeded Poisson stream with the serving workload's mix: grid drawn from
     GRIDS, four equal layers with a seeded permutation of LAYER_EPS, kappa0 at
     10 points per wavelength in the densest layer, 1-32 directions (theta in
     [0, pi/3], phi in [0, 2 pi), theta polarisation), field for grids up to
-    256^2."""
+    256^2.  catalogue > 0: the cavities (grid and fill) are drawn once, that
+    many, and every request names one of them (clients asking about the same
+    cavities again, so contexts are reused and requests batch); 0: a fresh
+    draw per request.  keep_every > 0: every keep_every-th request keeps its
+    aperture solution (for checks against a reference)."""
     rng = np.random.Generator(np.random.PCG64(seed))
+
+    def cavity():
+        nx, nz = GRIDS[rng.integers(len(GRIDS))]
+        eps = [LAYER_EPS[i] for i in rng.permutation(len(LAYER_EPS))]
+        return nx, nz, eps
+
+    cat = [cavity() for _ in range(catalogue)]
     t = 0.0
     out = []
     for rid in range(n):
         t += rng.exponential(1.0 / rate)
-        nx, nz = GRIDS[rng.integers(len(GRIDS))]
-        eps = [LAYER_EPS[i] for i in rng.permutation(len(LAYER_EPS))]
+        nx, nz, eps = cat[rng.integers(len(cat))] if cat else cavity()
         layers = tuple((nz // 4, e) for e in eps)
         h = c / nz
         nmax = max(np.sqrt(e).real for e in eps)
@@ -102,7 +112,8 @@ def workload_requests(n, rate, seed=5, a=1.0, c=0.5):
         th = rng.uniform(0.0, np.pi / 3, nd)
         ph = rng.uniform(0.0, 2 * np.pi, nd)
         out.append(Request(rid, t, (a, a, c, nx, nx, nz), kappa0, layers, th, ph, np.zeros(nd),
-                           want_field=nx <= 256))
+                           want_field=nx <= 256,
+                           keep_aperture=keep_every > 0 and rid % keep_every == 0))
     return out
 
 
@@ -166,7 +177,14 @@ class GpuBackend:
             ap, fl, it, res = cav.solve(kappa0, list(layers), theta, phi, alpha, field=want_field)
             sig = cav.rcs(ap, theta, phi, "theta")
         stream.synchronize()
-        return sig, it, res, (ap if keep_aperture else None), cav.nz * cav.n_ap
+        out = (sig, it, res, (ap.cpu() if keep_aperture else None), cav.nz * cav.n_ap)
+        if want_field:
+            # the field (up to tens of GB per batch) goes back to the caching
+            # allocator; hand it to the device so that the library's own
+            # allocations, which the admission budget counts, find it
+            del fl, ap
+            torch.cuda.empty_cache()
+        return out
 
     def close(self, handle):
         cav, stream = handle
@@ -210,6 +228,7 @@ class Server:
         self.batches = []                            # (key, number of requests, directions)
         self.t0 = None
         self.errors = []
+        self.enomem = 0                              # batches answered CAVITY_ENOMEM
 
     # ---------------------------------------------------------------- public
     def run(self, requests, time_scale=1.0):
@@ -329,10 +348,22 @@ class Server:
                 ctx.last_used = done
                 self._dispatch()
                 self.lock.notify_all()
-        except Exception as e:  # surface backend failures to run()
+        except Exception as e:
+            status = getattr(e, "status", None)
             with self.lock:
-                self.errors.append(e)
-                ctx.busy = False
+                if status == 2:
+                    # the device ran out of memory for this batch (the
+                    # footprint is an estimate): CAVITY_ENOMEM for its
+                    # requests, the server carries on
+                    now = self.clock() - self.t0
+                    for r in batch:
+                        self.results[r.rid] = Result(r.rid, 2, r._arr, now, now, len(batch))
+                    self.enomem += 1
+                    ctx.busy = False
+                    self._dispatch()
+                else:  # surface other backend failures to run()
+                    self.errors.append(e)
+                    ctx.busy = False
                 self.lock.notify_all()
 
 
@@ -354,34 +385,66 @@ def main():
                     help="arrivals per second; 0: 0.7 x the FP64 path's measured capacity")
     ap.add_argument("--budget-gb", type=float, default=200.0)
     ap.add_argument("--seed", type=int, default=5)
+    ap.add_argument("--catalogue", type=int, default=0,
+                    help="number of distinct cavities the requests draw from (0: one per request)")
+    ap.add_argument("--keep-every", type=int, default=0,
+                    help="keep the aperture of every n-th request and write it to --dump")
+    ap.add_argument("--dump", default="",
+                    help=".npz file for the kept requests (inputs, first direction's aperture, RCS)")
+    ap.add_argument("--rate-of", default="fp64", choices=["mixed", "fp64"],
+                    help="with --rate 0: the path whose measured capacity sets the rate")
+    ap.add_argument("--load", type=float, default=0.7,
+                    help="with --rate 0: arrivals as this fraction of that capacity")
     args = ap.parse_args()
     rate = args.rate
+    cap = None
     if rate <= 0:
-        # capacity of the FP64 path: requests per second when a stream of the
-        # same mix is solved one request at a time (each on a new context)
-        probe = [r for r in workload_requests(12, 1.0, seed=args.seed + 1000)
+        # capacity of a path: requests per second when a stream of the same
+        # mix is solved one request at a time (on contexts of the catalogue
+        # when there is one, else each on a new context)
+        probe = [r for r in workload_requests(12, 1.0, seed=args.seed + 1000, catalogue=args.catalogue)
                  if max(r.geom[3], r.geom[4]) <= MAX_SIDE][:8]
         for r in probe:
             r.arrival = 0.0
-        srv = Server(GpuBackend("fp64"), int(args.budget_gb * 2**30), precision="fp64",
+            r.keep_aperture = False
+        srv = Server(GpuBackend(args.rate_of), int(args.budget_gb * 2**30), precision=args.rate_of,
                      max_dirs=32)
         t0 = time.perf_counter()
         for r in probe:
             srv.run([r])
         cap = len(probe) / (time.perf_counter() - t0)
-        rate = 0.7 * cap
-    reqs = workload_requests(args.requests, rate, seed=args.seed)
+        rate = args.load * cap
+    reqs = workload_requests(args.requests, rate, seed=args.seed, catalogue=args.catalogue,
+                             keep_every=args.keep_every)
     srv = Server(GpuBackend(args.precision), int(args.budget_gb * 2**30),
                  precision=args.precision, max_dirs=64)
     t0 = time.perf_counter()
     res = srv.run(reqs)
     wall = time.perf_counter() - t0
     out = summary(res, wall)
+    by = collections.Counter(b[1] for b in srv.batches)
     out.update({"precision": args.precision, "requests": args.requests, "rate_per_s": rate,
-                "seed": args.seed, "batches": len(srv.batches),
+                "capacity_per_s": cap, "rate_of": args.rate_of if cap else None,
+                "seed": args.seed, "catalogue": args.catalogue, "batches": len(srv.batches),
                 "mean_requests_per_batch": float(np.mean([b[1] for b in srv.batches])),
+                "batch_sizes": {str(k): v for k, v in sorted(by.items())},
+                "contexts_opened": len({b[0] for b in srv.batches}),
+                "enomem_batches": srv.enomem,
                 "peak_admitted_gb": srv.peak / 2**30})
     print(json.dumps(out))
+    if args.dump:
+        kept = [r for r in reqs if r.keep_aperture and res[r.rid].status == 0]
+        # one aperture array per kept request (their grids differ)
+        aps = {"aperture_%d" % i: res[r.rid].aperture[0].numpy() for i, r in enumerate(kept)}
+        np.savez(args.dump, precision=args.precision, tol=1e-7,
+                 rid=np.array([r.rid for r in kept]),
+                 geom=np.array([r.geom for r in kept], dtype=float),
+                 kappa0=np.array([r.kappa0 for r in kept]),
+                 layers=np.array([[(n, e) for n, e in r.layers] for r in kept], dtype=complex),
+                 theta=np.array([r.theta[0] for r in kept]), phi=np.array([r.phi[0] for r in kept]),
+                 alpha=np.array([r.alpha[0] for r in kept]),
+                 rcs=np.array([res[r.rid].rcs[0] for r in kept]),
+                 resid=np.array([res[r.rid].resid[0] for r in kept]), **aps)
 
 
 if __name__ == "__main__":

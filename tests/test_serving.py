@@ -181,3 +181,27 @@ def test_request_stream_is_seeded_and_has_the_mix():
     assert all(r.want_field == (r.geom[3] <= 256) for r in a)
     gaps = np.diff([r.arrival for r in a])
     assert abs(gaps.mean() - 0.5) < 0.1   # rate 2 per second
+
+
+class OomBackend(FakeBackend):
+    """solve() of one key fails the way the library does when the device has
+    no memory left for the batch (an exception carrying CAVITY_ENOMEM)."""
+
+    class Err(RuntimeError):
+        status = 2
+
+    def solve(self, handle, key, theta, phi, alpha, want_field, keep_aperture):
+        if key[1] == 6.0:
+            raise OomBackend.Err("out of memory")
+        return super().solve(handle, key, theta, phi, alpha, want_field, keep_aperture)
+
+
+def test_out_of_memory_batch_is_answered_and_the_server_carries_on():
+    be = OomBackend()
+    srv = Server(be, budget_bytes=100, footprint=foot, max_dirs=16)
+    reqs = [req(0, 0.0, 16, 2), req(1, 0.01, 16, 2, kappa0=6.0), req(2, 0.02, 16, 2, kappa0=6.0),
+            req(3, 0.05, 16, 3)]
+    res = srv.run(reqs)
+    assert [res[i].status for i in range(4)] == [0, 2, 2, 0]
+    assert srv.enomem >= 1
+    assert np.allclose(res[3].rcs, 1000 * reqs[3].theta + reqs[3].phi)
