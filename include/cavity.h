@@ -65,7 +65,7 @@ enum { CAVITY_POL_THETA = 0, CAVITY_POL_PHI = 1 };
 
 typedef struct {
   double a, b, c;        /* aperture [0,a]x[0,b], depth c                     */
-  int nx, ny, nz;        /* grid intervals; nx, ny powers of two in [4, 512];  */
+  int nx, ny, nz;        /* grid intervals; nx, ny powers of two in [4, 1024]; */
                          /* nz >= 2                                            */
   int precision;         /* CAVITY_FP64: every step in FP64 (complex128 field) */
                          /* CAVITY_MIXED: FP64 elimination and FP64-accurate   */

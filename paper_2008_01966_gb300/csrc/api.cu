@@ -29,8 +29,8 @@ extern "C" cavity_status cavity_setup(const cavity_desc* desc, void* cuda_stream
     return CAVITY_EINVAL;
   };
   if (!(d.a > 0) || !(d.b > 0) || !(d.c > 0)) return bad("a, b, c must be positive");
-  if (!pow2(d.nx) || !pow2(d.ny) || d.nx < 4 || d.ny < 4 || d.nx > 512 || d.ny > 512)
-    return bad("nx, ny must be powers of two in [4, 512]");
+  if (!pow2(d.nx) || !pow2(d.ny) || d.nx < 4 || d.ny < 4 || d.nx > 1024 || d.ny > 1024)
+    return bad("nx, ny must be powers of two in [4, 1024]");
   if (d.nz < 2 || d.nz > 1 << 20) return bad("nz must be in [2, 2^20]");
   if (d.precision != CAVITY_FP64 && d.precision != CAVITY_MIXED) return bad("unknown precision");
   if (d.pad_factor != 0 && d.pad_factor != 4) return bad("pad_factor must be 0 or 4");

@@ -454,6 +454,6 @@ inline cavity_status dispatch_log(int v, F&& f) {
   }
 }
 __host__ __device__ constexpr int clog2(int v) { return v <= 1 ? 0 : 1 + clog2(v >> 1); }
-// log2 of the grid sizes nx, ny accepted by cavity_setup (4 .. 512)
+// log2 of the grid sizes nx, ny accepted by cavity_setup (4 .. 1024)
 #define CAV_LOG_MIN 2
-#define CAV_LOG_MAX 9
+#define CAV_LOG_MAX 10

@@ -33,8 +33,11 @@ __host__ __device__ constexpr int pidx(int i) { return i + (i >> 4); }
 // line length in shared memory: room for the padded layout and for the
 // transposed tile of the warp transform (n + n/8 for n >= 64)
 __host__ __device__ constexpr int padded_len(int n) { return n + (n >> 3) + 2; }
-// block transform: elements per thread (radix up to 8)
+// block transform: elements per thread (radix up to 8), and at most
+// FFT_MAX_TPL threads per line: lines longer than 8 FFT_MAX_TPL points give
+// each thread several butterflies per pass (16 points per thread at 4096)
 template <typename T> struct FftE { static constexpr int E = 8, LRMAX = 3; };
+#define FFT_MAX_TPL 256
 // warp transform (FP32, 64 <= n <= 1024): n = LW * RV lanes x values per lane
 __host__ __device__ constexpr bool warp_fft_ok(int n, int elem_bytes) {
   return elem_bytes == 8 && n >= 64 && n <= 1024;
@@ -47,7 +50,7 @@ __host__ __device__ constexpr int warp_lanes(int n) {
 // threads cooperating on one line (same as LineShape<T, log2 n>::TPL)
 template <typename T> __host__ __device__ constexpr int fft_tpl(int n) {
   if (warp_fft_ok(n, (int)sizeof(C<T>))) return warp_lanes(n);
-  return n >= FftE<T>::E ? n / FftE<T>::E : 1;
+  return n >= FftE<T>::E ? (n / FftE<T>::E < FFT_MAX_TPL ? n / FftE<T>::E : FFT_MAX_TPL) : 1;
 }
 
 // twiddle constants (forward sign); the inverse uses the conjugates
@@ -364,7 +367,8 @@ __device__ void fft_inplace(C<T>* base, int lstride, int n, int logn, int nlines
   constexpr int E = FftE<T>::E, LRMAX = FftE<T>::LRMAX;
   const int tid = threadIdx.x + threadIdx.y * blockDim.x;
   const int nthr = blockDim.x * blockDim.y;
-  const int tpl = n >= E ? n / E : 1;
+  const int tpl = fft_tpl<T>(n);
+  const int ept = n / tpl;               // points per thread: 8, or 16 at 4096
   const int lpg = nthr >= tpl ? nthr / tpl : 1;
   const int lg = tid / tpl, t = tid - lg * tpl;
   for (int l0 = 0; l0 < nlines; l0 += lpg) {
@@ -384,16 +388,33 @@ __device__ void fft_inplace(C<T>* base, int lstride, int n, int logn, int nlines
     int s = 0;
     for (int p = 0; p < k; ++p) {
       const int lr = logn / k + (p < logn % k ? 1 : 0);
-      switch (lr) {
-        case 3: fft_pass<T, INV, 3, 1>(line, n, s, t, tpl, tw, twlog, active); break;
-        case 2: fft_pass<T, INV, 2, 2>(line, n, s, t, tpl, tw, twlog, active); break;
-        default: fft_pass<T, INV, 1, 4>(line, n, s, t, tpl, tw, twlog, active); break;
+      if (ept == 16) {
+        switch (lr) {
+          case 3: fft_pass<T, INV, 3, 2>(line, n, s, t, tpl, tw, twlog, active); break;
+          case 2: fft_pass<T, INV, 2, 4>(line, n, s, t, tpl, tw, twlog, active); break;
+          default: fft_pass<T, INV, 1, 8>(line, n, s, t, tpl, tw, twlog, active); break;
+        }
+      } else {
+        switch (lr) {
+          case 3: fft_pass<T, INV, 3, 1>(line, n, s, t, tpl, tw, twlog, active); break;
+          case 2: fft_pass<T, INV, 2, 2>(line, n, s, t, tpl, tw, twlog, active); break;
+          default: fft_pass<T, INV, 1, 4>(line, n, s, t, tpl, tw, twlog, active); break;
+        }
       }
       s += lr;
     }
   }
   __syncthreads();
 }
+
+// threads cooperating on one line of length 2^LOGN
+template <typename T, int LOGN> struct LineShape {
+  static constexpr bool WARP = sizeof(T) == 4 && LOGN >= 6 && LOGN <= 10;
+  static constexpr int LW = 1 << (LOGN / 2);
+  static constexpr int RV = (1 << LOGN) / LW;
+  static constexpr int TPL =
+      WARP ? LW : (LOGN >= 3 ? ((1 << LOGN) / 8 < FFT_MAX_TPL ? (1 << LOGN) / 8 : FFT_MAX_TPL) : 1);
+};
 
 // radix (log2) of pass P of the balanced schedule for a length 2^LOGN
 template <int LOGN, int P> struct BlockRadix {
@@ -413,20 +434,14 @@ __device__ __forceinline__ void block_passes(C<T>* line, int t, int tpl, const C
   constexpr int K = BlockRadix<LOGN, 0>::K;
   if constexpr (P < K) {
     constexpr int LR = BlockRadix<LOGN, P>::LR;
-    constexpr int PER = 8 >> LR;
+    constexpr int EPT = (1 << LOGN) / LineShape<T, LOGN>::TPL;   // 8, or 16 at 4096
+    constexpr int PER = EPT >> LR;
     fft_pass<T, INV, LR, PER, P == 0, P == K - 1, Op>(line, 1 << LOGN, BlockRadix<LOGN, P>::S, t,
                                                       tpl, tw, twlog, active, lidx, op);
     block_passes<T, INV, LOGN, P + 1, Op>(line, t, tpl, tw, twlog, active, lidx, op);
   }
 }
 
-// threads cooperating on one line of length 2^LOGN
-template <typename T, int LOGN> struct LineShape {
-  static constexpr bool WARP = sizeof(T) == 4 && LOGN >= 6 && LOGN <= 10;
-  static constexpr int LW = 1 << (LOGN / 2);
-  static constexpr int RV = (1 << LOGN) / LW;
-  static constexpr int TPL = WARP ? LW : (LOGN >= 3 ? (1 << LOGN) / 8 : 1);
-};
 
 // In-place FFT of `nlines` padded lines (stride lstride) of the compile-time
 // length 2^LOGN: the warp transform where it applies, else the block

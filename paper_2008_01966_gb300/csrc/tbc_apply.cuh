@@ -65,6 +65,10 @@ template <typename T> __host__ __device__ constexpr int pairs_per_cta(int n) {
 // pair-of-FP32 ones spill ~450 bytes per thread at this bound, but one CTA per
 // SM without spills was slower: pass B 10.6 ms against 7.6 ms)
 #define TBC_BOUNDS __launch_bounds__(LINES_THREADS, 2)
+// the same per grid size: with 4096-point lines (1024-point sides) a CTA's
+// lines take most of the shared memory, so one CTA per SM, with the whole
+// register file for the 16 points per thread of the block transform
+#define TBC_BOUNDS_LN(LN) __launch_bounds__(LINES_THREADS, (LN) >= 10 ? 1 : 2)
 
 // The pass kernels are instantiated per grid size: LNY = log2 ny (passes A,
 // C), LNX = log2 nx (passes B, D).  With the period pad = 4: Px = 4 nx,
@@ -175,7 +179,7 @@ struct ScatterA : LineId<T> {
 };
 
 template <typename T, int LNY>
-__global__ void TBC_BOUNDS k_tbcA(const C<T>* __restrict__ x, C<T>* __restrict__ Vy, TbcP p,
+__global__ void TBC_BOUNDS_LN(LNY) k_tbcA(const C<T>* __restrict__ x, C<T>* __restrict__ Vy, TbcP p,
                                   const C<T>* __restrict__ tw, const C<T>* __restrict__ eh_c,
                                   const C<T>* __restrict__ eh_s) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
@@ -241,9 +245,11 @@ __global__ void TBC_BOUNDS k_tbcA(const C<T>* __restrict__ x, C<T>* __restrict__
 // last write of the first inverse transforms of pass B: output t (k = t mod
 // Px) of line (r, l), |t| < Px/4, times the kernel table at (|2t + r|, |j2|),
 // written to slot t mod Px/2 (other outputs are not needed)
-template <typename T, int LNX>
+// STAGED: kh holds the rows of the block's columns in shared memory,
+// [l][j1 < Px/2]; else kh is the whole quarter box in global memory, [j2][j1]
+template <typename T, int LNX, bool STAGED = true>
 struct KhatB : LineId<T> {
-  const C<T>* kh;                 // rows |j2| of the block's columns, [l][j1 < Px/2]
+  const C<T>* kh;
   int j0, Py, L;
   __device__ __forceinline__ void st(int lr, C<T>* line, int k, C<T> v) const {
     constexpr int Px = 4 << LNX, hp = Px / 2, qp = Px / 4;
@@ -257,14 +263,33 @@ struct KhatB : LineId<T> {
     C<T> o = czero<T>();
     if (j1 != -hp && j < Py && j != Py / 2) {
       const int j1a = j1 < 0 ? -j1 : j1;
-      o = cmul<T>(v, kh[l * hp + j1a]);
+      if constexpr (STAGED) {
+        o = cmul<T>(v, kh[l * hp + j1a]);
+      } else {
+        const int j2a = j < Py / 2 ? j : Py - j;
+        o = cmul<T>(v, kh[(size_t)j2a * hp + j1a]);
+      }
     }
     line[pidx(u)] = o;
   }
 };
 
+// pass B stages the two parity kernels and the kernel-table rows of its
+// columns in shared memory where they fit beside its lines (every FP32 grid;
+// 16-byte types up to 512 points per side); with 4096-point lines of 16-byte
+// types it reads them from global memory instead
+template <typename T> __host__ __device__ constexpr size_t smem_b_lines(int nx) {
+  return sizeof(C<T>) * 2 * (size_t)pairs_per_cta<T>(4 * nx) * (size_t)padded_len(4 * nx);
+}
+template <typename T> __host__ __device__ constexpr size_t smem_b_tables(int nx) {
+  return sizeof(C<T>) * (2 * 4 * (size_t)nx + (size_t)pairs_per_cta<T>(4 * nx) * 2 * (size_t)nx);
+}
+template <typename T> __host__ __device__ constexpr bool b_staged(int nx) {
+  return smem_b_lines<T>(nx) + smem_b_tables<T>(nx) <= 200 * 1024;
+}
+
 template <typename T, int LNX>
-__global__ void TBC_BOUNDS k_tbcB(const C<T>* __restrict__ Vy, C<T>* __restrict__ W, TbcP p,
+__global__ void TBC_BOUNDS_LN(LNX) k_tbcB(const C<T>* __restrict__ Vy, C<T>* __restrict__ W, TbcP p,
                                   const C<T>* __restrict__ tw, const C<T>* __restrict__ eh_c,
                                   const C<T>* __restrict__ eh_s, const C<T>* __restrict__ kh) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
@@ -282,9 +307,11 @@ __global__ void TBC_BOUNDS k_tbcB(const C<T>* __restrict__ Vy, C<T>* __restrict_
   // shared memory: 2L lines, then the two parity kernels [2][Px], then the
   // kernel-table rows |j2| of the L columns [L][Px/2] (staged once per block,
   // so the fused products read shared memory instead of waiting on loads)
+  constexpr bool STAGE = b_staged<T>(nx);
   C<T>* eh_sm = buf + (size_t)2 * L * ls;
   C<T>* kh_sm = eh_sm + 2 * Px;
-  {
+  const C<T>* eh_use = xcos ? eh_c : eh_s;
+  if constexpr (STAGE) {
     const C<T>* eh = xcos ? eh_c : eh_s;
     for (int t = tid; t < 2 * Px; t += nthr) eh_sm[t] = eh[t];
     for (int idx = tid; idx < L * (Px / 2); idx += nthr) {
@@ -293,6 +320,7 @@ __global__ void TBC_BOUNDS k_tbcB(const C<T>* __restrict__ Vy, C<T>* __restrict_
       const int j2a = j < Py / 2 ? j : Py - j;
       kh_sm[idx] = (j < Py && j != Py / 2) ? kh[(size_t)j2a * (Px / 2) + j1] : czero<T>();
     }
+    eh_use = eh_sm;
   }
   // cooperative, coalesced gather of the L columns (consecutive threads take
   // consecutive columns of a row); the mirrored lines cover every slot but
@@ -319,8 +347,8 @@ __global__ void TBC_BOUNDS k_tbcB(const C<T>* __restrict__ Vy, C<T>* __restrict_
     }
     __syncthreads();
   }
-  KhatB<T, LNX> kb;
-  kb.kh = kh_sm;
+  KhatB<T, LNX, STAGE> kb;
+  kb.kh = STAGE ? kh_sm : kh;
   kb.j0 = j0;
   kb.Py = Py;
   kb.L = L;
@@ -333,7 +361,7 @@ __global__ void TBC_BOUNDS k_tbcB(const C<T>* __restrict__ Vy, C<T>* __restrict_
     constexpr int LPW = 32 / LineShape<T, LPX>::TPL;
     const int first = (tid >> 5) * LPW;
     OwnParity<T> fwd;
-    fwd.eh = eh_sm;
+    fwd.eh = eh_use;
     fwd.P = Px;
     fwd.L = L;
     fft_warp_lines<T, false, LPX>(buf, ls, first, LPW, tw, p.twlog, fwd);
@@ -342,7 +370,7 @@ __global__ void TBC_BOUNDS k_tbcB(const C<T>* __restrict__ Vy, C<T>* __restrict_
     __syncthreads();
   } else {
     ParityProducts<T, LineId<T>> fwd;
-    fwd.eh = eh_sm;
+    fwd.eh = eh_use;
     fwd.P = Px;
     fwd.L = L;
     fwd.ls = ls;
@@ -407,7 +435,7 @@ struct StoreZ : LineId<T> {
 };
 
 template <typename T, int LNY>
-__global__ void TBC_BOUNDS k_tbcC(const C<T>* __restrict__ W, C<T>* __restrict__ Z, TbcP p,
+__global__ void TBC_BOUNDS_LN(LNY) k_tbcC(const C<T>* __restrict__ W, C<T>* __restrict__ Z, TbcP p,
                                   const C<T>* __restrict__ tw) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   C<T>* buf = (C<T>*)sm_raw;
@@ -463,7 +491,7 @@ struct ColD {
 };
 
 template <typename T, int LNX>
-__global__ void TBC_BOUNDS k_tbcD(const C<T>* __restrict__ Z, C<T>* __restrict__ O, TbcP p,
+__global__ void TBC_BOUNDS_LN(LNX) k_tbcD(const C<T>* __restrict__ Z, C<T>* __restrict__ O, TbcP p,
                                   const C<T>* __restrict__ tw) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   C<T>* buf = (C<T>*)sm_raw;
@@ -725,8 +753,7 @@ template <> struct Tabs<float> {
 // shared memory of each pass (bytes) for the grid sizes of g
 template <typename T> static size_t smem_a(int ny) { return sizeof(C<T>) * 2 * pairs_per_cta<T>(4 * ny) * (size_t)padded_len(4 * ny); }
 template <typename T> static size_t smem_b(int nx) {
-  const size_t L = pairs_per_cta<T>(4 * nx);
-  return sizeof(C<T>) * (2 * L * (size_t)padded_len(4 * nx) + 2 * 4 * (size_t)nx + L * 2 * (size_t)nx);
+  return smem_b_lines<T>(nx) + (b_staged<T>(nx) ? smem_b_tables<T>(nx) : 0);
 }
 template <typename T> static size_t smem_c(int ny) { return sizeof(C<T>) * lines_per_cta<T>(4 * ny) * (size_t)padded_len(4 * ny); }
 template <typename T> static size_t smem_d(int nx) { return sizeof(C<T>) * lines_per_cta<T>(2 * nx) * (size_t)padded_len(2 * nx); }

@@ -20,9 +20,7 @@ records arrival, start and completion times; p50/p99 latency and DOF/s
 
 runs a seeded Poisson stream with the mix of the serving workload (grids
 128^2 x 64, 256^2 x 128, 512^2 x 256 and 1024^2 x 512; four-layer fills;
-1-32 directions; field kept for grids up to 256^2).  The library's transforms
-support grids up to 512^2, so 1024^2 requests are answered with the status
-CAVITY_EINVAL without using the GPU.
+1-32 directions; field kept for grids up to 256^2).
 """
 
 import argparse
@@ -37,7 +35,7 @@ import numpy as np
 
 LAYER_EPS = (4 + 1j, 2 + 0.5j, 6 + 0.1j, 1 + 0j)
 GRIDS = ((128, 64), (256, 128), (512, 256), (1024, 512))
-MAX_SIDE = 512
+MAX_SIDE = 1024
 
 
 @dataclass

@@ -174,9 +174,12 @@ def test_operator_matches_fft_rule(gb, case):
     assert rel(y32, ref) < 1e-5
 
 
-# grid sizes covering log2 nx and log2 ny = 2..9: every per-size instantiation
-# of the transform passes (line lengths 8 .. 2048, warp and block transforms)
-SIZES = [(4, 256), (256, 4), (8, 512), (512, 8), (32, 64), (64, 32), (128, 128)]
+# grid sizes covering log2 nx and log2 ny = 2..10: every per-size instantiation
+# of the transform passes (line lengths 8 .. 4096, warp and block transforms;
+# at 4096 points 16 per thread, and pass B of the 16-byte types without its
+# tables in shared memory)
+SIZES = [(4, 256), (256, 4), (8, 512), (512, 8), (32, 64), (64, 32), (128, 128), (4, 1024),
+         (1024, 4)]
 
 
 @pytest.mark.parametrize("nx,ny", SIZES)
@@ -392,3 +395,52 @@ def test_truncated_expansion_matches_oracle(gb, precision):
         assert rel(ap[d], X[d]) < (1e-10 if fp64 else 1e-8)
         F = oracle_field(cav, sysm.prof, X[d]).ravel()
         assert rel(fl[d], F) < (1e-10 if fp64 else 1e-5)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("nx,ny", [(1024, 32), (32, 1024)])
+def test_solve_on_1024_point_sides(gb, precision, nx, ny):
+    """Whole solves with a 1024-point side (4096-point lines in the operator,
+    2048-point lines in the field synthesis) against the oracle's GMRES solve
+    (1e-12, true residual): aperture and field per direction, 1e-10 (FP64) and
+    1e-5 (mixed)."""
+    w = dict(a=1.0, b=1.0, c=0.25, nx=nx, ny=ny, nz=6, kappa0=2 * np.pi * 3.0,
+             layers=[(3, 2.0 + 0.5j), (3, 1.0 + 0j)])
+    cav = ocav(w)
+    sysm = ApertureSystem(cav)
+    th, ph, al = workloads.directions(2, 53)
+    B = np.array([oracle_rhs(cav, t, p, a) for t, p, a in zip(th, ph, al)])
+    X, res = sysm.solve_gmres(B, rtol=1e-13, restart=300, maxiter=300)
+    assert np.all(res < 1e-12), res
+    fp64 = precision == "fp64"
+    g = gcav(gb, w, precision=precision, gmres_tol=1e-13 if fp64 else 1e-10)
+    ap, fl, it, r = g.solve(w['kappa0'], w['layers'], th, ph, al)
+    ap, fl = ap.cpu().numpy(), fl.cpu().numpy()
+    for d in range(2):
+        assert rel(ap[d], X[d]) < (1e-10 if fp64 else 1e-5)
+        F = oracle_field(cav, sysm.prof, X[d]).ravel()
+        assert rel(fl[d], F) < (1e-10 if fp64 else 1e-5)
+
+
+def test_1024_square_layered_full_size(gb):
+    """The largest serving grid, 1024 x 1024 x 512 with the four-layer fill at
+    10 points per wavelength in the densest layer, 4 directions: the mixed and
+    the FP64 paths reach their residuals and agree (1e-6 on the aperture,
+    RCS to 1e-5), which the oracle cannot check at this size in a test's time;
+    the 1024-point lines themselves are checked against the oracle above."""
+    import workloads as wl
+    w = wl.scaled("layered4", 1024, nz=512, ndir=4)
+    sols = {}
+    for prec in ("mixed", "fp64"):
+        g = gcav(gb, w, precision=prec, gmres_tol=1e-10)
+        ap, _, it, r = g.solve(w['kappa0'], w['layers'], w['theta'], w['phi'], w['alpha'],
+                               field=False)
+        assert np.all(np.asarray(r) <= 1e-10), (prec, r)
+        sig = g.rcs(ap, w['theta'], w['phi'], "theta")
+        sols[prec] = (ap.cpu().numpy(), np.asarray(sig))
+        g.close()
+        del ap
+        torch.cuda.empty_cache()
+    for d in range(4):
+        assert rel(sols["mixed"][0][d], sols["fp64"][0][d]) < 1e-6
+    assert np.all(np.abs(sols["mixed"][1] - sols["fp64"][1]) <= 1e-5 * np.abs(sols["fp64"][1]))

@@ -164,9 +164,9 @@ def test_busy_context_is_never_evicted():
 def test_rejections():
     be = FakeBackend()
     srv = Server(be, budget_bytes=100, footprint=lambda g, *a: 10 * g[3], max_dirs=8)
-    reqs = [req(0, 0.0, 1024, 2), req(1, 0.0, 16, 2), req(2, 0.0, 8, 2)]
+    reqs = [req(0, 0.0, 2048, 2), req(1, 0.0, 16, 2), req(2, 0.0, 8, 2)]
     res = srv.run(reqs)
-    assert res[0].status == 1            # grid above the library's limit
+    assert res[0].status == 1            # grid above the library's limit (1024)
     assert res[1].status == 2            # footprint 160 > budget 100
     assert res[2].status == 0
 
