@@ -431,7 +431,9 @@ def main():
                 "peak_admitted_gb": srv.peak / 2**30})
     print(json.dumps(out))
     if args.dump:
-        kept = [r for r in reqs if r.keep_aperture and res[r.rid].status == 0]
+        # grids above 512 points per side are kept by RCS only (a 1024^2
+        # aperture vector is 50 MB, and no reference checks it)
+        kept = [r for r in reqs if r.keep_aperture and res[r.rid].status == 0 and r.geom[3] <= 512]
         # one aperture array per kept request (their grids differ)
         aps = {"aperture_%d" % i: res[r.rid].aperture[0].numpy() for i, r in enumerate(kept)}
         np.savez(args.dump, precision=args.precision, tol=1e-7,
