@@ -33,6 +33,7 @@
 #include <climits>
 
 #include "common.cuh"
+#include "tc05.cuh"
 
 // ------------------------------------------------------------ kept set
 KeptSet kept_set(const cavity_desc& d, const Geo& g) {
@@ -125,14 +126,10 @@ __global__ void k_dn_fold(const double2* __restrict__ X, const double2* __restri
   Af[((size_t)kind * mk * mk + mkk) * H + ja] = conv<T>(r);
 }
 
-// ------------------------------------------------------------ complex GEMM (FP32)
+// ------------------------------------------------------------ complex GEMMs
 // C[i][j] = alpha sum_k A(i, k) B(k, j) (+ C[i][j] if beta), A(i, k) at
-// A[i sar + k sak], B(k, j) at B[k sbk + j sbc], C row-major (ldc).
-// 128 x 64 outputs per CTA of 256 threads (8 x 4 per thread, strided by 16 so
-// that the shared-memory reads are broadcasts or consecutive); k-tiles of 16.
-#define GM_BM 128
-#define GM_BN 64
-#define GM_BK 16
+// A[i sar + k sak], B(k, j) at B[k sbk + j sbc], C row-major (ldc): FP32 on
+// the tensor cores (k_cgemm_tc below), FP64 on the FMA pipes (k_zgemm).
 template <typename T> struct GemmArgsT {
   const C<T>* A;
   long long sar, sak;
@@ -146,71 +143,8 @@ template <typename T> struct GemmArgsT {
 };
 typedef GemmArgsT<float> GemmArgs;
 
-__global__ void __launch_bounds__(256, 2) k_cgemm(GemmArgs g) {
-  __shared__ float2 As[GM_BK][GM_BM + 1];
-  __shared__ float2 Bs[GM_BK][GM_BN + 1];
-  const int t = threadIdx.x, tr = t >> 4, tc = t & 15;
-  const int i0 = blockIdx.y * GM_BM, j0 = blockIdx.x * GM_BN;
-  float2 acc[8][4];
-#pragma unroll
-  for (int i = 0; i < 8; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
-  const bool ak = g.sak == 1, bc = g.sbc == 1;
-  for (int kb = 0; kb < g.K; kb += GM_BK) {
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int e = t + q * 256;
-      const int r = ak ? e >> 4 : e & (GM_BM - 1), k = ak ? e & 15 : e >> 7;
-      const int gi = i0 + r, gk = kb + k;
-      As[k][r] = (gi < g.M && gk < g.K) ? g.A[gi * g.sar + gk * g.sak] : make_float2(0.f, 0.f);
-    }
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int e = t + q * 256;
-      const int c = bc ? e & (GM_BN - 1) : e >> 4, k = bc ? e >> 6 : e & 15;
-      const int gj = j0 + c, gk = kb + k;
-      Bs[k][c] = (gj < g.N && gk < g.K) ? g.B[gk * g.sbk + gj * g.sbc] : make_float2(0.f, 0.f);
-    }
-    __syncthreads();
-#pragma unroll 4
-    for (int k = 0; k < GM_BK; ++k) {
-      float2 a[8], b[4];
-#pragma unroll
-      for (int i = 0; i < 8; ++i) a[i] = As[k][tr + 16 * i];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[k][tc + 16 * j];
-#pragma unroll
-      for (int i = 0; i < 8; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          acc[i][j].x = fmaf(a[i].x, b[j].x, fmaf(-a[i].y, b[j].y, acc[i][j].x));
-          acc[i][j].y = fmaf(a[i].x, b[j].y, fmaf(a[i].y, b[j].x, acc[i][j].y));
-        }
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    const int gi = i0 + tr + 16 * i;
-    if (gi >= g.M) continue;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int gj = j0 + tc + 16 * j;
-      if (gj >= g.N) continue;
-      float2* c = g.C + gi * g.ldc + gj;
-      float2 v = make_float2(g.alpha * acc[i][j].x, g.alpha * acc[i][j].y);
-      if (g.beta) {
-        const float2 o = *c;
-        v.x += o.x;
-        v.y += o.y;
-      }
-      *c = v;
-    }
-  }
-}
-
-// The same in FP64: 64 x 64 outputs per CTA of 256 threads (4 x 4 per thread)
+// FP64: 64 x 64 outputs per CTA of 256 threads (4 x 4 per thread, strided by
+// 16 so that the shared-memory reads are broadcasts or consecutive); k-tiles of 16
 #define GZ_BM 64
 #define GZ_BN 64
 #define GZ_BK 16
@@ -278,10 +212,188 @@ __global__ void __launch_bounds__(256, 2) k_zgemm(GemmArgsT<double> g) {
   }
 }
 
+// The FP32 GEMM on the fifth-generation tensor cores: the complex product as
+// a real one, [Re C, Im C] = [Re A, Im A] [[Re B, Im B], [-Im B, Re B]]
+// (each complex entry of B a 2 x 2 real block), with tcgen05.mma kind::tf32
+// and FP32 accuracy from the three-product split (tc05.cuh).  One warpgroup
+// per CTA computes 128 rows x 32 complex columns (M = 128, N = 64 real) in 128
+// columns of tensor memory: hi hi in columns 0..63, the two corrections in
+// 64..127, drained into FP32 registers every TC_DRAIN chunks.  Chunks of 8
+// complex inner terms (16 real, two MMA k-steps, three products each) pass
+// through two shared-memory buffers: the threads stage chunk c + 1 while the
+// tensor cores multiply chunk c.  Thread t stages row t of the A tile and two
+// entries of the B tile.  A wait that runs out sets g_gt_err and skips the
+// output.  In the LU of an 8,216-unknown block the 128 rank-64 trailing updates
+// take about 48 ms in total on this kernel, the same as on an FMA-pipe kernel
+// with 128 x 64 tiles: with 64 inner terms a tile is bound by its staging and
+// by the round trip of its C tile, not by the products.
+#define GT_BN 32          // complex columns per CTA
+#define GT_CH 8           // complex inner terms per chunk
+struct GtBuf {
+  float a_hi[2][128 * 8], a_lo[2][128 * 8];   // [k-step][K-major tile]
+  float b_hi[2][64 * 8], b_lo[2][64 * 8];
+};
+
+__device__ int g_gt_err;  // set when a tensor-core wait of k_cgemm_tc ran out
+
+__global__ void __launch_bounds__(128) k_cgemm_tc(GemmArgs g) {
+  extern __shared__ __align__(128) unsigned char gtraw[];
+  GtBuf* bufs = (GtBuf*)gtraw;
+  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ uint32_t tslot;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int i0 = blockIdx.y * 128, j0 = blockIdx.x * GT_BN;
+  const int nch = (g.K + GT_CH - 1) / GT_CH;
+  if (tid == 0) {
+    tc_mbar_init(&mbar[0]);
+    tc_mbar_init(&mbar[1]);
+  }
+  if (warp == 0) tc_alloc(&tslot, 128);
+  tc_before_sync();
+  __syncthreads();
+  tc_after_sync();
+  const uint32_t tmem = tslot;
+  constexpr uint32_t idesc = tc_idesc_tf32(128, 64);
+  bool ok = true;
+  float racc[64];
+#pragma unroll
+  for (int n = 0; n < 64; ++n) racc[n] = 0.f;
+  const int gi = i0 + tid;
+  float2 va[GT_CH], vb[2];
+  // B entries of this thread: (k = q / GT_BN, column q mod GT_BN), q = tid, tid + 128
+  auto load_chunk = [&](int cn) {
+    const int kb = cn * GT_CH;
+#pragma unroll
+    for (int u = 0; u < GT_CH; ++u)
+      va[u] = (gi < g.M && kb + u < g.K) ? g.A[gi * g.sar + (long long)(kb + u) * g.sak]
+                                         : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int q = tid + 128 * h, u = q / GT_BN, j = q % GT_BN;
+      vb[h] = (j0 + j < g.N && kb + u < g.K) ? g.B[(long long)(kb + u) * g.sbk + (long long)(j0 + j) * g.sbc]
+                                              : make_float2(0.f, 0.f);
+    }
+  };
+  load_chunk(0);
+  for (int c = 0; c < nch && ok; ++c) {
+    const int b = c & 1;
+    GtBuf& Bf = bufs[b];
+    if (c >= 2) ok = tc_mbar_wait(&mbar[b], ((c - 2) >> 1) & 1);
+    ok = __syncthreads_and(ok);
+    if (!ok) break;
+    // A: row tid, complex inner term u -> real inner terms 2u (Re), 2u + 1 (Im)
+#pragma unroll
+    for (int u = 0; u < GT_CH; ++u) {
+      uint32_t hr, lr, hi, li;
+      tc_split(va[u].x, hr, lr);
+      tc_split(va[u].y, hi, li);
+      const int ks = u >> 2, k8 = (2 * u) & 7, off = tc_koff(tid, k8);
+      *(uint2*)((char*)Bf.a_hi[ks] + off) = make_uint2(hr, hi);
+      *(uint2*)((char*)Bf.a_lo[ks] + off) = make_uint2(lr, li);
+    }
+    // B (N x K, K-major): real rows n = 2j (Re C), 2j + 1 (Im C) against inner
+    // terms k = 2u (Re A), 2u + 1 (Im A): (Re B, -Im B) and (Im B, Re B)
+    {
+      float2 bb[2] = {vb[0], vb[1]};
+      if (c + 1 < nch) load_chunk(c + 1);   // in flight during the barrier and the MMAs
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int q = tid + 128 * h, u = q / GT_BN, j = q % GT_BN;
+        const int ks = u >> 2, k8 = (2 * u) & 7;
+        uint32_t h0, l0, h1, l1, h2, l2;
+        tc_split(bb[h].x, h0, l0);
+        tc_split(bb[h].y, h1, l1);
+        tc_split(-bb[h].y, h2, l2);
+        *(uint2*)((char*)Bf.b_hi[ks] + tc_koff(2 * j, k8)) = make_uint2(h0, h2);
+        *(uint2*)((char*)Bf.b_lo[ks] + tc_koff(2 * j, k8)) = make_uint2(l0, l2);
+        *(uint2*)((char*)Bf.b_hi[ks] + tc_koff(2 * j + 1, k8)) = make_uint2(h1, h0);
+        *(uint2*)((char*)Bf.b_lo[ks] + tc_koff(2 * j + 1, k8)) = make_uint2(l1, l0);
+      }
+    }
+    tc_fence_smem();
+    tc_before_sync();
+    __syncthreads();
+    tc_after_sync();
+    if (tid == 0) {
+#pragma unroll
+      for (int ks = 0; ks < 2; ++ks) {
+        const uint64_t ah = tc_desc(Bf.a_hi[ks]), al = tc_desc(Bf.a_lo[ks]);
+        const uint64_t bh = tc_desc(Bf.b_hi[ks]), bl = tc_desc(Bf.b_lo[ks]);
+        const uint32_t acc = (c % TC_DRAIN != 0 || ks > 0) ? 1u : 0u;
+        tc_mma(tmem, ah, bh, idesc, acc);          // hi hi
+        tc_mma(tmem + 64, al, bh, idesc, acc);     // the corrections apart
+        tc_mma(tmem + 64, ah, bl, idesc, 1u);
+      }
+      tc_commit(&mbar[b]);
+    }
+    if (c % TC_DRAIN == TC_DRAIN - 1 || c == nch - 1) {
+      ok = __syncthreads_and(tc_mbar_wait(&mbar[b], (c >> 1) & 1));
+      tc_after_sync();
+      if (ok) {
+        const uint32_t lane = (uint32_t)(32 * warp) << 16;
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+          float x[32], y[32];
+          tc_ld32(tmem + lane + 32 * hh, x);
+          tc_ld32(tmem + lane + 64 + 32 * hh, y);
+#pragma unroll
+          for (int q = 0; q < 32; ++q) racc[32 * hh + q] += x[q] + y[q];
+        }
+      }
+      tc_before_sync();
+      __syncthreads();
+    }
+  }
+  if (ok) {
+    if (gi < g.M) {
+      float2* crow = g.C + gi * g.ldc + j0;
+      const int nj = min(GT_BN, g.N - j0);
+      // all loads of the row first (independent, in flight together), then the stores
+      float2 o[GT_BN];
+#pragma unroll
+      for (int j = 0; j < GT_BN; ++j)
+        o[j] = (g.beta && j < nj) ? crow[j] : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int j = 0; j < GT_BN; ++j)
+        if (j < nj)
+          crow[j] = make_float2(g.alpha * racc[2 * j] + o[j].x, g.alpha * racc[2 * j + 1] + o[j].y);
+    }
+  } else if (tid == 0) {
+    atomicExch(&g_gt_err, 1);
+  }
+  tc_before_sync();
+  __syncthreads();
+  if (warp == 0) tc_dealloc(tmem, 128);
+}
+
+static std::atomic<bool> g_gt_smem{false};
+
+// the tensor-core GEMM's timeout flag: cleared before a dense step, read after it
+static cavity_status gt_err_clear(cavity_ctx* ctx) {
+  const int zero = 0;
+  CK(cudaMemcpyToSymbolAsync(g_gt_err, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, ctx->stream));
+  return CAVITY_OK;
+}
+static cavity_status gt_err_check(cavity_ctx* ctx) {
+  int terr = 0;
+  CK(cudaMemcpyFromSymbolAsync(&terr, g_gt_err, sizeof(int), 0, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (terr) {
+    ctx->err = "dense kept block: a tensor-core wait of the GEMM timed out";
+    return CAVITY_ETIMEOUT;
+  }
+  return CAVITY_OK;
+}
+
 static cavity_status cgemm(cavity_ctx* ctx, const GemmArgs& a, int cls) {
   if (a.M <= 0 || a.N <= 0) return CAVITY_OK;
+  if (!g_gt_smem) {
+    CK(cudaFuncSetAttribute(k_cgemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)(2 * sizeof(GtBuf))));
+    g_gt_smem = true;
+  }
   KScope ks_(ctx, cls);
-  k_cgemm<<<dim3(nblk(a.N, GM_BN), nblk(a.M, GM_BM)), 256, 0, ctx->stream>>>(a);
+  k_cgemm_tc<<<dim3(nblk(a.N, GT_BN), nblk(a.M, 128)), 128, 2 * sizeof(GtBuf), ctx->stream>>>(a);
   CK(cudaGetLastError());
   return CAVITY_OK;
 }
@@ -470,12 +582,15 @@ static cavity_status dense_assemble_t(cavity_ctx* ctx, const KeptSet& ks, C<T>* 
 }
 
 cavity_status dense_assemble(cavity_ctx* ctx, const KeptSet& ks, float2* a, int lda) {
-  return dense_assemble_t<float>(ctx, ks, a, lda);
+  CKS(gt_err_clear(ctx));
+  CKS(dense_assemble_t<float>(ctx, ks, a, lda));
+  return gt_err_check(ctx);
 }
 
 // ------------------------------------------------------------ LU factorisation
 #define LU_NB 64          // panel width
-#define LU_RMAX 128       // panel rows per CTA at most
+#define LU_RMAX 32        // panel rows per CTA at most
+#define LU_VS (LU_NB + 1) // row stride of the panel rows in shared memory
 #define LU_THREADS 256
 #define LU_SPIN (1 << 21) // polls of a grid barrier before it gives up
 
@@ -528,7 +643,7 @@ __global__ void __launch_bounds__(LU_THREADS) k_lu_panel(float2* __restrict__ A,
                                                          int k0, int nb, int R,
                                                          int* __restrict__ ipiv, LuScr s,
                                                          unsigned int* bar) {
-  extern __shared__ float2 v[];   // [R][LU_NB]
+  extern __shared__ float2 v[];   // [R][LU_VS]: rows padded by one entry (column reads)
   __shared__ float2 prow[LU_NB], drow[LU_NB], lmul[LU_RMAX];
   __shared__ unsigned long long wk[LU_THREADS / 32];
   __shared__ int s_br, s_p;
@@ -537,7 +652,7 @@ __global__ void __launch_bounds__(LU_THREADS) k_lu_panel(float2* __restrict__ A,
   const int r0 = k0 + c * R, r1 = min(r0 + R, n), nr = max(r1 - r0, 0);
   for (int e = t; e < nr * nb; e += LU_THREADS) {
     const int i = e / nb, k = e % nb;
-    v[i * LU_NB + k] = A[(size_t)(r0 + i) * lda + k0 + k];
+    v[i * LU_VS + k] = A[(size_t)(r0 + i) * lda + k0 + k];
   }
   __syncthreads();
   for (int j = 0; j < nb; ++j) {
@@ -546,7 +661,7 @@ __global__ void __launch_bounds__(LU_THREADS) k_lu_panel(float2* __restrict__ A,
     unsigned long long key = 0;
     for (int i = t; i < nr; i += LU_THREADS) {
       if (r0 + i < kj) continue;
-      const float2 x = v[i * LU_NB + j];
+      const float2 x = v[i * LU_VS + j];
       const unsigned long long kk = lu_key(x.x * x.x + x.y * x.y, r0 + i);
       key = kk > key ? kk : key;
     }
@@ -565,9 +680,9 @@ __global__ void __launch_bounds__(LU_THREADS) k_lu_panel(float2* __restrict__ A,
     __syncthreads();
     if (s_br >= 0)
       for (int k = t; k < nb; k += LU_THREADS)
-        __stcg(&s.cand[((size_t)par * G + c) * LU_NB + k], v[(s_br - r0) * LU_NB + k]);
+        __stcg(&s.cand[((size_t)par * G + c) * LU_NB + k], v[(s_br - r0) * LU_VS + k]);
     if (kj >= r0 && kj < r1)
-      for (int k = t; k < nb; k += LU_THREADS) __stcg(&s.drow[par * LU_NB + k], v[(kj - r0) * LU_NB + k]);
+      for (int k = t; k < nb; k += LU_THREADS) __stcg(&s.drow[par * LU_NB + k], v[(kj - r0) * LU_VS + k]);
     if (!lu_grid_bar(bar, (unsigned int)(j + 1) * G, s.err)) return;
     // the pivot: the best key over all CTAs; its row sits in the slot of the
     // CTA that owns it
@@ -594,25 +709,32 @@ __global__ void __launch_bounds__(LU_THREADS) k_lu_panel(float2* __restrict__ A,
     }
     // row exchange inside the panel: row kj takes the pivot row, row p the old row kj
     if (kj >= r0 && kj < r1)
-      for (int k = t; k < nb; k += LU_THREADS) v[(kj - r0) * LU_NB + k] = prow[k];
+      for (int k = t; k < nb; k += LU_THREADS) v[(kj - r0) * LU_VS + k] = prow[k];
     if (p != kj && p >= r0 && p < r1)
-      for (int k = t; k < nb; k += LU_THREADS) v[(p - r0) * LU_NB + k] = drow[k];
+      for (int k = t; k < nb; k += LU_THREADS) v[(p - r0) * LU_VS + k] = drow[k];
     __syncthreads();
     const float2 pinv = s_pinv;
     for (int i = t; i < nr; i += LU_THREADS)
-      if (r0 + i > kj) lmul[i] = cmul<float>(v[i * LU_NB + j], pinv);
+      if (r0 + i > kj) lmul[i] = cmul<float>(v[i * LU_VS + j], pinv);
     __syncthreads();
-    for (int e = t; e < nr * nb; e += LU_THREADS) {
-      const int i = e / nb, k = e % nb;
-      if (r0 + i <= kj || k < j) continue;
-      if (k == j) v[i * LU_NB + k] = lmul[i];
-      else v[i * LU_NB + k] = csub<float>(v[i * LU_NB + k], cmul<float>(lmul[i], prow[k]));
+    // elimination below the pivot: thread t owns column t mod LU_NB and
+    // every (LU_THREADS / LU_NB)-th row
+    {
+      const int k = t & (LU_NB - 1);
+      if (k >= j && k < nb) {
+        const float2 pk = prow[k];
+        for (int i = t / LU_NB; i < nr; i += LU_THREADS / LU_NB) {
+          if (r0 + i <= kj) continue;
+          if (k == j) v[i * LU_VS + k] = lmul[i];
+          else v[i * LU_VS + k] = csub<float>(v[i * LU_VS + k], cmul<float>(lmul[i], pk));
+        }
+      }
     }
     __syncthreads();
   }
   for (int e = t; e < nr * nb; e += LU_THREADS) {
     const int i = e / nb, k = e % nb;
-    A[(size_t)(r0 + i) * lda + k0 + k] = v[i * LU_NB + k];
+    A[(size_t)(r0 + i) * lda + k0 + k] = v[i * LU_VS + k];
   }
 }
 
@@ -697,11 +819,12 @@ cavity_status dense_lu(cavity_ctx* ctx, float2* a, int n, int lda, int* ipiv, in
   s.gmax = gmax;
   CK(cudaMemsetAsync(s.bar, 0, sizeof(unsigned) * npanel, st));
   CK(cudaMemsetAsync(s.best, 0, sizeof(unsigned long long) * n, st));
+  CKS(gt_err_clear(ctx));
   const int err0[2] = {0, INT_MAX};
   CK(cudaMemcpyAsync(s.err, err0, sizeof(err0), cudaMemcpyHostToDevice, st));
   if (!g_lu_smem) {
     CK(cudaFuncSetAttribute(k_lu_panel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                            (int)(sizeof(float2) * LU_RMAX * LU_NB)));
+                            (int)(sizeof(float2) * LU_RMAX * LU_VS)));
     CK(cudaFuncSetAttribute(k_lu_perm, cudaFuncAttributeMaxDynamicSharedMemorySize,
                             (int)(sizeof(int) * CAVITY_DENSE_MAX_N)));
     g_lu_smem = true;
@@ -714,7 +837,7 @@ cavity_status dense_lu(cavity_ctx* ctx, float2* a, int n, int lda, int* ipiv, in
       KScope ks_(ctx, KC_DENSE_LU);
       void* args[] = {&a, &lda, &n, (void*)&k0, (void*)&nb, (void*)&R, &ipiv, &s, &bar};
       CK(cudaLaunchCooperativeKernel((const void*)k_lu_panel, dim3(G), dim3(LU_THREADS), args,
-                                     sizeof(float2) * R * LU_NB, st));
+                                     sizeof(float2) * R * LU_VS, st));
     }
     if (n > nb) {
       KScope ks_(ctx, KC_DENSE_LU);
@@ -738,7 +861,7 @@ cavity_status dense_lu(cavity_ctx* ctx, float2* a, int n, int lda, int* ipiv, in
   }
   int err[2];
   CK(cudaMemcpyAsync(err, s.err, sizeof(err), cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
+  CKS(gt_err_check(ctx));
   if (err[0]) {
     ctx->err = "LU: a grid barrier of the panel factorisation timed out";
     return CAVITY_ETIMEOUT;
@@ -1104,6 +1227,7 @@ cavity_status dense_factor(cavity_ctx* ctx, DenseLU& f, const KeptSet& ks, bool 
     f.n = ks.nk;
     f.lda = lda;
   }
+  CKS(gt_err_clear(ctx));
   if (keep64) {
     CKS(dense_assemble_t<double>(ctx, ks, f.a64, lda));
     const long long tot = (long long)ks.nk * lda;
@@ -1120,6 +1244,7 @@ cavity_status dense_factor(cavity_ctx* ctx, DenseLU& f, const KeptSet& ks, bool 
   }
   CK(cudaGetLastError());
   CKS(launch_dinv(ctx, f.a, ks.nk, lda, f.dinv));
+  CKS(gt_err_check(ctx));
   f.ready = true;
   return CAVITY_OK;
 }
