@@ -275,9 +275,12 @@ struct KhatB : LineId<T> {
 };
 
 // pass B stages the two parity kernels and the kernel-table rows of its
-// columns in shared memory where they fit beside its lines (every FP32 grid;
-// 16-byte types up to 512 points per side); with 4096-point lines of 16-byte
-// types it reads them from global memory instead
+// columns in shared memory when lines and tables together take at most
+// 100 KB (every FP32 grid; 16-byte types up to 256 points per side); else it
+// reads them from global memory (they stay in L2), which leaves room for more
+// CTAs per SM: at 512 points per side the pair-of-FP32 pass B of the
+// four-layer 512^2 benchmark step went from 16.2 to 9.4 ms (one CTA per SM
+// with the 156 KB of staging, two without), and it is the only way at 1024
 template <typename T> __host__ __device__ constexpr size_t smem_b_lines(int nx) {
   return sizeof(C<T>) * 2 * (size_t)pairs_per_cta<T>(4 * nx) * (size_t)padded_len(4 * nx);
 }
@@ -285,7 +288,7 @@ template <typename T> __host__ __device__ constexpr size_t smem_b_tables(int nx)
   return sizeof(C<T>) * (2 * 4 * (size_t)nx + (size_t)pairs_per_cta<T>(4 * nx) * 2 * (size_t)nx);
 }
 template <typename T> __host__ __device__ constexpr bool b_staged(int nx) {
-  return smem_b_lines<T>(nx) + smem_b_tables<T>(nx) <= 200 * 1024;
+  return smem_b_lines<T>(nx) + smem_b_tables<T>(nx) <= 100 * 1024;
 }
 
 template <typename T, int LNX>
