@@ -14,11 +14,19 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libcavity.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["api.cu", "tbc.cu", "tbc_f32.cu", "tbc_df.cu", "zsweep.cu", "khat.cu", "rhs.cu", "precond.cu", "gmres.cu", "bgmres.cu", "dense.cu",
-           "field.cu", "field_fused.cu"]
+SOURCES = ["api.cu", "tbc.cu", "tbc_f32.cu", "tbc_df.cu", "tbc_df_k2.cu", "tbc_df_k5.cu",
+           "tbc_df_k7.cu", "tbc_df_k9.cu", "tbc_df_k10.cu", "zsweep.cu", "khat.cu", "rhs.cu",
+           "precond.cu", "gmres.cu", "bgmres.cu", "dense.cu", "field.cu", "field_fused.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fcx-limited-range",
          "-Xptxas", "-O3"]
+# The pair-of-FP32 pass kernels are instantiated in tbc_df_k*.cu (one unit per
+# size group, compiled in parallel) and launched from tbc_df.cu, which only
+# declares them: their host stubs need external linkage.  Each of these
+# kernels is instantiated in exactly one unit, so the linker's choice of stub
+# is unique.
+SPLIT = {"tbc_df.cu", "tbc_df_k2.cu", "tbc_df_k5.cu", "tbc_df_k7.cu", "tbc_df_k9.cu", "tbc_df_k10.cu"}
+SPLIT_FLAGS = ["-static-global-template-stub=false"]
 
 
 def _nvcc():
@@ -46,7 +54,7 @@ def build(verbose=False, ptxas_info=False):
         obj = os.path.join(BUILD, s.replace(".cu", ".o"))
         objs.append(obj)
         if _stale(obj, src) or ptxas_info:
-            cmd = [nvcc] + ARCH + FLAGS + ["-c", src, "-o", obj]
+            cmd = [nvcc] + ARCH + FLAGS + (SPLIT_FLAGS if s in SPLIT else []) + ["-c", src, "-o", obj]
             if ptxas_info:
                 cmd += ["-Xptxas", "-v"]
             jobs.append(cmd)

@@ -737,6 +737,18 @@ __global__ void k_combine(const C<T>* __restrict__ x, const C<T>* __restrict__ O
   }
 }
 
+// Explicit instantiation (EXT empty) or its declaration (EXT = extern) of the
+// four pass kernels of type T at log2 size LN; lets a type's instantiations
+// be compiled in several translation units (in parallel) while one unit
+// launches them.
+#define TBC_PASS_KERNELS(EXT, T, LN)                                                          \
+  EXT template __global__ void k_tbcA<T, LN>(const C<T>*, C<T>*, TbcP, const C<T>*,           \
+                                             const C<T>*, const C<T>*);                       \
+  EXT template __global__ void k_tbcB<T, LN>(const C<T>*, C<T>*, TbcP, const C<T>*,           \
+                                             const C<T>*, const C<T>*, const C<T>*);          \
+  EXT template __global__ void k_tbcC<T, LN>(const C<T>*, C<T>*, TbcP, const C<T>*);          \
+  EXT template __global__ void k_tbcD<T, LN>(const C<T>*, C<T>*, TbcP, const C<T>*);
+
 template <typename T> struct Tabs;
 template <> struct Tabs<double> {
   static const double2* tw(cavity_ctx* c) { return c->tw64; }

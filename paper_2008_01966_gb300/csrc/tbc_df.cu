@@ -13,6 +13,18 @@ template <> struct Tabs<df> {
   static const cdf* top(cavity_ctx* c) { return (const cdf*)c->top_p; }
 };
 
+// the pass kernels of the pair type are compiled in tbc_df_k*.cu (in
+// parallel: one unit with all sizes took three minutes)
+TBC_PASS_KERNELS(extern, df, 2)
+TBC_PASS_KERNELS(extern, df, 3)
+TBC_PASS_KERNELS(extern, df, 4)
+TBC_PASS_KERNELS(extern, df, 5)
+TBC_PASS_KERNELS(extern, df, 6)
+TBC_PASS_KERNELS(extern, df, 7)
+TBC_PASS_KERNELS(extern, df, 8)
+TBC_PASS_KERNELS(extern, df, 9)
+TBC_PASS_KERNELS(extern, df, 10)
+
 template cavity_status launch_apply<df>(cavity_ctx*, int, const cdf*, cdf*, void*, long long);
 
 __global__ void k_to_pair(const double2* __restrict__ a, cdf* __restrict__ b, long long n) {

@@ -1,0 +1,7 @@
+// Pass kernels of the pair-of-FP32 operator for log2 sizes 7, 8 (launched from
+// tbc_df.cu; one unit per group so that they compile in parallel).
+#include "df64.cuh"
+#include "tbc_apply.cuh"
+
+TBC_PASS_KERNELS(, df, 7)
+TBC_PASS_KERNELS(, df, 8)
