@@ -318,9 +318,16 @@ cavity_status cavity_lu_solve(cavity_ctx* ctx, const void* lu, int n, int lda, c
  *      at the first mixed solve after cavity_prepare or a change of mc; its
  *      3 mc^2 + 2 mc unknowns must not exceed CAVITY_DENSE_MAX_N.  Changes
  *      the iteration count, not the result beyond the solver tolerance.
+ *  CAVITY_OPT_FIELD_FUSED: the complex64 field synthesis of square grids of
+ *      32..512 points per side: 0 (default) = the fused persistent kernel at
+ *      512 points per side (faster there), the two-pass kernels elsewhere;
+ *      1 = the fused kernel on every square grid it supports; 2 = always the
+ *      two-pass kernels.  The fields agree to FP32 rounding.  The FP32
+ *      profiles are stored in the chosen kernel's layout at cavity_prepare,
+ *      so a change takes effect at the next prepare (a solve re-prepares).
  * CAVITY_EINVAL for an unknown option or a value out of range. */
 enum { CAVITY_OPT_PASS_B_2048 = 0, CAVITY_OPT_PASS_C_2048 = 1, CAVITY_OPT_GROUP_WIDTH = 2,
-       CAVITY_OPT_COARSE_MODES = 3, CAVITY_NUM_OPT = 4 };
+       CAVITY_OPT_COARSE_MODES = 3, CAVITY_OPT_FIELD_FUSED = 4, CAVITY_NUM_OPT = 5 };
 cavity_status cavity_set_option(cavity_ctx* ctx, int option, int value);
 cavity_status cavity_get_option(const cavity_ctx* ctx, int option, int* value);
 

@@ -32,9 +32,10 @@ SOLVERS = {"krylov": CAVITY_SOLVER_KRYLOV, "dense": CAVITY_SOLVER_DENSE}
 OUTER_RULES = {"trapezoid": 0, "parseval": 1}
 DENSE_MAX_N = 16384
 CAVITY_OPT_PASS_B_2048, CAVITY_OPT_PASS_C_2048, CAVITY_OPT_GROUP_WIDTH, \
-    CAVITY_OPT_COARSE_MODES = range(4)
+    CAVITY_OPT_COARSE_MODES, CAVITY_OPT_FIELD_FUSED = range(5)
 OPTIONS = {"pass_b_2048": CAVITY_OPT_PASS_B_2048, "pass_c_2048": CAVITY_OPT_PASS_C_2048,
-           "group_width": CAVITY_OPT_GROUP_WIDTH, "coarse_modes": CAVITY_OPT_COARSE_MODES}
+           "group_width": CAVITY_OPT_GROUP_WIDTH, "coarse_modes": CAVITY_OPT_COARSE_MODES,
+           "field_fused": CAVITY_OPT_FIELD_FUSED}
 NUM_KCLASS = 24
 
 

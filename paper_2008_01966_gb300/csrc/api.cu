@@ -505,6 +505,11 @@ extern "C" cavity_status cavity_set_option(cavity_ctx* ctx, int option, int valu
     case CAVITY_OPT_PASS_B_2048:
     case CAVITY_OPT_PASS_C_2048: ok = value == 0 || value == 1; break;
     case CAVITY_OPT_GROUP_WIDTH: ok = value >= 1 && value <= 16; break;
+    case CAVITY_OPT_FIELD_FUSED:
+      ok = value >= 0 && value <= 2;
+      // the FP32 profiles are laid out for one kernel or the other
+      if (ok && value != ctx->opt[option]) ctx->prepared = false;
+      break;
     case CAVITY_OPT_COARSE_MODES: {
       const KeptSet all = kept_set(ctx->desc, ctx->g);
       ok = value == 0 ||

@@ -185,7 +185,7 @@ struct cavity_ctx {
   size_t dn_scr_bytes = 0;
 
   // ---- implementation options (cavity_set_option)
-  int opt[CAVITY_NUM_OPT] = {0, 0, 16, 0};
+  int opt[CAVITY_NUM_OPT] = {0, 0, 16, 0, 0};
 
   // ---- launch accounting: counts always, CUDA-event times while timing is on
   long long nlaunch[KC_N] = {0};
@@ -349,6 +349,9 @@ cavity_status launch_field(cavity_ctx* ctx, int ndir, const double2* ap, C<T>* o
 // per-(level, m, n) FP32 profile records it reads, built from the FP64
 // profiles at prepare
 bool field_fused_supported(const Geo& g);
+// whether this context's complex64 field takes the fused kernel
+// (CAVITY_OPT_FIELD_FUSED; fixed at prepare, with the profile layout)
+bool field_fused_use(const cavity_ctx* ctx);
 cavity_status launch_prof_records(cavity_ctx* ctx);
 // the copy stream and at least n events for it (created once per context)
 inline cavity_status ensure_copy_stream(cavity_ctx* ctx, size_t n) {

@@ -295,7 +295,7 @@ cavity_status launch_field(cavity_ctx* ctx, int ndir, const double2* ap, C<T>* o
                            void* host_out) {
   const Geo& g = ctx->g;
   if constexpr (sizeof(T) == 4) {
-    if (field_fused_supported(g)) return launch_field_fused_all(ctx, ndir, ap, out, host_out);
+    if (field_fused_use(ctx)) return launch_field_fused_all(ctx, ndir, ap, out, host_out);
   }
   const bool layered = ctx->layers.size() > 1;
   const size_t slab = (size_t)3 * g.nx * (g.ny + 1) * sizeof(C<T>);

@@ -491,6 +491,15 @@ bool field_fused_supported(const Geo& g) {
   return g.nx == g.ny && g.lnx >= 5 && g.lnx <= 9;
 }
 
+// measured at the 16-direction 256^2 x 128 workload: fused 10.1 ms against
+// 5.5 ms for the two-pass kernels per step; at the 8-direction four-layer
+// 512^2 x 256 workload the fused kernel is the faster (20.5 against 26.8 ms)
+bool field_fused_use(const cavity_ctx* ctx) {
+  const int o = ctx->opt[CAVITY_OPT_FIELD_FUSED];
+  if (o == 2 || !field_fused_supported(ctx->g)) return false;
+  return o == 1 || ctx->g.lnx == 9;
+}
+
 size_t field_fused_work_bytes(const Geo& g) {
   return sizeof(float2) * (size_t)FF_RING * 3 * g.nx * (g.ny + 1) + 256;
 }

@@ -197,7 +197,7 @@ cavity_status launch_zsweep(cavity_ctx* ctx, double kappa0) {
   // FP32 copies of the profiles for the complex64 field of mixed contexts:
   // records for the fused kernel where it runs, else plain copies
   const bool mixed = ctx->desc.precision == CAVITY_MIXED;
-  const bool recs = mixed && field_fused_supported(g);
+  const bool recs = mixed && field_fused_use(ctx);
   const bool plain32 = mixed && !recs;
   if (!ctx->prof) CK(cudaMalloc(&ctx->prof, sizeof(double2) * nprof));
   if (plain32 && !ctx->prof32) CK(cudaMalloc(&ctx->prof32, sizeof(float2) * nprof));

@@ -86,3 +86,22 @@ def test_autotune_chooses_and_caches(gb, cav, tmp_path):
     for name in ("pass_b_2048", "pass_c_2048"):
         cav.set_option(name, 0)
     cav.set_option("group_width", 16)
+
+
+def test_field_paths_agree(gb):
+    """The complex64 field of a square grid from the fused kernel (option 1)
+    and from the two-pass kernels (option 2) agree to FP32 rounding; the
+    default takes the two-pass kernels below 512 points per side.  The option
+    re-prepares the context (the FP32 profiles change layout)."""
+    g = gb.Cavity(1.0, 1.0, 0.5, 128, 128, 16, precision="mixed", gmres_tol=1e-10)
+    rng = np.random.default_rng(9)
+    th, ph, al = rng.uniform(0, 1, 4), rng.uniform(0, 6, 4), np.zeros(4)
+    fields = {}
+    for o in (0, 1, 2):
+        g.set_option("field_fused", o)
+        assert g.get_option("field_fused") == o
+        ap, fl, it, res = g.solve(KAPPA0, LAYERS, th, ph, al)
+        assert np.all(np.asarray(res) <= 1e-10)
+        fields[o] = fl.to(torch.complex128)
+    assert rel(fields[1], fields[2]) < 1e-6
+    assert rel(fields[0], fields[2]) < 1e-12
