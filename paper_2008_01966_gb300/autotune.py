@@ -12,7 +12,11 @@ Options and what is timed:
       application of the FP32 operator to the batch (cavity_apply), per value;
   group_width (mixed precision): the aperture solve of the batch (cavity_solve
       without the field), per value among GROUP_WIDTHS; a width is kept only if
-      every direction converged.
+      every direction converged;
+  field_fused (mixed precision, square grids of 32..512 points per side): one
+      field synthesis of the batch (cavity_field) with the fused kernel (1)
+      and with the two-pass kernels (2), each after a prepare (the option
+      changes the layout of the FP32 profiles).
 Values are compared by the median of `reps` timed repetitions after one
 warm-up, measured with CUDA events on the context's stream.
 """
@@ -21,6 +25,7 @@ import json
 import os
 
 GROUP_WIDTHS = (16, 8, 4)
+FIELD_PATHS = (1, 2)   # fused kernel, two-pass kernels
 
 
 def shape_key(cav, ndir, layered):
@@ -39,6 +44,8 @@ def candidates(cav):
             out["pass_c_2048"] = (0, 1)
     if cav.precision != 0:
         out["group_width"] = GROUP_WIDTHS
+    if cav.precision != 0 and cav.nx == cav.ny and 32 <= cav.nx <= 512:
+        out["field_fused"] = FIELD_PATHS
     return out
 
 
@@ -99,9 +106,19 @@ def tune(cav, kappa0, layers, theta, phi, alpha, cache=None, reps=3, timer=None)
         return {"key": key, "choice": store[key]["choice"], "ms": store[key].get("ms", {}),
                 "cached": True}
     timer = timer or _Timer(cav)
-    cav.prepare(kappa0, layers)
     cands = candidates(cav)
     choice, ms = {}, {}
+    if "field_fused" in cands:
+        res = {}
+        for v in cands["field_fused"]:
+            cav.set_option("field_fused", v)
+            cav.prepare(kappa0, layers)
+            ap = cav.rhs(theta, phi, alpha)
+            res[v] = timer(lambda: cav.field(ap), reps)
+        best = min(res, key=res.get)
+        cav.set_option("field_fused", best)
+        choice["field_fused"], ms["field_fused"] = best, {str(k): t for k, t in res.items()}
+    cav.prepare(kappa0, layers)
     x = None
     for name in ("pass_b_2048", "pass_c_2048"):
         if name not in cands:

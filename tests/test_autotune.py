@@ -20,7 +20,7 @@ class FakeCav:
         self.nx = self.ny = n
         self.nz = nz
         self.precision = precision
-        self.opts = {"pass_b_2048": 0, "pass_c_2048": 0, "group_width": 16}
+        self.opts = {"pass_b_2048": 0, "pass_c_2048": 0, "group_width": 16, "field_fused": 0}
         self.last_status = 0
         self.prepared = 0
 
@@ -37,6 +37,9 @@ class FakeCav:
         return X()
 
     def apply(self, x, prec):
+        pass
+
+    def field(self, ap):
         pass
 
     def solve(self, *a, **k):
@@ -56,25 +59,31 @@ class FakeTimer:
         self.calls += 1
         o = self.cav.opts
         return (self.table["b"][o["pass_b_2048"]] + self.table["c"][o["pass_c_2048"]] +
-                self.table["g"][o["group_width"]])
+                self.table["g"][o["group_width"]] + self.table.get("f", {}).get(o["field_fused"], 0.0))
 
 
 def test_candidates_by_shape_and_precision():
     assert autotune.candidates(FakeCav(512)) == {"pass_b_2048": (0, 1), "pass_c_2048": (0, 1),
-                                                 "group_width": autotune.GROUP_WIDTHS}
-    assert autotune.candidates(FakeCav(256)) == {"group_width": autotune.GROUP_WIDTHS}
+                                                 "group_width": autotune.GROUP_WIDTHS,
+                                                 "field_fused": autotune.FIELD_PATHS}
+    assert autotune.candidates(FakeCav(256)) == {"group_width": autotune.GROUP_WIDTHS,
+                                                 "field_fused": autotune.FIELD_PATHS}
+    assert autotune.candidates(FakeCav(16)) == {"group_width": autotune.GROUP_WIDTHS}
     assert autotune.candidates(FakeCav(512, precision=0)) == {}
 
 
 def test_tune_keeps_the_fastest_skips_unconverged_and_caches(tmp_path):
     cav = FakeCav()
-    table = {"b": {0: 5.0, 1: 7.0}, "c": {0: 3.0, 1: 1.0}, "g": {16: 9.0, 8: 4.0, 4: 0.5}}
+    table = {"b": {0: 5.0, 1: 7.0}, "c": {0: 3.0, 1: 1.0}, "g": {16: 9.0, 8: 4.0, 4: 0.5},
+             "f": {1: 2.0, 2: 6.0}}
     timer = FakeTimer(cav, table)
     cache = str(tmp_path / "tune.json")
     out = autotune.tune(cav, 1.0, [(8, 1.0), (8, 2.0)], [0.1, 0.2], [0.0, 1.0], [0.0, 0.0],
                         cache=cache, reps=1, timer=timer)
-    # pass B: 0 faster; pass C: 1 faster; width 4 fastest but unconverged -> 8
-    assert out["choice"] == {"pass_b_2048": 0, "pass_c_2048": 1, "group_width": 8}
+    # pass B: 0 faster; pass C: 1 faster; width 4 fastest but unconverged -> 8;
+    # the fused field faster
+    assert out["choice"] == {"pass_b_2048": 0, "pass_c_2048": 1, "group_width": 8,
+                             "field_fused": 1}
     assert cav.opts == out["choice"] and not out["cached"]
     assert out["key"] == "512x512x16/mixed/layered/ndir2"
     stored = json.load(open(cache))

@@ -77,15 +77,16 @@ def test_autotune_chooses_and_caches(gb, cav, tmp_path):
     th, ph, al = rng.uniform(0, 1, 8), rng.uniform(0, 6, 8), np.zeros(8)
     cache = str(tmp_path / "tune.json")
     out = autotune.tune(cav, KAPPA0, LAYERS, th, ph, al, cache=cache, reps=2)
-    assert set(out["choice"]) == {"pass_b_2048", "pass_c_2048", "group_width"}
+    assert set(out["choice"]) == {"pass_b_2048", "pass_c_2048", "group_width", "field_fused"}
     for name, v in out["choice"].items():
         assert cav.get_option(name) == v
         assert min(out["ms"][name].values()) == out["ms"][name][str(v)]
     again = autotune.tune(cav, KAPPA0, LAYERS, th, ph, al, cache=cache, reps=2)
     assert again["cached"] and again["choice"] == out["choice"]
-    for name in ("pass_b_2048", "pass_c_2048"):
+    for name in ("pass_b_2048", "pass_c_2048", "field_fused"):
         cav.set_option(name, 0)
     cav.set_option("group_width", 16)
+    cav.prepare(KAPPA0, LAYERS)
 
 
 def test_field_paths_agree(gb):
