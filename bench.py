@@ -66,7 +66,10 @@ REF_ITERS = {"layered4": 31, "dirs16": 37}
 # capture, per launch of the benchmark (scaled by directions where the
 # capture had fewer; traffic is proportional to the directions).  Only valid
 # for the kernel as captured: emptied whenever the kernel changes.
-NCU_TRAFFIC = {("dirs16", "tbc_B_fp32"): 2 * (52.550656e6 + 21.679616e6)}
+NCU_TRAFFIC = {("dirs16", "tbc_B_fp32"): 2 * (52.550656e6 + 21.679616e6),
+               # one 8-direction launch of the 512^2 pass B (16-level case of
+               # the same kernel; the pass does not depend on the depth)
+               ("layered4", "tbc_B_fp32"): 210.693376e6 + 169.210624e6}
 # FP64 FMA throughput measured on a GB300 with a throughput kernel (16
 # independent FMA chains per thread, 8 blocks of 256 threads per SM, CUDA
 # events, best of 5): 1.254 TFLOP/s (FP32 by the same kernel: 78.4 TFLOP/s).
