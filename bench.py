@@ -206,13 +206,15 @@ def oracle_system(w):
     return cav, sysm, time.perf_counter() - t0
 
 
-def oracle_leg(w, th, ph, al, dirs, results):
+def oracle_leg(w, th, ph, al, dirs, results, modes=0):
     """The CPU oracle on directions `dirs` of the batch: aperture GMRES to a
-    relative residual of 1e-12 and the field on every level, timed (the
-    cpu_baseline), and each GPU result in `results` ({name: (aperture, field)}
-    device tensors of the whole batch) compared with it per direction:
-    rel-L2 of the aperture vector, and of the whole field of the direction,
-    accumulated level by level (plus the worst single level)."""
+    relative residual of 1e-12 (with `modes`, the direct solve of the kept
+    block of the modes m, n <= modes instead, its residual over the kept
+    rows) and the field on every level, timed (the cpu_baseline), and each
+    GPU result in `results` ({name: (aperture, field)} device tensors of the
+    whole batch) compared with it per direction: rel-L2 of the aperture
+    vector, and of the whole field of the direction, accumulated level by
+    level (plus the worst single level)."""
     from oracle.excitation import rhs
     from oracle.field import field_level, synth_mats
     cav, sysm, setup = oracle_system(w)
@@ -221,8 +223,15 @@ def oracle_leg(w, th, ph, al, dirs, results):
     t_solve = t_field = 0.0
     for d in dirs:
         t0 = time.perf_counter()
-        x, res = sysm.solve_gmres(rhs(cav, th[d], ph[d], al[d]), rtol=1e-12)
-        x = x[0]
+        b = rhs(cav, th[d], ph[d], al[d])
+        if modes:
+            keep = sysm.kept_modes(modes, modes)
+            x = sysm.solve_kept(b, modes, modes)[0]
+            r = (sysm.apply(x) - b)[keep]
+            res = np.array([np.linalg.norm(r) / np.linalg.norm(b[keep])])
+        else:
+            x, res = sysm.solve_gmres(b, rtol=1e-12)
+            x = x[0]
         t_solve += time.perf_counter() - t0
         for k, (ap, _) in results.items():
             g = ap[d].cpu().numpy()
@@ -395,8 +404,11 @@ def run_gb300(args, rank, world, local_rank):
     th, ph, al = rank_directions(w, rank, args.ndir or len(w['theta']), spec["seed"])
     ndir = len(th)
     tol = TOL
+    # the aperture solver (Krylov by default; the dense direct solve of a
+    # truncated expansion with --aperture-solver dense --modes M)
+    solver = dict(aperture_solver=args.aperture_solver, modes_m=args.modes, modes_n=args.modes)
     cav = gb.Cavity(w['a'], w['b'], w['c'], w['nx'], w['ny'], w['nz'], precision="mixed",
-                    gmres_tol=tol)
+                    gmres_tol=tol, **solver)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     cav.prepare(w['kappa0'], w['layers'])
@@ -458,7 +470,7 @@ def run_gb300(args, rank, world, local_rank):
     fp64_path = ap64 = fl64 = None
     if args.fp64_steps > 0:
         ref = gb.Cavity(w['a'], w['b'], w['c'], w['nx'], w['ny'], w['nz'], precision="fp64",
-                        gmres_tol=1e-12)
+                        gmres_tol=1e-12, **solver)
         ref.prepare(w['kappa0'], w['layers'])
         ap64 = torch.empty((ndir, cav.n_ap), dtype=torch.complex128, device=dev)
         fl64 = torch.empty((ndir, cav.field_per_dir), dtype=torch.complex128, device=dev)
@@ -512,7 +524,11 @@ def run_gb300(args, rank, world, local_rank):
             "data": "synthetic",
             "config": {"workload": spec["desc"] + ", mixed precision, aperture tol %.0e" % tol +
                                    (" [depth overridden: nz=%d, profiling case]" % w['nz']
-                                    if args.nz else ""),
+                                    if args.nz else "") +
+                                   (", aperture expansion truncated to m, n <= %d" % args.modes
+                                    if args.modes else "") +
+                                   (", dense direct aperture solve (FP32 LU, FP64 refinement)"
+                                    if args.aperture_solver == "dense" else ""),
                        "dof_per_step_per_gpu": dof_step,
                        "l2": "working set larger than L2 (%.1f GB field written per step)"
                              % (ndir * cav.field_per_dir * 8 / 1e9),
@@ -535,23 +551,27 @@ def run_gb300(args, rank, world, local_rank):
         res_in = {"mixed": (ap, fl)}
         if ap64 is not None:
             res_in["fp64_path"] = (ap64, fl64)
-        o = oracle_leg(w, th, ph, al, dirs, res_in)
+        o = oracle_leg(w, th, ph, al, dirs, res_in, modes=args.modes)
         em = o["errors"]["mixed"]
         e64 = o["errors"].get("fp64_path")
         ok = max(em["aperture"] + em["field"]) <= 1e-5
         if e64 is not None:
             ok = ok and max(e64["aperture"] + e64["field"]) <= 1e-10
         line["accuracy"] = {
-            "vs": "FP64 oracle (CPU, complex128; GMRES to 1e-12, max resid %.1e), directions %s"
+            "vs": ("FP64 oracle (CPU, complex128; " +
+                   ("direct solve of the kept block" if args.modes else "GMRES to 1e-12") +
+                   ", max resid %.1e), directions %s")
                   % (o["oracle_resid_max"], o["dirs"]),
             "mixed": em, "fp64_path": e64, "bound_mixed": 1e-5, "bound_fp64": 1e-10,
             "ok": bool(ok)}
         line["cpu_baseline"] = {
             "value": o["dof"] / (o["solve_s"] + o["field_s"]), "unit": "DOF/s",
             "cores": cores(), "kind": "oracle",
-            "sample": "%d of the %d directions: aperture GMRES to 1e-12 (%.1f s) + full field "
+            "sample": "%d of the %d directions: aperture %s (%.1f s) + full field "
                       "(%.1f s); oracle setup %.1f s excluded"
-                      % (len(dirs), ndir, o["solve_s"], o["field_s"], o["setup_s"])}
+                      % (len(dirs), ndir,
+                         "direct solve of the kept block" if args.modes else "GMRES to 1e-12",
+                         o["solve_s"], o["field_s"], o["setup_s"])}
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0
@@ -571,6 +591,11 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--ndir", type=int, default=0,
                     help="directions per GPU (0: the workload's batch; fewer only for profiling)")
+    ap.add_argument("--aperture-solver", default="krylov", choices=["krylov", "dense"],
+                    help="the aperture solve: Krylov (default) or the dense direct solve of the "
+                         "kept block (with --modes)")
+    ap.add_argument("--modes", type=int, default=0,
+                    help="truncate the aperture expansion to the modes m, n <= MODES (0: all)")
     ap.add_argument("--nz", type=int, default=0,
                     help="override the grid depth (layers scaled alike; only for small profiling "
                          "captures -- not the benchmark configuration)")
