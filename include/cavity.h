@@ -291,7 +291,9 @@ cavity_status cavity_field(cavity_ctx* ctx, int ndir, const void* aperture,
  *   returns CAVITY_ESINGULAR).  1 <= n <= CAVITY_DENSE_MAX_N.
  * cavity_lu_solve: overwrites the nrhs right-hand sides b (device, complex64,
  *   right-hand side r at b + r ldb, ldb >= n) with the solutions of
- *   A x = b from cavity_lu_factor's output. */
+ *   A x = b from cavity_lu_factor's output.  ipiv is read on the device and
+ *   checked before b is touched: an entry outside 0..n-1 returns
+ *   CAVITY_EINVAL with b unchanged.  b must not overlap lu or ipiv. */
 cavity_status cavity_dense_size(const cavity_ctx* ctx, int* n);
 cavity_status cavity_dense_assemble(cavity_ctx* ctx, void* a, int lda);
 cavity_status cavity_lu_factor(cavity_ctx* ctx, void* a, int n, int lda, int* ipiv, int* info);

@@ -63,6 +63,36 @@ def check_operator_io(x, y, dtype, n_ap, device):
         raise ValueError("y must not overlap x (the operator reads x while it writes y)")
 
 
+def _overlap(s, t):
+    s0, t0 = s.data_ptr(), t.data_ptr()
+    return s0 < t0 + t.numel() * t.element_size() and t0 < s0 + s.numel() * s.element_size()
+
+
+def check_lu_io(lu, ipiv, b, device):
+    """Argument checks of an LU solve that writes b through its raw pointer:
+    lu a contiguous square complex64 tensor, ipiv a contiguous int32 tensor of
+    n entries, b a contiguous nrhs x n complex64 tensor, all on `device`, and b
+    overlapping neither lu nor ipiv.  Raises ValueError before anything reaches
+    the library (the library checks ipiv's values itself)."""
+    for name, t in (("lu", lu), ("ipiv", ipiv), ("b", b)):
+        if not isinstance(t, torch.Tensor):
+            raise ValueError("%s must be a tensor" % name)
+        if t.device != device:
+            raise ValueError("%s must be on %s, not %s" % (name, device, t.device))
+        if not t.is_contiguous():
+            raise ValueError("%s must be contiguous" % name)
+    if lu.dtype != torch.complex64 or lu.dim() != 2 or lu.shape[0] != lu.shape[1] or \
+            lu.shape[0] < 1:
+        raise ValueError("lu must be a square complex64 tensor")
+    n = lu.shape[0]
+    if ipiv.dtype != torch.int32 or ipiv.dim() != 1 or ipiv.shape[0] != n:
+        raise ValueError("ipiv must be an int32 tensor of %d entries" % n)
+    if b.dtype != torch.complex64 or b.dim() != 2 or b.shape[1] != n or b.shape[0] < 1:
+        raise ValueError("b must be an nrhs x %d complex64 tensor" % n)
+    if _overlap(b, lu) or _overlap(b, ipiv):
+        raise ValueError("b must not overlap lu or ipiv")
+
+
 class Cavity:
     """One cavity geometry and grid with its resident device state."""
 
@@ -287,9 +317,8 @@ class Cavity:
     def lu_solve(self, lu, ipiv, b):
         """Solve with lu_factor's output for the rows of b (nrhs x n
         complex64 device tensor, overwritten and returned)."""
+        check_lu_io(lu, ipiv, b, self.device)
         n = lu.shape[0]
-        if b.dtype != torch.complex64 or b.dim() != 2 or b.shape[1] != n or not b.is_contiguous():
-            raise ValueError("b must be a contiguous nrhs x %d complex64 tensor" % n)
         self._check(self.lib.cavity_lu_solve(self.h, ctypes.c_void_p(lu.data_ptr()), n, n,
                                              ctypes.c_void_p(ipiv.data_ptr()), b.shape[0],
                                              ctypes.c_void_p(b.data_ptr()), n))
@@ -299,9 +328,11 @@ class Cavity:
     def set_option(self, name, value):
         """Implementation option (include/cavity.h, CAVITY_OPT_*): "pass_b_2048",
         "pass_c_2048" (0 warp pairs, 1 block transform), "group_width"
-        (1..16 directions per block Krylov group) or "coarse_modes" (0, or
+        (1..16 directions per block Krylov group), "coarse_modes" (0, or
         mc > 0: the mixed solve's two-level preconditioner with the exact
-        solve of the modes m, n <= mc as its coarse level)."""
+        solve of the modes m, n <= mc as its coarse level) or "field_fused"
+        (complex64 field synthesis: 0 the default per grid, 1 the fused
+        kernel where the grid allows it, 2 the two passes)."""
         self._check(self.lib.cavity_set_option(self.h, _lib.OPTIONS[name], int(value)))
 
     def get_option(self, name):

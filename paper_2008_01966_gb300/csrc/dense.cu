@@ -778,18 +778,27 @@ __global__ void __launch_bounds__(256) k_lu_trsm(float2* __restrict__ A, int lda
   }
 }
 
-// perm = the row exchanges ipiv applied in order to 0..n-1 (one CTA)
-__global__ void k_lu_perm(const int* __restrict__ ipiv, int* __restrict__ perm, int n) {
+// perm = the row exchanges ipiv applied in order to 0..n-1 (one CTA).  An
+// entry outside 0..n-1 is skipped and, when bad is given, *bad = 1 (else 0).
+__global__ void k_lu_perm(const int* __restrict__ ipiv, int* __restrict__ perm, int n,
+                          int* __restrict__ bad) {
   extern __shared__ int pm[];
   for (int i = threadIdx.x; i < n; i += blockDim.x) pm[i] = i;
   __syncthreads();
-  if (threadIdx.x == 0)
+  if (threadIdx.x == 0) {
+    int out = 0;
     for (int i = 0; i < n; ++i) {
       const int p = ipiv[i];
+      if (p < 0 || p >= n) {
+        out = 1;
+        continue;
+      }
       const int x = pm[i];
       pm[i] = pm[p];
       pm[p] = x;
     }
+    if (bad) *bad = out;
+  }
   __syncthreads();
   for (int i = threadIdx.x; i < n; i += blockDim.x) perm[i] = pm[i];
 }
@@ -1146,8 +1155,9 @@ cavity_status dense_lu_solve(cavity_ctx* ctx, const float2* lu, int n, int lda, 
     return CAVITY_EINVAL;
   }
   cudaStream_t st = ctx->stream;
-  // scratch: the permutation (unless given) and the permuted right-hand sides
-  const size_t bp = al256(sizeof(int) * n), by = al256(sizeof(float2) * (size_t)n * nrhs);
+  // scratch: the permutation (unless given) with its range flag, and the
+  // permuted right-hand sides
+  const size_t bp = al256(sizeof(int) * (n + 1)), by = al256(sizeof(float2) * (size_t)n * nrhs);
   const size_t bd = al256(dinv_bytes(n));
   CKS(ensure_ws(ctx, &ctx->ws, &ctx->ws_bytes, bp + by + bd + subst_scratch_bytes(nrhs)));
   int* pm = (int*)ctx->ws;
@@ -1160,8 +1170,19 @@ cavity_status dense_lu_solve(cavity_ctx* ctx, const float2* lu, int n, int lda, 
     g_lu_smem = true;
   }
   if (!perm) {
-    KScope ks_(ctx, KC_DENSE_TRS);
-    k_lu_perm<<<1, 256, sizeof(int) * n, st>>>(ipiv, pm, n);
+    {
+      KScope ks_(ctx, KC_DENSE_TRS);
+      k_lu_perm<<<1, 256, sizeof(int) * n, st>>>(ipiv, pm, n, pm + n);
+    }
+    CK(cudaGetLastError());
+    // a caller's ipiv is checked before b is touched
+    int bad = 0;
+    CK(cudaMemcpyAsync(&bad, pm + n, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (bad) {
+      ctx->err = "LU solve: an ipiv entry is outside 0..n-1";
+      return CAVITY_EINVAL;
+    }
     perm = pm;
   }
   CKS(launch_dinv(ctx, lu, n, lda, dinv));
@@ -1240,7 +1261,7 @@ cavity_status dense_factor(cavity_ctx* ctx, DenseLU& f, const KeptSet& ks, bool 
   CKS(dense_lu(ctx, f.a, ks.nk, lda, f.ipiv, &info));
   {
     KScope ks_(ctx, KC_DENSE_LU);
-    k_lu_perm<<<1, 256, sizeof(int) * ks.nk, ctx->stream>>>(f.ipiv, f.perm, ks.nk);
+    k_lu_perm<<<1, 256, sizeof(int) * ks.nk, ctx->stream>>>(f.ipiv, f.perm, ks.nk, nullptr);
   }
   CK(cudaGetLastError());
   CKS(launch_dinv(ctx, f.a, ks.nk, lda, f.dinv));

@@ -118,6 +118,33 @@ def test_lu_reports_a_zero_pivot_column(gb):
     assert info == 70
 
 
+def test_lu_solve_rejects_pivots_out_of_range(gb):
+    """A pivot sequence with an entry outside 0..n-1 (here n and -1) is
+    caught on the device before b is touched: CAVITY_EINVAL, b unchanged;
+    the same call with the factor's own pivots then solves."""
+    rng = np.random.default_rng(11)
+    n = 96
+    A = (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))).astype(np.complex64)
+    g = gcav(gb, CASES["homog"])
+    a = torch.from_numpy(A).to(g.device)
+    ipiv, info = g.lu_factor(a)
+    assert info == -1
+    B = (rng.standard_normal((2, n)) + 1j * rng.standard_normal((2, n))).astype(np.complex64)
+    for bad in (n, -1):
+        wrong = ipiv.clone()
+        wrong[n // 2] = bad
+        b = torch.from_numpy(B.copy()).to(g.device)
+        with pytest.raises(gb.CavityError) as e:
+            g.lu_solve(a, wrong, b)
+        assert e.value.status == gb._lib.CAVITY_EINVAL
+        assert torch.equal(b.cpu(), torch.from_numpy(B))
+    b = torch.from_numpy(B.copy()).to(g.device)
+    g.lu_solve(a, ipiv, b)
+    X = b.cpu().numpy().astype(np.complex128)
+    res = np.linalg.norm(A.astype(np.complex128) @ X.T - B.T) / np.linalg.norm(B)
+    assert res < 1e-4, res
+
+
 @pytest.mark.parametrize("case,mm,nn", [("homog", 5, 7), ("rect", 15, 7), ("layer3", 15, 15),
                                         ("layer3", 1, 1)])
 def test_kept_block_matches_oracle(gb, case, mm, nn):

@@ -83,6 +83,35 @@ def test_operator_io_checks_raise_before_the_library_is_called():
                              cpu)
 
 
+def test_lu_io_checks_raise_before_the_library_is_called():
+    """The binding checks lu, ipiv and b before the LU solve gets their raw
+    pointers: device, dtype, shape, stride, and b overlapping lu or ipiv."""
+    torch = pytest.importorskip("torch")
+    import paper_2008_01966_gb300 as gb
+    cpu = torch.device("cpu")
+    n = 6
+    lu = torch.zeros((n, n), dtype=torch.complex64)
+    ipiv = torch.zeros(n, dtype=torch.int32)
+    b = torch.zeros((2, n), dtype=torch.complex64)
+    gb.check_lu_io(lu, ipiv, b, cpu)
+    bad = [
+        (lu.to(torch.complex128), ipiv, b),                          # lu dtype
+        (torch.zeros((n, n + 1), dtype=torch.complex64), ipiv, b),   # lu not square
+        (lu.t(), ipiv, b),                                           # lu not contiguous
+        (lu, ipiv.to(torch.int64), b),                               # ipiv dtype
+        (lu, torch.zeros(n - 1, dtype=torch.int32), b),              # ipiv length
+        (lu, ipiv, b.to(torch.complex128)),                          # b dtype
+        (lu, ipiv, torch.zeros((2, n + 1), dtype=torch.complex64)),  # b width
+        (lu, ipiv, torch.zeros((n, 2), dtype=torch.complex64).t()),  # b not contiguous
+        (lu, ipiv, torch.zeros((2, n), dtype=torch.complex64, device="meta")),  # device
+        (lu, ipiv, lu[:2]),                                          # b inside lu
+        (lu, ipiv, "not a tensor"),
+    ]
+    for args in bad:
+        with pytest.raises(ValueError):
+            gb.check_lu_io(*args, cpu)
+
+
 def test_noalloc_precision_names_are_checked():
     """Only 'fp64' and 'mixed' reach the allocation-free entry point; any
     other name raises in the binding (no silent mapping to mixed)."""
