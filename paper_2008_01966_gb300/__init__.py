@@ -63,6 +63,31 @@ def check_operator_io(x, y, dtype, n_ap, device):
         raise ValueError("y must not overlap x (the operator reads x while it writes y)")
 
 
+def _angles(*arrays):
+    """Host float64 copies of per-direction angle arrays, all of one length."""
+    out = [_dptr(a) for a in arrays]
+    if len({len(a) for a, _ in out}) != 1:
+        raise ValueError("the per-direction angle arrays differ in length: %s"
+                         % [len(a) for a, _ in out])
+    return out
+
+
+def check_out(name, t, shape, dtype, host, device):
+    """Argument checks of an output tensor the library writes through its raw
+    pointer: exactly `shape` and `dtype`, contiguous, and on the host (host
+    True) or on `device`.  Raises ValueError."""
+    if not isinstance(t, torch.Tensor):
+        raise ValueError("%s must be a tensor" % name)
+    where = torch.device("cpu") if host else device
+    if t.device != where:
+        raise ValueError("%s must be on %s, not %s" % (name, where, t.device))
+    if t.dtype != dtype or tuple(t.shape) != tuple(shape):
+        raise ValueError("%s must be %s of shape %s, not %s of shape %s" % (
+            name, dtype, tuple(shape), t.dtype, tuple(t.shape)))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+
+
 def _overlap(s, t):
     s0, t0 = s.data_ptr(), t.data_ptr()
     return s0 < t0 + t.numel() * t.element_size() and t0 < s0 + s.numel() * s.element_size()
@@ -158,9 +183,7 @@ class Cavity:
         iterations and relative residuals.  host=True returns pinned host
         tensors filled through the library's own device-to-host copies."""
         lev, er, ei, pl, pr, pim = _layers(layers)
-        th, pth = _dptr(theta)
-        ph, pph = _dptr(phi)
-        al, pal = _dptr(alpha)
+        (th, pth), (ph, pph), (al, pal) = _angles(theta, phi, alpha)
         ndir = len(th)
         if host:
             ap = aperture_out if aperture_out is not None else torch.empty(
@@ -176,6 +199,12 @@ class Cavity:
             if field:
                 fl = field_out if field_out is not None else torch.empty(
                     (ndir, self.field_per_dir), dtype=self.field_dtype, device=self.device)
+        check_out("aperture_out", ap, (ndir, self.n_ap), torch.complex128, host, self.device)
+        if fl is not None:
+            check_out("field_out", fl, (ndir, self.field_per_dir), self.field_dtype, host,
+                      self.device)
+            if _overlap(ap, fl):
+                raise ValueError("aperture_out and field_out must not overlap")
         iters = np.zeros(ndir, dtype=np.int32)
         res = np.zeros(ndir, dtype=np.float64)
         st = self.lib.cavity_solve(
@@ -189,12 +218,13 @@ class Cavity:
         return ap, fl, iters, res
 
     def rcs(self, aperture, theta, phi, pol="theta"):
-        th, pth = _dptr(theta)
-        ph, pph = _dptr(phi)
+        (th, pth), (ph, pph) = _angles(theta, phi)
         out = np.zeros(len(th))
         aperture = aperture.contiguous()
-        if aperture.dtype != torch.complex128 or aperture.shape != (len(th), self.n_ap):
-            raise ValueError("aperture must be a (ndir, n_ap) complex128 tensor")
+        if aperture.dtype != torch.complex128 or aperture.shape != (len(th), self.n_ap) or \
+                (aperture.is_cuda and aperture.device != self.device):
+            raise ValueError("aperture must be a (ndir, n_ap) complex128 tensor on the host "
+                             "or on %s" % self.device)
         mem = _lib.CAVITY_MEM_DEVICE if aperture.is_cuda else _lib.CAVITY_MEM_HOST
         self._check(self.lib.cavity_rcs(
             self.h, len(th), ctypes.c_void_p(aperture.data_ptr()), mem, pth, pph,
@@ -204,9 +234,7 @@ class Cavity:
 
     # ------------------------------------------------------------ step level
     def rhs(self, theta, phi, alpha):
-        th, pth = _dptr(theta)
-        ph, pph = _dptr(phi)
-        al, pal = _dptr(alpha)
+        (th, pth), (ph, pph), (al, pal) = _angles(theta, phi, alpha)
         out = torch.empty((len(th), self.n_ap), dtype=torch.complex128, device=self.device)
         self._check(self.lib.cavity_rhs(self.h, len(th), pth, pph, pal, ctypes.c_void_p(out.data_ptr())))
         return out
@@ -220,8 +248,9 @@ class Cavity:
             "pair32": _lib.CAVITY_PAIR32}[precision]
         x = x.contiguous()
         want = torch.complex64 if prec == _lib.CAVITY_MIXED else torch.complex128
-        if x.dtype != want or not x.is_cuda or x.dim() != 2 or x.shape[1] != self.n_ap:
-            raise ValueError("x must be a CUDA (ndir, n_ap) tensor of %s" % want)
+        if x.dtype != want or x.device != self.device or x.dim() != 2 or \
+                x.shape[1] != self.n_ap:
+            raise ValueError("x must be a (ndir, n_ap) tensor of %s on %s" % (want, self.device))
         y = torch.empty_like(x)
         self._check(self.lib.cavity_apply(self.h, x.shape[0], prec, ctypes.c_void_p(x.data_ptr()),
                                           ctypes.c_void_p(y.data_ptr())))
@@ -257,9 +286,10 @@ class Cavity:
 
     def field(self, aperture):
         aperture = aperture.contiguous()
-        if aperture.dtype != torch.complex128 or not aperture.is_cuda or \
+        if aperture.dtype != torch.complex128 or aperture.device != self.device or \
                 aperture.dim() != 2 or aperture.shape[1] != self.n_ap:
-            raise ValueError("aperture must be a CUDA (ndir, n_ap) complex128 tensor")
+            raise ValueError("aperture must be a (ndir, n_ap) complex128 tensor on %s"
+                             % self.device)
         out = torch.empty((aperture.shape[0], self.field_per_dir), dtype=self.field_dtype,
                           device=self.device)
         self._check(self.lib.cavity_field(self.h, aperture.shape[0],

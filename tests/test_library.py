@@ -131,3 +131,49 @@ def test_noalloc_precision_names_are_checked():
     with pytest.raises(ValueError):          # a CPU context never reaches the library
         g.apply_noalloc(x, "fp64")
     g.h = None
+
+
+def test_solve_outputs_and_angles_are_checked_before_the_library():
+    """solve's caller-supplied output tensors (shape, dtype, place,
+    contiguity, no overlap) and the per-direction angle arrays of solve, rhs
+    and rcs (one length) are checked in the binding; a bad one never reaches
+    the library."""
+    torch = pytest.importorskip("torch")
+    import paper_2008_01966_gb300 as gb
+
+    class NoLib:
+        def __getattr__(self, name):
+            raise AssertionError("library called: " + name)
+    g = object.__new__(gb.Cavity)
+    g.lib, g.h, g.n_ap, g.precision, g.field_per_dir = NoLib(), None, 4, gb._lib.CAVITY_MIXED, 6
+    g.device = torch.device("meta")          # the "device" side of the checks
+    lay = [(2, 1.0)]
+    th = ph = al = [0.1, 0.2]
+    dev = dict(dtype=torch.complex128, device="meta")
+    good_ap = torch.empty((2, 4), **dev)
+    bad = [
+        dict(aperture_out=torch.empty((1, 4), **dev)),                       # ndir
+        dict(aperture_out=torch.empty((2, 5), **dev)),                       # n_ap
+        dict(aperture_out=torch.empty((2, 4), dtype=torch.complex64, device="meta")),
+        dict(aperture_out=torch.empty((4, 2), **dev).t()),                   # stride
+        dict(aperture_out=torch.empty((2, 4), dtype=torch.complex128)),      # host tensor
+        dict(aperture_out=good_ap, field_out=torch.empty((2, 6), **dev)),    # field dtype
+        dict(aperture_out=good_ap, field_out=torch.empty((2, 7), dtype=torch.complex64,
+                                                         device="meta")),
+    ]
+    for kw in bad:
+        with pytest.raises(ValueError):
+            g.solve(1.0, lay, th, ph, al, field=True, **kw)
+    with pytest.raises(ValueError):          # a device tensor for a host solve
+        g.solve(1.0, lay, th, ph, al, field=False, host=True, aperture_out=good_ap)
+    cpu_ap = torch.zeros((2, 4), dtype=torch.complex128)
+    with pytest.raises(ValueError):          # the two outputs share memory
+        big = torch.zeros(40, dtype=torch.complex128)
+        g.solve(1.0, lay, th, ph, al, field=True, host=True, aperture_out=big[:8].view(2, 4),
+                field_out=big[4:10].view(torch.complex64).view(2, 6))
+    for f in (lambda: g.solve(1.0, lay, [0.1, 0.2], [0.3], [0.0, 0.0], field=False),
+              lambda: g.rhs([0.1, 0.2], [0.3, 0.4], [0.0]),
+              lambda: g.rcs(cpu_ap, [0.1, 0.2], [0.3])):
+        with pytest.raises(ValueError):
+            f()
+    g.h = None
