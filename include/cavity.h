@@ -255,8 +255,8 @@ cavity_status cavity_apply(cavity_ctx* ctx, int ndir, int precision,
  * (held on every device that loads it, until exit) as scratch; sizes whose
  * scratch exceeds 4 MiB (e.g. more than about 2 directions at 64 x 64 in
  * FP64) are rejected with CAVITY_EINVAL and a message.  The first call on a
- * device looks up the array's device address (make that first call before
- * any stream capture); the context's device must be current.  The call
+ * device looks up the array's device address; the context's device must be
+ * current.  The call
  * synchronises the context's stream before it returns.  All calls share the
  * one array: calls that overlap on the GPU (other streams, other contexts,
  * other threads) race and must be serialised by the caller.  Nothing carries
