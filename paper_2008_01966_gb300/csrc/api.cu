@@ -200,10 +200,8 @@ extern "C" cavity_status cavity_prepare(cavity_ctx* ctx, double kappa0, int nlay
   ctx->dn.ready = false;
   ctx->cs.ready = false;
   bool kappa_same = ctx->khat64 && ctx->kappa0 == kappa0;
-  const bool was_layered = ctx->layers.size() > 1;
   ctx->kappa0 = kappa0;
   ctx->layers = L;
-  (void)was_layered;
   if (!kappa_same) CKS(launch_khat(ctx, kappa0));
   CKS(launch_zsweep(ctx, kappa0));
   if (ctx->g.fft_ok) {   // the Krylov path's preconditioner and operator tables
