@@ -1,4 +1,4 @@
-"""Mutation check of the oracle pins (run by hand; about 15 minutes):
+"""Mutation check of the oracle pins (run by hand; about 20 minutes):
 
     python tests/mutation_check.py
 
@@ -101,6 +101,26 @@ MUTATIONS = [
     ('tbc.py', "return (self._fx[kx].conj().T / self.Lx) @ V @ (self._fy[ky].conj() / self.Ly)", "return (self._fx[kx].T / self.Lx) @ V @ (self._fy[ky] / self.Ly)"),
     ('tbc.py', "            Xx = self._fx[kx].conj().T / self.Lx\n", "            Xx = self._fx[kx].conj().T\n"),
     ('tbc.py', "return (self._fx[kx].conj().T / self.Lx) @ V @ (self._fy[ky].conj() / self.Ly)", "return (self._fx[kx].conj().T / self.Lx) @ V @ (self._fy[ky].conj() / self.Lx)"),
+    # the backscatter RCS, the kept block's remaining terms, the level map,
+    # the trapezoid rule's far end and the x2 factors of the excitation
+    ('rcs.py', "return 0.5 * (_ef(g - k, a) + _ef(g + k, a))", "return 0.5 * (_ef(g - k, a) - _ef(g + k, a))"),
+    ('rcs.py', "return (_ef(g - k, a) - _ef(g + k, a)) / 2j", "return (_ef(g - k, a) - _ef(g + k, a)) / -2j"),
+    ('rcs.py', "(1.0 - np.exp(-1j * safe * a)) / (1j * safe)", "(1.0 - np.exp(1j * safe * a)) / (1j * safe)"),
+    ('rcs.py', "g1, g2 = cav.kappa0 * xh[0], cav.kappa0 * xh[1]", "g1, g2 = cav.kappa0 * xh[1], cav.kappa0 * xh[0]"),
+    ('rcs.py', "e = np.array([np.cos(theta) * np.cos(phi), np.cos(theta) * np.sin(phi), -np.sin(theta)])", "e = np.array([np.cos(theta) * np.cos(phi), np.cos(theta) * np.sin(phi), np.sin(theta)])"),
+    ('rcs.py', "e = np.array([-np.sin(phi), np.cos(phi), 0.0])", "e = np.array([np.sin(phi), np.cos(phi), 0.0])"),
+    ('rcs.py', "return cav.kappa0 ** 2 / np.pi * abs(v) ** 2", "return cav.kappa0 ** 2 / (4 * np.pi) * abs(v) ** 2"),
+    ('rcs.py', "S1y = sin_int(np.arange(1, N + 1), g2, cav.b)", "S1y = sin_int(np.arange(1, N + 1), g2, cav.a)"),
+    ('rcs.py', "I2 = S2x @ e2 @ C2y", "I2 = S2x @ e2 @ C2y.conj()"),
+    ('aperture.py', "B12 = (s1 * 2.0 * ny[None, 1:])[:, :, None, None] * \\\n            I3[:, 1:, 1:, :]", "B12 = -(s1 * 2.0 * ny[None, 1:])[:, :, None, None] * \\\n            I3[:, 1:, 1:, :]"),
+    ('aperture.py', "B22 -= (s2 * 2.0 * mx[1:, None])[:, :, None, None] * \\\n            I3[1:, :, 1:, :]", "B22 += (s2 * 2.0 * mx[1:, None])[:, :, None, None] * \\\n            I3[1:, :, 1:, :]"),
+    ('aperture.py', "A[i2, i2] += (-1.0 + p.tau2[m2 - 1, q2]).ravel()", "A[i2, i2] += (1.0 + p.tau2[m2 - 1, q2]).ravel()"),
+    ('aperture.py', "s2 = (h / self.cn[:nn + 1])[None, :]", "s2 = (h / self.cn[:nn + 1])[None, :] * 0.5"),
+    ('geometry.py', "out[bot + 1:top] = li", "out[bot:top] = li"),
+    ('tbc.py', "w[-1] *= 0.5", "w[-1] *= 1.0"),
+    ('tbc.py', "arg = np.pi * np.outer(ms, p) / n_int", "arg = np.pi * np.outer(ms, p) / (n_int + 1)"),
+    ('excitation.py', "cy = trap_matrix('c', np.arange(0, N + 1), cav.ny, cav.b) @ ey", "cy = trap_matrix('c', np.arange(0, N + 1), cav.ny, cav.b) @ ey.conj()"),
+    ('excitation.py', "ey = np.exp(1j * a2 * y)", "ey = np.exp(1j * a1 * y)"),
 ]
 
 KNOWN_SURVIVORS = {
