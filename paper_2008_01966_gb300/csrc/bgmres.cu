@@ -161,6 +161,7 @@ __global__ void __launch_bounds__(128) k_bnn_tc5(BGSet set, const double2* __res
   const uint32_t tmem = tslot;
   constexpr uint32_t idesc = tc_idesc_tf32(128, 32);
   bool ok = true;
+  int last = -1;   // the last chunk whose MMAs were committed
   float racc[32];
 #pragma unroll
   for (int n = 0; n < 32; ++n) racc[n] = 0.f;
@@ -227,6 +228,7 @@ __global__ void __launch_bounds__(128) k_bnn_tc5(BGSet set, const double2* __res
       }
       tc_commit(&mbar[b]);
     }
+    last = c;
     if (c % TC_DRAIN == TC_DRAIN - 1 || c == nch - 1) {
       ok = __syncthreads_and(tc_mbar_wait(&mbar[b], (c >> 1) & 1));
       tc_after_sync();
@@ -249,6 +251,7 @@ __global__ void __launch_bounds__(128) k_bnn_tc5(BGSet set, const double2* __res
     }
   } else if (tid == 0) {
     atomicExch(&g_tc_err, 1);
+    tc_settle(mbar, last);   // MMAs in flight end before the tensor memory is freed
   }
   tc_before_sync();
   __syncthreads();

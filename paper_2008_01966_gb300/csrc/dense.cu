@@ -222,8 +222,9 @@ __global__ void __launch_bounds__(256, 2) k_zgemm(GemmArgsT<double> g) {
 // complex inner terms (16 real, two MMA k-steps, three products each) pass
 // through two shared-memory buffers: the threads stage chunk c + 1 while the
 // tensor cores multiply chunk c.  Thread t stages row t of the A tile and two
-// entries of the B tile.  A wait that runs out sets g_gt_err and skips the
-// output.  In the LU of an 8,216-unknown block the 128 rank-64 trailing updates
+// entries of the B tile.  A wait that runs out sets g_gt_err, skips the
+// output, and waits (bounded) for the MMAs in flight before the tensor memory
+// is freed.  In the LU of an 8,216-unknown block the 128 rank-64 trailing updates
 // take about 48 ms in total on this kernel, the same as on an FMA-pipe kernel
 // with 128 x 64 tiles: with 64 inner terms a tile is bound by its staging and
 // by the round trip of its C tile, not by the products.
@@ -255,6 +256,7 @@ __global__ void __launch_bounds__(128) k_cgemm_tc(GemmArgs g) {
   const uint32_t tmem = tslot;
   constexpr uint32_t idesc = tc_idesc_tf32(128, 64);
   bool ok = true;
+  int last = -1;   // the last chunk whose MMAs were committed
   float racc[64];
 #pragma unroll
   for (int n = 0; n < 64; ++n) racc[n] = 0.f;
@@ -326,6 +328,7 @@ __global__ void __launch_bounds__(128) k_cgemm_tc(GemmArgs g) {
       }
       tc_commit(&mbar[b]);
     }
+    last = c;
     if (c % TC_DRAIN == TC_DRAIN - 1 || c == nch - 1) {
       ok = __syncthreads_and(tc_mbar_wait(&mbar[b], (c >> 1) & 1));
       tc_after_sync();
@@ -360,6 +363,7 @@ __global__ void __launch_bounds__(128) k_cgemm_tc(GemmArgs g) {
     }
   } else if (tid == 0) {
     atomicExch(&g_gt_err, 1);
+    tc_settle(mbar, last);   // MMAs in flight end before the tensor memory is freed
   }
   tc_before_sync();
   __syncthreads();

@@ -97,6 +97,14 @@ __device__ __forceinline__ bool tc_mbar_wait(uint64_t* mbar, uint32_t parity) {
   }
   return done != 0;
 }
+// After a wait ran out: the issuing thread waits, again bounded, for the MMAs
+// it still has in flight before the tensor memory is freed.  A commit
+// arrives once every MMA issued before it has completed, so the last one
+// covers all: `last` is the last chunk whose MMAs were committed (to
+// mbar[last & 1], phase last >> 1), -1 if none.
+__device__ __forceinline__ void tc_settle(uint64_t* mbar, int last) {
+  if (last >= 0) (void)tc_mbar_wait(&mbar[last & 1], (last >> 1) & 1);
+}
 // operand tiles written by threads become visible to the tensor cores
 __device__ __forceinline__ void tc_fence_smem() { asm volatile("fence.proxy.async.shared::cta;"); }
 __device__ __forceinline__ void tc_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;"); }
