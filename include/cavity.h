@@ -35,9 +35,9 @@
  *  - a context is not thread safe: one host thread at a time per context.
  *  - one device per process: the library raises the shared-memory limits of
  *    its kernels once per process, on the device current at that first use,
- *    so every context of a process must be set up on that device (contexts
- *    on another device fail at their first launch with a CUDA error status,
- *    without a fault).  Use one process per GPU.
+ *    so every context of a process must be set up on that device (on another
+ *    device, a launch that needs the raised limit returns a CUDA error
+ *    status, without a fault).  Use one process per GPU.
  */
 #ifndef CAVITY_H
 #define CAVITY_H
