@@ -21,6 +21,16 @@ def test_header_and_binding_agree():
     assert declared_symbols() == sorted(_lib.EXPORTS)
 
 
+def test_every_cuda_unit_is_built():
+    """build.py compiles every .cu file under csrc/ (a unit left out would
+    leave its kernels' explicit instantiations unresolved only at load time)."""
+    from paper_2008_01966_gb300 import build
+    csrc = os.path.join(ROOT, "paper_2008_01966_gb300", "csrc")
+    units = sorted(f for f in os.listdir(csrc) if f.endswith(".cu"))
+    assert sorted(os.path.basename(s) for s in build.SOURCES) == units
+    assert set(os.path.basename(s) for s in build.SPLIT) <= set(units)
+
+
 def test_library_builds_and_exports_every_symbol():
     import __graft_entry__
     __graft_entry__.build()
