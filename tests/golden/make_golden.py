@@ -15,6 +15,14 @@ Cases:
   layered16   the four-layer fill of Sec. 4 at 16 x 16 x 16 (same points
               per wavelength in the densest layer as the 512^2 workload),
               one seeded oblique direction, dense solve of (uT1)
+  small_kept10
+              the small case with the aperture expansion truncated to the
+              modes m, n <= 10 (the few-mode runs of Sec. 7, Table 2): the
+              kept block assembled from its restricted pieces and solved
+              densely (residual of the kept rows)
+  layered16_parseval
+              the layered16 case with the outer integral of Sec. 5.2 taken
+              exactly (the Parseval form), dense solve
 Each case stores n_ap, the solve residual, the backscatter RCS in both
 polarisations, the 2-norm of the aperture vector, aperture coefficients at
 12 seeded indices among those above 1e-6 of the largest, and field samples
@@ -30,14 +38,19 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
 
 import workloads  # noqa: E402
+from oracle.aperture import ApertureSystem  # noqa: E402
+from oracle.excitation import rhs  # noqa: E402
 from oracle.field import field_point  # noqa: E402
 from oracle.geometry import Cavity, Layer  # noqa: E402
 from oracle.rcs import backscatter  # noqa: E402
 from oracle.solver import solve  # noqa: E402
+from oracle.tbc import TBCOperator  # noqa: E402
+
+KEPT = 10   # modes kept per axis in small_kept10
 
 
 def case_inputs(name):
-    if name == 'small':
+    if name.startswith('small'):
         w = workloads.workload('small')
     else:
         w = workloads.scaled('layered4', 16, ndir=1)
@@ -65,8 +78,24 @@ def compute(name):
     cav = Cavity(w['a'], w['b'], w['c'], w['nx'], w['ny'], w['nz'], w['kappa0'],
                  layers=[Layer(n, e) for n, e in w['layers']])
     th, ph, al = w['theta'][:1], w['phi'][:1], w['alpha'][:1]
-    sol = solve(cav, th, ph, al, method='dense')
-    x = sol.x[0]
+    if name == 'small_kept10':
+        sysm = ApertureSystem(cav)
+        b = rhs(cav, th[0], ph[0], al[0])
+        k = sysm.kept_modes(KEPT, KEPT)
+        x = sysm.solve_kept(b, KEPT, KEPT)[0]
+        A = sysm.dense_kept(KEPT, KEPT)
+        resid = np.linalg.norm(A @ x[k] - b[k]) / np.linalg.norm(b[k])
+        prof = sysm.prof
+    elif name == 'layered16_parseval':
+        sysm = ApertureSystem(cav, tbc=TBCOperator(cav, outer='parseval'))
+        b = rhs(cav, th[0], ph[0], al[0])
+        A = sysm.dense()
+        x = np.linalg.solve(A, b)
+        resid = np.linalg.norm(A @ x - b) / np.linalg.norm(b)
+        prof = sysm.prof
+    else:
+        sol = solve(cav, th, ph, al, method='dense')
+        x, resid, prof = sol.x[0], sol.resid[0], sol.prof
     rng = np.random.Generator(np.random.PCG64(77))
     # coefficients that the selection rules of normal incidence do not zero
     # (entries at rounding level would make the fixture machine-dependent)
@@ -75,12 +104,12 @@ def compute(name):
     nodes = sample_nodes(cav, rng)
     vals = dict(
         n_ap=cav.n_ap,
-        resid=float(sol.resid[0]),
+        resid=float(resid),
         rcs_theta=float(backscatter(cav, x, th[0], ph[0], 'theta')),
         rcs_phi=float(backscatter(cav, x, th[0], ph[0], 'phi')),
         norm=float(np.linalg.norm(x)),
         aperture=[(i, complex(x[i])) for i in idx],
-        field=[(c, j, p, q, complex(field_point(cav, sol.prof, x, c, j, p, q)))
+        field=[(c, j, p, q, complex(field_point(cav, prof, x, c, j, p, q)))
                for c, j, p, q in nodes],
     )
     return vals
@@ -120,7 +149,7 @@ def read(path):
     return out
 
 
-CASES = ('small', 'layered16')
+CASES = ('small', 'layered16', 'small_kept10', 'layered16_parseval')
 
 if __name__ == '__main__':
     for name in CASES:
