@@ -252,14 +252,16 @@ def test_khat_static_limit_struve():
 
 def test_khat_against_adaptive_quadrature():
     """T5c: against QUADPACK's adaptive Gauss-Kronrod on the real and imaginary
-    parts (a different quadrature rule and subdivision)."""
+    parts (a different quadrature rule and subdivision), each asked for a
+    tolerance it can reach and certified by its own error estimate."""
     R, kap = np.sqrt(2.0), 25.0
     for rho in (0.0, 1.7, 3.9, 12.25):
         c = 2 * np.pi * rho
-        re = integrate.quad(lambda r: special.j0(c * r) * np.cos(kap * r), 0, R,
-                            limit=400, epsabs=1e-15, epsrel=1e-13)[0]
-        im = integrate.quad(lambda r: special.j0(c * r) * np.sin(kap * r), 0, R,
-                            limit=400, epsabs=1e-15, epsrel=1e-13)[0]
+        re, e_re = integrate.quad(lambda r: special.j0(c * r) * np.cos(kap * r), 0, R,
+                                  limit=400, epsabs=1e-14, epsrel=1e-12)
+        im, e_im = integrate.quad(lambda r: special.j0(c * r) * np.sin(kap * r), 0, R,
+                                  limit=400, epsabs=1e-14, epsrel=1e-12)
+        assert max(e_re, e_im) < 1e-13
         ref = 0.5 * (re + 1j * im)
         assert abs(khat(np.array([rho]), kap, R)[0] - ref) < 1e-12
 
