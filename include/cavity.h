@@ -346,7 +346,9 @@ cavity_status cavity_get_option(const cavity_ctx* ctx, int option, int* value);
  * cavity_timing(ctx, 0) stops.  cavity_timing_read synchronises the stream and
  * returns, per class, the summed event time in ms (0 when timing was off) and
  * the number of launches since the last reset; ms and launches are host arrays
- * of length nclass (<= CAVITY_NUM_KCLASS), either may be NULL. */
+ * of length nclass (<= CAVITY_NUM_KCLASS), either may be NULL.
+ * cavity_kernel_class(k): the name of class k, a static string owned by the
+ * library ("" for k outside 0..CAVITY_NUM_KCLASS-1). */
 #define CAVITY_NUM_KCLASS 24
 cavity_status cavity_timing(cavity_ctx* ctx, int enable);
 cavity_status cavity_timing_read(cavity_ctx* ctx, int nclass, double* ms,
